@@ -1,0 +1,269 @@
+/*
+ * hecnn.h -- C ABI of libhecnn, a GB300 (sm_103a) implementation of the
+ * ciphertext-by-ciphertext hot path of encrypted CNN inference in which both
+ * the images and the model weights are CKKS ciphertexts (Jain, Nandakumar,
+ * Ratha, Pankanti, Kumar, "Efficient CNN Building Blocks for Encrypted Data",
+ * arXiv 2102.00319).
+ *
+ * The calls follow the paper's statement of the problem (Sec. "Homomorphic
+ * Encryption"): f(x_1..x_d) = D(g([[x_1]]..[[x_d]]), sk).  Three parties
+ * (Sec. "Introduction", Fig. 1): the user holds the secret key, the model
+ * owner encrypts weights under the user's public key, the cloud evaluates
+ * with evaluation keys only.
+ *
+ * Conventions for every call
+ * --------------------------
+ * - Return value: HC_OK (0) or a negative HC_ERR_* code; hc_last_error()
+ *   gives a message.  Nothing aborts the process.
+ * - Out-parameters are written only on HC_OK.  Every returned handle is owned
+ *   by the caller and released with the matching hc_*_destroy.  Input
+ *   handles are borrowed and never freed by the library.
+ * - Handles belong to one context; destroy them before the context.
+ * - Work is enqueued on the context's CUDA stream and is asynchronous; calls
+ *   that return host data (export, decrypt+decode, hc_sync) synchronise.
+ * - Device memory comes from the context's allocator (default: a
+ *   stream-ordered pool on the context stream).
+ * - Ciphertexts live on the device in evaluation (NTT) form.  Import and
+ *   export use COEFFICIENT form: layout [poly][limb][coeff] of uint64
+ *   residues in [0, q_limb), limb i over prime q_i.
+ * - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef HECNN_H
+#define HECNN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- errors */
+enum {
+  HC_OK = 0,
+  HC_ERR_INVALID = -1,        /* bad argument, size or handle */
+  HC_ERR_LEVEL_MISMATCH = -2, /* operands at different levels */
+  HC_ERR_SCALE_MISMATCH = -3, /* scales differ by more than 2^-40 relative */
+  HC_ERR_NO_KEY = -4,         /* no Galois key for a requested rotation */
+  HC_ERR_DEPTH = -5,          /* rescale (or a layer) needs a level that is not left */
+  HC_ERR_OOM = -6,            /* allocator returned NULL */
+  HC_ERR_CUDA = -7,           /* a CUDA runtime call failed */
+  HC_ERR_TIMEOUT = -8         /* a bounded device wait ran out */
+};
+
+typedef struct hc_params hc_params;
+typedef struct hc_ctx hc_ctx;
+typedef struct hc_secret_key hc_sk;  /* user only */
+typedef struct hc_public_key hc_pk;  /* user and model owner */
+typedef struct hc_eval_keys hc_evk;  /* cloud: relinearisation + Galois keys, no secret */
+typedef struct hc_pt hc_pt;          /* plaintext polynomial at a level and scale */
+typedef struct hc_ct hc_ct;          /* ciphertext: degree 1 or 2, level, scale */
+
+/* ------------------------------------------------------------ parameters */
+/*
+ * Ring degree N = 2^log_n (the paper's phi(m) with m = 2N, K = N/2 slots;
+ * Sec. "Impact of FHE parameters").  The modulus chain q_0..q_L ("L" in the
+ * paper is the total bit size; here it is the number of rescalable primes)
+ * and the special primes p_0..p_{alpha-1} of hybrid key switching.  Each
+ * prime is the largest unused prime below 2^bits that is 1 mod 2N, chosen in
+ * the order q_0, q_1..q_L, p_0..  Key switching uses dnum = ceil((L+1)/alpha)
+ * digits of alpha consecutive primes from q_0.
+ */
+typedef struct hc_params_desc {
+  int log_n;          /* 10..16 */
+  int n_q;            /* L + 1, 1..60 */
+  const int *q_bits;  /* n_q bit sizes, each 20..61 */
+  int n_p;            /* alpha, 1..16 */
+  const int *p_bits;  /* n_p bit sizes, each 20..61 */
+  double log2_scale;  /* default scale Delta = 2^log2_scale */
+  double sigma;       /* error standard deviation (3.2); tail cut floor(6 sigma) */
+} hc_params_desc;
+
+/* Builds the prime chain and constants (host only).  HC_ERR_INVALID if a
+ * size is out of range or a bit size runs out of primes. */
+int hc_params_create(const hc_params_desc *desc, hc_params **out);
+void hc_params_destroy(hc_params *p);
+/* Writes q_0..q_L, p_0..p_{alpha-1} (n_q + n_p words) into out[cap]. */
+int hc_params_primes(const hc_params *p, uint64_t *out, int cap);
+/* Degree N, L, alpha, dnum. */
+int hc_params_info(const hc_params *p, int *n, int *L, int *alpha, int *dnum);
+/* The 63-bit cumulative table of the error sampler (tail-cut entries). */
+int hc_params_cdt(const hc_params *p, uint64_t *out, int cap);
+
+/* -------------------------------------------------------------- context */
+/* Optional allocator: alloc(bytes, stream, user) returns device memory
+ * usable on `stream` (or NULL), free(ptr, stream, user) releases it in
+ * stream order. */
+typedef struct hc_allocator {
+  void *(*alloc)(size_t bytes, void *stream, void *user);
+  void (*free)(void *ptr, void *stream, void *user);
+  void *user;
+} hc_allocator;
+
+/* Uploads twiddle and basis-conversion tables to `device` and binds the
+ * context to `cuda_stream` (a cudaStream_t, NULL = the legacy default
+ * stream).  `alloc` may be NULL (built-in stream-ordered pool).  The params
+ * object may be destroyed afterwards. */
+int hc_ctx_create(const hc_params *p, int device, void *cuda_stream, const hc_allocator *alloc,
+                  hc_ctx **out);
+void hc_ctx_destroy(hc_ctx *ctx);
+/* Blocks until all work enqueued by the context has finished. */
+int hc_sync(hc_ctx *ctx);
+/* Message of the last failing call on this context ("" if none). */
+const char *hc_last_error(const hc_ctx *ctx);
+/* Number of kernels this context has launched so far. */
+uint64_t hc_kernel_launches(const hc_ctx *ctx);
+
+/* ----------------------------------------------------------------- keys */
+/*
+ * Key generation from one 64-bit seed (Philox4x64-10 counter streams, key =
+ * (seed, domain tag)): secret s uniform ternary; public key
+ * (-a s + e, a) over q_0..q_L; relinearisation key, digit j:
+ * (-a_j s + e_j + P [limb in digit j] s^2, a_j) over q_0..q_L, p_0..;
+ * a Galois key, same with kappa_g(s) in place of s^2, for every rotation
+ * step in rot_steps (left rotation by r uses g = 5^r mod 2N; steps equal
+ * mod K share a key; steps = 0 mod K need none).
+ */
+int hc_keygen(hc_ctx *ctx, uint64_t seed, const int32_t *rot_steps, int n_rot, hc_sk **sk,
+              hc_pk **pk, hc_evk **evk);
+void hc_sk_destroy(hc_sk *);
+void hc_pk_destroy(hc_pk *);
+void hc_evk_destroy(hc_evk *);
+/* Secret coefficients (int8 values -1, 0, 1) into out[N]. */
+int hc_sk_export(hc_ctx *ctx, const hc_sk *sk, int8_t *out, size_t n);
+/* Public key, coefficient form: [2][L+1][N] words (b then a). */
+int hc_pk_export(hc_ctx *ctx, const hc_pk *pk, uint64_t *out, size_t cap_words);
+/* Switching key of rotation `galois_elt` (1 = relinearisation), coefficient
+ * form: [dnum][2][L+1+alpha][N] words (b_j then a_j). */
+int hc_evk_export(hc_ctx *ctx, const hc_evk *evk, uint64_t galois_elt, uint64_t *out,
+                  size_t cap_words);
+
+/* ------------------------------------------------ plaintext / ciphertext */
+/* Canonical-embedding encoding (Sec. "Convolution Operator": slot k holds
+ * value k): m_i = round(scale (2/N) Re sum_j z_j zeta^{-5^j i}), computed by
+ * an FFT in FP64 on the host; n <= K values (the rest zero); im may be NULL.
+ * level in 0..L. */
+int hc_encode(hc_ctx *ctx, const double *re, const double *im, size_t n, double scale, int level,
+              hc_pt **out);
+/* Integer plaintext from signed coefficients (|c| < 2^62), N of them. */
+int hc_pt_from_coeffs(hc_ctx *ctx, const int64_t *coeffs, size_t n, int level, double scale,
+                      hc_pt **out);
+/* Coefficient-form residues [level+1][N]. */
+int hc_pt_export(hc_ctx *ctx, const hc_pt *pt, uint64_t *out, size_t cap_words);
+/* Slots of a plaintext: centred CRT lift, then z_j = scale^{-1} m(zeta^{5^j}). */
+int hc_decode(hc_ctx *ctx, const hc_pt *pt, double *re, double *im, size_t n);
+int hc_pt_level(const hc_pt *pt);
+double hc_pt_scale(const hc_pt *pt);
+void hc_pt_destroy(hc_pt *);
+
+/* Public-key encryption (the model owner encrypts weights with the user's
+ * public key, Sec. "Introduction"): v ternary, e0, e1 Gaussian from streams
+ * (seed, tag of nonce); ct = (v b + e0 + m, v a + e1) at the plaintext's
+ * level.  nonce < 2^61; one (seed, nonce) per ciphertext. */
+int hc_encrypt(hc_ctx *ctx, const hc_pk *pk, const hc_pt *pt, uint64_t seed, uint64_t nonce,
+               hc_ct **out);
+/* m = c0 + c1 s (+ c2 s^2) at the ciphertext's level. */
+int hc_decrypt(hc_ctx *ctx, const hc_sk *sk, const hc_ct *ct, hc_pt **out);
+
+/* Metadata of a ciphertext in host form. */
+typedef struct hc_ct_meta {
+  int level;   /* limbs = level + 1 */
+  int degree;  /* 1 or 2 (polys = degree + 1) */
+  double scale;
+} hc_ct_meta;
+/* Coefficient-form export, [degree+1][level+1][N] words (synchronises). */
+int hc_ct_export(hc_ctx *ctx, const hc_ct *ct, uint64_t *out, size_t cap_words, hc_ct_meta *meta);
+/* Import from the same layout; residues must be < q (else HC_ERR_INVALID). */
+int hc_ct_import(hc_ctx *ctx, const uint64_t *host, const hc_ct_meta *meta, hc_ct **out);
+int hc_ct_meta_of(const hc_ct *ct, hc_ct_meta *meta);
+void hc_ct_destroy(hc_ct *);
+
+/* ----------------------------------------------------------- arithmetic */
+/* CT-CT add / sub (Sec. "Convolution Operator": "CT-CT add"): same level
+ * and degree, scales equal to 2^-40 relative; result takes x's scale. */
+int hc_add(hc_ctx *ctx, const hc_ct *x, const hc_ct *y, hc_ct **out);
+int hc_sub(hc_ctx *ctx, const hc_ct *x, const hc_ct *y, hc_ct **out);
+/* CT-PT add of the slot constant c: adds round(c * scale) to c0 (Eq. 4's
+ * constant term). */
+int hc_add_const(hc_ctx *ctx, const hc_ct *x, double c, hc_ct **out);
+/* CT-PT mult by the slot constant c encoded at const_scale: every limb times
+ * round(c * const_scale); scale multiplies; no rescale (Eq. 4, mean pool). */
+int hc_mul_const(hc_ctx *ctx, const hc_ct *x, double c, double const_scale, hc_ct **out);
+/* CT-CT mult (Eq. 3): tensor product (a0 b0, a0 b1 + a1 b0, a1 b1) -> degree 2. */
+int hc_mul(hc_ctx *ctx, const hc_ct *x, const hc_ct *y, hc_ct **out);
+/* Relinearisation by hybrid key switching: ModUp of c2 per digit (fast basis
+ * conversion), product with the relinearisation key, ModDown by P. */
+int hc_relin(hc_ctx *ctx, const hc_evk *evk, const hc_ct *x, hc_ct **out);
+/* Rescale by the last prime: c_i' = (c_i - [c_l]) q_l^{-1} mod q_i, [.]
+ * centred; scale /= q_l.  HC_ERR_DEPTH at level 0. */
+int hc_rescale(hc_ctx *ctx, const hc_ct *x, hc_ct **out);
+/* Drops limbs above `level` (scale unchanged). */
+int hc_drop_to_level(hc_ctx *ctx, const hc_ct *x, int level, hc_ct **out);
+/* Left rotation of the slots by `steps` ("rotation of values in the slots",
+ * Sec. "Convolution Operator"): kappa_g, g = 5^steps mod 2N, then a key
+ * switch from kappa_g(s) to s.  steps = 0 mod K copies. */
+int hc_rotate(hc_ctx *ctx, const hc_evk *evk, const hc_ct *x, int steps, hc_ct **out);
+/* n rotations of one ciphertext sharing a single ModUp of c1 (the
+ * automorphism is applied to the raised digits).  Decrypts like hc_rotate
+ * but is not bit-identical to it. */
+int hc_rotate_hoisted(hc_ctx *ctx, const hc_evk *evk, const hc_ct *x, const int32_t *steps, int n,
+                      hc_ct **outs);
+/* n independent CT-CT mult + relin + rescale on pairs (a[k], b[k]), batched
+ * into one pass of each kernel. */
+int hc_mul_relin_rescale_batch(hc_ctx *ctx, const hc_evk *evk, const hc_ct *const *a,
+                               const hc_ct *const *b, int n, hc_ct **outs);
+
+/* ---------------------------------------------------------- CNN layers */
+typedef enum hc_packing {
+  HC_PACK_BATCH = 0,  /* Fig. 2: one ciphertext per pixel / weight, slot k = image k */
+  HC_PACK_SINGLE = 1  /* whole image row-major in one ciphertext (Sec. "Parallelization",
+                         single-image latency) */
+} hc_packing;
+
+/*
+ * Encrypted convolution, Eq. 3: Y_{m,n} = < X^_{m,n}, W^ > over windows
+ * anchored top-left, no padding, stride `stride`.  Every output is the sum
+ * of all kh*kw*cin tensor products followed by ONE relinearisation and ONE
+ * rescale (one level).
+ * HC_PACK_BATCH: x[(h*W + w)*cin + ci] (H*W*cin ciphertexts),
+ *   w[((co*kh + p)*kw + q)*cin + ci] (cout*kh*kw*cin slot-constant
+ *   ciphertexts), y[(m*Wo + n)*cout + co] with Ho = (H-kh)/stride + 1.
+ * HC_PACK_SINGLE: cin = 1, stride = 1, x[0] holds the image row-major with
+ *   width W; y[co] = sum_{p,q} rot(x, p*W + q) (x) w[(co*kh + p)*kw + q]
+ *   (needs Galois keys for every p*W + q); output (m,n) in slot m*W + n.
+ * All inputs at one level >= 1 with one scale per operand kind.
+ */
+int hc_enc_conv2d(hc_ctx *ctx, const hc_evk *evk, hc_packing packing, const hc_ct *const *x,
+                  int H, int W, int cin, const hc_ct *const *w, int cout, int kh, int kw,
+                  int stride, hc_ct **y);
+/*
+ * Polynomial activation g(u) = c0 + c1 u + c2 u^2 (Eq. 4, the paper's
+ * 0.47, 0.50, 0.09 approximation of ReLU; (0,0,1) is x^2), elementwise over
+ * n ciphertexts.  x^2 uses one level: rescale(relin(u (x) u)).  The general
+ * form uses two: t = rescale(relin(u (x) u)); t = rescale(t * c2 @ q_{l-1});
+ * v = rescale(u * c1 @ s_t q_l / s_u) dropped to t's level; out = t + v + c0.
+ * degree must be 2.
+ */
+int hc_enc_poly_act(hc_ctx *ctx, const hc_evk *evk, const hc_ct *const *x, int n,
+                    const double *coeffs, int degree, hc_ct **y);
+/*
+ * Mean pooling over non-overlapping 2x2 blocks (Eq. 5-6 with the activation
+ * applied first): ((a + b) + (c + d)) * 1/4 @ q_l, rescale (one level).
+ * HC_PACK_BATCH: x[(h*W + w)*C + c] -> y[(i*(W/2) + j)*C + c].
+ * (Single-ciphertext pooling is not provided.)
+ */
+int hc_enc_pool(hc_ctx *ctx, const hc_evk *evk, hc_packing packing, const hc_ct *const *x, int C,
+                int H, int W, hc_ct **y);
+/*
+ * Fully connected layer Z = W X (+ bias) (Sec. "Convolutional Neural
+ * Network"): z_r = rescale(relin(sum_k x_k (x) w[r*n_in + k]) [+ bias_r]).
+ * Weights (and bias) at a level >= the activations' are dropped to it.
+ * bias may be NULL; if given, its scale must equal scale(x) * scale(w).
+ */
+int hc_enc_fc(hc_ctx *ctx, const hc_evk *evk, hc_packing packing, const hc_ct *const *x, int n_in,
+              const hc_ct *const *w, const hc_ct *const *bias, int n_out, hc_ct **y);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HECNN_H */

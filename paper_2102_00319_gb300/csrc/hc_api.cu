@@ -1,0 +1,1391 @@
+// C ABI of libhecnn (declared in include/hecnn.h): handle lifecycle and the
+// composition of the kernels into the scheme's operations and CNN layers.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "hc_internal.h"
+
+// ------------------------------------------------------------ memory
+DevBuf::~DevBuf() {
+  if (ctx && ptr) ctx->free_words(ptr);
+}
+
+u64* hc_ctx::alloc_words(size_t words) {
+  const size_t bytes = std::max<size_t>(words, 1) * sizeof(u64);
+  void* p = nullptr;
+  if (user_alloc) {
+    p = alloc.alloc(bytes, (void*)stream, alloc.user);
+  } else {
+    if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+  }
+  if (!p) throw HcError{HC_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed"};
+  return (u64*)p;
+}
+
+void hc_ctx::free_words(u64* p) {
+  if (!p) return;
+  if (user_alloc) alloc.free(p, (void*)stream, alloc.user);
+  else cudaFreeAsync(p, stream);
+}
+
+BufPtr hc_ctx::buffer(size_t words) {
+  auto b = std::make_shared<DevBuf>();
+  b->ctx = this;
+  b->ptr = alloc_words(words);
+  b->bytes = words * sizeof(u64);
+  return b;
+}
+
+namespace {
+
+// Run `f`, translating exceptions into return codes and the context error.
+template <class F>
+int guard(hc_ctx* ctx, F&& f) {
+  try {
+    f();
+    if (ctx) ctx->err.clear();
+    return HC_OK;
+  } catch (const HcError& e) {
+    if (ctx) ctx->err = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    if (ctx) ctx->err = "host allocation failed";
+    return HC_ERR_OOM;
+  } catch (...) {
+    if (ctx) ctx->err = "unexpected error";
+    return HC_ERR_INVALID;
+  }
+}
+
+hc_ct* new_ct(hc_ctx* ctx, int level, int degree, double scale) {
+  const size_t stride = (size_t)(level + 1) * ctx->P.n;
+  BufPtr b = ctx->buffer(stride * (degree + 1));
+  return new hc_ct{ctx, b, b->ptr, stride, level, degree, scale};
+}
+
+// Outputs sharing one slab.
+std::vector<hc_ct*> new_cts(hc_ctx* ctx, int count, int level, int degree, double scale) {
+  std::vector<hc_ct*> out;
+  if (count <= 0) return out;
+  const size_t stride = (size_t)(level + 1) * ctx->P.n;
+  const size_t per = stride * (degree + 1);
+  BufPtr b = ctx->buffer(per * count);
+  for (int i = 0; i < count; ++i) out.push_back(new hc_ct{ctx, b, b->ptr + per * i, stride, level, degree, scale});
+  return out;
+}
+
+CtRef* refs_dev(hc_ctx* ctx, const std::vector<CtRef>& v, std::vector<BufPtr>& keep) {
+  return upload(ctx, v, keep);
+}
+
+const int* ids_dev(hc_ctx* ctx, const std::vector<int>& v, std::vector<BufPtr>& keep) {
+  return upload(ctx, v, keep);
+}
+
+void check_scales(double a, double b) {
+  HC_CHECK(std::fabs(a - b) <= std::ldexp(1.0, -40) * std::max(std::fabs(a), std::fabs(b)),
+           HC_ERR_SCALE_MISMATCH, "operand scales differ");
+}
+
+LimbSet limbset_base(u64* base, u64 item_stride, u64 poly_stride, int npoly, int nlimb, int l0,
+                     const int* pmap) {
+  LimbSet s{};
+  s.refs = nullptr;
+  s.base = base;
+  s.item_stride = item_stride;
+  s.poly_stride = poly_stride;
+  s.npoly = npoly;
+  s.nlimb = nlimb;
+  s.l0 = l0;
+  s.prime_map = pmap;
+  return s;
+}
+
+// identity prime map [0..63] lives at the start of ext_map's buffer tail
+const int* ident_map(hc_ctx* ctx) { return ctx->ext_map + (ctx->P.L + 1) * (ctx->P.L + 1 + ctx->P.alpha); }
+
+// ---------------------------------------------------------------------
+// Key switching of a batch of single polynomials x (NTT form, level l):
+//   out_k = base_k + KS(x)_k,  k = 0, 1 (base_k may be null).
+// ---------------------------------------------------------------------
+void keyswitch_batch(hc_ctx* ctx, const u64* key, int level, const std::vector<CtRef>& x,
+                     const std::vector<CtRef>* base0, const std::vector<CtRef>* base1,
+                     const std::vector<CtRef>& out) {
+  const int n = ctx->P.n, alpha = ctx->P.alpha;
+  const int nq = level + 1, next = nq + alpha, dnum = ctx->lv[level].dnum;
+  const int total = (int)x.size();
+  const size_t ext_words = (size_t)next * n;
+  const size_t per_item = (size_t)nq * n + (size_t)dnum * ext_words + 2 * ext_words + 2 * (size_t)nq * n;
+  int chunk = (int)std::max<size_t>(1, ((size_t)3 << 30) / (per_item * 8));
+  chunk = std::min(chunk, 256);
+  const int* emap = ctx->ext_map_of(level);
+  for (int s0 = 0; s0 < total; s0 += chunk) {
+    const int m = std::min(chunk, total - s0);
+    std::vector<BufPtr> keep;
+    std::vector<CtRef> xs(x.begin() + s0, x.begin() + s0 + m);
+    std::vector<CtRef> os(out.begin() + s0, out.begin() + s0 + m);
+    const CtRef* xr = refs_dev(ctx, xs, keep);
+    const CtRef* orr = refs_dev(ctx, os, keep);
+    const CtRef* b0 = nullptr;
+    const CtRef* b1 = nullptr;
+    if (base0) b0 = refs_dev(ctx, std::vector<CtRef>(base0->begin() + s0, base0->begin() + s0 + m), keep);
+    if (base1) b1 = refs_dev(ctx, std::vector<CtRef>(base1->begin() + s0, base1->begin() + s0 + m), keep);
+    BufPtr work = ctx->buffer(per_item * m);
+    keep.push_back(work);
+    u64* xc = work->ptr;                                  // [m][nq][N] coefficient copy of x
+    u64* ext = xc + (size_t)m * nq * n;                   // [m][dnum][next][N]
+    u64* acc = ext + (size_t)m * dnum * ext_words;        // [m][2][next][N]
+    u64* zq = acc + (size_t)m * 2 * ext_words;            // [m][2][nq][N]
+    const u64 x_is = (u64)nq * n, ext_is = (u64)dnum * ext_words, acc_is = 2 * (u64)ext_words,
+              z_is = 2 * (u64)nq * n;
+    // x -> coefficient form
+    std::vector<CtRef> xcr(m);
+    for (int i = 0; i < m; ++i) xcr[i] = CtRef{xc + x_is * i, 0};
+    const CtRef* xcr_d = refs_dev(ctx, xcr, keep);
+    launch_ew(ctx, 3, xcr_d, xr, nullptr, m, 1, nq);
+    launch_ntt(ctx, limbset_base(xc, x_is, 0, 1, nq, 0, nullptr), m, true);
+    // ModUp per digit
+    for (int j = 0; j < dnum; ++j) {
+      const int d0 = j * alpha, d1 = std::min(d0 + alpha, nq);
+      // digit limbs: NTT-form copy of x
+      std::vector<CtRef> er(m);
+      for (int i = 0; i < m; ++i) er[i] = CtRef{ext + ext_is * i + (size_t)j * ext_words + (size_t)d0 * n, 0};
+      std::vector<CtRef> xsh(m);
+      for (int i = 0; i < m; ++i) xsh[i] = CtRef{xs[i].p + (size_t)d0 * n, 0};
+      launch_ew(ctx, 3, refs_dev(ctx, er, keep), refs_dev(ctx, xsh, keep), nullptr, m, 1, d1 - d0);
+      launch_modup_bconv(ctx, level, j, xc, x_is, ext + (size_t)j * ext_words, ext_is, m);
+      u64* ej = ext + (size_t)j * ext_words;
+      if (d0 > 0) launch_ntt(ctx, limbset_base(ej, ext_is, 0, 1, d0, 0, emap), m, false);
+      launch_ntt(ctx, limbset_base(ej, ext_is, 0, 1, next - d1, d1, emap), m, false);
+    }
+    launch_key_product(ctx, level, ext, ext_is, key, acc, acc_is, m);
+    // ModDown
+    launch_ntt(ctx, limbset_base(acc, acc_is, ext_words, 2, alpha, nq, emap), m, true);
+    launch_moddown_bconv(ctx, level, acc + (size_t)nq * n, acc_is, zq, z_is, m);
+    launch_ntt(ctx, limbset_base(zq, z_is, (u64)nq * n, 2, nq, 0, nullptr), m, false);
+    launch_moddown_combine(ctx, level, acc, acc_is, zq, z_is, b0, b1, orr, m);
+  }
+}
+
+// Rescale a batch in place-free fashion: out (level-1) from in (level).
+void rescale_batch(hc_ctx* ctx, const std::vector<CtRef>& in, const std::vector<CtRef>& out, int level,
+                   int npoly) {
+  const int n = ctx->P.n, total = (int)in.size();
+  const size_t per = (size_t)npoly * n * (1 + level);
+  int chunk = (int)std::min<size_t>(4096, std::max<size_t>(1, ((size_t)2 << 30) / (per * 8)));
+  for (int s0 = 0; s0 < total; s0 += chunk) {
+    const int m = std::min(chunk, total - s0);
+    std::vector<BufPtr> keep;
+    const CtRef* ir = refs_dev(ctx, std::vector<CtRef>(in.begin() + s0, in.begin() + s0 + m), keep);
+    const CtRef* orr = refs_dev(ctx, std::vector<CtRef>(out.begin() + s0, out.begin() + s0 + m), keep);
+    BufPtr work = ctx->buffer(per * m);
+    keep.push_back(work);
+    u64* last = work->ptr;                         // [m][npoly][N]
+    u64* lift = last + (size_t)m * npoly * n;      // [m][npoly][level][N]
+    launch_gather_limb(ctx, ir, level, last, m, npoly);
+    launch_ntt(ctx, limbset_base(last, (u64)npoly * n, (u64)n, npoly, 1, 0, ident_map(ctx) + level), m, true);
+    launch_rescale_lift(ctx, level, last, lift, m, npoly);
+    launch_ntt(ctx, limbset_base(lift, (u64)npoly * level * n, (u64)level * n, npoly, level, 0, nullptr), m, false);
+    launch_rescale_combine(ctx, level, ir, lift, orr, m, npoly);
+  }
+}
+
+void check_ct(const hc_ctx* ctx, const hc_ct* c) {
+  HC_CHECK(c != nullptr, HC_ERR_INVALID, "null ciphertext");
+  HC_CHECK(c->ctx == ctx, HC_ERR_INVALID, "ciphertext of another context");
+}
+
+void relin_batch(hc_ctx* ctx, const hc_evk* evk, const std::vector<const hc_ct*>& d, std::vector<hc_ct*>& out) {
+  if (d.empty()) return;
+  const int level = d[0]->level;
+  std::vector<CtRef> x, b0, b1, o;
+  for (size_t i = 0; i < d.size(); ++i) {
+    HC_CHECK(d[i]->degree == 2 && d[i]->level == level, HC_ERR_INVALID, "relin batch needs degree-2 cts at one level");
+    x.push_back(CtRef{d[i]->data + 2 * d[i]->stride, d[i]->stride});
+    b0.push_back(CtRef{d[i]->data, d[i]->stride});
+    b1.push_back(CtRef{d[i]->data + d[i]->stride, d[i]->stride});
+    o.push_back(out[i]->ref());
+  }
+  keyswitch_batch(ctx, evk->relin.buf->ptr, level, x, &b0, &b1, o);
+}
+
+void rescale_cts(hc_ctx* ctx, const std::vector<const hc_ct*>& in, std::vector<hc_ct*>& out) {
+  if (in.empty()) return;
+  const int level = in[0]->level, deg = in[0]->degree;
+  HC_CHECK(level >= 1, HC_ERR_DEPTH, "no level left to rescale");
+  std::vector<CtRef> ir, orr;
+  for (size_t i = 0; i < in.size(); ++i) {
+    HC_CHECK(in[i]->level == level && in[i]->degree == deg, HC_ERR_LEVEL_MISMATCH, "rescale batch mixes levels");
+    ir.push_back(in[i]->ref());
+    orr.push_back(out[i]->ref());
+  }
+  rescale_batch(ctx, ir, orr, level, deg + 1);
+}
+
+// Tensor-accumulate products into fresh degree-2 cts.
+std::vector<hc_ct*> tensor_acc(hc_ctx* ctx, const std::vector<const hc_ct*>& xs, const std::vector<const hc_ct*>& ws,
+                               const std::vector<int>& xi, const std::vector<int>& wi, const std::vector<int>& off,
+                               int level, double scale) {
+  const int nout = (int)off.size() - 1;
+  std::vector<hc_ct*> out = new_cts(ctx, nout, level, 2, scale);
+  std::vector<BufPtr> keep;
+  std::vector<CtRef> xr, wr, orr;
+  for (auto* c : xs) xr.push_back(c->ref());
+  for (auto* c : ws) wr.push_back(c->ref());
+  for (auto* c : out) orr.push_back(c->ref());
+  for (int o0 = 0; o0 < nout; o0 += 65535) {
+    const int m = std::min(65535, nout - o0);
+    std::vector<int> off_sub(off.begin() + o0, off.begin() + o0 + m + 1);
+    launch_tensor_acc(ctx, refs_dev(ctx, std::vector<CtRef>(orr.begin() + o0, orr.begin() + o0 + m), keep),
+                      refs_dev(ctx, xr, keep), refs_dev(ctx, wr, keep), ids_dev(ctx, xi, keep), ids_dev(ctx, wi, keep),
+                      ids_dev(ctx, off_sub, keep), m, level + 1);
+  }
+  return out;
+}
+
+// relin + rescale of a batch of degree-2 cts -> fresh degree-1 cts at level-1
+std::vector<hc_ct*> relin_rescale(hc_ctx* ctx, const hc_evk* evk, const std::vector<hc_ct*>& d,
+                                  const std::vector<const hc_ct*>* bias) {
+  if (d.empty()) return {};
+  const int level = d[0]->level;
+  HC_CHECK(level >= 1, HC_ERR_DEPTH, "no level left to rescale");
+  std::vector<hc_ct*> r = new_cts(ctx, (int)d.size(), level, 1, d[0]->scale);
+  std::vector<const hc_ct*> dc(d.begin(), d.end());
+  relin_batch(ctx, evk, dc, r);
+  if (bias) {
+    std::vector<BufPtr> keep;
+    std::vector<CtRef> rr, br;
+    for (size_t i = 0; i < r.size(); ++i) {
+      const hc_ct* b = (*bias)[i];
+      HC_CHECK(b->degree == 1 && b->level >= level, HC_ERR_LEVEL_MISMATCH, "bias level too low");
+      check_scales(r[i]->scale, b->scale);
+      rr.push_back(r[i]->ref());
+      br.push_back(b->ref());
+    }
+    const CtRef* rd = refs_dev(ctx, rr, keep);
+    launch_ew(ctx, 0, rd, rd, refs_dev(ctx, br, keep), (int)r.size(), 2, level + 1);
+  }
+  std::vector<hc_ct*> out = new_cts(ctx, (int)d.size(), level - 1, 1, d[0]->scale / (double)ctx->P.chain[level]);
+  std::vector<const hc_ct*> rc(r.begin(), r.end());
+  rescale_cts(ctx, rc, out);
+  for (auto* c : r) delete c;
+  return out;
+}
+
+void constant_residues(hc_ctx* ctx, int level, double value, bool with_shoup, std::vector<u64>& out) {
+  bool ok = false;
+  const int64_t m = hch::round_half_away(value, &ok);
+  HC_CHECK(ok, HC_ERR_INVALID, "constant out of range (|c * scale| >= 2^62)");
+  const int nl = level + 1;
+  out.assign(with_shoup ? 2 * nl : nl, 0);
+  for (int i = 0; i < nl; ++i) {
+    const u64 q = ctx->P.chain[i];
+    u64 r = m >= 0 ? (u64)m % q : (q - ((u64)(-(m + 1)) % q) - 1);
+    out[i] = r;
+    if (with_shoup) out[nl + i] = hch::shoup_of(r, q);
+  }
+}
+
+std::vector<hc_ct*> mul_const_cts(hc_ctx* ctx, const std::vector<const hc_ct*>& x, double c, double cs) {
+  if (x.empty()) return {};
+  const int level = x[0]->level, deg = x[0]->degree;
+  std::vector<u64> sc;
+  constant_residues(ctx, level, c * cs, true, sc);
+  std::vector<hc_ct*> out = new_cts(ctx, (int)x.size(), level, deg, x[0]->scale * cs);
+  std::vector<BufPtr> keep;
+  std::vector<CtRef> xr, orr;
+  for (size_t i = 0; i < x.size(); ++i) {
+    HC_CHECK(x[i]->level == level && x[i]->degree == deg, HC_ERR_LEVEL_MISMATCH, "batch mixes levels");
+    out[i]->scale = x[i]->scale * cs;
+    xr.push_back(x[i]->ref());
+    orr.push_back(out[i]->ref());
+  }
+  launch_scalar(ctx, false, refs_dev(ctx, orr, keep), refs_dev(ctx, xr, keep), (int)x.size(), deg + 1, level + 1,
+                upload(ctx, sc, keep));
+  return out;
+}
+
+std::vector<hc_ct*> rotate_one(hc_ctx* ctx, const hc_evk* evk, const hc_ct* x, const std::vector<int>& steps,
+                               bool hoisted);
+
+void free_all(std::vector<hc_ct*>& v) {
+  for (auto* c : v) delete c;
+  v.clear();
+}
+
+}  // namespace
+
+// =====================================================================
+// Parameters
+// =====================================================================
+extern "C" int hc_params_create(const hc_params_desc* d, hc_params** out) {
+  return guard(nullptr, [&] {
+    HC_CHECK(d && out, HC_ERR_INVALID, "null argument");
+    HC_CHECK(d->log_n >= 10 && d->log_n <= 16, HC_ERR_INVALID, "log_n must be 10..16");
+    HC_CHECK(d->n_q >= 1 && d->n_p >= 1 && d->n_p <= 16 && d->n_q + d->n_p <= HC_MAX_CHAIN, HC_ERR_INVALID,
+             "bad prime counts");
+    HC_CHECK(d->q_bits && d->p_bits, HC_ERR_INVALID, "null bit sizes");
+    HC_CHECK(d->sigma > 0 && d->sigma < 6.5, HC_ERR_INVALID, "sigma out of range");
+    std::vector<int> bits(d->q_bits, d->q_bits + d->n_q);
+    bits.insert(bits.end(), d->p_bits, d->p_bits + d->n_p);
+    for (int b : bits) HC_CHECK(b >= 20 && b <= 61, HC_ERR_INVALID, "prime bit size must be 20..61");
+    auto* p = new hc_params();
+    p->log_n = d->log_n;
+    p->n = 1 << d->log_n;
+    p->L = d->n_q - 1;
+    p->alpha = d->n_p;
+    p->dnum = (d->n_q + d->n_p - 1) / d->n_p;
+    p->chain.resize(bits.size());
+    if (hch::gen_primes(d->log_n, bits.data(), (int)bits.size(), p->chain.data()) != 0) {
+      delete p;
+      throw HcError{HC_ERR_INVALID, "not enough primes of the requested sizes"};
+    }
+    p->scale = std::exp2(d->log2_scale);
+    p->sigma = d->sigma;
+    p->cdt = hch::gaussian_cdt(d->sigma);
+    *out = p;
+  });
+}
+
+extern "C" void hc_params_destroy(hc_params* p) { delete p; }
+
+extern "C" int hc_params_primes(const hc_params* p, uint64_t* out, int cap) {
+  if (!p || !out || cap < p->nchain()) return HC_ERR_INVALID;
+  for (int i = 0; i < p->nchain(); ++i) out[i] = p->chain[i];
+  return HC_OK;
+}
+
+extern "C" int hc_params_info(const hc_params* p, int* n, int* L, int* alpha, int* dnum) {
+  if (!p) return HC_ERR_INVALID;
+  if (n) *n = p->n;
+  if (L) *L = p->L;
+  if (alpha) *alpha = p->alpha;
+  if (dnum) *dnum = p->dnum;
+  return HC_OK;
+}
+
+extern "C" int hc_params_cdt(const hc_params* p, uint64_t* out, int cap) {
+  if (!p || !out || cap < (int)p->cdt.size()) return HC_ERR_INVALID;
+  for (size_t i = 0; i < p->cdt.size(); ++i) out[i] = p->cdt[i];
+  return (int)p->cdt.size();
+}
+
+// =====================================================================
+// Context
+// =====================================================================
+namespace {
+void build_tables(hc_ctx* ctx) {
+  const hc_params& P = ctx->P;
+  const int n = P.n, nc = P.nchain(), logn = P.log_n;
+  std::vector<u64> fwd((size_t)nc * n), fwd_sh((size_t)nc * n), inv((size_t)nc * n), inv_sh((size_t)nc * n);
+  std::vector<u64> ninv(nc), ninv_sh(nc);
+  std::vector<DMod> mods(nc);
+  std::vector<u64> pw(n), ipw(n);
+  for (int c = 0; c < nc; ++c) {
+    const u64 q = P.chain[c];
+    const u64 psi = hch::primitive_2n_root(logn, q);
+    HC_CHECK(psi != 0, HC_ERR_INVALID, "no 2N-th root of unity");
+    const u64 ipsi = hch::invmod(psi, q);
+    pw[0] = ipw[0] = 1;
+    for (int k = 1; k < n; ++k) {
+      pw[k] = hch::mulmod(pw[k - 1], psi, q);
+      ipw[k] = hch::mulmod(ipw[k - 1], ipsi, q);
+    }
+    for (int k = 0; k < n; ++k) {
+      const int r = hch::bit_reverse(k, logn);
+      const size_t o = (size_t)c * n + k;
+      fwd[o] = pw[r];
+      fwd_sh[o] = hch::shoup_of(pw[r], q);
+      inv[o] = ipw[r];
+      inv_sh[o] = hch::shoup_of(ipw[r], q);
+    }
+    ninv[c] = hch::invmod((u64)n % q, q);
+    ninv_sh[c] = hch::shoup_of(ninv[c], q);
+    const u64 r64 = (u64)((((unsigned __int128)1) << 64) % q);
+    mods[c] = DMod{q, r64, hch::shoup_of(r64, q), hch::shoup_of(1, q)};
+  }
+  auto put = [&](const void* src, size_t bytes) {
+    void* d = nullptr;
+    HC_CUDA(cudaMalloc(&d, bytes));
+    ctx->owned.push_back(d);
+    HC_CUDA(cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice));
+    return d;
+  };
+  const size_t tb = (size_t)nc * n * sizeof(u64);
+  ctx->tab.fwd = (const u64*)put(fwd.data(), tb);
+  ctx->tab.fwd_sh = (const u64*)put(fwd_sh.data(), tb);
+  ctx->tab.inv = (const u64*)put(inv.data(), tb);
+  ctx->tab.inv_sh = (const u64*)put(inv_sh.data(), tb);
+  ctx->tab.ninv = (const u64*)put(ninv.data(), nc * sizeof(u64));
+  ctx->tab.ninv_sh = (const u64*)put(ninv_sh.data(), nc * sizeof(u64));
+  ctx->tab.mods = (const DMod*)put(mods.data(), nc * sizeof(DMod));
+  ctx->tab.log_n = logn;
+
+  // key-switching / rescale constants
+  const int L = P.L, alpha = P.alpha;
+  std::vector<u64> ks;
+  ctx->lv.assign(L + 1, LevelConsts{});
+  for (int l = 0; l <= L; ++l) {
+    LevelConsts& lc = ctx->lv[l];
+    const int nq = l + 1, next = nq + alpha;
+    lc.dnum = (nq + alpha - 1) / alpha;
+    std::vector<int> emap(next);
+    for (int s = 0; s < next; ++s) emap[s] = s < nq ? s : L + 1 + (s - nq);
+    for (int j = 0; j < lc.dnum; ++j) {
+      const int d0 = j * alpha, d1 = std::min(d0 + alpha, nq), ns = d1 - d0;
+      lc.modup_off.push_back((int)ks.size());
+      std::vector<u64> hinv(ns);
+      for (int i = 0; i < ns; ++i) {
+        const u64 qi = P.chain[d0 + i];
+        u64 prod = 1;
+        for (int k = 0; k < ns; ++k)
+          if (k != i) prod = hch::mulmod(prod, P.chain[d0 + k] % qi, qi);
+        hinv[i] = hch::invmod(prod, qi);
+      }
+      for (int i = 0; i < ns; ++i) ks.push_back(hinv[i]);
+      for (int i = 0; i < ns; ++i) ks.push_back(hch::shoup_of(hinv[i], P.chain[d0 + i]));
+      for (int s = 0; s < next; ++s) {
+        const u64 t = P.chain[emap[s]];
+        for (int i = 0; i < ns; ++i) {
+          u64 prod = 1 % t;
+          for (int k = 0; k < ns; ++k)
+            if (k != i) prod = hch::mulmod(prod, P.chain[d0 + k] % t, t);
+          ks.push_back(prod);
+        }
+      }
+    }
+    if (l >= 1) {
+      lc.rescale_off = (int)ks.size();
+      const u64 ql = P.chain[l];
+      std::vector<u64> inv_l(l);
+      for (int i = 0; i < l; ++i) inv_l[i] = hch::invmod(ql % P.chain[i], P.chain[i]);
+      for (int i = 0; i < l; ++i) ks.push_back(inv_l[i]);
+      for (int i = 0; i < l; ++i) ks.push_back(hch::shoup_of(inv_l[i], P.chain[i]));
+    }
+  }
+  ctx->moddown_off = (int)ks.size();
+  {
+    std::vector<u64> hinv(alpha);
+    for (int k = 0; k < alpha; ++k) {
+      const u64 pk = P.chain[L + 1 + k];
+      u64 prod = 1;
+      for (int m = 0; m < alpha; ++m)
+        if (m != k) prod = hch::mulmod(prod, P.chain[L + 1 + m] % pk, pk);
+      hinv[k] = hch::invmod(prod, pk);
+    }
+    for (int k = 0; k < alpha; ++k) ks.push_back(hinv[k]);
+    for (int k = 0; k < alpha; ++k) ks.push_back(hch::shoup_of(hinv[k], P.chain[L + 1 + k]));
+    for (int i = 0; i <= L; ++i) {
+      const u64 qi = P.chain[i];
+      for (int k = 0; k < alpha; ++k) {
+        u64 prod = 1 % qi;
+        for (int m = 0; m < alpha; ++m)
+          if (m != k) prod = hch::mulmod(prod, P.chain[L + 1 + m] % qi, qi);
+        ks.push_back(prod);
+      }
+    }
+    std::vector<u64> pinv(L + 1);
+    for (int i = 0; i <= L; ++i) {
+      const u64 qi = P.chain[i];
+      u64 prod = 1;
+      for (int m = 0; m < alpha; ++m) prod = hch::mulmod(prod, P.chain[L + 1 + m] % qi, qi);
+      pinv[i] = hch::invmod(prod, qi);
+    }
+    for (int i = 0; i <= L; ++i) ks.push_back(pinv[i]);
+    for (int i = 0; i <= L; ++i) ks.push_back(hch::shoup_of(pinv[i], P.chain[i]));
+  }
+  ctx->ks_dev = (u64*)put(ks.data(), ks.size() * sizeof(u64));
+  // ext maps per level followed by an identity map of HC_MAX_CHAIN entries
+  const int W = L + 1 + alpha;
+  std::vector<int> maps((size_t)(L + 1) * W + HC_MAX_CHAIN, 0);
+  for (int l = 0; l <= L; ++l)
+    for (int s = 0; s < l + 1 + alpha; ++s) maps[(size_t)l * W + s] = s <= l ? s : L + 1 + (s - l - 1);
+  for (int i = 0; i < HC_MAX_CHAIN; ++i) maps[(size_t)(L + 1) * W + i] = i;
+  ctx->ext_map = (int*)put(maps.data(), maps.size() * sizeof(int));
+}
+}  // namespace
+
+extern "C" int hc_ctx_create(const hc_params* p, int device, void* stream, const hc_allocator* alloc, hc_ctx** out) {
+  hc_ctx* ctx = nullptr;
+  int rc = guard(nullptr, [&] {
+    HC_CHECK(p && out, HC_ERR_INVALID, "null argument");
+    HC_CUDA(cudaSetDevice(device));
+    ctx = new hc_ctx();
+    ctx->P = *p;
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)stream;
+    if (!alloc) {
+      // keep freed pool memory cached instead of returning it at every sync
+      cudaMemPool_t pool;
+      HC_CUDA(cudaDeviceGetDefaultMemPool(&pool, device));
+      uint64_t keep_all = UINT64_MAX;
+      HC_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep_all));
+    }
+    if (alloc) {
+      HC_CHECK(alloc->alloc && alloc->free, HC_ERR_INVALID, "allocator needs alloc and free");
+      ctx->alloc = *alloc;
+      ctx->user_alloc = true;
+    }
+    build_tables(ctx);
+    *out = ctx;
+  });
+  if (rc != HC_OK && ctx) hc_ctx_destroy(ctx);
+  return rc;
+}
+
+extern "C" void hc_ctx_destroy(hc_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  for (void* d : ctx->owned) cudaFree(d);
+  delete ctx;
+}
+
+extern "C" int hc_sync(hc_ctx* ctx) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] { HC_CUDA(cudaStreamSynchronize(ctx->stream)); });
+}
+
+extern "C" const char* hc_last_error(const hc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+extern "C" uint64_t hc_kernel_launches(const hc_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+// =====================================================================
+// Keys
+// =====================================================================
+namespace {
+const u64 TAG_S = 1, TAG_PK_A = 2, TAG_PK_E = 3;
+u64 tag_swk_a(int j, u64 g) { return (g << 16) | (u64)(0x100 + 2 * j); }
+u64 tag_swk_e(int j, u64 g) { return (g << 16) | (u64)(0x101 + 2 * j); }
+u64 tag_enc(u64 nonce, int which) { return (1ull << 63) | (nonce << 2) | (u64)which; }
+
+u64 galois_elt(const hc_params& P, long long r) {
+  const long long K = P.n / 2;
+  long long rr = r % K;
+  if (rr < 0) rr += K;
+  return hch::powmod(5, (u64)rr, 2 * (u64)P.n);
+}
+
+// Switching key for s' (NTT form over the whole chain) -> s.
+void make_switch_key(hc_ctx* ctx, const u64* s_ntt, const u64* sp_ntt, u64 seed, u64 g, SwitchKeyDev& out) {
+  const hc_params& P = ctx->P;
+  const int nc = P.nchain(), n = P.n;
+  const size_t poly = (size_t)nc * n;
+  out.buf = ctx->buffer(2 * poly * P.dnum);
+  std::vector<BufPtr> keep;
+  std::vector<int> ids(nc);
+  std::iota(ids.begin(), ids.end(), 0);
+  const int* idd = ids_dev(ctx, ids, keep);
+  BufPtr tmp = ctx->buffer(poly);
+  keep.push_back(tmp);
+  u64 Pmod[HC_MAX_CHAIN];
+  for (int t = 0; t < nc; ++t) {
+    u64 pr = 1 % P.chain[t];
+    for (int k = 0; k < P.alpha; ++k) pr = hch::mulmod(pr, P.chain[P.L + 1 + k] % P.chain[t], P.chain[t]);
+    Pmod[t] = pr;
+  }
+  for (int j = 0; j < P.dnum; ++j) {
+    u64* b = out.buf->ptr + (size_t)(2 * j) * poly;
+    u64* a = b + poly;
+    launch_sample_uniform(ctx, seed, tag_swk_a(j, g), a, idd, nc);
+    launch_ntt(ctx, limbset_base(a, 0, 0, 1, nc, 0, nullptr), 1, false);
+    launch_sample_gauss(ctx, seed, tag_swk_e(j, g), b, idd, nc);
+    launch_ntt(ctx, limbset_base(b, 0, 0, 1, nc, 0, nullptr), 1, false);
+    // b = e - a s + P [t in digit j] s'
+    std::vector<CtRef> rb{CtRef{b, 0}}, ra{CtRef{a, 0}}, rs{CtRef{const_cast<u64*>(s_ntt), 0}},
+        rt{CtRef{tmp->ptr, 0}}, rsp{CtRef{const_cast<u64*>(sp_ntt), 0}};
+    const CtRef *db = refs_dev(ctx, rb, keep), *da = refs_dev(ctx, ra, keep), *ds = refs_dev(ctx, rs, keep),
+                *dt = refs_dev(ctx, rt, keep), *dsp = refs_dev(ctx, rsp, keep);
+    launch_ew(ctx, 2, dt, da, ds, 1, 1, nc);
+    launch_ew(ctx, 1, db, db, dt, 1, 1, nc);
+    std::vector<u64> sc(2 * nc, 0);
+    const int d0 = j * P.alpha, d1 = std::min(d0 + P.alpha, P.L + 1);
+    for (int t = 0; t < nc; ++t) {
+      const u64 v = (t >= d0 && t < d1) ? Pmod[t] : 0;
+      sc[t] = v;
+      sc[nc + t] = hch::shoup_of(v, P.chain[t]);
+    }
+    launch_scalar(ctx, false, dt, dsp, 1, 1, nc, upload(ctx, sc, keep));
+    launch_ew(ctx, 0, db, db, dt, 1, 1, nc);
+  }
+  HC_CUDA(cudaStreamSynchronize(ctx->stream));
+}
+}  // namespace
+
+extern "C" int hc_keygen(hc_ctx* ctx, uint64_t seed, const int32_t* rot_steps, int n_rot, hc_sk** sk_out,
+                         hc_pk** pk_out, hc_evk** evk_out) {
+  if (!ctx) return HC_ERR_INVALID;
+  hc_sk* sk = nullptr;
+  hc_pk* pk = nullptr;
+  hc_evk* evk = nullptr;
+  int rc = guard(ctx, [&] {
+    HC_CHECK(sk_out && pk_out && evk_out && (n_rot == 0 || rot_steps), HC_ERR_INVALID, "null argument");
+    const hc_params& P = ctx->P;
+    const int nc = P.nchain(), n = P.n, nq = P.L + 1;
+    std::vector<BufPtr> keep;
+    std::vector<int> ids(nc);
+    std::iota(ids.begin(), ids.end(), 0);
+    const int* idd = ids_dev(ctx, ids, keep);
+    sk = new hc_sk{ctx, ctx->buffer((size_t)nc * n), {}};
+    launch_sample_ternary(ctx, seed, TAG_S, sk->s_ntt->ptr, idd, nc);
+    {
+      // keep the ternary coefficients on the host for export
+      std::vector<u64> l0(n);
+      HC_CUDA(cudaMemcpyAsync(l0.data(), sk->s_ntt->ptr, n * sizeof(u64), cudaMemcpyDeviceToHost, ctx->stream));
+      HC_CUDA(cudaStreamSynchronize(ctx->stream));
+      sk->s_coeff.resize(n);
+      for (int i = 0; i < n; ++i) sk->s_coeff[i] = l0[i] == 0 ? 0 : (l0[i] == 1 ? 1 : -1);
+    }
+    launch_ntt(ctx, limbset_base(sk->s_ntt->ptr, 0, 0, 1, nc, 0, nullptr), 1, false);
+    // public key over q_0..q_L
+    pk = new hc_pk{ctx, ctx->buffer(2 * (size_t)nq * n)};
+    u64* b = pk->buf->ptr;
+    u64* a = b + (size_t)nq * n;
+    launch_sample_uniform(ctx, seed, TAG_PK_A, a, idd, nq);
+    launch_ntt(ctx, limbset_base(a, 0, 0, 1, nq, 0, nullptr), 1, false);
+    launch_sample_gauss(ctx, seed, TAG_PK_E, b, idd, nq);
+    launch_ntt(ctx, limbset_base(b, 0, 0, 1, nq, 0, nullptr), 1, false);
+    BufPtr tmp = ctx->buffer((size_t)nc * n);
+    keep.push_back(tmp);
+    std::vector<CtRef> rb{CtRef{b, 0}}, ra{CtRef{a, 0}}, rs{CtRef{sk->s_ntt->ptr, 0}}, rt{CtRef{tmp->ptr, 0}};
+    const CtRef *db = refs_dev(ctx, rb, keep), *da = refs_dev(ctx, ra, keep), *ds = refs_dev(ctx, rs, keep),
+                *dt = refs_dev(ctx, rt, keep);
+    launch_ew(ctx, 2, dt, da, ds, 1, 1, nq);
+    launch_ew(ctx, 1, db, db, dt, 1, 1, nq);
+    // relinearisation key: s' = s^2
+    evk = new hc_evk{ctx, {}, {}};
+    BufPtr s2 = ctx->buffer((size_t)nc * n);
+    keep.push_back(s2);
+    std::vector<CtRef> rs2{CtRef{s2->ptr, 0}};
+    launch_ew(ctx, 2, refs_dev(ctx, rs2, keep), ds, ds, 1, 1, nc);
+    make_switch_key(ctx, sk->s_ntt->ptr, s2->ptr, seed, 0, evk->relin);
+    for (int i = 0; i < n_rot; ++i) {
+      const u64 g = galois_elt(P, rot_steps[i]);
+      if (g == 1 || evk->galois.count(g)) continue;
+      BufPtr sg = ctx->buffer((size_t)nc * n);
+      std::vector<BufPtr> k2;
+      std::vector<CtRef> rsg{CtRef{sg->ptr, 0}};
+      launch_automorph(ctx, refs_dev(ctx, rsg, k2), ds, 1, 1, nc, g);
+      make_switch_key(ctx, sk->s_ntt->ptr, sg->ptr, seed, g, evk->galois[g]);
+    }
+    HC_CUDA(cudaStreamSynchronize(ctx->stream));
+    *sk_out = sk;
+    *pk_out = pk;
+    *evk_out = evk;
+  });
+  if (rc != HC_OK) {
+    delete sk;
+    delete pk;
+    delete evk;
+  }
+  return rc;
+}
+
+extern "C" void hc_sk_destroy(hc_sk* k) { delete k; }
+extern "C" void hc_pk_destroy(hc_pk* k) { delete k; }
+extern "C" void hc_evk_destroy(hc_evk* k) { delete k; }
+
+namespace {
+// Coefficient-form copy of `npoly` polys of `nl` limbs (poly stride ps) to host.
+void export_coeff(hc_ctx* ctx, const u64* src, u64 ps, int npoly, int nl, const int* pmap, u64* host) {
+  const int n = ctx->P.n;
+  std::vector<BufPtr> keep;
+  BufPtr tmp = ctx->buffer((size_t)npoly * nl * n);
+  keep.push_back(tmp);
+  for (int k = 0; k < npoly; ++k)
+    HC_CUDA(cudaMemcpyAsync(tmp->ptr + (size_t)k * nl * n, src + k * ps, (size_t)nl * n * sizeof(u64),
+                            cudaMemcpyDeviceToDevice, ctx->stream));
+  launch_ntt(ctx, limbset_base(tmp->ptr, 0, (u64)nl * n, npoly, nl, 0, pmap), 1, true);
+  HC_CUDA(cudaMemcpyAsync(host, tmp->ptr, (size_t)npoly * nl * n * sizeof(u64), cudaMemcpyDeviceToHost, ctx->stream));
+  HC_CUDA(cudaStreamSynchronize(ctx->stream));
+}
+}  // namespace
+
+extern "C" int hc_sk_export(hc_ctx* ctx, const hc_sk* sk, int8_t* out, size_t n) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    HC_CHECK(sk && out && n >= (size_t)ctx->P.n, HC_ERR_INVALID, "bad arguments");
+    std::copy(sk->s_coeff.begin(), sk->s_coeff.end(), out);
+  });
+}
+
+extern "C" int hc_pk_export(hc_ctx* ctx, const hc_pk* pk, uint64_t* out, size_t cap) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    const int nq = ctx->P.L + 1;
+    HC_CHECK(pk && out && cap >= 2 * (size_t)nq * ctx->P.n, HC_ERR_INVALID, "bad arguments");
+    export_coeff(ctx, pk->buf->ptr, (u64)nq * ctx->P.n, 2, nq, nullptr, (u64*)out);
+  });
+}
+
+extern "C" int hc_evk_export(hc_ctx* ctx, const hc_evk* evk, uint64_t g, uint64_t* out, size_t cap) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    const int nc = ctx->P.nchain();
+    const size_t poly = (size_t)nc * ctx->P.n;
+    HC_CHECK(evk && out && cap >= 2 * poly * ctx->P.dnum, HC_ERR_INVALID, "bad arguments");
+    const SwitchKeyDev* k = nullptr;
+    if (g == 1) k = &evk->relin;
+    else {
+      auto it = evk->galois.find(g);
+      HC_CHECK(it != evk->galois.end(), HC_ERR_NO_KEY, "no such Galois key");
+      k = &it->second;
+    }
+    export_coeff(ctx, k->buf->ptr, poly, 2 * ctx->P.dnum, nc, nullptr, (u64*)out);
+  });
+}
+
+// =====================================================================
+// Plaintexts
+// =====================================================================
+namespace {
+hc_pt* pt_from_signed(hc_ctx* ctx, const std::vector<int64_t>& coeffs, int level, double scale) {
+  const int n = ctx->P.n, nl = level + 1;
+  std::vector<BufPtr> keep;
+  BufPtr src = ctx->buffer(n);
+  keep.push_back(src);
+  HC_CUDA(cudaMemcpyAsync(src->ptr, coeffs.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
+  auto* pt = new hc_pt{ctx, ctx->buffer((size_t)nl * n), nullptr, level, scale};
+  pt->data = pt->buf->ptr;
+  launch_reduce_signed(ctx, (const int64_t*)src->ptr, pt->data, ident_map(ctx), nl);
+  launch_ntt(ctx, limbset_base(pt->data, 0, 0, 1, nl, 0, nullptr), 1, false);
+  HC_CUDA(cudaStreamSynchronize(ctx->stream));  // host source goes out of scope
+  return pt;
+}
+}  // namespace
+
+extern "C" int hc_encode(hc_ctx* ctx, const double* re, const double* im, size_t n, double scale, int level,
+                         hc_pt** out) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    HC_CHECK(out && (re || n == 0), HC_ERR_INVALID, "null argument");
+    HC_CHECK(n <= (size_t)ctx->P.n / 2, HC_ERR_INVALID, "more values than slots");
+    HC_CHECK(level >= 0 && level <= ctx->P.L, HC_ERR_INVALID, "bad level");
+    HC_CHECK(scale > 0, HC_ERR_INVALID, "bad scale");
+    std::vector<double> c;
+    hch::encode_coeffs(re, im, n, ctx->P.log_n, scale, c);
+    std::vector<int64_t> m(c.size());
+    for (size_t i = 0; i < c.size(); ++i) {
+      bool ok = false;
+      m[i] = hch::round_half_away(c[i], &ok);
+      HC_CHECK(ok, HC_ERR_INVALID, "encoded coefficient out of range");
+    }
+    *out = pt_from_signed(ctx, m, level, scale);
+  });
+}
+
+extern "C" int hc_pt_from_coeffs(hc_ctx* ctx, const int64_t* coeffs, size_t n, int level, double scale, hc_pt** out) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    HC_CHECK(out && coeffs && n == (size_t)ctx->P.n, HC_ERR_INVALID, "need N coefficients");
+    HC_CHECK(level >= 0 && level <= ctx->P.L, HC_ERR_INVALID, "bad level");
+    std::vector<int64_t> m(coeffs, coeffs + n);
+    for (auto v : m) HC_CHECK(v < (1LL << 62) && v > -(1LL << 62), HC_ERR_INVALID, "coefficient out of range");
+    *out = pt_from_signed(ctx, m, level, scale);
+  });
+}
+
+extern "C" int hc_pt_export(hc_ctx* ctx, const hc_pt* pt, uint64_t* out, size_t cap) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    HC_CHECK(pt && out && cap >= (size_t)(pt->level + 1) * ctx->P.n, HC_ERR_INVALID, "bad arguments");
+    export_coeff(ctx, pt->data, 0, 1, pt->level + 1, nullptr, (u64*)out);
+  });
+}
+
+extern "C" int hc_decode(hc_ctx* ctx, const hc_pt* pt, double* re, double* im, size_t n) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    HC_CHECK(pt && re, HC_ERR_INVALID, "null argument");
+    const int nl = pt->level + 1, N = ctx->P.n;
+    std::vector<u64> res((size_t)nl * N);
+    export_coeff(ctx, pt->data, 0, 1, nl, nullptr, res.data());
+    std::vector<double> c;
+    hch::crt_centred_to_double(res.data(), ctx->P.chain.data(), nl, N, c);
+    hch::decode_slots(c, ctx->P.log_n, pt->scale, re, im, std::min(n, (size_t)N / 2));
+  });
+}
+
+extern "C" int hc_pt_level(const hc_pt* pt) { return pt ? pt->level : -1; }
+extern "C" double hc_pt_scale(const hc_pt* pt) { return pt ? pt->scale : 0.0; }
+extern "C" void hc_pt_destroy(hc_pt* pt) { delete pt; }
+
+// =====================================================================
+// Encrypt / decrypt / import / export
+// =====================================================================
+extern "C" int hc_encrypt(hc_ctx* ctx, const hc_pk* pk, const hc_pt* pt, uint64_t seed, uint64_t nonce, hc_ct** out) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    HC_CHECK(pk && pt && out, HC_ERR_INVALID, "null argument");
+    HC_CHECK(nonce < (1ull << 61), HC_ERR_INVALID, "nonce must be < 2^61");
+    const int n = ctx->P.n, nl = pt->level + 1, nq = ctx->P.L + 1;
+    std::vector<BufPtr> keep;
+    BufPtr rnd = ctx->buffer(3 * (size_t)nl * n);
+    keep.push_back(rnd);
+    u64* v = rnd->ptr;
+    u64* e0 = v + (size_t)nl * n;
+    u64* e1 = e0 + (size_t)nl * n;
+    launch_sample_ternary(ctx, seed, tag_enc(nonce, 0), v, ident_map(ctx), nl);
+    launch_sample_gauss(ctx, seed, tag_enc(nonce, 1), e0, ident_map(ctx), nl);
+    launch_sample_gauss(ctx, seed, tag_enc(nonce, 2), e1, ident_map(ctx), nl);
+    launch_ntt(ctx, limbset_base(v, (u64)nl * n, 0, 1, nl, 0, nullptr), 3, false);
+    hc_ct* c = new_ct(ctx, pt->level, 1, pt->scale);
+    std::vector<CtRef> r0{CtRef{c->data, 0}}, r1{CtRef{c->data + c->stride, 0}}, rv{CtRef{v, 0}},
+        re0{CtRef{e0, 0}}, re1{CtRef{e1, 0}}, rb{CtRef{pk->buf->ptr, 0}}, ra{CtRef{pk->buf->ptr + (size_t)nq * n, 0}},
+        rm{CtRef{pt->data, 0}};
+    const CtRef *d0 = refs_dev(ctx, r0, keep), *d1 = refs_dev(ctx, r1, keep), *dv = refs_dev(ctx, rv, keep),
+                *de0 = refs_dev(ctx, re0, keep), *de1 = refs_dev(ctx, re1, keep), *db = refs_dev(ctx, rb, keep),
+                *da = refs_dev(ctx, ra, keep), *dm = refs_dev(ctx, rm, keep);
+    launch_ew(ctx, 2, d0, dv, db, 1, 1, nl);
+    launch_ew(ctx, 0, d0, d0, de0, 1, 1, nl);
+    launch_ew(ctx, 0, d0, d0, dm, 1, 1, nl);
+    launch_ew(ctx, 2, d1, dv, da, 1, 1, nl);
+    launch_ew(ctx, 0, d1, d1, de1, 1, 1, nl);
+    *out = c;
+  });
+}
+
+extern "C" int hc_decrypt(hc_ctx* ctx, const hc_sk* sk, const hc_ct* ct, hc_pt** out) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    HC_CHECK(sk && ct && out, HC_ERR_INVALID, "null argument");
+    check_ct(ctx, ct);
+    const int n = ctx->P.n, nl = ct->level + 1;
+    std::vector<BufPtr> keep;
+    auto* pt = new hc_pt{ctx, ctx->buffer((size_t)nl * n), nullptr, ct->level, ct->scale};
+    pt->data = pt->buf->ptr;
+    BufPtr tmp = ctx->buffer((size_t)2 * nl * n);
+    keep.push_back(tmp);
+    u64* t = tmp->ptr;
+    u64* sp = t + (size_t)nl * n;
+    std::vector<CtRef> rm{CtRef{pt->data, 0}}, rt{CtRef{t, 0}}, rs{CtRef{sk->s_ntt->ptr, 0}}, rsp{CtRef{sp, 0}};
+    const CtRef *dm = refs_dev(ctx, rm, keep), *dt = refs_dev(ctx, rt, keep), *ds = refs_dev(ctx, rs, keep),
+                *dsp = refs_dev(ctx, rsp, keep);
+    std::vector<CtRef> rc0{CtRef{ct->data, 0}};
+    launch_ew(ctx, 3, dm, refs_dev(ctx, rc0, keep), nullptr, 1, 1, nl);
+    launch_ew(ctx, 3, dsp, ds, nullptr, 1, 1, nl);
+    for (int k = 1; k <= ct->degree; ++k) {
+      std::vector<CtRef> rck{CtRef{ct->data + k * ct->stride, 0}};
+      launch_ew(ctx, 2, dt, refs_dev(ctx, rck, keep), dsp, 1, 1, nl);
+      launch_ew(ctx, 0, dm, dm, dt, 1, 1, nl);
+      if (k < ct->degree) launch_ew(ctx, 2, dsp, dsp, ds, 1, 1, nl);
+    }
+    HC_CUDA(cudaStreamSynchronize(ctx->stream));
+    *out = pt;
+  });
+}
+
+extern "C" int hc_ct_export(hc_ctx* ctx, const hc_ct* ct, uint64_t* out, size_t cap, hc_ct_meta* meta) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    check_ct(ctx, ct);
+    const size_t words = (size_t)(ct->degree + 1) * (ct->level + 1) * ctx->P.n;
+    HC_CHECK(out && cap >= words, HC_ERR_INVALID, "output buffer too small");
+    export_coeff(ctx, ct->data, ct->stride, ct->degree + 1, ct->level + 1, nullptr, (u64*)out);
+    if (meta) *meta = hc_ct_meta{ct->level, ct->degree, ct->scale};
+  });
+}
+
+extern "C" int hc_ct_import(hc_ctx* ctx, const uint64_t* host, const hc_ct_meta* meta, hc_ct** out) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    HC_CHECK(host && meta && out, HC_ERR_INVALID, "null argument");
+    HC_CHECK(meta->level >= 0 && meta->level <= ctx->P.L && (meta->degree == 1 || meta->degree == 2),
+             HC_ERR_INVALID, "bad metadata");
+    hc_ct* c = new_ct(ctx, meta->level, meta->degree, meta->scale);
+    std::unique_ptr<hc_ct> hold(c);
+    const size_t words = (size_t)(meta->degree + 1) * (meta->level + 1) * ctx->P.n;
+    HC_CUDA(cudaMemcpyAsync(c->data, host, words * sizeof(u64), cudaMemcpyHostToDevice, ctx->stream));
+    std::vector<BufPtr> keep;
+    BufPtr flag = ctx->buffer(1);
+    keep.push_back(flag);
+    HC_CUDA(cudaMemsetAsync(flag->ptr, 0, sizeof(u64), ctx->stream));
+    launch_check_range(ctx, c->data, meta->degree + 1, meta->level + 1, c->stride, (unsigned long long*)flag->ptr);
+    u64 bad = 0;
+    HC_CUDA(cudaMemcpyAsync(&bad, flag->ptr, sizeof(u64), cudaMemcpyDeviceToHost, ctx->stream));
+    HC_CUDA(cudaStreamSynchronize(ctx->stream));
+    HC_CHECK(bad == 0, HC_ERR_INVALID, "imported residue not below its prime");
+    launch_ntt(ctx, limbset_base(c->data, 0, c->stride, meta->degree + 1, meta->level + 1, 0, nullptr), 1, false);
+    *out = hold.release();
+  });
+}
+
+extern "C" int hc_ct_meta_of(const hc_ct* ct, hc_ct_meta* meta) {
+  if (!ct || !meta) return HC_ERR_INVALID;
+  *meta = hc_ct_meta{ct->level, ct->degree, ct->scale};
+  return HC_OK;
+}
+
+extern "C" void hc_ct_destroy(hc_ct* ct) { delete ct; }
+
+// =====================================================================
+// Arithmetic
+// =====================================================================
+namespace {
+int add_sub(hc_ctx* ctx, const hc_ct* x, const hc_ct* y, hc_ct** out, int op) {
+  return guard(ctx, [&] {
+    check_ct(ctx, x);
+    check_ct(ctx, y);
+    HC_CHECK(out, HC_ERR_INVALID, "null output");
+    HC_CHECK(x->level == y->level, HC_ERR_LEVEL_MISMATCH, "operands at different levels");
+    HC_CHECK(x->degree == y->degree, HC_ERR_INVALID, "operands of different degree");
+    check_scales(x->scale, y->scale);
+    hc_ct* c = new_ct(ctx, x->level, x->degree, x->scale);
+    std::vector<BufPtr> keep;
+    std::vector<CtRef> ro{c->ref()}, rx{x->ref()}, ry{y->ref()};
+    launch_ew(ctx, op, refs_dev(ctx, ro, keep), refs_dev(ctx, rx, keep), refs_dev(ctx, ry, keep), 1, x->degree + 1,
+              x->level + 1);
+    *out = c;
+  });
+}
+}  // namespace
+
+extern "C" int hc_add(hc_ctx* ctx, const hc_ct* x, const hc_ct* y, hc_ct** out) {
+  return ctx ? add_sub(ctx, x, y, out, 0) : HC_ERR_INVALID;
+}
+extern "C" int hc_sub(hc_ctx* ctx, const hc_ct* x, const hc_ct* y, hc_ct** out) {
+  return ctx ? add_sub(ctx, x, y, out, 1) : HC_ERR_INVALID;
+}
+
+extern "C" int hc_add_const(hc_ctx* ctx, const hc_ct* x, double c, hc_ct** out) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    check_ct(ctx, x);
+    HC_CHECK(out, HC_ERR_INVALID, "null output");
+    std::vector<u64> sc;
+    constant_residues(ctx, x->level, c * x->scale, false, sc);
+    hc_ct* o = new_ct(ctx, x->level, x->degree, x->scale);
+    std::vector<BufPtr> keep;
+    std::vector<CtRef> ro{o->ref()}, rx{x->ref()};
+    launch_scalar(ctx, true, refs_dev(ctx, ro, keep), refs_dev(ctx, rx, keep), 1, x->degree + 1, x->level + 1,
+                  upload(ctx, sc, keep));
+    *out = o;
+  });
+}
+
+extern "C" int hc_mul_const(hc_ctx* ctx, const hc_ct* x, double c, double cs, hc_ct** out) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    check_ct(ctx, x);
+    HC_CHECK(out && cs > 0, HC_ERR_INVALID, "bad arguments");
+    std::vector<hc_ct*> r = mul_const_cts(ctx, {x}, c, cs);
+    *out = r[0];
+  });
+}
+
+extern "C" int hc_mul(hc_ctx* ctx, const hc_ct* x, const hc_ct* y, hc_ct** out) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    check_ct(ctx, x);
+    check_ct(ctx, y);
+    HC_CHECK(out, HC_ERR_INVALID, "null output");
+    HC_CHECK(x->degree == 1 && y->degree == 1, HC_ERR_INVALID, "mul needs degree-1 ciphertexts");
+    HC_CHECK(x->level == y->level, HC_ERR_LEVEL_MISMATCH, "operands at different levels");
+    std::vector<hc_ct*> r = tensor_acc(ctx, {x}, {y}, {0}, {0}, {0, 1}, x->level, x->scale * y->scale);
+    *out = r[0];
+  });
+}
+
+extern "C" int hc_relin(hc_ctx* ctx, const hc_evk* evk, const hc_ct* x, hc_ct** out) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    check_ct(ctx, x);
+    HC_CHECK(evk && out, HC_ERR_INVALID, "null argument");
+    HC_CHECK(x->degree == 2, HC_ERR_INVALID, "relin needs a degree-2 ciphertext");
+    hc_ct* o = new_ct(ctx, x->level, 1, x->scale);
+    std::vector<hc_ct*> os{o};
+    relin_batch(ctx, evk, {x}, os);
+    *out = o;
+  });
+}
+
+extern "C" int hc_rescale(hc_ctx* ctx, const hc_ct* x, hc_ct** out) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    check_ct(ctx, x);
+    HC_CHECK(out, HC_ERR_INVALID, "null output");
+    HC_CHECK(x->level >= 1, HC_ERR_DEPTH, "no level left to rescale");
+    hc_ct* o = new_ct(ctx, x->level - 1, x->degree, x->scale / (double)ctx->P.chain[x->level]);
+    std::vector<hc_ct*> os{o};
+    rescale_cts(ctx, {x}, os);
+    *out = o;
+  });
+}
+
+extern "C" int hc_drop_to_level(hc_ctx* ctx, const hc_ct* x, int level, hc_ct** out) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    check_ct(ctx, x);
+    HC_CHECK(out && level >= 0 && level <= x->level, HC_ERR_INVALID, "bad level");
+    // a view: same polys, fewer limbs
+    *out = new hc_ct{ctx, x->buf, x->data, x->stride, level, x->degree, x->scale};
+  });
+}
+
+namespace {
+std::vector<hc_ct*> rotate_one(hc_ctx* ctx, const hc_evk* evk, const hc_ct* x, const std::vector<int>& steps,
+                               bool hoisted) {
+  HC_CHECK(x->degree == 1, HC_ERR_INVALID, "rotate needs a degree-1 ciphertext");
+  const int n = ctx->P.n, level = x->level, nq = level + 1, alpha = ctx->P.alpha;
+  std::vector<u64> gs;
+  for (int r : steps) {
+    const u64 g = galois_elt(ctx->P, r);
+    if (g != 1) HC_CHECK(evk->galois.count(g), HC_ERR_NO_KEY, "no Galois key for rotation " + std::to_string(r));
+    gs.push_back(g);
+  }
+  std::vector<hc_ct*> outs = new_cts(ctx, (int)steps.size(), level, 1, x->scale);
+  std::vector<BufPtr> keep;
+  const CtRef* xr = refs_dev(ctx, {x->ref()}, keep);
+  if (!hoisted) {
+    BufPtr tmp = ctx->buffer(2 * (size_t)nq * n);
+    keep.push_back(tmp);
+    const CtRef tr{tmp->ptr, (u64)nq * n};
+    const CtRef* trd = refs_dev(ctx, {tr}, keep);
+    for (size_t i = 0; i < gs.size(); ++i) {
+      const CtRef* od = refs_dev(ctx, {outs[i]->ref()}, keep);
+      if (gs[i] == 1) {
+        launch_ew(ctx, 3, od, xr, nullptr, 1, 2, nq);
+        continue;
+      }
+      launch_automorph(ctx, trd, xr, 1, 2, nq, gs[i]);
+      std::vector<CtRef> xs{CtRef{tmp->ptr + (size_t)nq * n, (u64)nq * n}}, b0{CtRef{tmp->ptr, (u64)nq * n}},
+          o{outs[i]->ref()};
+      keyswitch_batch(ctx, evk->galois.at(gs[i]).buf->ptr, level, xs, &b0, nullptr, o);
+    }
+    return outs;
+  }
+  // hoisted: one ModUp of c1, automorphism applied to the raised digits
+  const int next = nq + alpha, dnum = ctx->lv[level].dnum;
+  const size_t ext_words = (size_t)next * n;
+  const int* emap = ctx->ext_map_of(level);
+  BufPtr work = ctx->buffer((size_t)nq * n + 2 * (size_t)dnum * ext_words + 2 * ext_words + 2 * (size_t)nq * n +
+                            (size_t)nq * n);
+  keep.push_back(work);
+  u64* xc = work->ptr;
+  u64* ext = xc + (size_t)nq * n;
+  u64* extg = ext + (size_t)dnum * ext_words;
+  u64* acc = extg + (size_t)dnum * ext_words;
+  u64* zq = acc + 2 * ext_words;
+  u64* c0g = zq + 2 * (size_t)nq * n;
+  const CtRef* xcr = refs_dev(ctx, {CtRef{xc, 0}}, keep);
+  const CtRef* c1r = refs_dev(ctx, {CtRef{x->data + x->stride, 0}}, keep);
+  launch_ew(ctx, 3, xcr, c1r, nullptr, 1, 1, nq);
+  launch_ntt(ctx, limbset_base(xc, 0, 0, 1, nq, 0, nullptr), 1, true);
+  for (int j = 0; j < dnum; ++j) {
+    const int d0 = j * alpha, d1 = std::min(d0 + alpha, nq);
+    u64* ej = ext + (size_t)j * ext_words;
+    const CtRef* er = refs_dev(ctx, {CtRef{ej + (size_t)d0 * n, 0}}, keep);
+    const CtRef* xsr = refs_dev(ctx, {CtRef{x->data + x->stride + (size_t)d0 * n, 0}}, keep);
+    launch_ew(ctx, 3, er, xsr, nullptr, 1, 1, d1 - d0);
+    launch_modup_bconv(ctx, level, j, xc, 0, ej, 0, 1);
+    if (d0 > 0) launch_ntt(ctx, limbset_base(ej, 0, 0, 1, d0, 0, emap), 1, false);
+    launch_ntt(ctx, limbset_base(ej, 0, 0, 1, next - d1, d1, emap), 1, false);
+  }
+  for (size_t i = 0; i < gs.size(); ++i) {
+    const CtRef* od = refs_dev(ctx, {outs[i]->ref()}, keep);
+    if (gs[i] == 1) {
+      launch_ew(ctx, 3, od, xr, nullptr, 1, 2, nq);
+      continue;
+    }
+    // kappa_g on every raised digit (the NTT-domain permutation is the same for every prime)
+    const CtRef* src = refs_dev(ctx, {CtRef{ext, (u64)ext_words}}, keep);
+    const CtRef* dst = refs_dev(ctx, {CtRef{extg, (u64)ext_words}}, keep);
+    launch_automorph(ctx, dst, src, 1, dnum, next, gs[i]);
+    launch_key_product(ctx, level, extg, 0, evk->galois.at(gs[i]).buf->ptr, acc, 0, 1);
+    launch_ntt(ctx, limbset_base(acc, 0, ext_words, 2, alpha, nq, emap), 1, true);
+    launch_moddown_bconv(ctx, level, acc + (size_t)nq * n, 0, zq, 0, 1);
+    launch_ntt(ctx, limbset_base(zq, 0, (u64)nq * n, 2, nq, 0, nullptr), 1, false);
+    const CtRef* c0d = refs_dev(ctx, {CtRef{c0g, 0}}, keep);
+    const CtRef* c0s = refs_dev(ctx, {CtRef{x->data, 0}}, keep);
+    launch_automorph(ctx, c0d, c0s, 1, 1, nq, gs[i]);
+    launch_moddown_combine(ctx, level, acc, 0, zq, 0, c0d, nullptr, od, 1);
+  }
+  return outs;
+}
+}  // namespace
+
+extern "C" int hc_rotate(hc_ctx* ctx, const hc_evk* evk, const hc_ct* x, int steps, hc_ct** out) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    check_ct(ctx, x);
+    HC_CHECK(evk && out, HC_ERR_INVALID, "null argument");
+    *out = rotate_one(ctx, evk, x, {steps}, false)[0];
+  });
+}
+
+extern "C" int hc_rotate_hoisted(hc_ctx* ctx, const hc_evk* evk, const hc_ct* x, const int32_t* steps, int n,
+                                 hc_ct** outs) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    check_ct(ctx, x);
+    HC_CHECK(evk && outs && (n == 0 || steps) && n >= 0, HC_ERR_INVALID, "null argument");
+    std::vector<int> st(steps, steps + n);
+    std::vector<hc_ct*> r = rotate_one(ctx, evk, x, st, true);
+    for (int i = 0; i < n; ++i) outs[i] = r[i];
+  });
+}
+
+extern "C" int hc_mul_relin_rescale_batch(hc_ctx* ctx, const hc_evk* evk, const hc_ct* const* a,
+                                          const hc_ct* const* b, int n, hc_ct** outs) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    HC_CHECK(evk && n >= 0 && (n == 0 || (a && b && outs)), HC_ERR_INVALID, "null argument");
+    if (n == 0) return;
+    const int level = a[0]->level;
+    std::vector<const hc_ct*> xs, ws;
+    std::vector<int> xi, wi, off{0};
+    for (int i = 0; i < n; ++i) {
+      check_ct(ctx, a[i]);
+      check_ct(ctx, b[i]);
+      HC_CHECK(a[i]->level == level && b[i]->level == level, HC_ERR_LEVEL_MISMATCH, "batch mixes levels");
+      HC_CHECK(a[i]->degree == 1 && b[i]->degree == 1, HC_ERR_INVALID, "degree-1 operands expected");
+      xs.push_back(a[i]);
+      ws.push_back(b[i]);
+      xi.push_back(i);
+      wi.push_back(i);
+      off.push_back(i + 1);
+    }
+    HC_CHECK(level >= 1, HC_ERR_DEPTH, "no level left to rescale");
+    std::vector<hc_ct*> d = tensor_acc(ctx, xs, ws, xi, wi, off, level, a[0]->scale * b[0]->scale);
+    for (int i = 0; i < n; ++i) d[i]->scale = a[i]->scale * b[i]->scale;
+    std::vector<hc_ct*> r = relin_rescale(ctx, evk, d, nullptr);
+    for (int i = 0; i < n; ++i) {
+      r[i]->scale = d[i]->scale / (double)ctx->P.chain[level];
+      outs[i] = r[i];
+    }
+    free_all(d);
+  });
+}
+
+// =====================================================================
+// CNN layers
+// =====================================================================
+extern "C" int hc_enc_conv2d(hc_ctx* ctx, const hc_evk* evk, hc_packing packing, const hc_ct* const* x, int H,
+                             int W, int cin, const hc_ct* const* w, int cout, int kh, int kw, int stride, hc_ct** y) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    HC_CHECK(evk && x && w && y, HC_ERR_INVALID, "null argument");
+    HC_CHECK(H > 0 && W > 0 && cin > 0 && cout > 0 && kh > 0 && kw > 0 && stride > 0 && kh <= H && kw <= W,
+             HC_ERR_INVALID, "bad shape");
+    if (packing == HC_PACK_BATCH) {
+      const int Ho = (H - kh) / stride + 1, Wo = (W - kw) / stride + 1;
+      const int nx = H * W * cin, nw = cout * kh * kw * cin;
+      std::vector<const hc_ct*> xs(x, x + nx), ws(w, w + nw);
+      const int level = xs[0]->level;
+      for (auto* c : xs) {
+        check_ct(ctx, c);
+        HC_CHECK(c->level == level && c->degree == 1, HC_ERR_LEVEL_MISMATCH, "inputs at different levels");
+        check_scales(c->scale, xs[0]->scale);
+      }
+      for (auto* c : ws) {
+        check_ct(ctx, c);
+        HC_CHECK(c->level == level && c->degree == 1, HC_ERR_LEVEL_MISMATCH, "weights at another level");
+        check_scales(c->scale, ws[0]->scale);
+      }
+      HC_CHECK(level >= 1, HC_ERR_DEPTH, "no level left");
+      std::vector<int> xi, wi, off{0};
+      for (int m = 0; m < Ho; ++m)
+        for (int nn = 0; nn < Wo; ++nn)
+          for (int co = 0; co < cout; ++co) {
+            for (int p = 0; p < kh; ++p)
+              for (int q = 0; q < kw; ++q)
+                for (int ci = 0; ci < cin; ++ci) {
+                  xi.push_back(((m * stride + p) * W + (nn * stride + q)) * cin + ci);
+                  wi.push_back(((co * kh + p) * kw + q) * cin + ci);
+                }
+            off.push_back((int)xi.size());
+          }
+      std::vector<hc_ct*> d = tensor_acc(ctx, xs, ws, xi, wi, off, level, xs[0]->scale * ws[0]->scale);
+      std::vector<hc_ct*> r = relin_rescale(ctx, evk, d, nullptr);
+      free_all(d);
+      for (size_t i = 0; i < r.size(); ++i) y[i] = r[i];
+    } else {
+      HC_CHECK(cin == 1 && stride == 1, HC_ERR_INVALID, "single packing supports cin = 1, stride 1");
+      const hc_ct* x0 = x[0];
+      check_ct(ctx, x0);
+      std::vector<int> steps;
+      for (int p = 0; p < kh; ++p)
+        for (int q = 0; q < kw; ++q) steps.push_back(p * W + q);
+      std::vector<hc_ct*> rots = rotate_one(ctx, evk, x0, steps, false);
+      std::vector<const hc_ct*> xs(rots.begin(), rots.end()), ws(w, w + cout * kh * kw);
+      for (auto* c : ws) {
+        check_ct(ctx, c);
+        HC_CHECK(c->level == x0->level && c->degree == 1, HC_ERR_LEVEL_MISMATCH, "weights at another level");
+      }
+      std::vector<int> xi, wi, off{0};
+      for (int co = 0; co < cout; ++co) {
+        for (int t = 0; t < kh * kw; ++t) {
+          xi.push_back(t);
+          wi.push_back(co * kh * kw + t);
+        }
+        off.push_back((int)xi.size());
+      }
+      std::vector<hc_ct*> d = tensor_acc(ctx, xs, ws, xi, wi, off, x0->level, x0->scale * ws[0]->scale);
+      std::vector<hc_ct*> r = relin_rescale(ctx, evk, d, nullptr);
+      free_all(d);
+      free_all(rots);
+      for (size_t i = 0; i < r.size(); ++i) y[i] = r[i];
+    }
+  });
+}
+
+extern "C" int hc_enc_poly_act(hc_ctx* ctx, const hc_evk* evk, const hc_ct* const* x, int n, const double* coeffs,
+                               int degree, hc_ct** y) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    HC_CHECK(evk && coeffs && degree == 2 && n >= 0 && (n == 0 || (x && y)), HC_ERR_INVALID, "bad arguments");
+    if (n == 0) return;
+    std::vector<const hc_ct*> xs(x, x + n);
+    const int level = xs[0]->level;
+    for (auto* c : xs) {
+      check_ct(ctx, c);
+      HC_CHECK(c->level == level && c->degree == 1, HC_ERR_LEVEL_MISMATCH, "inputs at different levels");
+      check_scales(c->scale, xs[0]->scale);
+    }
+    const double a0 = coeffs[0], a1 = coeffs[1], a2 = coeffs[2];
+    const bool square = (a0 == 0 && a1 == 0 && a2 == 1);
+    HC_CHECK(level >= (square ? 1 : 2), HC_ERR_DEPTH, "not enough levels for the activation");
+    std::vector<int> idx(n), off(n + 1);
+    for (int i = 0; i < n; ++i) idx[i] = i;
+    std::iota(off.begin(), off.end(), 0);
+    std::vector<hc_ct*> d = tensor_acc(ctx, xs, xs, idx, idx, off, level, xs[0]->scale * xs[0]->scale);
+    std::vector<hc_ct*> t = relin_rescale(ctx, evk, d, nullptr);
+    free_all(d);
+    if (square) {
+      for (int i = 0; i < n; ++i) y[i] = t[i];
+      return;
+    }
+    std::vector<const hc_ct*> tc(t.begin(), t.end());
+    std::vector<hc_ct*> t2m = mul_const_cts(ctx, tc, a2, (double)ctx->P.chain[level - 1]);
+    std::vector<hc_ct*> t2(n);
+    {
+      std::vector<const hc_ct*> c(t2m.begin(), t2m.end());
+      t2 = new_cts(ctx, n, level - 2, 1, t2m[0]->scale / (double)ctx->P.chain[level - 1]);
+      rescale_cts(ctx, c, t2);
+      for (int i = 0; i < n; ++i) t2[i]->scale = t2m[i]->scale / (double)ctx->P.chain[level - 1];
+    }
+    free_all(t2m);
+    free_all(t);
+    if (a1 != 0) {
+      const double cs = t2[0]->scale * (double)ctx->P.chain[level] / xs[0]->scale;
+      std::vector<hc_ct*> vm = mul_const_cts(ctx, xs, a1, cs);
+      std::vector<const hc_ct*> c(vm.begin(), vm.end());
+      std::vector<hc_ct*> v = new_cts(ctx, n, level - 1, 1, vm[0]->scale / (double)ctx->P.chain[level]);
+      rescale_cts(ctx, c, v);
+      free_all(vm);
+      std::vector<BufPtr> keep;
+      std::vector<CtRef> tr, vr;
+      for (int i = 0; i < n; ++i) {
+        check_scales(t2[i]->scale, v[i]->scale);
+        tr.push_back(t2[i]->ref());
+        vr.push_back(v[i]->ref());  // v's limbs 0..level-2 are its drop to t2's level
+      }
+      const CtRef* td = refs_dev(ctx, tr, keep);
+      launch_ew(ctx, 0, td, td, refs_dev(ctx, vr, keep), n, 2, level - 1);
+      free_all(v);
+    }
+    if (a0 != 0) {
+      std::vector<u64> sc;
+      constant_residues(ctx, level - 2, a0 * t2[0]->scale, false, sc);
+      std::vector<BufPtr> keep;
+      std::vector<CtRef> tr;
+      for (int i = 0; i < n; ++i) tr.push_back(t2[i]->ref());
+      const CtRef* td = refs_dev(ctx, tr, keep);
+      launch_scalar(ctx, true, td, td, n, 2, level - 1, upload(ctx, sc, keep));
+    }
+    for (int i = 0; i < n; ++i) y[i] = t2[i];
+  });
+}
+
+extern "C" int hc_enc_pool(hc_ctx* ctx, const hc_evk* evk, hc_packing packing, const hc_ct* const* x, int C, int H,
+                           int W, hc_ct** y) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    (void)evk;
+    HC_CHECK(packing == HC_PACK_BATCH, HC_ERR_INVALID, "pooling supports batch packing");
+    HC_CHECK(x && y && C > 0 && H >= 2 && W >= 2, HC_ERR_INVALID, "bad arguments");
+    const int Ho = H / 2, Wo = W / 2, nin = H * W * C, nout = Ho * Wo * C;
+    std::vector<const hc_ct*> xs(x, x + nin);
+    const int level = xs[0]->level;
+    for (auto* c : xs) {
+      check_ct(ctx, c);
+      HC_CHECK(c->level == level && c->degree == 1, HC_ERR_LEVEL_MISMATCH, "inputs at different levels");
+      check_scales(c->scale, xs[0]->scale);
+    }
+    HC_CHECK(level >= 1, HC_ERR_DEPTH, "no level left");
+    std::vector<int> idx;
+    for (int i = 0; i < Ho; ++i)
+      for (int j = 0; j < Wo; ++j)
+        for (int c = 0; c < C; ++c) {
+          idx.push_back(((2 * i) * W + 2 * j) * C + c);
+          idx.push_back(((2 * i + 1) * W + 2 * j) * C + c);
+          idx.push_back(((2 * i) * W + 2 * j + 1) * C + c);
+          idx.push_back(((2 * i + 1) * W + 2 * j + 1) * C + c);
+        }
+    std::vector<hc_ct*> s = new_cts(ctx, nout, level, 1, xs[0]->scale);
+    {
+      std::vector<BufPtr> keep;
+      std::vector<CtRef> xr, sr;
+      for (auto* c : xs) xr.push_back(c->ref());
+      for (auto* c : s) sr.push_back(c->ref());
+      launch_sum4(ctx, refs_dev(ctx, sr, keep), refs_dev(ctx, xr, keep), ids_dev(ctx, idx, keep), nout, level + 1);
+    }
+    std::vector<const hc_ct*> sc(s.begin(), s.end());
+    std::vector<hc_ct*> m = mul_const_cts(ctx, sc, 0.25, (double)ctx->P.chain[level]);
+    free_all(s);
+    std::vector<const hc_ct*> mc(m.begin(), m.end());
+    std::vector<hc_ct*> out = new_cts(ctx, nout, level - 1, 1, m[0]->scale / (double)ctx->P.chain[level]);
+    rescale_cts(ctx, mc, out);
+    free_all(m);
+    for (int i = 0; i < nout; ++i) y[i] = out[i];
+  });
+}
+
+extern "C" int hc_enc_fc(hc_ctx* ctx, const hc_evk* evk, hc_packing packing, const hc_ct* const* x, int n_in,
+                         const hc_ct* const* w, const hc_ct* const* bias, int n_out, hc_ct** y) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    HC_CHECK(packing == HC_PACK_BATCH, HC_ERR_INVALID, "fc supports batch packing");
+    HC_CHECK(evk && x && w && y && n_in > 0 && n_out > 0, HC_ERR_INVALID, "bad arguments");
+    std::vector<const hc_ct*> xs(x, x + n_in);
+    const int level = xs[0]->level;
+    for (auto* c : xs) {
+      check_ct(ctx, c);
+      HC_CHECK(c->level == level && c->degree == 1, HC_ERR_LEVEL_MISMATCH, "inputs at different levels");
+      check_scales(c->scale, xs[0]->scale);
+    }
+    HC_CHECK(level >= 1, HC_ERR_DEPTH, "no level left");
+    std::vector<const hc_ct*> ws;
+    std::vector<hc_ct*> views;
+    for (int i = 0; i < n_in * n_out; ++i) {
+      check_ct(ctx, w[i]);
+      HC_CHECK(w[i]->level >= level && w[i]->degree == 1, HC_ERR_LEVEL_MISMATCH, "weight below the activations");
+      check_scales(w[i]->scale, w[0]->scale);
+      views.push_back(new hc_ct{ctx, w[i]->buf, w[i]->data, w[i]->stride, level, 1, w[i]->scale});
+      ws.push_back(views.back());
+    }
+    std::vector<int> xi, wi, off{0};
+    for (int r = 0; r < n_out; ++r) {
+      for (int k = 0; k < n_in; ++k) {
+        xi.push_back(k);
+        wi.push_back(r * n_in + k);
+      }
+      off.push_back((int)xi.size());
+    }
+    std::vector<hc_ct*> d = tensor_acc(ctx, xs, ws, xi, wi, off, level, xs[0]->scale * ws[0]->scale);
+    std::vector<const hc_ct*> bs;
+    if (bias)
+      for (int r = 0; r < n_out; ++r) {
+        check_ct(ctx, bias[r]);
+        bs.push_back(bias[r]);
+      }
+    std::vector<hc_ct*> r = relin_rescale(ctx, evk, d, bias ? &bs : nullptr);
+    free_all(d);
+    free_all(views);
+    for (int i = 0; i < n_out; ++i) y[i] = r[i];
+  });
+}

@@ -1,0 +1,107 @@
+// Device-side modular arithmetic and addressing shared by the kernels of
+// libhecnn.  All residues are uint64 words for primes q < 2^61.
+//
+// Constant multiplications use Shoup's precomputed quotient (V. Shoup, NTL;
+// D. Harvey, "Faster arithmetic for number-theoretic transforms", 2014):
+// with w' = floor(w 2^64 / q), a w - floor(a w' / 2^64) q lies in [0, 2q)
+// for every a < 2^64.  Products of two variable residues are accumulated
+// exactly in 128 bits and reduced once, by splitting the 128-bit value as
+// hi 2^64 + lo and reducing both halves with Shoup multiplications by the
+// constants 2^64 mod q and 1.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+
+#define HC_MAX_CHAIN 64
+
+// Per-prime constants.
+struct DMod {
+  u64 q;
+  u64 r64;     // 2^64 mod q
+  u64 r64_sh;  // floor(r64 * 2^64 / q)
+  u64 one_sh;  // floor(2^64 / q)
+};
+
+// Read-only tables of one context.
+struct Tables {
+  const u64* fwd;     // [chain][N]  psi^{brv(k)}
+  const u64* fwd_sh;  // Shoup companions
+  const u64* inv;     // [chain][N]  psi^{-brv(k)}
+  const u64* inv_sh;
+  const u64* ninv;    // [chain] N^{-1} mod q
+  const u64* ninv_sh;
+  const DMod* mods;   // [chain]
+  int log_n;
+};
+
+// A ciphertext (or any group of polynomials) in device memory: poly k, limb
+// i at p + k*stride + i*N.
+struct CtRef {
+  u64* p;
+  u64 stride;
+};
+
+// A set of limbs for batched per-limb kernels (NTT, copies): for batch item
+// z, poly k < npoly and limb slot l0 <= s < l0 + nlimb the limb lives at
+//   (refs ? refs[z].p + k*refs[z].stride : base + z*item_stride + k*poly_stride) + s*N
+// and is taken modulo chain prime prime_map ? prime_map[s] : s.
+struct LimbSet {
+  const CtRef* refs;
+  u64* base;
+  u64 item_stride;
+  u64 poly_stride;
+  int npoly;
+  int nlimb;
+  int l0;
+  const int* prime_map;
+};
+
+__device__ __forceinline__ u64* limb_ptr(const LimbSet& s, int z, int k, int slot, int n) {
+  u64* b = s.refs ? s.refs[z].p + (u64)k * s.refs[z].stride
+                  : s.base + (u64)z * s.item_stride + (u64)k * s.poly_stride;
+  return b + (u64)slot * n;
+}
+
+__device__ __forceinline__ int limb_prime(const LimbSet& s, int slot) {
+  return s.prime_map ? s.prime_map[slot] : slot;
+}
+
+// ------------------------------------------------------------ arithmetic
+#ifdef __CUDACC__
+__device__ __forceinline__ u64 csub(u64 x, u64 q) { return x >= q ? x - q : x; }
+__device__ __forceinline__ u64 addm(u64 a, u64 b, u64 q) { return csub(a + b, q); }
+__device__ __forceinline__ u64 subm(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
+__device__ __forceinline__ u64 negm(u64 a, u64 q) { return a ? q - a : 0; }
+
+// a * w mod q in [0, 2q), w < q, wsh = floor(w 2^64 / q).
+__device__ __forceinline__ u64 shoup_lazy(u64 a, u64 w, u64 wsh, u64 q) {
+  return a * w - __umul64hi(a, wsh) * q;
+}
+__device__ __forceinline__ u64 shoup(u64 a, u64 w, u64 wsh, u64 q) {
+  return csub(shoup_lazy(a, w, wsh, q), q);
+}
+
+struct U128 {
+  u64 lo, hi;
+};
+__device__ __forceinline__ void mac(U128& acc, u64 a, u64 b) {
+  u64 lo = a * b, hi = __umul64hi(a, b);
+  acc.lo += lo;
+  acc.hi += hi + (acc.lo < lo ? 1ull : 0ull);
+}
+// Fully reduced value of hi 2^64 + lo.
+__device__ __forceinline__ u64 reduce128(U128 x, const DMod& m) {
+  u64 t = shoup_lazy(x.hi, m.r64, m.r64_sh, m.q);     // hi 2^64 mod q, [0, 2q)
+  u64 r = x.lo - __umul64hi(x.lo, m.one_sh) * m.q;     // lo mod q,      [0, 2q)
+  u64 s = t + r;                                       // [0, 4q)
+  s = csub(s, 2 * m.q);
+  return csub(s, m.q);
+}
+__device__ __forceinline__ u64 mulm(u64 a, u64 b, const DMod& m) {
+  U128 x{a * b, __umul64hi(a, b)};
+  return reduce128(x, m);
+}
+#endif  // __CUDACC__

@@ -1,0 +1,205 @@
+// Host-side internals of libhecnn: handle layouts and the launchers that the
+// C ABI (hc_api.cu) composes.  Not part of the public interface.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "hc_device.cuh"
+#include "hecnn.h"
+
+// ----------------------------------------------------------- host helpers
+namespace hch {
+u64 mulmod(u64 a, u64 b, u64 q);
+u64 powmod(u64 a, u64 e, u64 q);
+u64 invmod(u64 a, u64 q);
+u64 shoup_of(u64 w, u64 q);  // floor(w 2^64 / q)
+bool is_prime(u64 n);
+int gen_primes(int log_n, const int* bits, int n, u64* out);
+std::vector<u64> gaussian_cdt(double sigma);
+u64 primitive_2n_root(int log_n, u64 q);
+int bit_reverse(int x, int bits);
+int64_t round_half_away(double x, bool* ok);
+// encode / decode (host FFT, FP64)
+void encode_coeffs(const double* re, const double* im, size_t n_slots, int log_n, double scale,
+                   std::vector<double>& coeffs);
+void decode_slots(const std::vector<double>& coeffs, int log_n, double scale, double* re,
+                  double* im, size_t n);
+// centred CRT lift of residues [limbs][N] to doubles
+void crt_centred_to_double(const u64* res, const u64* primes, int nl, int n, std::vector<double>& out);
+}  // namespace hch
+
+struct hc_params {
+  int log_n = 0, n = 0, L = 0, alpha = 0, dnum = 0;
+  std::vector<u64> chain;  // q_0..q_L, p_0..p_{alpha-1}
+  double scale = 0, sigma = 0;
+  std::vector<u64> cdt;
+  int nchain() const { return (int)chain.size(); }
+};
+
+struct hc_ctx;
+
+// A device allocation returned to the context allocator when the last
+// handle referencing it goes away.
+struct DevBuf {
+  hc_ctx* ctx = nullptr;
+  u64* ptr = nullptr;
+  size_t bytes = 0;
+  ~DevBuf();
+};
+using BufPtr = std::shared_ptr<DevBuf>;
+
+// Key-switching constants of one level (offsets into ctx->ks_dev).
+struct LevelConsts {
+  int dnum = 0;
+  // ModUp digit j: hat_inv[i] (+sh) for i < |D_j|, then hat_mod[t][i] for t < ext
+  std::vector<int> modup_off;
+  // rescale: q_l^{-1} mod q_i (+sh) for i < l, q_l mod q_i
+  int rescale_off = -1;
+};
+
+struct hc_ctx {
+  hc_params P;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  hc_allocator alloc{};
+  bool user_alloc = false;
+  Tables tab{};
+  std::vector<void*> owned;  // table allocations
+  u64* ks_dev = nullptr;     // flat constant buffer
+  std::vector<LevelConsts> lv;
+  int moddown_off = -1;      // (P/p_k)^{-1} mod p_k (+sh); (P/p_k) mod q_i; P^{-1} mod q_i (+sh)
+  int* ext_map = nullptr;    // [level][L+1+alpha] chain index of ext slot
+  std::string err;
+  uint64_t launches = 0;
+
+  u64* alloc_words(size_t words);
+  void free_words(u64* p);
+  BufPtr buffer(size_t words);
+  const int* ext_map_of(int level) const { return ext_map + level * (P.L + 1 + P.alpha); }
+  const u64* ks(int off) const { return ks_dev + off; }
+};
+
+struct hc_pt {
+  hc_ctx* ctx;
+  BufPtr buf;
+  u64* data;  // [level+1][N], NTT form
+  int level;
+  double scale;
+};
+
+struct hc_ct {
+  hc_ctx* ctx;
+  BufPtr buf;
+  u64* data;  // poly k, limb i at data + k*stride + i*N (NTT form)
+  u64 stride;
+  int level;
+  int degree;
+  double scale;
+  CtRef ref() const { return CtRef{data, stride}; }
+};
+
+struct SwitchKeyDev {
+  BufPtr buf;  // [dnum][2][L+1+alpha][N], NTT form, chain order
+};
+
+struct hc_secret_key {
+  hc_ctx* ctx;
+  BufPtr s_ntt;  // [L+1+alpha][N] s in NTT form over the whole chain
+  std::vector<int8_t> s_coeff;
+};
+
+struct hc_public_key {
+  hc_ctx* ctx;
+  BufPtr buf;  // [2][L+1][N] (b, a) NTT form
+};
+
+struct hc_eval_keys {
+  hc_ctx* ctx;
+  SwitchKeyDev relin;
+  std::map<u64, SwitchKeyDev> galois;
+};
+
+// Error plumbing.
+struct HcError {
+  int code;
+  std::string msg;
+};
+#define HC_CUDA(call)                                                                   \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      throw HcError{HC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+#define HC_CHECK(cond, code, msg) \
+  do {                            \
+    if (!(cond)) throw HcError{code, msg}; \
+  } while (0)
+
+void check_launch(hc_ctx* ctx);
+
+// Upload a small host array to fresh device memory owned by `keep`.
+template <class T>
+T* upload(hc_ctx* ctx, const std::vector<T>& v, std::vector<BufPtr>& keep) {
+  if (v.empty()) return nullptr;
+  size_t words = (v.size() * sizeof(T) + 7) / 8;
+  BufPtr b = ctx->buffer(words);
+  HC_CUDA(cudaMemcpyAsync(b->ptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+  keep.push_back(b);
+  return reinterpret_cast<T*>(b->ptr);
+}
+
+// --------------------------------------------------------------- launchers
+// NTT (forward) / inverse NTT of every limb of a LimbSet, `items` items.
+void launch_ntt(hc_ctx* ctx, const LimbSet& s, int items, bool inverse);
+
+// Samplers writing coefficient-form limbs dst + r*N for chain indices ids[r].
+void launch_sample_ternary(hc_ctx* ctx, u64 seed, u64 tag, u64* dst, const int* ids, int nl);
+void launch_sample_gauss(hc_ctx* ctx, u64 seed, u64 tag, u64* dst, const int* ids, int nl);
+void launch_sample_uniform(hc_ctx* ctx, u64 seed, u64 tag, u64* dst, const int* ids, int nl);
+void launch_reduce_signed(hc_ctx* ctx, const int64_t* src, u64* dst, const int* ids, int nl);
+
+// Elementwise over `items` cts of `npoly` polys x `nl` limbs (limb i mod q_i):
+// op 0: out = a + b, 1: out = a - b, 2: out = a * b (pointwise), 3: out = a (copy)
+void launch_ew(hc_ctx* ctx, int op, const CtRef* out, const CtRef* a, const CtRef* b, int items,
+               int npoly, int nl);
+// out = a * s_i (per-limb scalar, all polys) / out = a + s_i on poly 0 only
+void launch_scalar(hc_ctx* ctx, bool add, const CtRef* out, const CtRef* a, int items, int npoly,
+                   int nl, const u64* scal_dev);
+// Tensor products with lazy 128-bit accumulation:
+// out[o] = sum_{t<terms[o]} x[xi[o0+t]] (x) w[wi[o0+t]], o0 = off[o].
+void launch_tensor_acc(hc_ctx* ctx, const CtRef* out, const CtRef* x, const CtRef* w,
+                       const int* xi, const int* wi, const int* off, int nout, int nl);
+// NTT-domain automorphism: out = kappa_g(a) for `items` refs, npoly polys, nl limbs.
+void launch_automorph(hc_ctx* ctx, const CtRef* out, const CtRef* a, int items, int npoly, int nl,
+                      u64 g);
+// ModUp basis conversion of digit j at level `level`: reads coefficient-form
+// limbs of x (items), writes the ext limbs outside the digit into ext.
+void launch_modup_bconv(hc_ctx* ctx, int level, int j, const u64* xcoef, u64 x_item_stride,
+                        u64* ext, u64 ext_item_stride, int items);
+// Key product: acc[z][k][slot] = sum_j ext[z][j][slot] * key_j[k][chain(slot)].
+void launch_key_product(hc_ctx* ctx, int level, const u64* ext, u64 ext_item_stride,
+                        const u64* key, u64* acc, u64 acc_item_stride, int items);
+// ModDown conversion of the P part of acc (coefficient form) into z over Q_level.
+void launch_moddown_bconv(hc_ctx* ctx, int level, const u64* accp_coef, u64 accp_item_stride,
+                          u64* z, u64 z_item_stride, int items);
+// out_k = base_k + (acc_k - z_k) P^{-1} over Q_level (base may be null per k).
+void launch_moddown_combine(hc_ctx* ctx, int level, const u64* acc, u64 acc_item_stride,
+                            const u64* z, u64 z_item_stride, const CtRef* base0,
+                            const CtRef* base1, const CtRef* out, int items);
+// Rescale: lift[z][k][i] = centred(last[z][k]) mod q_i, i < level.
+void launch_rescale_lift(hc_ctx* ctx, int level, const u64* last, u64* lift, int items, int npoly);
+// out[z][k][i] = (in_i - lift_i) * q_level^{-1}.
+void launch_rescale_combine(hc_ctx* ctx, int level, const CtRef* in, const u64* lift,
+                            const CtRef* out, int items, int npoly);
+// Copies limb `slot` of each poly of each item into dst[z][k].
+void launch_gather_limb(hc_ctx* ctx, const CtRef* src, int slot, u64* dst, int items, int npoly);
+// Validity check: counts residues >= q (writes count to *bad).
+void launch_check_range(hc_ctx* ctx, const u64* data, int npoly, int nl, u64 poly_stride,
+                        unsigned long long* bad);
+// Pool sums: out[o] = (x[i0] + x[i1]) + (x[i2] + x[i3]) with idx[4o..4o+3].
+void launch_sum4(hc_ctx* ctx, const CtRef* out, const CtRef* x, const int* idx, int nout, int nl);

@@ -1,0 +1,474 @@
+// Pointwise and basis-conversion kernels of libhecnn.  Every kernel maps one
+// thread to one coefficient of one limb; grids are (N / 256, limbs, items).
+#include <algorithm>
+
+#include "hc_internal.h"
+
+namespace {
+constexpr int kT = 256;
+
+inline dim3 grid_for(hc_ctx* ctx, int ylimbs, int items) {
+  return dim3((unsigned)((ctx->P.n + kT - 1) / kT), (unsigned)ylimbs, (unsigned)items);
+}
+
+// --------------------------------------------------------------- Philox
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, key bumped
+// by the Weyl constants between rounds.
+__device__ void philox4x64(u64 c0, u64 c1, u64 c2, u64 c3, u64 k0, u64 k1, u64 out[4]) {
+  const u64 M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const u64 W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += W0;
+      k1 += W1;
+    }
+    const u64 lo0 = M0 * c0, hi0 = __umul64hi(M0, c0);
+    const u64 lo1 = M1 * c2, hi1 = __umul64hi(M1, c2);
+    const u64 n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  out[0] = c0;
+  out[1] = c1;
+  out[2] = c2;
+  out[3] = c3;
+}
+
+// Word i of stream (seed, tag, lane).
+__device__ __forceinline__ u64 stream_word(u64 seed, u64 tag, u64 lane, u64 i) {
+  u64 o[4];
+  philox4x64(i >> 2, lane, 0, 0, seed, tag, o);
+  return o[i & 3];
+}
+
+__device__ __forceinline__ u64 signed_res(long long v, u64 q) {
+  if (v >= 0) return (u64)v % q;
+  u64 m = (u64)(-(v + 1)) % q;
+  return q - 1 - m;
+}
+
+__global__ void k_ternary(u64 seed, u64 tag, u64* dst, const int* ids, int nl, Tables T) {
+  const int n = 1 << T.log_n;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const long long v = (long long)(stream_word(seed, tag, 0, (u64)i) % 3) - 1;
+  for (int r = 0; r < nl; ++r) dst[(size_t)r * n + i] = signed_res(v, T.mods[ids[r]].q);
+}
+
+struct Cdt {
+  u64 t[40];
+  int n;
+};
+
+__global__ void k_gauss(u64 seed, u64 tag, u64* dst, const int* ids, int nl, Tables T, Cdt cdt) {
+  const int n = 1 << T.log_n;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const u64 w = stream_word(seed, tag, 0, (u64)i), r = w >> 1;
+  long long mag = 0;
+  for (int k = 0; k < cdt.n; ++k) mag += (r >= cdt.t[k]) ? 1 : 0;
+  const long long v = (w & 1) ? -mag : mag;
+  for (int l = 0; l < nl; ++l) dst[(size_t)l * n + i] = signed_res(v, T.mods[ids[l]].q);
+}
+
+__global__ void k_uniform(u64 seed, u64 tag, u64* dst, const int* ids, Tables T) {
+  const int n = 1 << T.log_n;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int pid = ids[blockIdx.y];
+  u64 o[4];
+  philox4x64((u64)i >> 1, (u64)pid, 0, 0, seed, tag, o);
+  const int w = 2 * (i & 1);
+  dst[(size_t)blockIdx.y * n + i] = reduce128(U128{o[w], o[w + 1]}, T.mods[pid]);
+}
+
+__global__ void k_reduce_signed(const long long* src, u64* dst, const int* ids, Tables T) {
+  const int n = 1 << T.log_n;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  dst[(size_t)blockIdx.y * n + i] = signed_res(src[i], T.mods[ids[blockIdx.y]].q);
+}
+
+// ---------------------------------------------------------- elementwise
+__global__ void k_ew(int op, const CtRef* out, const CtRef* a, const CtRef* b, int nl, Tables T) {
+  const int n = 1 << T.log_n;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int k = blockIdx.y / nl, l = blockIdx.y % nl, z = blockIdx.z;
+  const size_t off = (size_t)l * n + c;
+  const u64 x = a[z].p[k * a[z].stride + off];
+  const u64 q = T.mods[l].q;
+  u64 r;
+  if (op == 3) {
+    r = x;
+  } else {
+    const u64 y = b[z].p[k * b[z].stride + off];
+    if (op == 0) r = addm(x, y, q);
+    else if (op == 1) r = subm(x, y, q);
+    else r = mulm(x, y, T.mods[l]);
+  }
+  out[z].p[k * out[z].stride + off] = r;
+}
+
+// scal: [nl] values then [nl] Shoup companions (for the multiply)
+__global__ void k_scalar(bool add, const CtRef* out, const CtRef* a, int nl, const u64* scal, Tables T) {
+  const int n = 1 << T.log_n;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int k = blockIdx.y / nl, l = blockIdx.y % nl, z = blockIdx.z;
+  const size_t off = (size_t)l * n + c;
+  const u64 x = a[z].p[k * a[z].stride + off];
+  const u64 q = T.mods[l].q;
+  u64 r;
+  if (add) r = (k == 0) ? addm(x, scal[l], q) : x;
+  else r = shoup(x, scal[l], scal[nl + l], q);
+  out[z].p[k * out[z].stride + off] = r;
+}
+
+// out[o] = sum_t x[xi[off[o]+t]] (x) w[wi[off[o]+t]], degree 2, lazily in 128 bits.
+__global__ void k_tensor_acc(const CtRef* out, const CtRef* x, const CtRef* w, const int* xi, const int* wi,
+                             const int* off, int nl, int chunk, Tables T) {
+  const int n = 1 << T.log_n;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int l = blockIdx.y, o = blockIdx.z;
+  const DMod md = T.mods[l];
+  const size_t lo = (size_t)l * n + c;
+  U128 a0{0, 0}, a1{0, 0}, a2{0, 0};
+  const int t0 = off[o], t1 = off[o + 1];
+  int cnt = 0;
+  for (int t = t0; t < t1; ++t) {
+    const CtRef X = x[xi[t]], Wt = w[wi[t]];
+    const u64 x0 = X.p[lo], x1 = X.p[X.stride + lo];
+    const u64 w0 = Wt.p[lo], w1 = Wt.p[Wt.stride + lo];
+    mac(a0, x0, w0);
+    mac(a1, x0, w1);
+    mac(a1, x1, w0);
+    mac(a2, x1, w1);
+    if (++cnt == chunk) {
+      cnt = 0;
+      a0 = U128{reduce128(a0, md), 0};
+      a1 = U128{reduce128(a1, md), 0};
+      a2 = U128{reduce128(a2, md), 0};
+    }
+  }
+  const CtRef O = out[o];
+  O.p[lo] = reduce128(a0, md);
+  O.p[O.stride + lo] = reduce128(a1, md);
+  O.p[2 * O.stride + lo] = reduce128(a2, md);
+}
+
+// NTT-domain automorphism: slot k holds a(psi^{e_k}), e_k = 2 brv(k) + 1;
+// kappa_g(a)(psi^{e}) = a(psi^{e g}).
+__global__ void k_automorph(const CtRef* out, const CtRef* a, int nl, u64 g, Tables T) {
+  const int logn = T.log_n, n = 1 << logn;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int poly = blockIdx.y / nl, l = blockIdx.y % nl, z = blockIdx.z;
+  const u64 mask = 2 * (u64)n - 1;
+  const u64 e = 2 * (u64)(__brev((unsigned)k) >> (32 - logn)) + 1;
+  const u64 e2 = (e * g) & mask;
+  const int src = (int)(__brev((unsigned)((e2 - 1) >> 1)) >> (32 - logn));
+  out[z].p[poly * out[z].stride + (size_t)l * n + k] = a[z].p[poly * a[z].stride + (size_t)l * n + src];
+}
+
+// ModUp: v_i = [x_i hat_inv_i]_{q_i}; y_t = sum_i v_i hat_mod[t][i] mod q_t.
+__global__ void k_modup_bconv(const u64* xcoef, u64 x_item_stride, u64* ext, u64 ext_item_stride,
+                              const u64* cst, int d0, int ns, int next, const int* emap, Tables T) {
+  const int n = 1 << T.log_n;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int z = blockIdx.z;
+  const u64* x = xcoef + (size_t)z * x_item_stride;
+  u64* y = ext + (size_t)z * ext_item_stride;
+  u64 v[16];
+  for (int i = 0; i < ns; ++i) {
+    const u64 q = T.mods[emap[d0 + i]].q;
+    v[i] = shoup(x[(size_t)(d0 + i) * n + c], cst[i], cst[ns + i], q);
+  }
+  const u64* hm = cst + 2 * ns;
+  for (int t = 0; t < next; ++t) {
+    if (t >= d0 && t < d0 + ns) continue;
+    const DMod md = T.mods[emap[t]];
+    U128 acc{0, 0};
+    for (int i = 0; i < ns; ++i) mac(acc, v[i], hm[t * ns + i]);
+    y[(size_t)t * n + c] = reduce128(acc, md);
+  }
+}
+
+// acc[z][k][s] = sum_j ext[z][j][s] * key[j][k][emap[s]]
+__global__ void k_key_product(const u64* ext, u64 ext_item_stride, const u64* key, u64* acc,
+                              u64 acc_item_stride, int dnum, int next, int nchain, const int* emap,
+                              Tables T) {
+  const int n = 1 << T.log_n;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int s = blockIdx.y, z = blockIdx.z;
+  const int pid = emap[s];
+  const DMod md = T.mods[pid];
+  const u64* e = ext + (size_t)z * ext_item_stride + (size_t)s * n + c;
+  U128 a0{0, 0}, a1{0, 0};
+  for (int j = 0; j < dnum; ++j) {
+    const u64 y = e[(size_t)j * next * n];
+    const u64* kb = key + ((size_t)(2 * j) * nchain + pid) * n + c;
+    const u64* ka = key + ((size_t)(2 * j + 1) * nchain + pid) * n + c;
+    mac(a0, y, *kb);
+    mac(a1, y, *ka);
+  }
+  u64* o = acc + (size_t)z * acc_item_stride + (size_t)s * n + c;
+  o[0] = reduce128(a0, md);
+  o[(size_t)next * n] = reduce128(a1, md);
+}
+
+// ModDown conversion P -> Q_level of both polys.
+// cst: [alpha] hat_inv, [alpha] hat_inv_sh, [L+1][alpha] hat_mod, [L+1] pinv, [L+1] pinv_sh
+__global__ void k_moddown_bconv(const u64* src, u64 src_item_stride, u64 src_poly_stride, u64* zq,
+                                u64 z_item_stride, const u64* cst, int alpha, int nq, int L,
+                                Tables T) {
+  const int n = 1 << T.log_n;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int k = blockIdx.y, z = blockIdx.z;
+  const u64* x = src + (size_t)z * src_item_stride + (size_t)k * src_poly_stride;
+  u64 v[16];
+  for (int i = 0; i < alpha; ++i) {
+    const u64 q = T.mods[L + 1 + i].q;
+    v[i] = shoup(x[(size_t)i * n + c], cst[i], cst[alpha + i], q);
+  }
+  const u64* hm = cst + 2 * alpha;
+  u64* out = zq + (size_t)z * z_item_stride + (size_t)k * nq * n;
+  for (int t = 0; t < nq; ++t) {
+    U128 acc{0, 0};
+    for (int i = 0; i < alpha; ++i) mac(acc, v[i], hm[t * alpha + i]);
+    out[(size_t)t * n + c] = reduce128(acc, T.mods[t]);
+  }
+}
+
+__global__ void k_moddown_combine(const u64* acc, u64 acc_item_stride, u64 acc_poly_stride,
+                                  const u64* zq, u64 z_item_stride, const CtRef* base0,
+                                  const CtRef* base1, const CtRef* out, const u64* pinv,
+                                  const u64* pinv_sh, int nq, Tables T) {
+  const int n = 1 << T.log_n;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int k = blockIdx.y / nq, i = blockIdx.y % nq, z = blockIdx.z;
+  const u64 q = T.mods[i].q;
+  const size_t li = (size_t)i * n + c;
+  const u64 u = acc[(size_t)z * acc_item_stride + (size_t)k * acc_poly_stride + li];
+  const u64 zz = zq[(size_t)z * z_item_stride + (size_t)k * nq * n + li];
+  u64 r = shoup(subm(u, zz, q), pinv[i], pinv_sh[i], q);
+  const CtRef* base = k == 0 ? base0 : base1;
+  if (base) r = addm(r, base[z].p[li], q);
+  out[z].p[(size_t)k * out[z].stride + li] = r;
+}
+
+__global__ void k_gather_limb(const CtRef* src, int slot, u64* dst, int npoly, Tables T) {
+  const int n = 1 << T.log_n;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int k = blockIdx.y, z = blockIdx.z;
+  dst[((size_t)z * npoly + k) * n + c] = src[z].p[(size_t)k * src[z].stride + (size_t)slot * n + c];
+}
+
+// lift[z][k][i] = centred(last[z][k]) mod q_i
+__global__ void k_rescale_lift(const u64* last, u64* lift, int level, int npoly, Tables T) {
+  const int n = 1 << T.log_n;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int i = blockIdx.y % level, k = blockIdx.y / level, z = blockIdx.z;
+  const u64 ql = T.mods[level].q;
+  const DMod mi = T.mods[i];
+  const u64 r = last[((size_t)z * npoly + k) * n + c];
+  u64 v;
+  if (r > (ql - 1) / 2) {
+    const u64 m = csub(shoup_lazy(ql - r, 1, mi.one_sh, mi.q), mi.q);  // (q_l - r) mod q_i
+    v = negm(m, mi.q);
+  } else {
+    v = csub(shoup_lazy(r, 1, mi.one_sh, mi.q), mi.q);
+  }
+  lift[(((size_t)z * npoly + k) * level + i) * n + c] = v;
+}
+
+// cst: [level] q_l^{-1} mod q_i, [level] Shoup companions
+__global__ void k_rescale_combine(const CtRef* in, const u64* lift, const CtRef* out, const u64* cst,
+                                  int level, int npoly, Tables T) {
+  const int n = 1 << T.log_n;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int i = blockIdx.y % level, k = blockIdx.y / level, z = blockIdx.z;
+  const u64 q = T.mods[i].q;
+  const u64 x = in[z].p[(size_t)k * in[z].stride + (size_t)i * n + c];
+  const u64 y = lift[(((size_t)z * npoly + k) * level + i) * n + c];
+  out[z].p[(size_t)k * out[z].stride + (size_t)i * n + c] = shoup(subm(x, y, q), cst[i], cst[level + i], q);
+}
+
+__global__ void k_check_range(const u64* data, int nl, u64 poly_stride, unsigned long long* bad, Tables T) {
+  const int n = 1 << T.log_n;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int k = blockIdx.y / nl, l = blockIdx.y % nl;
+  if (data[(size_t)k * poly_stride + (size_t)l * n + c] >= T.mods[l].q) atomicAdd(bad, 1ull);
+}
+
+__global__ void k_sum4(const CtRef* out, const CtRef* x, const int* idx, int nl, Tables T) {
+  const int n = 1 << T.log_n;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int k = blockIdx.y / nl, l = blockIdx.y % nl, o = blockIdx.z;
+  const u64 q = T.mods[l].q;
+  const size_t off = (size_t)l * n + c;
+  const int* id = idx + 4 * o;
+  const CtRef A = x[id[0]], B = x[id[1]], C = x[id[2]], D = x[id[3]];
+  const u64 s1 = addm(A.p[k * A.stride + off], B.p[k * B.stride + off], q);
+  const u64 s2 = addm(C.p[k * C.stride + off], D.p[k * D.stride + off], q);
+  out[o].p[k * out[o].stride + off] = addm(s1, s2, q);
+}
+
+}  // namespace
+
+void check_launch(hc_ctx* ctx) {
+  (void)ctx;
+  HC_CUDA(cudaGetLastError());
+}
+
+#define LAUNCH_DONE(ctx) \
+  do {                   \
+    (ctx)->launches++;   \
+    check_launch(ctx);   \
+  } while (0)
+
+void launch_sample_ternary(hc_ctx* ctx, u64 seed, u64 tag, u64* dst, const int* ids, int nl) {
+  k_ternary<<<grid_for(ctx, 1, 1), kT, 0, ctx->stream>>>(seed, tag, dst, ids, nl, ctx->tab);
+  LAUNCH_DONE(ctx);
+}
+
+void launch_sample_gauss(hc_ctx* ctx, u64 seed, u64 tag, u64* dst, const int* ids, int nl) {
+  Cdt cdt{};
+  HC_CHECK(ctx->P.cdt.size() <= 40, HC_ERR_INVALID, "sigma too large");
+  cdt.n = (int)ctx->P.cdt.size();
+  for (int i = 0; i < cdt.n; ++i) cdt.t[i] = ctx->P.cdt[i];
+  k_gauss<<<grid_for(ctx, 1, 1), kT, 0, ctx->stream>>>(seed, tag, dst, ids, nl, ctx->tab, cdt);
+  LAUNCH_DONE(ctx);
+}
+
+void launch_sample_uniform(hc_ctx* ctx, u64 seed, u64 tag, u64* dst, const int* ids, int nl) {
+  k_uniform<<<grid_for(ctx, nl, 1), kT, 0, ctx->stream>>>(seed, tag, dst, ids, ctx->tab);
+  LAUNCH_DONE(ctx);
+}
+
+void launch_reduce_signed(hc_ctx* ctx, const int64_t* src, u64* dst, const int* ids, int nl) {
+  k_reduce_signed<<<grid_for(ctx, nl, 1), kT, 0, ctx->stream>>>((const long long*)src, dst, ids, ctx->tab);
+  LAUNCH_DONE(ctx);
+}
+
+void launch_ew(hc_ctx* ctx, int op, const CtRef* out, const CtRef* a, const CtRef* b, int items,
+               int npoly, int nl) {
+  if (items <= 0) return;
+  k_ew<<<grid_for(ctx, npoly * nl, items), kT, 0, ctx->stream>>>(op, out, a, b, nl, ctx->tab);
+  LAUNCH_DONE(ctx);
+}
+
+void launch_scalar(hc_ctx* ctx, bool add, const CtRef* out, const CtRef* a, int items, int npoly,
+                   int nl, const u64* scal_dev) {
+  if (items <= 0) return;
+  k_scalar<<<grid_for(ctx, npoly * nl, items), kT, 0, ctx->stream>>>(add, out, a, nl, scal_dev, ctx->tab);
+  LAUNCH_DONE(ctx);
+}
+
+void launch_tensor_acc(hc_ctx* ctx, const CtRef* out, const CtRef* x, const CtRef* w, const int* xi,
+                       const int* wi, const int* off, int nout, int nl) {
+  if (nout <= 0) return;
+  // products are < qmax^2 and a1 gains two per term: fold before 2^128
+  u64 qmax = 0;
+  for (int i = 0; i < nl; ++i) qmax = ctx->P.chain[i] > qmax ? ctx->P.chain[i] : qmax;
+  unsigned __int128 sq = (unsigned __int128)qmax * qmax;
+  unsigned __int128 lim = (~(unsigned __int128)0) - ((unsigned __int128)1 << 64);
+  unsigned __int128 per = lim / (2 * sq);
+  int chunk = per > 1024 ? 1024 : (int)per - 1;
+  HC_CHECK(chunk >= 1, HC_ERR_INVALID, "primes too large for lazy accumulation");
+  HC_CHECK(nout <= 65535, HC_ERR_INVALID, "too many outputs in one launch");
+  k_tensor_acc<<<grid_for(ctx, nl, nout), kT, 0, ctx->stream>>>(out, x, w, xi, wi, off, nl, chunk, ctx->tab);
+  LAUNCH_DONE(ctx);
+}
+
+void launch_automorph(hc_ctx* ctx, const CtRef* out, const CtRef* a, int items, int npoly, int nl, u64 g) {
+  if (items <= 0) return;
+  k_automorph<<<grid_for(ctx, npoly * nl, items), kT, 0, ctx->stream>>>(out, a, nl, g, ctx->tab);
+  LAUNCH_DONE(ctx);
+}
+
+void launch_modup_bconv(hc_ctx* ctx, int level, int j, const u64* xcoef, u64 x_item_stride, u64* ext,
+                        u64 ext_item_stride, int items) {
+  const int alpha = ctx->P.alpha;
+  const int d0 = j * alpha;
+  const int ns = std::min(alpha, level + 1 - d0);
+  const int next = level + 1 + alpha;
+  HC_CHECK(ns >= 1 && ns <= 16, HC_ERR_INVALID, "bad digit");
+  k_modup_bconv<<<grid_for(ctx, 1, items), kT, 0, ctx->stream>>>(
+      xcoef, x_item_stride, ext, ext_item_stride, ctx->ks(ctx->lv[level].modup_off[j]), d0, ns, next,
+      ctx->ext_map_of(level), ctx->tab);
+  LAUNCH_DONE(ctx);
+}
+
+void launch_key_product(hc_ctx* ctx, int level, const u64* ext, u64 ext_item_stride, const u64* key,
+                        u64* acc, u64 acc_item_stride, int items) {
+  const int next = level + 1 + ctx->P.alpha;
+  k_key_product<<<grid_for(ctx, next, items), kT, 0, ctx->stream>>>(
+      ext, ext_item_stride, key, acc, acc_item_stride, ctx->lv[level].dnum, next, ctx->P.nchain(),
+      ctx->ext_map_of(level), ctx->tab);
+  LAUNCH_DONE(ctx);
+}
+
+void launch_moddown_bconv(hc_ctx* ctx, int level, const u64* accp_coef, u64 accp_item_stride,
+                          u64* z, u64 z_item_stride, int items) {
+  const int next = level + 1 + ctx->P.alpha;
+  k_moddown_bconv<<<grid_for(ctx, 2, items), kT, 0, ctx->stream>>>(
+      accp_coef, accp_item_stride, (u64)next * ctx->P.n, z, z_item_stride, ctx->ks(ctx->moddown_off),
+      ctx->P.alpha, level + 1, ctx->P.L, ctx->tab);
+  LAUNCH_DONE(ctx);
+}
+
+void launch_moddown_combine(hc_ctx* ctx, int level, const u64* acc, u64 acc_item_stride, const u64* z,
+                            u64 z_item_stride, const CtRef* base0, const CtRef* base1, const CtRef* out,
+                            int items) {
+  const int nq = level + 1, next = level + 1 + ctx->P.alpha, L = ctx->P.L, a = ctx->P.alpha;
+  const u64* cst = ctx->ks(ctx->moddown_off);
+  const u64* pinv = cst + 2 * a + (size_t)(L + 1) * a;
+  const u64* pinv_sh = pinv + (L + 1);
+  k_moddown_combine<<<grid_for(ctx, 2 * nq, items), kT, 0, ctx->stream>>>(
+      acc, acc_item_stride, (u64)next * ctx->P.n, z, z_item_stride, base0, base1, out, pinv, pinv_sh, nq,
+      ctx->tab);
+  LAUNCH_DONE(ctx);
+}
+
+void launch_rescale_lift(hc_ctx* ctx, int level, const u64* last, u64* lift, int items, int npoly) {
+  k_rescale_lift<<<grid_for(ctx, npoly * level, items), kT, 0, ctx->stream>>>(last, lift, level, npoly, ctx->tab);
+  LAUNCH_DONE(ctx);
+}
+
+void launch_rescale_combine(hc_ctx* ctx, int level, const CtRef* in, const u64* lift, const CtRef* out,
+                            int items, int npoly) {
+  k_rescale_combine<<<grid_for(ctx, npoly * level, items), kT, 0, ctx->stream>>>(
+      in, lift, out, ctx->ks(ctx->lv[level].rescale_off), level, npoly, ctx->tab);
+  LAUNCH_DONE(ctx);
+}
+
+void launch_gather_limb(hc_ctx* ctx, const CtRef* src, int slot, u64* dst, int items, int npoly) {
+  k_gather_limb<<<grid_for(ctx, npoly, items), kT, 0, ctx->stream>>>(src, slot, dst, npoly, ctx->tab);
+  LAUNCH_DONE(ctx);
+}
+
+void launch_check_range(hc_ctx* ctx, const u64* data, int npoly, int nl, u64 poly_stride,
+                        unsigned long long* bad) {
+  k_check_range<<<grid_for(ctx, npoly * nl, 1), kT, 0, ctx->stream>>>(data, nl, poly_stride, bad, ctx->tab);
+  LAUNCH_DONE(ctx);
+}
+
+void launch_sum4(hc_ctx* ctx, const CtRef* out, const CtRef* x, const int* idx, int nout, int nl) {
+  if (nout <= 0) return;
+  k_sum4<<<grid_for(ctx, 2 * nl, nout), kT, 0, ctx->stream>>>(out, x, idx, nl, ctx->tab);
+  LAUNCH_DONE(ctx);
+}

@@ -1,0 +1,79 @@
+"""Parameter sets and seeded synthetic inputs (no homomorphic arithmetic here).
+
+Inputs stand in for the paper's MNIST workload (Sec. "Dataset and Inference
+Results": 28x28 grayscale images) and trained weights, which are not
+available: images are U[0,1] 28x28, weights N(0, 0.3), drawn from
+numpy.random.Generator(PCG64(seed)).  Integer plaintexts for bit-exact
+parity runs are drawn the same way.  Both the GPU path and the CPU oracle
+consume these arrays; neither side's arithmetic lives in this module.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+MASTER_SEED = 0x2102_0031_9000
+
+
+@dataclass(frozen=True)
+class ParamSet:
+    name: str
+    log_n: int
+    q_bits: tuple
+    p_bits: tuple
+    log2_scale: float
+    sigma: float = 3.2
+
+    @property
+    def n(self):
+        return 1 << self.log_n
+
+    @property
+    def slots(self):
+        return self.n // 2
+
+
+# N = 2^12, primes 50, 30, 30 bits + one 50-bit special prime, scale 2^30:
+# one 8x8 image per ciphertext, conv by rotations then x^2 (two levels, so a
+# second 30-bit rescale prime is added to the 50 + 30 chain).
+SINGLE_N12 = ParamSet("single_n12", 12, (50, 30, 30), (50,), 30)
+# N = 2^14, q_0 60 bits + six 40-bit primes, one 60-bit special prime,
+# scale 2^40 (logQP = 360 <= 438): batch-packed CNN, 8192 images.
+BATCH_N14 = ParamSet("batch_n14", 14, (60,) + (40,) * 6, (60,), 40)
+# N = 2^16, q_0 60 bits + twenty 50-bit primes, seven 60-bit special primes
+# (dnum = 3), scale 2^50: the per-operation HMult + relin + rescale workload.
+DEEP_N16 = ParamSet("deep_n16_l20", 16, (60,) + (50,) * 20, (60,) * 7, 50)
+
+PARAM_SETS = {p.name: p for p in (SINGLE_N12, BATCH_N14, DEEP_N16)}
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def images(seed: int, count: int, h: int = 28, w: int = 28) -> np.ndarray:
+    """count x h x w images with U[0,1] pixels."""
+    return rng(seed).uniform(0.0, 1.0, (count, h, w))
+
+
+def conv_weights(seed: int, cout: int, kh: int, kw: int, cin: int = 1) -> np.ndarray:
+    return rng(seed).normal(0.0, 0.3, (cout, kh, kw, cin))
+
+
+def fc_weights(seed: int, n_out: int, n_in: int) -> np.ndarray:
+    return rng(seed).normal(0.0, 0.3, (n_out, n_in))
+
+
+def slot_values(seed: int, count: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
+    return rng(seed).uniform(lo, hi, count)
+
+
+def int_plaintext(seed: int, n: int, bound: int) -> np.ndarray:
+    """A random integer polynomial with coefficients in [-bound, bound]."""
+    return rng(seed).integers(-bound, bound + 1, n, dtype=np.int64)
+
+
+# Batch-packed CNN of the N = 2^14 workload: conv 5x5 stride 2 with 5
+# channels -> x^2 -> 2x2 mean pool -> FC 180 -> 10.
+CNN_BATCH = dict(H=28, W=28, cin=1, cout=5, k=5, stride=2, act=(0.0, 0.0, 1.0), n_out=10)

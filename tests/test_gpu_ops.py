@@ -1,0 +1,173 @@
+"""GPU parity of the scheme operations against the CPU oracle, through the C
+ABI.  Integer results are compared bit for bit in coefficient form."""
+import numpy as np
+import pytest
+
+from oracle import ckks, encoding
+from paper_2102_00319_gb300 import hecnn as H
+from paper_2102_00319_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pair():
+    from hc_pair import Pair
+    # N = 2^10, five q primes and two special primes: dnum = 3 with a
+    # truncated last digit; several NTT tiles per limb.
+    return Pair(10, [60, 40, 40, 40, 40], [60, 60], 40, seed=11, rot_steps=[1, 3, -1, 5, 17])
+
+
+@pytest.fixture(scope="module")
+def pair12():
+    from hc_pair import Pair
+    return Pair(12, [50, 30, 30], [50], 30, seed=12, rot_steps=[1, 8])
+
+
+def test_keys_bit_exact(pair):
+    ctx = pair.ctx
+    s = H.hc_sk_export(ctx, pair.g_sk)
+    assert np.array_equal(s.astype(np.int64), pair.o_sk.s)
+    pk = H.hc_pk_export(ctx, pair.g_pk)
+    assert np.array_equal(pk[0], pair.o_pk.b) and np.array_equal(pk[1], pair.o_pk.a)
+    rk = H.hc_evk_export(ctx, pair.g_evk, 1)
+    for j in range(pair.op.dnum):
+        assert np.array_equal(rk[j, 0], pair.o_evk.relin.b[j]), j
+        assert np.array_equal(rk[j, 1], pair.o_evk.relin.a[j]), j
+    for g, swk in pair.o_evk.galois.items():
+        gk = H.hc_evk_export(ctx, pair.g_evk, g)
+        for j in range(pair.op.dnum):
+            assert np.array_equal(gk[j, 0], swk.b[j]) and np.array_equal(gk[j, 1], swk.a[j]), (g, j)
+
+
+def test_encrypt_bit_exact_all_levels(pair):
+    for lv in range(pair.op.L + 1):
+        m = W.int_plaintext(100 + lv, pair.op.N, 2 ** 45)
+        g, o = pair.encrypt(m, level=lv, nonce=lv)
+        pair.assert_same(g, o, "encrypt level %d" % lv)
+
+
+def test_import_export_roundtrip(pair):
+    rng = W.rng(5)
+    q = pair.op.q
+    data = np.stack([np.stack([rng.integers(0, qi, pair.op.N, dtype=np.uint64) for qi in q[:4]]) for _ in range(2)])
+    ct = H.hc_ct_import(pair.ctx, data, 3, 1, 2.0 ** 40)
+    back, meta = H.hc_ct_export(pair.ctx, ct)
+    assert np.array_equal(back, data) and meta.level == 3
+
+
+def test_import_rejects_out_of_range(pair):
+    data = np.zeros((2, 1, pair.op.N), dtype=np.uint64)
+    data[1, 0, 7] = pair.op.q[0]
+    with pytest.raises(H.HcError) as e:
+        H.hc_ct_import(pair.ctx, data, 0, 1, 1.0)
+    assert e.value.code == -1
+
+
+def test_mul_relin_rescale_bit_exact(pair):
+    op = pair.op
+    za, zb = W.slot_values(1, op.K), W.slot_values(2, op.K)
+    for lv in (op.L, 3, 2, 1):
+        ga, oa = pair.encrypt(pair.encode_int(za), level=lv, nonce=10 + lv)
+        gb, ob = pair.encrypt(pair.encode_int(zb), level=lv, nonce=20 + lv)
+        gd = H.hc_mul(pair.ctx, ga, gb)
+        od = ckks.mul(op, oa, ob)
+        pair.assert_same(gd, od, "tensor l=%d" % lv)
+        gr = H.hc_relin(pair.ctx, pair.g_evk, gd)
+        orl = ckks.relin(op, pair.o_evk, od)
+        pair.assert_same(gr, orl, "relin l=%d" % lv)
+        gs = H.hc_rescale(pair.ctx, gr)
+        os_ = ckks.rescale(op, orl)
+        pair.assert_same(gs, os_, "rescale l=%d" % lv)
+        got = pair.decrypt_gpu(gs)
+        assert np.max(np.abs(got - za * zb)) < 2.0 ** -15
+
+
+def test_rescale_degree2_and_level_errors(pair):
+    op = pair.op
+    ga, oa = pair.encrypt_values(W.slot_values(3, op.K), level=2, nonce=40)
+    gd, od = H.hc_mul(pair.ctx, ga, ga), ckks.mul(op, oa, oa)
+    pair.assert_same(H.hc_rescale(pair.ctx, gd), ckks.rescale(op, od), "rescale degree 2")
+    g0, _ = pair.encrypt_values(W.slot_values(3, op.K), level=0, nonce=41)
+    with pytest.raises(H.HcError) as e:
+        H.hc_rescale(pair.ctx, g0)
+    assert e.value.code == -5
+    with pytest.raises(H.HcError) as e:
+        H.hc_add(pair.ctx, ga, g0)
+    assert e.value.code == -2
+
+
+def test_rotations_bit_exact(pair):
+    op = pair.op
+    z = W.slot_values(4, op.K)
+    g, o = pair.encrypt_values(z, level=3, nonce=50)
+    for r in (1, 3, -1, 5, 0, op.K):
+        pair.assert_same(H.hc_rotate(pair.ctx, pair.g_evk, g, r), ckks.rotate(op, pair.o_evk, o, r), "rot %d" % r)
+    steps = [1, 5, 17, 0]
+    gh = H.hc_rotate_hoisted(pair.ctx, pair.g_evk, g, steps)
+    oh = ckks.rotate_hoisted(op, pair.o_evk, o, steps)
+    for r, a, b in zip(steps, gh, oh):
+        pair.assert_same(a, b, "hoisted %d" % r)
+        assert np.max(np.abs(pair.decrypt_gpu(a) - np.roll(z, -r))) < 2.0 ** -15
+    with pytest.raises(H.HcError) as e:
+        H.hc_rotate(pair.ctx, pair.g_evk, g, 2)
+    assert e.value.code == -4
+
+
+def test_add_sub_constants(pair):
+    op = pair.op
+    ga, oa = pair.encrypt_values(W.slot_values(6, op.K), level=4, nonce=60)
+    gb, ob = pair.encrypt_values(W.slot_values(7, op.K), level=4, nonce=61)
+    pair.assert_same(H.hc_add(pair.ctx, ga, gb), ckks.add(op, oa, ob), "add")
+    pair.assert_same(H.hc_sub(pair.ctx, ga, gb), ckks.sub(op, oa, ob), "sub")
+    pair.assert_same(H.hc_add_const(pair.ctx, ga, -0.47), ckks.add_const(op, oa, -0.47), "add_const")
+    cs = float(op.q[4])
+    pair.assert_same(H.hc_mul_const(pair.ctx, ga, 0.25, cs), ckks.mul_const(op, oa, 0.25, cs), "mul_const")
+    pair.assert_same(H.hc_drop_to_level(pair.ctx, ga, 1), ckks.drop_to_level(op, oa, 1), "drop")
+    gm = H.hc_mul_const(pair.ctx, ga, 0.5, 2.0 ** 20)
+    with pytest.raises(H.HcError) as e:
+        H.hc_add(pair.ctx, ga, gm)
+    assert e.value.code == -3
+
+
+def test_decrypt_matches_oracle(pair):
+    op = pair.op
+    z = W.slot_values(8, op.K)
+    g, o = pair.encrypt_values(z, level=2, nonce=70)
+    gpt = H.hc_decrypt(pair.ctx, pair.g_sk, g)
+    assert np.array_equal(H.hc_pt_export(pair.ctx, gpt), ckks.decrypt(op, pair.o_sk, o).m)
+    got = H.hc_decode(pair.ctx, gpt)
+    exp = pair.decrypt_oracle(o)
+    assert np.max(np.abs(got - exp)) < 1e-9
+    assert np.max(np.abs(got - z)) < 2.0 ** -20
+
+
+def test_encode_within_one_of_oracle(pair12):
+    op = pair12.op
+    z = W.slot_values(9, op.K) + 1j * W.slot_values(10, op.K)
+    gpt = H.hc_encode(pair12.ctx, z, op.scale, 2)
+    got = H.hc_pt_export(pair12.ctx, gpt)
+    m = encoding.encode(z, op.N, op.scale)
+    exp = ckks.reduce_signed(m, op.q[:3])
+    # FP64 rounding may move a coefficient by one: |GPU - oracle| <= 1
+    for l in range(3):
+        q = op.q[l]
+        d = (got[l].astype(object) - exp[l].astype(object)) % q
+        assert all(x in (0, 1, q - 1) for x in d), l
+    back = H.hc_decode(pair12.ctx, gpt)
+    assert np.max(np.abs(back - z)) < 2.0 ** -18
+
+
+def test_batch_mul_relin_rescale(pair12):
+    op = pair12.op
+    gs, os_ = [], []
+    for i in range(5):
+        ga, oa = pair12.encrypt_values(W.slot_values(200 + i, op.K), nonce=100 + i)
+        gb, ob = pair12.encrypt_values(W.slot_values(300 + i, op.K), nonce=200 + i)
+        gs.append((ga, gb))
+        os_.append((oa, ob))
+    outs = H.hc_mul_relin_rescale_batch(pair12.ctx, pair12.g_evk, [a for a, _ in gs], [b for _, b in gs])
+    for i, (oa, ob) in enumerate(os_):
+        exp = ckks.rescale(op, ckks.relin(op, pair12.o_evk, ckks.mul(op, oa, ob)))
+        pair12.assert_same(outs[i], exp, "batch %d" % i)
+    assert H.hc_mul_relin_rescale_batch(pair12.ctx, pair12.g_evk, [], []) == []

@@ -88,7 +88,7 @@ def test_sampler_statistics():
 def test_cdt_against_mpmath():
     mpmath = pytest.importorskip("mpmath")
     mpmath.mp.dps = 100
-    sigma = mpmath.mpf("3.2")
+    sigma = mpmath.mpf(3.2)  # the double nearest 3.2, exactly
     tail = 19
     rho = [mpmath.e ** (-(k * k) / (2 * sigma * sigma)) for k in range(tail + 1)]
     z = rho[0] + 2 * sum(rho[1:])
