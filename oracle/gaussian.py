@@ -10,8 +10,9 @@ magnitude by comparing 63 random bits with the cumulative table
     cdt[k] = floor(2^63 * Pr[|X| <= k]),  k = 0 .. tail-1,
 
 with Pr[|X| = 0] = rho(0)/Z, Pr[|X| = k] = 2 rho(k)/Z and
-Z = rho(0) + 2 sum_{k=1..tail} rho(k).  The table is computed here in
-60-digit decimal arithmetic, exactly enough for 63-bit thresholds.
+Z = rho(0) + 2 sum_{k=1..tail} rho(k).  sigma is the exact value of the IEEE
+double passed in (3.2 is 3.2000000000000001776...).  The table is computed
+here in 60-digit decimal arithmetic, exactly enough for 63-bit thresholds.
 """
 import decimal
 import math
@@ -26,7 +27,7 @@ def tail_cut(sigma: float) -> int:
 def cdt_table(sigma: float = 3.2) -> np.ndarray:
     tail = tail_cut(sigma)
     ctx = decimal.Context(prec=60)
-    s = ctx.create_decimal(repr(sigma))
+    s = decimal.Decimal(float(sigma))  # exact binary value of the double
     two_s2 = ctx.multiply(2, ctx.multiply(s, s))
     rho = [ctx.exp(ctx.divide(-decimal.Decimal(k * k), two_s2)) for k in range(tail + 1)]
     z = rho[0]
