@@ -113,6 +113,19 @@ int hc_sync(hc_ctx *ctx);
 const char *hc_last_error(const hc_ctx *ctx);
 /* Number of kernels this context has launched so far. */
 uint64_t hc_kernel_launches(const hc_ctx *ctx);
+/* Per-kernel device timing (tracing aid): while enabled, every kernel launch
+ * of the context is bracketed by two CUDA events on the context stream.
+ * Enabling (on = 1) clears previous records; on = 0 stops recording. */
+int hc_profile_enable(hc_ctx *ctx, int on);
+/* Launch count, summed device time (ms) and work units of the kernel `name`
+ * since the last enable (synchronises).  A unit is one N-coefficient limb of
+ * the launch's output domain (NTT passes: limbs transformed; key product:
+ * output slots; conversions and combines: output limbs).  Unknown names
+ * report zero. */
+int hc_profile_kernel(hc_ctx *ctx, const char *name, uint64_t *launches, double *total_ms,
+                      uint64_t *units);
+/* Names of the kernels recorded, comma separated, into buf[cap]. */
+int hc_profile_names(hc_ctx *ctx, char *buf, size_t cap);
 
 /* ----------------------------------------------------------------- keys */
 /*

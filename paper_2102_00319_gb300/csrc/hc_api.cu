@@ -41,6 +41,43 @@ BufPtr hc_ctx::buffer(size_t words) {
   return b;
 }
 
+ProfScope::ProfScope(hc_ctx* c, const char* n, uint64_t u) : ctx(c), name(n), units(u) {
+  if (!ctx->prof) return;
+  auto take = [&]() {
+    cudaEvent_t e = nullptr;
+    if (!ctx->event_pool.empty()) {
+      e = ctx->event_pool.back();
+      ctx->event_pool.pop_back();
+    } else {
+      HC_CUDA(cudaEventCreate(&e));
+    }
+    return e;
+  };
+  a = take();
+  b = take();
+  HC_CUDA(cudaEventRecord(a, ctx->stream));
+}
+
+ProfScope::~ProfScope() {
+  if (!a) return;
+  cudaEventRecord(b, ctx->stream);
+  ctx->prof_events[name].push_back({a, b});
+  ctx->prof_units[name] += units;
+}
+
+namespace {
+void recycle_events(hc_ctx* ctx) {
+  for (auto& kv : ctx->prof_events)
+    for (auto& pr : kv.second) {
+      ctx->event_pool.push_back(pr.first);
+      ctx->event_pool.push_back(pr.second);
+    }
+  ctx->prof_events.clear();
+  ctx->prof_units.clear();
+}
+}  // namespace
+
+
 namespace {
 
 // Run `f`, translating exceptions into return codes and the context error.
@@ -541,6 +578,8 @@ extern "C" int hc_ctx_create(const hc_params* p, int device, void* stream, const
 extern "C" void hc_ctx_destroy(hc_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
+  recycle_events(ctx);
+  for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
   for (void* d : ctx->owned) cudaFree(d);
   delete ctx;
 }
@@ -553,6 +592,52 @@ extern "C" int hc_sync(hc_ctx* ctx) {
 extern "C" const char* hc_last_error(const hc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 extern "C" uint64_t hc_kernel_launches(const hc_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+extern "C" int hc_profile_enable(hc_ctx* ctx, int on) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    if (on) {
+      HC_CUDA(cudaStreamSynchronize(ctx->stream));
+      recycle_events(ctx);
+    }
+    ctx->prof = on != 0;
+  });
+}
+
+extern "C" int hc_profile_kernel(hc_ctx* ctx, const char* name, uint64_t* launches, double* total_ms,
+                                 uint64_t* units) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    HC_CHECK(name && launches && total_ms && units, HC_ERR_INVALID, "null argument");
+    *launches = 0;
+    *total_ms = 0;
+    *units = 0;
+    auto it = ctx->prof_events.find(name);
+    if (it == ctx->prof_events.end()) return;
+    HC_CUDA(cudaStreamSynchronize(ctx->stream));
+    double ms = 0;
+    for (auto& pr : it->second) {
+      float t = 0;
+      HC_CUDA(cudaEventElapsedTime(&t, pr.first, pr.second));
+      ms += t;
+    }
+    *launches = it->second.size();
+    *total_ms = ms;
+    *units = ctx->prof_units[name];
+  });
+}
+
+extern "C" int hc_profile_names(hc_ctx* ctx, char* buf, size_t cap) {
+  if (!ctx || !buf || cap == 0) return HC_ERR_INVALID;
+  std::string all;
+  for (auto& kv : ctx->prof_events) {
+    if (!all.empty()) all += ",";
+    all += kv.first;
+  }
+  if (all.size() + 1 > cap) return HC_ERR_INVALID;
+  std::memcpy(buf, all.c_str(), all.size() + 1);
+  return HC_OK;
+}
 
 // =====================================================================
 // Keys

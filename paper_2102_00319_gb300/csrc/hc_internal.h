@@ -76,6 +76,11 @@ struct hc_ctx {
   int* ext_map = nullptr;    // [level][L+1+alpha] chain index of ext slot
   std::string err;
   uint64_t launches = 0;
+  // tracing: events around launches while `prof` is set
+  bool prof = false;
+  std::map<std::string, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>> prof_events;
+  std::map<std::string, uint64_t> prof_units;
+  std::vector<cudaEvent_t> event_pool;
 
   u64* alloc_words(size_t words);
   void free_words(u64* p);
@@ -141,6 +146,16 @@ struct HcError {
   } while (0)
 
 void check_launch(hc_ctx* ctx);
+
+// Brackets one kernel launch with events when the context is profiling.
+struct ProfScope {
+  hc_ctx* ctx;
+  cudaEvent_t a = nullptr, b = nullptr;
+  const char* name;
+  uint64_t units;
+  ProfScope(hc_ctx* c, const char* n, uint64_t u = 0);
+  ~ProfScope();
+};
 
 // Upload a small host array to fresh device memory owned by `keep`.
 template <class T>

@@ -341,7 +341,10 @@ void check_launch(hc_ctx* ctx) {
   } while (0)
 
 void launch_sample_ternary(hc_ctx* ctx, u64 seed, u64 tag, u64* dst, const int* ids, int nl) {
-  k_ternary<<<grid_for(ctx, 1, 1), kT, 0, ctx->stream>>>(seed, tag, dst, ids, nl, ctx->tab);
+    {
+      ProfScope prof_(ctx, "k_ternary");
+      k_ternary<<<grid_for(ctx, 1, 1), kT, 0, ctx->stream>>>(seed, tag, dst, ids, nl, ctx->tab);
+    }
   LAUNCH_DONE(ctx);
 }
 
@@ -350,31 +353,46 @@ void launch_sample_gauss(hc_ctx* ctx, u64 seed, u64 tag, u64* dst, const int* id
   HC_CHECK(ctx->P.cdt.size() <= 40, HC_ERR_INVALID, "sigma too large");
   cdt.n = (int)ctx->P.cdt.size();
   for (int i = 0; i < cdt.n; ++i) cdt.t[i] = ctx->P.cdt[i];
-  k_gauss<<<grid_for(ctx, 1, 1), kT, 0, ctx->stream>>>(seed, tag, dst, ids, nl, ctx->tab, cdt);
+    {
+      ProfScope prof_(ctx, "k_gauss");
+      k_gauss<<<grid_for(ctx, 1, 1), kT, 0, ctx->stream>>>(seed, tag, dst, ids, nl, ctx->tab, cdt);
+    }
   LAUNCH_DONE(ctx);
 }
 
 void launch_sample_uniform(hc_ctx* ctx, u64 seed, u64 tag, u64* dst, const int* ids, int nl) {
-  k_uniform<<<grid_for(ctx, nl, 1), kT, 0, ctx->stream>>>(seed, tag, dst, ids, ctx->tab);
+    {
+      ProfScope prof_(ctx, "k_uniform");
+      k_uniform<<<grid_for(ctx, nl, 1), kT, 0, ctx->stream>>>(seed, tag, dst, ids, ctx->tab);
+    }
   LAUNCH_DONE(ctx);
 }
 
 void launch_reduce_signed(hc_ctx* ctx, const int64_t* src, u64* dst, const int* ids, int nl) {
-  k_reduce_signed<<<grid_for(ctx, nl, 1), kT, 0, ctx->stream>>>((const long long*)src, dst, ids, ctx->tab);
+    {
+      ProfScope prof_(ctx, "k_reduce_signed");
+      k_reduce_signed<<<grid_for(ctx, nl, 1), kT, 0, ctx->stream>>>((const long long*)src, dst, ids, ctx->tab);
+    }
   LAUNCH_DONE(ctx);
 }
 
 void launch_ew(hc_ctx* ctx, int op, const CtRef* out, const CtRef* a, const CtRef* b, int items,
                int npoly, int nl) {
   if (items <= 0) return;
-  k_ew<<<grid_for(ctx, npoly * nl, items), kT, 0, ctx->stream>>>(op, out, a, b, nl, ctx->tab);
+    {
+      ProfScope prof_(ctx, "k_ew", (uint64_t)items * npoly * nl);
+      k_ew<<<grid_for(ctx, npoly * nl, items), kT, 0, ctx->stream>>>(op, out, a, b, nl, ctx->tab);
+    }
   LAUNCH_DONE(ctx);
 }
 
 void launch_scalar(hc_ctx* ctx, bool add, const CtRef* out, const CtRef* a, int items, int npoly,
                    int nl, const u64* scal_dev) {
   if (items <= 0) return;
-  k_scalar<<<grid_for(ctx, npoly * nl, items), kT, 0, ctx->stream>>>(add, out, a, nl, scal_dev, ctx->tab);
+    {
+      ProfScope prof_(ctx, "k_scalar", (uint64_t)items * npoly * nl);
+      k_scalar<<<grid_for(ctx, npoly * nl, items), kT, 0, ctx->stream>>>(add, out, a, nl, scal_dev, ctx->tab);
+    }
   LAUNCH_DONE(ctx);
 }
 
@@ -390,13 +408,19 @@ void launch_tensor_acc(hc_ctx* ctx, const CtRef* out, const CtRef* x, const CtRe
   int chunk = per > 1024 ? 1024 : (int)per - 1;
   HC_CHECK(chunk >= 1, HC_ERR_INVALID, "primes too large for lazy accumulation");
   HC_CHECK(nout <= 65535, HC_ERR_INVALID, "too many outputs in one launch");
-  k_tensor_acc<<<grid_for(ctx, nl, nout), kT, 0, ctx->stream>>>(out, x, w, xi, wi, off, nl, chunk, ctx->tab);
+    {
+      ProfScope prof_(ctx, "k_tensor_acc", (uint64_t)nout * nl);
+      k_tensor_acc<<<grid_for(ctx, nl, nout), kT, 0, ctx->stream>>>(out, x, w, xi, wi, off, nl, chunk, ctx->tab);
+    }
   LAUNCH_DONE(ctx);
 }
 
 void launch_automorph(hc_ctx* ctx, const CtRef* out, const CtRef* a, int items, int npoly, int nl, u64 g) {
   if (items <= 0) return;
-  k_automorph<<<grid_for(ctx, npoly * nl, items), kT, 0, ctx->stream>>>(out, a, nl, g, ctx->tab);
+    {
+      ProfScope prof_(ctx, "k_automorph", (uint64_t)items * npoly * nl);
+      k_automorph<<<grid_for(ctx, npoly * nl, items), kT, 0, ctx->stream>>>(out, a, nl, g, ctx->tab);
+    }
   LAUNCH_DONE(ctx);
 }
 
@@ -407,27 +431,36 @@ void launch_modup_bconv(hc_ctx* ctx, int level, int j, const u64* xcoef, u64 x_i
   const int ns = std::min(alpha, level + 1 - d0);
   const int next = level + 1 + alpha;
   HC_CHECK(ns >= 1 && ns <= 16, HC_ERR_INVALID, "bad digit");
-  k_modup_bconv<<<grid_for(ctx, 1, items), kT, 0, ctx->stream>>>(
-      xcoef, x_item_stride, ext, ext_item_stride, ctx->ks(ctx->lv[level].modup_off[j]), d0, ns, next,
-      ctx->ext_map_of(level), ctx->tab);
+    {
+      ProfScope prof_(ctx, "k_modup_bconv", (uint64_t)items * (next - ns));
+      k_modup_bconv<<<grid_for(ctx, 1, items), kT, 0, ctx->stream>>>(
+        xcoef, x_item_stride, ext, ext_item_stride, ctx->ks(ctx->lv[level].modup_off[j]), d0, ns, next,
+        ctx->ext_map_of(level), ctx->tab);
+    }
   LAUNCH_DONE(ctx);
 }
 
 void launch_key_product(hc_ctx* ctx, int level, const u64* ext, u64 ext_item_stride, const u64* key,
                         u64* acc, u64 acc_item_stride, int items) {
   const int next = level + 1 + ctx->P.alpha;
-  k_key_product<<<grid_for(ctx, next, items), kT, 0, ctx->stream>>>(
-      ext, ext_item_stride, key, acc, acc_item_stride, ctx->lv[level].dnum, next, ctx->P.nchain(),
-      ctx->ext_map_of(level), ctx->tab);
+    {
+      ProfScope prof_(ctx, "k_key_product", (uint64_t)items * next);
+      k_key_product<<<grid_for(ctx, next, items), kT, 0, ctx->stream>>>(
+        ext, ext_item_stride, key, acc, acc_item_stride, ctx->lv[level].dnum, next, ctx->P.nchain(),
+        ctx->ext_map_of(level), ctx->tab);
+    }
   LAUNCH_DONE(ctx);
 }
 
 void launch_moddown_bconv(hc_ctx* ctx, int level, const u64* accp_coef, u64 accp_item_stride,
                           u64* z, u64 z_item_stride, int items) {
   const int next = level + 1 + ctx->P.alpha;
-  k_moddown_bconv<<<grid_for(ctx, 2, items), kT, 0, ctx->stream>>>(
-      accp_coef, accp_item_stride, (u64)next * ctx->P.n, z, z_item_stride, ctx->ks(ctx->moddown_off),
-      ctx->P.alpha, level + 1, ctx->P.L, ctx->tab);
+    {
+      ProfScope prof_(ctx, "k_moddown_bconv", (uint64_t)items * 2 * (level + 1));
+      k_moddown_bconv<<<grid_for(ctx, 2, items), kT, 0, ctx->stream>>>(
+        accp_coef, accp_item_stride, (u64)next * ctx->P.n, z, z_item_stride, ctx->ks(ctx->moddown_off),
+        ctx->P.alpha, level + 1, ctx->P.L, ctx->tab);
+    }
   LAUNCH_DONE(ctx);
 }
 
@@ -438,37 +471,55 @@ void launch_moddown_combine(hc_ctx* ctx, int level, const u64* acc, u64 acc_item
   const u64* cst = ctx->ks(ctx->moddown_off);
   const u64* pinv = cst + 2 * a + (size_t)(L + 1) * a;
   const u64* pinv_sh = pinv + (L + 1);
-  k_moddown_combine<<<grid_for(ctx, 2 * nq, items), kT, 0, ctx->stream>>>(
-      acc, acc_item_stride, (u64)next * ctx->P.n, z, z_item_stride, base0, base1, out, pinv, pinv_sh, nq,
-      ctx->tab);
+    {
+      ProfScope prof_(ctx, "k_moddown_combine", (uint64_t)items * 2 * nq);
+      k_moddown_combine<<<grid_for(ctx, 2 * nq, items), kT, 0, ctx->stream>>>(
+        acc, acc_item_stride, (u64)next * ctx->P.n, z, z_item_stride, base0, base1, out, pinv, pinv_sh, nq,
+        ctx->tab);
+    }
   LAUNCH_DONE(ctx);
 }
 
 void launch_rescale_lift(hc_ctx* ctx, int level, const u64* last, u64* lift, int items, int npoly) {
-  k_rescale_lift<<<grid_for(ctx, npoly * level, items), kT, 0, ctx->stream>>>(last, lift, level, npoly, ctx->tab);
+    {
+      ProfScope prof_(ctx, "k_rescale_lift", (uint64_t)items * npoly * level);
+      k_rescale_lift<<<grid_for(ctx, npoly * level, items), kT, 0, ctx->stream>>>(last, lift, level, npoly, ctx->tab);
+    }
   LAUNCH_DONE(ctx);
 }
 
 void launch_rescale_combine(hc_ctx* ctx, int level, const CtRef* in, const u64* lift, const CtRef* out,
                             int items, int npoly) {
-  k_rescale_combine<<<grid_for(ctx, npoly * level, items), kT, 0, ctx->stream>>>(
-      in, lift, out, ctx->ks(ctx->lv[level].rescale_off), level, npoly, ctx->tab);
+    {
+      ProfScope prof_(ctx, "k_rescale_combine", (uint64_t)items * npoly * level);
+      k_rescale_combine<<<grid_for(ctx, npoly * level, items), kT, 0, ctx->stream>>>(
+        in, lift, out, ctx->ks(ctx->lv[level].rescale_off), level, npoly, ctx->tab);
+    }
   LAUNCH_DONE(ctx);
 }
 
 void launch_gather_limb(hc_ctx* ctx, const CtRef* src, int slot, u64* dst, int items, int npoly) {
-  k_gather_limb<<<grid_for(ctx, npoly, items), kT, 0, ctx->stream>>>(src, slot, dst, npoly, ctx->tab);
+    {
+      ProfScope prof_(ctx, "k_gather_limb", (uint64_t)items * npoly);
+      k_gather_limb<<<grid_for(ctx, npoly, items), kT, 0, ctx->stream>>>(src, slot, dst, npoly, ctx->tab);
+    }
   LAUNCH_DONE(ctx);
 }
 
 void launch_check_range(hc_ctx* ctx, const u64* data, int npoly, int nl, u64 poly_stride,
                         unsigned long long* bad) {
-  k_check_range<<<grid_for(ctx, npoly * nl, 1), kT, 0, ctx->stream>>>(data, nl, poly_stride, bad, ctx->tab);
+    {
+      ProfScope prof_(ctx, "k_check_range");
+      k_check_range<<<grid_for(ctx, npoly * nl, 1), kT, 0, ctx->stream>>>(data, nl, poly_stride, bad, ctx->tab);
+    }
   LAUNCH_DONE(ctx);
 }
 
 void launch_sum4(hc_ctx* ctx, const CtRef* out, const CtRef* x, const int* idx, int nout, int nl) {
   if (nout <= 0) return;
-  k_sum4<<<grid_for(ctx, 2 * nl, nout), kT, 0, ctx->stream>>>(out, x, idx, nl, ctx->tab);
+    {
+      ProfScope prof_(ctx, "k_sum4", (uint64_t)nout * 2 * nl);
+      k_sum4<<<grid_for(ctx, 2 * nl, nout), kT, 0, ctx->stream>>>(out, x, idx, nl, ctx->tab);
+    }
   LAUNCH_DONE(ctx);
 }

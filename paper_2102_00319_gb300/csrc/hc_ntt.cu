@@ -138,11 +138,23 @@ void launch_ntt(hc_ctx* ctx, const LimbSet& s, int items, bool inverse) {
   dim3 gc(Cn / tc, ylimbs, items), gr(R / rp, ylimbs, items);
   const size_t smc = (size_t)R * tc * sizeof(u64), smr = (size_t)rp * Cn * sizeof(u64);
   if (!inverse) {
-    k_cols<false><<<gc, kThreads, smc, ctx->stream>>>(s, ctx->tab, n1, n2, tc);
-    k_rows<false><<<gr, kThreads, smr, ctx->stream>>>(s, ctx->tab, n1, n2, rp);
+    {
+      ProfScope p(ctx, "ntt_fwd_cols", (uint64_t)ylimbs * items);
+      k_cols<false><<<gc, kThreads, smc, ctx->stream>>>(s, ctx->tab, n1, n2, tc);
+    }
+    {
+      ProfScope p(ctx, "ntt_fwd_rows", (uint64_t)ylimbs * items);
+      k_rows<false><<<gr, kThreads, smr, ctx->stream>>>(s, ctx->tab, n1, n2, rp);
+    }
   } else {
-    k_rows<true><<<gr, kThreads, smr, ctx->stream>>>(s, ctx->tab, n1, n2, rp);
-    k_cols<true><<<gc, kThreads, smc, ctx->stream>>>(s, ctx->tab, n1, n2, tc);
+    {
+      ProfScope p(ctx, "ntt_inv_rows", (uint64_t)ylimbs * items);
+      k_rows<true><<<gr, kThreads, smr, ctx->stream>>>(s, ctx->tab, n1, n2, rp);
+    }
+    {
+      ProfScope p(ctx, "ntt_inv_cols", (uint64_t)ylimbs * items);
+      k_cols<true><<<gc, kThreads, smc, ctx->stream>>>(s, ctx->tab, n1, n2, tc);
+    }
   }
   ctx->launches += 2;
   check_launch(ctx);

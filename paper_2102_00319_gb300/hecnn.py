@@ -30,6 +30,7 @@ HC_PACK_SINGLE = 1
 EXPORTS = [
     "hc_params_create", "hc_params_destroy", "hc_params_primes", "hc_params_info", "hc_params_cdt",
     "hc_ctx_create", "hc_ctx_destroy", "hc_sync", "hc_last_error", "hc_kernel_launches",
+    "hc_profile_enable", "hc_profile_kernel", "hc_profile_names",
     "hc_keygen", "hc_sk_destroy", "hc_pk_destroy", "hc_evk_destroy", "hc_sk_export", "hc_pk_export",
     "hc_evk_export", "hc_encode", "hc_pt_from_coeffs", "hc_pt_export", "hc_decode", "hc_pt_level",
     "hc_pt_scale", "hc_pt_destroy", "hc_encrypt", "hc_decrypt", "hc_ct_export", "hc_ct_import",
@@ -87,6 +88,10 @@ def load(path: str = LIB_PATH):
         "hc_sync": (c_int, [vp]),
         "hc_last_error": (ctypes.c_char_p, [vp]),
         "hc_kernel_launches": (u64, [vp]),
+        "hc_profile_enable": (c_int, [vp, c_int]),
+        "hc_profile_kernel": (c_int, [vp, ctypes.c_char_p, ctypes.POINTER(u64), ctypes.POINTER(dbl),
+                                      ctypes.POINTER(u64)]),
+        "hc_profile_names": (c_int, [vp, ctypes.c_char_p, ctypes.c_size_t]),
         "hc_keygen": (c_int, [vp, u64, ctypes.POINTER(ctypes.c_int32), c_int, pp, pp, pp]),
         "hc_sk_destroy": (None, [vp]), "hc_pk_destroy": (None, [vp]), "hc_evk_destroy": (None, [vp]),
         "hc_sk_export": (c_int, [vp, vp, ctypes.POINTER(ctypes.c_int8), ctypes.c_size_t]),
@@ -294,6 +299,23 @@ def hc_sync(ctx):
 
 def hc_kernel_launches(ctx) -> int:
     return int(load().hc_kernel_launches(ctx.ptr))
+
+
+def hc_profile_enable(ctx, on=True):
+    _check(ctx, load().hc_profile_enable(ctx.ptr, 1 if on else 0))
+
+
+def hc_profile_kernel(ctx, name):
+    """(launches, total device ms, work units) of kernel `name` since profiling was enabled."""
+    n, ms, u = ctypes.c_uint64(), ctypes.c_double(), ctypes.c_uint64()
+    _check(ctx, load().hc_profile_kernel(ctx.ptr, name.encode(), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(u)))
+    return int(n.value), float(ms.value), int(u.value)
+
+
+def hc_profile_names(ctx):
+    buf = ctypes.create_string_buffer(8192)
+    _check(ctx, load().hc_profile_names(ctx.ptr, buf, 8192))
+    return [x for x in buf.value.decode().split(",") if x]
 
 
 def hc_keygen(ctx, seed, rot_steps=()):
