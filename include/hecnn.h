@@ -226,6 +226,24 @@ int hc_rotate_hoisted(hc_ctx *ctx, const hc_evk *evk, const hc_ct *x, const int3
 int hc_mul_relin_rescale_batch(hc_ctx *ctx, const hc_evk *evk, const hc_ct *const *a,
                                const hc_ct *const *b, int n, hc_ct **outs);
 
+/*
+ * Relinearisation that allocates no device memory.  The paper has no
+ * counterpart: this exists for callers that cannot allocate while they run
+ * (device memory fixed at start-up, a host thread capturing a CUDA graph,
+ * a serving loop that must not enter the allocator).  Same result as
+ * hc_relin, written into `out`, a degree-1 ciphertext at x's level that the
+ * caller allocated earlier (for example by hc_ct_import); its contents are
+ * overwritten and its scale set to x's.  Scratch comes from one static
+ * device array of 2^21 64-bit words (16 MiB) that every GPU loading the
+ * library holds until exit; a level whose key switch needs more returns
+ * HC_ERR_INVALID with the sizes in hc_last_error.  The first call on a
+ * device looks up the array's device address (with that device current):
+ * make that first call before any stream capture.  All calls share the
+ * array and it keeps the last call's contents; calls whose work overlaps on
+ * the GPU (other streams, other threads) race and must be serialised.
+ */
+int hc_relin_noalloc(hc_ctx *ctx, const hc_evk *evk, const hc_ct *x, hc_ct *out);
+
 /* ---------------------------------------------------------- CNN layers */
 typedef enum hc_packing {
   HC_PACK_BATCH = 0,  /* Fig. 2: one ciphertext per pixel / weight, slot k = image k */

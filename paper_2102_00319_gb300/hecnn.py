@@ -37,6 +37,7 @@ EXPORTS = [
     "hc_ct_meta_of", "hc_ct_destroy", "hc_add", "hc_sub", "hc_add_const", "hc_mul_const", "hc_mul",
     "hc_relin", "hc_rescale", "hc_drop_to_level", "hc_rotate", "hc_rotate_hoisted",
     "hc_mul_relin_rescale_batch", "hc_enc_conv2d", "hc_enc_poly_act", "hc_enc_pool", "hc_enc_fc",
+    "hc_relin_noalloc",
 ]
 
 
@@ -122,6 +123,7 @@ def load(path: str = LIB_PATH):
         "hc_enc_poly_act": (c_int, [vp, vp, pp, c_int, ctypes.POINTER(dbl), c_int, pp]),
         "hc_enc_pool": (c_int, [vp, vp, c_int, pp, c_int, c_int, c_int, pp]),
         "hc_enc_fc": (c_int, [vp, vp, c_int, pp, c_int, pp, pp, c_int, pp]),
+        "hc_relin_noalloc": (c_int, [vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -435,6 +437,13 @@ def hc_mul(ctx, x, y):
 
 def hc_relin(ctx, evk, x):
     return _unary("hc_relin", ctx, evk.ptr, x.ptr)
+
+
+def hc_relin_noalloc(ctx, evk, x, out):
+    """Relinearises x into the caller's existing ciphertext `out` without
+    allocating device memory (see include/hecnn.h)."""
+    _check(ctx, load().hc_relin_noalloc(ctx.ptr, evk.ptr, x.ptr, out.ptr))
+    return out
 
 
 def hc_rescale(ctx, x):
