@@ -419,7 +419,7 @@ namespace {
 void build_tables(hc_ctx* ctx) {
   const hc_params& P = ctx->P;
   const int n = P.n, nc = P.nchain(), logn = P.log_n;
-  std::vector<u64> fwd((size_t)nc * n), fwd_sh((size_t)nc * n), inv((size_t)nc * n), inv_sh((size_t)nc * n);
+  std::vector<u64> fwd(2 * (size_t)nc * n), inv(2 * (size_t)nc * n);  // interleaved (w, w')
   std::vector<u64> ninv(nc), ninv_sh(nc);
   std::vector<DMod> mods(nc);
   std::vector<u64> pw(n), ipw(n);
@@ -435,11 +435,11 @@ void build_tables(hc_ctx* ctx) {
     }
     for (int k = 0; k < n; ++k) {
       const int r = hch::bit_reverse(k, logn);
-      const size_t o = (size_t)c * n + k;
+      const size_t o = 2 * ((size_t)c * n + k);
       fwd[o] = pw[r];
-      fwd_sh[o] = hch::shoup_of(pw[r], q);
+      fwd[o + 1] = hch::shoup_of(pw[r], q);
       inv[o] = ipw[r];
-      inv_sh[o] = hch::shoup_of(ipw[r], q);
+      inv[o + 1] = hch::shoup_of(ipw[r], q);
     }
     ninv[c] = hch::invmod((u64)n % q, q);
     ninv_sh[c] = hch::shoup_of(ninv[c], q);
@@ -453,11 +453,9 @@ void build_tables(hc_ctx* ctx) {
     HC_CUDA(cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice));
     return d;
   };
-  const size_t tb = (size_t)nc * n * sizeof(u64);
-  ctx->tab.fwd = (const u64*)put(fwd.data(), tb);
-  ctx->tab.fwd_sh = (const u64*)put(fwd_sh.data(), tb);
-  ctx->tab.inv = (const u64*)put(inv.data(), tb);
-  ctx->tab.inv_sh = (const u64*)put(inv_sh.data(), tb);
+  const size_t tb = 2 * (size_t)nc * n * sizeof(u64);
+  ctx->tab.fwd2 = (const ulonglong2*)put(fwd.data(), tb);
+  ctx->tab.inv2 = (const ulonglong2*)put(inv.data(), tb);
   ctx->tab.ninv = (const u64*)put(ninv.data(), nc * sizeof(u64));
   ctx->tab.ninv_sh = (const u64*)put(ninv_sh.data(), nc * sizeof(u64));
   ctx->tab.mods = (const DMod*)put(mods.data(), nc * sizeof(DMod));

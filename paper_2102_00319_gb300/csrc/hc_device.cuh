@@ -27,10 +27,8 @@ struct DMod {
 
 // Read-only tables of one context.
 struct Tables {
-  const u64* fwd;     // [chain][N]  psi^{brv(k)}
-  const u64* fwd_sh;  // Shoup companions
-  const u64* inv;     // [chain][N]  psi^{-brv(k)}
-  const u64* inv_sh;
+  const ulonglong2* fwd2;  // [chain][N] (psi^{brv(k)}, Shoup companion)
+  const ulonglong2* inv2;  // [chain][N] (psi^{-brv(k)}, Shoup companion)
   const u64* ninv;    // [chain] N^{-1} mod q
   const u64* ninv_sh;
   const DMod* mods;   // [chain]

@@ -6,120 +6,268 @@
 // Ideal Lattice-Based Cryptography", 2016).  Input in natural order, output
 // in bit-reversed order: slot k holds a(psi^{2 brv(k) + 1}).
 // Inverse: Gentleman-Sande butterflies with psi^{-brv(k)}, then N^{-1}.
+// In stage st (m = 2^st groups, half distance t = N / 2^{st+1}) the pair
+// (j, j + t) uses twiddle index m + (j >> (log N - st)).
 //
-// N = 2^n is split as R x Cn with R = 2^n1 rows and Cn = 2^n2 columns
-// (element j = row * Cn + col).  The first n1 forward stages mix only rows
-// (strides >= Cn): a "column pass" CTA owns a tile of all R rows x TC
-// adjacent columns in shared memory.  The remaining n2 stages mix only
-// within a row: a "row pass" CTA owns RP whole rows.  The inverse runs the
-// row pass first.  Each pass reads and writes every limb once.
+// Butterflies are Harvey's lazy forms (values in [0, 4q) forward, [0, 2q)
+// inverse; "Faster arithmetic for number-theoretic transforms", 2014); each
+// pass ends fully reduced.
+//
+// N = 2^n is split as R x C with R = 2^n1 rows and C = 2^n2 columns
+// (j = row * C + col).  The first n1 forward stages mix only rows: a
+// "column pass" CTA owns all R rows of TC adjacent columns.  The remaining
+// n2 stages mix only within a row: a "row pass" CTA owns RP whole rows.
+// Inside a pass the stages run in two register rounds: 2^K1 points strided
+// by 2^K2 (the K1 long-distance stages), then 2^K2 adjacent points (the K2
+// short-distance stages), with one shared-memory exchange between them.
+// The inverse runs the rounds and the passes in the opposite order.  Each
+// pass reads and writes each limb once.
 #include "hc_internal.h"
 
 namespace {
 
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ void load_limb_meta(const LimbSet& s, const Tables& T, u64*& a, int& pid) {
-  const int n = 1 << T.log_n;
+// Forward CT stages st0 .. st0+K-1 on 2^K points; point i has global index
+// jb + (i << ls); in local stage s the pair distance is 2^{K-1-s} points.
+template <int K>
+__device__ __forceinline__ void fwd_block(u64 (&x)[1 << K], u64 jb, int ls, int st0, const ulonglong2* tw, u64 q,
+                                          int log_n) {
+  const u64 q2 = 2 * q;
+#pragma unroll
+  for (int s = 0; s < K; ++s) {
+    const int st = st0 + s;
+    const int half = 1 << (K - 1 - s);
+#pragma unroll
+    for (int i = 0; i < (1 << K); ++i) {
+      if (i & half) continue;
+      const u64 j = jb + ((u64)i << ls);
+      const ulonglong2 w = __ldg(tw + ((1ull << st) + (j >> (log_n - st))));
+      u64 X = x[i];
+      X = X >= q2 ? X - q2 : X;
+      const u64 T = shoup_lazy(x[i + half], w.x, w.y, q);
+      x[i] = X + T;
+      x[i + half] = X - T + q2;
+    }
+  }
+}
+
+// Inverse GS stages st_hi, st_hi-1, .. st_hi-K+1 on 2^K points with global
+// indices jb + (i << ls); in local stage s the pair distance is 2^s points.
+// Inputs and outputs in [0, 2q).
+template <int K>
+__device__ __forceinline__ void inv_block(u64 (&x)[1 << K], u64 jb, int ls, int st_hi, const ulonglong2* tw, u64 q,
+                                          int log_n) {
+  const u64 q2 = 2 * q;
+#pragma unroll
+  for (int s = 0; s < K; ++s) {
+    const int st = st_hi - s;
+    const int half = 1 << s;
+#pragma unroll
+    for (int i = 0; i < (1 << K); ++i) {
+      if (i & half) continue;
+      const u64 j = jb + ((u64)i << ls);
+      const ulonglong2 w = __ldg(tw + ((1ull << st) + (j >> (log_n - st))));
+      const u64 U = x[i], V = x[i + half];
+      u64 S = U + V;
+      S = S >= q2 ? S - q2 : S;
+      x[i] = S;
+      x[i + half] = shoup_lazy(U - V + q2, w.x, w.y, q);
+    }
+  }
+}
+
+__device__ __forceinline__ u64 reduce4(u64 x, u64 q) {
+  x = x >= 2 * q ? x - 2 * q : x;
+  return x >= q ? x - q : x;
+}
+
+__device__ __forceinline__ void limb_meta(const LimbSet& s, int log_n, u64*& a, int& pid) {
   const int y = blockIdx.y;
   const int k = y / s.nlimb;
-  const int slot = s.l0 + y % s.nlimb;
-  a = limb_ptr(s, blockIdx.z, k, slot, n);
+  const int slot = s.l0 + y - k * s.nlimb;
+  a = limb_ptr(s, blockIdx.z, k, slot, 1 << log_n);
   pid = limb_prime(s, slot);
 }
 
-template <bool INV>
-__global__ void __launch_bounds__(kThreads) k_cols(LimbSet s, Tables T, int n1, int n2, int tc) {
+// Column pass: stages 0..n1-1 (forward) over R = 2^(K1+K2) rows of TC = 2^tcl
+// columns starting at blockIdx.x * TC.  Shared tile [row][col].
+template <bool INV, int K1, int K2>
+__global__ void __launch_bounds__(kThreads) k_cols(LimbSet s, Tables T, int n2, int tcl) {
+  constexpr int n1 = K1 + K2;
   extern __shared__ u64 sm[];
+  const int log_n = T.log_n;
   u64* a;
   int pid;
-  load_limb_meta(s, T, a, pid);
-  const int n = 1 << T.log_n, R = 1 << n1;
+  limb_meta(s, log_n, a, pid);
   const u64 q = T.mods[pid].q;
-  const u64* w = (INV ? T.inv : T.fwd) + (size_t)pid * n;
-  const u64* wsh = (INV ? T.inv_sh : T.fwd_sh) + (size_t)pid * n;
-  const int c0 = blockIdx.x * tc;
-  const int tot = R * tc;
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-    const int r = e / tc, c = e - r * tc;
-    sm[e] = a[((size_t)r << n2) + c0 + c];
-  }
-  __syncthreads();
-  const int nb = (R >> 1) * tc;
-  for (int it = 0; it < n1; ++it) {
-    const int st = INV ? (n1 - 1 - it) : it;
-    const int m = 1 << st, th = R >> (st + 1);
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-      const int bb = b / tc, c = b - bb * tc;
-      const int grp = bb / th, off = bb - grp * th;
-      const int r = grp * 2 * th + off;
-      const u64 W = __ldg(w + m + grp), Ws = __ldg(wsh + m + grp);
-      u64* px = sm + r * tc + c;
-      u64* py = px + th * tc;
-      const u64 U = *px, V = *py;
-      if (!INV) {
-        const u64 t = shoup(V, W, Ws, q);
-        *px = addm(U, t, q);
-        *py = subm(U, t, q);
-      } else {
-        *px = addm(U, V, q);
-        *py = shoup(subm(U, V, q), W, Ws, q);
-      }
+  const ulonglong2* tw = (INV ? T.inv2 : T.fwd2) + ((size_t)pid << log_n);
+  const int TC = 1 << tcl;
+  const int c0 = blockIdx.x * TC;
+  if (!INV) {
+    // round 1: 2^K1 rows strided by 2^K2 -> stages 0..K1-1
+    for (int w = threadIdx.x; w < (TC << K2); w += blockDim.x) {
+      const int c = w & (TC - 1), r0 = w >> tcl;
+      u64 x[1 << K1];
+#pragma unroll
+      for (int i = 0; i < (1 << K1); ++i) x[i] = a[((size_t)(r0 + (i << K2)) << n2) + c0 + c];
+      fwd_block<K1>(x, (u64)r0 << n2, K2 + n2, 0, tw, q, log_n);
+#pragma unroll
+      for (int i = 0; i < (1 << K1); ++i) sm[((r0 + (i << K2)) << tcl) + c] = x[i];
     }
     __syncthreads();
-  }
-  if (INV) {
-    const u64 ni = T.ninv[pid], nis = T.ninv_sh[pid];
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) sm[e] = shoup(sm[e], ni, nis, q);
+    // round 2: 2^K2 adjacent rows -> stages K1..n1-1
+    for (int w = threadIdx.x; w < (TC << K1); w += blockDim.x) {
+      const int c = w & (TC - 1), g = w >> tcl;
+      u64 x[1 << K2];
+#pragma unroll
+      for (int i = 0; i < (1 << K2); ++i) x[i] = sm[(((g << K2) + i) << tcl) + c];
+      fwd_block<K2>(x, (u64)(g << K2) << n2, n2, K1, tw, q, log_n);
+#pragma unroll
+      for (int i = 0; i < (1 << K2); ++i) a[((size_t)((g << K2) + i) << n2) + c0 + c] = reduce4(x[i], q);
+    }
+  } else {
+    // round A: 2^K2 adjacent rows -> stages n1-1 .. K1
+    for (int w = threadIdx.x; w < (TC << K1); w += blockDim.x) {
+      const int c = w & (TC - 1), g = w >> tcl;
+      u64 x[1 << K2];
+#pragma unroll
+      for (int i = 0; i < (1 << K2); ++i) x[i] = a[((size_t)((g << K2) + i) << n2) + c0 + c];
+      inv_block<K2>(x, (u64)(g << K2) << n2, n2, n1 - 1, tw, q, log_n);
+#pragma unroll
+      for (int i = 0; i < (1 << K2); ++i) sm[(((g << K2) + i) << tcl) + c] = x[i];
+    }
     __syncthreads();
+    // round B: 2^K1 rows strided by 2^K2 -> stages K1-1 .. 0, then N^{-1}
+    const u64 ni = T.ninv[pid], nis = T.ninv_sh[pid];
+    for (int w = threadIdx.x; w < (TC << K2); w += blockDim.x) {
+      const int c = w & (TC - 1), r0 = w >> tcl;
+      u64 x[1 << K1];
+#pragma unroll
+      for (int i = 0; i < (1 << K1); ++i) x[i] = sm[((r0 + (i << K2)) << tcl) + c];
+      inv_block<K1>(x, (u64)r0 << n2, K2 + n2, K1 - 1, tw, q, log_n);
+#pragma unroll
+      for (int i = 0; i < (1 << K1); ++i)
+        a[((size_t)(r0 + (i << K2)) << n2) + c0 + c] = reduce4(shoup_lazy(x[i], ni, nis, q), q);
+    }
   }
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-    const int r = e / tc, c = e - r * tc;
-    a[((size_t)r << n2) + c0 + c] = sm[e];
+}
+
+// Row pass: stages n1..log_n-1 (forward) inside RP rows of C = 2^(K1+K2)
+// adjacent points.  Shared rows padded by one word per 2^K2 words.
+template <bool INV, int K1, int K2>
+__global__ void __launch_bounds__(kThreads) k_rows(LimbSet s, Tables T, int n1, int rpl) {
+  constexpr int n2 = K1 + K2, C = 1 << n2;
+  constexpr int PADW = C + (C >> K2);  // padded row width
+  extern __shared__ u64 sm[];
+  const int log_n = T.log_n;
+  u64* a;
+  int pid;
+  limb_meta(s, log_n, a, pid);
+  const u64 q = T.mods[pid].q;
+  const ulonglong2* tw = (INV ? T.inv2 : T.fwd2) + ((size_t)pid << log_n);
+  const int RP = 1 << rpl;
+  const int row0 = blockIdx.x * RP;
+  u64* src = a + ((size_t)row0 << n2);
+  auto sidx = [&](int r, int j) { return r * PADW + j + (j >> K2); };
+  if (!INV) {
+    // round 1: 2^K1 points strided by 2^K2 (straight from global)
+    for (int w = threadIdx.x; w < (RP << K2); w += blockDim.x) {
+      const int r = w >> K2, r0 = w & ((1 << K2) - 1);
+      u64 x[1 << K1];
+#pragma unroll
+      for (int i = 0; i < (1 << K1); ++i) x[i] = src[((size_t)r << n2) + r0 + (i << K2)];
+      fwd_block<K1>(x, ((u64)(row0 + r) << n2) + r0, K2, n1, tw, q, log_n);
+#pragma unroll
+      for (int i = 0; i < (1 << K1); ++i) sm[sidx(r, r0 + (i << K2))] = x[i];
+    }
+    __syncthreads();
+    // round 2: 2^K2 adjacent points
+    for (int w = threadIdx.x; w < (RP << K1); w += blockDim.x) {
+      const int r = w >> K1, g = w & ((1 << K1) - 1);
+      u64 x[1 << K2];
+#pragma unroll
+      for (int i = 0; i < (1 << K2); ++i) x[i] = sm[sidx(r, (g << K2) + i)];
+      fwd_block<K2>(x, ((u64)(row0 + r) << n2) + (g << K2), 0, n1 + K1, tw, q, log_n);
+#pragma unroll
+      for (int i = 0; i < (1 << K2); ++i) sm[sidx(r, (g << K2) + i)] = reduce4(x[i], q);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < (RP << n2); e += blockDim.x) src[e] = sm[sidx(e >> n2, e & (C - 1))];
+  } else {
+    for (int e = threadIdx.x; e < (RP << n2); e += blockDim.x) sm[sidx(e >> n2, e & (C - 1))] = src[e];
+    __syncthreads();
+    // round A: 2^K2 adjacent points -> stages log_n-1 .. log_n-K2
+    for (int w = threadIdx.x; w < (RP << K1); w += blockDim.x) {
+      const int r = w >> K1, g = w & ((1 << K1) - 1);
+      u64 x[1 << K2];
+#pragma unroll
+      for (int i = 0; i < (1 << K2); ++i) x[i] = sm[sidx(r, (g << K2) + i)];
+      inv_block<K2>(x, ((u64)(row0 + r) << n2) + (g << K2), 0, log_n - 1, tw, q, log_n);
+#pragma unroll
+      for (int i = 0; i < (1 << K2); ++i) sm[sidx(r, (g << K2) + i)] = x[i];
+    }
+    __syncthreads();
+    // round B: 2^K1 points strided by 2^K2 -> stages log_n-K2-1 .. n1 (to global)
+    for (int w = threadIdx.x; w < (RP << K2); w += blockDim.x) {
+      const int r = w >> K2, r0 = w & ((1 << K2) - 1);
+      u64 x[1 << K1];
+#pragma unroll
+      for (int i = 0; i < (1 << K1); ++i) x[i] = sm[sidx(r, r0 + (i << K2))];
+      inv_block<K1>(x, ((u64)(row0 + r) << n2) + r0, K2, log_n - 1 - K2, tw, q, log_n);
+#pragma unroll
+      for (int i = 0; i < (1 << K1); ++i) src[((size_t)r << n2) + r0 + (i << K2)] = reduce4(x[i], q);
+    }
+  }
+}
+
+template <bool INV, int K1, int K2>
+void launch_cols(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, int n2) {
+  constexpr int n1 = K1 + K2;
+  // enough (column, offset) work items for every thread in both rounds
+  int tcl = 8 - (K1 < K2 ? K1 : K2);
+  if (tcl > n2) tcl = n2;
+  while (((size_t)1 << (n1 + tcl)) * sizeof(u64) > 48 * 1024) --tcl;
+  dim3 grid(1u << (n2 - tcl), ylimbs, items);
+  const size_t smem = ((size_t)1 << (n1 + tcl)) * sizeof(u64);
+  ProfScope p(ctx, INV ? "ntt_inv_cols" : "ntt_fwd_cols", (uint64_t)ylimbs * items);
+  k_cols<INV, K1, K2><<<grid, kThreads, smem, ctx->stream>>>(s, ctx->tab, n2, tcl);
+}
+
+template <bool INV, int K1, int K2>
+void launch_rows(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, int n1) {
+  constexpr int n2 = K1 + K2;
+  int rpl = 8 - (K1 < K2 ? K1 : K2);
+  if (rpl > n1) rpl = n1;
+  const size_t padw = ((size_t)1 << n2) + ((size_t)1 << (n2 - K2));
+  while (((size_t)1 << rpl) * padw * sizeof(u64) > 48 * 1024) --rpl;
+  dim3 grid(1u << (n1 - rpl), ylimbs, items);
+  const size_t smem = ((size_t)1 << rpl) * padw * sizeof(u64);
+  ProfScope p(ctx, INV ? "ntt_inv_rows" : "ntt_fwd_rows", (uint64_t)ylimbs * items);
+  k_rows<INV, K1, K2><<<grid, kThreads, smem, ctx->stream>>>(s, ctx->tab, n1, rpl);
+}
+
+// Stage splits of a pass of n stages into two register rounds.
+template <bool INV>
+void cols_dispatch(hc_ctx* ctx, const LimbSet& s, int items, int y, int n1, int n2) {
+  switch (n1) {
+    case 5: launch_cols<INV, 3, 2>(ctx, s, items, y, n2); break;
+    case 6: launch_cols<INV, 3, 3>(ctx, s, items, y, n2); break;
+    case 7: launch_cols<INV, 4, 3>(ctx, s, items, y, n2); break;
+    case 8: launch_cols<INV, 4, 4>(ctx, s, items, y, n2); break;
+    default: throw HcError{HC_ERR_INVALID, "unsupported ring degree"};
   }
 }
 
 template <bool INV>
-__global__ void __launch_bounds__(kThreads) k_rows(LimbSet s, Tables T, int n1, int n2, int rp) {
-  extern __shared__ u64 sm[];
-  u64* a;
-  int pid;
-  load_limb_meta(s, T, a, pid);
-  const int n = 1 << T.log_n, rowlen = 1 << n2, half = rowlen >> 1;
-  const u64 q = T.mods[pid].q;
-  const u64* w = (INV ? T.inv : T.fwd) + (size_t)pid * n;
-  const u64* wsh = (INV ? T.inv_sh : T.fwd_sh) + (size_t)pid * n;
-  const int row0 = blockIdx.x * rp;
-  const int tot = rp * rowlen;
-  u64* src = a + (size_t)row0 * rowlen;
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) sm[e] = src[e];
-  __syncthreads();
-  const int nb = rp * half;
-  for (int it = 0; it < n2; ++it) {
-    const int st = INV ? (T.log_n - 1 - it) : (n1 + it);
-    const int m = 1 << st, t = n >> (st + 1);
-    const int groups_per_row = rowlen / (2 * t);
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-      const int row = b / half, bl = b - row * half;
-      const int gl = bl / t, off = bl - gl * t;
-      const int j = gl * 2 * t + off;
-      const int i = (row0 + row) * groups_per_row + gl;
-      const u64 W = __ldg(w + m + i), Ws = __ldg(wsh + m + i);
-      u64* px = sm + row * rowlen + j;
-      u64* py = px + t;
-      const u64 U = *px, V = *py;
-      if (!INV) {
-        const u64 tt = shoup(V, W, Ws, q);
-        *px = addm(U, tt, q);
-        *py = subm(U, tt, q);
-      } else {
-        *px = addm(U, V, q);
-        *py = shoup(subm(U, V, q), W, Ws, q);
-      }
-    }
-    __syncthreads();
+void rows_dispatch(hc_ctx* ctx, const LimbSet& s, int items, int y, int n1, int n2) {
+  switch (n2) {
+    case 5: launch_rows<INV, 3, 2>(ctx, s, items, y, n1); break;
+    case 6: launch_rows<INV, 3, 3>(ctx, s, items, y, n1); break;
+    case 7: launch_rows<INV, 4, 3>(ctx, s, items, y, n1); break;
+    case 8: launch_rows<INV, 4, 4>(ctx, s, items, y, n1); break;
+    default: throw HcError{HC_ERR_INVALID, "unsupported ring degree"};
   }
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) src[e] = sm[e];
 }
 
 }  // namespace
@@ -128,33 +276,14 @@ void launch_ntt(hc_ctx* ctx, const LimbSet& s, int items, bool inverse) {
   if (items <= 0 || s.nlimb <= 0 || s.npoly <= 0) return;
   const int log_n = ctx->P.log_n;
   const int n1 = log_n / 2, n2 = log_n - n1;
-  const int R = 1 << n1, Cn = 1 << n2;
-  const int tc = Cn < 16 ? Cn : 16;
-  int rp = 4096 >> n2;
-  if (rp < 1) rp = 1;
-  if (rp > R) rp = R;
   const int ylimbs = s.npoly * s.nlimb;
   HC_CHECK(ylimbs <= 65535 && items <= 65535, HC_ERR_INVALID, "NTT batch too large");
-  dim3 gc(Cn / tc, ylimbs, items), gr(R / rp, ylimbs, items);
-  const size_t smc = (size_t)R * tc * sizeof(u64), smr = (size_t)rp * Cn * sizeof(u64);
   if (!inverse) {
-    {
-      ProfScope p(ctx, "ntt_fwd_cols", (uint64_t)ylimbs * items);
-      k_cols<false><<<gc, kThreads, smc, ctx->stream>>>(s, ctx->tab, n1, n2, tc);
-    }
-    {
-      ProfScope p(ctx, "ntt_fwd_rows", (uint64_t)ylimbs * items);
-      k_rows<false><<<gr, kThreads, smr, ctx->stream>>>(s, ctx->tab, n1, n2, rp);
-    }
+    cols_dispatch<false>(ctx, s, items, ylimbs, n1, n2);
+    rows_dispatch<false>(ctx, s, items, ylimbs, n1, n2);
   } else {
-    {
-      ProfScope p(ctx, "ntt_inv_rows", (uint64_t)ylimbs * items);
-      k_rows<true><<<gr, kThreads, smr, ctx->stream>>>(s, ctx->tab, n1, n2, rp);
-    }
-    {
-      ProfScope p(ctx, "ntt_inv_cols", (uint64_t)ylimbs * items);
-      k_cols<true><<<gc, kThreads, smc, ctx->stream>>>(s, ctx->tab, n1, n2, tc);
-    }
+    rows_dispatch<true>(ctx, s, items, ylimbs, n1, n2);
+    cols_dispatch<true>(ctx, s, items, ylimbs, n1, n2);
   }
   ctx->launches += 2;
   check_launch(ctx);
