@@ -28,21 +28,22 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// Forward CT stages st0 .. st0+K-1 on 2^K points; point i has global index
-// jb + (i << ls); in local stage s the pair distance is 2^{K-1-s} points.
-template <int K>
-__device__ __forceinline__ void fwd_block(u64 (&x)[1 << K], u64 jb, int ls, int st0, const ulonglong2* tw, u64 q,
-                                          int log_n) {
+// Forward CT stages ST0 .. ST0+K-1 on 2^K points; point i has global index
+// jb + (i << LS), where jb has no bits in common with i << LS (so the
+// twiddle index splits into a per-stage part from jb and a constant from i).
+// In local stage s the pair distance is 2^{K-1-s} points.
+template <int K, int LS, int ST0, int LOGN>
+__device__ __forceinline__ void fwd_block(u64 (&x)[1 << K], u32 jb, const ulonglong2* tw, u64 q) {
   const u64 q2 = 2 * q;
 #pragma unroll
   for (int s = 0; s < K; ++s) {
-    const int st = st0 + s;
+    const int st = ST0 + s;
     const int half = 1 << (K - 1 - s);
+    const ulonglong2* tws = tw + ((1u << st) + (jb >> (LOGN - st)));
 #pragma unroll
     for (int i = 0; i < (1 << K); ++i) {
       if (i & half) continue;
-      const u64 j = jb + ((u64)i << ls);
-      const ulonglong2 w = __ldg(tw + ((1ull << st) + (j >> (log_n - st))));
+      const ulonglong2 w = __ldg(tws + (((u32)i << LS) >> (LOGN - st)));
       u64 X = x[i];
       X = X >= q2 ? X - q2 : X;
       const u64 T = shoup_lazy(x[i + half], w.x, w.y, q);
@@ -52,22 +53,21 @@ __device__ __forceinline__ void fwd_block(u64 (&x)[1 << K], u64 jb, int ls, int 
   }
 }
 
-// Inverse GS stages st_hi, st_hi-1, .. st_hi-K+1 on 2^K points with global
-// indices jb + (i << ls); in local stage s the pair distance is 2^s points.
-// Inputs and outputs in [0, 2q).
-template <int K>
-__device__ __forceinline__ void inv_block(u64 (&x)[1 << K], u64 jb, int ls, int st_hi, const ulonglong2* tw, u64 q,
-                                          int log_n) {
+// Inverse GS stages STH, STH-1, .. STH-K+1 on 2^K points with global indices
+// jb + (i << LS) (disjoint bits as above); in local stage s the pair distance
+// is 2^s points.  Inputs and outputs in [0, 2q).
+template <int K, int LS, int STH, int LOGN>
+__device__ __forceinline__ void inv_block(u64 (&x)[1 << K], u32 jb, const ulonglong2* tw, u64 q) {
   const u64 q2 = 2 * q;
 #pragma unroll
   for (int s = 0; s < K; ++s) {
-    const int st = st_hi - s;
+    const int st = STH - s;
     const int half = 1 << s;
+    const ulonglong2* tws = tw + ((1u << st) + (jb >> (LOGN - st)));
 #pragma unroll
     for (int i = 0; i < (1 << K); ++i) {
       if (i & half) continue;
-      const u64 j = jb + ((u64)i << ls);
-      const ulonglong2 w = __ldg(tw + ((1ull << st) + (j >> (log_n - st))));
+      const ulonglong2 w = __ldg(tws + (((u32)i << LS) >> (LOGN - st)));
       const u64 U = x[i], V = x[i + half];
       u64 S = U + V;
       S = S >= q2 ? S - q2 : S;
@@ -82,191 +82,197 @@ __device__ __forceinline__ u64 reduce4(u64 x, u64 q) {
   return x >= q ? x - q : x;
 }
 
-__device__ __forceinline__ void limb_meta(const LimbSet& s, int log_n, u64*& a, int& pid) {
+template <int LOGN>
+__device__ __forceinline__ void limb_meta(const LimbSet& s, u64*& a, int& pid) {
   const int y = blockIdx.y;
   const int k = y / s.nlimb;
   const int slot = s.l0 + y - k * s.nlimb;
-  a = limb_ptr(s, blockIdx.z, k, slot, 1 << log_n);
+  a = limb_ptr(s, blockIdx.z, k, slot, 1 << LOGN);
   pid = limb_prime(s, slot);
 }
 
-// Column pass: stages 0..n1-1 (forward) over R = 2^(K1+K2) rows of TC = 2^tcl
-// columns starting at blockIdx.x * TC.  Shared tile [row][col].
-template <bool INV, int K1, int K2>
-__global__ void __launch_bounds__(kThreads) k_cols(LimbSet s, Tables T, int n2, int tcl) {
-  constexpr int n1 = K1 + K2;
+// Column pass: stages 0..N1-1 (forward) over R = 2^N1 rows (N1 = K1 + K2) of
+// TC = 2^TCL columns starting at blockIdx.x * TC.  Shared tile [row][col].
+template <bool INV, int LOGN, int K1, int K2, int TCL>
+__global__ void __launch_bounds__(kThreads) k_cols(LimbSet s, Tables T) {
+  constexpr int N1 = K1 + K2, N2 = LOGN - N1, TC = 1 << TCL;
   extern __shared__ u64 sm[];
-  const int log_n = T.log_n;
   u64* a;
   int pid;
-  limb_meta(s, log_n, a, pid);
+  limb_meta<LOGN>(s, a, pid);
   const u64 q = T.mods[pid].q;
-  const ulonglong2* tw = (INV ? T.inv2 : T.fwd2) + ((size_t)pid << log_n);
-  const int TC = 1 << tcl;
-  const int c0 = blockIdx.x * TC;
+  const ulonglong2* tw = (INV ? T.inv2 : T.fwd2) + ((size_t)pid << LOGN);
+  a += blockIdx.x * TC;
   if (!INV) {
     // round 1: 2^K1 rows strided by 2^K2 -> stages 0..K1-1
-    for (int w = threadIdx.x; w < (TC << K2); w += blockDim.x) {
-      const int c = w & (TC - 1), r0 = w >> tcl;
+    for (u32 w = threadIdx.x; w < (TC << K2); w += kThreads) {
+      const u32 c = w & (TC - 1), r0 = w >> TCL;
       u64 x[1 << K1];
 #pragma unroll
-      for (int i = 0; i < (1 << K1); ++i) x[i] = a[((size_t)(r0 + (i << K2)) << n2) + c0 + c];
-      fwd_block<K1>(x, (u64)r0 << n2, K2 + n2, 0, tw, q, log_n);
+      for (int i = 0; i < (1 << K1); ++i) x[i] = a[((r0 + (i << K2)) << N2) + c];
+      fwd_block<K1, K2 + N2, 0, LOGN>(x, r0 << N2, tw, q);
 #pragma unroll
-      for (int i = 0; i < (1 << K1); ++i) sm[((r0 + (i << K2)) << tcl) + c] = x[i];
+      for (int i = 0; i < (1 << K1); ++i) sm[((r0 + (i << K2)) << TCL) + c] = x[i];
     }
     __syncthreads();
-    // round 2: 2^K2 adjacent rows -> stages K1..n1-1
-    for (int w = threadIdx.x; w < (TC << K1); w += blockDim.x) {
-      const int c = w & (TC - 1), g = w >> tcl;
+    // round 2: 2^K2 adjacent rows -> stages K1..N1-1
+    for (u32 w = threadIdx.x; w < (TC << K1); w += kThreads) {
+      const u32 c = w & (TC - 1), g = w >> TCL;
       u64 x[1 << K2];
 #pragma unroll
-      for (int i = 0; i < (1 << K2); ++i) x[i] = sm[(((g << K2) + i) << tcl) + c];
-      fwd_block<K2>(x, (u64)(g << K2) << n2, n2, K1, tw, q, log_n);
+      for (int i = 0; i < (1 << K2); ++i) x[i] = sm[(((g << K2) + i) << TCL) + c];
+      fwd_block<K2, N2, K1, LOGN>(x, (g << K2) << N2, tw, q);
 #pragma unroll
-      for (int i = 0; i < (1 << K2); ++i) a[((size_t)((g << K2) + i) << n2) + c0 + c] = reduce4(x[i], q);
+      for (int i = 0; i < (1 << K2); ++i) a[(((g << K2) + i) << N2) + c] = reduce4(x[i], q);
     }
   } else {
-    // round A: 2^K2 adjacent rows -> stages n1-1 .. K1
-    for (int w = threadIdx.x; w < (TC << K1); w += blockDim.x) {
-      const int c = w & (TC - 1), g = w >> tcl;
+    // round A: 2^K2 adjacent rows -> stages N1-1 .. K1
+    for (u32 w = threadIdx.x; w < (TC << K1); w += kThreads) {
+      const u32 c = w & (TC - 1), g = w >> TCL;
       u64 x[1 << K2];
 #pragma unroll
-      for (int i = 0; i < (1 << K2); ++i) x[i] = a[((size_t)((g << K2) + i) << n2) + c0 + c];
-      inv_block<K2>(x, (u64)(g << K2) << n2, n2, n1 - 1, tw, q, log_n);
+      for (int i = 0; i < (1 << K2); ++i) x[i] = a[(((g << K2) + i) << N2) + c];
+      inv_block<K2, N2, N1 - 1, LOGN>(x, (g << K2) << N2, tw, q);
 #pragma unroll
-      for (int i = 0; i < (1 << K2); ++i) sm[(((g << K2) + i) << tcl) + c] = x[i];
+      for (int i = 0; i < (1 << K2); ++i) sm[(((g << K2) + i) << TCL) + c] = x[i];
     }
     __syncthreads();
     // round B: 2^K1 rows strided by 2^K2 -> stages K1-1 .. 0, then N^{-1}
     const u64 ni = T.ninv[pid], nis = T.ninv_sh[pid];
-    for (int w = threadIdx.x; w < (TC << K2); w += blockDim.x) {
-      const int c = w & (TC - 1), r0 = w >> tcl;
+    for (u32 w = threadIdx.x; w < (TC << K2); w += kThreads) {
+      const u32 c = w & (TC - 1), r0 = w >> TCL;
       u64 x[1 << K1];
 #pragma unroll
-      for (int i = 0; i < (1 << K1); ++i) x[i] = sm[((r0 + (i << K2)) << tcl) + c];
-      inv_block<K1>(x, (u64)r0 << n2, K2 + n2, K1 - 1, tw, q, log_n);
+      for (int i = 0; i < (1 << K1); ++i) x[i] = sm[((r0 + (i << K2)) << TCL) + c];
+      inv_block<K1, K2 + N2, K1 - 1, LOGN>(x, r0 << N2, tw, q);
 #pragma unroll
-      for (int i = 0; i < (1 << K1); ++i)
-        a[((size_t)(r0 + (i << K2)) << n2) + c0 + c] = reduce4(shoup_lazy(x[i], ni, nis, q), q);
+      for (int i = 0; i < (1 << K1); ++i) a[((r0 + (i << K2)) << N2) + c] = reduce4(shoup_lazy(x[i], ni, nis, q), q);
     }
   }
 }
 
-// Row pass: stages n1..log_n-1 (forward) inside RP rows of C = 2^(K1+K2)
-// adjacent points.  Shared rows padded by one word per 2^K2 words.
-template <bool INV, int K1, int K2>
-__global__ void __launch_bounds__(kThreads) k_rows(LimbSet s, Tables T, int n1, int rpl) {
-  constexpr int n2 = K1 + K2, C = 1 << n2;
-  constexpr int PADW = C + (C >> K2);  // padded row width
+// Row pass: stages N1..LOGN-1 (forward) inside RP = 2^RPL rows of C = 2^N2
+// adjacent points (N2 = K1 + K2).  Shared rows padded by one word per 2^K2.
+template <bool INV, int LOGN, int K1, int K2, int RPL>
+__global__ void __launch_bounds__(kThreads) k_rows(LimbSet s, Tables T) {
+  constexpr int N2 = K1 + K2, N1 = LOGN - N2, C = 1 << N2, RP = 1 << RPL;
+  constexpr int PADW = C + (C >> K2);
   extern __shared__ u64 sm[];
-  const int log_n = T.log_n;
   u64* a;
   int pid;
-  limb_meta(s, log_n, a, pid);
+  limb_meta<LOGN>(s, a, pid);
   const u64 q = T.mods[pid].q;
-  const ulonglong2* tw = (INV ? T.inv2 : T.fwd2) + ((size_t)pid << log_n);
-  const int RP = 1 << rpl;
-  const int row0 = blockIdx.x * RP;
-  u64* src = a + ((size_t)row0 << n2);
-  auto sidx = [&](int r, int j) { return r * PADW + j + (j >> K2); };
+  const ulonglong2* tw = (INV ? T.inv2 : T.fwd2) + ((size_t)pid << LOGN);
+  const u32 row0 = blockIdx.x * RP;
+  u64* src = a + ((size_t)row0 << N2);
+  auto sidx = [](u32 r, u32 j) { return r * PADW + j + (j >> K2); };
   if (!INV) {
     // round 1: 2^K1 points strided by 2^K2 (straight from global)
-    for (int w = threadIdx.x; w < (RP << K2); w += blockDim.x) {
-      const int r = w >> K2, r0 = w & ((1 << K2) - 1);
+    for (u32 w = threadIdx.x; w < (RP << K2); w += kThreads) {
+      const u32 r = w >> K2, r0 = w & ((1 << K2) - 1);
       u64 x[1 << K1];
 #pragma unroll
-      for (int i = 0; i < (1 << K1); ++i) x[i] = src[((size_t)r << n2) + r0 + (i << K2)];
-      fwd_block<K1>(x, ((u64)(row0 + r) << n2) + r0, K2, n1, tw, q, log_n);
+      for (int i = 0; i < (1 << K1); ++i) x[i] = src[(r << N2) + r0 + (i << K2)];
+      fwd_block<K1, K2, N1, LOGN>(x, ((row0 + r) << N2) + r0, tw, q);
 #pragma unroll
       for (int i = 0; i < (1 << K1); ++i) sm[sidx(r, r0 + (i << K2))] = x[i];
     }
     __syncthreads();
     // round 2: 2^K2 adjacent points
-    for (int w = threadIdx.x; w < (RP << K1); w += blockDim.x) {
-      const int r = w >> K1, g = w & ((1 << K1) - 1);
+    for (u32 w = threadIdx.x; w < (RP << K1); w += kThreads) {
+      const u32 r = w >> K1, g = w & ((1 << K1) - 1);
       u64 x[1 << K2];
 #pragma unroll
       for (int i = 0; i < (1 << K2); ++i) x[i] = sm[sidx(r, (g << K2) + i)];
-      fwd_block<K2>(x, ((u64)(row0 + r) << n2) + (g << K2), 0, n1 + K1, tw, q, log_n);
+      fwd_block<K2, 0, N1 + K1, LOGN>(x, ((row0 + r) << N2) + (g << K2), tw, q);
 #pragma unroll
       for (int i = 0; i < (1 << K2); ++i) sm[sidx(r, (g << K2) + i)] = reduce4(x[i], q);
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < (RP << n2); e += blockDim.x) src[e] = sm[sidx(e >> n2, e & (C - 1))];
+    for (u32 e = threadIdx.x; e < (RP << N2); e += kThreads) src[e] = sm[sidx(e >> N2, e & (C - 1))];
   } else {
-    for (int e = threadIdx.x; e < (RP << n2); e += blockDim.x) sm[sidx(e >> n2, e & (C - 1))] = src[e];
+    for (u32 e = threadIdx.x; e < (RP << N2); e += kThreads) sm[sidx(e >> N2, e & (C - 1))] = src[e];
     __syncthreads();
-    // round A: 2^K2 adjacent points -> stages log_n-1 .. log_n-K2
-    for (int w = threadIdx.x; w < (RP << K1); w += blockDim.x) {
-      const int r = w >> K1, g = w & ((1 << K1) - 1);
+    // round A: 2^K2 adjacent points -> stages LOGN-1 .. LOGN-K2
+    for (u32 w = threadIdx.x; w < (RP << K1); w += kThreads) {
+      const u32 r = w >> K1, g = w & ((1 << K1) - 1);
       u64 x[1 << K2];
 #pragma unroll
       for (int i = 0; i < (1 << K2); ++i) x[i] = sm[sidx(r, (g << K2) + i)];
-      inv_block<K2>(x, ((u64)(row0 + r) << n2) + (g << K2), 0, log_n - 1, tw, q, log_n);
+      inv_block<K2, 0, LOGN - 1, LOGN>(x, ((row0 + r) << N2) + (g << K2), tw, q);
 #pragma unroll
       for (int i = 0; i < (1 << K2); ++i) sm[sidx(r, (g << K2) + i)] = x[i];
     }
     __syncthreads();
-    // round B: 2^K1 points strided by 2^K2 -> stages log_n-K2-1 .. n1 (to global)
-    for (int w = threadIdx.x; w < (RP << K2); w += blockDim.x) {
-      const int r = w >> K2, r0 = w & ((1 << K2) - 1);
+    // round B: 2^K1 points strided by 2^K2 -> stages LOGN-K2-1 .. N1 (to global)
+    for (u32 w = threadIdx.x; w < (RP << K2); w += kThreads) {
+      const u32 r = w >> K2, r0 = w & ((1 << K2) - 1);
       u64 x[1 << K1];
 #pragma unroll
       for (int i = 0; i < (1 << K1); ++i) x[i] = sm[sidx(r, r0 + (i << K2))];
-      inv_block<K1>(x, ((u64)(row0 + r) << n2) + r0, K2, log_n - 1 - K2, tw, q, log_n);
+      inv_block<K1, K2, LOGN - 1 - K2, LOGN>(x, ((row0 + r) << N2) + r0, tw, q);
 #pragma unroll
-      for (int i = 0; i < (1 << K1); ++i) src[((size_t)r << n2) + r0 + (i << K2)] = reduce4(x[i], q);
+      for (int i = 0; i < (1 << K1); ++i) src[(r << N2) + r0 + (i << K2)] = reduce4(x[i], q);
     }
   }
 }
 
-template <bool INV, int K1, int K2>
-void launch_cols(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, int n2) {
-  constexpr int n1 = K1 + K2;
-  // enough (column, offset) work items for every thread in both rounds
-  int tcl = 8 - (K1 < K2 ? K1 : K2);
-  if (tcl > n2) tcl = n2;
-  while (((size_t)1 << (n1 + tcl)) * sizeof(u64) > 48 * 1024) --tcl;
-  dim3 grid(1u << (n2 - tcl), ylimbs, items);
-  const size_t smem = ((size_t)1 << (n1 + tcl)) * sizeof(u64);
+// Pass geometry for ring degree 2^LOGN: the column pass takes floor(LOGN/2)
+// stages, the row pass the rest; each pass splits into two register rounds.
+template <int n>
+struct Split {
+  static constexpr int K1 = n == 5 ? 3 : (n == 6 ? 3 : 4);
+  static constexpr int K2 = n - K1;
+  static constexpr int KMIN = K1 < K2 ? K1 : K2;
+};
+
+constexpr int cmin(int a, int b) { return a < b ? a : b; }
+
+// tiles: enough (column or row, offset) work items for all 256 threads, at
+// most 48 KB of shared memory
+template <int N1, int N2>
+struct ColTile {
+  static constexpr int raw = cmin(8 - Split<N1>::KMIN, N2);
+  static constexpr int TCL = (1 << (N1 + raw)) * 8 > 48 * 1024 ? raw - 1 : raw;
+};
+template <int N1, int N2>
+struct RowTile {
+  static constexpr int K2 = Split<N2>::K2;
+  static constexpr int PADW = (1 << N2) + (1 << (N2 - K2));
+  static constexpr int raw = cmin(8 - Split<N2>::KMIN, N1);
+  static constexpr int RPL = (1 << raw) * PADW * 8 > 48 * 1024 ? raw - 1 : raw;
+};
+
+template <bool INV, int LOGN>
+void launch_pass_cols(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs) {
+  constexpr int N1 = LOGN / 2, N2 = LOGN - N1;
+  using Sp = Split<N1>;
+  constexpr int TCL = ColTile<N1, N2>::TCL;
+  dim3 grid(1u << (N2 - TCL), ylimbs, items);
+  const size_t smem = ((size_t)1 << (N1 + TCL)) * sizeof(u64);
   ProfScope p(ctx, INV ? "ntt_inv_cols" : "ntt_fwd_cols", (uint64_t)ylimbs * items);
-  k_cols<INV, K1, K2><<<grid, kThreads, smem, ctx->stream>>>(s, ctx->tab, n2, tcl);
+  k_cols<INV, LOGN, Sp::K1, Sp::K2, TCL><<<grid, kThreads, smem, ctx->stream>>>(s, ctx->tab);
 }
 
-template <bool INV, int K1, int K2>
-void launch_rows(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, int n1) {
-  constexpr int n2 = K1 + K2;
-  int rpl = 8 - (K1 < K2 ? K1 : K2);
-  if (rpl > n1) rpl = n1;
-  const size_t padw = ((size_t)1 << n2) + ((size_t)1 << (n2 - K2));
-  while (((size_t)1 << rpl) * padw * sizeof(u64) > 48 * 1024) --rpl;
-  dim3 grid(1u << (n1 - rpl), ylimbs, items);
-  const size_t smem = ((size_t)1 << rpl) * padw * sizeof(u64);
+template <bool INV, int LOGN>
+void launch_pass_rows(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs) {
+  constexpr int N1 = LOGN / 2, N2 = LOGN - N1;
+  using Sp = Split<N2>;
+  constexpr int RPL = RowTile<N1, N2>::RPL;
+  dim3 grid(1u << (N1 - RPL), ylimbs, items);
+  const size_t smem = ((size_t)1 << RPL) * RowTile<N1, N2>::PADW * sizeof(u64);
   ProfScope p(ctx, INV ? "ntt_inv_rows" : "ntt_fwd_rows", (uint64_t)ylimbs * items);
-  k_rows<INV, K1, K2><<<grid, kThreads, smem, ctx->stream>>>(s, ctx->tab, n1, rpl);
+  k_rows<INV, LOGN, Sp::K1, Sp::K2, RPL><<<grid, kThreads, smem, ctx->stream>>>(s, ctx->tab);
 }
 
-// Stage splits of a pass of n stages into two register rounds.
-template <bool INV>
-void cols_dispatch(hc_ctx* ctx, const LimbSet& s, int items, int y, int n1, int n2) {
-  switch (n1) {
-    case 5: launch_cols<INV, 3, 2>(ctx, s, items, y, n2); break;
-    case 6: launch_cols<INV, 3, 3>(ctx, s, items, y, n2); break;
-    case 7: launch_cols<INV, 4, 3>(ctx, s, items, y, n2); break;
-    case 8: launch_cols<INV, 4, 4>(ctx, s, items, y, n2); break;
-    default: throw HcError{HC_ERR_INVALID, "unsupported ring degree"};
-  }
-}
-
-template <bool INV>
-void rows_dispatch(hc_ctx* ctx, const LimbSet& s, int items, int y, int n1, int n2) {
-  switch (n2) {
-    case 5: launch_rows<INV, 3, 2>(ctx, s, items, y, n1); break;
-    case 6: launch_rows<INV, 3, 3>(ctx, s, items, y, n1); break;
-    case 7: launch_rows<INV, 4, 3>(ctx, s, items, y, n1); break;
-    case 8: launch_rows<INV, 4, 4>(ctx, s, items, y, n1); break;
-    default: throw HcError{HC_ERR_INVALID, "unsupported ring degree"};
+template <int LOGN>
+void ntt_logn(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, bool inverse) {
+  if (!inverse) {
+    launch_pass_cols<false, LOGN>(ctx, s, items, ylimbs);
+    launch_pass_rows<false, LOGN>(ctx, s, items, ylimbs);
+  } else {
+    launch_pass_rows<true, LOGN>(ctx, s, items, ylimbs);
+    launch_pass_cols<true, LOGN>(ctx, s, items, ylimbs);
   }
 }
 
@@ -274,16 +280,17 @@ void rows_dispatch(hc_ctx* ctx, const LimbSet& s, int items, int y, int n1, int 
 
 void launch_ntt(hc_ctx* ctx, const LimbSet& s, int items, bool inverse) {
   if (items <= 0 || s.nlimb <= 0 || s.npoly <= 0) return;
-  const int log_n = ctx->P.log_n;
-  const int n1 = log_n / 2, n2 = log_n - n1;
   const int ylimbs = s.npoly * s.nlimb;
   HC_CHECK(ylimbs <= 65535 && items <= 65535, HC_ERR_INVALID, "NTT batch too large");
-  if (!inverse) {
-    cols_dispatch<false>(ctx, s, items, ylimbs, n1, n2);
-    rows_dispatch<false>(ctx, s, items, ylimbs, n1, n2);
-  } else {
-    rows_dispatch<true>(ctx, s, items, ylimbs, n1, n2);
-    cols_dispatch<true>(ctx, s, items, ylimbs, n1, n2);
+  switch (ctx->P.log_n) {
+    case 10: ntt_logn<10>(ctx, s, items, ylimbs, inverse); break;
+    case 11: ntt_logn<11>(ctx, s, items, ylimbs, inverse); break;
+    case 12: ntt_logn<12>(ctx, s, items, ylimbs, inverse); break;
+    case 13: ntt_logn<13>(ctx, s, items, ylimbs, inverse); break;
+    case 14: ntt_logn<14>(ctx, s, items, ylimbs, inverse); break;
+    case 15: ntt_logn<15>(ctx, s, items, ylimbs, inverse); break;
+    case 16: ntt_logn<16>(ctx, s, items, ylimbs, inverse); break;
+    default: throw HcError{HC_ERR_INVALID, "unsupported ring degree"};
   }
   ctx->launches += 2;
   check_launch(ctx);
