@@ -80,6 +80,9 @@ void recycle_events(hc_ctx* ctx) {
 
 namespace {
 
+// Device workspace budget of one batched key switch (chunks beyond it run in turn).
+constexpr size_t kWorkspaceBytes = (size_t)8 << 30;
+
 // Run `f`, translating exceptions into return codes and the context error.
 template <class F>
 int guard(hc_ctx* ctx, F&& f) {
@@ -158,7 +161,7 @@ void keyswitch_batch(hc_ctx* ctx, const u64* key, int level, const std::vector<C
   const int total = (int)x.size();
   const size_t ext_words = (size_t)next * n;
   const size_t per_item = (size_t)nq * n + (size_t)dnum * ext_words + 2 * ext_words + 2 * (size_t)nq * n;
-  int chunk = (int)std::max<size_t>(1, ((size_t)3 << 30) / (per_item * 8));
+  int chunk = (int)std::max<size_t>(1, kWorkspaceBytes / (per_item * 8));
   chunk = std::min(chunk, 256);
   const int* emap = ctx->ext_map_of(level);
   for (int s0 = 0; s0 < total; s0 += chunk) {
@@ -195,17 +198,84 @@ void keyswitch_batch(hc_ctx* ctx, const u64* key, int level, const std::vector<C
       std::vector<CtRef> xsh(m);
       for (int i = 0; i < m; ++i) xsh[i] = CtRef{xs[i].p + (size_t)d0 * n, 0};
       launch_ew(ctx, 3, refs_dev(ctx, er, keep), refs_dev(ctx, xsh, keep), nullptr, m, 1, d1 - d0);
-      launch_modup_bconv(ctx, level, j, xc, x_is, ext + (size_t)j * ext_words, ext_is, m);
+      launch_modup_bconv_fast(ctx, level, j, xc, x_is, ext + (size_t)j * ext_words, ext_is, m);
       u64* ej = ext + (size_t)j * ext_words;
       if (d0 > 0) launch_ntt(ctx, limbset_base(ej, ext_is, 0, 1, d0, 0, emap), m, false);
       launch_ntt(ctx, limbset_base(ej, ext_is, 0, 1, next - d1, d1, emap), m, false);
     }
-    launch_key_product(ctx, level, ext, ext_is, key, acc, acc_is, m);
+    launch_key_product_batched(ctx, level, ext, ext_is, key, acc, acc_is, m);
     // ModDown
     launch_ntt(ctx, limbset_base(acc, acc_is, ext_words, 2, alpha, nq, emap), m, true);
-    launch_moddown_bconv(ctx, level, acc + (size_t)nq * n, acc_is, zq, z_is, m);
+    launch_moddown_bconv_fast(ctx, level, acc + (size_t)nq * n, acc_is, zq, z_is, m);
     launch_ntt(ctx, limbset_base(zq, z_is, (u64)nq * n, 2, nq, 0, nullptr), m, false);
     launch_moddown_combine(ctx, level, acc, acc_is, zq, z_is, b0, b1, orr, m);
+  }
+}
+
+// Key switch of x followed by a rescale, fused: with u = key product over
+// Q_l u P and z = FastBConv_{P->Q}([u]_P) (coefficient form),
+//   relin_k[i]  = base_k[i] + u_k[i] P^{-1} - NTT(z_k[i] P^{-1}),
+//   rescale_k[i] = (relin_k[i] - NTT([relin_k[l]] mod q_i)) q_l^{-1},
+// and NTT is linear, so one NTT of (z_k[i] P^{-1} + [relin_k[l]] mod q_i)
+// per limb serves both; the last limb of relin_k is formed in coefficient
+// form from INTT(base_k[l] + u_k[l] P^{-1}) - z_k[l] P^{-1}.  Bit-identical to
+// keyswitch_batch followed by rescale_batch.  out: degree-1, level l-1.
+void keyswitch_rescale_batch(hc_ctx* ctx, const u64* key, int level, const std::vector<CtRef>& x,
+                             const std::vector<CtRef>* base0, const std::vector<CtRef>* base1,
+                             const std::vector<CtRef>& out) {
+  const int n = ctx->P.n, alpha = ctx->P.alpha;
+  const int nq = level + 1, next = nq + alpha, dnum = ctx->lv[level].dnum;
+  const int total = (int)x.size();
+  const size_t ext_words = (size_t)next * n;
+  const size_t per_item =
+      (size_t)nq * n + (size_t)dnum * ext_words + 2 * ext_words + 2 * (size_t)nq * n + 2 * (size_t)n;
+  int chunk = (int)std::max<size_t>(1, kWorkspaceBytes / (per_item * 8));
+  chunk = std::min(chunk, 256);
+  const int* emap = ctx->ext_map_of(level);
+  for (int s0 = 0; s0 < total; s0 += chunk) {
+    const int m = std::min(chunk, total - s0);
+    std::vector<BufPtr> keep;
+    std::vector<CtRef> xs(x.begin() + s0, x.begin() + s0 + m);
+    const CtRef* xr = refs_dev(ctx, xs, keep);
+    const CtRef* orr = refs_dev(ctx, std::vector<CtRef>(out.begin() + s0, out.begin() + s0 + m), keep);
+    const CtRef* b0 = nullptr;
+    const CtRef* b1 = nullptr;
+    if (base0) b0 = refs_dev(ctx, std::vector<CtRef>(base0->begin() + s0, base0->begin() + s0 + m), keep);
+    if (base1) b1 = refs_dev(ctx, std::vector<CtRef>(base1->begin() + s0, base1->begin() + s0 + m), keep);
+    BufPtr work = ctx->buffer(per_item * m);
+    keep.push_back(work);
+    u64* xc = work->ptr;                            // [m][nq][N]
+    u64* ext = xc + (size_t)m * nq * n;             // [m][dnum][next][N]
+    u64* acc = ext + (size_t)m * dnum * ext_words;  // [m][2][next][N]
+    u64* zq = acc + (size_t)m * 2 * ext_words;      // [m][2][nq][N]
+    u64* tl = zq + (size_t)m * 2 * nq * n;          // [m][2][N]
+    const u64 x_is = (u64)nq * n, ext_is = (u64)dnum * ext_words, acc_is = 2 * (u64)ext_words,
+              z_is = 2 * (u64)nq * n;
+    std::vector<CtRef> xcr(m);
+    for (int i = 0; i < m; ++i) xcr[i] = CtRef{xc + x_is * i, 0};
+    launch_ew(ctx, 3, refs_dev(ctx, xcr, keep), xr, nullptr, m, 1, nq);
+    launch_ntt(ctx, limbset_base(xc, x_is, 0, 1, nq, 0, nullptr), m, true);
+    for (int j = 0; j < dnum; ++j) {
+      const int d0 = j * alpha, d1 = std::min(d0 + alpha, nq);
+      std::vector<CtRef> er(m), xsh(m);
+      for (int i = 0; i < m; ++i) {
+        er[i] = CtRef{ext + ext_is * i + (size_t)j * ext_words + (size_t)d0 * n, 0};
+        xsh[i] = CtRef{xs[i].p + (size_t)d0 * n, 0};
+      }
+      launch_ew(ctx, 3, refs_dev(ctx, er, keep), refs_dev(ctx, xsh, keep), nullptr, m, 1, d1 - d0);
+      launch_modup_bconv_fast(ctx, level, j, xc, x_is, ext + (size_t)j * ext_words, ext_is, m);
+      u64* ej = ext + (size_t)j * ext_words;
+      if (d0 > 0) launch_ntt(ctx, limbset_base(ej, ext_is, 0, 1, d0, 0, emap), m, false);
+      launch_ntt(ctx, limbset_base(ej, ext_is, 0, 1, next - d1, d1, emap), m, false);
+    }
+    launch_key_product_batched(ctx, level, ext, ext_is, key, acc, acc_is, m);
+    launch_ntt(ctx, limbset_base(acc, acc_is, ext_words, 2, alpha, nq, emap), m, true);
+    launch_moddown_bconv_fast(ctx, level, acc + (size_t)nq * n, acc_is, zq, z_is, m);
+    launch_ksr_last(ctx, level, acc, acc_is, b0, b1, tl, m);
+    launch_ntt(ctx, limbset_base(tl, 2 * (u64)n, (u64)n, 2, 1, 0, ident_map(ctx) + level), m, true);
+    launch_ksr_lift(ctx, level, tl, zq, z_is, m);
+    launch_ntt(ctx, limbset_base(zq, z_is, (u64)nq * n, 2, level, 0, nullptr), m, false);
+    launch_ksr_combine(ctx, level, acc, acc_is, zq, z_is, b0, b1, orr, m);
   }
 }
 
@@ -285,32 +355,38 @@ std::vector<hc_ct*> tensor_acc(hc_ctx* ctx, const std::vector<const hc_ct*>& xs,
   return out;
 }
 
-// relin + rescale of a batch of degree-2 cts -> fresh degree-1 cts at level-1
+// relin + rescale of a batch of degree-2 cts -> fresh degree-1 cts at level-1.
+// A bias is added to (d0, d1) before the key switch, which equals adding it
+// to the relinearised ciphertext.
 std::vector<hc_ct*> relin_rescale(hc_ctx* ctx, const hc_evk* evk, const std::vector<hc_ct*>& d,
                                   const std::vector<const hc_ct*>* bias) {
   if (d.empty()) return {};
   const int level = d[0]->level;
   HC_CHECK(level >= 1, HC_ERR_DEPTH, "no level left to rescale");
-  std::vector<hc_ct*> r = new_cts(ctx, (int)d.size(), level, 1, d[0]->scale);
-  std::vector<const hc_ct*> dc(d.begin(), d.end());
-  relin_batch(ctx, evk, dc, r);
   if (bias) {
     std::vector<BufPtr> keep;
-    std::vector<CtRef> rr, br;
-    for (size_t i = 0; i < r.size(); ++i) {
+    std::vector<CtRef> dr, br;
+    for (size_t i = 0; i < d.size(); ++i) {
       const hc_ct* b = (*bias)[i];
       HC_CHECK(b->degree == 1 && b->level >= level, HC_ERR_LEVEL_MISMATCH, "bias level too low");
-      check_scales(r[i]->scale, b->scale);
-      rr.push_back(r[i]->ref());
+      check_scales(d[i]->scale, b->scale);
+      dr.push_back(d[i]->ref());
       br.push_back(b->ref());
     }
-    const CtRef* rd = refs_dev(ctx, rr, keep);
-    launch_ew(ctx, 0, rd, rd, refs_dev(ctx, br, keep), (int)r.size(), 2, level + 1);
+    const CtRef* dd = refs_dev(ctx, dr, keep);
+    launch_ew(ctx, 0, dd, dd, refs_dev(ctx, br, keep), (int)d.size(), 2, level + 1);
   }
   std::vector<hc_ct*> out = new_cts(ctx, (int)d.size(), level - 1, 1, d[0]->scale / (double)ctx->P.chain[level]);
-  std::vector<const hc_ct*> rc(r.begin(), r.end());
-  rescale_cts(ctx, rc, out);
-  for (auto* c : r) delete c;
+  std::vector<CtRef> x, b0, b1, o;
+  for (size_t i = 0; i < d.size(); ++i) {
+    HC_CHECK(d[i]->degree == 2 && d[i]->level == level, HC_ERR_INVALID, "relin batch needs degree-2 cts at one level");
+    out[i]->scale = d[i]->scale / (double)ctx->P.chain[level];
+    x.push_back(CtRef{d[i]->data + 2 * d[i]->stride, d[i]->stride});
+    b0.push_back(CtRef{d[i]->data, d[i]->stride});
+    b1.push_back(CtRef{d[i]->data + d[i]->stride, d[i]->stride});
+    o.push_back(out[i]->ref());
+  }
+  keyswitch_rescale_batch(ctx, evk->relin.buf->ptr, level, x, &b0, &b1, o);
   return out;
 }
 
@@ -1164,7 +1240,7 @@ std::vector<hc_ct*> rotate_one(hc_ctx* ctx, const hc_evk* evk, const hc_ct* x, c
     const CtRef* er = refs_dev(ctx, {CtRef{ej + (size_t)d0 * n, 0}}, keep);
     const CtRef* xsr = refs_dev(ctx, {CtRef{x->data + x->stride + (size_t)d0 * n, 0}}, keep);
     launch_ew(ctx, 3, er, xsr, nullptr, 1, 1, d1 - d0);
-    launch_modup_bconv(ctx, level, j, xc, 0, ej, 0, 1);
+    launch_modup_bconv_fast(ctx, level, j, xc, 0, ej, 0, 1);
     if (d0 > 0) launch_ntt(ctx, limbset_base(ej, 0, 0, 1, d0, 0, emap), 1, false);
     launch_ntt(ctx, limbset_base(ej, 0, 0, 1, next - d1, d1, emap), 1, false);
   }
@@ -1178,9 +1254,9 @@ std::vector<hc_ct*> rotate_one(hc_ctx* ctx, const hc_evk* evk, const hc_ct* x, c
     const CtRef* src = refs_dev(ctx, {CtRef{ext, (u64)ext_words}}, keep);
     const CtRef* dst = refs_dev(ctx, {CtRef{extg, (u64)ext_words}}, keep);
     launch_automorph(ctx, dst, src, 1, dnum, next, gs[i]);
-    launch_key_product(ctx, level, extg, 0, evk->galois.at(gs[i]).buf->ptr, acc, 0, 1);
+    launch_key_product_batched(ctx, level, extg, 0, evk->galois.at(gs[i]).buf->ptr, acc, 0, 1);
     launch_ntt(ctx, limbset_base(acc, 0, ext_words, 2, alpha, nq, emap), 1, true);
-    launch_moddown_bconv(ctx, level, acc + (size_t)nq * n, 0, zq, 0, 1);
+    launch_moddown_bconv_fast(ctx, level, acc + (size_t)nq * n, 0, zq, 0, 1);
     launch_ntt(ctx, limbset_base(zq, 0, (u64)nq * n, 2, nq, 0, nullptr), 1, false);
     const CtRef* c0d = refs_dev(ctx, {CtRef{c0g, 0}}, keep);
     const CtRef* c0s = refs_dev(ctx, {CtRef{x->data, 0}}, keep);

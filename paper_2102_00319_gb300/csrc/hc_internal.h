@@ -218,3 +218,17 @@ void launch_check_range(hc_ctx* ctx, const u64* data, int npoly, int nl, u64 pol
                         unsigned long long* bad);
 // Pool sums: out[o] = (x[i0] + x[i1]) + (x[i2] + x[i3]) with idx[4o..4o+3].
 void launch_sum4(hc_ctx* ctx, const CtRef* out, const CtRef* x, const int* idx, int nout, int nl);
+
+// Specialised key-switching launchers (same results as the generic ones).
+void launch_modup_bconv_fast(hc_ctx* ctx, int level, int j, const u64* xcoef, u64 x_item_stride, u64* ext,
+                             u64 ext_item_stride, int items);
+void launch_moddown_bconv_fast(hc_ctx* ctx, int level, const u64* accp_coef, u64 accp_item_stride, u64* z,
+                               u64 z_item_stride, int items);
+void launch_key_product_batched(hc_ctx* ctx, int level, const u64* ext, u64 ext_item_stride, const u64* key,
+                                u64* acc, u64 acc_item_stride, int items);
+// Fused relinearise + rescale tail (see hc_kernels.cu).
+void launch_ksr_last(hc_ctx* ctx, int level, const u64* acc, u64 acc_item_stride, const CtRef* base0,
+                     const CtRef* base1, u64* tl, int items);
+void launch_ksr_lift(hc_ctx* ctx, int level, const u64* tl, u64* zq, u64 z_item_stride, int items);
+void launch_ksr_combine(hc_ctx* ctx, int level, const u64* acc, u64 acc_item_stride, const u64* w, u64 w_item_stride,
+                        const CtRef* base0, const CtRef* base1, const CtRef* out, int items);

@@ -523,3 +523,276 @@ void launch_sum4(hc_ctx* ctx, const CtRef* out, const CtRef* x, const int* idx, 
     }
   LAUNCH_DONE(ctx);
 }
+
+// ===========================================================================
+// Specialised key-switching kernels (digit size / digit count known at
+// compile time, constants staged in shared memory, key limbs reused across
+// the batch) and the fused relinearise + rescale tail.
+// ===========================================================================
+namespace {
+
+// ModUp: v_i = [x_i hat_inv_i]_{q_i}; y_t = sum_i v_i hat_mod[t][i] mod q_t
+// for every ext slot t outside the digit [d0, d0 + NS).
+template <int NS>
+__global__ void __launch_bounds__(kT) k_modup_bconv_t(const u64* xcoef, u64 x_item_stride, u64* ext,
+                                                       u64 ext_item_stride, const u64* cst, int d0, int next,
+                                                       const int* emap, Tables T) {
+  extern __shared__ u64 sh[];
+  u64* hm = sh;                          // [next][NS]
+  DMod* md = (DMod*)(sh + next * NS);    // [next]
+  for (int e = threadIdx.x; e < next * NS; e += blockDim.x) hm[e] = cst[2 * NS + e];
+  for (int t = threadIdx.x; t < next; t += blockDim.x) md[t] = T.mods[emap[t]];
+  __syncthreads();
+  const int n = 1 << T.log_n;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int z = blockIdx.z;
+  const u64* x = xcoef + (size_t)z * x_item_stride;
+  u64* y = ext + (size_t)z * ext_item_stride;
+  u64 v[NS];
+#pragma unroll
+  for (int i = 0; i < NS; ++i) v[i] = shoup(x[(size_t)(d0 + i) * n + c], cst[i], cst[NS + i], md[d0 + i].q);
+  for (int t = 0; t < next; ++t) {
+    if (t >= d0 && t < d0 + NS) continue;
+    U128 acc{0, 0};
+#pragma unroll
+    for (int i = 0; i < NS; ++i) mac(acc, v[i], hm[t * NS + i]);
+    y[(size_t)t * n + c] = reduce128(acc, md[t]);
+  }
+}
+
+// ModDown conversion P -> Q_level of both polys (ALPHA special primes).
+template <int ALPHA>
+__global__ void __launch_bounds__(kT) k_moddown_bconv_t(const u64* src, u64 src_item_stride, u64 src_poly_stride,
+                                                         u64* zq, u64 z_item_stride, const u64* cst, int nq, int L,
+                                                         Tables T) {
+  extern __shared__ u64 sh[];
+  u64* hm = sh;                          // [nq][ALPHA]
+  DMod* md = (DMod*)(sh + nq * ALPHA);   // [nq]
+  for (int e = threadIdx.x; e < nq * ALPHA; e += blockDim.x) hm[e] = cst[2 * ALPHA + e];
+  for (int t = threadIdx.x; t < nq; t += blockDim.x) md[t] = T.mods[t];
+  __syncthreads();
+  const int n = 1 << T.log_n;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int k = blockIdx.y, z = blockIdx.z;
+  const u64* x = src + (size_t)z * src_item_stride + (size_t)k * src_poly_stride;
+  u64 v[ALPHA];
+#pragma unroll
+  for (int i = 0; i < ALPHA; ++i) v[i] = shoup(x[(size_t)i * n + c], cst[i], cst[ALPHA + i], T.mods[L + 1 + i].q);
+  u64* out = zq + (size_t)z * z_item_stride + (size_t)k * nq * n;
+  for (int t = 0; t < nq; ++t) {
+    U128 acc{0, 0};
+#pragma unroll
+    for (int i = 0; i < ALPHA; ++i) mac(acc, v[i], hm[t * ALPHA + i]);
+    out[(size_t)t * n + c] = reduce128(acc, md[t]);
+  }
+}
+
+// acc[z][k][s] = sum_j ext[z][j][s] * key[j][k][emap[s]] for all items z:
+// the 2 DNUM key words of (s, c) stay in registers across the batch.
+template <int DNUM>
+__global__ void __launch_bounds__(kT) k_key_product_t(const u64* ext, u64 ext_item_stride, const u64* key, u64* acc,
+                                                       u64 acc_item_stride, int next, int nchain, const int* emap,
+                                                       int items, Tables T) {
+  const int n = 1 << T.log_n;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int s = blockIdx.y;
+  const int pid = emap[s];
+  const DMod md = T.mods[pid];
+  u64 kb[DNUM], ka[DNUM];
+#pragma unroll
+  for (int j = 0; j < DNUM; ++j) {
+    kb[j] = key[((size_t)(2 * j) * nchain + pid) * n + c];
+    ka[j] = key[((size_t)(2 * j + 1) * nchain + pid) * n + c];
+  }
+  for (int z = blockIdx.z; z < items; z += gridDim.z) {
+    const u64* e = ext + (size_t)z * ext_item_stride + (size_t)s * n + c;
+    U128 a0{0, 0}, a1{0, 0};
+#pragma unroll
+    for (int j = 0; j < DNUM; ++j) {
+      const u64 y = e[(size_t)j * next * n];
+      mac(a0, y, kb[j]);
+      mac(a1, y, ka[j]);
+    }
+    u64* o = acc + (size_t)z * acc_item_stride + (size_t)s * n + c;
+    o[0] = reduce128(a0, md);
+    o[(size_t)next * n] = reduce128(a1, md);
+  }
+}
+
+// Fused relinearise + rescale, step 1: t_k = base_k[l] + acc_k[l] P^{-1}
+// (NTT form, last limb only).
+__global__ void k_ksr_last(const u64* acc, u64 acc_item_stride, u64 acc_poly_stride, const CtRef* base0,
+                           const CtRef* base1, u64* tl, int level, u64 pinv, u64 pinv_sh, Tables T) {
+  const int n = 1 << T.log_n;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int k = blockIdx.y, z = blockIdx.z;
+  const u64 q = T.mods[level].q;
+  const size_t li = (size_t)level * n + c;
+  u64 r = shoup(acc[(size_t)z * acc_item_stride + (size_t)k * acc_poly_stride + li], pinv, pinv_sh, q);
+  const CtRef* base = k == 0 ? base0 : base1;
+  if (base) r = addm(r, base[z].p[li], q);
+  tl[((size_t)z * 2 + k) * n + c] = r;
+}
+
+// Step 2 (coefficient form): c_l = t_k - z_k[l] P^{-1} mod q_l is the relinearised
+// last limb; w_k[i] = z_k[i] P^{-1} + centred(c_l) mod q_i for i < l, written
+// over z_k[i].
+__global__ void k_ksr_lift(const u64* tl, u64* zq, u64 z_item_stride, int level, const u64* pinv,
+                           const u64* pinv_sh, Tables T) {
+  const int n = 1 << T.log_n;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int k = blockIdx.y, z = blockIdx.z;
+  const int nq = level + 1;
+  u64* zk = zq + (size_t)z * z_item_stride + (size_t)k * nq * n;
+  const u64 ql = T.mods[level].q;
+  const u64 cl = subm(tl[((size_t)z * 2 + k) * n + c], shoup(zk[(size_t)level * n + c], pinv[level], pinv_sh[level], ql), ql);
+  const bool neg = cl > (ql - 1) / 2;
+  const u64 mag = neg ? ql - cl : cl;
+  for (int i = 0; i < level; ++i) {
+    const DMod mi = T.mods[i];
+    const u64 m = csub(shoup_lazy(mag, 1, mi.one_sh, mi.q), mi.q);
+    const u64 r = neg ? negm(m, mi.q) : m;
+    const u64 w = shoup(zk[(size_t)i * n + c], pinv[i], pinv_sh[i], mi.q);
+    zk[(size_t)i * n + c] = addm(w, r, mi.q);
+  }
+}
+
+// Step 3: out_k[i] = (base_k[i] + acc_k[i] P^{-1} - w_k[i]) q_l^{-1}, i < l.
+__global__ void k_ksr_combine(const u64* acc, u64 acc_item_stride, u64 acc_poly_stride, const u64* w,
+                              u64 w_item_stride, const CtRef* base0, const CtRef* base1, const CtRef* out,
+                              const u64* pinv, const u64* pinv_sh, const u64* qlinv, int level, Tables T) {
+  const int n = 1 << T.log_n;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int k = blockIdx.y / level, i = blockIdx.y % level, z = blockIdx.z;
+  const u64 q = T.mods[i].q;
+  const size_t li = (size_t)i * n + c;
+  u64 r = shoup(acc[(size_t)z * acc_item_stride + (size_t)k * acc_poly_stride + li], pinv[i], pinv_sh[i], q);
+  const CtRef* base = k == 0 ? base0 : base1;
+  if (base) r = addm(r, base[z].p[li], q);
+  r = subm(r, w[(size_t)z * w_item_stride + (size_t)k * (level + 1) * n + li], q);
+  out[z].p[(size_t)k * out[z].stride + li] = shoup(r, qlinv[i], qlinv[level + i], q);
+}
+
+}  // namespace
+
+void launch_modup_bconv_fast(hc_ctx* ctx, int level, int j, const u64* xcoef, u64 x_item_stride, u64* ext,
+                             u64 ext_item_stride, int items) {
+  const int alpha = ctx->P.alpha;
+  const int d0 = j * alpha;
+  const int ns = std::min(alpha, level + 1 - d0);
+  const int next = level + 1 + alpha;
+  const u64* cst = ctx->ks(ctx->lv[level].modup_off[j]);
+  const size_t smem = (size_t)next * ns * sizeof(u64) + (size_t)next * sizeof(DMod);
+  const dim3 g = grid_for(ctx, 1, items);
+  ProfScope prof_(ctx, "k_modup_bconv", (uint64_t)items * (next - ns));
+#define HC_MODUP(NS)                                                                                          \
+  case NS:                                                                                                    \
+    k_modup_bconv_t<NS><<<g, kT, smem, ctx->stream>>>(xcoef, x_item_stride, ext, ext_item_stride, cst, d0, \
+                                                       next, ctx->ext_map_of(level), ctx->tab);             \
+    break;
+  switch (ns) {
+    HC_MODUP(1) HC_MODUP(2) HC_MODUP(3) HC_MODUP(4) HC_MODUP(5) HC_MODUP(6) HC_MODUP(7) HC_MODUP(8)
+    default:
+      k_modup_bconv<<<g, kT, 0, ctx->stream>>>(xcoef, x_item_stride, ext, ext_item_stride, cst, d0, ns, next,
+                                              ctx->ext_map_of(level), ctx->tab);
+  }
+#undef HC_MODUP
+  ctx->launches++;
+  check_launch(ctx);
+}
+
+void launch_moddown_bconv_fast(hc_ctx* ctx, int level, const u64* accp_coef, u64 accp_item_stride, u64* z,
+                               u64 z_item_stride, int items) {
+  const int alpha = ctx->P.alpha, nq = level + 1, next = nq + alpha;
+  const u64* cst = ctx->ks(ctx->moddown_off);
+  const size_t smem = (size_t)nq * alpha * sizeof(u64) + (size_t)nq * sizeof(DMod);
+  const dim3 g = grid_for(ctx, 2, items);
+  const u64 ps = (u64)next * ctx->P.n;
+  ProfScope prof_(ctx, "k_moddown_bconv", (uint64_t)items * 2 * nq);
+#define HC_MODDOWN(A)                                                                                          \
+  case A:                                                                                                      \
+    k_moddown_bconv_t<A><<<g, kT, smem, ctx->stream>>>(accp_coef, accp_item_stride, ps, z, z_item_stride, cst, \
+                                                        nq, ctx->P.L, ctx->tab);                               \
+    break;
+  switch (alpha) {
+    HC_MODDOWN(1) HC_MODDOWN(2) HC_MODDOWN(3) HC_MODDOWN(4) HC_MODDOWN(5) HC_MODDOWN(6) HC_MODDOWN(7) HC_MODDOWN(8)
+    default:
+      k_moddown_bconv<<<g, kT, 0, ctx->stream>>>(accp_coef, accp_item_stride, ps, z, z_item_stride, cst, alpha, nq,
+                                                ctx->P.L, ctx->tab);
+  }
+#undef HC_MODDOWN
+  ctx->launches++;
+  check_launch(ctx);
+}
+
+void launch_key_product_batched(hc_ctx* ctx, int level, const u64* ext, u64 ext_item_stride, const u64* key,
+                                u64* acc, u64 acc_item_stride, int items) {
+  const int next = level + 1 + ctx->P.alpha, dnum = ctx->lv[level].dnum;
+  // a few item groups in z so small batches still fill the GPU
+  const int zgroups = std::min(items, std::max(1, 2048 / (next * ((ctx->P.n + kT - 1) / kT))));
+  const dim3 g = grid_for(ctx, next, zgroups);
+  ProfScope prof_(ctx, "k_key_product", (uint64_t)items * next);
+#define HC_KP(D)                                                                                                \
+  case D:                                                                                                       \
+    k_key_product_t<D><<<g, kT, 0, ctx->stream>>>(ext, ext_item_stride, key, acc, acc_item_stride, next,      \
+                                                  ctx->P.nchain(), ctx->ext_map_of(level), items, ctx->tab); \
+    break;
+  switch (dnum) {
+    HC_KP(1) HC_KP(2) HC_KP(3) HC_KP(4) HC_KP(5) HC_KP(6) HC_KP(7) HC_KP(8)
+    default: {
+      const dim3 g2 = grid_for(ctx, next, items);
+      k_key_product<<<g2, kT, 0, ctx->stream>>>(ext, ext_item_stride, key, acc, acc_item_stride, dnum, next,
+                                                ctx->P.nchain(), ctx->ext_map_of(level), ctx->tab);
+    }
+  }
+#undef HC_KP
+  ctx->launches++;
+  check_launch(ctx);
+}
+
+void launch_ksr_last(hc_ctx* ctx, int level, const u64* acc, u64 acc_item_stride, const CtRef* base0,
+                     const CtRef* base1, u64* tl, int items) {
+  const int L = ctx->P.L, a = ctx->P.alpha, next = level + 1 + a;
+  const u64* cst = ctx->ks(ctx->moddown_off);
+  (void)cst;
+  // P^{-1} mod q_level, computed on the host
+  u64 pl = 1;
+  const u64 ql = ctx->P.chain[level];
+  for (int m = 0; m < a; ++m) pl = hch::mulmod(pl, ctx->P.chain[L + 1 + m] % ql, ql);
+  pl = hch::invmod(pl, ql);
+  ProfScope prof_(ctx, "k_ksr_last", (uint64_t)items * 2);
+  k_ksr_last<<<grid_for(ctx, 2, items), kT, 0, ctx->stream>>>(acc, acc_item_stride, (u64)next * ctx->P.n, base0, base1,
+                                                             tl, level, pl, hch::shoup_of(pl, ql), ctx->tab);
+  ctx->launches++;
+  check_launch(ctx);
+}
+
+void launch_ksr_lift(hc_ctx* ctx, int level, const u64* tl, u64* zq, u64 z_item_stride, int items) {
+  const int L = ctx->P.L, a = ctx->P.alpha;
+  const u64* cst = ctx->ks(ctx->moddown_off);
+  const u64* pinv = cst + 2 * a + (size_t)(L + 1) * a;
+  ProfScope prof_(ctx, "k_ksr_lift", (uint64_t)items * 2 * level);
+  k_ksr_lift<<<grid_for(ctx, 2, items), kT, 0, ctx->stream>>>(tl, zq, z_item_stride, level, pinv, pinv + (L + 1),
+                                                             ctx->tab);
+  ctx->launches++;
+  check_launch(ctx);
+}
+
+void launch_ksr_combine(hc_ctx* ctx, int level, const u64* acc, u64 acc_item_stride, const u64* w, u64 w_item_stride,
+                        const CtRef* base0, const CtRef* base1, const CtRef* out, int items) {
+  const int L = ctx->P.L, a = ctx->P.alpha, next = level + 1 + a;
+  const u64* cst = ctx->ks(ctx->moddown_off);
+  const u64* pinv = cst + 2 * a + (size_t)(L + 1) * a;
+  ProfScope prof_(ctx, "k_ksr_combine", (uint64_t)items * 2 * level);
+  k_ksr_combine<<<grid_for(ctx, 2 * level, items), kT, 0, ctx->stream>>>(
+      acc, acc_item_stride, (u64)next * ctx->P.n, w, w_item_stride, base0, base1, out, pinv, pinv + (L + 1),
+      ctx->ks(ctx->lv[level].rescale_off), level, ctx->tab);
+  ctx->launches++;
+  check_launch(ctx);
+}
