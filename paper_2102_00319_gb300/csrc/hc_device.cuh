@@ -85,10 +85,11 @@ __device__ __forceinline__ u64 shoup(u64 a, u64 w, u64 wsh, u64 q) {
 struct U128 {
   u64 lo, hi;
 };
+// acc += a * b exactly (carry through the PTX carry flag).
 __device__ __forceinline__ void mac(U128& acc, u64 a, u64 b) {
-  u64 lo = a * b, hi = __umul64hi(a, b);
-  acc.lo += lo;
-  acc.hi += hi + (acc.lo < lo ? 1ull : 0ull);
+  asm("mad.lo.cc.u64 %0, %2, %3, %0;\n\tmadc.hi.u64 %1, %2, %3, %1;"
+      : "+l"(acc.lo), "+l"(acc.hi)
+      : "l"(a), "l"(b));
 }
 // Fully reduced value of hi 2^64 + lo.
 __device__ __forceinline__ u64 reduce128(U128 x, const DMod& m) {
