@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-ops", type=int, default=1, help="oracle operations in the CPU sample")
+    ap.add_argument("--no-cnn", action="store_true", help="skip the encrypted-CNN images/s leg")
+    ap.add_argument("--cnn-steps", type=int, default=3)
     ap.add_argument("--summarize-ncu", metavar="CSV",
                     help="summarise an ncu launch list (gpu__time_duration.sum) of the timed step and exit")
     ap.add_argument("--step-occurrence", type=int, default=2,
@@ -80,6 +82,24 @@ def summarize_ncu(path, occurrence):
     for k, (c, t) in sorted(per.items(), key=lambda kv: -kv[1][1]):
         print("| %s | %d | %.1f | %.3f |" % (k, c, t, t / total))
     print("| (step) | %d | %.1f | 1.000 |" % (b - a, total))
+
+
+def max_over_ranks(t, device=None):
+    """The largest of the ranks' timings (replicas: the slowest rank bounds
+    the job); a single process returns t."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(t)
+    x = torch.tensor([float(t)], dtype=torch.float64, device=device)
+    dist.all_reduce(x, op=dist.ReduceOp.MAX)
+    return float(x.item())
+
+
+def replica_seed(base, rank):
+    """Each replica draws its own keys and inputs."""
+    return base + 1000 * rank
 
 
 def dist_env():
@@ -214,6 +234,136 @@ def bytes_per_unit(name, n, dnum):
     return 2 * limb
 
 
+def cnn_leg(args, H, W, np, torch, local):
+    """Encrypted images/s of the batch-packed CNN at N = 2^14 (8192 images of
+    28x28: conv 5x5 stride 2 with 5 channels -> x^2 -> 2x2 mean pool -> FC
+    180 -> 10), through the layer calls (batched) and through one ABI call
+    per homomorphic operation (per-op); plus the latency of the N = 2^12
+    single-ciphertext conv (eight rotations) + x^2."""
+    from oracle import cnn as ref_cnn  # FP64 plaintext network only (correctness guard)
+
+    ps, c = W.BATCH_N14, W.CNN_BATCH
+    params = H.hc_params_create(ps.log_n, list(ps.q_bits), list(ps.p_bits), ps.log2_scale)
+    stream = torch.cuda.current_stream()
+    ctx = H.hc_ctx_create(params, local, stream.cuda_stream)
+    K = ctx.n // 2
+    seed = W.MASTER_SEED + 2
+    sk, pk, evk = H.hc_keygen(ctx, seed)
+    imgs = W.images(seed + 20, K, c["H"], c["W"])
+    cw = W.conv_weights(seed + 21, c["cout"], c["k"], c["k"])
+    Ho = (c["H"] - c["k"]) // c["stride"] + 1
+    n_in = (Ho // 2) ** 2 * c["cout"]
+    fw = W.fc_weights(seed + 22, c["n_out"], n_in)
+    scale = 2.0 ** ps.log2_scale
+
+    def const_ct(v, nonce):  # slot constant: the constant polynomial round(v * scale)
+        m = np.zeros(ctx.n, dtype=np.int64)
+        m[0] = int(np.round(v * scale)) if abs(v * scale) < 2 ** 52 else 0
+        return H.hc_encrypt(ctx, pk, H.hc_pt_from_coeffs(ctx, m, ctx.L, scale), seed + 5, nonce)
+
+    xs = [H.hc_encrypt(ctx, pk, H.hc_encode(ctx, imgs[:, h, w], scale, ctx.L), seed + 5, h * c["W"] + w)
+          for h in range(c["H"]) for w in range(c["W"])]
+    ws = [const_ct(cw[co, a, b, 0], 1000 + (co * c["k"] + a) * c["k"] + b)
+          for co in range(c["cout"]) for a in range(c["k"]) for b in range(c["k"])]
+    fws = [const_ct(fw[r, i], 2000 + r * n_in + i) for r in range(c["n_out"]) for i in range(n_in)]
+    H.hc_sync(ctx)
+
+    def batched():
+        y = H.hc_enc_conv2d(ctx, evk, H.HC_PACK_BATCH, xs, c["H"], c["W"], 1, ws, c["cout"], c["k"], c["k"],
+                            c["stride"])
+        a = H.hc_enc_poly_act(ctx, evk, y, c["act"])
+        p = H.hc_enc_pool(ctx, evk, H.HC_PACK_BATCH, a, c["cout"], Ho, Ho)
+        return H.hc_enc_fc(ctx, evk, H.HC_PACK_BATCH, p, fws, c["n_out"])
+
+    def per_op():
+        """The same canonical circuit, one ABI call per homomorphic operation."""
+        y = []
+        for m in range(Ho):
+            for n in range(Ho):
+                for co in range(c["cout"]):
+                    acc = None
+                    for a in range(c["k"]):
+                        for b in range(c["k"]):
+                            t = H.hc_mul(ctx, xs[(m * c["stride"] + a) * c["W"] + n * c["stride"] + b],
+                                         ws[(co * c["k"] + a) * c["k"] + b])
+                            acc = t if acc is None else H.hc_add(ctx, acc, t)
+                    y.append(H.hc_rescale(ctx, H.hc_relin(ctx, evk, acc)))
+        a = [H.hc_rescale(ctx, H.hc_relin(ctx, evk, H.hc_mul(ctx, t, t))) for t in y]
+        p = []
+        for i in range(Ho // 2):
+            for j in range(Ho // 2):
+                for ch in range(c["cout"]):
+                    g = lambda r, q: a[(r * Ho + q) * c["cout"] + ch]
+                    s4 = H.hc_add(ctx, H.hc_add(ctx, g(2 * i, 2 * j), g(2 * i + 1, 2 * j)),
+                                  H.hc_add(ctx, g(2 * i, 2 * j + 1), g(2 * i + 1, 2 * j + 1)))
+                    lv = s4.level
+                    p.append(H.hc_rescale(ctx, H.hc_mul_const(ctx, s4, 0.25, float(H.hc_params_primes(params)[lv]))))
+        z = []
+        for r in range(c["n_out"]):
+            acc = None
+            for k in range(n_in):
+                wv = H.hc_drop_to_level(ctx, fws[r * n_in + k], p[k].level)
+                t = H.hc_mul(ctx, p[k], wv)
+                acc = t if acc is None else H.hc_add(ctx, acc, t)
+            z.append(H.hc_rescale(ctx, H.hc_relin(ctx, evk, acc)))
+        return z
+
+    zb = batched()
+    H.hc_sync(ctx)
+    launches0 = H.hc_kernel_launches(ctx)
+    t0 = time.perf_counter()
+    for _ in range(args.cnn_steps):
+        zb = batched()
+    H.hc_sync(ctx)
+    t_b = (time.perf_counter() - t0) / args.cnn_steps
+    launches_b = (H.hc_kernel_launches(ctx) - launches0) / args.cnn_steps
+    launches0 = H.hc_kernel_launches(ctx)
+    t0 = time.perf_counter()
+    zp = per_op()
+    H.hc_sync(ctx)
+    t_p = time.perf_counter() - t0
+    launches_p = H.hc_kernel_launches(ctx) - launches0
+    same = all(np.array_equal(H.hc_ct_export(ctx, u)[0], H.hc_ct_export(ctx, v)[0]) for u, v in zip(zb, zp))
+    logits = np.stack([H.hc_decode(ctx, H.hc_decrypt(ctx, sk, t)).real for t in zb], axis=1)
+    ref = ref_cnn.network(imgs[..., None], cw, c["stride"], c["act"], fw)
+    err = float(np.max(np.abs(logits - ref)))
+    assert err < 2.0 ** -15 and same, (err, same)
+
+    # single-ciphertext conv + x^2 (rotations), N = 2^12
+    ps1 = W.SINGLE_N12
+    p1 = H.hc_params_create(ps1.log_n, list(ps1.q_bits), list(ps1.p_bits), ps1.log2_scale)
+    ctx1 = H.hc_ctx_create(p1, local, stream.cuda_stream)
+    rots = [a * 8 + b for a in range(3) for b in range(3)]
+    sk1, pk1, evk1 = H.hc_keygen(ctx1, W.MASTER_SEED + 1, rots)
+    img = W.images(5, 1, 8, 8)[0].reshape(-1)
+    w1 = W.conv_weights(6, 1, 3, 3)[0, :, :, 0].reshape(-1)
+    s1 = 2.0 ** ps1.log2_scale
+    x1 = H.hc_encrypt(ctx1, pk1, H.hc_encode(ctx1, img, s1, ctx1.L), 9, 0)
+    w1c = [H.hc_encrypt(ctx1, pk1, H.hc_encode(ctx1, np.full(ctx1.n // 2, v), s1, ctx1.L), 9, 1 + i)
+           for i, v in enumerate(w1)]
+
+    def single():
+        y = H.hc_enc_conv2d(ctx1, evk1, H.HC_PACK_SINGLE, [x1], 8, 8, 1, w1c, 1, 3, 3, 1)
+        return H.hc_enc_poly_act(ctx1, evk1, y, (0.0, 0.0, 1.0))
+
+    single()
+    H.hc_sync(ctx1)
+    t0 = time.perf_counter()
+    for _ in range(5):
+        single()
+    H.hc_sync(ctx1)
+    t_single = (time.perf_counter() - t0) / 5
+    return {
+        "workload": "batch_n14: 8192 images 28x28, conv 5x5/2 x5 -> x^2 -> pool -> fc 180->10",
+        "images_per_s_batched": K / t_b, "images_per_s_per_op": K / t_p,
+        "ms_batched": 1000 * t_b, "ms_per_op": 1000 * t_p, "speedup_batched_vs_per_op": t_p / t_b,
+        "launches_batched": launches_b, "launches_per_op": launches_p,
+        "bit_identical_batched_vs_per_op": same, "max_logit_error_vs_fp64": err,
+        "single_ct_conv_x2_ms": 1000 * t_single,
+        "single_ct_workload": "single_n12: 8x8 image, 3x3 conv by 8 rotations, x^2",
+    }
+
+
 def run_gpu(args, rank, world, local):
     import numpy as np
     import torch
@@ -232,7 +382,7 @@ def run_gpu(args, rank, world, local):
     params = H.hc_params_create(ps.log_n, list(ps.q_bits), list(ps.p_bits), ps.log2_scale)
     ctx = H.hc_ctx_create(params, local, stream.cuda_stream)
     n, L, alpha, dnum = ctx.n, ctx.L, ctx.alpha, ctx.dnum
-    seed = W.MASTER_SEED + 4 + 1000 * rank
+    seed = replica_seed(W.MASTER_SEED + 4, rank)
     sk, pk, evk = H.hc_keygen(ctx, seed)
     Bn = args.batch
     A, Bc = [], []
@@ -282,13 +432,7 @@ def run_gpu(args, rank, world, local):
         cnt, tot, units = H.hc_profile_kernel(ctx, name)
         kernels[name] = (cnt, tot, units)
     H.hc_profile_enable(ctx, False)
-    t_local = ms / 1000.0
-    if world > 1:
-        t = torch.tensor([t_local], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    else:
-        t_max = t_local
+    t_max = max_over_ranks(ms / 1000.0, device="cuda")
     value = Bn * args.steps * world / t_max
 
     # ---------------- e2e through the C ABI from pinned host memory
@@ -319,11 +463,7 @@ def run_gpu(args, rank, world, local):
     for _ in range(args.e2e_steps):
         e2e_step()
     barrier()
-    t_e2e = max(time.perf_counter() - t0, 1e-9)
-    if world > 1:
-        t = torch.tensor([t_e2e], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_e2e = float(t.item())
+    t_e2e = max_over_ranks(max(time.perf_counter() - t0, 1e-9), device="cuda")
     e2e_value = Bn * args.e2e_steps * world / t_e2e if args.e2e_steps > 0 else None
 
     if rank != 0:
@@ -354,6 +494,8 @@ def run_gpu(args, rank, world, local):
         "gpu_launches": launches, "roofline": roofline, "clocks": clk, "kernels": kern_summary,
         "check": {"max_slot_error": err},
     }
+    if not args.no_cnn:
+        line["cnn"] = cnn_leg(args, H, W, np, torch, local)
     if world == 1 and not args.no_cpu_baseline:
         ob = OracleBench()
         dt = ob.run(args.cpu_ops)
