@@ -16,7 +16,7 @@ Activations are channel-last: flat index (i W + j) C + c.
 Encrypted circuits (the canonical circuit both implementations follow):
   * conv, batch packing (Fig. 2, Eq. 3): each output ciphertext is the sum of
     all kh*kw*Cin tensor products X (x) W, then ONE relinearisation and ONE
-    rescale.
+    rescale.  Weights above the inputs' level are dropped to it first.
   * conv, single-ciphertext packing: Y = sum_{p,q} rot(X, p W + q) (x) W_{p,q},
     then one relinearisation and one rescale.
   * poly_act: see `enc_poly_act`.
@@ -80,9 +80,15 @@ def network(x, conv_w, stride, act_coeffs, fc_w, fc_b=None):
 # ---------------------------------------------------------------------------
 # Encrypted circuits (batch packing: one ciphertext per pixel / weight)
 # ---------------------------------------------------------------------------
+def _at_level(params, cts, level):
+    """Weights above the activations' level are dropped to it (as in the FC)."""
+    return [c if c.level == level else ckks.drop_to_level(params, c, level) for c in cts]
+
+
 def enc_conv2d_batch(params, evk, x_cts, H, W, Cin, w_cts, Cout, kh, kw, stride):
     """x_cts[(h W + w) Cin + ci]; w_cts[((co kh + p) kw + q) Cin + ci];
     returns y[(m Wo + n) Cout + co]."""
+    w_cts = _at_level(params, w_cts, x_cts[0].level)
     Ho = (H - kh) // stride + 1
     Wo = (W - kw) // stride + 1
     out = []
@@ -173,5 +179,5 @@ def enc_conv2d_single(params, evk, x_ct, W, w_cts, kh, kw):
     """Y = sum_{p,q} rot(X, p W + q) (x) W_{p,q}; relin; rescale.
     Output slot m W + n holds Y_{m,n} for valid (m, n)."""
     xs = [ckks.rotate(params, evk, x_ct, r) for r in conv_rotations(W, kh, kw)]
-    d = ckks.tensor_sum(params, xs, w_cts)
+    d = ckks.tensor_sum(params, xs, _at_level(params, w_cts, x_ct.level))
     return ckks.rescale(params, ckks.relin(params, evk, d))
