@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--cpu-ops", type=int, default=1, help="oracle operations in the CPU sample")
     ap.add_argument("--no-cnn", action="store_true", help="skip the encrypted-CNN images/s leg")
     ap.add_argument("--cnn-steps", type=int, default=3)
+    ap.add_argument("--no-uneven", action="store_true", help="skip the uneven multi-instance leg")
     ap.add_argument("--summarize-ncu", metavar="CSV",
                     help="summarise an ncu launch list (gpu__time_duration.sum) of the timed step and exit")
     ap.add_argument("--step-occurrence", type=int, default=2,
@@ -219,6 +220,16 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------------------
 # Algorithmic HBM bytes per work unit (one N-word limb of the launch's output
 # domain), per kernel; dnum = 3 at the top level of this workload.
+# DRAM bytes (read + write) per work unit from one ncu capture of the same
+# kernel version on a smaller batch (profiles/ntt_fwd_passes_deep_n16_l20.md:
+# 336 limbs per launch), scaled to a launch by its units.  Set an entry to
+# None when its kernel changes until it is captured again.
+NCU_TRAFFIC_PER_UNIT = {
+    "ntt_fwd_cols": (176.285440e6 + 114.261248e6) / 336,
+    "ntt_fwd_rows": (209.567744e6 + 123.331584e6) / 336,
+}
+
+
 def bytes_per_unit(name, n, dnum):
     limb = 8 * n
     if name.startswith("ntt_"):
@@ -364,6 +375,103 @@ def cnn_leg(args, H, W, np, torch, local):
     }
 
 
+def uneven_leg(H, W, np, torch, local):
+    """64 independent single-ciphertext inferences (8x8 image, 3x3 conv by
+    rotations, x^2) at N = 2^13 / 2^14 / 2^15 and 3..12 levels, run four ways:
+    one ABI call per HE op, one layer call per instance, batched per ring
+    degree and level, and the batched form captured in one CUDA graph."""
+    stream = torch.cuda.Stream(device=local)
+    inst = W.uneven_instances(64)
+    ctxs, keys, ws, xs = {}, {}, {}, []
+    for log_n in (13, 14, 15):
+        ps = W.uneven_params(log_n)
+        params = H.hc_params_create(ps.log_n, list(ps.q_bits), list(ps.p_bits), ps.log2_scale)
+        ctx = H.hc_ctx_create(params, local, stream.cuda_stream)
+        ctxs[log_n] = ctx
+        keys[log_n] = H.hc_keygen(ctx, W.MASTER_SEED + 3 + log_n, W.SINGLE_CONV_STEPS)
+        filt = W.conv_weights(40 + log_n, 1, 3, 3)[0, :, :, 0].reshape(-1)
+        ws[log_n] = [H.hc_encrypt(ctx, keys[log_n][1], H.hc_encode(ctx, np.full(ctx.n // 2, v), 2.0 ** 30, ctx.L), 7, t)
+                     for t, v in enumerate(filt)]
+    for i, (log_n, lv) in enumerate(inst):
+        ctx = ctxs[log_n]
+        z = np.zeros(ctx.n // 2)
+        z[:64] = W.images(1000 + i, 1, 8, 8)[0].reshape(-1)
+        xs.append(H.hc_encrypt(ctx, keys[log_n][1], H.hc_encode(ctx, z, 2.0 ** 30, lv), 9, i))
+    order = [ctxs[k] for k in (13, 14, 15)]
+
+    def sync():
+        for c in order:
+            H.hc_sync(c)
+
+    def per_op():
+        out = []
+        for i, (log_n, lv) in enumerate(inst):
+            ctx, evk = ctxs[log_n], keys[log_n][2]
+            acc = None
+            for t, r in enumerate(W.SINGLE_CONV_STEPS):
+                xr = H.hc_rotate(ctx, evk, xs[i], r)
+                wt = H.hc_drop_to_level(ctx, ws[log_n][t], lv)
+                p = H.hc_mul(ctx, xr, wt)
+                acc = p if acc is None else H.hc_add(ctx, acc, p)
+            y = H.hc_rescale(ctx, H.hc_relin(ctx, evk, acc))
+            out.append(H.hc_rescale(ctx, H.hc_relin(ctx, evk, H.hc_mul(ctx, y, y))))
+        return out
+
+    def per_instance():
+        out = []
+        for i, (log_n, lv) in enumerate(inst):
+            ctx, evk = ctxs[log_n], keys[log_n][2]
+            y = H.hc_enc_conv2d(ctx, evk, H.HC_PACK_SINGLE, [xs[i]], 8, 8, 1, ws[log_n], 1, 3, 3, 1)
+            out.append(H.hc_enc_poly_act(ctx, evk, y, (0.0, 0.0, 1.0))[0])
+        return out
+
+    def batched():
+        out = [None] * len(inst)
+        for log_n, ctx in ctxs.items():
+            idx = [i for i, (ln, _) in enumerate(inst) if ln == log_n]
+            evk = keys[log_n][2]
+            y = H.hc_enc_conv2d_single_batch(ctx, evk, [xs[i] for i in idx], 8, ws[log_n], 1, 3, 3)
+            groups = {}
+            for i, c in zip(idx, y):
+                groups.setdefault(inst[i][1], []).append((i, c))
+            for lv, items in sorted(groups.items()):
+                for (i, _), r in zip(items, H.hc_enc_poly_act(ctx, evk, [c for _, c in items], (0.0, 0.0, 1.0))):
+                    out[i] = r
+        return out
+
+    def timed(fn, reps):
+        fn()
+        sync()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            r = fn()
+        sync()
+        return (time.perf_counter() - t0) / reps, r
+
+    t_op, r_op = timed(per_op, 1)
+    t_inst, r_inst = timed(per_instance, 2)
+    t_b, r_b = timed(batched, 3)
+    H.hc_graph_begin(order, 8 << 30)
+    r_g = batched()
+    g = H.hc_graph_end(order)
+    t_g, _ = timed(lambda: H.hc_graph_launch(g), 5)
+    same = True
+    for i in range(len(inst)):
+        ctx = ctxs[inst[i][0]]
+        ref = H.hc_ct_export(ctx, r_inst[i])[0]
+        for other in (r_op[i], r_b[i], r_g[i]):
+            same &= bool(np.array_equal(H.hc_ct_export(ctx, other)[0], ref))
+    del r_g
+    del g
+    return {
+        "workload": "64 single-ct inferences (8x8, conv 3x3 by rotations, x^2), N in {2^13, 2^14, 2^15}, 3-12 levels",
+        "ms_per_op_calls": 1000 * t_op, "ms_per_instance_layers": 1000 * t_inst,
+        "ms_batched": 1000 * t_b, "ms_graph_launch": 1000 * t_g,
+        "inferences_per_s_graph": len(inst) / t_g, "speedup_graph_vs_per_op": t_op / t_g,
+        "bit_identical_all_forms": same,
+    }
+
+
 def run_gpu(args, rank, world, local):
     import numpy as np
     import torch
@@ -476,8 +584,10 @@ def run_gpu(args, rank, world, local):
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = peaks.get("hbm_gbs", 6800.0)
+    tpu = NCU_TRAFFIC_PER_UNIT.get(dom)
+    traffic = tpu * units / max(cnt, 1) if tpu else None
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "bytes_per_launch": alg_bytes / max(cnt, 1), "avg_launch_us": 1000.0 * tot / max(cnt, 1),
                 "share_of_step": tot / ms}
@@ -496,6 +606,8 @@ def run_gpu(args, rank, world, local):
     }
     if not args.no_cnn:
         line["cnn"] = cnn_leg(args, H, W, np, torch, local)
+    if not args.no_uneven:
+        line["uneven"] = uneven_leg(H, W, np, torch, local)
     if world == 1 and not args.no_cpu_baseline:
         ob = OracleBench()
         dt = ob.run(args.cpu_ops)

@@ -244,6 +244,27 @@ int hc_mul_relin_rescale_batch(hc_ctx *ctx, const hc_evk *evk, const hc_ct *cons
  */
 int hc_relin_noalloc(hc_ctx *ctx, const hc_evk *evk, const hc_ct *x, hc_ct *out);
 
+/* ------------------------------------------------------- graph capture */
+/*
+ * One CUDA graph for a whole multi-instance computation, replayed with one
+ * launch.  The n contexts must share one CUDA stream that is not the legacy
+ * default stream.  hc_graph_begin gives each context an arena of
+ * arena_bytes device bytes (allocated before capture starts) from which every
+ * temporary and every output created until hc_graph_end is carved, so the
+ * captured work allocates nothing; small index tables are written by kernels
+ * that carry them as parameters.  Only evaluation calls (arithmetic, key
+ * switching, layers) may be issued while capturing; calls that synchronise
+ * (import, export, encrypt, decrypt, keygen) fail.  Handles created while
+ * capturing point into the arenas: each hc_graph_launch overwrites their
+ * contents; destroy them before the graph.  HC_ERR_OOM if an arena runs out
+ * (the capture is then abandoned by hc_graph_end).
+ */
+typedef struct hc_graph hc_graph;
+int hc_graph_begin(hc_ctx *const *ctxs, int n, size_t arena_bytes);
+int hc_graph_end(hc_ctx *const *ctxs, int n, hc_graph **out);
+int hc_graph_launch(hc_graph *g);
+void hc_graph_destroy(hc_graph *g);
+
 /* ---------------------------------------------------------- CNN layers */
 typedef enum hc_packing {
   HC_PACK_BATCH = 0,  /* Fig. 2: one ciphertext per pixel / weight, slot k = image k */
@@ -262,11 +283,26 @@ typedef enum hc_packing {
  * HC_PACK_SINGLE: cin = 1, stride = 1, x[0] holds the image row-major with
  *   width W; y[co] = sum_{p,q} rot(x, p*W + q) (x) w[(co*kh + p)*kw + q]
  *   (needs Galois keys for every p*W + q); output (m,n) in slot m*W + n.
- * All inputs at one level >= 1 with one scale per operand kind.
+ * Inputs at one level >= 1 with one scale per operand kind; weights at a
+ * higher level are dropped to the inputs' level.
  */
 int hc_enc_conv2d(hc_ctx *ctx, const hc_evk *evk, hc_packing packing, const hc_ct *const *x,
                   int H, int W, int cin, const hc_ct *const *w, int cout, int kh, int kw,
                   int stride, hc_ct **y);
+/*
+ * Single-ciphertext-packed convolution of many images (one ciphertext each,
+ * image row-major with width W, cin = 1, stride 1) with one set of
+ * cout x kh x kw slot-constant weights:
+ *   y[i*cout + co] = sum_{p,q} rot(x[i], p*W + q) (x) w[(co*kh + p)*kw + q],
+ * one relinearisation and one rescale per output.  Images may sit at
+ * different levels: they are grouped by level and every rotation step runs
+ * as one batched key switch per group; weights at a higher level are
+ * dropped to each group's level.  Bit-identical to hc_enc_conv2d with
+ * HC_PACK_SINGLE applied image by image.
+ */
+int hc_enc_conv2d_single_batch(hc_ctx *ctx, const hc_evk *evk, const hc_ct *const *x, int nimg, int W,
+                               const hc_ct *const *w, int cout, int kh, int kw, hc_ct **y);
+
 /*
  * Polynomial activation g(u) = c0 + c1 u + c2 u^2 (Eq. 4, the paper's
  * 0.47, 0.50, 0.09 approximation of ReLU; (0,0,1) is x^2), elementwise over

@@ -9,7 +9,7 @@
 
 // ------------------------------------------------------------ memory
 DevBuf::~DevBuf() {
-  if (ctx && ptr) ctx->free_words(ptr);
+  if (ctx && ptr && owned) ctx->free_words(ptr);
 }
 
 u64* hc_ctx::alloc_words(size_t words) {
@@ -36,8 +36,17 @@ void hc_ctx::free_words(u64* p) {
 BufPtr hc_ctx::buffer(size_t words) {
   auto b = std::make_shared<DevBuf>();
   b->ctx = this;
-  b->ptr = alloc_words(words);
-  b->bytes = words * sizeof(u64);
+  b->bytes = std::max<size_t>(words, 1) * sizeof(u64);
+  if (arena) {
+    const size_t w = (std::max<size_t>(words, 1) + 31) & ~(size_t)31;  // 256-byte steps
+    if (arena_off + w > arena_words)
+      throw HcError{HC_ERR_OOM, "capture arena exhausted (" + std::to_string(arena_words * 8) + " bytes)"};
+    b->ptr = arena + arena_off;
+    arena_off += w;
+    b->owned = false;
+  } else {
+    b->ptr = alloc_words(words);
+  }
   return b;
 }
 
@@ -1356,10 +1365,15 @@ extern "C" int hc_enc_conv2d(hc_ctx* ctx, const hc_evk* evk, hc_packing packing,
         HC_CHECK(c->level == level && c->degree == 1, HC_ERR_LEVEL_MISMATCH, "inputs at different levels");
         check_scales(c->scale, xs[0]->scale);
       }
-      for (auto* c : ws) {
+      std::vector<hc_ct*> wviews;  // weights above the inputs' level, dropped to it
+      for (auto*& c : ws) {
         check_ct(ctx, c);
-        HC_CHECK(c->level == level && c->degree == 1, HC_ERR_LEVEL_MISMATCH, "weights at another level");
+        HC_CHECK(c->level >= level && c->degree == 1, HC_ERR_LEVEL_MISMATCH, "weights below the inputs' level");
         check_scales(c->scale, ws[0]->scale);
+        if (c->level != level) {
+          wviews.push_back(new hc_ct{ctx, c->buf, c->data, c->stride, level, 1, c->scale});
+          c = wviews.back();
+        }
       }
       HC_CHECK(level >= 1, HC_ERR_DEPTH, "no level left");
       std::vector<int> xi, wi, off{0};
@@ -1377,6 +1391,7 @@ extern "C" int hc_enc_conv2d(hc_ctx* ctx, const hc_evk* evk, hc_packing packing,
       std::vector<hc_ct*> d = tensor_acc(ctx, xs, ws, xi, wi, off, level, xs[0]->scale * ws[0]->scale);
       std::vector<hc_ct*> r = relin_rescale(ctx, evk, d, nullptr);
       free_all(d);
+      free_all(wviews);
       for (size_t i = 0; i < r.size(); ++i) y[i] = r[i];
     } else {
       HC_CHECK(cin == 1 && stride == 1, HC_ERR_INVALID, "single packing supports cin = 1, stride 1");
@@ -1387,9 +1402,14 @@ extern "C" int hc_enc_conv2d(hc_ctx* ctx, const hc_evk* evk, hc_packing packing,
         for (int q = 0; q < kw; ++q) steps.push_back(p * W + q);
       std::vector<hc_ct*> rots = rotate_one(ctx, evk, x0, steps, false);
       std::vector<const hc_ct*> xs(rots.begin(), rots.end()), ws(w, w + cout * kh * kw);
-      for (auto* c : ws) {
+      std::vector<hc_ct*> wviews;
+      for (auto*& c : ws) {
         check_ct(ctx, c);
-        HC_CHECK(c->level == x0->level && c->degree == 1, HC_ERR_LEVEL_MISMATCH, "weights at another level");
+        HC_CHECK(c->level >= x0->level && c->degree == 1, HC_ERR_LEVEL_MISMATCH, "weights below the input's level");
+        if (c->level != x0->level) {
+          wviews.push_back(new hc_ct{ctx, c->buf, c->data, c->stride, x0->level, 1, c->scale});
+          c = wviews.back();
+        }
       }
       std::vector<int> xi, wi, off{0};
       for (int co = 0; co < cout; ++co) {
@@ -1403,6 +1423,7 @@ extern "C" int hc_enc_conv2d(hc_ctx* ctx, const hc_evk* evk, hc_packing packing,
       std::vector<hc_ct*> r = relin_rescale(ctx, evk, d, nullptr);
       free_all(d);
       free_all(rots);
+      free_all(wviews);
       for (size_t i = 0; i < r.size(); ++i) y[i] = r[i];
     }
   });
@@ -1562,5 +1583,182 @@ extern "C" int hc_enc_fc(hc_ctx* ctx, const hc_evk* evk, hc_packing packing, con
     free_all(d);
     free_all(views);
     for (int i = 0; i < n_out; ++i) y[i] = r[i];
+  });
+}
+
+// =====================================================================
+// Graph capture
+// =====================================================================
+struct hc_graph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t stream = nullptr;
+  std::vector<void*> arenas;
+};
+
+namespace {
+int check_graph_ctxs(hc_ctx* const* ctxs, int n, cudaStream_t* stream) {
+  if (!ctxs || n <= 0) return HC_ERR_INVALID;
+  for (int i = 0; i < n; ++i)
+    if (!ctxs[i] || ctxs[i]->stream != ctxs[0]->stream) return HC_ERR_INVALID;
+  if (ctxs[0]->stream == nullptr) return HC_ERR_INVALID;
+  *stream = ctxs[0]->stream;
+  return HC_OK;
+}
+}  // namespace
+
+extern "C" int hc_graph_begin(hc_ctx* const* ctxs, int n, size_t arena_bytes) {
+  cudaStream_t st;
+  int rc = check_graph_ctxs(ctxs, n, &st);
+  if (rc != HC_OK) return rc;
+  return guard(ctxs[0], [&] {
+    const size_t words = std::max<size_t>(arena_bytes / 8, 32);
+    for (int i = 0; i < n; ++i) HC_CHECK(!ctxs[i]->arena, HC_ERR_INVALID, "context already capturing");
+    HC_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < n; ++i) {
+      void* p = nullptr;
+      if (cudaMalloc(&p, words * 8) != cudaSuccess) {
+        cudaGetLastError();
+        for (int k = 0; k < i; ++k) {
+          cudaFree(ctxs[k]->arena);
+          ctxs[k]->arena = nullptr;
+        }
+        throw HcError{HC_ERR_OOM, "cannot allocate the capture arena"};
+      }
+      ctxs[i]->arena = (u64*)p;
+      ctxs[i]->arena_words = words;
+      ctxs[i]->arena_off = 0;
+    }
+    HC_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  });
+}
+
+extern "C" int hc_graph_end(hc_ctx* const* ctxs, int n, hc_graph** out) {
+  cudaStream_t st;
+  int rc = check_graph_ctxs(ctxs, n, &st);
+  if (rc != HC_OK) return rc;
+  auto* g = new hc_graph();
+  g->stream = st;
+  for (int i = 0; i < n; ++i) {
+    if (ctxs[i]->arena) g->arenas.push_back(ctxs[i]->arena);
+    ctxs[i]->arena = nullptr;
+    ctxs[i]->arena_words = ctxs[i]->arena_off = 0;
+  }
+  rc = guard(ctxs[0], [&] {
+    HC_CHECK(out, HC_ERR_INVALID, "null output");
+    cudaError_t e = cudaStreamEndCapture(st, &g->graph);
+    HC_CHECK(e == cudaSuccess && g->graph, HC_ERR_CUDA,
+             std::string("capture failed: ") + cudaGetErrorString(e));
+    HC_CUDA(cudaGraphInstantiate(&g->exec, g->graph, 0));
+    *out = g;
+  });
+  if (rc != HC_OK) {
+    cudaGetLastError();
+    hc_graph_destroy(g);
+  }
+  return rc;
+}
+
+extern "C" int hc_graph_launch(hc_graph* g) {
+  if (!g || !g->exec) return HC_ERR_INVALID;
+  return cudaGraphLaunch(g->exec, g->stream) == cudaSuccess ? HC_OK : HC_ERR_CUDA;
+}
+
+extern "C" void hc_graph_destroy(hc_graph* g) {
+  if (!g) return;
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  for (void* p : g->arenas) cudaFree(p);
+  delete g;
+}
+
+// =====================================================================
+// Batched single-ciphertext convolution
+// =====================================================================
+extern "C" int hc_enc_conv2d_single_batch(hc_ctx* ctx, const hc_evk* evk, const hc_ct* const* x, int nimg, int W,
+                                          const hc_ct* const* w, int cout, int kh, int kw, hc_ct** y) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    HC_CHECK(evk && nimg >= 0 && (nimg == 0 || (x && w && y)) && W > 0 && cout > 0 && kh > 0 && kw > 0,
+             HC_ERR_INVALID, "bad arguments");
+    if (nimg == 0) return;
+    const int n = ctx->P.n, T = kh * kw;
+    std::vector<int> steps;
+    for (int p = 0; p < kh; ++p)
+      for (int q = 0; q < kw; ++q) steps.push_back(p * W + q);
+    std::vector<u64> gs;
+    for (int r : steps) {
+      const u64 g = galois_elt(ctx->P, r);
+      if (g != 1) HC_CHECK(evk->galois.count(g), HC_ERR_NO_KEY, "no Galois key for rotation " + std::to_string(r));
+      gs.push_back(g);
+    }
+    std::map<int, std::vector<int>> groups;  // level -> image indices
+    for (int i = 0; i < nimg; ++i) {
+      check_ct(ctx, x[i]);
+      HC_CHECK(x[i]->degree == 1 && x[i]->level >= 1, HC_ERR_DEPTH, "images need degree 1 and a level to spend");
+      groups[x[i]->level].push_back(i);
+    }
+    for (int i = 0; i < cout * T; ++i) {
+      check_ct(ctx, w[i]);
+      HC_CHECK(w[i]->degree == 1, HC_ERR_INVALID, "weights need degree 1");
+    }
+    for (auto& kv : groups) {
+      const int level = kv.first, nq = level + 1;
+      const std::vector<int>& idx = kv.second;
+      const int G = (int)idx.size();
+      std::vector<BufPtr> keep;
+      // rotated images, step-major: rot[t * G + g]
+      std::vector<hc_ct*> rot = new_cts(ctx, T * G, level, 1, x[idx[0]]->scale);
+      BufPtr tmp = ctx->buffer(2 * (size_t)G * nq * n);
+      keep.push_back(tmp);
+      std::vector<CtRef> xr, tr, t0, t1;
+      for (int gi = 0; gi < G; ++gi) {
+        const hc_ct* c = x[idx[gi]];
+        check_scales(c->scale, x[idx[0]]->scale);
+        xr.push_back(c->ref());
+        u64* base = tmp->ptr + (size_t)gi * 2 * nq * n;
+        tr.push_back(CtRef{base, (u64)nq * n});
+        t0.push_back(CtRef{base, (u64)nq * n});
+        t1.push_back(CtRef{base + (size_t)nq * n, (u64)nq * n});
+      }
+      const CtRef* xrd = refs_dev(ctx, xr, keep);
+      const CtRef* trd = refs_dev(ctx, tr, keep);
+      for (int t = 0; t < T; ++t) {
+        std::vector<CtRef> o;
+        for (int gi = 0; gi < G; ++gi) o.push_back(rot[t * G + gi]->ref());
+        if (gs[t] == 1) {
+          launch_ew(ctx, 3, refs_dev(ctx, o, keep), xrd, nullptr, G, 2, nq);
+          continue;
+        }
+        launch_automorph(ctx, trd, xrd, G, 2, nq, gs[t]);
+        keyswitch_batch(ctx, evk->galois.at(gs[t]).buf->ptr, level, t1, &t0, nullptr, o);
+      }
+      // weights viewed at this level
+      std::vector<hc_ct*> wv;
+      std::vector<const hc_ct*> ws;
+      for (int i = 0; i < cout * T; ++i) {
+        HC_CHECK(w[i]->level >= level, HC_ERR_LEVEL_MISMATCH, "weight below an image's level");
+        wv.push_back(new hc_ct{ctx, w[i]->buf, w[i]->data, w[i]->stride, level, 1, w[i]->scale});
+        ws.push_back(wv.back());
+      }
+      std::vector<const hc_ct*> xs(rot.begin(), rot.end());
+      std::vector<int> xi, wi, off{0};
+      for (int gi = 0; gi < G; ++gi)
+        for (int co = 0; co < cout; ++co) {
+          for (int t = 0; t < T; ++t) {
+            xi.push_back(t * G + gi);
+            wi.push_back(co * T + t);
+          }
+          off.push_back((int)xi.size());
+        }
+      std::vector<hc_ct*> d = tensor_acc(ctx, xs, ws, xi, wi, off, level, xs[0]->scale * ws[0]->scale);
+      std::vector<hc_ct*> r = relin_rescale(ctx, evk, d, nullptr);
+      for (int gi = 0; gi < G; ++gi)
+        for (int co = 0; co < cout; ++co) y[idx[gi] * cout + co] = r[gi * cout + co];
+      free_all(d);
+      free_all(rot);
+      free_all(wv);
+    }
   });
 }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 #include <map>
 #include <memory>
 #include <string>
@@ -49,6 +50,7 @@ struct DevBuf {
   hc_ctx* ctx = nullptr;
   u64* ptr = nullptr;
   size_t bytes = 0;
+  bool owned = true;  // false: carved from the context's capture arena
   ~DevBuf();
 };
 using BufPtr = std::shared_ptr<DevBuf>;
@@ -84,6 +86,9 @@ struct hc_ctx {
   std::map<std::string, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>> prof_events;
   std::map<std::string, uint64_t> prof_units;
   std::vector<cudaEvent_t> event_pool;
+  // capture arena: while set, buffer() bump-allocates here instead of the allocator
+  u64* arena = nullptr;
+  size_t arena_words = 0, arena_off = 0;
 
   u64* alloc_words(size_t words);
   void free_words(u64* p);
@@ -160,13 +165,20 @@ struct ProfScope {
   ~ProfScope();
 };
 
+// Writes `words` host words to device memory in stream order: a pageable
+// copy normally, kernels carrying the words as parameters while the stream
+// is being captured into a graph (so the graph holds the values).
+void upload_words(hc_ctx* ctx, u64* dst, const u64* src, size_t words);
+
 // Upload a small host array to fresh device memory owned by `keep`.
 template <class T>
 T* upload(hc_ctx* ctx, const std::vector<T>& v, std::vector<BufPtr>& keep) {
   if (v.empty()) return nullptr;
   size_t words = (v.size() * sizeof(T) + 7) / 8;
   BufPtr b = ctx->buffer(words);
-  HC_CUDA(cudaMemcpyAsync(b->ptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+  std::vector<u64> tmp(words, 0);
+  std::memcpy(tmp.data(), v.data(), v.size() * sizeof(T));
+  upload_words(ctx, b->ptr, tmp.data(), words);
   keep.push_back(b);
   return reinterpret_cast<T*>(b->ptr);
 }

@@ -329,6 +329,33 @@ __global__ void k_sum4(const CtRef* out, const CtRef* x, const int* idx, int nl,
 
 }  // namespace
 
+namespace {
+constexpr int kFillWords = 480;  // 3840 bytes of kernel parameters
+struct FillBlock {
+  u64 w[kFillWords];
+};
+__global__ void k_fill(u64* dst, FillBlock b, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = b.w[i];
+}
+}  // namespace
+
+void upload_words(hc_ctx* ctx, u64* dst, const u64* src, size_t words) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  HC_CUDA(cudaStreamIsCapturing(ctx->stream, &st));
+  if (st == cudaStreamCaptureStatusNone) {
+    HC_CUDA(cudaMemcpyAsync(dst, src, words * sizeof(u64), cudaMemcpyHostToDevice, ctx->stream));
+    return;
+  }
+  for (size_t o = 0; o < words; o += kFillWords) {
+    FillBlock b;
+    const int n = (int)std::min<size_t>(kFillWords, words - o);
+    std::memcpy(b.w, src + o, n * sizeof(u64));
+    k_fill<<<1, 128, 0, ctx->stream>>>(dst + o, b, n);
+    ctx->launches++;
+  }
+  HC_CUDA(cudaGetLastError());
+}
+
 void check_launch(hc_ctx* ctx) {
   (void)ctx;
   HC_CUDA(cudaGetLastError());

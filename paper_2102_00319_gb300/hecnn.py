@@ -37,7 +37,8 @@ EXPORTS = [
     "hc_ct_meta_of", "hc_ct_destroy", "hc_add", "hc_sub", "hc_add_const", "hc_mul_const", "hc_mul",
     "hc_relin", "hc_rescale", "hc_drop_to_level", "hc_rotate", "hc_rotate_hoisted",
     "hc_mul_relin_rescale_batch", "hc_enc_conv2d", "hc_enc_poly_act", "hc_enc_pool", "hc_enc_fc",
-    "hc_relin_noalloc",
+    "hc_relin_noalloc", "hc_graph_begin", "hc_graph_end", "hc_graph_launch", "hc_graph_destroy",
+    "hc_enc_conv2d_single_batch",
 ]
 
 
@@ -124,6 +125,11 @@ def load(path: str = LIB_PATH):
         "hc_enc_pool": (c_int, [vp, vp, c_int, pp, c_int, c_int, c_int, pp]),
         "hc_enc_fc": (c_int, [vp, vp, c_int, pp, c_int, pp, pp, c_int, pp]),
         "hc_relin_noalloc": (c_int, [vp, vp, vp, vp]),
+        "hc_graph_begin": (c_int, [pp, c_int, ctypes.c_size_t]),
+        "hc_graph_end": (c_int, [pp, c_int, pp]),
+        "hc_graph_launch": (c_int, [vp]),
+        "hc_graph_destroy": (None, [vp]),
+        "hc_enc_conv2d_single_batch": (c_int, [vp, vp, pp, c_int, c_int, pp, c_int, c_int, c_int, pp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -487,6 +493,37 @@ def hc_enc_conv2d(ctx, evk, packing, x, H, W, cin, w, cout, kh, kw, stride):
     outs = _outs(nout)
     _check(ctx, load().hc_enc_conv2d(ctx.ptr, evk.ptr, packing, _ptr_array(x), H, W, cin, _ptr_array(w), cout, kh, kw,
                                      stride, outs))
+    return _wrap_outs(ctx, outs, nout)
+
+
+class Graph(_Handle):
+    _destroy = "hc_graph_destroy"
+
+
+def hc_graph_begin(ctxs, arena_bytes):
+    arr = _ptr_array(ctxs)
+    rc = load().hc_graph_begin(arr, len(ctxs), arena_bytes)
+    _check(ctxs[0], rc)
+
+
+def hc_graph_end(ctxs):
+    arr = _ptr_array(ctxs)
+    out = _out()
+    _check(ctxs[0], load().hc_graph_end(arr, len(ctxs), ctypes.byref(out)))
+    return Graph(out.value, list(ctxs))
+
+
+def hc_graph_launch(g):
+    rc = load().hc_graph_launch(g.ptr)
+    if rc != HC_OK:
+        raise HcError(rc, "hc_graph_launch")
+
+
+def hc_enc_conv2d_single_batch(ctx, evk, x, W, w, cout, kh, kw):
+    nout = len(x) * cout
+    outs = _outs(nout)
+    _check(ctx, load().hc_enc_conv2d_single_batch(ctx.ptr, evk.ptr, _ptr_array(x), len(x), W, _ptr_array(w), cout,
+                                                  kh, kw, outs))
     return _wrap_outs(ctx, outs, nout)
 
 

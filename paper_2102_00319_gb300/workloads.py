@@ -77,3 +77,25 @@ def int_plaintext(seed: int, n: int, bound: int) -> np.ndarray:
 # Batch-packed CNN of the N = 2^14 workload: conv 5x5 stride 2 with 5
 # channels -> x^2 -> 2x2 mean pool -> FC 180 -> 10.
 CNN_BATCH = dict(H=28, W=28, cin=1, cout=5, k=5, stride=2, act=(0.0, 0.0, 1.0), n_out=10)
+
+
+# Uneven multi-instance batch: 64 independent single-ciphertext inferences
+# (8x8 image, 3x3 conv by rotations, x^2) with instance i at ring degree
+# N = 2^(13 + i mod 3) and 3 + (7 i mod 10) rescalable primes (3..12).  The
+# parameter style is the N = 2^12 workload's: a 50-bit q_0, 30-bit rescale
+# primes, one 50-bit special prime, scale 2^30.  One 12-level context per
+# ring degree serves every instance of that degree: prime chains and key
+# limbs of a shorter chain are prefixes of the longer one.
+UNEVEN_LMAX = 12
+
+
+def uneven_params(log_n):
+    return ParamSet("uneven_n%d" % log_n, log_n, (50,) + (30,) * UNEVEN_LMAX, (50,), 30)
+
+
+def uneven_instances(count=64):
+    """(log_n, level) of each instance."""
+    return [(13 + i % 3, 3 + (7 * i) % 10) for i in range(count)]
+
+
+SINGLE_CONV_STEPS = [p * 8 + q for p in range(3) for q in range(3)]

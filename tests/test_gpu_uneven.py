@@ -1,0 +1,130 @@
+"""Batched uneven multi-instance execution: 64 single-ciphertext inferences
+(conv by rotations, then x^2) at mixed ring degrees and levels, run (a) one
+instance at a time through the layer calls, (b) batched per ring degree with
+hc_enc_conv2d_single_batch, (c) captured into one CUDA graph and replayed.
+(a), (b), (c) are bit-identical; sampled instances match the oracle."""
+import numpy as np
+import pytest
+
+from oracle import ckks, cnn
+from paper_2102_00319_gb300 import hecnn as H
+from paper_2102_00319_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+SAMPLED = {0, 1, 2}  # one instance per ring degree (levels 3, 10, 7)
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import torch
+
+    stream = torch.cuda.Stream()
+    ctxs, keys, oracle_keys, ws, ows = {}, {}, {}, {}, {}
+    for log_n in (13, 14, 15):
+        ps = W.uneven_params(log_n)
+        params = H.hc_params_create(ps.log_n, list(ps.q_bits), list(ps.p_bits), ps.log2_scale)
+        ctx = H.hc_ctx_create(params, 0, stream.cuda_stream)
+        seed = W.MASTER_SEED + 3 + log_n
+        keys[log_n] = H.hc_keygen(ctx, seed, W.SINGLE_CONV_STEPS)
+        ctxs[log_n] = ctx
+        op = ckks.Params(ps.log_n, list(ps.q_bits), list(ps.p_bits), ps.log2_scale)
+        oracle_keys[log_n] = (op,) + ckks.keygen(op, seed, W.SINGLE_CONV_STEPS)
+        filt = W.conv_weights(40 + log_n, 1, 3, 3)[0, :, :, 0].reshape(-1)
+        wl, owl = [], []
+        for t, v in enumerate(filt):
+            m = np.zeros(ctx.n, dtype=np.int64)
+            m[0] = ckks.llround(float(v) * 2.0 ** 30)
+            wl.append(H.hc_encrypt(ctx, keys[log_n][1], H.hc_pt_from_coeffs(ctx, m, ctx.L, 2.0 ** 30), 7, 100 + t))
+            owl.append(ckks.encrypt(op, oracle_keys[log_n][2], ckks.plaintext_from_ints(op, m, op.L, 2.0 ** 30), 7,
+                                    100 + t))
+        ws[log_n], ows[log_n] = wl, owl
+    inst = W.uneven_instances(64)
+    xs, oxs, imgs = [], {}, []
+    for i, (log_n, lv) in enumerate(inst):
+        ctx = ctxs[log_n]
+        img = W.images(1000 + i, 1, 8, 8)[0]
+        imgs.append(img)
+        if i in SAMPLED:  # an integer plaintext both sides encrypt
+            m = W.int_plaintext(2000 + i, ctx.n, 2 ** 35)
+            op, osk, opk, oevk = oracle_keys[log_n]
+            oxs[i] = ckks.encrypt(op, opk, ckks.plaintext_from_ints(op, m, lv, 2.0 ** 30), 9, i)
+            pt = H.hc_pt_from_coeffs(ctx, m, lv, 2.0 ** 30)
+        else:
+            z = np.zeros(ctx.n // 2)
+            z[:64] = img.reshape(-1)
+            pt = H.hc_encode(ctx, z, 2.0 ** 30, lv)
+        xs.append(H.hc_encrypt(ctx, keys[log_n][1], pt, 9, i))
+    for c in ctxs.values():
+        H.hc_sync(c)
+    return dict(ctxs=ctxs, keys=keys, oracle_keys=oracle_keys, ws=ws, ows=ows, inst=inst, xs=xs, oxs=oxs, imgs=imgs)
+
+
+def run_batched(S):
+    out = [None] * len(S["inst"])
+    for log_n, ctx in S["ctxs"].items():
+        idx = [i for i, (ln, _) in enumerate(S["inst"]) if ln == log_n]
+        evk = S["keys"][log_n][2]
+        y = H.hc_enc_conv2d_single_batch(ctx, evk, [S["xs"][i] for i in idx], 8, S["ws"][log_n], 1, 3, 3)
+        by_level = {}
+        for i, c in zip(idx, y):
+            by_level.setdefault(S["inst"][i][1], []).append((i, c))
+        for lv, items in sorted(by_level.items()):
+            a = H.hc_enc_poly_act(ctx, evk, [c for _, c in items], (0.0, 0.0, 1.0))
+            for (i, _), r in zip(items, a):
+                out[i] = r
+    return out
+
+
+def export(S, i, ct):
+    return H.hc_ct_export(S["ctxs"][S["inst"][i][0]], ct)[0]
+
+
+def test_uneven_batched_and_graph_match_per_instance(setup):
+    S = setup
+    ref = []
+    for i, (log_n, lv) in enumerate(S["inst"]):
+        ctx, evk = S["ctxs"][log_n], S["keys"][log_n][2]
+        y = H.hc_enc_conv2d(ctx, evk, H.HC_PACK_SINGLE, [S["xs"][i]], 8, 8, 1, S["ws"][log_n], 1, 3, 3, 1)
+        ref.append(H.hc_enc_poly_act(ctx, evk, y, (0.0, 0.0, 1.0))[0])
+    got = run_batched(S)
+    for i in range(len(ref)):
+        assert np.array_equal(export(S, i, got[i]), export(S, i, ref[i])), i
+    ctx_list = [S["ctxs"][k] for k in (13, 14, 15)]
+    H.hc_graph_begin(ctx_list, 8 << 30)
+    cap = run_batched(S)
+    g = H.hc_graph_end(ctx_list)
+    for rep in range(2):
+        H.hc_graph_launch(g)
+        for c in ctx_list:
+            H.hc_sync(c)
+        for i in range(len(ref)):
+            assert np.array_equal(export(S, i, cap[i]), export(S, i, ref[i])), (rep, i)
+    del cap
+    del g
+
+
+def test_uneven_sampled_instances_match_oracle(setup):
+    S = setup
+    got = run_batched(S)
+    for i in sorted(SAMPLED):
+        log_n, lv = S["inst"][i]
+        op, osk, opk, oevk = S["oracle_keys"][log_n]
+        y = cnn.enc_conv2d_single(op, oevk, S["oxs"][i], 8, S["ows"][log_n], 3, 3)
+        exp = cnn.enc_poly_act(op, oevk, y, (0.0, 0.0, 1.0))
+        data, meta = H.hc_ct_export(S["ctxs"][log_n], got[i])
+        assert meta.level == exp.level == lv - 2 and np.array_equal(data, exp.c), i
+
+
+def test_uneven_outputs_decrypt_to_conv_squared(setup):
+    S = setup
+    got = run_batched(S)
+    for i in (3, 4, 5, 30, 63):
+        log_n, lv = S["inst"][i]
+        ctx, sk = S["ctxs"][log_n], S["keys"][log_n][0]
+        v = H.hc_decode(ctx, H.hc_decrypt(ctx, sk, got[i])).real
+        filt = W.conv_weights(40 + log_n, 1, 3, 3)[0, :, :, 0]
+        ref = cnn.conv2d(S["imgs"][i][None, :, :, None], filt[None, :, :, None])[0, :, :, 0] ** 2
+        valid = np.array([v[m * 8 + n] for m in range(6) for n in range(6)])
+        # scale 2^30 with 30-bit primes at N up to 2^15 keeps about ten bits
+        # of slot precision through conv and x^2 (observed errors ~1e-3)
+        assert np.max(np.abs(valid - ref.reshape(-1))) < 2.0 ** -8, i
