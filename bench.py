@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-cnn", action="store_true", help="skip the encrypted-CNN images/s leg")
     ap.add_argument("--cnn-steps", type=int, default=3)
     ap.add_argument("--no-uneven", action="store_true", help="skip the uneven multi-instance leg")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop leg")
+    ap.add_argument("--serve-requests", type=int, default=60, help="requests per arrival rate")
     ap.add_argument("--summarize-ncu", metavar="CSV",
                     help="summarise an ncu launch list (gpu__time_duration.sum) of the timed step and exit")
     ap.add_argument("--step-occurrence", type=int, default=2,
@@ -472,6 +474,50 @@ def uneven_leg(H, W, np, torch, local):
     }
 
 
+def serving_leg(args, H, W, np, torch, local):
+    """Poisson arrivals at 20..200 req/s mixing N = 2^12 single-ciphertext
+    requests with the uneven multi-instance requests; keys, weights and request
+    ciphertexts device-resident; admission by device footprint."""
+    from paper_2102_00319_gb300 import serving
+
+    stream = torch.cuda.Stream(device=local)
+
+    def event():
+        e = torch.cuda.Event()
+        e.record(stream)
+        return e
+
+    models, pks = {}, {}
+    sets = [(12, W.SINGLE_N12)] + [(k, W.uneven_params(k)) for k in (13, 14, 15)]
+    for log_n, ps in sets:
+        params = H.hc_params_create(ps.log_n, list(ps.q_bits), list(ps.p_bits), ps.log2_scale)
+        ctx = H.hc_ctx_create(params, local, stream.cuda_stream)
+        sk, pk, evk = H.hc_keygen(ctx, W.MASTER_SEED + 5 + log_n, W.SINGLE_CONV_STEPS)
+        filt = W.conv_weights(60 + log_n, 1, 3, 3)[0, :, :, 0].reshape(-1)
+        ws = [H.hc_encrypt(ctx, pk, H.hc_encode(ctx, np.full(ctx.n // 2, v), 2.0 ** 30, ctx.L), 3, t)
+              for t, v in enumerate(filt)]
+        models[log_n] = serving.Model(ctx=ctx, evk=evk, weights=ws, n=ctx.n, n_special=len(ps.p_bits))
+        pks[log_n] = pk
+    budget = 16 << 30
+    out = {"workload": "single-ct conv 3x3 + x^2 requests: 1/4 at N=2^12 (L=2), 3/4 uneven N=2^13..2^15 (3-12 levels)",
+           "budget_bytes": budget, "rates": {}}
+    inst = W.uneven_instances(args.serve_requests)
+    for k, rate in enumerate((20.0, 50.0, 100.0, 200.0)):
+        reqs = []
+        for i in range(args.serve_requests):
+            log_n, lv = (12, 2) if i % 4 == 0 else inst[i]
+            m = models[log_n]
+            z = np.zeros(m.n // 2)
+            z[:64] = W.images(7000 + 100 * k + i, 1, 8, 8)[0].reshape(-1)
+            ct = H.hc_encrypt(m.ctx, pks[log_n], H.hc_encode(m.ctx, z, 2.0 ** 30, lv), 13, 1000 * k + i)
+            reqs.append(serving.Request(i, log_n, ct, 0.0))
+        for m in models.values():
+            H.hc_sync(m.ctx)
+        srv = serving.Server(models=models, budget_bytes=budget, max_batch=64)
+        out["rates"][str(int(rate))] = serving.run(srv, reqs, serving.poisson_arrivals(rate, len(reqs), 70 + k), event)
+    return out
+
+
 def run_gpu(args, rank, world, local):
     import numpy as np
     import torch
@@ -608,6 +654,8 @@ def run_gpu(args, rank, world, local):
         line["cnn"] = cnn_leg(args, H, W, np, torch, local)
     if not args.no_uneven:
         line["uneven"] = uneven_leg(H, W, np, torch, local)
+    if not args.no_serve:
+        line["serving"] = serving_leg(args, H, W, np, torch, local)
     if world == 1 and not args.no_cpu_baseline:
         ob = OracleBench()
         dt = ob.run(args.cpu_ops)
