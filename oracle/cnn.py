@@ -181,3 +181,91 @@ def enc_conv2d_single(params, evk, x_ct, W, w_cts, kh, kw):
     xs = [ckks.rotate(params, evk, x_ct, r) for r in conv_rotations(W, kh, kw)]
     d = ckks.tensor_sum(params, xs, _at_level(params, w_cts, x_ct.level))
     return ckks.rescale(params, ckks.relin(params, evk, d))
+
+
+# ---------------------------------------------------------------------------
+# Deep single-ciphertext network (one image per ciphertext, N = 2^16 class)
+# ---------------------------------------------------------------------------
+def poly_eval(x, c):
+    """sum_i c_i x^i (FP64)."""
+    y = np.zeros_like(x)
+    for ci in reversed(c):
+        y = y * x + ci
+    return y
+
+
+def deep_network(img, conv_w, act, fc_w):
+    """img [H][W], conv_w [C][3][3], act: coefficients c_0..c_d, fc_w
+    [n_out][(H'/2)(W'/2)C] (channel-last flatten) -> logits [n_out]."""
+    y = conv2d(img[None, :, :, None], conv_w[:, :, :, None])[0]  # [Ho][Wo][C]
+    y = poly_eval(y, act)
+    z = mean_pool2(y[None])[0]
+    return fc_w @ z.reshape(-1)
+
+
+def enc_conv2d_single_hoisted(params, evk, x_ct, W, w_cts, kh, kw, cout):
+    """Conv with cout filters by one set of hoisted rotations of x:
+    y_co = sum_t rot(x, r_t) (x) w[co kh kw + t]; relin; rescale."""
+    rots = ckks.rotate_hoisted(params, evk, x_ct, conv_rotations(W, kh, kw))
+    out = []
+    T = kh * kw
+    for co in range(cout):
+        ws = _at_level(params, w_cts[co * T:(co + 1) * T], x_ct.level)
+        d = ckks.tensor_sum(params, rots, ws)
+        out.append(ckks.rescale(params, ckks.relin(params, evk, d)))
+    return out
+
+
+def enc_poly7(params, evk, u, c):
+    """Degree-7 activation sum_i c_i u^i by a Paterson-Stockmeyer split
+    (baby steps u, u^2, u^3, giant step u^4), four levels:
+      u2 = rs(rl(u u))                       l-1
+      u4 = rs(rl(u2 u2)),  u3 = rs(rl(u2 u))  l-2
+      deg3(a, b, c, d) = a + b u + c u2 + d u3 at l-3 with the scale of
+        rs(u3 * d @ q_{l-2}); the u and u2 terms are brought to it by their
+        constant's scale, as in the degree-2 activation
+      qa = deg3(c0..c3), qb = deg3(c4..c7)
+      out = rs(rl(qb u4)) + rs(qa * 1 @ (target scale) q_{l-3} / s_qa)   l-4"""
+    lv = u.level
+    q = params.q
+    u2 = enc_square(params, evk, u)
+    u4 = enc_square(params, evk, u2)
+    u3 = ckks.rescale(params, ckks.relin(params, evk, ckks.mul(params, u2, ckks.drop_to_level(params, u, lv - 1))))
+
+    def deg3(a0, a1, a2, a3):
+        t3 = ckks.rescale(params, ckks.mul_const(params, u3, a3, float(q[lv - 2])))
+        u2d = ckks.drop_to_level(params, u2, lv - 2)
+        t2 = ckks.rescale(params, ckks.mul_const(params, u2d, a2, t3.scale * float(q[lv - 2]) / u2d.scale))
+        ud = ckks.drop_to_level(params, u, lv - 2)
+        t1 = ckks.rescale(params, ckks.mul_const(params, ud, a1, t3.scale * float(q[lv - 2]) / ud.scale))
+        return ckks.add_const(params, ckks.add(params, ckks.add(params, t3, t2), t1), a0)
+
+    qa = deg3(*c[0:4])
+    qb = deg3(*c[4:8])
+    prod = ckks.rescale(params, ckks.relin(params, evk, ckks.mul(params, qb, ckks.drop_to_level(params, u4, lv - 3))))
+    qa2 = ckks.rescale(params, ckks.mul_const(params, qa, 1.0, prod.scale * float(q[lv - 3]) / qa.scale))
+    return ckks.add(params, prod, qa2)
+
+
+def enc_pool_single(params, evk, y, W):
+    """2x2 mean inside one ciphertext: ((y + rot W) + (rot 1 + rot W+1)) / 4,
+    the three rotations hoisted; pooled (i, j) lands in slot 2i W + 2j."""
+    rW, r1, rW1 = ckks.rotate_hoisted(params, evk, y, [W, 1, W + 1])
+    s = ckks.add(params, ckks.add(params, y, rW), ckks.add(params, r1, rW1))
+    s = ckks.mul_const(params, s, 0.25, float(params.q[s.level]))
+    return ckks.rescale(params, s)
+
+
+def enc_fc_rotsum(params, evk, x_cts, w_cts, n_out, span_log2):
+    """z_r = rotate-and-sum over 2^span_log2 slots of rs(rl(sum_c x_c (x) w[r C + c]));
+    the class score lands in slot 0."""
+    C = len(x_cts)
+    lv = x_cts[0].level
+    out = []
+    for r in range(n_out):
+        ws = [ckks.drop_to_level(params, w_cts[r * C + c], lv) for c in range(C)]
+        z = ckks.rescale(params, ckks.relin(params, evk, ckks.tensor_sum(params, x_cts, ws)))
+        for k in range(span_log2):
+            z = ckks.add(params, z, ckks.rotate(params, evk, z, 1 << k))
+        out.append(z)
+    return out

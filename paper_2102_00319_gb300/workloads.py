@@ -99,3 +99,40 @@ def uneven_instances(count=64):
 
 
 SINGLE_CONV_STEPS = [p * 8 + q for p in range(3) for q in range(3)]
+
+
+# Deep single-ciphertext CNN at N = 2^16, L = 20: a 28x28 image per
+# ciphertext, conv 3x3 with 16 channels by hoisted rotations, a degree-7
+# ReLU approximation, 2x2 mean pool by rotations, FC 13*13*16 -> 10 by
+# encrypted weight vectors and rotate-and-sum.
+DEEP_CNN = dict(H=28, W=28, cout=16, k=3, n_out=10)
+
+
+def relu_cheb7(bound=2.0 ** 0.5):
+    """Monomial coefficients c_0..c_7 of the degree-7 interpolant of ReLU at
+    the 8 Chebyshev nodes of [-bound, bound] (the model's activation)."""
+    k = np.arange(8)
+    nodes = bound * np.cos((2 * k + 1) * np.pi / 16)
+    V = np.vander(nodes, 8, increasing=True)
+    return np.linalg.solve(V, np.maximum(nodes, 0.0))
+
+
+def deep_conv_steps(W=28, k=3):
+    return [p * W + q for p in range(k) for q in range(k)]
+
+
+def deep_rot_steps(W=28, span_log2=10):
+    steps = set(deep_conv_steps(W)) | {1, W, W + 1} | {1 << j for j in range(span_log2)}
+    steps.discard(0)
+    return sorted(steps)
+
+
+def deep_fc_vectors(fc_w, C, Hp, Wp, W, slots):
+    """Weight vectors V[r][c]: slot (2i W + 2j) holds fc_w[r, (i Wp + j) C + c]."""
+    n_out = fc_w.shape[0]
+    V = np.zeros((n_out, C, slots))
+    for i in range(Hp):
+        for j in range(Wp):
+            for c in range(C):
+                V[:, c, 2 * i * W + 2 * j] = fc_w[:, (i * Wp + j) * C + c]
+    return V
