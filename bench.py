@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--cnn-steps", type=int, default=3)
     ap.add_argument("--no-uneven", action="store_true", help="skip the uneven multi-instance leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop leg")
+    ap.add_argument("--no-deep", action="store_true", help="skip the deep single-ciphertext CNN leg")
     ap.add_argument("--serve-requests", type=int, default=60, help="requests per arrival rate")
     ap.add_argument("--summarize-ncu", metavar="CSV",
                     help="summarise an ncu launch list (gpu__time_duration.sum) of the timed step and exit")
@@ -518,6 +519,52 @@ def serving_leg(args, H, W, np, torch, local):
     return out
 
 
+def deep_leg(H, W, np, torch, local):
+    """Latency of one 28x28 image through the deep single-ciphertext CNN at
+    N = 2^16, L = 20: conv 3x3 x16 by hoisted rotations, degree-7 ReLU
+    interpolant, 2x2 mean pool by rotations, FC 2704 -> 10 by rotate-and-sum."""
+    from oracle import cnn as ref_cnn  # FP64 plaintext network only (correctness guard)
+
+    ps, d = W.DEEP_N16, W.DEEP_CNN
+    params = H.hc_params_create(ps.log_n, list(ps.q_bits), list(ps.p_bits), ps.log2_scale)
+    stream = torch.cuda.current_stream()
+    ctx = H.hc_ctx_create(params, local, stream.cuda_stream)
+    sk, pk, evk = H.hc_keygen(ctx, W.MASTER_SEED + 4, W.deep_rot_steps(28, 10))
+    scale = 2.0 ** ps.log2_scale
+    C, n_out, K = d["cout"], d["n_out"], ctx.n // 2
+    img = W.images(60, 1, 28, 28)[0]
+    cw = W.conv_weights(61, C, 3, 3)[:, :, :, 0]
+    fw = W.fc_weights(62, n_out, 13 * 13 * C)
+    act = list(W.relu_cheb7())
+    z = np.zeros(K)
+    z[:784] = img.reshape(-1)
+    x = H.hc_encrypt(ctx, pk, H.hc_encode(ctx, z, scale, ctx.L), 3, 0)
+    wc = [H.hc_encrypt(ctx, pk, H.hc_encode(ctx, np.full(K, cw[co, t // 3, t % 3]), scale, ctx.L), 3, 10 + co * 9 + t)
+          for co in range(C) for t in range(9)]
+    V = W.deep_fc_vectors(fw, C, 13, 13, 28, K)
+    vc = [H.hc_encrypt(ctx, pk, H.hc_encode(ctx, V[r, c], scale, ctx.L), 3, 1000 + r * C + c)
+          for r in range(n_out) for c in range(C)]
+
+    def infer():
+        y = H.hc_enc_conv2d(ctx, evk, H.HC_PACK_SINGLE_HOISTED, [x], 28, 28, 1, wc, C, 3, 3, 1)
+        a = H.hc_enc_poly_act(ctx, evk, y, act)
+        pl = H.hc_enc_pool(ctx, evk, H.HC_PACK_SINGLE, a, C, 26, 28)
+        return H.hc_enc_fc_rotsum(ctx, evk, pl, vc, n_out, 10)
+
+    out = infer()
+    H.hc_sync(ctx)
+    t0 = time.perf_counter()
+    for _ in range(3):
+        out = infer()
+    H.hc_sync(ctx)
+    t = (time.perf_counter() - t0) / 3
+    got = np.array([H.hc_decode(ctx, H.hc_decrypt(ctx, sk, c))[0].real for c in out])
+    err = float(np.max(np.abs(got - ref_cnn.deep_network(img, cw, act, fw))))
+    assert err < 2.0 ** -15, err
+    return {"workload": "deep_n16_l20: 28x28 image per ciphertext, conv 3x3 x16 (hoisted), degree-7 ReLU, pool, fc 10",
+            "latency_ms": 1000 * t, "images_per_s": 1.0 / t, "max_logit_error_vs_fp64": err}
+
+
 def run_gpu(args, rank, world, local):
     import numpy as np
     import torch
@@ -656,6 +703,8 @@ def run_gpu(args, rank, world, local):
         line["uneven"] = uneven_leg(H, W, np, torch, local)
     if not args.no_serve:
         line["serving"] = serving_leg(args, H, W, np, torch, local)
+    if not args.no_deep:
+        line["deep"] = deep_leg(H, W, np, torch, local)
     if world == 1 and not args.no_cpu_baseline:
         ob = OracleBench()
         dt = ob.run(args.cpu_ops)

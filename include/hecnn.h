@@ -267,9 +267,10 @@ void hc_graph_destroy(hc_graph *g);
 
 /* ---------------------------------------------------------- CNN layers */
 typedef enum hc_packing {
-  HC_PACK_BATCH = 0,  /* Fig. 2: one ciphertext per pixel / weight, slot k = image k */
-  HC_PACK_SINGLE = 1  /* whole image row-major in one ciphertext (Sec. "Parallelization",
-                         single-image latency) */
+  HC_PACK_BATCH = 0,          /* Fig. 2: one ciphertext per pixel / weight, slot k = image k */
+  HC_PACK_SINGLE = 1,         /* whole image row-major in one ciphertext (Sec. "Parallelization",
+                                 single-image latency) */
+  HC_PACK_SINGLE_HOISTED = 2  /* as HC_PACK_SINGLE, the rotations share one ModUp (conv only) */
 } hc_packing;
 
 /*
@@ -283,6 +284,8 @@ typedef enum hc_packing {
  * HC_PACK_SINGLE: cin = 1, stride = 1, x[0] holds the image row-major with
  *   width W; y[co] = sum_{p,q} rot(x, p*W + q) (x) w[(co*kh + p)*kw + q]
  *   (needs Galois keys for every p*W + q); output (m,n) in slot m*W + n.
+ * HC_PACK_SINGLE_HOISTED: the same with hoisted rotations (one ModUp of x
+ *   for all kh*kw steps); decrypts alike, not bit-identical to SINGLE.
  * Inputs at one level >= 1 with one scale per operand kind; weights at a
  * higher level are dropped to the inputs' level.
  */
@@ -309,7 +312,13 @@ int hc_enc_conv2d_single_batch(hc_ctx *ctx, const hc_evk *evk, const hc_ct *cons
  * n ciphertexts.  x^2 uses one level: rescale(relin(u (x) u)).  The general
  * form uses two: t = rescale(relin(u (x) u)); t = rescale(t * c2 @ q_{l-1});
  * v = rescale(u * c1 @ s_t q_l / s_u) dropped to t's level; out = t + v + c0.
- * degree must be 2.
+ * degree 7 (coeffs c_0..c_7, e.g. a ReLU interpolant) uses four levels, a
+ * Paterson-Stockmeyer split with baby steps u, u^2, u^3 and giant step u^4:
+ * u2 = rs(rl(u u)); u4 = rs(rl(u2 u2)); u3 = rs(rl(u2 u));
+ * deg3(a) = a0 + a1 u + a2 u2 + a3 u3 at level l-3 with the scale of
+ * rs(u3 * a3 @ q_{l-2}) (the u and u2 terms brought to it by their
+ * constant's scale); out = rs(rl(deg3(c4..c7) u4)) + rs(deg3(c0..c3) * 1 @ s)
+ * with s chosen to match scales.  degree must be 2 or 7.
  */
 int hc_enc_poly_act(hc_ctx *ctx, const hc_evk *evk, const hc_ct *const *x, int n,
                     const double *coeffs, int degree, hc_ct **y);
@@ -317,7 +326,9 @@ int hc_enc_poly_act(hc_ctx *ctx, const hc_evk *evk, const hc_ct *const *x, int n
  * Mean pooling over non-overlapping 2x2 blocks (Eq. 5-6 with the activation
  * applied first): ((a + b) + (c + d)) * 1/4 @ q_l, rescale (one level).
  * HC_PACK_BATCH: x[(h*W + w)*C + c] -> y[(i*(W/2) + j)*C + c].
- * (Single-ciphertext pooling is not provided.)
+ * HC_PACK_SINGLE: x[c] holds channel c row-major with width W (H unused):
+ *   y[c] = ((x + rot(x, W)) + (rot(x, 1) + rot(x, W+1))) * 1/4 @ q_l, rescaled,
+ *   the three rotations hoisted; pooled (i, j) lands in slot 2i W + 2j.
  */
 int hc_enc_pool(hc_ctx *ctx, const hc_evk *evk, hc_packing packing, const hc_ct *const *x, int C,
                 int H, int W, hc_ct **y);
@@ -329,6 +340,18 @@ int hc_enc_pool(hc_ctx *ctx, const hc_evk *evk, hc_packing packing, const hc_ct 
  */
 int hc_enc_fc(hc_ctx *ctx, const hc_evk *evk, hc_packing packing, const hc_ct *const *x, int n_in,
               const hc_ct *const *w, const hc_ct *const *bias, int n_out, hc_ct **y);
+
+/*
+ * Fully connected layer on single-ciphertext activations: x[c] (c < C)
+ * hold the features of channel c at arbitrary slots; w[r*C + c] holds, in
+ * the same slots, the weights of class r for channel c (the model owner
+ * encrypts these vectors).  z_r = rs(rl(sum_c x_c (x) w[r*C+c])), then
+ * z_r += rot(z_r, 2^k) for k < span_log2: slot 0 of y[r] holds the class
+ * score when the features lie in slots below 2^span_log2.  Needs Galois
+ * keys for the powers of two; weights above x's level are dropped to it.
+ */
+int hc_enc_fc_rotsum(hc_ctx *ctx, const hc_evk *evk, const hc_ct *const *x, int C, const hc_ct *const *w,
+                     int n_out, int span_log2, hc_ct **y);
 
 #ifdef __cplusplus
 }

@@ -1394,13 +1394,14 @@ extern "C" int hc_enc_conv2d(hc_ctx* ctx, const hc_evk* evk, hc_packing packing,
       free_all(wviews);
       for (size_t i = 0; i < r.size(); ++i) y[i] = r[i];
     } else {
+      HC_CHECK(packing == HC_PACK_SINGLE || packing == HC_PACK_SINGLE_HOISTED, HC_ERR_INVALID, "unknown packing");
       HC_CHECK(cin == 1 && stride == 1, HC_ERR_INVALID, "single packing supports cin = 1, stride 1");
       const hc_ct* x0 = x[0];
       check_ct(ctx, x0);
       std::vector<int> steps;
       for (int p = 0; p < kh; ++p)
         for (int q = 0; q < kw; ++q) steps.push_back(p * W + q);
-      std::vector<hc_ct*> rots = rotate_one(ctx, evk, x0, steps, false);
+      std::vector<hc_ct*> rots = rotate_one(ctx, evk, x0, steps, packing == HC_PACK_SINGLE_HOISTED);
       std::vector<const hc_ct*> xs(rots.begin(), rots.end()), ws(w, w + cout * kh * kw);
       std::vector<hc_ct*> wviews;
       for (auto*& c : ws) {
@@ -1429,11 +1430,112 @@ extern "C" int hc_enc_conv2d(hc_ctx* ctx, const hc_evk* evk, hc_packing packing,
   });
 }
 
+namespace {
+std::vector<hc_ct*> views_at(hc_ctx* ctx, const std::vector<const hc_ct*>& xs, int level) {
+  std::vector<hc_ct*> v;
+  for (auto* c : xs) v.push_back(new hc_ct{ctx, c->buf, c->data, c->stride, level, c->degree, c->scale});
+  return v;
+}
+
+std::vector<const hc_ct*> to_const(const std::vector<hc_ct*>& v) { return std::vector<const hc_ct*>(v.begin(), v.end()); }
+
+// rs(rl(a (x) b)) elementwise over two equal-length lists at one level
+std::vector<hc_ct*> mul_rr(hc_ctx* ctx, const hc_evk* evk, const std::vector<const hc_ct*>& a,
+                           const std::vector<const hc_ct*>& b) {
+  const int n = (int)a.size();
+  std::vector<int> ai(n), bi(n), off(n + 1);
+  std::iota(ai.begin(), ai.end(), 0);
+  std::iota(bi.begin(), bi.end(), 0);
+  std::iota(off.begin(), off.end(), 0);
+  std::vector<hc_ct*> d = tensor_acc(ctx, a, b, ai, bi, off, a[0]->level, a[0]->scale * b[0]->scale);
+  for (int i = 0; i < n; ++i) d[i]->scale = a[i]->scale * b[i]->scale;
+  std::vector<hc_ct*> r = relin_rescale(ctx, evk, d, nullptr);
+  for (int i = 0; i < n; ++i) r[i]->scale = d[i]->scale / (double)ctx->P.chain[a[0]->level];
+  free_all(d);
+  return r;
+}
+
+// rescale(x * c @ cs) with cs chosen per element by cs_of(i)
+std::vector<hc_ct*> mulc_rs(hc_ctx* ctx, const std::vector<const hc_ct*>& x, double c, double cs) {
+  std::vector<hc_ct*> m = mul_const_cts(ctx, x, c, cs);
+  const double q = (double)ctx->P.chain[x[0]->level];
+  std::vector<hc_ct*> out = new_cts(ctx, (int)x.size(), x[0]->level - 1, x[0]->degree, m[0]->scale / q);
+  rescale_cts(ctx, to_const(m), out);
+  for (size_t i = 0; i < out.size(); ++i) out[i]->scale = m[i]->scale / q;
+  free_all(m);
+  return out;
+}
+
+// a += b elementwise (scales must agree; a keeps its scale)
+void add_into(hc_ctx* ctx, const std::vector<hc_ct*>& a, const std::vector<const hc_ct*>& b, int level) {
+  std::vector<BufPtr> keep;
+  std::vector<CtRef> ar, br;
+  for (size_t i = 0; i < a.size(); ++i) {
+    check_scales(a[i]->scale, b[i]->scale);
+    ar.push_back(a[i]->ref());
+    br.push_back(b[i]->ref());
+  }
+  const CtRef* ad = refs_dev(ctx, ar, keep);
+  launch_ew(ctx, 0, ad, ad, refs_dev(ctx, br, keep), (int)a.size(), 2, level + 1);
+}
+
+// Degree-7 activation (Paterson-Stockmeyer split, four levels), batched.
+std::vector<hc_ct*> poly7(hc_ctx* ctx, const hc_evk* evk, const std::vector<const hc_ct*>& u, const double* c) {
+  const int lv = u[0]->level;
+  HC_CHECK(lv >= 4, HC_ERR_DEPTH, "the degree-7 activation needs four levels");
+  const double q2 = (double)ctx->P.chain[lv - 2], q3 = (double)ctx->P.chain[lv - 3];
+  std::vector<hc_ct*> u2 = mul_rr(ctx, evk, u, u);                                   // lv-1
+  std::vector<hc_ct*> u4 = mul_rr(ctx, evk, to_const(u2), to_const(u2));             // lv-2
+  std::vector<hc_ct*> ud1 = views_at(ctx, u, lv - 1);
+  std::vector<hc_ct*> u3 = mul_rr(ctx, evk, to_const(u2), to_const(ud1));            // lv-2
+  std::vector<hc_ct*> u2d = views_at(ctx, to_const(u2), lv - 2);
+  std::vector<hc_ct*> ud2 = views_at(ctx, u, lv - 2);
+  auto deg3 = [&](double a0, double a1, double a2, double a3) {
+    std::vector<hc_ct*> t3 = mulc_rs(ctx, to_const(u3), a3, q2);                      // lv-3
+    const double s3 = t3[0]->scale;
+    std::vector<hc_ct*> t2 = mulc_rs(ctx, to_const(u2d), a2, s3 * q2 / u2d[0]->scale);
+    std::vector<hc_ct*> t1 = mulc_rs(ctx, to_const(ud2), a1, s3 * q2 / ud2[0]->scale);
+    add_into(ctx, t3, to_const(t2), lv - 3);
+    add_into(ctx, t3, to_const(t1), lv - 3);
+    std::vector<u64> sc;
+    constant_residues(ctx, lv - 3, a0 * s3, false, sc);
+    std::vector<BufPtr> keep;
+    std::vector<CtRef> tr;
+    for (auto* t : t3) tr.push_back(t->ref());
+    const CtRef* td = refs_dev(ctx, tr, keep);
+    launch_scalar(ctx, true, td, td, (int)t3.size(), 2, lv - 2, upload(ctx, sc, keep));
+    free_all(t2);
+    free_all(t1);
+    return t3;
+  };
+  std::vector<hc_ct*> qa = deg3(c[0], c[1], c[2], c[3]);
+  std::vector<hc_ct*> qb = deg3(c[4], c[5], c[6], c[7]);
+  std::vector<hc_ct*> u4d = views_at(ctx, to_const(u4), lv - 3);
+  std::vector<hc_ct*> prod = mul_rr(ctx, evk, to_const(qb), to_const(u4d));         // lv-4
+  std::vector<hc_ct*> qa2 = mulc_rs(ctx, to_const(qa), 1.0, prod[0]->scale * q3 / qa[0]->scale);
+  add_into(ctx, prod, to_const(qa2), lv - 4);
+  for (auto* v : {&u2, &u4, &ud1, &u3, &u2d, &ud2, &qa, &qb, &u4d, &qa2}) free_all(*v);
+  return prod;
+}
+}  // namespace
+
 extern "C" int hc_enc_poly_act(hc_ctx* ctx, const hc_evk* evk, const hc_ct* const* x, int n, const double* coeffs,
                                int degree, hc_ct** y) {
   if (!ctx) return HC_ERR_INVALID;
   return guard(ctx, [&] {
-    HC_CHECK(evk && coeffs && degree == 2 && n >= 0 && (n == 0 || (x && y)), HC_ERR_INVALID, "bad arguments");
+    HC_CHECK(evk && coeffs && (degree == 2 || degree == 7) && n >= 0 && (n == 0 || (x && y)), HC_ERR_INVALID,
+             "bad arguments");
+    if (degree == 7 && n > 0) {
+      std::vector<const hc_ct*> xs(x, x + n);
+      for (auto* c : xs) {
+        check_ct(ctx, c);
+        HC_CHECK(c->level == xs[0]->level && c->degree == 1, HC_ERR_LEVEL_MISMATCH, "inputs at different levels");
+        check_scales(c->scale, xs[0]->scale);
+      }
+      std::vector<hc_ct*> r = poly7(ctx, evk, xs, coeffs);
+      for (int i = 0; i < n; ++i) y[i] = r[i];
+      return;
+    }
     if (n == 0) return;
     std::vector<const hc_ct*> xs(x, x + n);
     const int level = xs[0]->level;
@@ -1501,9 +1603,33 @@ extern "C" int hc_enc_pool(hc_ctx* ctx, const hc_evk* evk, hc_packing packing, c
                            int W, hc_ct** y) {
   if (!ctx) return HC_ERR_INVALID;
   return guard(ctx, [&] {
-    (void)evk;
-    HC_CHECK(packing == HC_PACK_BATCH, HC_ERR_INVALID, "pooling supports batch packing");
     HC_CHECK(x && y && C > 0 && H >= 2 && W >= 2, HC_ERR_INVALID, "bad arguments");
+    if (packing == HC_PACK_SINGLE) {
+      HC_CHECK(evk, HC_ERR_INVALID, "single-ciphertext pooling needs Galois keys");
+      for (int c = 0; c < C; ++c) {
+        check_ct(ctx, x[c]);
+        HC_CHECK(x[c]->degree == 1 && x[c]->level >= 1, HC_ERR_DEPTH, "pooling needs a level");
+        std::vector<hc_ct*> r = rotate_one(ctx, evk, x[c], {W, 1, W + 1}, true);
+        hc_ct* s0 = new_ct(ctx, x[c]->level, 1, x[c]->scale);
+        hc_ct* s1 = new_ct(ctx, x[c]->level, 1, r[1]->scale);
+        {
+          std::vector<BufPtr> keep;
+          const CtRef *d0 = refs_dev(ctx, {s0->ref()}, keep), *d1 = refs_dev(ctx, {s1->ref()}, keep);
+          launch_ew(ctx, 0, d0, refs_dev(ctx, {x[c]->ref()}, keep), refs_dev(ctx, {r[0]->ref()}, keep), 1, 2,
+                    x[c]->level + 1);
+          launch_ew(ctx, 0, d1, refs_dev(ctx, {r[1]->ref()}, keep), refs_dev(ctx, {r[2]->ref()}, keep), 1, 2,
+                    x[c]->level + 1);
+          launch_ew(ctx, 0, d0, d0, d1, 1, 2, x[c]->level + 1);
+        }
+        std::vector<hc_ct*> o = mulc_rs(ctx, {s0}, 0.25, (double)ctx->P.chain[x[c]->level]);
+        y[c] = o[0];
+        delete s0;
+        delete s1;
+        free_all(r);
+      }
+      return;
+    }
+    HC_CHECK(packing == HC_PACK_BATCH, HC_ERR_INVALID, "unknown packing");
     const int Ho = H / 2, Wo = W / 2, nin = H * W * C, nout = Ho * Wo * C;
     std::vector<const hc_ct*> xs(x, x + nin);
     const int level = xs[0]->level;
@@ -1760,5 +1886,57 @@ extern "C" int hc_enc_conv2d_single_batch(hc_ctx* ctx, const hc_evk* evk, const 
       free_all(rot);
       free_all(wv);
     }
+  });
+}
+
+// =====================================================================
+// FC by rotate-and-sum (single-ciphertext activations)
+// =====================================================================
+extern "C" int hc_enc_fc_rotsum(hc_ctx* ctx, const hc_evk* evk, const hc_ct* const* x, int C, const hc_ct* const* w,
+                                int n_out, int span_log2, hc_ct** y) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    HC_CHECK(evk && x && w && y && C > 0 && n_out > 0 && span_log2 >= 0 && span_log2 < ctx->P.log_n, HC_ERR_INVALID,
+             "bad arguments");
+    std::vector<const hc_ct*> xs(x, x + C);
+    const int level = xs[0]->level;
+    for (auto* c : xs) {
+      check_ct(ctx, c);
+      HC_CHECK(c->level == level && c->degree == 1, HC_ERR_LEVEL_MISMATCH, "inputs at different levels");
+      check_scales(c->scale, xs[0]->scale);
+    }
+    HC_CHECK(level >= 1, HC_ERR_DEPTH, "no level left");
+    std::vector<hc_ct*> views;
+    std::vector<const hc_ct*> ws;
+    for (int i = 0; i < C * n_out; ++i) {
+      check_ct(ctx, w[i]);
+      HC_CHECK(w[i]->level >= level && w[i]->degree == 1, HC_ERR_LEVEL_MISMATCH, "weight below the activations");
+      views.push_back(new hc_ct{ctx, w[i]->buf, w[i]->data, w[i]->stride, level, 1, w[i]->scale});
+      ws.push_back(views.back());
+    }
+    std::vector<int> xi, wi, off{0};
+    for (int r = 0; r < n_out; ++r) {
+      for (int c = 0; c < C; ++c) {
+        xi.push_back(c);
+        wi.push_back(r * C + c);
+      }
+      off.push_back((int)xi.size());
+    }
+    std::vector<hc_ct*> d = tensor_acc(ctx, xs, ws, xi, wi, off, level, xs[0]->scale * ws[0]->scale);
+    std::vector<hc_ct*> z = relin_rescale(ctx, evk, d, nullptr);
+    free_all(d);
+    free_all(views);
+    const int nq = level;  // limbs after the rescale = level
+    for (int k = 0; k < span_log2; ++k) {
+      for (int r = 0; r < n_out; ++r) {
+        std::vector<hc_ct*> rot = rotate_one(ctx, evk, z[r], {1 << k}, false);
+        std::vector<BufPtr> keep;
+        check_scales(z[r]->scale, rot[0]->scale);
+        const CtRef* zd = refs_dev(ctx, {z[r]->ref()}, keep);
+        launch_ew(ctx, 0, zd, zd, refs_dev(ctx, {rot[0]->ref()}, keep), 1, 2, nq);
+        free_all(rot);
+      }
+    }
+    for (int r = 0; r < n_out; ++r) y[r] = z[r];
   });
 }

@@ -25,6 +25,7 @@ ERRORS = {
 }
 HC_PACK_BATCH = 0
 HC_PACK_SINGLE = 1
+HC_PACK_SINGLE_HOISTED = 2
 
 # every symbol declared in include/hecnn.h
 EXPORTS = [
@@ -38,7 +39,7 @@ EXPORTS = [
     "hc_relin", "hc_rescale", "hc_drop_to_level", "hc_rotate", "hc_rotate_hoisted",
     "hc_mul_relin_rescale_batch", "hc_enc_conv2d", "hc_enc_poly_act", "hc_enc_pool", "hc_enc_fc",
     "hc_relin_noalloc", "hc_graph_begin", "hc_graph_end", "hc_graph_launch", "hc_graph_destroy",
-    "hc_enc_conv2d_single_batch",
+    "hc_enc_conv2d_single_batch", "hc_enc_fc_rotsum",
 ]
 
 
@@ -130,6 +131,7 @@ def load(path: str = LIB_PATH):
         "hc_graph_launch": (c_int, [vp]),
         "hc_graph_destroy": (None, [vp]),
         "hc_enc_conv2d_single_batch": (c_int, [vp, vp, pp, c_int, c_int, pp, c_int, c_int, c_int, pp]),
+        "hc_enc_fc_rotsum": (c_int, [vp, vp, pp, c_int, pp, c_int, c_int, pp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -528,18 +530,27 @@ def hc_enc_conv2d_single_batch(ctx, evk, x, W, w, cout, kh, kw):
 
 
 def hc_enc_poly_act(ctx, evk, x, coeffs):
-    c = (ctypes.c_double * 3)(*coeffs)
+    """coeffs: 3 values (degree 2) or 8 values (degree 7)."""
+    deg = len(coeffs) - 1
+    c = (ctypes.c_double * len(coeffs))(*coeffs)
     outs = _outs(len(x))
-    _check(ctx, load().hc_enc_poly_act(ctx.ptr, evk.ptr, _ptr_array(x), len(x), c, 2, outs))
+    _check(ctx, load().hc_enc_poly_act(ctx.ptr, evk.ptr, _ptr_array(x), len(x), c, deg, outs))
     return _wrap_outs(ctx, outs, len(x))
 
 
 def hc_enc_pool(ctx, evk, packing, x, C, H, W):
-    nout = (H // 2) * (W // 2) * C
+    nout = C if packing == HC_PACK_SINGLE else (H // 2) * (W // 2) * C
     outs = _outs(nout)
     _check(ctx, load().hc_enc_pool(ctx.ptr, evk.ptr if evk is not None else None, packing, _ptr_array(x), C, H, W,
                                    outs))
     return _wrap_outs(ctx, outs, nout)
+
+
+def hc_enc_fc_rotsum(ctx, evk, x, w, n_out, span_log2):
+    outs = _outs(n_out)
+    _check(ctx, load().hc_enc_fc_rotsum(ctx.ptr, evk.ptr, _ptr_array(x), len(x), _ptr_array(w), n_out, span_log2,
+                                        outs))
+    return _wrap_outs(ctx, outs, n_out)
 
 
 def hc_enc_fc(ctx, evk, packing, x, w, n_out, bias=None):
