@@ -158,6 +158,32 @@ LimbSet limbset_base(u64* base, u64 item_stride, u64 poly_stride, int npoly, int
 // identity prime map [0..63] lives at the start of ext_map's buffer tail
 const int* ident_map(hc_ctx* ctx) { return ctx->ext_map + (ctx->P.L + 1) * (ctx->P.L + 1 + ctx->P.alpha); }
 
+// ModUp of a batch: for every digit j, the conversions of the digit's limbs
+// of xc (coefficient form) to the other slots of Q_l u P, in NTT form.  A
+// digit's own slots are taken from x by the specialised key product; with
+// more than eight digits they are copied into ext instead.
+void modup_digits(hc_ctx* ctx, int level, const std::vector<CtRef>& xs, const u64* xc, u64 x_is, u64* ext, u64 ext_is,
+                  int m, std::vector<BufPtr>& keep) {
+  const int n = ctx->P.n, alpha = ctx->P.alpha, nq = level + 1, next = nq + alpha, dnum = ctx->lv[level].dnum;
+  const size_t ext_words = (size_t)next * n;
+  const int* emap = ctx->ext_map_of(level);
+  for (int j = 0; j < dnum; ++j) {
+    const int d0 = j * alpha, d1 = std::min(d0 + alpha, nq);
+    if (dnum > 8) {
+      std::vector<CtRef> er(m), xsh(m);
+      for (int i = 0; i < m; ++i) {
+        er[i] = CtRef{ext + ext_is * i + (size_t)j * ext_words + (size_t)d0 * n, 0};
+        xsh[i] = CtRef{xs[i].p + (size_t)d0 * n, 0};
+      }
+      launch_ew(ctx, 3, refs_dev(ctx, er, keep), refs_dev(ctx, xsh, keep), nullptr, m, 1, d1 - d0);
+    }
+    launch_modup_bconv_fast(ctx, level, j, xc, x_is, ext + (size_t)j * ext_words, ext_is, m);
+    u64* ej = ext + (size_t)j * ext_words;
+    if (d0 > 0) launch_ntt(ctx, limbset_base(ej, ext_is, 0, 1, d0, 0, emap), m, false);
+    launch_ntt(ctx, limbset_base(ej, ext_is, 0, 1, next - d1, d1, emap), m, false);
+  }
+}
+
 // ---------------------------------------------------------------------
 // Key switching of a batch of single polynomials x (NTT form, level l):
 //   out_k = base_k + KS(x)_k,  k = 0, 1 (base_k may be null).
@@ -192,27 +218,14 @@ void keyswitch_batch(hc_ctx* ctx, const u64* key, int level, const std::vector<C
     u64* zq = acc + (size_t)m * 2 * ext_words;            // [m][2][nq][N]
     const u64 x_is = (u64)nq * n, ext_is = (u64)dnum * ext_words, acc_is = 2 * (u64)ext_words,
               z_is = 2 * (u64)nq * n;
-    // x -> coefficient form
-    std::vector<CtRef> xcr(m);
-    for (int i = 0; i < m; ++i) xcr[i] = CtRef{xc + x_is * i, 0};
-    const CtRef* xcr_d = refs_dev(ctx, xcr, keep);
-    launch_ew(ctx, 3, xcr_d, xr, nullptr, m, 1, nq);
-    launch_ntt(ctx, limbset_base(xc, x_is, 0, 1, nq, 0, nullptr), m, true);
-    // ModUp per digit
-    for (int j = 0; j < dnum; ++j) {
-      const int d0 = j * alpha, d1 = std::min(d0 + alpha, nq);
-      // digit limbs: NTT-form copy of x
-      std::vector<CtRef> er(m);
-      for (int i = 0; i < m; ++i) er[i] = CtRef{ext + ext_is * i + (size_t)j * ext_words + (size_t)d0 * n, 0};
-      std::vector<CtRef> xsh(m);
-      for (int i = 0; i < m; ++i) xsh[i] = CtRef{xs[i].p + (size_t)d0 * n, 0};
-      launch_ew(ctx, 3, refs_dev(ctx, er, keep), refs_dev(ctx, xsh, keep), nullptr, m, 1, d1 - d0);
-      launch_modup_bconv_fast(ctx, level, j, xc, x_is, ext + (size_t)j * ext_words, ext_is, m);
-      u64* ej = ext + (size_t)j * ext_words;
-      if (d0 > 0) launch_ntt(ctx, limbset_base(ej, ext_is, 0, 1, d0, 0, emap), m, false);
-      launch_ntt(ctx, limbset_base(ej, ext_is, 0, 1, next - d1, d1, emap), m, false);
-    }
-    launch_key_product_batched(ctx, level, ext, ext_is, key, acc, acc_is, m);
+    // x -> coefficient form, read in place by the first inverse pass
+    LimbSet xin{};
+    xin.refs = xr;
+    xin.npoly = 1;
+    xin.nlimb = nq;
+    launch_ntt_from(ctx, limbset_base(xc, x_is, 0, 1, nq, 0, nullptr), &xin, m, true);
+    modup_digits(ctx, level, xs, xc, x_is, ext, ext_is, m, keep);
+    launch_key_product_batched(ctx, level, ext, ext_is, key, acc, acc_is, m, dnum <= 8 ? xr : nullptr);
     // ModDown
     launch_ntt(ctx, limbset_base(acc, acc_is, ext_words, 2, alpha, nq, emap), m, true);
     launch_moddown_bconv_fast(ctx, level, acc + (size_t)nq * n, acc_is, zq, z_is, m);
@@ -260,24 +273,16 @@ void keyswitch_rescale_batch(hc_ctx* ctx, const u64* key, int level, const std::
     u64* tl = zq + (size_t)m * 2 * nq * n;          // [m][2][N]
     const u64 x_is = (u64)nq * n, ext_is = (u64)dnum * ext_words, acc_is = 2 * (u64)ext_words,
               z_is = 2 * (u64)nq * n;
-    std::vector<CtRef> xcr(m);
-    for (int i = 0; i < m; ++i) xcr[i] = CtRef{xc + x_is * i, 0};
-    launch_ew(ctx, 3, refs_dev(ctx, xcr, keep), xr, nullptr, m, 1, nq);
-    launch_ntt(ctx, limbset_base(xc, x_is, 0, 1, nq, 0, nullptr), m, true);
-    for (int j = 0; j < dnum; ++j) {
-      const int d0 = j * alpha, d1 = std::min(d0 + alpha, nq);
-      std::vector<CtRef> er(m), xsh(m);
-      for (int i = 0; i < m; ++i) {
-        er[i] = CtRef{ext + ext_is * i + (size_t)j * ext_words + (size_t)d0 * n, 0};
-        xsh[i] = CtRef{xs[i].p + (size_t)d0 * n, 0};
-      }
-      launch_ew(ctx, 3, refs_dev(ctx, er, keep), refs_dev(ctx, xsh, keep), nullptr, m, 1, d1 - d0);
-      launch_modup_bconv_fast(ctx, level, j, xc, x_is, ext + (size_t)j * ext_words, ext_is, m);
-      u64* ej = ext + (size_t)j * ext_words;
-      if (d0 > 0) launch_ntt(ctx, limbset_base(ej, ext_is, 0, 1, d0, 0, emap), m, false);
-      launch_ntt(ctx, limbset_base(ej, ext_is, 0, 1, next - d1, d1, emap), m, false);
-    }
-    launch_key_product_batched(ctx, level, ext, ext_is, key, acc, acc_is, m);
+    // x -> coefficient form, read in place by the first inverse pass
+    LimbSet xin{};
+    xin.refs = xr;
+    xin.npoly = 1;
+    xin.nlimb = nq;
+    const LimbSet xcs = limbset_base(xc, x_is, 0, 1, nq, 0, nullptr);
+    launch_ntt_from(ctx, xcs, &xin, m, true);
+    modup_digits(ctx, level, xs, xc, x_is, ext, ext_is, m, keep);
+    // the digits' own slots are read from x itself (specialised key product)
+    launch_key_product_batched(ctx, level, ext, ext_is, key, acc, acc_is, m, dnum <= 8 ? xr : nullptr);
     launch_ntt(ctx, limbset_base(acc, acc_is, ext_words, 2, alpha, nq, emap), m, true);
     launch_moddown_bconv_fast(ctx, level, acc + (size_t)nq * n, acc_is, zq, z_is, m);
     launch_ksr_last(ctx, level, acc, acc_is, b0, b1, tl, m);

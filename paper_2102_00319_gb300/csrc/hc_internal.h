@@ -186,6 +186,9 @@ T* upload(hc_ctx* ctx, const std::vector<T>& v, std::vector<BufPtr>& keep) {
 // --------------------------------------------------------------- launchers
 // NTT (forward) / inverse NTT of every limb of a LimbSet, `items` items.
 void launch_ntt(hc_ctx* ctx, const LimbSet& s, int items, bool inverse);
+// Out-of-place: the first pass reads limb (item, poly, limb) from `in`
+// (same poly/limb counts as s), the result lands in s.
+void launch_ntt_from(hc_ctx* ctx, const LimbSet& s, const LimbSet* in, int items, bool inverse);
 
 // Samplers writing coefficient-form limbs dst + r*N for chain indices ids[r].
 void launch_sample_ternary(hc_ctx* ctx, u64 seed, u64 tag, u64* dst, const int* ids, int nl);
@@ -240,7 +243,7 @@ void launch_modup_bconv_fast(hc_ctx* ctx, int level, int j, const u64* xcoef, u6
 void launch_moddown_bconv_fast(hc_ctx* ctx, int level, const u64* accp_coef, u64 accp_item_stride, u64* z,
                                u64 z_item_stride, int items);
 void launch_key_product_batched(hc_ctx* ctx, int level, const u64* ext, u64 ext_item_stride, const u64* key,
-                                u64* acc, u64 acc_item_stride, int items);
+                                u64* acc, u64 acc_item_stride, int items, const CtRef* digit_src = nullptr);
 // Fused relinearise + rescale tail (see hc_kernels.cu).
 void launch_ksr_last(hc_ctx* ctx, int level, const u64* acc, u64 acc_item_stride, const CtRef* base0,
                      const CtRef* base1, u64* tl, int items);

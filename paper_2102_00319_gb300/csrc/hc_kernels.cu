@@ -618,10 +618,13 @@ __global__ void __launch_bounds__(kT) k_moddown_bconv_t(const u64* src, u64 src_
 
 // acc[z][k][s] = sum_j ext[z][j][s] * key[j][k][emap[s]] for all items z:
 // the 2 DNUM key words of (s, c) stay in registers across the batch.
+// digit_src (optional): the digit's own slots s in [j alpha, j alpha + alpha)
+// come from digit_src[z] (NTT-form input) instead of ext.
 template <int DNUM>
 __global__ void __launch_bounds__(kT) k_key_product_t(const u64* ext, u64 ext_item_stride, const u64* key, u64* acc,
                                                        u64 acc_item_stride, int next, int nchain, const int* emap,
-                                                       int items, Tables T) {
+                                                       int items, const CtRef* digit_src, int alpha, int nq,
+                                                       Tables T) {
   const int n = 1 << T.log_n;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
@@ -634,12 +637,13 @@ __global__ void __launch_bounds__(kT) k_key_product_t(const u64* ext, u64 ext_it
     kb[j] = key[((size_t)(2 * j) * nchain + pid) * n + c];
     ka[j] = key[((size_t)(2 * j + 1) * nchain + pid) * n + c];
   }
+  const int own = (digit_src && s < nq) ? s / alpha : -1;  // the digit whose block holds slot s
   for (int z = blockIdx.z; z < items; z += gridDim.z) {
     const u64* e = ext + (size_t)z * ext_item_stride + (size_t)s * n + c;
     U128 a0{0, 0}, a1{0, 0};
 #pragma unroll
     for (int j = 0; j < DNUM; ++j) {
-      const u64 y = e[(size_t)j * next * n];
+      const u64 y = (j == own) ? digit_src[z].p[(size_t)s * n + c] : e[(size_t)j * next * n];
       mac(a0, y, kb[j]);
       mac(a1, y, ka[j]);
     }
@@ -860,7 +864,7 @@ void launch_moddown_bconv_fast(hc_ctx* ctx, int level, const u64* accp_coef, u64
 }
 
 void launch_key_product_batched(hc_ctx* ctx, int level, const u64* ext, u64 ext_item_stride, const u64* key,
-                                u64* acc, u64 acc_item_stride, int items) {
+                                u64* acc, u64 acc_item_stride, int items, const CtRef* digit_src) {
   const int next = level + 1 + ctx->P.alpha, dnum = ctx->lv[level].dnum;
   // a few item groups in z so small batches still fill the GPU
   const int zgroups = std::min(items, std::max(1, 2048 / (next * ((ctx->P.n + kT - 1) / kT))));
@@ -869,11 +873,13 @@ void launch_key_product_batched(hc_ctx* ctx, int level, const u64* ext, u64 ext_
 #define HC_KP(D)                                                                                                \
   case D:                                                                                                       \
     k_key_product_t<D><<<g, kT, 0, ctx->stream>>>(ext, ext_item_stride, key, acc, acc_item_stride, next,      \
-                                                  ctx->P.nchain(), ctx->ext_map_of(level), items, ctx->tab); \
+                                                  ctx->P.nchain(), ctx->ext_map_of(level), items, digit_src, \
+                                                  ctx->P.alpha, level + 1, ctx->tab);                          \
     break;
   switch (dnum) {
     HC_KP(1) HC_KP(2) HC_KP(3) HC_KP(4) HC_KP(5) HC_KP(6) HC_KP(7) HC_KP(8)
     default: {
+      HC_CHECK(!digit_src, HC_ERR_INVALID, "digit sources need a specialised key product");
       const dim3 g2 = grid_for(ctx, next, items);
       k_key_product<<<g2, kT, 0, ctx->stream>>>(ext, ext_item_stride, key, acc, acc_item_stride, dnum, next,
                                                 ctx->P.nchain(), ctx->ext_map_of(level), ctx->tab);

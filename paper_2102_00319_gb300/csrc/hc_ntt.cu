@@ -91,25 +91,36 @@ __device__ __forceinline__ void limb_meta(const LimbSet& s, u64*& a, int& pid) {
   pid = limb_prime(s, slot);
 }
 
+// The input limb of an out-of-place pass: same (item, poly, limb) position in `in`.
+template <int LOGN>
+__device__ __forceinline__ const u64* input_limb(const LimbSet& s, const LimbSet& in) {
+  const int y = blockIdx.y;
+  const int k = y / s.nlimb;
+  const int l = y - k * s.nlimb;
+  return limb_ptr(in, blockIdx.z, k, in.l0 + l, 1 << LOGN);
+}
+
 // Column pass: stages 0..N1-1 (forward) over R = 2^N1 rows (N1 = K1 + K2) of
 // TC = 2^TCL columns starting at blockIdx.x * TC.  Shared tile [row][col].
 template <bool INV, int LOGN, int K1, int K2, int TCL>
-__global__ void __launch_bounds__(kThreads) k_cols(LimbSet s, Tables T) {
+__global__ void __launch_bounds__(kThreads) k_cols(LimbSet s, LimbSet in, int use_in, Tables T) {
   constexpr int N1 = K1 + K2, N2 = LOGN - N1, TC = 1 << TCL;
   extern __shared__ u64 sm[];
   u64* a;
   int pid;
   limb_meta<LOGN>(s, a, pid);
+  const u64* ain = use_in ? input_limb<LOGN>(s, in) : a;  // first loads (out-of-place pass)
   const u64 q = T.mods[pid].q;
   const ulonglong2* tw = (INV ? T.inv2 : T.fwd2) + ((size_t)pid << LOGN);
   a += blockIdx.x * TC;
+  ain += blockIdx.x * TC;
   if (!INV) {
     // round 1: 2^K1 rows strided by 2^K2 -> stages 0..K1-1
     for (u32 w = threadIdx.x; w < (TC << K2); w += kThreads) {
       const u32 c = w & (TC - 1), r0 = w >> TCL;
       u64 x[1 << K1];
 #pragma unroll
-      for (int i = 0; i < (1 << K1); ++i) x[i] = a[((r0 + (i << K2)) << N2) + c];
+      for (int i = 0; i < (1 << K1); ++i) x[i] = ain[((r0 + (i << K2)) << N2) + c];
       fwd_block<K1, K2 + N2, 0, LOGN>(x, r0 << N2, tw, q);
 #pragma unroll
       for (int i = 0; i < (1 << K1); ++i) sm[((r0 + (i << K2)) << TCL) + c] = x[i];
@@ -131,7 +142,7 @@ __global__ void __launch_bounds__(kThreads) k_cols(LimbSet s, Tables T) {
       const u32 c = w & (TC - 1), g = w >> TCL;
       u64 x[1 << K2];
 #pragma unroll
-      for (int i = 0; i < (1 << K2); ++i) x[i] = a[(((g << K2) + i) << N2) + c];
+      for (int i = 0; i < (1 << K2); ++i) x[i] = ain[(((g << K2) + i) << N2) + c];
       inv_block<K2, N2, N1 - 1, LOGN>(x, (g << K2) << N2, tw, q);
 #pragma unroll
       for (int i = 0; i < (1 << K2); ++i) sm[(((g << K2) + i) << TCL) + c] = x[i];
@@ -154,17 +165,19 @@ __global__ void __launch_bounds__(kThreads) k_cols(LimbSet s, Tables T) {
 // Row pass: stages N1..LOGN-1 (forward) inside RP = 2^RPL rows of C = 2^N2
 // adjacent points (N2 = K1 + K2).  Shared rows padded by one word per 2^K2.
 template <bool INV, int LOGN, int K1, int K2, int RPL>
-__global__ void __launch_bounds__(kThreads) k_rows(LimbSet s, Tables T) {
+__global__ void __launch_bounds__(kThreads) k_rows(LimbSet s, LimbSet in, int use_in, Tables T) {
   constexpr int N2 = K1 + K2, N1 = LOGN - N2, C = 1 << N2, RP = 1 << RPL;
   constexpr int PADW = C + (C >> K2);
   extern __shared__ u64 sm[];
   u64* a;
   int pid;
   limb_meta<LOGN>(s, a, pid);
+  const u64* ain = use_in ? input_limb<LOGN>(s, in) : a;  // first loads (out-of-place pass)
   const u64 q = T.mods[pid].q;
   const ulonglong2* tw = (INV ? T.inv2 : T.fwd2) + ((size_t)pid << LOGN);
   const u32 row0 = blockIdx.x * RP;
   u64* src = a + ((size_t)row0 << N2);
+  const u64* srcin = ain + ((size_t)row0 << N2);
   auto sidx = [](u32 r, u32 j) { return r * PADW + j + (j >> K2); };
   if (!INV) {
     // round 1: 2^K1 points strided by 2^K2 (straight from global)
@@ -172,7 +185,7 @@ __global__ void __launch_bounds__(kThreads) k_rows(LimbSet s, Tables T) {
       const u32 r = w >> K2, r0 = w & ((1 << K2) - 1);
       u64 x[1 << K1];
 #pragma unroll
-      for (int i = 0; i < (1 << K1); ++i) x[i] = src[(r << N2) + r0 + (i << K2)];
+      for (int i = 0; i < (1 << K1); ++i) x[i] = srcin[(r << N2) + r0 + (i << K2)];
       fwd_block<K1, K2, N1, LOGN>(x, ((row0 + r) << N2) + r0, tw, q);
 #pragma unroll
       for (int i = 0; i < (1 << K1); ++i) sm[sidx(r, r0 + (i << K2))] = x[i];
@@ -191,7 +204,7 @@ __global__ void __launch_bounds__(kThreads) k_rows(LimbSet s, Tables T) {
     __syncthreads();
     for (u32 e = threadIdx.x; e < (RP << N2); e += kThreads) src[e] = sm[sidx(e >> N2, e & (C - 1))];
   } else {
-    for (u32 e = threadIdx.x; e < (RP << N2); e += kThreads) sm[sidx(e >> N2, e & (C - 1))] = src[e];
+    for (u32 e = threadIdx.x; e < (RP << N2); e += kThreads) sm[sidx(e >> N2, e & (C - 1))] = srcin[e];
     __syncthreads();
     // round A: 2^K2 adjacent points -> stages LOGN-1 .. LOGN-K2
     for (u32 w = threadIdx.x; w < (RP << K1); w += kThreads) {
@@ -244,52 +257,54 @@ struct RowTile {
 };
 
 template <bool INV, int LOGN>
-void launch_pass_cols(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs) {
+void launch_pass_cols(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, const LimbSet* in = nullptr) {
   constexpr int N1 = LOGN / 2, N2 = LOGN - N1;
   using Sp = Split<N1>;
   constexpr int TCL = ColTile<N1, N2>::TCL;
   dim3 grid(1u << (N2 - TCL), ylimbs, items);
   const size_t smem = ((size_t)1 << (N1 + TCL)) * sizeof(u64);
   ProfScope p(ctx, INV ? "ntt_inv_cols" : "ntt_fwd_cols", (uint64_t)ylimbs * items);
-  k_cols<INV, LOGN, Sp::K1, Sp::K2, TCL><<<grid, kThreads, smem, ctx->stream>>>(s, ctx->tab);
+  k_cols<INV, LOGN, Sp::K1, Sp::K2, TCL><<<grid, kThreads, smem, ctx->stream>>>(s, in ? *in : s, in ? 1 : 0, ctx->tab);
 }
 
 template <bool INV, int LOGN>
-void launch_pass_rows(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs) {
+void launch_pass_rows(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, const LimbSet* in = nullptr) {
   constexpr int N1 = LOGN / 2, N2 = LOGN - N1;
   using Sp = Split<N2>;
   constexpr int RPL = RowTile<N1, N2>::RPL;
   dim3 grid(1u << (N1 - RPL), ylimbs, items);
   const size_t smem = ((size_t)1 << RPL) * RowTile<N1, N2>::PADW * sizeof(u64);
   ProfScope p(ctx, INV ? "ntt_inv_rows" : "ntt_fwd_rows", (uint64_t)ylimbs * items);
-  k_rows<INV, LOGN, Sp::K1, Sp::K2, RPL><<<grid, kThreads, smem, ctx->stream>>>(s, ctx->tab);
+  k_rows<INV, LOGN, Sp::K1, Sp::K2, RPL><<<grid, kThreads, smem, ctx->stream>>>(s, in ? *in : s, in ? 1 : 0, ctx->tab);
 }
 
 template <int LOGN>
-void ntt_logn(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, bool inverse) {
+void ntt_logn(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, bool inverse, const LimbSet* in) {
   if (!inverse) {
-    launch_pass_cols<false, LOGN>(ctx, s, items, ylimbs);
+    launch_pass_cols<false, LOGN>(ctx, s, items, ylimbs, in);
     launch_pass_rows<false, LOGN>(ctx, s, items, ylimbs);
   } else {
-    launch_pass_rows<true, LOGN>(ctx, s, items, ylimbs);
+    launch_pass_rows<true, LOGN>(ctx, s, items, ylimbs, in);
     launch_pass_cols<true, LOGN>(ctx, s, items, ylimbs);
   }
 }
 
 }  // namespace
 
-void launch_ntt(hc_ctx* ctx, const LimbSet& s, int items, bool inverse) {
+void launch_ntt(hc_ctx* ctx, const LimbSet& s, int items, bool inverse) { launch_ntt_from(ctx, s, nullptr, items, inverse); }
+
+void launch_ntt_from(hc_ctx* ctx, const LimbSet& s, const LimbSet* in, int items, bool inverse) {
   if (items <= 0 || s.nlimb <= 0 || s.npoly <= 0) return;
   const int ylimbs = s.npoly * s.nlimb;
   HC_CHECK(ylimbs <= 65535 && items <= 65535, HC_ERR_INVALID, "NTT batch too large");
   switch (ctx->P.log_n) {
-    case 10: ntt_logn<10>(ctx, s, items, ylimbs, inverse); break;
-    case 11: ntt_logn<11>(ctx, s, items, ylimbs, inverse); break;
-    case 12: ntt_logn<12>(ctx, s, items, ylimbs, inverse); break;
-    case 13: ntt_logn<13>(ctx, s, items, ylimbs, inverse); break;
-    case 14: ntt_logn<14>(ctx, s, items, ylimbs, inverse); break;
-    case 15: ntt_logn<15>(ctx, s, items, ylimbs, inverse); break;
-    case 16: ntt_logn<16>(ctx, s, items, ylimbs, inverse); break;
+    case 10: ntt_logn<10>(ctx, s, items, ylimbs, inverse, in); break;
+    case 11: ntt_logn<11>(ctx, s, items, ylimbs, inverse, in); break;
+    case 12: ntt_logn<12>(ctx, s, items, ylimbs, inverse, in); break;
+    case 13: ntt_logn<13>(ctx, s, items, ylimbs, inverse, in); break;
+    case 14: ntt_logn<14>(ctx, s, items, ylimbs, inverse, in); break;
+    case 15: ntt_logn<15>(ctx, s, items, ylimbs, inverse, in); break;
+    case 16: ntt_logn<16>(ctx, s, items, ylimbs, inverse, in); break;
     default: throw HcError{HC_ERR_INVALID, "unsupported ring degree"};
   }
   ctx->launches += 2;
