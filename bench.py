@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-uneven", action="store_true", help="skip the uneven multi-instance leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop leg")
     ap.add_argument("--no-deep", action="store_true", help="skip the deep single-ciphertext CNN leg")
+    ap.add_argument("--paper-shape", action="store_true",
+                    help="also run the paper's own network (N=2^15, 16384 images; ~80 GB of device memory)")
     ap.add_argument("--serve-requests", type=int, default=60, help="requests per arrival rate")
     ap.add_argument("--summarize-ncu", metavar="CSV",
                     help="summarise an ncu launch list (gpu__time_duration.sum) of the timed step and exit")
@@ -565,6 +567,68 @@ def deep_leg(H, W, np, torch, local):
             "latency_ms": 1000 * t, "images_per_s": 1.0 / t, "max_logit_error_vs_fp64": err}
 
 
+def paper_shape_leg(H, W, np, torch, local):
+    """The paper's network at N = 2^15 on 16384 synthetic 28x28 images,
+    filter by filter as in the paper (conv 3x3 -> Eq. 4 activation -> mean
+    pool per filter, then FC 4732 -> 10), inference time on the device."""
+    from oracle import cnn as ref_cnn  # FP64 plaintext network only (correctness guard)
+
+    ps, c = W.PAPER_N15, W.PAPER_CNN
+    params = H.hc_params_create(ps.log_n, list(ps.q_bits), list(ps.p_bits), ps.log2_scale)
+    stream = torch.cuda.current_stream()
+    ctx = H.hc_ctx_create(params, local, stream.cuda_stream)
+    K, scale = ctx.n // 2, 2.0 ** ps.log2_scale
+    sk, pk, evk = H.hc_keygen(ctx, W.MASTER_SEED + 6)
+    imgs = W.images(W.MASTER_SEED + 30, K, 28, 28)
+    cw = W.conv_weights(W.MASTER_SEED + 31, c["cout"], 3, 3)
+    n_in = 13 * 13 * c["cout"]
+    fw = W.fc_weights(W.MASTER_SEED + 32, c["n_out"], n_in) * 0.05
+
+    def const(v, level, nonce):
+        m = np.zeros(ctx.n, dtype=np.int64)
+        m[0] = int(round(v * scale))
+        return H.hc_encrypt(ctx, pk, H.hc_pt_from_coeffs(ctx, m, level, scale), 5, nonce)
+
+    xs = [H.hc_encrypt(ctx, pk, H.hc_encode(ctx, imgs[:, h, w], scale, ctx.L), 5, h * 28 + w)
+          for h in range(28) for w in range(28)]
+    ws = [[const(cw[f, a, b, 0], ctx.L, 10000 + f * 9 + a * 3 + b) for a in range(3) for b in range(3)]
+          for f in range(c["cout"])]
+    fws = [const(fw[r, i], 2, 100000 + r * n_in + i) for r in range(c["n_out"]) for i in range(n_in)]
+    H.hc_sync(ctx)
+    t0 = time.perf_counter()
+    pooled = [None] * n_in
+    t_conv = t_act = t_pool = 0.0
+    for f in range(c["cout"]):
+        ta = time.perf_counter()
+        y = H.hc_enc_conv2d(ctx, evk, H.HC_PACK_BATCH, xs, 28, 28, 1, ws[f], 1, 3, 3, 1)
+        H.hc_sync(ctx)
+        tb = time.perf_counter()
+        a = H.hc_enc_poly_act(ctx, evk, y, c["act"])
+        del y
+        H.hc_sync(ctx)
+        tc = time.perf_counter()
+        p = H.hc_enc_pool(ctx, evk, H.HC_PACK_BATCH, a, 1, 26, 26)
+        del a
+        H.hc_sync(ctx)
+        td = time.perf_counter()
+        t_conv, t_act, t_pool = t_conv + tb - ta, t_act + tc - tb, t_pool + td - tc
+        for i in range(13):
+            for j in range(13):
+                pooled[(i * 13 + j) * c["cout"] + f] = p[i * 13 + j]
+    te = time.perf_counter()
+    z = H.hc_enc_fc(ctx, evk, H.HC_PACK_BATCH, pooled, fws, c["n_out"])
+    H.hc_sync(ctx)
+    t_fc = time.perf_counter() - te
+    total = time.perf_counter() - t0
+    logits = np.stack([H.hc_decode(ctx, H.hc_decrypt(ctx, sk, t)).real for t in z], axis=1)
+    ref = ref_cnn.network(imgs[..., None], cw, 1, c["act"], fw)
+    err = float(np.max(np.abs(logits - ref)))
+    return {"workload": "paper_n15: 16384 images 28x28, 28 filters 3x3 -> ActPool (0.47, 0.50, 0.09) -> fc 4732->10",
+            "seconds": total, "images_per_s": K / total, "seconds_conv": t_conv, "seconds_act": t_act,
+            "seconds_pool": t_pool, "seconds_fc": t_fc, "max_logit_error_vs_fp64": err,
+            "argmax_agreement": float(np.mean(np.argmax(logits, 1) == np.argmax(ref, 1)))}
+
+
 def run_gpu(args, rank, world, local):
     import numpy as np
     import torch
@@ -705,6 +769,8 @@ def run_gpu(args, rank, world, local):
         line["serving"] = serving_leg(args, H, W, np, torch, local)
     if not args.no_deep:
         line["deep"] = deep_leg(H, W, np, torch, local)
+    if args.paper_shape:
+        line["paper_shape"] = paper_shape_leg(H, W, np, torch, local)
     if world == 1 and not args.no_cpu_baseline:
         ob = OracleBench()
         dt = ob.run(args.cpu_ops)

@@ -136,3 +136,13 @@ def deep_fc_vectors(fc_w, C, Hp, Wp, W, slots):
             for c in range(C):
                 V[:, c, 2 * i * W + 2 * j] = fc_w[:, (i * Wp + j) * C + c]
     return V
+
+
+# The paper's network (Sec. "Dataset and Inference Results"): 28 filters
+# 3x3 without padding on 28x28 images -> ActPool (Eq. 4 activation, then 2x2
+# mean) -> flatten 13*13*28 = 4732 -> FC 4732 x 10, K = 16384 images per batch
+# at N = 2^15 (the paper's m = 2^16).  Levels: conv 6 -> 5, activation -> 3,
+# pool -> 2, FC -> 1; q_0 60 bits, six 40-bit primes, one 60-bit special prime,
+# scale 2^40 (logQP = 360).
+PAPER_N15 = ParamSet("paper_n15", 15, (60,) + (40,) * 6, (60,), 40)
+PAPER_CNN = dict(H=28, W=28, cout=28, k=3, stride=1, act=(0.47, 0.50, 0.09), n_out=10)
