@@ -700,6 +700,18 @@ def run_gpu(args, rank, world, local):
     t_max = max_over_ranks(ms / 1000.0, device="cuda")
     value = Bn * args.steps * world / t_max
 
+    # ---------------- the same work as one ABI call per operation (per-op form)
+    def per_op_step():
+        return [H.hc_rescale(ctx, H.hc_relin(ctx, evk, H.hc_mul(ctx, a, b))) for a, b in zip(A, Bc)]
+
+    per_op_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(2):
+        per_op_step()
+    barrier()
+    per_op_value = Bn * 2 * world / max_over_ranks(time.perf_counter() - t0, device="cuda")
+
     # ---------------- e2e through the C ABI from pinned host memory
     host_in = []
     for c in A + Bc:
@@ -759,6 +771,8 @@ def run_gpu(args, rank, world, local):
                    "l2": "inputs larger than L2 (%.2f GB of resident ciphertexts)" % (2 * Bn * 2 * (L + 1) * n * 8 / 1e9)},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches, "roofline": roofline, "clocks": clk, "kernels": kern_summary,
+        "per_op": {"value": per_op_value, "unit": UNIT,
+                   "form": "hc_mul, hc_relin, hc_rescale per pair (unfused relin and rescale, one pair per call)"},
         "check": {"max_slot_error": err},
     }
     if not args.no_cnn:
