@@ -74,8 +74,8 @@ def summarize_ncu(path, occurrence):
     starts = [i for i, n in enumerate(names) if n == "k_tensor_acc"]
     a = starts[occurrence - 1]
     b = starts[occurrence] if occurrence < len(starts) else len(rows)
-    # the step ends at its last rescale combine
-    ends = [i for i in range(a, b) if names[i] == "k_rescale_combine"]
+    # the step ends at its last rescale combine (fused or not)
+    ends = [i for i in range(a, b) if names[i] in ("k_ksr_combine", "k_rescale_combine")]
     b = ends[-1] + 1
     per = {}
     for i in range(a, b):
@@ -230,8 +230,8 @@ def run_reference(args, rank, world):
 # 336 limbs per launch), scaled to a launch by its units.  Set an entry to
 # None when its kernel changes until it is captured again.
 NCU_TRAFFIC_PER_UNIT = {
-    "ntt_fwd_cols": (176.285440e6 + 114.261248e6) / 336,
-    "ntt_fwd_rows": (209.567744e6 + 123.331584e6) / 336,
+    "ntt_fwd_cols": (176.307712e6 + 114.424832e6) / 336,
+    "ntt_fwd_rows": (209.289984e6 + 123.394560e6) / 336,
 }
 
 

@@ -574,7 +574,6 @@ void build_tables(hc_ctx* ctx) {
       }
       for (int i = 0; i < ns; ++i) ks.push_back(hinv[i]);
       for (int i = 0; i < ns; ++i) ks.push_back(hch::shoup_of(hinv[i], P.chain[d0 + i]));
-      std::vector<u64> hsh;
       for (int s = 0; s < next; ++s) {
         const u64 t = P.chain[emap[s]];
         for (int i = 0; i < ns; ++i) {
@@ -582,11 +581,8 @@ void build_tables(hc_ctx* ctx) {
           for (int k = 0; k < ns; ++k)
             if (k != i) prod = hch::mulmod(prod, P.chain[d0 + k] % t, t);
           ks.push_back(prod);
-          hsh.push_back(hch::shoup_of(prod, t));
         }
       }
-      lc.modup_sh_off.push_back((int)ks.size());
-      ks.insert(ks.end(), hsh.begin(), hsh.end());
     }
     if (l >= 1) {
       lc.rescale_off = (int)ks.size();
@@ -627,19 +623,7 @@ void build_tables(hc_ctx* ctx) {
     }
     for (int i = 0; i <= L; ++i) ks.push_back(pinv[i]);
     for (int i = 0; i <= L; ++i) ks.push_back(hch::shoup_of(pinv[i], P.chain[i]));
-    ctx->moddown_sh_off = (int)ks.size();
-    for (int i = 0; i <= L; ++i) {
-      const u64 qi = P.chain[i];
-      for (int k = 0; k < alpha; ++k) {
-        u64 prod = 1 % qi;
-        for (int m = 0; m < alpha; ++m)
-          if (m != k) prod = hch::mulmod(prod, P.chain[L + 1 + m] % qi, qi);
-        ks.push_back(hch::shoup_of(prod, qi));
-      }
-    }
   }
-  ctx->small_primes = true;
-  for (u64 q : P.chain) ctx->small_primes &= (q < ((u64)1 << 60));
   ctx->ks_dev = (u64*)put(ks.data(), ks.size() * sizeof(u64));
   // ext maps per level followed by an identity map of HC_MAX_CHAIN entries
   const int W = L + 1 + alpha;

@@ -60,7 +60,6 @@ struct LevelConsts {
   int dnum = 0;
   // ModUp digit j: hat_inv[i] (+sh) for i < |D_j|, then hat_mod[t][i] for t < ext
   std::vector<int> modup_off;
-  std::vector<int> modup_sh_off;  // Shoup companions of hat_mod[t][i] (mod the target prime)
   // rescale: q_l^{-1} mod q_i (+sh) for i < l, q_l mod q_i
   int rescale_off = -1;
 };
@@ -76,8 +75,6 @@ struct hc_ctx {
   u64* ks_dev = nullptr;     // flat constant buffer
   std::vector<LevelConsts> lv;
   int moddown_off = -1;      // (P/p_k)^{-1} mod p_k (+sh); (P/p_k) mod q_i; P^{-1} mod q_i (+sh)
-  int moddown_sh_off = -1;   // Shoup companions of (P/p_k) mod q_i, [L+1][alpha]
-  bool small_primes = false; // every prime < 2^60: lazy Shoup sums of 8 terms fit 64 bits
   int* ext_map = nullptr;    // [level][L+1+alpha] chain index of ext slot
   std::string err;
   uint64_t launches = 0;

@@ -710,79 +710,6 @@ __global__ void k_ksr_combine(const u64* acc, u64 acc_item_stride, u64 acc_poly_
   out[z].p[(size_t)k * out[z].stride + li] = shoup(r, qlinv[i], qlinv[level + i], q);
 }
 
-// Shoup-lazy conversions (all primes < 2^60, at most 8 terms): each term
-// v_i h_{t,i} mod t is formed in [0, 2t) with the precomputed companion of
-// h_{t,i}, the sum of at most 8 terms stays below 16 t < 2^64 and is reduced
-// once.  Same values as the 128-bit accumulating kernels.
-__device__ __forceinline__ u64 reduce_lazy_sum(u64 s, const DMod& m) {
-  return csub(s - __umul64hi(s, m.one_sh) * m.q, m.q);
-}
-
-template <int NS>
-__global__ void __launch_bounds__(kT) k_modup_bconv_s(const u64* xcoef, u64 x_item_stride, u64* ext,
-                                                       u64 ext_item_stride, const u64* cst, const u64* cst_sh, int d0,
-                                                       int next, const int* emap, Tables T) {
-  extern __shared__ u64 sh[];
-  u64* hm = sh;                            // [next][NS]
-  u64* hs = sh + next * NS;                // [next][NS]
-  DMod* md = (DMod*)(sh + 2 * next * NS);  // [next]
-  for (int e = threadIdx.x; e < next * NS; e += blockDim.x) {
-    hm[e] = cst[2 * NS + e];
-    hs[e] = cst_sh[e];
-  }
-  for (int t = threadIdx.x; t < next; t += blockDim.x) md[t] = T.mods[emap[t]];
-  __syncthreads();
-  const int n = 1 << T.log_n;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n) return;
-  const int z = blockIdx.z;
-  const u64* x = xcoef + (size_t)z * x_item_stride;
-  u64* y = ext + (size_t)z * ext_item_stride;
-  u64 v[NS];
-#pragma unroll
-  for (int i = 0; i < NS; ++i) v[i] = shoup(x[(size_t)(d0 + i) * n + c], cst[i], cst[NS + i], md[d0 + i].q);
-  for (int t = 0; t < next; ++t) {
-    if (t >= d0 && t < d0 + NS) continue;
-    const u64 q = md[t].q;
-    u64 acc = 0;
-#pragma unroll
-    for (int i = 0; i < NS; ++i) acc += shoup_lazy(v[i], hm[t * NS + i], hs[t * NS + i], q);
-    y[(size_t)t * n + c] = reduce_lazy_sum(acc, md[t]);
-  }
-}
-
-template <int ALPHA>
-__global__ void __launch_bounds__(kT) k_moddown_bconv_s(const u64* src, u64 src_item_stride, u64 src_poly_stride,
-                                                         u64* zq, u64 z_item_stride, const u64* cst,
-                                                         const u64* cst_sh, int nq, int L, Tables T) {
-  extern __shared__ u64 sh[];
-  u64* hm = sh;                              // [nq][ALPHA]
-  u64* hs = sh + nq * ALPHA;                 // [nq][ALPHA]
-  DMod* md = (DMod*)(sh + 2 * nq * ALPHA);   // [nq]
-  for (int e = threadIdx.x; e < nq * ALPHA; e += blockDim.x) {
-    hm[e] = cst[2 * ALPHA + e];
-    hs[e] = cst_sh[e];
-  }
-  for (int t = threadIdx.x; t < nq; t += blockDim.x) md[t] = T.mods[t];
-  __syncthreads();
-  const int n = 1 << T.log_n;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n) return;
-  const int k = blockIdx.y, z = blockIdx.z;
-  const u64* x = src + (size_t)z * src_item_stride + (size_t)k * src_poly_stride;
-  u64 v[ALPHA];
-#pragma unroll
-  for (int i = 0; i < ALPHA; ++i) v[i] = shoup(x[(size_t)i * n + c], cst[i], cst[ALPHA + i], T.mods[L + 1 + i].q);
-  u64* out = zq + (size_t)z * z_item_stride + (size_t)k * nq * n;
-  for (int t = 0; t < nq; ++t) {
-    const u64 q = md[t].q;
-    u64 acc = 0;
-#pragma unroll
-    for (int i = 0; i < ALPHA; ++i) acc += shoup_lazy(v[i], hm[t * ALPHA + i], hs[t * ALPHA + i], q);
-    out[(size_t)t * n + c] = reduce_lazy_sum(acc, md[t]);
-  }
-}
-
 }  // namespace
 
 void launch_modup_bconv_fast(hc_ctx* ctx, int level, int j, const u64* xcoef, u64 x_item_stride, u64* ext,
@@ -795,20 +722,6 @@ void launch_modup_bconv_fast(hc_ctx* ctx, int level, int j, const u64* xcoef, u6
   const size_t smem = (size_t)next * ns * sizeof(u64) + (size_t)next * sizeof(DMod);
   const dim3 g = grid_for(ctx, 1, items);
   ProfScope prof_(ctx, "k_modup_bconv", (uint64_t)items * (next - ns));
-  if (ctx->small_primes && ns <= 8) {
-    const u64* csh = ctx->ks(ctx->lv[level].modup_sh_off[j]);
-    const size_t smem_s = 2 * (size_t)next * ns * sizeof(u64) + (size_t)next * sizeof(DMod);
-#define HC_MODUP_S(NS)                                                                                           \
-  case NS:                                                                                                       \
-    k_modup_bconv_s<NS><<<g, kT, smem_s, ctx->stream>>>(xcoef, x_item_stride, ext, ext_item_stride, cst, csh, d0, \
-                                                         next, ctx->ext_map_of(level), ctx->tab);                \
-    break;
-    switch (ns) { HC_MODUP_S(1) HC_MODUP_S(2) HC_MODUP_S(3) HC_MODUP_S(4) HC_MODUP_S(5) HC_MODUP_S(6) HC_MODUP_S(7) HC_MODUP_S(8) }
-#undef HC_MODUP_S
-    ctx->launches++;
-    check_launch(ctx);
-    return;
-  }
 #define HC_MODUP(NS)                                                                                          \
   case NS:                                                                                                    \
     k_modup_bconv_t<NS><<<g, kT, smem, ctx->stream>>>(xcoef, x_item_stride, ext, ext_item_stride, cst, d0, \
@@ -833,20 +746,6 @@ void launch_moddown_bconv_fast(hc_ctx* ctx, int level, const u64* accp_coef, u64
   const dim3 g = grid_for(ctx, 2, items);
   const u64 ps = (u64)next * ctx->P.n;
   ProfScope prof_(ctx, "k_moddown_bconv", (uint64_t)items * 2 * nq);
-  if (ctx->small_primes && alpha <= 8) {
-    const u64* csh = ctx->ks(ctx->moddown_sh_off);
-    const size_t smem_s = 2 * (size_t)nq * alpha * sizeof(u64) + (size_t)nq * sizeof(DMod);
-#define HC_MODDOWN_S(A)                                                                                        \
-  case A:                                                                                                      \
-    k_moddown_bconv_s<A><<<g, kT, smem_s, ctx->stream>>>(accp_coef, accp_item_stride, ps, z, z_item_stride, cst, \
-                                                          csh, nq, ctx->P.L, ctx->tab);                        \
-    break;
-    switch (alpha) { HC_MODDOWN_S(1) HC_MODDOWN_S(2) HC_MODDOWN_S(3) HC_MODDOWN_S(4) HC_MODDOWN_S(5) HC_MODDOWN_S(6) HC_MODDOWN_S(7) HC_MODDOWN_S(8) }
-#undef HC_MODDOWN_S
-    ctx->launches++;
-    check_launch(ctx);
-    return;
-  }
 #define HC_MODDOWN(A)                                                                                          \
   case A:                                                                                                      \
     k_moddown_bconv_t<A><<<g, kT, smem, ctx->stream>>>(accp_coef, accp_item_stride, ps, z, z_item_stride, cst, \
