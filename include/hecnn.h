@@ -188,6 +188,13 @@ typedef struct hc_ct_meta {
 int hc_ct_export(hc_ctx *ctx, const hc_ct *ct, uint64_t *out, size_t cap_words, hc_ct_meta *meta);
 /* Import from the same layout; residues must be < q (else HC_ERR_INVALID). */
 int hc_ct_import(hc_ctx *ctx, const uint64_t *host, const hc_ct_meta *meta, hc_ct **out);
+/* Batched import of n ciphertexts (host[i] with metas[i]): one copy per
+ * ciphertext, one range check and one synchronisation for the batch; on any
+ * residue >= q nothing is returned (HC_ERR_INVALID). */
+int hc_ct_import_batch(hc_ctx *ctx, const uint64_t *const *host, const hc_ct_meta *metas, int n, hc_ct **out);
+/* Batched export: one inverse NTT launch for all, asynchronous copies into
+ * host[i] (capacity cap[i] words), one synchronisation. */
+int hc_ct_export_batch(hc_ctx *ctx, const hc_ct *const *cts, int n, uint64_t *const *host, const size_t *cap);
 int hc_ct_meta_of(const hc_ct *ct, hc_ct_meta *meta);
 void hc_ct_destroy(hc_ct *);
 
@@ -225,6 +232,22 @@ int hc_rotate_hoisted(hc_ctx *ctx, const hc_evk *evk, const hc_ct *x, const int3
  * into one pass of each kernel. */
 int hc_mul_relin_rescale_batch(hc_ctx *ctx, const hc_evk *evk, const hc_ct *const *a,
                                const hc_ct *const *b, int n, hc_ct **outs);
+/* The same n operations from host memory to host memory.  a_host[k] and
+ * b_host[k] hold degree-1 ciphertexts in coefficient form
+ * ([2][level+1][N] words, the hc_ct_export layout) at one level >= 1
+ * (a_meta/b_meta give level, degree and scale); out_host[k] (capacity
+ * out_cap[k] words >= 2 level N) receives the product, rescaled, in the same
+ * layout, and out_meta[k] its metadata.  The batch runs as a pipeline of
+ * chunks of `chunk` pairs (0: about an eighth of n): copies in, the batched
+ * operation and copies out of successive chunks overlap on separate CUDA
+ * streams.  Pinned host buffers are needed for the overlap.  Inputs are
+ * range-checked on the device; a residue >= its prime gives
+ * HC_ERR_INVALID after the call has run, with out_host not valid.  Returns
+ * when every output is in host memory.  Not capturable in a graph. */
+int hc_mul_relin_rescale_host(hc_ctx *ctx, const hc_evk *evk, const uint64_t *const *a_host,
+                              const hc_ct_meta *a_meta, const uint64_t *const *b_host,
+                              const hc_ct_meta *b_meta, int n, int chunk, uint64_t *const *out_host,
+                              const size_t *out_cap, hc_ct_meta *out_meta);
 
 /*
  * Relinearisation that allocates no device memory.  The paper has no

@@ -472,6 +472,7 @@ extern "C" int hc_params_create(const hc_params_desc* d, hc_params** out) {
       delete p;
       throw HcError{HC_ERR_INVALID, "not enough primes of the requested sizes"};
     }
+    p->below_2_60 = std::all_of(p->chain.begin(), p->chain.end(), [](u64 q) { return q < (1ull << 60); });
     p->scale = std::exp2(d->log2_scale);
     p->sigma = d->sigma;
     p->cdt = hch::gaussian_cdt(d->sigma);
@@ -1087,6 +1088,94 @@ extern "C" int hc_ct_import(hc_ctx* ctx, const uint64_t* host, const hc_ct_meta*
   });
 }
 
+extern "C" int hc_ct_import_batch(hc_ctx* ctx, const uint64_t* const* host, const hc_ct_meta* metas, int n,
+                                  hc_ct** out) {
+  if (!ctx) return HC_ERR_INVALID;
+  std::vector<hc_ct*> made;
+  int rc = guard(ctx, [&] {
+    HC_CHECK(n >= 0 && (n == 0 || (host && metas && out)), HC_ERR_INVALID, "null argument");
+    if (n == 0) return;
+    std::vector<BufPtr> keep;
+    BufPtr flag = ctx->buffer(1);
+    keep.push_back(flag);
+    HC_CUDA(cudaMemsetAsync(flag->ptr, 0, sizeof(u64), ctx->stream));
+    for (int i = 0; i < n; ++i) {
+      const hc_ct_meta& m = metas[i];
+      HC_CHECK(host[i] && m.level >= 0 && m.level <= ctx->P.L && (m.degree == 1 || m.degree == 2), HC_ERR_INVALID,
+               "bad metadata");
+      hc_ct* c = new_ct(ctx, m.level, m.degree, m.scale);
+      made.push_back(c);
+      const size_t words = (size_t)(m.degree + 1) * (m.level + 1) * ctx->P.n;
+      HC_CUDA(cudaMemcpyAsync(c->data, host[i], words * sizeof(u64), cudaMemcpyHostToDevice, ctx->stream));
+      launch_check_range(ctx, c->data, m.degree + 1, m.level + 1, c->stride, (unsigned long long*)flag->ptr);
+    }
+    u64 bad = 0;
+    HC_CUDA(cudaMemcpyAsync(&bad, flag->ptr, sizeof(u64), cudaMemcpyDeviceToHost, ctx->stream));
+    HC_CUDA(cudaStreamSynchronize(ctx->stream));
+    HC_CHECK(bad == 0, HC_ERR_INVALID, "imported residue not below its prime");
+    // one forward NTT launch per (level, degree) group
+    std::map<std::pair<int, int>, std::vector<CtRef>> groups;
+    for (auto* c : made) groups[{c->level, c->degree}].push_back(c->ref());
+    for (auto& kv : groups) {
+      LimbSet sset{};
+      sset.refs = refs_dev(ctx, kv.second, keep);
+      sset.npoly = kv.first.second + 1;
+      sset.nlimb = kv.first.first + 1;
+      launch_ntt(ctx, sset, (int)kv.second.size(), false);
+    }
+    for (int i = 0; i < n; ++i) out[i] = made[i];
+    made.clear();
+  });
+  for (auto* c : made) delete c;
+  return rc;
+}
+
+extern "C" int hc_ct_export_batch(hc_ctx* ctx, const hc_ct* const* cts, int n, uint64_t* const* host,
+                                  const size_t* cap) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    HC_CHECK(n >= 0 && (n == 0 || (cts && host && cap)), HC_ERR_INVALID, "null argument");
+    if (n == 0) return;
+    const int N = ctx->P.n;
+    size_t total = 0;
+    std::vector<size_t> off(n);
+    for (int i = 0; i < n; ++i) {
+      check_ct(ctx, cts[i]);
+      const size_t words = (size_t)(cts[i]->degree + 1) * (cts[i]->level + 1) * N;
+      HC_CHECK(host[i] && cap[i] >= words, HC_ERR_INVALID, "output buffer too small");
+      off[i] = total;
+      total += words;
+    }
+    std::vector<BufPtr> keep;
+    BufPtr tmp = ctx->buffer(total);
+    keep.push_back(tmp);
+    std::map<std::pair<int, int>, std::vector<std::pair<CtRef, CtRef>>> groups;  // (src, dst)
+    for (int i = 0; i < n; ++i) {
+      const hc_ct* c = cts[i];
+      const u64 ps = (u64)(c->level + 1) * N;
+      groups[{c->level, c->degree}].push_back({c->ref(), CtRef{tmp->ptr + off[i], ps}});
+    }
+    for (auto& kv : groups) {
+      std::vector<CtRef> src, dst;
+      for (auto& pr : kv.second) {
+        src.push_back(pr.first);
+        dst.push_back(pr.second);
+      }
+      LimbSet in{}, out{};
+      in.refs = refs_dev(ctx, src, keep);
+      out.refs = refs_dev(ctx, dst, keep);
+      in.npoly = out.npoly = kv.first.second + 1;
+      in.nlimb = out.nlimb = kv.first.first + 1;
+      launch_ntt_from(ctx, out, &in, (int)src.size(), true);
+    }
+    for (int i = 0; i < n; ++i) {
+      const size_t words = (size_t)(cts[i]->degree + 1) * (cts[i]->level + 1) * N;
+      HC_CUDA(cudaMemcpyAsync(host[i], tmp->ptr + off[i], words * sizeof(u64), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    HC_CUDA(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
 extern "C" int hc_ct_meta_of(const hc_ct* ct, hc_ct_meta* meta) {
   if (!ct || !meta) return HC_ERR_INVALID;
   *meta = hc_ct_meta{ct->level, ct->degree, ct->scale};
@@ -1302,36 +1391,154 @@ extern "C" int hc_rotate_hoisted(hc_ctx* ctx, const hc_evk* evk, const hc_ct* x,
   });
 }
 
+namespace {
+// n products a[i] b[i], relinearised and rescaled (one pass of each kernel).
+std::vector<hc_ct*> mul_relin_rescale_cts(hc_ctx* ctx, const hc_evk* evk, const hc_ct* const* a,
+                                          const hc_ct* const* b, int n) {
+  const int level = a[0]->level;
+  std::vector<const hc_ct*> xs, ws;
+  std::vector<int> xi, wi, off{0};
+  for (int i = 0; i < n; ++i) {
+    check_ct(ctx, a[i]);
+    check_ct(ctx, b[i]);
+    HC_CHECK(a[i]->level == level && b[i]->level == level, HC_ERR_LEVEL_MISMATCH, "batch mixes levels");
+    HC_CHECK(a[i]->degree == 1 && b[i]->degree == 1, HC_ERR_INVALID, "degree-1 operands expected");
+    xs.push_back(a[i]);
+    ws.push_back(b[i]);
+    xi.push_back(i);
+    wi.push_back(i);
+    off.push_back(i + 1);
+  }
+  HC_CHECK(level >= 1, HC_ERR_DEPTH, "no level left to rescale");
+  std::vector<hc_ct*> d = tensor_acc(ctx, xs, ws, xi, wi, off, level, a[0]->scale * b[0]->scale);
+  for (int i = 0; i < n; ++i) d[i]->scale = a[i]->scale * b[i]->scale;
+  std::vector<hc_ct*> r = relin_rescale(ctx, evk, d, nullptr);
+  for (int i = 0; i < n; ++i) r[i]->scale = d[i]->scale / (double)ctx->P.chain[level];
+  free_all(d);
+  return r;
+}
+}  // namespace
+
 extern "C" int hc_mul_relin_rescale_batch(hc_ctx* ctx, const hc_evk* evk, const hc_ct* const* a,
                                           const hc_ct* const* b, int n, hc_ct** outs) {
   if (!ctx) return HC_ERR_INVALID;
   return guard(ctx, [&] {
     HC_CHECK(evk && n >= 0 && (n == 0 || (a && b && outs)), HC_ERR_INVALID, "null argument");
     if (n == 0) return;
-    const int level = a[0]->level;
-    std::vector<const hc_ct*> xs, ws;
-    std::vector<int> xi, wi, off{0};
-    for (int i = 0; i < n; ++i) {
-      check_ct(ctx, a[i]);
-      check_ct(ctx, b[i]);
-      HC_CHECK(a[i]->level == level && b[i]->level == level, HC_ERR_LEVEL_MISMATCH, "batch mixes levels");
-      HC_CHECK(a[i]->degree == 1 && b[i]->degree == 1, HC_ERR_INVALID, "degree-1 operands expected");
-      xs.push_back(a[i]);
-      ws.push_back(b[i]);
-      xi.push_back(i);
-      wi.push_back(i);
-      off.push_back(i + 1);
-    }
-    HC_CHECK(level >= 1, HC_ERR_DEPTH, "no level left to rescale");
-    std::vector<hc_ct*> d = tensor_acc(ctx, xs, ws, xi, wi, off, level, a[0]->scale * b[0]->scale);
-    for (int i = 0; i < n; ++i) d[i]->scale = a[i]->scale * b[i]->scale;
-    std::vector<hc_ct*> r = relin_rescale(ctx, evk, d, nullptr);
-    for (int i = 0; i < n; ++i) {
-      r[i]->scale = d[i]->scale / (double)ctx->P.chain[level];
-      outs[i] = r[i];
-    }
-    free_all(d);
+    std::vector<hc_ct*> r = mul_relin_rescale_cts(ctx, evk, a, b, n);
+    for (int i = 0; i < n; ++i) outs[i] = r[i];
   });
+}
+
+// Host-to-host pipeline: all input slabs are allocated up front (so the copy
+// stream never waits on the compute stream), every chunk's inputs are queued
+// on the copy-in stream at once, and chunk c's compute waits only for its own
+// copies; its outputs go back on the copy-out stream while chunk c + 1 runs.
+extern "C" int hc_mul_relin_rescale_host(hc_ctx* ctx, const hc_evk* evk, const uint64_t* const* a_host,
+                                         const hc_ct_meta* a_meta, const uint64_t* const* b_host,
+                                         const hc_ct_meta* b_meta, int n, int chunk, uint64_t* const* out_host,
+                                         const size_t* out_cap, hc_ct_meta* out_meta) {
+  if (!ctx) return HC_ERR_INVALID;
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  std::vector<cudaEvent_t> evs;
+  std::vector<std::vector<hc_ct*>> ins;
+  int rc = guard(ctx, [&] {
+    HC_CHECK(evk && n >= 0 && (n == 0 || (a_host && b_host && a_meta && b_meta && out_host && out_cap && out_meta)),
+             HC_ERR_INVALID, "null argument");
+    HC_CHECK(!ctx->arena, HC_ERR_INVALID, "host-buffer calls cannot be captured");
+    if (n == 0) return;
+    const int level = a_meta[0].level, N = ctx->P.n;
+    HC_CHECK(level >= 0 && level <= ctx->P.L, HC_ERR_INVALID, "bad level");
+    HC_CHECK(level >= 1, HC_ERR_DEPTH, "no level left to rescale");
+    const size_t out_words = (size_t)2 * level * N;
+    for (int i = 0; i < n; ++i) {
+      HC_CHECK(a_meta[i].level == level && b_meta[i].level == level, HC_ERR_LEVEL_MISMATCH, "batch mixes levels");
+      HC_CHECK(a_meta[i].degree == 1 && b_meta[i].degree == 1, HC_ERR_INVALID, "degree-1 operands expected");
+      HC_CHECK(a_host[i] && b_host[i] && out_host[i], HC_ERR_INVALID, "null buffer");
+      HC_CHECK(out_cap[i] >= out_words, HC_ERR_INVALID, "output buffer too small");
+    }
+    const int m0 = chunk > 0 ? std::min(chunk, n) : std::max(1, (n + 7) / 8);
+    const int nch = (n + m0 - 1) / m0;
+    HC_CUDA(cudaStreamCreateWithFlags(&h2d, cudaStreamNonBlocking));
+    HC_CUDA(cudaStreamCreateWithFlags(&d2h, cudaStreamNonBlocking));
+    auto event = [&]() {
+      cudaEvent_t e;
+      HC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      evs.push_back(e);
+      return e;
+    };
+    std::vector<BufPtr> keep;
+    BufPtr flags = ctx->buffer(nch);
+    keep.push_back(flags);
+    HC_CUDA(cudaMemsetAsync(flags->ptr, 0, nch * sizeof(u64), ctx->stream));
+    const size_t stride = (size_t)(level + 1) * N;  // one polynomial
+    for (int c = 0; c < nch; ++c) {
+      const int m = std::min(m0, n - c * m0);
+      ins.push_back(new_cts(ctx, 2 * m, level, 1, 1.0));  // a's then b's, one slab
+    }
+    const cudaEvent_t allocated = event();
+    HC_CUDA(cudaEventRecord(allocated, ctx->stream));
+    HC_CUDA(cudaStreamWaitEvent(h2d, allocated, 0));
+    std::vector<cudaEvent_t> copied(nch);
+    for (int c = 0; c < nch; ++c) {
+      const int m = (int)ins[c].size() / 2;
+      for (int j = 0; j < m; ++j) {
+        const int i = c * m0 + j;
+        HC_CUDA(cudaMemcpyAsync(ins[c][j]->data, a_host[i], 2 * stride * sizeof(u64), cudaMemcpyHostToDevice, h2d));
+        HC_CUDA(cudaMemcpyAsync(ins[c][m + j]->data, b_host[i], 2 * stride * sizeof(u64), cudaMemcpyHostToDevice,
+                                h2d));
+      }
+      copied[c] = event();
+      HC_CUDA(cudaEventRecord(copied[c], h2d));
+    }
+    for (int c = 0; c < nch; ++c) {
+      std::vector<hc_ct*>& x = ins[c];
+      const int m = (int)x.size() / 2;
+      HC_CUDA(cudaStreamWaitEvent(ctx->stream, copied[c], 0));
+      launch_check_range(ctx, x[0]->data, 4 * m, level + 1, stride, (unsigned long long*)(flags->ptr + c));
+      launch_ntt(ctx, limbset_base(x[0]->data, 2 * stride, stride, 2, level + 1, 0, nullptr), 2 * m, false);
+      for (int j = 0; j < m; ++j) {
+        x[j]->scale = a_meta[c * m0 + j].scale;
+        x[m + j]->scale = b_meta[c * m0 + j].scale;
+      }
+      std::vector<hc_ct*> r = mul_relin_rescale_cts(ctx, evk, x.data(), x.data() + m, m);
+      free_all(x);  // stream-ordered: the copies into x finished before this stream's first use
+      BufPtr staged = ctx->buffer(m * out_words);
+      keep.push_back(staged);
+      std::vector<CtRef> rr;
+      for (auto* ct : r) rr.push_back(ct->ref());
+      LimbSet src{};
+      src.refs = refs_dev(ctx, rr, keep);
+      src.npoly = 2;
+      src.nlimb = level;
+      launch_ntt_from(ctx, limbset_base(staged->ptr, out_words, (u64)level * N, 2, level, 0, nullptr), &src, m,
+                      true);
+      for (int j = 0; j < m; ++j) out_meta[c * m0 + j] = hc_ct_meta{level - 1, 1, r[j]->scale};
+      free_all(r);
+      const cudaEvent_t done = event();
+      HC_CUDA(cudaEventRecord(done, ctx->stream));
+      HC_CUDA(cudaStreamWaitEvent(d2h, done, 0));
+      for (int j = 0; j < m; ++j)
+        HC_CUDA(cudaMemcpyAsync(out_host[c * m0 + j], staged->ptr + (size_t)j * out_words, out_words * sizeof(u64),
+                                cudaMemcpyDeviceToHost, d2h));
+    }
+    // staged buffers go back to the pool only after the copies out
+    const cudaEvent_t drained = event();
+    HC_CUDA(cudaEventRecord(drained, d2h));
+    HC_CUDA(cudaStreamWaitEvent(ctx->stream, drained, 0));
+    std::vector<u64> bad(nch);
+    HC_CUDA(cudaMemcpyAsync(bad.data(), flags->ptr, nch * sizeof(u64), cudaMemcpyDeviceToHost, ctx->stream));
+    HC_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (u64 b : bad) HC_CHECK(b == 0, HC_ERR_INVALID, "input residue not below its prime (outputs not valid)");
+  });
+  // on an error the side streams may still be writing into inputs: drain them first
+  if (h2d) cudaStreamSynchronize(h2d);
+  if (d2h) cudaStreamSynchronize(d2h);
+  for (auto& v : ins) free_all(v);
+  for (cudaEvent_t e : evs) cudaEventDestroy(e);
+  if (h2d) cudaStreamDestroy(h2d);
+  if (d2h) cudaStreamDestroy(d2h);
+  return rc;
 }
 
 // =====================================================================

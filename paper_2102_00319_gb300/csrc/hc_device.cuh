@@ -82,6 +82,24 @@ __device__ __forceinline__ u64 shoup(u64 a, u64 w, u64 wsh, u64 q) {
   return csub(shoup_lazy(a, w, wsh, q), q);
 }
 
+// Estimate of floor(y wsh / 2^64) from three of the four 32 x 32-bit partial
+// products: the low x low product and the carries out of the low words are
+// dropped, so the estimate is the exact quotient minus 0, 1 or 2.  Integer
+// multiplies are the scarce resource on this GPU (wide and high-half forms
+// take two issue slots of the one pipe that runs them); this saves about a
+// third of a full 64-bit high product (whether that wins depends on the
+// kernel's mix of integer and ALU work).
+__device__ __forceinline__ u64 mulhi_est(u64 y, u64 wsh) {
+  const uint32_t y0 = (uint32_t)y, y1 = (uint32_t)(y >> 32);
+  const uint32_t w0 = (uint32_t)wsh, w1 = (uint32_t)(wsh >> 32);
+  return (u64)y1 * w1 + __umulhi(y1, w0) + __umulhi(y0, w1);
+}
+// a * w mod q in [0, 4q) for any 64-bit a (w < q, wsh as above): Shoup's
+// product with the estimated quotient; needs q < 2^62.
+__device__ __forceinline__ u64 shoup_lazy4(u64 a, u64 w, u64 wsh, u64 q) {
+  return a * w - mulhi_est(a, wsh) * q;
+}
+
 struct U128 {
   u64 lo, hi;
 };
@@ -96,6 +114,17 @@ __device__ __forceinline__ u64 reduce128(U128 x, const DMod& m) {
   u64 t = shoup_lazy(x.hi, m.r64, m.r64_sh, m.q);     // hi 2^64 mod q, [0, 2q)
   u64 r = x.lo - __umul64hi(x.lo, m.one_sh) * m.q;     // lo mod q,      [0, 2q)
   u64 s = t + r;                                       // [0, 4q)
+  s = csub(s, 2 * m.q);
+  return csub(s, m.q);
+}
+// The same value with estimated quotients (q < 2^61, so 8q < 2^64): fewer
+// integer multiplies and one more conditional subtraction.  Which form is
+// faster depends on the kernel's instruction mix; measured per kernel.
+__device__ __forceinline__ u64 reduce128_est(U128 x, const DMod& m) {
+  u64 t = shoup_lazy4(x.hi, m.r64, m.r64_sh, m.q);     // [0, 4q)
+  u64 r = x.lo - mulhi_est(x.lo, m.one_sh) * m.q;      // [0, 4q)
+  u64 s = t + r;                                       // [0, 8q)
+  s = csub(s, 4 * m.q);
   s = csub(s, 2 * m.q);
   return csub(s, m.q);
 }

@@ -39,6 +39,7 @@ struct hc_params {
   std::vector<u64> chain;  // q_0..q_L, p_0..p_{alpha-1}
   double scale = 0, sigma = 0;
   std::vector<u64> cdt;
+  bool below_2_60 = false;  // every prime < 2^60: basis conversions use 30-bit halves
   int nchain() const { return (int)chain.size(); }
 };
 

@@ -150,15 +150,15 @@ __global__ void k_tensor_acc(const CtRef* out, const CtRef* x, const CtRef* w, c
     mac(a2, x1, w1);
     if (++cnt == chunk) {
       cnt = 0;
-      a0 = U128{reduce128(a0, md), 0};
-      a1 = U128{reduce128(a1, md), 0};
-      a2 = U128{reduce128(a2, md), 0};
+      a0 = U128{reduce128_est(a0, md), 0};
+      a1 = U128{reduce128_est(a1, md), 0};
+      a2 = U128{reduce128_est(a2, md), 0};
     }
   }
   const CtRef O = out[o];
-  O.p[lo] = reduce128(a0, md);
-  O.p[O.stride + lo] = reduce128(a1, md);
-  O.p[2 * O.stride + lo] = reduce128(a2, md);
+  O.p[lo] = reduce128_est(a0, md);
+  O.p[O.stride + lo] = reduce128_est(a1, md);
+  O.p[2 * O.stride + lo] = reduce128_est(a2, md);
 }
 
 // NTT-domain automorphism: slot k holds a(psi^{e_k}), e_k = 2 brv(k) + 1;
@@ -588,6 +588,98 @@ __global__ void __launch_bounds__(kT) k_modup_bconv_t(const u64* xcoef, u64 x_it
   }
 }
 
+// Exact sum of up to 8 products v_i h_i with v_i, h_i < 2^60, each operand
+// split into 30-bit halves (v = vh 2^30 + vl).  The three partial sums
+// (low x low, the cross terms, high x high) stay below 2^64 -- the cross sum
+// has at most 16 terms of at most (2^30 - 1)^2 -- so the loop is one 32 x 32
+// -> 64-bit multiply-add per partial product with no carry handling; the
+// 128-bit value is assembled once at the end.
+struct Acc30 {
+  u64 lo, mid, hi;
+};
+constexpr uint32_t kMask30 = (1u << 30) - 1;
+__device__ __forceinline__ void mac30(Acc30& s, uint32_t vl, uint32_t vh, uint2 h) {
+  s.lo += (u64)vl * h.x;
+  s.mid += (u64)vh * h.x;
+  s.mid += (u64)vl * h.y;
+  s.hi += (u64)vh * h.y;
+}
+// lo + mid 2^30 + hi 2^60 as a 128-bit value.
+__device__ __forceinline__ U128 acc30_value(const Acc30& s) {
+  const u64 x = s.lo + (s.mid << 30);
+  const u64 c1 = x < s.lo;
+  const u64 y = x + (s.hi << 60);
+  const u64 c2 = y < x;
+  return U128{y, (s.mid >> 34) + (s.hi >> 4) + c1 + c2};
+}
+__device__ __forceinline__ uint2 halves30(u64 h) { return make_uint2((uint32_t)h & kMask30, (uint32_t)(h >> 30)); }
+
+// ModUp conversion as k_modup_bconv_t with every prime below 2^60: the
+// constants sit in shared memory as 30-bit halves.
+template <int NS>
+__global__ void __launch_bounds__(kT) k_modup_bconv_h(const u64* xcoef, u64 x_item_stride, u64* ext,
+                                                       u64 ext_item_stride, const u64* cst, int d0, int next,
+                                                       const int* emap, Tables T) {
+  extern __shared__ u64 sh[];
+  uint2* hm = reinterpret_cast<uint2*>(sh);  // [next][NS]
+  DMod* md = (DMod*)(sh + next * NS);        // [next]
+  for (int e = threadIdx.x; e < next * NS; e += blockDim.x) hm[e] = halves30(cst[2 * NS + e]);
+  for (int t = threadIdx.x; t < next; t += blockDim.x) md[t] = T.mods[emap[t]];
+  __syncthreads();
+  const int n = 1 << T.log_n;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int z = blockIdx.z;
+  const u64* x = xcoef + (size_t)z * x_item_stride;
+  u64* y = ext + (size_t)z * ext_item_stride;
+  uint32_t vl[NS], vh[NS];
+#pragma unroll
+  for (int i = 0; i < NS; ++i) {
+    const u64 v = shoup(x[(size_t)(d0 + i) * n + c], cst[i], cst[NS + i], md[d0 + i].q);
+    vl[i] = (uint32_t)v & kMask30;
+    vh[i] = (uint32_t)(v >> 30);
+  }
+  for (int t = 0; t < next; ++t) {
+    if (t >= d0 && t < d0 + NS) continue;
+    Acc30 acc{0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < NS; ++i) mac30(acc, vl[i], vh[i], hm[t * NS + i]);
+    y[(size_t)t * n + c] = reduce128(acc30_value(acc), md[t]);
+  }
+}
+
+// ModDown conversion as k_moddown_bconv_t with every prime below 2^60.
+template <int ALPHA>
+__global__ void __launch_bounds__(kT) k_moddown_bconv_h(const u64* src, u64 src_item_stride, u64 src_poly_stride,
+                                                         u64* zq, u64 z_item_stride, const u64* cst, int nq, int L,
+                                                         Tables T) {
+  extern __shared__ u64 sh[];
+  uint2* hm = reinterpret_cast<uint2*>(sh);  // [nq][ALPHA]
+  DMod* md = (DMod*)(sh + nq * ALPHA);       // [nq]
+  for (int e = threadIdx.x; e < nq * ALPHA; e += blockDim.x) hm[e] = halves30(cst[2 * ALPHA + e]);
+  for (int t = threadIdx.x; t < nq; t += blockDim.x) md[t] = T.mods[t];
+  __syncthreads();
+  const int n = 1 << T.log_n;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int k = blockIdx.y, z = blockIdx.z;
+  const u64* x = src + (size_t)z * src_item_stride + (size_t)k * src_poly_stride;
+  uint32_t vl[ALPHA], vh[ALPHA];
+#pragma unroll
+  for (int i = 0; i < ALPHA; ++i) {
+    const u64 v = shoup(x[(size_t)i * n + c], cst[i], cst[ALPHA + i], T.mods[L + 1 + i].q);
+    vl[i] = (uint32_t)v & kMask30;
+    vh[i] = (uint32_t)(v >> 30);
+  }
+  u64* out = zq + (size_t)z * z_item_stride + (size_t)k * nq * n;
+  for (int t = 0; t < nq; ++t) {
+    Acc30 acc{0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < ALPHA; ++i) mac30(acc, vl[i], vh[i], hm[t * ALPHA + i]);
+    out[(size_t)t * n + c] = reduce128(acc30_value(acc), md[t]);
+  }
+}
+
 // ModDown conversion P -> Q_level of both polys (ALPHA special primes).
 template <int ALPHA>
 __global__ void __launch_bounds__(kT) k_moddown_bconv_t(const u64* src, u64 src_item_stride, u64 src_poly_stride,
@@ -620,7 +712,7 @@ __global__ void __launch_bounds__(kT) k_moddown_bconv_t(const u64* src, u64 src_
 // the 2 DNUM key words of (s, c) stay in registers across the batch.
 // digit_src (optional): the digit's own slots s in [j alpha, j alpha + alpha)
 // come from digit_src[z] (NTT-form input) instead of ext.
-template <int DNUM>
+template <int DNUM, bool HALVES>
 __global__ void __launch_bounds__(kT) k_key_product_t(const u64* ext, u64 ext_item_stride, const u64* key, u64* acc,
                                                        u64 acc_item_stride, int next, int nchain, const int* emap,
                                                        int items, const CtRef* digit_src, int alpha, int nq,
@@ -640,16 +732,30 @@ __global__ void __launch_bounds__(kT) k_key_product_t(const u64* ext, u64 ext_it
   const int own = (digit_src && s < nq) ? s / alpha : -1;  // the digit whose block holds slot s
   for (int z = blockIdx.z; z < items; z += gridDim.z) {
     const u64* e = ext + (size_t)z * ext_item_stride + (size_t)s * n + c;
-    U128 a0{0, 0}, a1{0, 0};
-#pragma unroll
-    for (int j = 0; j < DNUM; ++j) {
-      const u64 y = (j == own) ? digit_src[z].p[(size_t)s * n + c] : e[(size_t)j * next * n];
-      mac(a0, y, kb[j]);
-      mac(a1, y, ka[j]);
-    }
     u64* o = acc + (size_t)z * acc_item_stride + (size_t)s * n + c;
-    o[0] = reduce128(a0, md);
-    o[(size_t)next * n] = reduce128(a1, md);
+    if constexpr (HALVES) {
+      // every operand below 2^60: 30-bit halves, carry-free partial sums
+      Acc30 a0{0, 0, 0}, a1{0, 0, 0};
+#pragma unroll
+      for (int j = 0; j < DNUM; ++j) {
+        const u64 y = (j == own) ? digit_src[z].p[(size_t)s * n + c] : e[(size_t)j * next * n];
+        const uint32_t yl = (uint32_t)y & kMask30, yh = (uint32_t)(y >> 30);
+        mac30(a0, yl, yh, halves30(kb[j]));
+        mac30(a1, yl, yh, halves30(ka[j]));
+      }
+      o[0] = reduce128(acc30_value(a0), md);
+      o[(size_t)next * n] = reduce128(acc30_value(a1), md);
+    } else {
+      U128 a0{0, 0}, a1{0, 0};
+#pragma unroll
+      for (int j = 0; j < DNUM; ++j) {
+        const u64 y = (j == own) ? digit_src[z].p[(size_t)s * n + c] : e[(size_t)j * next * n];
+        mac(a0, y, kb[j]);
+        mac(a1, y, ka[j]);
+      }
+      o[0] = reduce128(a0, md);
+      o[(size_t)next * n] = reduce128(a1, md);
+    }
   }
 }
 
@@ -722,10 +828,15 @@ void launch_modup_bconv_fast(hc_ctx* ctx, int level, int j, const u64* xcoef, u6
   const size_t smem = (size_t)next * ns * sizeof(u64) + (size_t)next * sizeof(DMod);
   const dim3 g = grid_for(ctx, 1, items);
   ProfScope prof_(ctx, "k_modup_bconv", (uint64_t)items * (next - ns));
+  const bool halves = ctx->P.below_2_60;
 #define HC_MODUP(NS)                                                                                          \
   case NS:                                                                                                    \
-    k_modup_bconv_t<NS><<<g, kT, smem, ctx->stream>>>(xcoef, x_item_stride, ext, ext_item_stride, cst, d0, \
-                                                       next, ctx->ext_map_of(level), ctx->tab);             \
+    if (halves)                                                                                               \
+      k_modup_bconv_h<NS><<<g, kT, smem, ctx->stream>>>(xcoef, x_item_stride, ext, ext_item_stride, cst, d0, \
+                                                         next, ctx->ext_map_of(level), ctx->tab);             \
+    else                                                                                                      \
+      k_modup_bconv_t<NS><<<g, kT, smem, ctx->stream>>>(xcoef, x_item_stride, ext, ext_item_stride, cst, d0, \
+                                                         next, ctx->ext_map_of(level), ctx->tab);             \
     break;
   switch (ns) {
     HC_MODUP(1) HC_MODUP(2) HC_MODUP(3) HC_MODUP(4) HC_MODUP(5) HC_MODUP(6) HC_MODUP(7) HC_MODUP(8)
@@ -746,10 +857,15 @@ void launch_moddown_bconv_fast(hc_ctx* ctx, int level, const u64* accp_coef, u64
   const dim3 g = grid_for(ctx, 2, items);
   const u64 ps = (u64)next * ctx->P.n;
   ProfScope prof_(ctx, "k_moddown_bconv", (uint64_t)items * 2 * nq);
+  const bool halves = ctx->P.below_2_60;
 #define HC_MODDOWN(A)                                                                                          \
   case A:                                                                                                      \
-    k_moddown_bconv_t<A><<<g, kT, smem, ctx->stream>>>(accp_coef, accp_item_stride, ps, z, z_item_stride, cst, \
-                                                        nq, ctx->P.L, ctx->tab);                               \
+    if (halves)                                                                                                \
+      k_moddown_bconv_h<A><<<g, kT, smem, ctx->stream>>>(accp_coef, accp_item_stride, ps, z, z_item_stride,   \
+                                                          cst, nq, ctx->P.L, ctx->tab);                        \
+    else                                                                                                       \
+      k_moddown_bconv_t<A><<<g, kT, smem, ctx->stream>>>(accp_coef, accp_item_stride, ps, z, z_item_stride,   \
+                                                          cst, nq, ctx->P.L, ctx->tab);                        \
     break;
   switch (alpha) {
     HC_MODDOWN(1) HC_MODDOWN(2) HC_MODDOWN(3) HC_MODDOWN(4) HC_MODDOWN(5) HC_MODDOWN(6) HC_MODDOWN(7) HC_MODDOWN(8)
@@ -769,11 +885,17 @@ void launch_key_product_batched(hc_ctx* ctx, int level, const u64* ext, u64 ext_
   const int zgroups = std::min(items, std::max(1, 2048 / (next * ((ctx->P.n + kT - 1) / kT))));
   const dim3 g = grid_for(ctx, next, zgroups);
   ProfScope prof_(ctx, "k_key_product", (uint64_t)items * next);
+  const bool halves = ctx->P.below_2_60;
 #define HC_KP(D)                                                                                                \
   case D:                                                                                                       \
-    k_key_product_t<D><<<g, kT, 0, ctx->stream>>>(ext, ext_item_stride, key, acc, acc_item_stride, next,      \
-                                                  ctx->P.nchain(), ctx->ext_map_of(level), items, digit_src, \
-                                                  ctx->P.alpha, level + 1, ctx->tab);                          \
+    if (halves)                                                                                                 \
+      k_key_product_t<D, true><<<g, kT, 0, ctx->stream>>>(ext, ext_item_stride, key, acc, acc_item_stride,    \
+                                                          next, ctx->P.nchain(), ctx->ext_map_of(level), items, \
+                                                          digit_src, ctx->P.alpha, level + 1, ctx->tab);       \
+    else                                                                                                        \
+      k_key_product_t<D, false><<<g, kT, 0, ctx->stream>>>(ext, ext_item_stride, key, acc, acc_item_stride,   \
+                                                           next, ctx->P.nchain(), ctx->ext_map_of(level),      \
+                                                           items, digit_src, ctx->P.alpha, level + 1, ctx->tab); \
     break;
   switch (dnum) {
     HC_KP(1) HC_KP(2) HC_KP(3) HC_KP(4) HC_KP(5) HC_KP(6) HC_KP(7) HC_KP(8)

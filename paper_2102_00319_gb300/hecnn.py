@@ -39,7 +39,8 @@ EXPORTS = [
     "hc_relin", "hc_rescale", "hc_drop_to_level", "hc_rotate", "hc_rotate_hoisted",
     "hc_mul_relin_rescale_batch", "hc_enc_conv2d", "hc_enc_poly_act", "hc_enc_pool", "hc_enc_fc",
     "hc_relin_noalloc", "hc_graph_begin", "hc_graph_end", "hc_graph_launch", "hc_graph_destroy",
-    "hc_enc_conv2d_single_batch", "hc_enc_fc_rotsum",
+    "hc_enc_conv2d_single_batch", "hc_enc_fc_rotsum", "hc_ct_import_batch", "hc_ct_export_batch",
+    "hc_mul_relin_rescale_host",
 ]
 
 
@@ -110,6 +111,10 @@ def load(path: str = LIB_PATH):
         "hc_ct_export": (c_int, [vp, vp, ctypes.POINTER(u64), ctypes.c_size_t, ctypes.POINTER(CtMeta)]),
         "hc_ct_import": (c_int, [vp, ctypes.POINTER(u64), ctypes.POINTER(CtMeta), pp]),
         "hc_ct_meta_of": (c_int, [vp, ctypes.POINTER(CtMeta)]),
+        "hc_ct_import_batch": (c_int, [vp, pp, ctypes.POINTER(CtMeta), c_int, pp]),
+        "hc_ct_export_batch": (c_int, [vp, pp, c_int, pp, ctypes.POINTER(ctypes.c_size_t)]),
+        "hc_mul_relin_rescale_host": (c_int, [vp, vp, pp, ctypes.POINTER(CtMeta), pp, ctypes.POINTER(CtMeta), c_int,
+                                              c_int, pp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(CtMeta)]),
         "hc_ct_destroy": (None, [vp]),
         "hc_add": (c_int, [vp, vp, vp, pp]), "hc_sub": (c_int, [vp, vp, vp, pp]),
         "hc_add_const": (c_int, [vp, vp, dbl, pp]),
@@ -415,6 +420,58 @@ def hc_ct_import(ctx, data, level, degree, scale) -> Ciphertext:
     out = _out()
     _check(ctx, load().hc_ct_import(ctx.ptr, _u64p(d), ctypes.byref(meta), ctypes.byref(out)))
     return Ciphertext(out.value, ctx)
+
+
+def hc_ct_import_batch(ctx, arrays, metas):
+    """arrays: C-contiguous uint64 arrays [degree+1][level+1][N] (pinned for
+    asynchronous copies); metas: (level, degree, scale) per ciphertext."""
+    n = len(arrays)
+    if len(metas) != n:
+        raise ValueError("one meta per array")
+    for a, (lv, dg, _) in zip(arrays, metas):
+        if a.dtype != np.uint64 or not a.flags.c_contiguous or a.size != (dg + 1) * (lv + 1) * ctx.n:
+            raise ValueError("each array must be C-contiguous uint64 of (degree+1)*(level+1)*N words")
+    ptrs = (ctypes.c_void_p * max(1, n))(*[a.ctypes.data for a in arrays])
+    m = (CtMeta * max(1, n))(*[CtMeta(lv, dg, float(sc)) for lv, dg, sc in metas])
+    outs = _outs(n)
+    _check(ctx, load().hc_ct_import_batch(ctx.ptr, ptrs, m, n, outs))
+    return _wrap_outs(ctx, outs, n)
+
+
+def hc_ct_export_batch(ctx, cts, arrays):
+    """Writes each ciphertext (coefficient form) into the matching uint64 array."""
+    n = len(cts)
+    if len(arrays) != n or any(a.dtype != np.uint64 or not a.flags.c_contiguous for a in arrays):
+        raise ValueError("one C-contiguous uint64 array per ciphertext")
+    ptrs = (ctypes.c_void_p * max(1, n))(*[a.ctypes.data for a in arrays])
+    caps = (ctypes.c_size_t * max(1, n))(*[a.size for a in arrays])
+    _check(ctx, load().hc_ct_export_batch(ctx.ptr, _ptr_array(cts), n, ptrs, caps))
+
+
+def hc_mul_relin_rescale_host(ctx, evk, a_arrays, a_metas, b_arrays, b_metas, out_arrays, chunk=0):
+    """Host-to-host batch: a_arrays/b_arrays are C-contiguous uint64
+    [2][level+1][N] coefficient-form ciphertexts with (level, degree, scale)
+    metas; out_arrays receive [2][level][N].  Returns the output metas."""
+    n = len(a_arrays)
+    if not (len(b_arrays) == len(a_metas) == len(b_metas) == len(out_arrays) == n):
+        raise ValueError("one entry per pair in every list")
+    for a, (lv, dg, _) in zip(list(a_arrays) + list(b_arrays), list(a_metas) + list(b_metas)):
+        if a.dtype != np.uint64 or not a.flags.c_contiguous or a.size != (dg + 1) * (lv + 1) * ctx.n:
+            raise ValueError("inputs must be C-contiguous uint64 of (degree+1)*(level+1)*N words")
+    if any(o.dtype != np.uint64 or not o.flags.c_contiguous or not o.flags.writeable for o in out_arrays):
+        raise ValueError("outputs must be writeable C-contiguous uint64 arrays")
+
+    def ptrs(arrs):
+        return (ctypes.c_void_p * max(1, n))(*[x.ctypes.data for x in arrs])
+
+    def metas(ms):
+        return (CtMeta * max(1, n))(*[CtMeta(lv, dg, float(sc)) for lv, dg, sc in ms])
+
+    caps = (ctypes.c_size_t * max(1, n))(*[o.size for o in out_arrays])
+    out_m = (CtMeta * max(1, n))()
+    _check(ctx, load().hc_mul_relin_rescale_host(ctx.ptr, evk.ptr, ptrs(a_arrays), metas(a_metas), ptrs(b_arrays),
+                                                 metas(b_metas), n, int(chunk), ptrs(out_arrays), caps, out_m))
+    return [out_m[i] for i in range(n)]
 
 
 def _unary(name, ctx, *args):

@@ -56,6 +56,58 @@ def test_import_export_roundtrip(pair):
     assert np.array_equal(back, data) and meta.level == 3
 
 
+def test_batch_import_export_match_single(pair):
+    """The batched import/export calls give the single calls' results (mixed
+    levels and degrees in one batch) and reject an out-of-range residue."""
+    r = np.random.Generator(np.random.PCG64(77))
+    n, q = pair.op.N, pair.op.q
+    arrays, metas = [], []
+    for lv, dg in [(3, 1), (1, 2), (3, 1), (0, 1)]:
+        a = np.stack([np.stack([r.integers(0, q[j], n, dtype=np.uint64) for j in range(lv + 1)])
+                      for _ in range(dg + 1)])
+        arrays.append(np.ascontiguousarray(a))
+        metas.append((lv, dg, 2.0 ** 40))
+    cts = H.hc_ct_import_batch(pair.ctx, arrays, metas)
+    singles = [H.hc_ct_import(pair.ctx, a, lv, dg, sc) for a, (lv, dg, sc) in zip(arrays, metas)]
+    outs = [np.zeros_like(a) for a in arrays]
+    H.hc_ct_export_batch(pair.ctx, cts, outs)
+    for c, s1, a, o in zip(cts, singles, arrays, outs):
+        np.testing.assert_array_equal(o, a)
+        np.testing.assert_array_equal(H.hc_ct_export(pair.ctx, s1)[0], a)
+        m = c.meta()
+        assert (m.level, m.degree) == (s1.meta().level, s1.meta().degree)
+    bad = [a.copy() for a in arrays]
+    bad[2][1, 0, 5] = np.uint64(q[0])
+    with pytest.raises(H.HcError):
+        H.hc_ct_import_batch(pair.ctx, bad, metas)
+
+
+def test_host_pipeline_matches_device_batch(pair):
+    """The host-to-host pipelined call gives, word for word, the exported
+    results of the device-resident batch call, for a ragged last chunk and
+    for the automatic chunking; an out-of-range input residue is rejected."""
+    op = pair.op
+    lv, n = 3, 5
+    ga = [pair.encrypt_values(W.slot_values(60 + i, op.K), level=lv, nonce=600 + i)[0] for i in range(n)]
+    gb = [pair.encrypt_values(W.slot_values(70 + i, op.K), level=lv, nonce=700 + i)[0] for i in range(n)]
+    want = [H.hc_ct_export(pair.ctx, c)[0] for c in H.hc_mul_relin_rescale_batch(pair.ctx, pair.g_evk, ga, gb)]
+    a_arr = [H.hc_ct_export(pair.ctx, c)[0] for c in ga]
+    b_arr = [H.hc_ct_export(pair.ctx, c)[0] for c in gb]
+    a_m = [(lv, 1, c.meta().scale) for c in ga]
+    b_m = [(lv, 1, c.meta().scale) for c in gb]
+    for chunk in (2, 0, 7):
+        outs = [np.zeros((2, lv, op.N), dtype=np.uint64) for _ in range(n)]
+        metas = H.hc_mul_relin_rescale_host(pair.ctx, pair.g_evk, a_arr, a_m, b_arr, b_m, outs, chunk=chunk)
+        for o, w, m in zip(outs, want, metas):
+            np.testing.assert_array_equal(o, w)
+            assert (m.level, m.degree) == (lv - 1, 1)
+    bad = [a.copy() for a in a_arr]
+    bad[4][0, 1, 3] = np.uint64(op.q[1])
+    outs = [np.zeros((2, lv, op.N), dtype=np.uint64) for _ in range(n)]
+    with pytest.raises(H.HcError):
+        H.hc_mul_relin_rescale_host(pair.ctx, pair.g_evk, bad, a_m, b_arr, b_m, outs, chunk=2)
+
+
 def test_import_rejects_out_of_range(pair):
     data = np.zeros((2, 1, pair.op.N), dtype=np.uint64)
     data[1, 0, 7] = pair.op.q[0]
@@ -81,6 +133,22 @@ def test_mul_relin_rescale_bit_exact(pair):
         pair.assert_same(gs, os_, "rescale l=%d" % lv)
         got = pair.decrypt_gpu(gs)
         assert np.max(np.abs(got - za * zb)) < 2.0 ** -15
+
+
+def test_mul_relin_rescale_61bit_primes():
+    """61-bit primes leave the 30-bit-halves basis conversions and key
+    product for their 128-bit carry-chained form: both stay bit-exact."""
+    from hc_pair import Pair
+    p = Pair(10, [61, 61, 61, 61], [61, 61], 40, seed=13)
+    op = p.op
+    za, zb = W.slot_values(11, op.K), W.slot_values(12, op.K)
+    ga, oa = p.encrypt(p.encode_int(za), nonce=1)
+    gb, ob = p.encrypt(p.encode_int(zb), nonce=2)
+    gs = H.hc_mul_relin_rescale_batch(p.ctx, p.g_evk, [ga], [gb])[0]
+    os_ = ckks.rescale(op, ckks.relin(op, p.o_evk, ckks.mul(op, oa, ob)))
+    p.assert_same(gs, os_, "61-bit mul+relin+rescale")
+    gr = H.hc_relin(p.ctx, p.g_evk, H.hc_mul(p.ctx, ga, gb))
+    p.assert_same(gr, ckks.relin(op, p.o_evk, ckks.mul(op, oa, ob)), "61-bit relin")
 
 
 def test_rescale_degree2_and_level_errors(pair):
