@@ -535,7 +535,9 @@ void build_tables(hc_ctx* ctx) {
     ninv[c] = hch::invmod((u64)n % q, q);
     ninv_sh[c] = hch::shoup_of(ninv[c], q);
     const u64 r64 = (u64)((((unsigned __int128)1) << 64) % q);
-    mods[c] = DMod{q, r64, hch::shoup_of(r64, q), hch::shoup_of(1, q)};
+    u64 qinv = q;  // Newton's iteration for q^{-1} mod 2^64 (q odd: q q = 1 mod 8)
+    for (int it = 0; it < 5; ++it) qinv *= 2 - q * qinv;
+    mods[c] = DMod{q, r64, hch::shoup_of(r64, q), hch::shoup_of(1, q), qinv};
   }
   auto put = [&](const void* src, size_t bytes) {
     void* d = nullptr;
@@ -745,6 +747,22 @@ u64 galois_elt(const hc_params& P, long long r) {
 }
 
 // Switching key for s' (NTT form over the whole chain) -> s.
+// Multiplies every limb of a switching key ([npoly][chain][N]) by 2^64 mod q
+// (into Montgomery form) or by its inverse (back), in place.
+void key_scale(hc_ctx* ctx, u64* key, int npoly, bool inverse, std::vector<BufPtr>& keep) {
+  const int nc = ctx->P.nchain();
+  std::vector<u64> sc(2 * nc);
+  for (int t = 0; t < nc; ++t) {
+    const u64 q = ctx->P.chain[t];
+    const u64 r = (u64)(((unsigned __int128)1 << 64) % q);
+    sc[t] = inverse ? hch::invmod(r, q) : r;
+    sc[nc + t] = hch::shoup_of(sc[t], q);
+  }
+  std::vector<CtRef> rk{CtRef{key, (u64)nc * ctx->P.n}};
+  const CtRef* dk = refs_dev(ctx, rk, keep);
+  launch_scalar(ctx, false, dk, dk, 1, npoly, nc, upload(ctx, sc, keep));
+}
+
 void make_switch_key(hc_ctx* ctx, const u64* s_ntt, const u64* sp_ntt, u64 seed, u64 g, SwitchKeyDev& out) {
   const hc_params& P = ctx->P;
   const int nc = P.nchain(), n = P.n;
@@ -786,6 +804,9 @@ void make_switch_key(hc_ctx* ctx, const u64* s_ntt, const u64* sp_ntt, u64 seed,
     launch_scalar(ctx, false, dt, dsp, 1, 1, nc, upload(ctx, sc, keep));
     launch_ew(ctx, 0, db, db, dt, 1, 1, nc);
   }
+  // stored in Montgomery form (x 2^64 mod q): the key product reduces its
+  // sums with one Montgomery reduction
+  key_scale(ctx, out.buf->ptr, 2 * P.dnum, false, keep);
   HC_CUDA(cudaStreamSynchronize(ctx->stream));
 }
 }  // namespace
@@ -909,7 +930,14 @@ extern "C" int hc_evk_export(hc_ctx* ctx, const hc_evk* evk, uint64_t g, uint64_
       HC_CHECK(it != evk->galois.end(), HC_ERR_NO_KEY, "no such Galois key");
       k = &it->second;
     }
-    export_coeff(ctx, k->buf->ptr, poly, 2 * ctx->P.dnum, nc, nullptr, (u64*)out);
+    // back from the stored Montgomery form, then as any other polynomial
+    std::vector<BufPtr> keep;
+    BufPtr plain = ctx->buffer(2 * poly * ctx->P.dnum);
+    keep.push_back(plain);
+    HC_CUDA(cudaMemcpyAsync(plain->ptr, k->buf->ptr, 2 * poly * ctx->P.dnum * sizeof(u64), cudaMemcpyDeviceToDevice,
+                            ctx->stream));
+    key_scale(ctx, plain->ptr, 2 * ctx->P.dnum, true, keep);
+    export_coeff(ctx, plain->ptr, poly, 2 * ctx->P.dnum, nc, nullptr, (u64*)out);
   });
 }
 

@@ -23,6 +23,7 @@ struct DMod {
   u64 r64;     // 2^64 mod q
   u64 r64_sh;  // floor(r64 * 2^64 / q)
   u64 one_sh;  // floor(2^64 / q)
+  u64 qinv;    // q^{-1} mod 2^64
 };
 
 // Read-only tables of one context.
@@ -127,6 +128,16 @@ __device__ __forceinline__ u64 reduce128_est(U128 x, const DMod& m) {
   s = csub(s, 4 * m.q);
   s = csub(s, 2 * m.q);
   return csub(s, m.q);
+}
+// Montgomery's reduction ("Modular multiplication without trial division",
+// 1985) with R = 2^64: s R^{-1} mod q, fully reduced, for s = hi 2^64 + lo
+// with hi < q.  With m = lo q^{-1} mod 2^64 the low words of s and m q agree,
+// so s - m q = (hi - floor(m q / 2^64)) 2^64 with the bracket in (-q, q).
+// One low and one high 64-bit product: half the multiplier work of
+// reduce128.  Callers fold the factor R into a constant operand.
+__device__ __forceinline__ u64 redc(U128 s, const DMod& m) {
+  const u64 mh = __umul64hi(s.lo * m.qinv, m.q);
+  return s.hi >= mh ? s.hi - mh : s.hi - mh + m.q;
 }
 __device__ __forceinline__ u64 mulm(u64 a, u64 b, const DMod& m) {
   U128 x{a * b, __umul64hi(a, b)};

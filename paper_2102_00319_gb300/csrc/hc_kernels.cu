@@ -199,7 +199,11 @@ __global__ void k_modup_bconv(const u64* xcoef, u64 x_item_stride, u64* ext, u64
   }
 }
 
-// acc[z][k][s] = sum_j ext[z][j][s] * key[j][k][emap[s]]
+// acc[z][k][s] = sum_j ext[z][j][s] * key[j][k][emap[s]].  Switching keys are
+// stored in Montgomery form (key 2^64 mod q), so one Montgomery reduction of
+// the sum gives the plain residue.  Any digit count: the sum is folded (an
+// exact reduction that keeps the factor 2^64) after every 7 terms, so its
+// high word stays below q.
 __global__ void k_key_product(const u64* ext, u64 ext_item_stride, const u64* key, u64* acc,
                               u64 acc_item_stride, int dnum, int next, int nchain, const int* emap,
                               Tables T) {
@@ -212,6 +216,10 @@ __global__ void k_key_product(const u64* ext, u64 ext_item_stride, const u64* ke
   const u64* e = ext + (size_t)z * ext_item_stride + (size_t)s * n + c;
   U128 a0{0, 0}, a1{0, 0};
   for (int j = 0; j < dnum; ++j) {
+    if (j > 0 && j % 7 == 0) {
+      a0 = U128{reduce128(a0, md), 0};
+      a1 = U128{reduce128(a1, md), 0};
+    }
     const u64 y = e[(size_t)j * next * n];
     const u64* kb = key + ((size_t)(2 * j) * nchain + pid) * n + c;
     const u64* ka = key + ((size_t)(2 * j + 1) * nchain + pid) * n + c;
@@ -219,8 +227,8 @@ __global__ void k_key_product(const u64* ext, u64 ext_item_stride, const u64* ke
     mac(a1, y, *ka);
   }
   u64* o = acc + (size_t)z * acc_item_stride + (size_t)s * n + c;
-  o[0] = reduce128(a0, md);
-  o[(size_t)next * n] = reduce128(a1, md);
+  o[0] = redc(a0, md);
+  o[(size_t)next * n] = redc(a1, md);
 }
 
 // ModDown conversion P -> Q_level of both polys.
@@ -621,10 +629,14 @@ __global__ void __launch_bounds__(kT) k_modup_bconv_h(const u64* xcoef, u64 x_it
                                                        u64 ext_item_stride, const u64* cst, int d0, int next,
                                                        const int* emap, Tables T) {
   extern __shared__ u64 sh[];
-  uint2* hm = reinterpret_cast<uint2*>(sh);  // [next][NS]
+  uint2* hm = reinterpret_cast<uint2*>(sh);  // [next][NS], Montgomery form
   DMod* md = (DMod*)(sh + next * NS);        // [next]
-  for (int e = threadIdx.x; e < next * NS; e += blockDim.x) hm[e] = halves30(cst[2 * NS + e]);
   for (int t = threadIdx.x; t < next; t += blockDim.x) md[t] = T.mods[emap[t]];
+  __syncthreads();
+  for (int e = threadIdx.x; e < next * NS; e += blockDim.x) {
+    const DMod& mt = md[e / NS];
+    hm[e] = halves30(shoup(cst[2 * NS + e], mt.r64, mt.r64_sh, mt.q));  // h 2^64 mod q_t
+  }
   __syncthreads();
   const int n = 1 << T.log_n;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -644,7 +656,7 @@ __global__ void __launch_bounds__(kT) k_modup_bconv_h(const u64* xcoef, u64 x_it
     Acc30 acc{0, 0, 0};
 #pragma unroll
     for (int i = 0; i < NS; ++i) mac30(acc, vl[i], vh[i], hm[t * NS + i]);
-    y[(size_t)t * n + c] = reduce128(acc30_value(acc), md[t]);
+    y[(size_t)t * n + c] = redc(acc30_value(acc), md[t]);  // sum < 8 2^60 q_t: high word < q_t
   }
 }
 
@@ -654,10 +666,14 @@ __global__ void __launch_bounds__(kT) k_moddown_bconv_h(const u64* src, u64 src_
                                                          u64* zq, u64 z_item_stride, const u64* cst, int nq, int L,
                                                          Tables T) {
   extern __shared__ u64 sh[];
-  uint2* hm = reinterpret_cast<uint2*>(sh);  // [nq][ALPHA]
+  uint2* hm = reinterpret_cast<uint2*>(sh);  // [nq][ALPHA], Montgomery form
   DMod* md = (DMod*)(sh + nq * ALPHA);       // [nq]
-  for (int e = threadIdx.x; e < nq * ALPHA; e += blockDim.x) hm[e] = halves30(cst[2 * ALPHA + e]);
   for (int t = threadIdx.x; t < nq; t += blockDim.x) md[t] = T.mods[t];
+  __syncthreads();
+  for (int e = threadIdx.x; e < nq * ALPHA; e += blockDim.x) {
+    const DMod& mt = md[e / ALPHA];
+    hm[e] = halves30(shoup(cst[2 * ALPHA + e], mt.r64, mt.r64_sh, mt.q));
+  }
   __syncthreads();
   const int n = 1 << T.log_n;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -676,7 +692,7 @@ __global__ void __launch_bounds__(kT) k_moddown_bconv_h(const u64* src, u64 src_
     Acc30 acc{0, 0, 0};
 #pragma unroll
     for (int i = 0; i < ALPHA; ++i) mac30(acc, vl[i], vh[i], hm[t * ALPHA + i]);
-    out[(size_t)t * n + c] = reduce128(acc30_value(acc), md[t]);
+    out[(size_t)t * n + c] = redc(acc30_value(acc), md[t]);
   }
 }
 
@@ -743,8 +759,8 @@ __global__ void __launch_bounds__(kT) k_key_product_t(const u64* ext, u64 ext_it
         mac30(a0, yl, yh, halves30(kb[j]));
         mac30(a1, yl, yh, halves30(ka[j]));
       }
-      o[0] = reduce128(acc30_value(a0), md);
-      o[(size_t)next * n] = reduce128(acc30_value(a1), md);
+      o[0] = redc(acc30_value(a0), md);  // keys in Montgomery form; sum < 8 q^2
+      o[(size_t)next * n] = redc(acc30_value(a1), md);
     } else {
       U128 a0{0, 0}, a1{0, 0};
 #pragma unroll
@@ -753,8 +769,8 @@ __global__ void __launch_bounds__(kT) k_key_product_t(const u64* ext, u64 ext_it
         mac(a0, y, kb[j]);
         mac(a1, y, ka[j]);
       }
-      o[0] = reduce128(a0, md);
-      o[(size_t)next * n] = reduce128(a1, md);
+      o[0] = redc(a0, md);
+      o[(size_t)next * n] = redc(a1, md);
     }
   }
 }
