@@ -236,6 +236,23 @@ NCU_TRAFFIC_PER_UNIT = {
 }
 
 
+# Integer-multiplier roofline of the NTT passes: 64-bit low and high
+# products per SM per clock on GB300, measured by
+# paper_2102_00319_gb300/probes/intmul_throughput.cu.  A Shoup butterfly
+# takes two low products and one high product.
+LO64_PER_SM_CLK = 14.4
+HI64_PER_SM_CLK = 6.6
+BUTTERFLIES_PER_SM_CLK = 1.0 / (2.0 / LO64_PER_SM_CLK + 1.0 / HI64_PER_SM_CLK)
+
+
+def butterflies_per_unit(name, n):
+    """Butterflies of one limb in one NTT pass (the column pass takes the first
+    floor(log N / 2) stages, the row pass the rest)."""
+    log_n = n.bit_length() - 1
+    stages = log_n // 2 if "cols" in name else log_n - log_n // 2
+    return stages * (n // 2)
+
+
 def bytes_per_unit(name, n, dnum):
     limb = 8 * n
     if name.startswith("ntt_"):
@@ -763,11 +780,25 @@ def run_gpu(args, rank, world, local):
     peak = peaks.get("hbm_gbs", 6800.0)
     tpu = NCU_TRAFFIC_PER_UNIT.get(dom)
     traffic = tpu * units / max(cnt, 1) if tpu else None
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                "bytes_per_launch": alg_bytes / max(cnt, 1), "avg_launch_us": 1000.0 * tot / max(cnt, 1),
-                "share_of_step": tot / ms}
+    hbm = {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    if dom.startswith("ntt_"):
+        # bound by the integer multiplier, not by DRAM: butterflies per second
+        # against the multiplier's rate at the SM clock sampled in the timed region
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+        peak_alu = BUTTERFLIES_PER_SM_CLK * sms * mhz * 1e6 / 1e9
+        got = units * butterflies_per_unit(dom, n) / (tot / 1000.0) / 1e9
+        roofline = {"bound": "alu", "kernel": dom, "achieved": got, "peak": peak_alu, "unit": "Gbutterfly/s",
+                    "frac": got / peak_alu, "traffic": traffic,
+                    "peak_source": "derived from measured 64-bit multiply rates: %.2f Shoup butterflies/SM/clk"
+                                   " x %d SMs x %.0f MHz" % (BUTTERFLIES_PER_SM_CLK, sms, mhz),
+                    "hbm": hbm}
+    else:
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": traffic, "peak_source": hbm["peak_source"]}
+    roofline.update({"bytes_per_launch": alg_bytes / max(cnt, 1), "avg_launch_us": 1000.0 * tot / max(cnt, 1),
+                     "share_of_step": tot / ms})
     kern_summary = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / ms, 4)}
                     for k, v in sorted(kernels.items(), key=lambda kv: -kv[1][1])}
     line = {
