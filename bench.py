@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--batch", type=int, default=64, help="ciphertext pairs per step")
+    ap.add_argument("--no-graph", action="store_true", help="time the eager step only")
+    ap.add_argument("--graph-arena-gib", type=int, default=16, help="device arena of the captured step")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--e2e-chunk", type=int, default=0, help="pairs per pipeline chunk of the host call (0: auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -660,7 +662,9 @@ def run_gpu(args, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    stream = torch.cuda.current_stream()
+    # a stream of our own (the legacy default stream cannot be captured into a graph)
+    stream = torch.cuda.Stream(device=local)
+    torch.cuda.set_stream(stream)
     ps = W.DEEP_N16
     params = H.hc_params_create(ps.log_n, list(ps.q_bits), list(ps.p_bits), ps.log2_scale)
     ctx = H.hc_ctx_create(params, local, stream.cuda_stream)
@@ -716,7 +720,33 @@ def run_gpu(args, rank, world, local):
         kernels[name] = (cnt, tot, units)
     H.hc_profile_enable(ctx, False)
     t_max = max_over_ranks(ms / 1000.0, device="cuda")
-    value = Bn * args.steps * world / t_max
+    eager_value = Bn * args.steps * world / t_max
+
+    # ---------------- the same step captured once into a CUDA graph and replayed
+    # (the arena holds every temporary and output of one step; each replay
+    # recomputes all of them from the resident inputs)
+    graph_value, graph_same = None, None
+    if not args.no_graph:
+        H.hc_graph_begin([ctx], args.graph_arena_gib << 30)
+        g_outs = step()
+        graph = H.hc_graph_end([ctx])
+        for _ in range(args.warmup):
+            H.hc_graph_launch(graph)
+        barrier()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(args.steps):
+            H.hc_graph_launch(graph)
+        g1.record(stream)
+        barrier()
+        graph_value = Bn * args.steps * world / max_over_ranks(g0.elapsed_time(g1) / 1000.0, device="cuda")
+        ref = step()
+        graph_same = all(np.array_equal(H.hc_ct_export(ctx, g_outs[i])[0], H.hc_ct_export(ctx, ref[i])[0])
+                         for i in (0, Bn - 1))
+        assert graph_same, "graph replay differs from the eager step"
+        del g_outs, ref  # handles into the arena go before the graph that owns it
+        del graph
+    value = graph_value if graph_value is not None else eager_value
 
     # ---------------- the same work as one ABI call per operation (per-op form)
     def per_op_step():
@@ -803,13 +833,16 @@ def run_gpu(args, rank, world, local):
                     for k, v in sorted(kernels.items(), key=lambda kv: -kv[1][1])}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": 1000.0 * Bn * world / value, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": "deep_n16_l20", "N": n, "L": L, "alpha": alpha, "dnum": dnum, "batch": Bn,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (%.2f GB of resident ciphertexts)" % (2 * Bn * 2 * (L + 1) * n * 8 / 1e9)},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches, "roofline": roofline, "clocks": clk, "kernels": kern_summary,
+        "forms": {"graph": graph_value, "eager": eager_value, "unit": UNIT,
+                  "graph_bit_identical_to_eager": graph_same,
+                  "value_is": "graph" if graph_value is not None else "eager"},
         "per_op": {"value": per_op_value, "unit": UNIT,
                    "form": "hc_mul, hc_relin, hc_rescale per pair (unfused relin and rescale, one pair per call)"},
         "check": {"max_slot_error": err},
