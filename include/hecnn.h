@@ -94,6 +94,9 @@ int hc_params_cdt(const hc_params *p, uint64_t *out, int cap);
 /* Optional allocator: alloc(bytes, stream, user) returns device memory
  * usable on `stream` (or NULL), free(ptr, stream, user) releases it in
  * stream order. */
+/* Device memory callbacks.  Returned blocks must be 16-byte aligned (the
+ * kernels move limbs in 16-byte vectors); a misaligned block is freed and
+ * the call fails with HC_ERR_INVALID. */
 typedef struct hc_allocator {
   void *(*alloc)(size_t bytes, void *stream, void *user);
   void (*free)(void *ptr, void *stream, void *user);

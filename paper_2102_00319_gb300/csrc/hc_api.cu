@@ -24,6 +24,10 @@ u64* hc_ctx::alloc_words(size_t words) {
     }
   }
   if (!p) throw HcError{HC_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed"};
+  if (((uintptr_t)p & 15) != 0) {  // kernels move limbs in 16-byte vectors
+    if (user_alloc) alloc.free(p, (void*)stream, alloc.user);
+    throw HcError{HC_ERR_INVALID, "allocator returned memory not aligned to 16 bytes"};
+  }
   return (u64*)p;
 }
 
@@ -223,11 +227,11 @@ void keyswitch_batch(hc_ctx* ctx, const u64* key, int level, const std::vector<C
     xin.refs = xr;
     xin.npoly = 1;
     xin.nlimb = nq;
-    launch_ntt_from(ctx, limbset_base(xc, x_is, 0, 1, nq, 0, nullptr), &xin, m, true);
+    launch_ntt_from(ctx, limbset_base(xc, x_is, 0, 1, nq, 0, nullptr), &xin, m, true, false);
     modup_digits(ctx, level, xs, xc, x_is, ext, ext_is, m, keep);
     launch_key_product_batched(ctx, level, ext, ext_is, key, acc, acc_is, m, dnum <= 8 ? xr : nullptr);
     // ModDown
-    launch_ntt(ctx, limbset_base(acc, acc_is, ext_words, 2, alpha, nq, emap), m, true);
+    launch_ntt(ctx, limbset_base(acc, acc_is, ext_words, 2, alpha, nq, emap), m, true, false);
     launch_moddown_bconv_fast(ctx, level, acc + (size_t)nq * n, acc_is, zq, z_is, m);
     launch_ntt(ctx, limbset_base(zq, z_is, (u64)nq * n, 2, nq, 0, nullptr), m, false);
     launch_moddown_combine(ctx, level, acc, acc_is, zq, z_is, b0, b1, orr, m);
@@ -279,11 +283,11 @@ void keyswitch_rescale_batch(hc_ctx* ctx, const u64* key, int level, const std::
     xin.npoly = 1;
     xin.nlimb = nq;
     const LimbSet xcs = limbset_base(xc, x_is, 0, 1, nq, 0, nullptr);
-    launch_ntt_from(ctx, xcs, &xin, m, true);
+    launch_ntt_from(ctx, xcs, &xin, m, true, false);
     modup_digits(ctx, level, xs, xc, x_is, ext, ext_is, m, keep);
     // the digits' own slots are read from x itself (specialised key product)
     launch_key_product_batched(ctx, level, ext, ext_is, key, acc, acc_is, m, dnum <= 8 ? xr : nullptr);
-    launch_ntt(ctx, limbset_base(acc, acc_is, ext_words, 2, alpha, nq, emap), m, true);
+    launch_ntt(ctx, limbset_base(acc, acc_is, ext_words, 2, alpha, nq, emap), m, true, false);
     launch_moddown_bconv_fast(ctx, level, acc + (size_t)nq * n, acc_is, zq, z_is, m);
     launch_ksr_last(ctx, level, acc, acc_is, b0, b1, tl, m);
     launch_ntt(ctx, limbset_base(tl, 2 * (u64)n, (u64)n, 2, 1, 0, ident_map(ctx) + level), m, true);
@@ -573,7 +577,9 @@ void build_tables(hc_ctx* ctx) {
         u64 prod = 1;
         for (int k = 0; k < ns; ++k)
           if (k != i) prod = hch::mulmod(prod, P.chain[d0 + k] % qi, qi);
-        hinv[i] = hch::invmod(prod, qi);
+        // N^{-1} folded in: the conversion's input comes from an inverse NTT
+        // without its N^{-1} factor
+        hinv[i] = hch::mulmod(hch::invmod(prod, qi), hch::invmod((u64)P.n % qi, qi), qi);
       }
       for (int i = 0; i < ns; ++i) ks.push_back(hinv[i]);
       for (int i = 0; i < ns; ++i) ks.push_back(hch::shoup_of(hinv[i], P.chain[d0 + i]));
@@ -604,7 +610,7 @@ void build_tables(hc_ctx* ctx) {
       u64 prod = 1;
       for (int m = 0; m < alpha; ++m)
         if (m != k) prod = hch::mulmod(prod, P.chain[L + 1 + m] % pk, pk);
-      hinv[k] = hch::invmod(prod, pk);
+      hinv[k] = hch::mulmod(hch::invmod(prod, pk), hch::invmod((u64)P.n % pk, pk), pk);  // N^{-1} folded in
     }
     for (int k = 0; k < alpha; ++k) ks.push_back(hinv[k]);
     for (int k = 0; k < alpha; ++k) ks.push_back(hch::shoup_of(hinv[k], P.chain[L + 1 + k]));
@@ -1364,7 +1370,7 @@ std::vector<hc_ct*> rotate_one(hc_ctx* ctx, const hc_evk* evk, const hc_ct* x, c
   const CtRef* xcr = refs_dev(ctx, {CtRef{xc, 0}}, keep);
   const CtRef* c1r = refs_dev(ctx, {CtRef{x->data + x->stride, 0}}, keep);
   launch_ew(ctx, 3, xcr, c1r, nullptr, 1, 1, nq);
-  launch_ntt(ctx, limbset_base(xc, 0, 0, 1, nq, 0, nullptr), 1, true);
+  launch_ntt(ctx, limbset_base(xc, 0, 0, 1, nq, 0, nullptr), 1, true, false);
   for (int j = 0; j < dnum; ++j) {
     const int d0 = j * alpha, d1 = std::min(d0 + alpha, nq);
     u64* ej = ext + (size_t)j * ext_words;
@@ -1386,7 +1392,7 @@ std::vector<hc_ct*> rotate_one(hc_ctx* ctx, const hc_evk* evk, const hc_ct* x, c
     const CtRef* dst = refs_dev(ctx, {CtRef{extg, (u64)ext_words}}, keep);
     launch_automorph(ctx, dst, src, 1, dnum, next, gs[i]);
     launch_key_product_batched(ctx, level, extg, 0, evk->galois.at(gs[i]).buf->ptr, acc, 0, 1);
-    launch_ntt(ctx, limbset_base(acc, 0, ext_words, 2, alpha, nq, emap), 1, true);
+    launch_ntt(ctx, limbset_base(acc, 0, ext_words, 2, alpha, nq, emap), 1, true, false);
     launch_moddown_bconv_fast(ctx, level, acc + (size_t)nq * n, 0, zq, 0, 1);
     launch_ntt(ctx, limbset_base(zq, 0, (u64)nq * n, 2, nq, 0, nullptr), 1, false);
     const CtRef* c0d = refs_dev(ctx, {CtRef{c0g, 0}}, keep);

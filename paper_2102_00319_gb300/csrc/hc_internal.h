@@ -183,10 +183,14 @@ T* upload(hc_ctx* ctx, const std::vector<T>& v, std::vector<BufPtr>& keep) {
 
 // --------------------------------------------------------------- launchers
 // NTT (forward) / inverse NTT of every limb of a LimbSet, `items` items.
-void launch_ntt(hc_ctx* ctx, const LimbSet& s, int items, bool inverse);
+// scale = false (inverse only) leaves out the factor N^{-1}: the result is N
+// times the inverse transform, for consumers that fold N^{-1} into their
+// own constants (the basis conversions of ModUp and ModDown).
+void launch_ntt(hc_ctx* ctx, const LimbSet& s, int items, bool inverse, bool scale = true);
 // Out-of-place: the first pass reads limb (item, poly, limb) from `in`
 // (same poly/limb counts as s), the result lands in s.
-void launch_ntt_from(hc_ctx* ctx, const LimbSet& s, const LimbSet* in, int items, bool inverse);
+void launch_ntt_from(hc_ctx* ctx, const LimbSet& s, const LimbSet* in, int items, bool inverse,
+                     bool scale = true);
 
 // Samplers writing coefficient-form limbs dst + r*N for chain indices ids[r].
 void launch_sample_ternary(hc_ctx* ctx, u64 seed, u64 tag, u64* dst, const int* ids, int nl);

@@ -110,7 +110,7 @@ extern "C" int hc_relin_noalloc(hc_ctx* ctx, const hc_evk* evk, const hc_ct* x, 
     s.base = xc;
     s.npoly = 1;
     s.nlimb = nq;
-    launch_ntt(ctx, s, 1, true);
+    launch_ntt(ctx, s, 1, true, false);  // N^{-1} is folded into the conversion constants
     // ModUp per digit
     for (int j = 0; j < dnum; ++j) {
       const int d0 = j * alpha, d1 = std::min(d0 + alpha, nq);
@@ -139,7 +139,7 @@ extern "C" int hc_relin_noalloc(hc_ctx* ctx, const hc_evk* evk, const hc_ct* x, 
     a.nlimb = alpha;
     a.l0 = nq;
     a.prime_map = emap;
-    launch_ntt(ctx, a, 1, true);
+    launch_ntt(ctx, a, 1, true, false);
     launch_moddown_bconv(ctx, level, acc + (size_t)nq * n, 0, zq, 0, 1);
     LimbSet z{};
     z.base = zq;

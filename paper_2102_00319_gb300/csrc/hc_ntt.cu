@@ -103,7 +103,7 @@ __device__ __forceinline__ const u64* input_limb(const LimbSet& s, const LimbSet
 // Column pass: stages 0..N1-1 (forward) over R = 2^N1 rows (N1 = K1 + K2) of
 // TC = 2^TCL columns starting at blockIdx.x * TC.  Shared tile [row][col].
 template <bool INV, int LOGN, int K1, int K2, int TCL>
-__global__ void __launch_bounds__(kThreads) k_cols(LimbSet s, LimbSet in, int use_in, Tables T) {
+__global__ void __launch_bounds__(kThreads) k_cols(LimbSet s, LimbSet in, int use_in, int scale, Tables T) {
   constexpr int N1 = K1 + K2, N2 = LOGN - N1, TC = 1 << TCL;
   extern __shared__ u64 sm[];
   u64* a;
@@ -157,7 +157,8 @@ __global__ void __launch_bounds__(kThreads) k_cols(LimbSet s, LimbSet in, int us
       for (int i = 0; i < (1 << K1); ++i) x[i] = sm[((r0 + (i << K2)) << TCL) + c];
       inv_block<K1, K2 + N2, K1 - 1, LOGN>(x, r0 << N2, tw, q);
 #pragma unroll
-      for (int i = 0; i < (1 << K1); ++i) a[((r0 + (i << K2)) << N2) + c] = reduce4(shoup_lazy(x[i], ni, nis, q), q);
+      for (int i = 0; i < (1 << K1); ++i)
+        a[((r0 + (i << K2)) << N2) + c] = reduce4(scale ? shoup_lazy(x[i], ni, nis, q) : x[i], q);
     }
   }
 }
@@ -191,7 +192,9 @@ __global__ void __launch_bounds__(kThreads) k_rows(LimbSet s, LimbSet in, int us
       for (int i = 0; i < (1 << K1); ++i) sm[sidx(r, r0 + (i << K2))] = x[i];
     }
     __syncthreads();
-    // round 2: 2^K2 adjacent points
+    // round 2: 2^K2 adjacent points; the results go back through shared
+    // memory so that the stores to global memory are row-contiguous across
+    // the warp (measured faster than each thread storing its own points)
     for (u32 w = threadIdx.x; w < (RP << K1); w += kThreads) {
       const u32 r = w >> K1, g = w & ((1 << K1) - 1);
       u64 x[1 << K2];
@@ -204,14 +207,20 @@ __global__ void __launch_bounds__(kThreads) k_rows(LimbSet s, LimbSet in, int us
     __syncthreads();
     for (u32 e = threadIdx.x; e < (RP << N2); e += kThreads) src[e] = sm[sidx(e >> N2, e & (C - 1))];
   } else {
-    for (u32 e = threadIdx.x; e < (RP << N2); e += kThreads) sm[sidx(e >> N2, e & (C - 1))] = srcin[e];
-    __syncthreads();
-    // round A: 2^K2 adjacent points -> stages LOGN-1 .. LOGN-K2
+    // round A: 2^K2 adjacent points read straight from global memory as
+    // 16-byte pairs (a thread's points are contiguous and 16-byte aligned;
+    // measured faster than staging the tile through shared memory)
+    // -> stages LOGN-1 .. LOGN-K2
     for (u32 w = threadIdx.x; w < (RP << K1); w += kThreads) {
       const u32 r = w >> K1, g = w & ((1 << K1) - 1);
       u64 x[1 << K2];
+      const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(srcin + (r << N2) + (g << K2));
 #pragma unroll
-      for (int i = 0; i < (1 << K2); ++i) x[i] = sm[sidx(r, (g << K2) + i)];
+      for (int i = 0; i < (1 << K2); i += 2) {
+        const ulonglong2 v = s2[i >> 1];
+        x[i] = v.x;
+        x[i + 1] = v.y;
+      }
       inv_block<K2, 0, LOGN - 1, LOGN>(x, ((row0 + r) << N2) + (g << K2), tw, q);
 #pragma unroll
       for (int i = 0; i < (1 << K2); ++i) sm[sidx(r, (g << K2) + i)] = x[i];
@@ -257,14 +266,16 @@ struct RowTile {
 };
 
 template <bool INV, int LOGN>
-void launch_pass_cols(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, const LimbSet* in = nullptr) {
+void launch_pass_cols(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, const LimbSet* in = nullptr,
+                      bool scale = true) {
   constexpr int N1 = LOGN / 2, N2 = LOGN - N1;
   using Sp = Split<N1>;
   constexpr int TCL = ColTile<N1, N2>::TCL;
   dim3 grid(1u << (N2 - TCL), ylimbs, items);
   const size_t smem = ((size_t)1 << (N1 + TCL)) * sizeof(u64);
   ProfScope p(ctx, INV ? "ntt_inv_cols" : "ntt_fwd_cols", (uint64_t)ylimbs * items);
-  k_cols<INV, LOGN, Sp::K1, Sp::K2, TCL><<<grid, kThreads, smem, ctx->stream>>>(s, in ? *in : s, in ? 1 : 0, ctx->tab);
+  k_cols<INV, LOGN, Sp::K1, Sp::K2, TCL><<<grid, kThreads, smem, ctx->stream>>>(s, in ? *in : s, in ? 1 : 0, scale ? 1 : 0,
+                                                                                      ctx->tab);
 }
 
 template <bool INV, int LOGN>
@@ -279,32 +290,34 @@ void launch_pass_rows(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, cons
 }
 
 template <int LOGN>
-void ntt_logn(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, bool inverse, const LimbSet* in) {
+void ntt_logn(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, bool inverse, const LimbSet* in, bool scale) {
   if (!inverse) {
     launch_pass_cols<false, LOGN>(ctx, s, items, ylimbs, in);
     launch_pass_rows<false, LOGN>(ctx, s, items, ylimbs);
   } else {
     launch_pass_rows<true, LOGN>(ctx, s, items, ylimbs, in);
-    launch_pass_cols<true, LOGN>(ctx, s, items, ylimbs);
+    launch_pass_cols<true, LOGN>(ctx, s, items, ylimbs, nullptr, scale);
   }
 }
 
 }  // namespace
 
-void launch_ntt(hc_ctx* ctx, const LimbSet& s, int items, bool inverse) { launch_ntt_from(ctx, s, nullptr, items, inverse); }
+void launch_ntt(hc_ctx* ctx, const LimbSet& s, int items, bool inverse, bool scale) {
+  launch_ntt_from(ctx, s, nullptr, items, inverse, scale);
+}
 
-void launch_ntt_from(hc_ctx* ctx, const LimbSet& s, const LimbSet* in, int items, bool inverse) {
+void launch_ntt_from(hc_ctx* ctx, const LimbSet& s, const LimbSet* in, int items, bool inverse, bool scale) {
   if (items <= 0 || s.nlimb <= 0 || s.npoly <= 0) return;
   const int ylimbs = s.npoly * s.nlimb;
   HC_CHECK(ylimbs <= 65535 && items <= 65535, HC_ERR_INVALID, "NTT batch too large");
   switch (ctx->P.log_n) {
-    case 10: ntt_logn<10>(ctx, s, items, ylimbs, inverse, in); break;
-    case 11: ntt_logn<11>(ctx, s, items, ylimbs, inverse, in); break;
-    case 12: ntt_logn<12>(ctx, s, items, ylimbs, inverse, in); break;
-    case 13: ntt_logn<13>(ctx, s, items, ylimbs, inverse, in); break;
-    case 14: ntt_logn<14>(ctx, s, items, ylimbs, inverse, in); break;
-    case 15: ntt_logn<15>(ctx, s, items, ylimbs, inverse, in); break;
-    case 16: ntt_logn<16>(ctx, s, items, ylimbs, inverse, in); break;
+    case 10: ntt_logn<10>(ctx, s, items, ylimbs, inverse, in, scale); break;
+    case 11: ntt_logn<11>(ctx, s, items, ylimbs, inverse, in, scale); break;
+    case 12: ntt_logn<12>(ctx, s, items, ylimbs, inverse, in, scale); break;
+    case 13: ntt_logn<13>(ctx, s, items, ylimbs, inverse, in, scale); break;
+    case 14: ntt_logn<14>(ctx, s, items, ylimbs, inverse, in, scale); break;
+    case 15: ntt_logn<15>(ctx, s, items, ylimbs, inverse, in, scale); break;
+    case 16: ntt_logn<16>(ctx, s, items, ylimbs, inverse, in, scale); break;
     default: throw HcError{HC_ERR_INVALID, "unsupported ring degree"};
   }
   ctx->launches += 2;
