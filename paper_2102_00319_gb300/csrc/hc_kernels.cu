@@ -597,30 +597,46 @@ __global__ void __launch_bounds__(kT) k_modup_bconv_t(const u64* xcoef, u64 x_it
 }
 
 // Exact sum of up to 8 products v_i h_i with v_i, h_i < 2^60, each operand
-// split into 30-bit halves (v = vh 2^30 + vl).  The three partial sums
-// (low x low, the cross terms, high x high) stay below 2^64 -- the cross sum
-// has at most 16 terms of at most (2^30 - 1)^2 -- so the loop is one 32 x 32
-// -> 64-bit multiply-add per partial product with no carry handling; the
-// 128-bit value is assembled once at the end.
+// split into 30-bit halves (v = vh 2^30 + vl, vs = vl + vh < 2^31).  Three
+// 32 x 32 -> 64-bit multiply-adds per term (Karatsuba): lo = sum vl hl,
+// hi = sum vh hh and sm = sum vs hs, each accumulated in 64 bits without
+// carry handling.  lo and hi stay below 2^63; sm may wrap, but the cross
+// sum sm - lo - hi = sum (vl hh + vh hl) is below 16 (2^30 - 1)^2 < 2^64,
+// so it comes out exact modulo 2^64.  The 128-bit value is assembled once.
 struct Acc30 {
-  u64 lo, mid, hi;
+  u64 lo, hi, sm;
+};
+struct Half30 {
+  uint32_t l, h, s;
 };
 constexpr uint32_t kMask30 = (1u << 30) - 1;
-__device__ __forceinline__ void mac30(Acc30& s, uint32_t vl, uint32_t vh, uint2 h) {
-  s.lo += (u64)vl * h.x;
-  s.mid += (u64)vh * h.x;
-  s.mid += (u64)vl * h.y;
-  s.hi += (u64)vh * h.y;
+__device__ __forceinline__ Half30 halves30(u64 v) {
+  const uint32_t l = (uint32_t)v & kMask30, h = (uint32_t)(v >> 30);
+  return Half30{l, h, l + h};
 }
-// lo + mid 2^30 + hi 2^60 as a 128-bit value.
-__device__ __forceinline__ U128 acc30_value(const Acc30& s) {
-  const u64 x = s.lo + (s.mid << 30);
-  const u64 c1 = x < s.lo;
-  const u64 y = x + (s.hi << 60);
+__device__ __forceinline__ uint4 halves30_packed(u64 v) {
+  const Half30 x = halves30(v);
+  return make_uint4(x.l, x.h, x.s, 0u);
+}
+__device__ __forceinline__ void mac30(Acc30& a, const Half30& v, uint4 h) {
+  a.lo += (u64)v.l * h.x;
+  a.hi += (u64)v.h * h.y;
+  a.sm += (u64)v.s * h.z;
+}
+__device__ __forceinline__ void mac30(Acc30& a, const Half30& v, const Half30& h) {
+  a.lo += (u64)v.l * h.l;
+  a.hi += (u64)v.h * h.h;
+  a.sm += (u64)v.s * h.s;
+}
+// lo + mid 2^30 + hi 2^60 as a 128-bit value, mid = sm - lo - hi.
+__device__ __forceinline__ U128 acc30_value(const Acc30& a) {
+  const u64 mid = a.sm - a.lo - a.hi;
+  const u64 x = a.lo + (mid << 30);
+  const u64 c1 = x < a.lo;
+  const u64 y = x + (a.hi << 60);
   const u64 c2 = y < x;
-  return U128{y, (s.mid >> 34) + (s.hi >> 4) + c1 + c2};
+  return U128{y, (mid >> 34) + (a.hi >> 4) + c1 + c2};
 }
-__device__ __forceinline__ uint2 halves30(u64 h) { return make_uint2((uint32_t)h & kMask30, (uint32_t)(h >> 30)); }
 
 // ModUp conversion as k_modup_bconv_t with every prime below 2^60: the
 // constants sit in shared memory as 30-bit halves.
@@ -629,13 +645,13 @@ __global__ void __launch_bounds__(kT) k_modup_bconv_h(const u64* xcoef, u64 x_it
                                                        u64 ext_item_stride, const u64* cst, int d0, int next,
                                                        const int* emap, Tables T) {
   extern __shared__ u64 sh[];
-  uint2* hm = reinterpret_cast<uint2*>(sh);  // [next][NS], Montgomery form
-  DMod* md = (DMod*)(sh + next * NS);        // [next]
+  uint4* hm = reinterpret_cast<uint4*>(sh);  // [next][NS] halves, Montgomery form
+  DMod* md = (DMod*)(sh + 2 * next * NS);    // [next]
   for (int t = threadIdx.x; t < next; t += blockDim.x) md[t] = T.mods[emap[t]];
   __syncthreads();
   for (int e = threadIdx.x; e < next * NS; e += blockDim.x) {
     const DMod& mt = md[e / NS];
-    hm[e] = halves30(shoup(cst[2 * NS + e], mt.r64, mt.r64_sh, mt.q));  // h 2^64 mod q_t
+    hm[e] = halves30_packed(shoup(cst[2 * NS + e], mt.r64, mt.r64_sh, mt.q));  // h 2^64 mod q_t
   }
   __syncthreads();
   const int n = 1 << T.log_n;
@@ -644,18 +660,14 @@ __global__ void __launch_bounds__(kT) k_modup_bconv_h(const u64* xcoef, u64 x_it
   const int z = blockIdx.z;
   const u64* x = xcoef + (size_t)z * x_item_stride;
   u64* y = ext + (size_t)z * ext_item_stride;
-  uint32_t vl[NS], vh[NS];
+  Half30 v[NS];
 #pragma unroll
-  for (int i = 0; i < NS; ++i) {
-    const u64 v = shoup(x[(size_t)(d0 + i) * n + c], cst[i], cst[NS + i], md[d0 + i].q);
-    vl[i] = (uint32_t)v & kMask30;
-    vh[i] = (uint32_t)(v >> 30);
-  }
+  for (int i = 0; i < NS; ++i) v[i] = halves30(shoup(x[(size_t)(d0 + i) * n + c], cst[i], cst[NS + i], md[d0 + i].q));
   for (int t = 0; t < next; ++t) {
     if (t >= d0 && t < d0 + NS) continue;
     Acc30 acc{0, 0, 0};
 #pragma unroll
-    for (int i = 0; i < NS; ++i) mac30(acc, vl[i], vh[i], hm[t * NS + i]);
+    for (int i = 0; i < NS; ++i) mac30(acc, v[i], hm[t * NS + i]);
     y[(size_t)t * n + c] = redc(acc30_value(acc), md[t]);  // sum < 8 2^60 q_t: high word < q_t
   }
 }
@@ -666,13 +678,13 @@ __global__ void __launch_bounds__(kT) k_moddown_bconv_h(const u64* src, u64 src_
                                                          u64* zq, u64 z_item_stride, const u64* cst, int nq, int L,
                                                          Tables T) {
   extern __shared__ u64 sh[];
-  uint2* hm = reinterpret_cast<uint2*>(sh);  // [nq][ALPHA], Montgomery form
-  DMod* md = (DMod*)(sh + nq * ALPHA);       // [nq]
+  uint4* hm = reinterpret_cast<uint4*>(sh);  // [nq][ALPHA] halves, Montgomery form
+  DMod* md = (DMod*)(sh + 2 * nq * ALPHA);   // [nq]
   for (int t = threadIdx.x; t < nq; t += blockDim.x) md[t] = T.mods[t];
   __syncthreads();
   for (int e = threadIdx.x; e < nq * ALPHA; e += blockDim.x) {
     const DMod& mt = md[e / ALPHA];
-    hm[e] = halves30(shoup(cst[2 * ALPHA + e], mt.r64, mt.r64_sh, mt.q));
+    hm[e] = halves30_packed(shoup(cst[2 * ALPHA + e], mt.r64, mt.r64_sh, mt.q));
   }
   __syncthreads();
   const int n = 1 << T.log_n;
@@ -680,18 +692,14 @@ __global__ void __launch_bounds__(kT) k_moddown_bconv_h(const u64* src, u64 src_
   if (c >= n) return;
   const int k = blockIdx.y, z = blockIdx.z;
   const u64* x = src + (size_t)z * src_item_stride + (size_t)k * src_poly_stride;
-  uint32_t vl[ALPHA], vh[ALPHA];
+  Half30 v[ALPHA];
 #pragma unroll
-  for (int i = 0; i < ALPHA; ++i) {
-    const u64 v = shoup(x[(size_t)i * n + c], cst[i], cst[ALPHA + i], T.mods[L + 1 + i].q);
-    vl[i] = (uint32_t)v & kMask30;
-    vh[i] = (uint32_t)(v >> 30);
-  }
+  for (int i = 0; i < ALPHA; ++i) v[i] = halves30(shoup(x[(size_t)i * n + c], cst[i], cst[ALPHA + i], T.mods[L + 1 + i].q));
   u64* out = zq + (size_t)z * z_item_stride + (size_t)k * nq * n;
   for (int t = 0; t < nq; ++t) {
     Acc30 acc{0, 0, 0};
 #pragma unroll
-    for (int i = 0; i < ALPHA; ++i) mac30(acc, vl[i], vh[i], hm[t * ALPHA + i]);
+    for (int i = 0; i < ALPHA; ++i) mac30(acc, v[i], hm[t * ALPHA + i]);
     out[(size_t)t * n + c] = redc(acc30_value(acc), md[t]);
   }
 }
@@ -740,10 +748,15 @@ __global__ void __launch_bounds__(kT) k_key_product_t(const u64* ext, u64 ext_it
   const int pid = emap[s];
   const DMod md = T.mods[pid];
   u64 kb[DNUM], ka[DNUM];
+  Half30 hb[DNUM], ha[DNUM];  // (used by the halves form only)
 #pragma unroll
   for (int j = 0; j < DNUM; ++j) {
     kb[j] = key[((size_t)(2 * j) * nchain + pid) * n + c];
     ka[j] = key[((size_t)(2 * j + 1) * nchain + pid) * n + c];
+    if constexpr (HALVES) {
+      hb[j] = halves30(kb[j]);
+      ha[j] = halves30(ka[j]);
+    }
   }
   const int own = (digit_src && s < nq) ? s / alpha : -1;  // the digit whose block holds slot s
   for (int z = blockIdx.z; z < items; z += gridDim.z) {
@@ -754,10 +767,9 @@ __global__ void __launch_bounds__(kT) k_key_product_t(const u64* ext, u64 ext_it
       Acc30 a0{0, 0, 0}, a1{0, 0, 0};
 #pragma unroll
       for (int j = 0; j < DNUM; ++j) {
-        const u64 y = (j == own) ? digit_src[z].p[(size_t)s * n + c] : e[(size_t)j * next * n];
-        const uint32_t yl = (uint32_t)y & kMask30, yh = (uint32_t)(y >> 30);
-        mac30(a0, yl, yh, halves30(kb[j]));
-        mac30(a1, yl, yh, halves30(ka[j]));
+        const Half30 y = halves30((j == own) ? digit_src[z].p[(size_t)s * n + c] : e[(size_t)j * next * n]);
+        mac30(a0, y, hb[j]);
+        mac30(a1, y, ha[j]);
       }
       o[0] = redc(acc30_value(a0), md);  // keys in Montgomery form; sum < 8 q^2
       o[(size_t)next * n] = redc(acc30_value(a1), md);
@@ -841,7 +853,8 @@ void launch_modup_bconv_fast(hc_ctx* ctx, int level, int j, const u64* xcoef, u6
   const int ns = std::min(alpha, level + 1 - d0);
   const int next = level + 1 + alpha;
   const u64* cst = ctx->ks(ctx->lv[level].modup_off[j]);
-  const size_t smem = (size_t)next * ns * sizeof(u64) + (size_t)next * sizeof(DMod);
+  // (the halves form stages 16 bytes per constant, the other 8)
+  const size_t smem = (size_t)next * ns * 2 * sizeof(u64) + (size_t)next * sizeof(DMod);
   const dim3 g = grid_for(ctx, 1, items);
   ProfScope prof_(ctx, "k_modup_bconv", (uint64_t)items * (next - ns));
   const bool halves = ctx->P.below_2_60;
@@ -869,7 +882,7 @@ void launch_moddown_bconv_fast(hc_ctx* ctx, int level, const u64* accp_coef, u64
                                u64 z_item_stride, int items) {
   const int alpha = ctx->P.alpha, nq = level + 1, next = nq + alpha;
   const u64* cst = ctx->ks(ctx->moddown_off);
-  const size_t smem = (size_t)nq * alpha * sizeof(u64) + (size_t)nq * sizeof(DMod);
+  const size_t smem = (size_t)nq * alpha * 2 * sizeof(u64) + (size_t)nq * sizeof(DMod);
   const dim3 g = grid_for(ctx, 2, items);
   const u64 ps = (u64)next * ctx->P.n;
   ProfScope prof_(ctx, "k_moddown_bconv", (uint64_t)items * 2 * nq);
