@@ -443,6 +443,10 @@ std::vector<hc_ct*> mul_const_cts(hc_ctx* ctx, const std::vector<const hc_ct*>& 
 
 std::vector<hc_ct*> rotate_one(hc_ctx* ctx, const hc_evk* evk, const hc_ct* x, const std::vector<int>& steps,
                                bool hoisted);
+std::vector<hc_ct*> rotate_batch(hc_ctx* ctx, const hc_evk* evk, const std::vector<const hc_ct*>& xs, int step);
+std::vector<std::vector<hc_ct*>> rotate_hoisted_batch(hc_ctx* ctx, const hc_evk* evk,
+                                                      const std::vector<const hc_ct*>& xs,
+                                                      const std::vector<int>& steps);
 
 void free_all(std::vector<hc_ct*>& v) {
   for (auto* c : v) delete c;
@@ -1323,82 +1327,172 @@ extern "C" int hc_drop_to_level(hc_ctx* ctx, const hc_ct* x, int level, hc_ct** 
 }
 
 namespace {
-std::vector<hc_ct*> rotate_one(hc_ctx* ctx, const hc_evk* evk, const hc_ct* x, const std::vector<int>& steps,
-                               bool hoisted) {
-  HC_CHECK(x->degree == 1, HC_ERR_INVALID, "rotate needs a degree-1 ciphertext");
-  const int n = ctx->P.n, level = x->level, nq = level + 1, alpha = ctx->P.alpha;
+// The same rotation of many ciphertexts at one level (plain form, bit-identical
+// to rotate_one of each): one automorphism launch and one batched key switch.
+std::vector<hc_ct*> rotate_batch(hc_ctx* ctx, const hc_evk* evk, const std::vector<const hc_ct*>& xs, int step) {
+  const int m = (int)xs.size();
+  if (m == 0) return {};
+  const int n = ctx->P.n, level = xs[0]->level, nq = level + 1;
+  for (auto* c : xs)
+    HC_CHECK(c->degree == 1 && c->level == level, HC_ERR_INVALID, "rotate batch needs degree-1 cts at one level");
+  const u64 g = galois_elt(ctx->P, step);
+  std::vector<hc_ct*> outs = new_cts(ctx, m, level, 1, xs[0]->scale);
+  for (int i = 0; i < m; ++i) outs[i]->scale = xs[i]->scale;
+  std::vector<BufPtr> keep;
+  std::vector<CtRef> xr, orr;
+  for (int i = 0; i < m; ++i) {
+    xr.push_back(xs[i]->ref());
+    orr.push_back(outs[i]->ref());
+  }
+  if (g == 1) {
+    launch_ew(ctx, 3, refs_dev(ctx, orr, keep), refs_dev(ctx, xr, keep), nullptr, m, 2, nq);
+    return outs;
+  }
+  HC_CHECK(evk->galois.count(g), HC_ERR_NO_KEY, "no Galois key for rotation " + std::to_string(step));
+  const u64 ps = (u64)nq * n;
+  BufPtr tmp = ctx->buffer(2 * ps * m);  // kappa_g of (c0, c1) per item
+  keep.push_back(tmp);
+  std::vector<CtRef> tr, t1, t0;
+  for (int i = 0; i < m; ++i) {
+    tr.push_back(CtRef{tmp->ptr + 2 * ps * i, ps});
+    t0.push_back(CtRef{tmp->ptr + 2 * ps * i, ps});
+    t1.push_back(CtRef{tmp->ptr + 2 * ps * i + ps, ps});
+  }
+  launch_automorph(ctx, refs_dev(ctx, tr, keep), refs_dev(ctx, xr, keep), m, 2, nq, g);
+  keyswitch_batch(ctx, evk->galois.at(g).buf->ptr, level, t1, &t0, nullptr, orr);
+  return outs;
+}
+
+// Hoisted rotations of m ciphertexts at one level by every step in `steps`:
+// one ModUp of all the c1's, then per step the automorphism of the raised
+// digits, the key product, ModDown and the automorphism of c0, each one
+// launch over the m items.  out[step][item]; the same words as m separate
+// hoisted calls.
+std::vector<std::vector<hc_ct*>> rotate_hoisted_batch(hc_ctx* ctx, const hc_evk* evk,
+                                                      const std::vector<const hc_ct*>& xs,
+                                                      const std::vector<int>& steps) {
+  const int total = (int)xs.size();
+  std::vector<std::vector<hc_ct*>> outs(steps.size());
+  if (total == 0) return outs;
+  const int n = ctx->P.n, level = xs[0]->level, nq = level + 1, alpha = ctx->P.alpha;
+  const int next = nq + alpha, dnum = ctx->lv[level].dnum;
+  for (auto* c : xs)
+    HC_CHECK(c->degree == 1 && c->level == level, HC_ERR_INVALID, "hoisted batch needs degree-1 cts at one level");
   std::vector<u64> gs;
   for (int r : steps) {
     const u64 g = galois_elt(ctx->P, r);
     if (g != 1) HC_CHECK(evk->galois.count(g), HC_ERR_NO_KEY, "no Galois key for rotation " + std::to_string(r));
     gs.push_back(g);
   }
+  for (size_t k = 0; k < steps.size(); ++k) {
+    outs[k] = new_cts(ctx, total, level, 1, xs[0]->scale);
+    for (int i = 0; i < total; ++i) outs[k][i]->scale = xs[i]->scale;
+  }
+  const size_t ext_words = (size_t)next * n;
+  const int* emap = ctx->ext_map_of(level);
+  const u64 x_is = (u64)nq * n, ext_is = (u64)dnum * ext_words, acc_is = 2 * (u64)ext_words,
+            z_is = 2 * (u64)nq * n, c0_is = (u64)nq * n;
+  const size_t per_item = x_is + 2 * ext_is + acc_is + z_is + c0_is;
+  const int chunk = (int)std::min<size_t>(256, std::max<size_t>(1, kWorkspaceBytes / (per_item * 8)));
+  for (int s0 = 0; s0 < total; s0 += chunk) {
+    const int m = std::min(chunk, total - s0);
+    std::vector<BufPtr> keep;
+    BufPtr work = ctx->buffer(per_item * m);
+    keep.push_back(work);
+    u64* xc = work->ptr;                      // [m][nq][N]
+    u64* ext = xc + x_is * m;                 // [m][dnum][next][N]
+    u64* extg = ext + ext_is * m;             // [m][dnum][next][N]
+    u64* acc = extg + ext_is * m;             // [m][2][next][N]
+    u64* zq = acc + acc_is * m;               // [m][2][nq][N]
+    u64* c0g = zq + z_is * m;                 // [m][nq][N]
+    std::vector<CtRef> c1s, c0s, xsr, ers, egr, c0d, od;
+    for (int i = 0; i < m; ++i) {
+      const hc_ct* x = xs[s0 + i];
+      c1s.push_back(CtRef{x->data + x->stride, 0});
+      c0s.push_back(CtRef{x->data, 0});
+      ers.push_back(CtRef{ext + ext_is * i, (u64)ext_words});
+      egr.push_back(CtRef{extg + ext_is * i, (u64)ext_words});
+      c0d.push_back(CtRef{c0g + c0_is * i, 0});
+    }
+    // c1 -> coefficient form (N^{-1} left to the conversion constants)
+    LimbSet c1in{};
+    c1in.refs = refs_dev(ctx, c1s, keep);
+    c1in.npoly = 1;
+    c1in.nlimb = nq;
+    launch_ntt_from(ctx, limbset_base(xc, x_is, 0, 1, nq, 0, nullptr), &c1in, m, true, false);
+    for (int j = 0; j < dnum; ++j) {
+      const int d0 = j * alpha, d1 = std::min(d0 + alpha, nq);
+      // the digit's own slots are c1 itself (the automorphism below moves them too)
+      std::vector<CtRef> own_dst(m), own_src(m);
+      for (int i = 0; i < m; ++i) {
+        own_dst[i] = CtRef{ext + ext_is * i + (size_t)j * ext_words + (size_t)d0 * n, 0};
+        own_src[i] = CtRef{c1s[i].p + (size_t)d0 * n, 0};
+      }
+      launch_ew(ctx, 3, refs_dev(ctx, own_dst, keep), refs_dev(ctx, own_src, keep), nullptr, m, 1, d1 - d0);
+      u64* ej = ext + (size_t)j * ext_words;
+      launch_modup_bconv_fast(ctx, level, j, xc, x_is, ej, ext_is, m);
+      if (d0 > 0) launch_ntt(ctx, limbset_base(ej, ext_is, 0, 1, d0, 0, emap), m, false);
+      launch_ntt(ctx, limbset_base(ej, ext_is, 0, 1, next - d1, d1, emap), m, false);
+    }
+    const CtRef* ext_r = refs_dev(ctx, ers, keep);
+    const CtRef* extg_r = refs_dev(ctx, egr, keep);
+    const CtRef* c0s_r = refs_dev(ctx, c0s, keep);
+    const CtRef* c0d_r = refs_dev(ctx, c0d, keep);
+    for (size_t k = 0; k < gs.size(); ++k) {
+      std::vector<CtRef> orr;
+      for (int i = 0; i < m; ++i) orr.push_back(outs[k][s0 + i]->ref());
+      const CtRef* od_r = refs_dev(ctx, orr, keep);
+      if (gs[k] == 1) {
+        std::vector<CtRef> xr;
+        for (int i = 0; i < m; ++i) xr.push_back(xs[s0 + i]->ref());
+        launch_ew(ctx, 3, od_r, refs_dev(ctx, xr, keep), nullptr, m, 2, nq);
+        continue;
+      }
+      // kappa_g on every raised digit (the NTT-domain permutation is the same for every prime)
+      launch_automorph(ctx, extg_r, ext_r, m, dnum, next, gs[k]);
+      launch_key_product_batched(ctx, level, extg, ext_is, evk->galois.at(gs[k]).buf->ptr, acc, acc_is, m);
+      launch_ntt(ctx, limbset_base(acc, acc_is, ext_words, 2, alpha, nq, emap), m, true, false);
+      launch_moddown_bconv_fast(ctx, level, acc + (size_t)nq * n, acc_is, zq, z_is, m);
+      launch_ntt(ctx, limbset_base(zq, z_is, (u64)nq * n, 2, nq, 0, nullptr), m, false);
+      launch_automorph(ctx, c0d_r, c0s_r, m, 1, nq, gs[k]);
+      launch_moddown_combine(ctx, level, acc, acc_is, zq, z_is, c0d_r, nullptr, od_r, m);
+    }
+  }
+  return outs;
+}
+
+std::vector<hc_ct*> rotate_one(hc_ctx* ctx, const hc_evk* evk, const hc_ct* x, const std::vector<int>& steps,
+                               bool hoisted) {
+  HC_CHECK(x->degree == 1, HC_ERR_INVALID, "rotate needs a degree-1 ciphertext");
+  const int n = ctx->P.n, level = x->level, nq = level + 1;
+  std::vector<u64> gs;
+  for (int r : steps) {
+    const u64 g = galois_elt(ctx->P, r);
+    if (g != 1) HC_CHECK(evk->galois.count(g), HC_ERR_NO_KEY, "no Galois key for rotation " + std::to_string(r));
+    gs.push_back(g);
+  }
+  if (hoisted) {  // one ModUp of c1, automorphism applied to the raised digits
+    std::vector<hc_ct*> outs;
+    for (auto& v : rotate_hoisted_batch(ctx, evk, {x}, steps)) outs.push_back(v[0]);
+    return outs;
+  }
   std::vector<hc_ct*> outs = new_cts(ctx, (int)steps.size(), level, 1, x->scale);
   std::vector<BufPtr> keep;
   const CtRef* xr = refs_dev(ctx, {x->ref()}, keep);
-  if (!hoisted) {
-    BufPtr tmp = ctx->buffer(2 * (size_t)nq * n);
-    keep.push_back(tmp);
-    const CtRef tr{tmp->ptr, (u64)nq * n};
-    const CtRef* trd = refs_dev(ctx, {tr}, keep);
-    for (size_t i = 0; i < gs.size(); ++i) {
-      const CtRef* od = refs_dev(ctx, {outs[i]->ref()}, keep);
-      if (gs[i] == 1) {
-        launch_ew(ctx, 3, od, xr, nullptr, 1, 2, nq);
-        continue;
-      }
-      launch_automorph(ctx, trd, xr, 1, 2, nq, gs[i]);
-      std::vector<CtRef> xs{CtRef{tmp->ptr + (size_t)nq * n, (u64)nq * n}}, b0{CtRef{tmp->ptr, (u64)nq * n}},
-          o{outs[i]->ref()};
-      keyswitch_batch(ctx, evk->galois.at(gs[i]).buf->ptr, level, xs, &b0, nullptr, o);
-    }
-    return outs;
-  }
-  // hoisted: one ModUp of c1, automorphism applied to the raised digits
-  const int next = nq + alpha, dnum = ctx->lv[level].dnum;
-  const size_t ext_words = (size_t)next * n;
-  const int* emap = ctx->ext_map_of(level);
-  BufPtr work = ctx->buffer((size_t)nq * n + 2 * (size_t)dnum * ext_words + 2 * ext_words + 2 * (size_t)nq * n +
-                            (size_t)nq * n);
-  keep.push_back(work);
-  u64* xc = work->ptr;
-  u64* ext = xc + (size_t)nq * n;
-  u64* extg = ext + (size_t)dnum * ext_words;
-  u64* acc = extg + (size_t)dnum * ext_words;
-  u64* zq = acc + 2 * ext_words;
-  u64* c0g = zq + 2 * (size_t)nq * n;
-  const CtRef* xcr = refs_dev(ctx, {CtRef{xc, 0}}, keep);
-  const CtRef* c1r = refs_dev(ctx, {CtRef{x->data + x->stride, 0}}, keep);
-  launch_ew(ctx, 3, xcr, c1r, nullptr, 1, 1, nq);
-  launch_ntt(ctx, limbset_base(xc, 0, 0, 1, nq, 0, nullptr), 1, true, false);
-  for (int j = 0; j < dnum; ++j) {
-    const int d0 = j * alpha, d1 = std::min(d0 + alpha, nq);
-    u64* ej = ext + (size_t)j * ext_words;
-    const CtRef* er = refs_dev(ctx, {CtRef{ej + (size_t)d0 * n, 0}}, keep);
-    const CtRef* xsr = refs_dev(ctx, {CtRef{x->data + x->stride + (size_t)d0 * n, 0}}, keep);
-    launch_ew(ctx, 3, er, xsr, nullptr, 1, 1, d1 - d0);
-    launch_modup_bconv_fast(ctx, level, j, xc, 0, ej, 0, 1);
-    if (d0 > 0) launch_ntt(ctx, limbset_base(ej, 0, 0, 1, d0, 0, emap), 1, false);
-    launch_ntt(ctx, limbset_base(ej, 0, 0, 1, next - d1, d1, emap), 1, false);
-  }
+  BufPtr tmp = ctx->buffer(2 * (size_t)nq * n);
+  keep.push_back(tmp);
+  const CtRef tr{tmp->ptr, (u64)nq * n};
+  const CtRef* trd = refs_dev(ctx, {tr}, keep);
   for (size_t i = 0; i < gs.size(); ++i) {
     const CtRef* od = refs_dev(ctx, {outs[i]->ref()}, keep);
     if (gs[i] == 1) {
       launch_ew(ctx, 3, od, xr, nullptr, 1, 2, nq);
       continue;
     }
-    // kappa_g on every raised digit (the NTT-domain permutation is the same for every prime)
-    const CtRef* src = refs_dev(ctx, {CtRef{ext, (u64)ext_words}}, keep);
-    const CtRef* dst = refs_dev(ctx, {CtRef{extg, (u64)ext_words}}, keep);
-    launch_automorph(ctx, dst, src, 1, dnum, next, gs[i]);
-    launch_key_product_batched(ctx, level, extg, 0, evk->galois.at(gs[i]).buf->ptr, acc, 0, 1);
-    launch_ntt(ctx, limbset_base(acc, 0, ext_words, 2, alpha, nq, emap), 1, true, false);
-    launch_moddown_bconv_fast(ctx, level, acc + (size_t)nq * n, 0, zq, 0, 1);
-    launch_ntt(ctx, limbset_base(zq, 0, (u64)nq * n, 2, nq, 0, nullptr), 1, false);
-    const CtRef* c0d = refs_dev(ctx, {CtRef{c0g, 0}}, keep);
-    const CtRef* c0s = refs_dev(ctx, {CtRef{x->data, 0}}, keep);
-    launch_automorph(ctx, c0d, c0s, 1, 1, nq, gs[i]);
-    launch_moddown_combine(ctx, level, acc, 0, zq, 0, c0d, nullptr, od, 1);
+    launch_automorph(ctx, trd, xr, 1, 2, nq, gs[i]);
+    std::vector<CtRef> xs{CtRef{tmp->ptr + (size_t)nq * n, (u64)nq * n}}, b0{CtRef{tmp->ptr, (u64)nq * n}},
+        o{outs[i]->ref()};
+    keyswitch_batch(ctx, evk->galois.at(gs[i]).buf->ptr, level, xs, &b0, nullptr, o);
   }
   return outs;
 }
@@ -1835,28 +1929,42 @@ extern "C" int hc_enc_pool(hc_ctx* ctx, const hc_evk* evk, hc_packing packing, c
   return guard(ctx, [&] {
     HC_CHECK(x && y && C > 0 && H >= 2 && W >= 2, HC_ERR_INVALID, "bad arguments");
     if (packing == HC_PACK_SINGLE) {
+      // y + rot(y, W) + rot(y, 1) + rot(y, W + 1), all channels' rotations
+      // hoisted together, then x 1/4 and one rescale
       HC_CHECK(evk, HC_ERR_INVALID, "single-ciphertext pooling needs Galois keys");
-      for (int c = 0; c < C; ++c) {
-        check_ct(ctx, x[c]);
-        HC_CHECK(x[c]->degree == 1 && x[c]->level >= 1, HC_ERR_DEPTH, "pooling needs a level");
-        std::vector<hc_ct*> r = rotate_one(ctx, evk, x[c], {W, 1, W + 1}, true);
-        hc_ct* s0 = new_ct(ctx, x[c]->level, 1, x[c]->scale);
-        hc_ct* s1 = new_ct(ctx, x[c]->level, 1, r[1]->scale);
-        {
-          std::vector<BufPtr> keep;
-          const CtRef *d0 = refs_dev(ctx, {s0->ref()}, keep), *d1 = refs_dev(ctx, {s1->ref()}, keep);
-          launch_ew(ctx, 0, d0, refs_dev(ctx, {x[c]->ref()}, keep), refs_dev(ctx, {r[0]->ref()}, keep), 1, 2,
-                    x[c]->level + 1);
-          launch_ew(ctx, 0, d1, refs_dev(ctx, {r[1]->ref()}, keep), refs_dev(ctx, {r[2]->ref()}, keep), 1, 2,
-                    x[c]->level + 1);
-          launch_ew(ctx, 0, d0, d0, d1, 1, 2, x[c]->level + 1);
-        }
-        std::vector<hc_ct*> o = mulc_rs(ctx, {s0}, 0.25, (double)ctx->P.chain[x[c]->level]);
-        y[c] = o[0];
-        delete s0;
-        delete s1;
-        free_all(r);
+      std::vector<const hc_ct*> xs(x, x + C);
+      for (auto* c : xs) {
+        check_ct(ctx, c);
+        HC_CHECK(c->degree == 1 && c->level >= 1, HC_ERR_DEPTH, "pooling needs a level");
+        HC_CHECK(c->level == xs[0]->level, HC_ERR_LEVEL_MISMATCH, "channels at different levels");
       }
+      const int nl = xs[0]->level + 1;
+      std::vector<std::vector<hc_ct*>> r = rotate_hoisted_batch(ctx, evk, xs, {W, 1, W + 1});
+      std::vector<hc_ct*> s0 = new_cts(ctx, C, xs[0]->level, 1, xs[0]->scale), s1 = new_cts(ctx, C, xs[0]->level, 1, 1.0);
+      {
+        std::vector<BufPtr> keep;
+        std::vector<CtRef> d0, d1, xr, r0, r1, r2;
+        for (int c = 0; c < C; ++c) {
+          s0[c]->scale = xs[c]->scale;
+          s1[c]->scale = r[1][c]->scale;
+          d0.push_back(s0[c]->ref());
+          d1.push_back(s1[c]->ref());
+          xr.push_back(xs[c]->ref());
+          r0.push_back(r[0][c]->ref());
+          r1.push_back(r[1][c]->ref());
+          r2.push_back(r[2][c]->ref());
+        }
+        const CtRef *dd0 = refs_dev(ctx, d0, keep), *dd1 = refs_dev(ctx, d1, keep);
+        launch_ew(ctx, 0, dd0, refs_dev(ctx, xr, keep), refs_dev(ctx, r0, keep), C, 2, nl);
+        launch_ew(ctx, 0, dd1, refs_dev(ctx, r1, keep), refs_dev(ctx, r2, keep), C, 2, nl);
+        launch_ew(ctx, 0, dd0, dd0, dd1, C, 2, nl);
+      }
+      std::vector<hc_ct*> o = mulc_rs(ctx, std::vector<const hc_ct*>(s0.begin(), s0.end()), 0.25,
+                                      (double)ctx->P.chain[xs[0]->level]);
+      for (int c = 0; c < C; ++c) y[c] = o[c];
+      free_all(s0);
+      free_all(s1);
+      for (auto& v : r) free_all(v);
       return;
     }
     HC_CHECK(packing == HC_PACK_BATCH, HC_ERR_INVALID, "unknown packing");
@@ -2157,15 +2265,19 @@ extern "C" int hc_enc_fc_rotsum(hc_ctx* ctx, const hc_evk* evk, const hc_ct* con
     free_all(d);
     free_all(views);
     const int nq = level;  // limbs after the rescale = level
+    // z += rot(z, 2^k): all outputs rotate together, one batched key switch per k
     for (int k = 0; k < span_log2; ++k) {
+      std::vector<hc_ct*> rot = rotate_batch(ctx, evk, std::vector<const hc_ct*>(z.begin(), z.end()), 1 << k);
+      std::vector<BufPtr> keep;
+      std::vector<CtRef> zr, rr;
       for (int r = 0; r < n_out; ++r) {
-        std::vector<hc_ct*> rot = rotate_one(ctx, evk, z[r], {1 << k}, false);
-        std::vector<BufPtr> keep;
-        check_scales(z[r]->scale, rot[0]->scale);
-        const CtRef* zd = refs_dev(ctx, {z[r]->ref()}, keep);
-        launch_ew(ctx, 0, zd, zd, refs_dev(ctx, {rot[0]->ref()}, keep), 1, 2, nq);
-        free_all(rot);
+        check_scales(z[r]->scale, rot[r]->scale);
+        zr.push_back(z[r]->ref());
+        rr.push_back(rot[r]->ref());
       }
+      const CtRef* zd = refs_dev(ctx, zr, keep);
+      launch_ew(ctx, 0, zd, zd, refs_dev(ctx, rr, keep), n_out, 2, nq);
+      free_all(rot);
     }
     for (int r = 0; r < n_out; ++r) y[r] = z[r];
   });
