@@ -77,9 +77,10 @@ def summarize_ncu(path, occurrence):
     starts = [i for i, n in enumerate(names) if n == "k_tensor_acc"]
     a = starts[occurrence - 1]
     b = starts[occurrence] if occurrence < len(starts) else len(rows)
-    # the step ends at its last rescale combine (fused or not)
-    ends = [i for i in range(a, b) if names[i] in ("k_ksr_combine", "k_rescale_combine")]
-    b = ends[-1] + 1
+    # the step ends with the forward NTT (column then row pass) that carries the
+    # fused relinearise + rescale tail, right after the c_l kernel
+    ends = [i for i in range(a, b) if names[i] == "k_ksr_cl"]
+    b = min(ends[-1] + 3, b)
     per = {}
     for i in range(a, b):
         t = float(rows[i]["Metric Value"]) * (1e-3 if rows[i]["Metric Unit"] == "ns" else 1.0)
@@ -233,8 +234,8 @@ def run_reference(args, rank, world):
 # 336 limbs per launch), scaled to a launch by its units.  Set an entry to
 # None when its kernel changes until it is captured again.
 NCU_TRAFFIC_PER_UNIT = {
-    "ntt_fwd_cols": (176.307712e6 + 114.424832e6) / 336,
-    "ntt_fwd_rows": (209.289984e6 + 123.394560e6) / 336,
+    "ntt_fwd_cols": None,
+    "ntt_fwd_rows": None,
 }
 
 
@@ -249,7 +250,8 @@ BUTTERFLIES_PER_SM_CLK = 1.0 / (2.0 / LO64_PER_SM_CLK + 1.0 / HI64_PER_SM_CLK)
 
 def butterflies_per_unit(name, n):
     """Butterflies of one limb in one NTT pass (the column pass takes the first
-    floor(log N / 2) stages, the row pass the rest)."""
+    floor(log N / 2) stages, the row pass the rest).  The `_ksr` passes carry
+    the fused relinearise + rescale tail on top of their butterflies."""
     log_n = n.bit_length() - 1
     stages = log_n // 2 if "cols" in name else log_n - log_n // 2
     return stages * (n // 2)
@@ -257,6 +259,8 @@ def butterflies_per_unit(name, n):
 
 def bytes_per_unit(name, n, dnum):
     limb = 8 * n
+    if name == "ntt_fwd_rows_ksr":
+        return 4 * limb                       # limb in, output out, accumulator and base in
     if name.startswith("ntt_"):
         return 2 * limb                       # read + write the limb
     if name == "k_key_product":

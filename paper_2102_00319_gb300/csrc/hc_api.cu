@@ -291,9 +291,19 @@ void keyswitch_rescale_batch(hc_ctx* ctx, const u64* key, int level, const std::
     launch_moddown_bconv_fast(ctx, level, acc + (size_t)nq * n, acc_is, zq, z_is, m);
     launch_ksr_last(ctx, level, acc, acc_is, b0, b1, tl, m);
     launch_ntt(ctx, limbset_base(tl, 2 * (u64)n, (u64)n, 2, 1, 0, ident_map(ctx) + level), m, true);
-    launch_ksr_lift(ctx, level, tl, zq, z_is, m);
-    launch_ntt(ctx, limbset_base(zq, z_is, (u64)nq * n, 2, level, 0, nullptr), m, false);
-    launch_ksr_combine(ctx, level, acc, acc_is, zq, z_is, b0, b1, orr, m);
+    // c_l (centred, signed) over tl; the forward NTT of z lifts it on load and
+    // forms (base + acc P^{-1} - NTT(.)) q_l^{-1} on store
+    launch_ksr_cl(ctx, level, tl, zq, z_is, m);
+    KsrFuse f{};
+    ksr_constants(ctx, level, f);
+    f.cl = tl;
+    f.acc = acc;
+    f.acc_item_stride = acc_is;
+    f.acc_poly_stride = ext_words;
+    f.base0 = b0;
+    f.base1 = b1;
+    f.out = orr;
+    launch_ntt_ksr(ctx, limbset_base(zq, z_is, (u64)nq * n, 2, level, 0, nullptr), m, f);
   }
 }
 

@@ -43,6 +43,26 @@ struct CtRef {
   u64 stride;
 };
 
+// The fused tail of relinearise + rescale carried by the forward NTT of the
+// converted limbs z_k[i] (i < level, poly k < 2, item z):
+// - first pass, on load: x = z_k[i] P^{-1} + [c_l]_{q_i}, with c_l the
+//   centred last limb of the relinearised poly stored as a signed integer in
+//   cl[z][k][coefficient];
+// - last pass, on store: out_k[i] = (base_k[i] + acc_k[i] P^{-1} - NTT(x))
+//   q_l^{-1}, written to the output ciphertexts instead of back into z.
+struct KsrFuse {
+  const u64* cl;        // [item][2][N] signed centred c_l
+  const u64* pinv;      // P^{-1} mod q_i (i <= level)
+  const u64* pinv_sh;
+  const u64* acc;       // key-product accumulators, NTT form
+  u64 acc_item_stride, acc_poly_stride;
+  const CtRef* base0;   // (d0, d1) or null
+  const CtRef* base1;
+  const CtRef* out;     // level-1 outputs
+  const u64* qlinv;     // q_l^{-1} mod q_i, then its Shoup companions
+  int level;
+};
+
 // A set of limbs for batched per-limb kernels (NTT, copies): for batch item
 // z, poly k < npoly and limb slot l0 <= s < l0 + nlimb the limb lives at
 //   (refs ? refs[z].p + k*refs[z].stride : base + z*item_stride + k*poly_stride) + s*N

@@ -191,6 +191,9 @@ void launch_ntt(hc_ctx* ctx, const LimbSet& s, int items, bool inverse, bool sca
 // (same poly/limb counts as s), the result lands in s.
 void launch_ntt_from(hc_ctx* ctx, const LimbSet& s, const LimbSet* in, int items, bool inverse,
                      bool scale = true);
+// Forward NTT of the converted limbs z (2 polys x level limbs per item)
+// carrying the fused relinearise + rescale tail (KsrFuse): writes f.out.
+void launch_ntt_ksr(hc_ctx* ctx, const LimbSet& z, int items, const KsrFuse& f);
 
 // Samplers writing coefficient-form limbs dst + r*N for chain indices ids[r].
 void launch_sample_ternary(hc_ctx* ctx, u64 seed, u64 tag, u64* dst, const int* ids, int nl);
@@ -249,6 +252,8 @@ void launch_key_product_batched(hc_ctx* ctx, int level, const u64* ext, u64 ext_
 // Fused relinearise + rescale tail (see hc_kernels.cu).
 void launch_ksr_last(hc_ctx* ctx, int level, const u64* acc, u64 acc_item_stride, const CtRef* base0,
                      const CtRef* base1, u64* tl, int items);
-void launch_ksr_lift(hc_ctx* ctx, int level, const u64* tl, u64* zq, u64 z_item_stride, int items);
-void launch_ksr_combine(hc_ctx* ctx, int level, const u64* acc, u64 acc_item_stride, const u64* w, u64 w_item_stride,
-                        const CtRef* base0, const CtRef* base1, const CtRef* out, int items);
+// In place over tl: the centred c_l = t_k - z_k[l] P^{-1} mod q_l as a signed
+// integer per coefficient (coefficient-form tl from the inverse NTT).
+void launch_ksr_cl(hc_ctx* ctx, int level, u64* tl, const u64* zq, u64 z_item_stride, int items);
+// Constants of the fused tail at `level` (pinv, pinv_sh, qlinv into f).
+void ksr_constants(hc_ctx* ctx, int level, KsrFuse& f);

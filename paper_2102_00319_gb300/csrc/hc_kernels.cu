@@ -803,46 +803,22 @@ __global__ void k_ksr_last(const u64* acc, u64 acc_item_stride, u64 acc_poly_str
   tl[((size_t)z * 2 + k) * n + c] = r;
 }
 
-// Step 2 (coefficient form): c_l = t_k - z_k[l] P^{-1} mod q_l is the relinearised
-// last limb; w_k[i] = z_k[i] P^{-1} + centred(c_l) mod q_i for i < l, written
-// over z_k[i].
-__global__ void k_ksr_lift(const u64* tl, u64* zq, u64 z_item_stride, int level, const u64* pinv,
-                           const u64* pinv_sh, Tables T) {
+// Step 2 of the fused form: the centred c_l = t_k - z_k[l] P^{-1} mod q_l
+// stored over t_k as a signed integer (the forward NTT of z lifts it).
+__global__ void k_ksr_cl(u64* tl, const u64* zq, u64 z_item_stride, int level, u64 pinv_l, u64 pinv_l_sh,
+                         Tables T) {
   const int n = 1 << T.log_n;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
   const int k = blockIdx.y, z = blockIdx.z;
-  const int nq = level + 1;
-  u64* zk = zq + (size_t)z * z_item_stride + (size_t)k * nq * n;
   const u64 ql = T.mods[level].q;
-  const u64 cl = subm(tl[((size_t)z * 2 + k) * n + c], shoup(zk[(size_t)level * n + c], pinv[level], pinv_sh[level], ql), ql);
+  const u64* zk = zq + (size_t)z * z_item_stride + (size_t)k * (level + 1) * n;
+  u64* t = tl + ((size_t)z * 2 + k) * n + c;
+  const u64 cl = subm(*t, shoup(zk[(size_t)level * n + c], pinv_l, pinv_l_sh, ql), ql);
   const bool neg = cl > (ql - 1) / 2;
-  const u64 mag = neg ? ql - cl : cl;
-  for (int i = 0; i < level; ++i) {
-    const DMod mi = T.mods[i];
-    const u64 m = csub(shoup_lazy(mag, 1, mi.one_sh, mi.q), mi.q);
-    const u64 r = neg ? negm(m, mi.q) : m;
-    const u64 w = shoup(zk[(size_t)i * n + c], pinv[i], pinv_sh[i], mi.q);
-    zk[(size_t)i * n + c] = addm(w, r, mi.q);
-  }
+  *t = neg ? (u64)(-(long long)(ql - cl)) : cl;
 }
 
-// Step 3: out_k[i] = (base_k[i] + acc_k[i] P^{-1} - w_k[i]) q_l^{-1}, i < l.
-__global__ void k_ksr_combine(const u64* acc, u64 acc_item_stride, u64 acc_poly_stride, const u64* w,
-                              u64 w_item_stride, const CtRef* base0, const CtRef* base1, const CtRef* out,
-                              const u64* pinv, const u64* pinv_sh, const u64* qlinv, int level, Tables T) {
-  const int n = 1 << T.log_n;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n) return;
-  const int k = blockIdx.y / level, i = blockIdx.y % level, z = blockIdx.z;
-  const u64 q = T.mods[i].q;
-  const size_t li = (size_t)i * n + c;
-  u64 r = shoup(acc[(size_t)z * acc_item_stride + (size_t)k * acc_poly_stride + li], pinv[i], pinv_sh[i], q);
-  const CtRef* base = k == 0 ? base0 : base1;
-  if (base) r = addm(r, base[z].p[li], q);
-  r = subm(r, w[(size_t)z * w_item_stride + (size_t)k * (level + 1) * n + li], q);
-  out[z].p[(size_t)k * out[z].stride + li] = shoup(r, qlinv[i], qlinv[level + i], q);
-}
 
 }  // namespace
 
@@ -957,26 +933,26 @@ void launch_ksr_last(hc_ctx* ctx, int level, const u64* acc, u64 acc_item_stride
   check_launch(ctx);
 }
 
-void launch_ksr_lift(hc_ctx* ctx, int level, const u64* tl, u64* zq, u64 z_item_stride, int items) {
+
+void launch_ksr_cl(hc_ctx* ctx, int level, u64* tl, const u64* zq, u64 z_item_stride, int items) {
   const int L = ctx->P.L, a = ctx->P.alpha;
-  const u64* cst = ctx->ks(ctx->moddown_off);
-  const u64* pinv = cst + 2 * a + (size_t)(L + 1) * a;
-  ProfScope prof_(ctx, "k_ksr_lift", (uint64_t)items * 2 * level);
-  k_ksr_lift<<<grid_for(ctx, 2, items), kT, 0, ctx->stream>>>(tl, zq, z_item_stride, level, pinv, pinv + (L + 1),
+  ProfScope prof_(ctx, "k_ksr_cl", (uint64_t)items * 2);
+  const u64 ql = ctx->P.chain[level];
+  u64 p = 1;
+  for (int m = 0; m < a; ++m) p = hch::mulmod(p, ctx->P.chain[L + 1 + m] % ql, ql);
+  p = hch::invmod(p, ql);
+  k_ksr_cl<<<grid_for(ctx, 2, items), kT, 0, ctx->stream>>>(tl, zq, z_item_stride, level, p, hch::shoup_of(p, ql),
                                                              ctx->tab);
   ctx->launches++;
   check_launch(ctx);
 }
 
-void launch_ksr_combine(hc_ctx* ctx, int level, const u64* acc, u64 acc_item_stride, const u64* w, u64 w_item_stride,
-                        const CtRef* base0, const CtRef* base1, const CtRef* out, int items) {
-  const int L = ctx->P.L, a = ctx->P.alpha, next = level + 1 + a;
-  const u64* cst = ctx->ks(ctx->moddown_off);
-  const u64* pinv = cst + 2 * a + (size_t)(L + 1) * a;
-  ProfScope prof_(ctx, "k_ksr_combine", (uint64_t)items * 2 * level);
-  k_ksr_combine<<<grid_for(ctx, 2 * level, items), kT, 0, ctx->stream>>>(
-      acc, acc_item_stride, (u64)next * ctx->P.n, w, w_item_stride, base0, base1, out, pinv, pinv + (L + 1),
-      ctx->ks(ctx->lv[level].rescale_off), level, ctx->tab);
-  ctx->launches++;
-  check_launch(ctx);
+void ksr_constants(hc_ctx* ctx, int level, KsrFuse& f) {
+  const int L = ctx->P.L, a = ctx->P.alpha;
+  const u64* pinv = ctx->ks(ctx->moddown_off) + 2 * a + (size_t)(L + 1) * a;
+  f.pinv = pinv;
+  f.pinv_sh = pinv + (L + 1);
+  f.qlinv = ctx->ks(ctx->lv[level].rescale_off);
+  f.level = level;
 }
+

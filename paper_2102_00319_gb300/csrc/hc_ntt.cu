@@ -102,8 +102,9 @@ __device__ __forceinline__ const u64* input_limb(const LimbSet& s, const LimbSet
 
 // Column pass: stages 0..N1-1 (forward) over R = 2^N1 rows (N1 = K1 + K2) of
 // TC = 2^TCL columns starting at blockIdx.x * TC.  Shared tile [row][col].
-template <bool INV, int LOGN, int K1, int K2, int TCL>
-__global__ void __launch_bounds__(kThreads) k_cols(LimbSet s, LimbSet in, int use_in, int scale, Tables T) {
+template <bool INV, int LOGN, int K1, int K2, int TCL, bool FUSE>
+__global__ void __launch_bounds__(kThreads) k_cols(LimbSet s, LimbSet in, int use_in, int scale, KsrFuse f,
+                                                   Tables T) {
   constexpr int N1 = K1 + K2, N2 = LOGN - N1, TC = 1 << TCL;
   extern __shared__ u64 sm[];
   u64* a;
@@ -114,13 +115,29 @@ __global__ void __launch_bounds__(kThreads) k_cols(LimbSet s, LimbSet in, int us
   const ulonglong2* tw = (INV ? T.inv2 : T.fwd2) + ((size_t)pid << LOGN);
   a += blockIdx.x * TC;
   ain += blockIdx.x * TC;
+  // fused relinearise + rescale: limb slot (prime) and the c_l row of this block
+  const int fslot = blockIdx.y % s.nlimb, fpoly = blockIdx.y / s.nlimb;
+  const u64* fcl = FUSE ? f.cl + ((size_t)blockIdx.z * 2 + fpoly) * ((size_t)1 << LOGN) + blockIdx.x * TC : nullptr;
   if (!INV) {
     // round 1: 2^K1 rows strided by 2^K2 -> stages 0..K1-1
     for (u32 w = threadIdx.x; w < (TC << K2); w += kThreads) {
       const u32 c = w & (TC - 1), r0 = w >> TCL;
       u64 x[1 << K1];
 #pragma unroll
-      for (int i = 0; i < (1 << K1); ++i) x[i] = ain[((r0 + (i << K2)) << N2) + c];
+      for (int i = 0; i < (1 << K1); ++i) {
+        const u32 e = ((r0 + (i << K2)) << N2) + c;
+        if constexpr (FUSE) {
+          // z P^{-1} + [c_l]_{q_i}, c_l centred (its sign carried by the stored integer)
+          const DMod md = T.mods[pid];
+          const u64 zp = shoup(ain[e], f.pinv[fslot], f.pinv_sh[fslot], q);
+          const long long cl = (long long)fcl[e];
+          const u64 mag = cl < 0 ? (u64)(-cl) : (u64)cl;
+          const u64 m = csub(shoup_lazy(mag, 1, md.one_sh, q), q);
+          x[i] = addm(zp, cl < 0 ? negm(m, q) : m, q);
+        } else {
+          x[i] = ain[e];
+        }
+      }
       fwd_block<K1, K2 + N2, 0, LOGN>(x, r0 << N2, tw, q);
 #pragma unroll
       for (int i = 0; i < (1 << K1); ++i) sm[((r0 + (i << K2)) << TCL) + c] = x[i];
@@ -165,8 +182,8 @@ __global__ void __launch_bounds__(kThreads) k_cols(LimbSet s, LimbSet in, int us
 
 // Row pass: stages N1..LOGN-1 (forward) inside RP = 2^RPL rows of C = 2^N2
 // adjacent points (N2 = K1 + K2).  Shared rows padded by one word per 2^K2.
-template <bool INV, int LOGN, int K1, int K2, int RPL>
-__global__ void __launch_bounds__(kThreads) k_rows(LimbSet s, LimbSet in, int use_in, Tables T) {
+template <bool INV, int LOGN, int K1, int K2, int RPL, bool FUSE>
+__global__ void __launch_bounds__(kThreads) k_rows(LimbSet s, LimbSet in, int use_in, KsrFuse f, Tables T) {
   constexpr int N2 = K1 + K2, N1 = LOGN - N2, C = 1 << N2, RP = 1 << RPL;
   constexpr int PADW = C + (C >> K2);
   extern __shared__ u64 sm[];
@@ -205,7 +222,24 @@ __global__ void __launch_bounds__(kThreads) k_rows(LimbSet s, LimbSet in, int us
       for (int i = 0; i < (1 << K2); ++i) sm[sidx(r, (g << K2) + i)] = reduce4(x[i], q);
     }
     __syncthreads();
-    for (u32 e = threadIdx.x; e < (RP << N2); e += kThreads) src[e] = sm[sidx(e >> N2, e & (C - 1))];
+    if constexpr (FUSE) {
+      // out_k[i] = (base_k[i] + acc_k[i] P^{-1} - w) q_l^{-1} for the NTT output w
+      const int slot = blockIdx.y % s.nlimb, k = blockIdx.y / s.nlimb, z = blockIdx.z;
+      const size_t li0 = ((size_t)slot << LOGN) + ((size_t)row0 << N2);
+      const u64* accp = f.acc + (size_t)z * f.acc_item_stride + (size_t)k * f.acc_poly_stride + li0;
+      const CtRef* base = k == 0 ? f.base0 : f.base1;
+      const u64* bp = base ? base[z].p + li0 : nullptr;
+      u64* op = f.out[z].p + (size_t)k * f.out[z].stride + li0;
+      const u64 pv = f.pinv[slot], pvs = f.pinv_sh[slot], qv = f.qlinv[slot], qvs = f.qlinv[f.level + slot];
+      for (u32 e = threadIdx.x; e < (RP << N2); e += kThreads) {
+        u64 r = shoup(accp[e], pv, pvs, q);
+        if (bp) r = addm(r, bp[e], q);
+        r = subm(r, sm[sidx(e >> N2, e & (C - 1))], q);
+        op[e] = shoup(r, qv, qvs, q);
+      }
+    } else {
+      for (u32 e = threadIdx.x; e < (RP << N2); e += kThreads) src[e] = sm[sidx(e >> N2, e & (C - 1))];
+    }
   } else {
     // round A: 2^K2 adjacent points read straight from global memory as
     // 16-byte pairs (a thread's points are contiguous and 16-byte aligned;
@@ -267,33 +301,42 @@ struct RowTile {
 
 template <bool INV, int LOGN>
 void launch_pass_cols(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, const LimbSet* in = nullptr,
-                      bool scale = true) {
+                      bool scale = true, const KsrFuse* fuse = nullptr) {
   constexpr int N1 = LOGN / 2, N2 = LOGN - N1;
   using Sp = Split<N1>;
   constexpr int TCL = ColTile<N1, N2>::TCL;
   dim3 grid(1u << (N2 - TCL), ylimbs, items);
   const size_t smem = ((size_t)1 << (N1 + TCL)) * sizeof(u64);
-  ProfScope p(ctx, INV ? "ntt_inv_cols" : "ntt_fwd_cols", (uint64_t)ylimbs * items);
-  k_cols<INV, LOGN, Sp::K1, Sp::K2, TCL><<<grid, kThreads, smem, ctx->stream>>>(s, in ? *in : s, in ? 1 : 0, scale ? 1 : 0,
-                                                                                      ctx->tab);
+  ProfScope p(ctx, INV ? "ntt_inv_cols" : (fuse ? "ntt_fwd_cols_ksr" : "ntt_fwd_cols"), (uint64_t)ylimbs * items);
+  if (!INV && fuse)
+    k_cols<false, LOGN, Sp::K1, Sp::K2, TCL, true><<<grid, kThreads, smem, ctx->stream>>>(s, s, 0, 1, *fuse, ctx->tab);
+  else
+    k_cols<INV, LOGN, Sp::K1, Sp::K2, TCL, false><<<grid, kThreads, smem, ctx->stream>>>(
+        s, in ? *in : s, in ? 1 : 0, scale ? 1 : 0, KsrFuse{}, ctx->tab);
 }
 
 template <bool INV, int LOGN>
-void launch_pass_rows(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, const LimbSet* in = nullptr) {
+void launch_pass_rows(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, const LimbSet* in = nullptr,
+                      const KsrFuse* fuse = nullptr) {
   constexpr int N1 = LOGN / 2, N2 = LOGN - N1;
   using Sp = Split<N2>;
   constexpr int RPL = RowTile<N1, N2>::RPL;
   dim3 grid(1u << (N1 - RPL), ylimbs, items);
   const size_t smem = ((size_t)1 << RPL) * RowTile<N1, N2>::PADW * sizeof(u64);
-  ProfScope p(ctx, INV ? "ntt_inv_rows" : "ntt_fwd_rows", (uint64_t)ylimbs * items);
-  k_rows<INV, LOGN, Sp::K1, Sp::K2, RPL><<<grid, kThreads, smem, ctx->stream>>>(s, in ? *in : s, in ? 1 : 0, ctx->tab);
+  ProfScope p(ctx, INV ? "ntt_inv_rows" : (fuse ? "ntt_fwd_rows_ksr" : "ntt_fwd_rows"), (uint64_t)ylimbs * items);
+  if (!INV && fuse)
+    k_rows<false, LOGN, Sp::K1, Sp::K2, RPL, true><<<grid, kThreads, smem, ctx->stream>>>(s, s, 0, *fuse, ctx->tab);
+  else
+    k_rows<INV, LOGN, Sp::K1, Sp::K2, RPL, false><<<grid, kThreads, smem, ctx->stream>>>(s, in ? *in : s, in ? 1 : 0,
+                                                                                         KsrFuse{}, ctx->tab);
 }
 
 template <int LOGN>
-void ntt_logn(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, bool inverse, const LimbSet* in, bool scale) {
+void ntt_logn(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, bool inverse, const LimbSet* in, bool scale,
+              const KsrFuse* fuse = nullptr) {
   if (!inverse) {
-    launch_pass_cols<false, LOGN>(ctx, s, items, ylimbs, in);
-    launch_pass_rows<false, LOGN>(ctx, s, items, ylimbs);
+    launch_pass_cols<false, LOGN>(ctx, s, items, ylimbs, in, true, fuse);
+    launch_pass_rows<false, LOGN>(ctx, s, items, ylimbs, nullptr, fuse);
   } else {
     launch_pass_rows<true, LOGN>(ctx, s, items, ylimbs, in);
     launch_pass_cols<true, LOGN>(ctx, s, items, ylimbs, nullptr, scale);
@@ -306,20 +349,32 @@ void launch_ntt(hc_ctx* ctx, const LimbSet& s, int items, bool inverse, bool sca
   launch_ntt_from(ctx, s, nullptr, items, inverse, scale);
 }
 
-void launch_ntt_from(hc_ctx* ctx, const LimbSet& s, const LimbSet* in, int items, bool inverse, bool scale) {
+namespace {
+void ntt_dispatch(hc_ctx* ctx, const LimbSet& s, const LimbSet* in, int items, bool inverse, bool scale,
+                  const KsrFuse* fuse) {
   if (items <= 0 || s.nlimb <= 0 || s.npoly <= 0) return;
   const int ylimbs = s.npoly * s.nlimb;
   HC_CHECK(ylimbs <= 65535 && items <= 65535, HC_ERR_INVALID, "NTT batch too large");
   switch (ctx->P.log_n) {
-    case 10: ntt_logn<10>(ctx, s, items, ylimbs, inverse, in, scale); break;
-    case 11: ntt_logn<11>(ctx, s, items, ylimbs, inverse, in, scale); break;
-    case 12: ntt_logn<12>(ctx, s, items, ylimbs, inverse, in, scale); break;
-    case 13: ntt_logn<13>(ctx, s, items, ylimbs, inverse, in, scale); break;
-    case 14: ntt_logn<14>(ctx, s, items, ylimbs, inverse, in, scale); break;
-    case 15: ntt_logn<15>(ctx, s, items, ylimbs, inverse, in, scale); break;
-    case 16: ntt_logn<16>(ctx, s, items, ylimbs, inverse, in, scale); break;
+    case 10: ntt_logn<10>(ctx, s, items, ylimbs, inverse, in, scale, fuse); break;
+    case 11: ntt_logn<11>(ctx, s, items, ylimbs, inverse, in, scale, fuse); break;
+    case 12: ntt_logn<12>(ctx, s, items, ylimbs, inverse, in, scale, fuse); break;
+    case 13: ntt_logn<13>(ctx, s, items, ylimbs, inverse, in, scale, fuse); break;
+    case 14: ntt_logn<14>(ctx, s, items, ylimbs, inverse, in, scale, fuse); break;
+    case 15: ntt_logn<15>(ctx, s, items, ylimbs, inverse, in, scale, fuse); break;
+    case 16: ntt_logn<16>(ctx, s, items, ylimbs, inverse, in, scale, fuse); break;
     default: throw HcError{HC_ERR_INVALID, "unsupported ring degree"};
   }
   ctx->launches += 2;
   check_launch(ctx);
+}
+}  // namespace
+
+void launch_ntt_from(hc_ctx* ctx, const LimbSet& s, const LimbSet* in, int items, bool inverse, bool scale) {
+  ntt_dispatch(ctx, s, in, items, inverse, scale, nullptr);
+}
+
+void launch_ntt_ksr(hc_ctx* ctx, const LimbSet& s, int items, const KsrFuse& fuse) {
+  HC_CHECK(s.npoly == 2 && s.l0 == 0 && !s.prime_map && !s.refs, HC_ERR_INVALID, "fused tail needs plain z limbs");
+  ntt_dispatch(ctx, s, nullptr, items, false, true, &fuse);
 }
