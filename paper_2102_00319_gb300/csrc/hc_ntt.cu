@@ -231,11 +231,23 @@ __global__ void __launch_bounds__(kThreads) k_rows(LimbSet s, LimbSet in, int us
       const u64* bp = base ? base[z].p + li0 : nullptr;
       u64* op = f.out[z].p + (size_t)k * f.out[z].stride + li0;
       const u64 pv = f.pinv[slot], pvs = f.pinv_sh[slot], qv = f.qlinv[slot], qvs = f.qlinv[f.level + slot];
-      for (u32 e = threadIdx.x; e < (RP << N2); e += kThreads) {
-        u64 r = shoup(accp[e], pv, pvs, q);
-        if (bp) r = addm(r, bp[e], q);
-        r = subm(r, sm[sidx(e >> N2, e & (C - 1))], q);
-        op[e] = shoup(r, qv, qvs, q);
+      // four elements per thread per step: their global loads are in flight together
+      constexpr u32 kTile = RP << N2, kU = 4;
+      static_assert(kTile % (kThreads * kU) == 0, "epilogue tile");
+      for (u32 e0 = threadIdx.x; e0 < kTile; e0 += kThreads * kU) {
+        u64 av[kU], bv[kU];
+#pragma unroll
+        for (u32 u = 0; u < kU; ++u) {
+          av[u] = accp[e0 + u * kThreads];
+          bv[u] = bp ? bp[e0 + u * kThreads] : 0;
+        }
+#pragma unroll
+        for (u32 u = 0; u < kU; ++u) {
+          const u32 e = e0 + u * kThreads;
+          u64 r = addm(shoup(av[u], pv, pvs, q), bv[u], q);
+          r = subm(r, sm[sidx(e >> N2, e & (C - 1))], q);
+          op[e] = shoup(r, qv, qvs, q);
+        }
       }
     } else {
       for (u32 e = threadIdx.x; e < (RP << N2); e += kThreads) src[e] = sm[sidx(e >> N2, e & (C - 1))];
