@@ -66,7 +66,7 @@ def parse():
 
 def summarize_ncu(path, occurrence):
     """Per-kernel launches, total time and share over one timed step of an ncu
-    launch list: the step starts at the given occurrence of k_tensor_acc and
+    launch list: the step starts at the given occurrence of k_tensor_pair and
     ends before the next step's first kernel or the end of the step's kernels."""
     import csv
     import re
@@ -74,7 +74,7 @@ def summarize_ncu(path, occurrence):
     rows = [r for r in csv.DictReader(l for l in open(path) if l.startswith('"'))
             if r.get("Metric Name") == "gpu__time_duration.sum"]
     names = [re.sub(r"^.*?::", "", r["Kernel Name"]).split("(")[0].split("<")[0] for r in rows]
-    starts = [i for i, n in enumerate(names) if n == "k_tensor_acc"]
+    starts = [i for i, n in enumerate(names) if n == "k_tensor_pair"]
     a = starts[occurrence - 1]
     b = starts[occurrence] if occurrence < len(starts) else len(rows)
     # the step ends with the forward NTT (column then row pass) that carries the
@@ -265,7 +265,7 @@ def bytes_per_unit(name, n, dnum):
         return 2 * limb                       # read + write the limb
     if name == "k_key_product":
         return (3 * dnum + 2) * limb          # dnum raised limbs + 2 dnum key limbs in, 2 out
-    if name == "k_tensor_acc":
+    if name in ("k_tensor_acc", "k_tensor_pair"):
         return 7 * limb                       # 4 operand limbs in, 3 out (one term per output here)
     if name in ("k_moddown_combine",):
         return 4 * limb                       # acc, converted limb, base in; out

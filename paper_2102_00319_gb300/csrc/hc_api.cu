@@ -1534,21 +1534,29 @@ namespace {
 std::vector<hc_ct*> mul_relin_rescale_cts(hc_ctx* ctx, const hc_evk* evk, const hc_ct* const* a,
                                           const hc_ct* const* b, int n) {
   const int level = a[0]->level;
-  std::vector<const hc_ct*> xs, ws;
-  std::vector<int> xi, wi, off{0};
   for (int i = 0; i < n; ++i) {
     check_ct(ctx, a[i]);
     check_ct(ctx, b[i]);
     HC_CHECK(a[i]->level == level && b[i]->level == level, HC_ERR_LEVEL_MISMATCH, "batch mixes levels");
     HC_CHECK(a[i]->degree == 1 && b[i]->degree == 1, HC_ERR_INVALID, "degree-1 operands expected");
-    xs.push_back(a[i]);
-    ws.push_back(b[i]);
-    xi.push_back(i);
-    wi.push_back(i);
-    off.push_back(i + 1);
   }
   HC_CHECK(level >= 1, HC_ERR_DEPTH, "no level left to rescale");
-  std::vector<hc_ct*> d = tensor_acc(ctx, xs, ws, xi, wi, off, level, a[0]->scale * b[0]->scale);
+  std::vector<hc_ct*> d = new_cts(ctx, n, level, 2, a[0]->scale * b[0]->scale);
+  {
+    std::vector<BufPtr> keep;
+    std::vector<CtRef> ar, br, dr;
+    for (int i = 0; i < n; ++i) {
+      ar.push_back(a[i]->ref());
+      br.push_back(b[i]->ref());
+      dr.push_back(d[i]->ref());
+    }
+    for (int o0 = 0; o0 < n; o0 += 65535) {
+      const int m = std::min(65535, n - o0);
+      launch_tensor_pair(ctx, refs_dev(ctx, std::vector<CtRef>(dr.begin() + o0, dr.begin() + o0 + m), keep),
+                         refs_dev(ctx, std::vector<CtRef>(ar.begin() + o0, ar.begin() + o0 + m), keep),
+                         refs_dev(ctx, std::vector<CtRef>(br.begin() + o0, br.begin() + o0 + m), keep), m, level + 1);
+    }
+  }
   for (int i = 0; i < n; ++i) d[i]->scale = a[i]->scale * b[i]->scale;
   std::vector<hc_ct*> r = relin_rescale(ctx, evk, d, nullptr);
   for (int i = 0; i < n; ++i) r[i]->scale = d[i]->scale / (double)ctx->P.chain[level];

@@ -161,6 +161,34 @@ __global__ void k_tensor_acc(const CtRef* out, const CtRef* x, const CtRef* w, c
   O.p[2 * O.stride + lo] = reduce128_est(a2, md);
 }
 
+// out[z] = a[z] (x) b[z] (one term per output): d0 = a0 b0, d2 = a1 b1 and
+// d1 = (a0 + a1)(b0 + b1) - d0 - d2 in 128 bits (three products instead of
+// four; a0 + a1 < 2q keeps the product below 2^124 and the difference is the
+// exact a0 b1 + a1 b0).
+__global__ void k_tensor_pair(const CtRef* out, const CtRef* a, const CtRef* b, Tables T) {
+  const int n = 1 << T.log_n;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int l = blockIdx.y, z = blockIdx.z;
+  const DMod md = T.mods[l];
+  const CtRef A = a[z], B = b[z], O = out[z];
+  const size_t lo = (size_t)l * n + c;
+  const u64 a0 = A.p[lo], a1 = A.p[A.stride + lo], b0 = B.p[lo], b1 = B.p[B.stride + lo];
+  const U128 p0{a0 * b0, __umul64hi(a0, b0)}, p2{a1 * b1, __umul64hi(a1, b1)};
+  const u64 sa = a0 + a1, sb = b0 + b1;
+  U128 p1{sa * sb, __umul64hi(sa, sb)};
+  // p1 -= p0 + p2 (no borrow out: the result is a0 b1 + a1 b0 >= 0)
+  u64 t = p1.lo - p0.lo;
+  p1.hi -= p0.hi + (p1.lo < p0.lo);
+  p1.lo = t;
+  t = p1.lo - p2.lo;
+  p1.hi -= p2.hi + (p1.lo < p2.lo);
+  p1.lo = t;
+  O.p[lo] = reduce128_est(p0, md);
+  O.p[O.stride + lo] = reduce128_est(p1, md);
+  O.p[2 * O.stride + lo] = reduce128_est(p2, md);
+}
+
 // NTT-domain automorphism: slot k holds a(psi^{e_k}), e_k = 2 brv(k) + 1;
 // kappa_g(a)(psi^{e}) = a(psi^{e g}).
 __global__ void k_automorph(const CtRef* out, const CtRef* a, int nl, u64 g, Tables T) {
@@ -429,6 +457,17 @@ void launch_scalar(hc_ctx* ctx, bool add, const CtRef* out, const CtRef* a, int 
       k_scalar<<<grid_for(ctx, npoly * nl, items), kT, 0, ctx->stream>>>(add, out, a, nl, scal_dev, ctx->tab);
     }
   LAUNCH_DONE(ctx);
+}
+
+void launch_tensor_pair(hc_ctx* ctx, const CtRef* out, const CtRef* a, const CtRef* b, int items, int nl) {
+  if (items <= 0) return;
+  HC_CHECK(items <= 65535, HC_ERR_INVALID, "too many outputs in one launch");
+  {
+    ProfScope prof_(ctx, "k_tensor_pair", (uint64_t)items * nl);
+    k_tensor_pair<<<grid_for(ctx, nl, items), kT, 0, ctx->stream>>>(out, a, b, ctx->tab);
+  }
+  ctx->launches++;
+  check_launch(ctx);
 }
 
 void launch_tensor_acc(hc_ctx* ctx, const CtRef* out, const CtRef* x, const CtRef* w, const int* xi,
