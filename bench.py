@@ -241,20 +241,33 @@ NCU_TRAFFIC_PER_UNIT = {
 
 # Integer-multiplier roofline of the NTT passes: 64-bit low and high
 # products per SM per clock on GB300, measured by
-# paper_2102_00319_gb300/probes/intmul_throughput.cu.  A Shoup butterfly
-# takes two low products and one high product.
+# paper_2102_00319_gb300/probes/intmul_throughput.cu.  A Shoup product (one
+# per butterfly) takes two low products and one high product.
 LO64_PER_SM_CLK = 14.4
 HI64_PER_SM_CLK = 6.6
-BUTTERFLIES_PER_SM_CLK = 1.0 / (2.0 / LO64_PER_SM_CLK + 1.0 / HI64_PER_SM_CLK)
+MULMODS_PER_SM_CLK = 1.0 / (2.0 / LO64_PER_SM_CLK + 1.0 / HI64_PER_SM_CLK)
 
 
 def butterflies_per_unit(name, n):
     """Butterflies of one limb in one NTT pass (the column pass takes the first
-    floor(log N / 2) stages, the row pass the rest).  The `_ksr` passes carry
-    the fused relinearise + rescale tail on top of their butterflies."""
+    floor(log N / 2) stages, the row pass the rest)."""
     log_n = n.bit_length() - 1
     stages = log_n // 2 if "cols" in name else log_n - log_n // 2
     return stages * (n // 2)
+
+
+def mulmods_per_unit(name, n):
+    """Shoup modular products (two 64-bit low products and one high) of one limb
+    in one NTT pass: one per butterfly, plus the fused relinearise + rescale
+    tail of the `_ksr` passes (row pass: acc P^{-1} and the q_l^{-1} factor per
+    coefficient; column pass: z P^{-1} and the reduction of the lifted |c_l|,
+    a low and a high product, counted as 0.75)."""
+    b = butterflies_per_unit(name, n)
+    if name == "ntt_fwd_rows_ksr":
+        return b + 2 * n
+    if name == "ntt_fwd_cols_ksr":
+        return b + 1.75 * n
+    return b
 
 
 def bytes_per_unit(name, n, dnum):
@@ -821,12 +834,12 @@ def run_gpu(args, rank, world, local):
         # against the multiplier's rate at the SM clock sampled in the timed region
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
-        peak_alu = BUTTERFLIES_PER_SM_CLK * sms * mhz * 1e6 / 1e9
-        got = units * butterflies_per_unit(dom, n) / (tot / 1000.0) / 1e9
-        roofline = {"bound": "alu", "kernel": dom, "achieved": got, "peak": peak_alu, "unit": "Gbutterfly/s",
+        peak_alu = MULMODS_PER_SM_CLK * sms * mhz * 1e6 / 1e9
+        got = units * mulmods_per_unit(dom, n) / (tot / 1000.0) / 1e9
+        roofline = {"bound": "alu", "kernel": dom, "achieved": got, "peak": peak_alu, "unit": "G Shoup mulmod/s",
                     "frac": got / peak_alu, "traffic": traffic,
-                    "peak_source": "derived from measured 64-bit multiply rates: %.2f Shoup butterflies/SM/clk"
-                                   " x %d SMs x %.0f MHz" % (BUTTERFLIES_PER_SM_CLK, sms, mhz),
+                    "peak_source": "derived from measured 64-bit multiply rates: %.2f Shoup products/SM/clk"
+                                   " x %d SMs x %.0f MHz" % (MULMODS_PER_SM_CLK, sms, mhz),
                     "hbm": hbm}
     else:
         roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
