@@ -234,8 +234,10 @@ def run_reference(args, rank, world):
 # 336 limbs per launch), scaled to a launch by its units.  Set an entry to
 # None when its kernel changes until it is captured again.
 NCU_TRAFFIC_PER_UNIT = {
-    "ntt_fwd_cols": None,
-    "ntt_fwd_rows": None,
+    "ntt_fwd_cols": (176.305e6 + 113.815e6) / 336,
+    "ntt_fwd_rows": (209.311e6 + 123.126e6) / 336,
+    "ntt_fwd_cols_ksr": None,
+    "ntt_fwd_rows_ksr": None,
 }
 
 
