@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--batch", type=int, default=64, help="ciphertext pairs per step")
     ap.add_argument("--no-graph", action="store_true", help="time the eager step only")
-    ap.add_argument("--graph-arena-gib", type=int, default=16, help="device arena of the captured step")
+    ap.add_argument("--graph-arena-gib", type=int, default=0,
+                    help="device arena of the captured step (0: 4 GiB + 0.2 GiB per pair)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--e2e-chunk", type=int, default=0, help="pairs per pipeline chunk of the host call (0: auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -234,10 +235,10 @@ def run_reference(args, rank, world):
 # 336 limbs per launch), scaled to a launch by its units.  Set an entry to
 # None when its kernel changes until it is captured again.
 NCU_TRAFFIC_PER_UNIT = {
-    "ntt_fwd_cols": (176.305e6 + 113.815e6) / 336,
-    "ntt_fwd_rows": (209.311e6 + 123.126e6) / 336,
-    "ntt_fwd_cols_ksr": None,
-    "ntt_fwd_rows_ksr": None,
+    "ntt_fwd_cols": (176.306e6 + 113.967e6) / 336,
+    "ntt_fwd_rows": (209.365e6 + 122.659e6) / 336,
+    "ntt_fwd_cols_ksr": (352.484e6 + 273.803e6) / 640,
+    "ntt_fwd_rows_ksr": (1105.544e6 + 317.109e6) / 640,
 }
 
 
@@ -746,7 +747,8 @@ def run_gpu(args, rank, world, local):
     # recomputes all of them from the resident inputs)
     graph_value, graph_same = None, None
     if not args.no_graph:
-        H.hc_graph_begin([ctx], args.graph_arena_gib << 30)
+        arena_gib = args.graph_arena_gib or int(4 + 0.2 * Bn + 0.999)
+        H.hc_graph_begin([ctx], arena_gib << 30)
         g_outs = step()
         graph = H.hc_graph_end([ctx])
         for _ in range(args.warmup):
