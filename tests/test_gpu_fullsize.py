@@ -16,27 +16,53 @@ TOL = 2.0 ** -15
 
 
 def test_deep_n16_batch_sampled_bit_exact():
-    """hc_mul_relin_rescale_batch at N = 2^16, L = 20, dnum = 3, batch 32 (the
-    benchmark's step); pair 5 is recomputed by the oracle."""
+    """hc_mul_relin_rescale_batch at N = 2^16, L = 20, dnum = 3, batch 64 (the
+    benchmark's step, eager and captured into a CUDA graph as the benchmark
+    times it, and through the host-to-host pipelined call); pairs 5 and 63
+    are recomputed by the oracle, every other pair is checked equal across
+    the three forms."""
+    import torch
     from hc_pair import Pair
     ps = W.DEEP_N16
-    p = Pair(ps.log_n, ps.q_bits, ps.p_bits, ps.log2_scale, seed=W.MASTER_SEED + 4)
-    B, k = 32, 5
-    A, Bc = [], []
-    oa = ob = None
+    stream = torch.cuda.Stream()  # a stream of its own: capturable
+    p = Pair(ps.log_n, ps.q_bits, ps.p_bits, ps.log2_scale, seed=W.MASTER_SEED + 4, stream=stream.cuda_stream)
+    B, ks = 64, (5, 63)
+    A, Bc, oracle_in = [], [], {}
     for i in range(B):
         ma, mb = W.int_plaintext(10 + i, p.op.N, 2 ** 50), W.int_plaintext(100 + i, p.op.N, 2 ** 50)
-        if i == k:
+        if i in ks:
             ga, oa = p.encrypt(ma, nonce=2 * i)
             gb, ob = p.encrypt(mb, nonce=2 * i + 1)
+            oracle_in[i] = (oa, ob)
         else:
             ga = H.hc_encrypt(p.ctx, p.g_pk, H.hc_pt_from_coeffs(p.ctx, ma, p.op.L, p.op.scale), p.seed + 1, 2 * i)
             gb = H.hc_encrypt(p.ctx, p.g_pk, H.hc_pt_from_coeffs(p.ctx, mb, p.op.L, p.op.scale), p.seed + 1, 2 * i + 1)
         A.append(ga)
         Bc.append(gb)
     outs = H.hc_mul_relin_rescale_batch(p.ctx, p.g_evk, A, Bc)
-    exp = ckks.rescale(p.op, ckks.relin(p.op, p.o_evk, ckks.mul(p.op, oa, ob)))
-    p.assert_same(outs[k], exp, "batch item %d" % k)
+    for k in ks:
+        oa, ob = oracle_in[k]
+        exp = ckks.rescale(p.op, ckks.relin(p.op, p.o_evk, ckks.mul(p.op, oa, ob)))
+        p.assert_same(outs[k], exp, "batch item %d" % k)
+    eager = [H.hc_ct_export(p.ctx, c)[0] for c in outs]
+    # the captured step, replayed twice
+    H.hc_graph_begin([p.ctx], int(4 + 0.2 * B + 1) << 30)
+    g_outs = H.hc_mul_relin_rescale_batch(p.ctx, p.g_evk, A, Bc)
+    graph = H.hc_graph_end([p.ctx])
+    H.hc_graph_launch(graph)
+    H.hc_graph_launch(graph)
+    for i in range(B):
+        np.testing.assert_array_equal(H.hc_ct_export(p.ctx, g_outs[i])[0], eager[i])
+    del g_outs
+    del graph
+    # host buffers in, host buffers out
+    a_arr = [H.hc_ct_export(p.ctx, c)[0] for c in A]
+    b_arr = [H.hc_ct_export(p.ctx, c)[0] for c in Bc]
+    metas = [(p.op.L, 1, c.meta().scale) for c in A]
+    host = [np.zeros((2, p.op.L, p.op.N), dtype=np.uint64) for _ in range(B)]
+    H.hc_mul_relin_rescale_host(p.ctx, p.g_evk, a_arr, metas, b_arr, metas, host)
+    for i in range(B):
+        np.testing.assert_array_equal(host[i], eager[i])
     # property at full size: slot products of encoded vectors
     za, zb = W.slot_values(1, p.op.K), W.slot_values(2, p.op.K)
     ca = H.hc_encrypt(p.ctx, p.g_pk, H.hc_encode(p.ctx, za, p.op.scale, p.op.L), 3, 0)

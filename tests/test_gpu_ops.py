@@ -108,6 +108,27 @@ def test_host_pipeline_matches_device_batch(pair):
         H.hc_mul_relin_rescale_host(pair.ctx, pair.g_evk, bad, a_m, b_arr, b_m, outs, chunk=2)
 
 
+def test_batch_mul_relin_rescale_every_level_and_edges(pair):
+    """The fused batch at every level down to 1 (truncated last digit at low
+    levels, a one-limb fused tail at level 1) equals the oracle; an empty
+    batch, an aliased pair (a is b) and level 0 behave."""
+    op = pair.op
+    for lv in range(op.L, 0, -1):
+        ga, oa = pair.encrypt_values(W.slot_values(80 + lv, op.K), level=lv, nonce=800 + lv)
+        gb, ob = pair.encrypt_values(W.slot_values(90 + lv, op.K), level=lv, nonce=900 + lv)
+        r = H.hc_mul_relin_rescale_batch(pair.ctx, pair.g_evk, [ga, ga], [gb, ga])
+        pair.assert_same(r[0], ckks.rescale(op, ckks.relin(op, pair.o_evk, ckks.mul(op, oa, ob))), "l=%d" % lv)
+        pair.assert_same(r[1], ckks.rescale(op, ckks.relin(op, pair.o_evk, ckks.mul(op, oa, oa))), "a*a l=%d" % lv)
+    assert H.hc_mul_relin_rescale_batch(pair.ctx, pair.g_evk, [], []) == []
+    assert H.hc_ct_import_batch(pair.ctx, [], []) == []
+    H.hc_ct_export_batch(pair.ctx, [], [])
+    assert H.hc_mul_relin_rescale_host(pair.ctx, pair.g_evk, [], [], [], [], []) == []
+    g0, _ = pair.encrypt_values(W.slot_values(99, op.K), level=0, nonce=999)
+    with pytest.raises(H.HcError) as e:
+        H.hc_mul_relin_rescale_batch(pair.ctx, pair.g_evk, [g0], [g0])
+    assert e.value.code == -5  # HC_ERR_DEPTH
+
+
 def test_import_rejects_out_of_range(pair):
     data = np.zeros((2, 1, pair.op.N), dtype=np.uint64)
     data[1, 0, 7] = pair.op.q[0]
