@@ -270,6 +270,33 @@ int hc_mul_relin_rescale_host(hc_ctx *ctx, const hc_evk *evk, const uint64_t *co
  */
 int hc_relin_noalloc(hc_ctx *ctx, const hc_evk *evk, const hc_ct *x, hc_ct *out);
 
+/* ------------------------------------------------------------ autotuning */
+/*
+ * Tile and launch shapes picked by measurement.  The paper has no
+ * counterpart (its CPU code has no tiles); results are bit-identical for
+ * every choice, only the speed changes.  Knobs:
+ *   HC_TUNE_NTT             NTT block size for the context's ring degree:
+ *                           0 = 256 threads (tiles of 16 columns / rows at
+ *                           N = 2^16), 1 = 128 threads (tiles of 8, the
+ *                           default), 2 = 64 threads (tiles of 4; N >= 2^13);
+ *   HC_TUNE_KEY_PRODUCT_Z   item groups of a key-product launch, as a
+ *                           multiple (1..64) of the default;
+ *   HC_TUNE_MODUP_SPLIT     blocks (1..64) over which a ModUp conversion
+ *                           splits its output primes.
+ * hc_autotune times each knob's candidates on scratch data shaped like
+ * `items` ciphertext pairs at the top level (one knob at a time, the others
+ * at their current values, three timed launches each after a warm-up) and
+ * keeps the fastest.  `report` (may be NULL; cap bytes, always
+ * NUL-terminated) receives one line per knob: the chosen value and the
+ * microseconds per launch of every candidate.  Not capturable; it
+ * synchronises the context stream.
+ */
+enum { HC_TUNE_NTT = 0, HC_TUNE_KEY_PRODUCT_Z = 1, HC_TUNE_MODUP_SPLIT = 2 };
+int hc_autotune(hc_ctx *ctx, const hc_evk *evk, int items, char *report, size_t cap);
+int hc_tune_set(hc_ctx *ctx, int knob, int value);
+/* The knob's current value, or a negative error code. */
+int hc_tune_get(const hc_ctx *ctx, int knob);
+
 /* ------------------------------------------------------- graph capture */
 /*
  * One CUDA graph for a whole multi-instance computation, replayed with one

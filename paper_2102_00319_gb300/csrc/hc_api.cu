@@ -1,6 +1,7 @@
 // C ABI of libhecnn (declared in include/hecnn.h): handle lifecycle and the
 // composition of the kernels into the scheme's operations and CNN layers.
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -1574,6 +1575,144 @@ extern "C" int hc_mul_relin_rescale_batch(hc_ctx* ctx, const hc_evk* evk, const 
     std::vector<hc_ct*> r = mul_relin_rescale_cts(ctx, evk, a, b, n);
     for (int i = 0; i < n; ++i) outs[i] = r[i];
   });
+}
+
+// =====================================================================
+// Autotuning
+// =====================================================================
+extern "C" int hc_tune_set(hc_ctx* ctx, int knob, int value) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    switch (knob) {
+      case HC_TUNE_NTT:
+        HC_CHECK(value >= 0 && value <= (ctx->P.log_n >= 13 ? 2 : 1), HC_ERR_INVALID,
+                 "NTT variant must be 0, 1 (or 2 for N >= 2^13)");
+        ctx->tune.ntt_variant[ctx->P.log_n] = value;
+        break;
+      case HC_TUNE_KEY_PRODUCT_Z:
+        HC_CHECK(value >= 1 && value <= 64, HC_ERR_INVALID, "key-product groups must be 1..64");
+        ctx->tune.kp_zmul = value;
+        break;
+      case HC_TUNE_MODUP_SPLIT:
+        HC_CHECK(value >= 1 && value <= 64, HC_ERR_INVALID, "ModUp split must be 1..64");
+        ctx->tune.modup_split = value;
+        break;
+      default:
+        throw HcError{HC_ERR_INVALID, "unknown tuning knob"};
+    }
+  });
+}
+
+extern "C" int hc_tune_get(const hc_ctx* ctx, int knob) {
+  if (!ctx) return HC_ERR_INVALID;
+  switch (knob) {
+    case HC_TUNE_NTT: return ctx->tune.ntt_variant[ctx->P.log_n];
+    case HC_TUNE_KEY_PRODUCT_Z: return ctx->tune.kp_zmul;
+    case HC_TUNE_MODUP_SPLIT: return ctx->tune.modup_split;
+    default: return HC_ERR_INVALID;
+  }
+}
+
+extern "C" int hc_autotune(hc_ctx* ctx, const hc_evk* evk, int items, char* report, size_t cap) {
+  if (!ctx) return HC_ERR_INVALID;
+  std::vector<cudaEvent_t> evs;
+  int rc = guard(ctx, [&] {
+    HC_CHECK(evk && items >= 1, HC_ERR_INVALID, "bad arguments");
+    HC_CHECK(!ctx->arena, HC_ERR_INVALID, "autotuning cannot be captured");
+    const int n = ctx->P.n, level = ctx->P.L, nq = level + 1, alpha = ctx->P.alpha;
+    const int next = nq + alpha, dnum = ctx->lv[level].dnum;
+    const size_t limb = (size_t)n, ext_words = (size_t)next * limb;
+    // scratch for `m` items, at most ~6 GiB
+    const size_t per_item = (size_t)2 * nq * limb + (size_t)dnum * ext_words + 2 * ext_words;
+    const int m = (int)std::max<size_t>(1, std::min<size_t>((size_t)items, ((size_t)6 << 30) / (per_item * 8)));
+    std::vector<BufPtr> keep;
+    BufPtr work = ctx->buffer(per_item * m);
+    keep.push_back(work);
+    HC_CUDA(cudaMemsetAsync(work->ptr, 0, per_item * m * sizeof(u64), ctx->stream));
+    u64* cts = work->ptr;                              // [m][2][nq][N]
+    u64* ext = cts + (size_t)m * 2 * nq * limb;        // [m][dnum][next][N]
+    u64* acc = ext + (size_t)m * dnum * ext_words;     // [m][2][next][N]
+    for (int i = 0; i < 2; ++i) {
+      cudaEvent_t e;
+      HC_CUDA(cudaEventCreate(&e));
+      evs.push_back(e);
+    }
+    auto time_us = [&](const std::function<void()>& f) {
+      f();  // warm-up
+      HC_CUDA(cudaEventRecord(evs[0], ctx->stream));
+      for (int r = 0; r < 3; ++r) f();
+      HC_CUDA(cudaEventRecord(evs[1], ctx->stream));
+      HC_CUDA(cudaEventSynchronize(evs[1]));
+      float ms = 0;
+      HC_CUDA(cudaEventElapsedTime(&ms, evs[0], evs[1]));
+      return 1000.0 * ms / 3;
+    };
+    std::string rep;
+    char line[256];
+    // NTT: forward and inverse transforms of m degree-1 ciphertexts
+    {
+      const LimbSet cs = limbset_base(cts, 2 * nq * limb, nq * limb, 2, nq, 0, nullptr);
+      double best = 1e300;
+      int pick = 0;
+      std::string t;
+      for (int v = 0; v <= (ctx->P.log_n >= 13 ? 2 : 1); ++v) {
+        ctx->tune.ntt_variant[ctx->P.log_n] = v;
+        const double us = time_us([&] {
+          launch_ntt(ctx, cs, m, false);
+          launch_ntt(ctx, cs, m, true);
+        });
+        std::snprintf(line, sizeof line, " %d:%.1f", v, us);
+        t += line;
+        if (us < best) best = us, pick = v;
+      }
+      ctx->tune.ntt_variant[ctx->P.log_n] = pick;
+      std::snprintf(line, sizeof line, "ntt_variant %d us%s\n", pick, t.c_str());
+      rep += line;
+    }
+    // key product over the raised digits
+    {
+      double best = 1e300;
+      int pick = 1;
+      std::string t;
+      for (int z : {1, 2, 4, 8}) {
+        ctx->tune.kp_zmul = z;
+        const double us = time_us([&] {
+          launch_key_product_batched(ctx, level, ext, (u64)dnum * ext_words, evk->relin.buf->ptr, acc,
+                                     2 * (u64)ext_words, m);
+        });
+        std::snprintf(line, sizeof line, " %d:%.1f", z, us);
+        t += line;
+        if (us < best) best = us, pick = z;
+      }
+      ctx->tune.kp_zmul = pick;
+      std::snprintf(line, sizeof line, "key_product_z %d us%s\n", pick, t.c_str());
+      rep += line;
+    }
+    // ModUp conversion of digit 0
+    {
+      double best = 1e300;
+      int pick = 1;
+      std::string t;
+      for (int sp : {1, 2, 4}) {
+        ctx->tune.modup_split = sp;
+        const double us = time_us([&] {
+          launch_modup_bconv_fast(ctx, level, 0, cts, 2 * (u64)nq * limb, ext, (u64)dnum * ext_words, m);
+        });
+        std::snprintf(line, sizeof line, " %d:%.1f", sp, us);
+        t += line;
+        if (us < best) best = us, pick = sp;
+      }
+      ctx->tune.modup_split = pick;
+      std::snprintf(line, sizeof line, "modup_split %d us%s\n", pick, t.c_str());
+      rep += line;
+    }
+    HC_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (report && cap > 0) {
+      std::snprintf(report, cap, "%s", rep.c_str());
+    }
+  });
+  for (cudaEvent_t e : evs) cudaEventDestroy(e);
+  return rc;
 }
 
 // Host-to-host pipeline: all input slabs are allocated up front (so the copy

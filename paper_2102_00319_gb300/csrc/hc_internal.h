@@ -65,8 +65,18 @@ struct LevelConsts {
   int rescale_off = -1;
 };
 
+// Tile and launch-shape choices (set by hc_autotune or hc_tune_set).
+struct HcTune {
+  // per log N: 0 = 256-thread blocks, 1 = 128 (the default: measured fastest
+  // at N = 2^13..2^16 on GB300), 2 = 64 (N >= 2^13)
+  int ntt_variant[17] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
+  int kp_zmul = 1;           // key product: item groups in the grid's z, times the default
+  int modup_split = 1;       // ModUp conversion: output primes split over this many blocks
+};
+
 struct hc_ctx {
   hc_params P;
+  HcTune tune;
   int device = 0;
   cudaStream_t stream = nullptr;
   hc_allocator alloc{};

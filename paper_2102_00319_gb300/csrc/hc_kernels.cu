@@ -702,7 +702,9 @@ __global__ void __launch_bounds__(kT) k_modup_bconv_h(const u64* xcoef, u64 x_it
   Half30 v[NS];
 #pragma unroll
   for (int i = 0; i < NS; ++i) v[i] = halves30(shoup(x[(size_t)(d0 + i) * n + c], cst[i], cst[NS + i], md[d0 + i].q));
-  for (int t = 0; t < next; ++t) {
+  // the output primes may be split over gridDim.y blocks (a tuning choice)
+  const int per = (next + gridDim.y - 1) / gridDim.y, t_end = min(next, ((int)blockIdx.y + 1) * per);
+  for (int t = blockIdx.y * per; t < t_end; ++t) {
     if (t >= d0 && t < d0 + NS) continue;
     Acc30 acc{0, 0, 0};
 #pragma unroll
@@ -870,7 +872,8 @@ void launch_modup_bconv_fast(hc_ctx* ctx, int level, int j, const u64* xcoef, u6
   const u64* cst = ctx->ks(ctx->lv[level].modup_off[j]);
   // (the halves form stages 16 bytes per constant, the other 8)
   const size_t smem = (size_t)next * ns * 2 * sizeof(u64) + (size_t)next * sizeof(DMod);
-  const dim3 g = grid_for(ctx, 1, items);
+  const bool halves_split = ctx->P.below_2_60 && ns <= 8;
+  const dim3 g = grid_for(ctx, halves_split ? std::max(1, std::min(ctx->tune.modup_split, next)) : 1, items);
   ProfScope prof_(ctx, "k_modup_bconv", (uint64_t)items * (next - ns));
   const bool halves = ctx->P.below_2_60;
 #define HC_MODUP(NS)                                                                                          \
@@ -926,7 +929,8 @@ void launch_key_product_batched(hc_ctx* ctx, int level, const u64* ext, u64 ext_
                                 u64* acc, u64 acc_item_stride, int items, const CtRef* digit_src) {
   const int next = level + 1 + ctx->P.alpha, dnum = ctx->lv[level].dnum;
   // a few item groups in z so small batches still fill the GPU
-  const int zgroups = std::min(items, std::max(1, 2048 / (next * ((ctx->P.n + kT - 1) / kT))));
+  const int zgroups =
+      std::min(items, std::max(1, 2048 / (next * ((ctx->P.n + kT - 1) / kT))) * std::max(1, ctx->tune.kp_zmul));
   const dim3 g = grid_for(ctx, next, zgroups);
   ProfScope prof_(ctx, "k_key_product", (uint64_t)items * next);
   const bool halves = ctx->P.below_2_60;

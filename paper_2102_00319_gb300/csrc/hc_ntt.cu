@@ -26,7 +26,8 @@
 
 namespace {
 
-constexpr int kThreads = 256;
+// Block sizes: 2^8 threads (tiles of 16 columns / rows at N = 2^16) or 2^7
+// (tiles of 8); the context's tuning table picks one per ring degree.
 
 // Forward CT stages ST0 .. ST0+K-1 on 2^K points; point i has global index
 // jb + (i << LS), where jb has no bits in common with i << LS (so the
@@ -102,10 +103,11 @@ __device__ __forceinline__ const u64* input_limb(const LimbSet& s, const LimbSet
 
 // Column pass: stages 0..N1-1 (forward) over R = 2^N1 rows (N1 = K1 + K2) of
 // TC = 2^TCL columns starting at blockIdx.x * TC.  Shared tile [row][col].
-template <bool INV, int LOGN, int K1, int K2, int TCL, bool FUSE>
-__global__ void __launch_bounds__(kThreads) k_cols(LimbSet s, LimbSet in, int use_in, int scale, KsrFuse f,
-                                                   Tables T) {
+template <bool INV, int LOGN, int K1, int K2, int TCL, bool FUSE, int TL>
+__global__ void __launch_bounds__(1 << TL) k_cols(LimbSet s, LimbSet in, int use_in, int scale, KsrFuse f,
+                                                  Tables T) {
   constexpr int N1 = K1 + K2, N2 = LOGN - N1, TC = 1 << TCL;
+  constexpr u32 kThreads = 1u << TL;
   extern __shared__ u64 sm[];
   u64* a;
   int pid;
@@ -182,8 +184,9 @@ __global__ void __launch_bounds__(kThreads) k_cols(LimbSet s, LimbSet in, int us
 
 // Row pass: stages N1..LOGN-1 (forward) inside RP = 2^RPL rows of C = 2^N2
 // adjacent points (N2 = K1 + K2).  Shared rows padded by one word per 2^K2.
-template <bool INV, int LOGN, int K1, int K2, int RPL, bool FUSE>
-__global__ void __launch_bounds__(kThreads) k_rows(LimbSet s, LimbSet in, int use_in, KsrFuse f, Tables T) {
+template <bool INV, int LOGN, int K1, int K2, int RPL, bool FUSE, int TL>
+__global__ void __launch_bounds__(1 << TL) k_rows(LimbSet s, LimbSet in, int use_in, KsrFuse f, Tables T) {
+  constexpr u32 kThreads = 1u << TL;
   constexpr int N2 = K1 + K2, N1 = LOGN - N2, C = 1 << N2, RP = 1 << RPL;
   constexpr int PADW = C + (C >> K2);
   extern __shared__ u64 sm[];
@@ -296,51 +299,81 @@ struct Split {
 
 constexpr int cmin(int a, int b) { return a < b ? a : b; }
 
-// tiles: enough (column or row, offset) work items for all 256 threads, at
+// tiles: enough (column or row, offset) work items for all 2^TL threads, at
 // most 48 KB of shared memory
-template <int N1, int N2>
+template <int N1, int N2, int TL>
 struct ColTile {
-  static constexpr int raw = cmin(8 - Split<N1>::KMIN, N2);
+  static constexpr int raw = cmin(TL - Split<N1>::KMIN, N2);
   static constexpr int TCL = (1 << (N1 + raw)) * 8 > 48 * 1024 ? raw - 1 : raw;
 };
-template <int N1, int N2>
+template <int N1, int N2, int TL>
 struct RowTile {
   static constexpr int K2 = Split<N2>::K2;
   static constexpr int PADW = (1 << N2) + (1 << (N2 - K2));
-  static constexpr int raw = cmin(8 - Split<N2>::KMIN, N1);
+  static constexpr int raw = cmin(TL - Split<N2>::KMIN, N1);
   static constexpr int RPL = (1 << raw) * PADW * 8 > 48 * 1024 ? raw - 1 : raw;
 };
 
-template <bool INV, int LOGN>
-void launch_pass_cols(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, const LimbSet* in = nullptr,
-                      bool scale = true, const KsrFuse* fuse = nullptr) {
+template <bool INV, int LOGN, int TL>
+void launch_pass_cols_t(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, const LimbSet* in, bool scale,
+                        const KsrFuse* fuse) {
   constexpr int N1 = LOGN / 2, N2 = LOGN - N1;
   using Sp = Split<N1>;
-  constexpr int TCL = ColTile<N1, N2>::TCL;
+  constexpr int TCL = ColTile<N1, N2, TL>::TCL;
   dim3 grid(1u << (N2 - TCL), ylimbs, items);
   const size_t smem = ((size_t)1 << (N1 + TCL)) * sizeof(u64);
   ProfScope p(ctx, INV ? "ntt_inv_cols" : (fuse ? "ntt_fwd_cols_ksr" : "ntt_fwd_cols"), (uint64_t)ylimbs * items);
   if (!INV && fuse)
-    k_cols<false, LOGN, Sp::K1, Sp::K2, TCL, true><<<grid, kThreads, smem, ctx->stream>>>(s, s, 0, 1, *fuse, ctx->tab);
+    k_cols<false, LOGN, Sp::K1, Sp::K2, TCL, true, TL><<<grid, 1 << TL, smem, ctx->stream>>>(s, s, 0, 1, *fuse,
+                                                                                           ctx->tab);
   else
-    k_cols<INV, LOGN, Sp::K1, Sp::K2, TCL, false><<<grid, kThreads, smem, ctx->stream>>>(
+    k_cols<INV, LOGN, Sp::K1, Sp::K2, TCL, false, TL><<<grid, 1 << TL, smem, ctx->stream>>>(
         s, in ? *in : s, in ? 1 : 0, scale ? 1 : 0, KsrFuse{}, ctx->tab);
+}
+
+template <bool INV, int LOGN, int TL>
+void launch_pass_rows_t(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, const LimbSet* in,
+                        const KsrFuse* fuse) {
+  constexpr int N1 = LOGN / 2, N2 = LOGN - N1;
+  using Sp = Split<N2>;
+  constexpr int RPL = RowTile<N1, N2, TL>::RPL;
+  dim3 grid(1u << (N1 - RPL), ylimbs, items);
+  const size_t smem = ((size_t)1 << RPL) * RowTile<N1, N2, TL>::PADW * sizeof(u64);
+  ProfScope p(ctx, INV ? "ntt_inv_rows" : (fuse ? "ntt_fwd_rows_ksr" : "ntt_fwd_rows"), (uint64_t)ylimbs * items);
+  if (!INV && fuse)
+    k_rows<false, LOGN, Sp::K1, Sp::K2, RPL, true, TL><<<grid, 1 << TL, smem, ctx->stream>>>(s, s, 0, *fuse,
+                                                                                           ctx->tab);
+  else
+    k_rows<INV, LOGN, Sp::K1, Sp::K2, RPL, false, TL><<<grid, 1 << TL, smem, ctx->stream>>>(
+        s, in ? *in : s, in ? 1 : 0, KsrFuse{}, ctx->tab);
+}
+
+// variant 0: 256-thread blocks, 1: 128-thread blocks, 2: 64-thread blocks
+// (N >= 2^13 only; smaller rings fall back to 128)
+template <bool INV, int LOGN>
+void launch_pass_cols(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, const LimbSet* in = nullptr,
+                      bool scale = true, const KsrFuse* fuse = nullptr) {
+  const int v = ctx->tune.ntt_variant[LOGN];
+  if constexpr (LOGN >= 13) {
+    if (v == 2) return launch_pass_cols_t<INV, LOGN, 6>(ctx, s, items, ylimbs, in, scale, fuse);
+  }
+  if (v >= 1)
+    launch_pass_cols_t<INV, LOGN, 7>(ctx, s, items, ylimbs, in, scale, fuse);
+  else
+    launch_pass_cols_t<INV, LOGN, 8>(ctx, s, items, ylimbs, in, scale, fuse);
 }
 
 template <bool INV, int LOGN>
 void launch_pass_rows(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, const LimbSet* in = nullptr,
                       const KsrFuse* fuse = nullptr) {
-  constexpr int N1 = LOGN / 2, N2 = LOGN - N1;
-  using Sp = Split<N2>;
-  constexpr int RPL = RowTile<N1, N2>::RPL;
-  dim3 grid(1u << (N1 - RPL), ylimbs, items);
-  const size_t smem = ((size_t)1 << RPL) * RowTile<N1, N2>::PADW * sizeof(u64);
-  ProfScope p(ctx, INV ? "ntt_inv_rows" : (fuse ? "ntt_fwd_rows_ksr" : "ntt_fwd_rows"), (uint64_t)ylimbs * items);
-  if (!INV && fuse)
-    k_rows<false, LOGN, Sp::K1, Sp::K2, RPL, true><<<grid, kThreads, smem, ctx->stream>>>(s, s, 0, *fuse, ctx->tab);
+  const int v = ctx->tune.ntt_variant[LOGN];
+  if constexpr (LOGN >= 13) {
+    if (v == 2) return launch_pass_rows_t<INV, LOGN, 6>(ctx, s, items, ylimbs, in, fuse);
+  }
+  if (v >= 1)
+    launch_pass_rows_t<INV, LOGN, 7>(ctx, s, items, ylimbs, in, fuse);
   else
-    k_rows<INV, LOGN, Sp::K1, Sp::K2, RPL, false><<<grid, kThreads, smem, ctx->stream>>>(s, in ? *in : s, in ? 1 : 0,
-                                                                                         KsrFuse{}, ctx->tab);
+    launch_pass_rows_t<INV, LOGN, 8>(ctx, s, items, ylimbs, in, fuse);
 }
 
 template <int LOGN>

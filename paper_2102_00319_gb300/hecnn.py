@@ -23,6 +23,9 @@ ERRORS = {
     -1: "HC_ERR_INVALID", -2: "HC_ERR_LEVEL_MISMATCH", -3: "HC_ERR_SCALE_MISMATCH", -4: "HC_ERR_NO_KEY",
     -5: "HC_ERR_DEPTH", -6: "HC_ERR_OOM", -7: "HC_ERR_CUDA", -8: "HC_ERR_TIMEOUT",
 }
+HC_TUNE_NTT = 0
+HC_TUNE_KEY_PRODUCT_Z = 1
+HC_TUNE_MODUP_SPLIT = 2
 HC_PACK_BATCH = 0
 HC_PACK_SINGLE = 1
 HC_PACK_SINGLE_HOISTED = 2
@@ -40,7 +43,7 @@ EXPORTS = [
     "hc_mul_relin_rescale_batch", "hc_enc_conv2d", "hc_enc_poly_act", "hc_enc_pool", "hc_enc_fc",
     "hc_relin_noalloc", "hc_graph_begin", "hc_graph_end", "hc_graph_launch", "hc_graph_destroy",
     "hc_enc_conv2d_single_batch", "hc_enc_fc_rotsum", "hc_ct_import_batch", "hc_ct_export_batch",
-    "hc_mul_relin_rescale_host",
+    "hc_mul_relin_rescale_host", "hc_autotune", "hc_tune_set", "hc_tune_get",
 ]
 
 
@@ -113,6 +116,9 @@ def load(path: str = LIB_PATH):
         "hc_ct_meta_of": (c_int, [vp, ctypes.POINTER(CtMeta)]),
         "hc_ct_import_batch": (c_int, [vp, pp, ctypes.POINTER(CtMeta), c_int, pp]),
         "hc_ct_export_batch": (c_int, [vp, pp, c_int, pp, ctypes.POINTER(ctypes.c_size_t)]),
+        "hc_autotune": (c_int, [vp, vp, c_int, ctypes.c_char_p, ctypes.c_size_t]),
+        "hc_tune_set": (c_int, [vp, c_int, c_int]),
+        "hc_tune_get": (c_int, [vp, c_int]),
         "hc_mul_relin_rescale_host": (c_int, [vp, vp, pp, ctypes.POINTER(CtMeta), pp, ctypes.POINTER(CtMeta), c_int,
                                               c_int, pp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(CtMeta)]),
         "hc_ct_destroy": (None, [vp]),
@@ -472,6 +478,25 @@ def hc_mul_relin_rescale_host(ctx, evk, a_arrays, a_metas, b_arrays, b_metas, ou
     _check(ctx, load().hc_mul_relin_rescale_host(ctx.ptr, evk.ptr, ptrs(a_arrays), metas(a_metas), ptrs(b_arrays),
                                                  metas(b_metas), n, int(chunk), ptrs(out_arrays), caps, out_m))
     return [out_m[i] for i in range(n)]
+
+
+def hc_autotune(ctx, evk, items):
+    """Times the tuning knobs' candidates and keeps the fastest; returns the
+    report (one line per knob: chosen value, microseconds per candidate)."""
+    buf = ctypes.create_string_buffer(4096)
+    _check(ctx, load().hc_autotune(ctx.ptr, evk.ptr, int(items), buf, len(buf)))
+    return buf.value.decode()
+
+
+def hc_tune_set(ctx, knob, value):
+    _check(ctx, load().hc_tune_set(ctx.ptr, int(knob), int(value)))
+
+
+def hc_tune_get(ctx, knob):
+    v = load().hc_tune_get(ctx.ptr, int(knob))
+    if v < 0:
+        raise HcError(v, "hc_tune_get")
+    return v
 
 
 def _unary(name, ctx, *args):

@@ -63,6 +63,14 @@ def test_deep_n16_batch_sampled_bit_exact():
     H.hc_mul_relin_rescale_host(p.ctx, p.g_evk, a_arr, metas, b_arr, metas, host)
     for i in range(B):
         np.testing.assert_array_equal(host[i], eager[i])
+    # the other NTT tile shapes at N = 2^16 (autotuning choices) give the same words
+    default = H.hc_tune_get(p.ctx, H.HC_TUNE_NTT)
+    for v in (0, 1, 2):
+        H.hc_tune_set(p.ctx, H.HC_TUNE_NTT, v)
+        r = H.hc_mul_relin_rescale_batch(p.ctx, p.g_evk, [A[k] for k in ks], [Bc[k] for k in ks])
+        for k, c in zip(ks, r):
+            np.testing.assert_array_equal(H.hc_ct_export(p.ctx, c)[0], eager[k])
+    H.hc_tune_set(p.ctx, H.HC_TUNE_NTT, default)
     # property at full size: slot products of encoded vectors
     za, zb = W.slot_values(1, p.op.K), W.slot_values(2, p.op.K)
     ca = H.hc_encrypt(p.ctx, p.g_pk, H.hc_encode(p.ctx, za, p.op.scale, p.op.L), 3, 0)

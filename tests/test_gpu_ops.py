@@ -129,6 +129,59 @@ def test_batch_mul_relin_rescale_every_level_and_edges(pair):
     assert e.value.code == -5  # HC_ERR_DEPTH
 
 
+def test_autotune_and_every_tuning_choice_bit_identical(pair):
+    """hc_autotune picks a value for every knob; every candidate value of every
+    knob gives the same words (tiles and launch shapes only)."""
+    op = pair.op
+    ga, _ = pair.encrypt_values(W.slot_values(41, op.K), nonce=4100)
+    gb, _ = pair.encrypt_values(W.slot_values(42, op.K), nonce=4200)
+    report = H.hc_autotune(pair.ctx, pair.g_evk, 4)
+    lines = dict(l.split(" ", 1) for l in report.strip().splitlines())
+    assert set(lines) == {"ntt_variant", "key_product_z", "modup_split"}
+    assert int(lines["ntt_variant"].split()[0]) == H.hc_tune_get(pair.ctx, H.HC_TUNE_NTT)
+    want = None
+    for ntt in (0, 1):
+        for kz in (1, 4):
+            for sp in (1, 3):
+                H.hc_tune_set(pair.ctx, H.HC_TUNE_NTT, ntt)
+                H.hc_tune_set(pair.ctx, H.HC_TUNE_KEY_PRODUCT_Z, kz)
+                H.hc_tune_set(pair.ctx, H.HC_TUNE_MODUP_SPLIT, sp)
+                r = H.hc_mul_relin_rescale_batch(pair.ctx, pair.g_evk, [ga, gb], [gb, gb])
+                got = [H.hc_ct_export(pair.ctx, c)[0] for c in r]
+                rot = H.hc_rotate_hoisted(pair.ctx, pair.g_evk, ga, [1, 3])
+                got += [H.hc_ct_export(pair.ctx, c)[0] for c in rot]
+                if want is None:
+                    want = got
+                for x, y in zip(got, want):
+                    np.testing.assert_array_equal(x, y)
+    for knob, bad in ((H.HC_TUNE_NTT, 2), (H.HC_TUNE_KEY_PRODUCT_Z, 0), (H.HC_TUNE_MODUP_SPLIT, 65), (7, 1)):  # N = 2^10: no variant 2
+        with pytest.raises(H.HcError):
+            H.hc_tune_set(pair.ctx, knob, bad)
+    H.hc_tune_set(pair.ctx, H.HC_TUNE_NTT, 1)
+    H.hc_tune_set(pair.ctx, H.HC_TUNE_KEY_PRODUCT_Z, 1)
+    H.hc_tune_set(pair.ctx, H.HC_TUNE_MODUP_SPLIT, 1)
+
+
+@pytest.mark.parametrize("log_n", [13, 14, 15])
+def test_ntt_tile_variants_match_oracle(log_n):
+    """Every NTT block size the tuner can pick at N = 2^13..2^15 (including
+    the 64-thread tiles that exist only there) gives the oracle's words for a
+    multiply + relinearise + rescale and a rotation."""
+    from hc_pair import Pair
+    p = Pair(log_n, [50, 30, 30], [50], 30, seed=70 + log_n, rot_steps=[5])
+    op = p.op
+    ga, oa = p.encrypt_values(W.slot_values(71, op.K), nonce=1)
+    gb, ob = p.encrypt_values(W.slot_values(72, op.K), nonce=2)
+    want_m = ckks.rescale(op, ckks.relin(op, p.o_evk, ckks.mul(op, oa, ob)))
+    want_r = ckks.rotate(op, p.o_evk, oa, 5)
+    for v in (0, 1, 2):
+        H.hc_tune_set(p.ctx, H.HC_TUNE_NTT, v)
+        p.assert_same(H.hc_mul_relin_rescale_batch(p.ctx, p.g_evk, [ga], [gb])[0], want_m, "mul v=%d" % v)
+        p.assert_same(H.hc_rotate(p.ctx, p.g_evk, ga, 5), want_r, "rot v=%d" % v)
+    with pytest.raises(H.HcError):
+        H.hc_tune_set(p.ctx, H.HC_TUNE_NTT, 3)
+
+
 def test_import_rejects_out_of_range(pair):
     data = np.zeros((2, 1, pair.op.N), dtype=np.uint64)
     data[1, 0, 7] = pair.op.q[0]
