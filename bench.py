@@ -236,10 +236,10 @@ def run_reference(args, rank, world):
 # 336 limbs per launch), scaled to a launch by its units.  Set an entry to
 # None when its kernel changes until it is captured again.
 NCU_TRAFFIC_PER_UNIT = {
-    "ntt_fwd_cols": (176.306e6 + 113.967e6) / 336,
-    "ntt_fwd_rows": (209.365e6 + 122.659e6) / 336,
-    "ntt_fwd_cols_ksr": (352.484e6 + 273.803e6) / 640,
-    "ntt_fwd_rows_ksr": (1105.544e6 + 317.109e6) / 640,
+    "ntt_fwd_cols": (176.303e6 + 120.248e6) / 336,
+    "ntt_fwd_rows": (209.214e6 + 122.685e6) / 336,
+    "ntt_fwd_cols_ksr": (352.510e6 + 279.961e6) / 640,
+    "ntt_fwd_rows_ksr": (1114.173e6 + 317.006e6) / 640,
 }
 
 
