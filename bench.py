@@ -306,6 +306,7 @@ def cnn_leg(args, H, W, np, torch, local):
     K = ctx.n // 2
     seed = W.MASTER_SEED + 2
     sk, pk, evk = H.hc_keygen(ctx, seed)
+    tuning = H.hc_autotune(ctx, evk, 64)
     imgs = W.images(seed + 20, K, c["H"], c["W"])
     cw = W.conv_weights(seed + 21, c["cout"], c["k"], c["k"])
     Ho = (c["H"] - c["k"]) // c["stride"] + 1
@@ -415,7 +416,7 @@ def cnn_leg(args, H, W, np, torch, local):
         "images_per_s_batched": K / t_b, "images_per_s_per_op": K / t_p,
         "ms_batched": 1000 * t_b, "ms_per_op": 1000 * t_p, "speedup_batched_vs_per_op": t_p / t_b,
         "launches_batched": launches_b, "launches_per_op": launches_p,
-        "bit_identical_batched_vs_per_op": same, "max_logit_error_vs_fp64": err,
+        "bit_identical_batched_vs_per_op": same, "max_logit_error_vs_fp64": err, "tuning": tuning,
         "single_ct_conv_x2_ms": 1000 * t_single,
         "single_ct_workload": "single_n12: 8x8 image, 3x3 conv by 8 rotations, x^2",
     }
@@ -588,6 +589,7 @@ def deep_leg(H, W, np, torch, local):
     stream = torch.cuda.current_stream()
     ctx = H.hc_ctx_create(params, local, stream.cuda_stream)
     sk, pk, evk = H.hc_keygen(ctx, W.MASTER_SEED + 4, W.deep_rot_steps(28, 10))
+    tuning = H.hc_autotune(ctx, evk, 16)
     scale = 2.0 ** ps.log2_scale
     C, n_out, K = d["cout"], d["n_out"], ctx.n // 2
     img = W.images(60, 1, 28, 28)[0]
@@ -620,7 +622,7 @@ def deep_leg(H, W, np, torch, local):
     err = float(np.max(np.abs(got - ref_cnn.deep_network(img, cw, act, fw))))
     assert err < 2.0 ** -15, err
     return {"workload": "deep_n16_l20: 28x28 image per ciphertext, conv 3x3 x16 (hoisted), degree-7 ReLU, pool, fc 10",
-            "latency_ms": 1000 * t, "images_per_s": 1.0 / t, "max_logit_error_vs_fp64": err}
+            "latency_ms": 1000 * t, "images_per_s": 1.0 / t, "max_logit_error_vs_fp64": err, "tuning": tuning}
 
 
 def paper_shape_leg(H, W, np, torch, local):

@@ -134,7 +134,10 @@ __global__ void k_tensor_acc(const CtRef* out, const CtRef* x, const CtRef* w, c
   const int n = 1 << T.log_n;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
-  const int l = blockIdx.y, o = blockIdx.z;
+  // limb-major grid: every output of one limb runs before the next limb, so
+  // the operands shared by many outputs (a conv's weights, overlapping
+  // windows) stay in L2 while that limb is processed
+  const int o = blockIdx.y, l = blockIdx.z;
   const DMod md = T.mods[l];
   const size_t lo = (size_t)l * n + c;
   U128 a0{0, 0}, a1{0, 0}, a2{0, 0};
@@ -484,7 +487,7 @@ void launch_tensor_acc(hc_ctx* ctx, const CtRef* out, const CtRef* x, const CtRe
   HC_CHECK(nout <= 65535, HC_ERR_INVALID, "too many outputs in one launch");
     {
       ProfScope prof_(ctx, "k_tensor_acc", (uint64_t)nout * nl);
-      k_tensor_acc<<<grid_for(ctx, nl, nout), kT, 0, ctx->stream>>>(out, x, w, xi, wi, off, nl, chunk, ctx->tab);
+      k_tensor_acc<<<grid_for(ctx, nout, nl), kT, 0, ctx->stream>>>(out, x, w, xi, wi, off, nl, chunk, ctx->tab);
     }
   LAUNCH_DONE(ctx);
 }
