@@ -1727,6 +1727,7 @@ extern "C" int hc_mul_relin_rescale_host(hc_ctx* ctx, const hc_evk* evk, const u
   cudaStream_t h2d = nullptr, d2h = nullptr;
   std::vector<cudaEvent_t> evs;
   std::vector<std::vector<hc_ct*>> ins;
+  std::vector<BufPtr> keep;  // released only after the side streams are drained
   int rc = guard(ctx, [&] {
     HC_CHECK(evk && n >= 0 && (n == 0 || (a_host && b_host && a_meta && b_meta && out_host && out_cap && out_meta)),
              HC_ERR_INVALID, "null argument");
@@ -1752,7 +1753,6 @@ extern "C" int hc_mul_relin_rescale_host(hc_ctx* ctx, const hc_evk* evk, const u
       evs.push_back(e);
       return e;
     };
-    std::vector<BufPtr> keep;
     BufPtr flags = ctx->buffer(nch);
     keep.push_back(flags);
     HC_CUDA(cudaMemsetAsync(flags->ptr, 0, nch * sizeof(u64), ctx->stream));
@@ -1819,6 +1819,7 @@ extern "C" int hc_mul_relin_rescale_host(hc_ctx* ctx, const hc_evk* evk, const u
   // on an error the side streams may still be writing into inputs: drain them first
   if (h2d) cudaStreamSynchronize(h2d);
   if (d2h) cudaStreamSynchronize(d2h);
+  keep.clear();
   for (auto& v : ins) free_all(v);
   for (cudaEvent_t e : evs) cudaEventDestroy(e);
   if (h2d) cudaStreamDestroy(h2d);
