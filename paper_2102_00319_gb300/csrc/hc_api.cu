@@ -1924,17 +1924,7 @@ std::vector<const hc_ct*> to_const(const std::vector<hc_ct*>& v) { return std::v
 // rs(rl(a (x) b)) elementwise over two equal-length lists at one level
 std::vector<hc_ct*> mul_rr(hc_ctx* ctx, const hc_evk* evk, const std::vector<const hc_ct*>& a,
                            const std::vector<const hc_ct*>& b) {
-  const int n = (int)a.size();
-  std::vector<int> ai(n), bi(n), off(n + 1);
-  std::iota(ai.begin(), ai.end(), 0);
-  std::iota(bi.begin(), bi.end(), 0);
-  std::iota(off.begin(), off.end(), 0);
-  std::vector<hc_ct*> d = tensor_acc(ctx, a, b, ai, bi, off, a[0]->level, a[0]->scale * b[0]->scale);
-  for (int i = 0; i < n; ++i) d[i]->scale = a[i]->scale * b[i]->scale;
-  std::vector<hc_ct*> r = relin_rescale(ctx, evk, d, nullptr);
-  for (int i = 0; i < n; ++i) r[i]->scale = d[i]->scale / (double)ctx->P.chain[a[0]->level];
-  free_all(d);
-  return r;
+  return mul_relin_rescale_cts(ctx, evk, a.data(), b.data(), (int)a.size());
 }
 
 // rescale(x * c @ cs) with cs chosen per element by cs_of(i)
@@ -1966,37 +1956,63 @@ std::vector<hc_ct*> poly7(hc_ctx* ctx, const hc_evk* evk, const std::vector<cons
   const int lv = u[0]->level;
   HC_CHECK(lv >= 4, HC_ERR_DEPTH, "the degree-7 activation needs four levels");
   const double q2 = (double)ctx->P.chain[lv - 2], q3 = (double)ctx->P.chain[lv - 3];
+  const size_t n = u.size();
   std::vector<hc_ct*> u2 = mul_rr(ctx, evk, u, u);                                   // lv-1
-  std::vector<hc_ct*> u4 = mul_rr(ctx, evk, to_const(u2), to_const(u2));             // lv-2
   std::vector<hc_ct*> ud1 = views_at(ctx, u, lv - 1);
-  std::vector<hc_ct*> u3 = mul_rr(ctx, evk, to_const(u2), to_const(ud1));            // lv-2
+  // u4 = u2 u2 and u3 = u2 u in one batch                                              lv-2
+  std::vector<const hc_ct*> la = to_const(u2), lb = to_const(u2);
+  la.insert(la.end(), u2.begin(), u2.end());
+  lb.insert(lb.end(), ud1.begin(), ud1.end());
+  std::vector<hc_ct*> u43 = mul_rr(ctx, evk, la, lb);
+  std::vector<hc_ct*> u4(u43.begin(), u43.begin() + n), u3(u43.begin() + n, u43.end());
   std::vector<hc_ct*> u2d = views_at(ctx, to_const(u2), lv - 2);
   std::vector<hc_ct*> ud2 = views_at(ctx, u, lv - 2);
-  auto deg3 = [&](double a0, double a1, double a2, double a3) {
-    std::vector<hc_ct*> t3 = mulc_rs(ctx, to_const(u3), a3, q2);                      // lv-3
-    const double s3 = t3[0]->scale;
-    std::vector<hc_ct*> t2 = mulc_rs(ctx, to_const(u2d), a2, s3 * q2 / u2d[0]->scale);
-    std::vector<hc_ct*> t1 = mulc_rs(ctx, to_const(ud2), a1, s3 * q2 / ud2[0]->scale);
-    add_into(ctx, t3, to_const(t2), lv - 3);
-    add_into(ctx, t3, to_const(t1), lv - 3);
+  // the six constant products of both cubic parts, then one rescale for all   lv-3
+  // (t3 = u3 a3 @ q_{l-2}; t2 and t1 at t3's scale through their constants' scale)
+  const double s3 = u3[0]->scale * q2 / q2;  // scale of rs(u3 * a3 @ q2)
+  std::vector<hc_ct*> m;
+  for (int h = 0; h < 2; ++h) {
+    const double a1 = c[4 * h + 1], a2 = c[4 * h + 2], a3 = c[4 * h + 3];
+    for (auto& v : std::vector<std::vector<hc_ct*>>{mul_const_cts(ctx, to_const(u3), a3, q2),
+                                                   mul_const_cts(ctx, to_const(u2d), a2, s3 * q2 / u2d[0]->scale),
+                                                   mul_const_cts(ctx, to_const(ud2), a1, s3 * q2 / ud2[0]->scale)})
+      m.insert(m.end(), v.begin(), v.end());
+  }
+  std::vector<hc_ct*> t(m.size());
+  {
+    std::vector<hc_ct*> outs = new_cts(ctx, (int)m.size(), lv - 3, 1, 1.0);
+    rescale_cts(ctx, to_const(m), outs);
+    for (size_t i = 0; i < m.size(); ++i) {
+      outs[i]->scale = m[i]->scale / q2;
+      t[i] = outs[i];
+    }
+  }
+  auto deg3 = [&](int h) {  // t3 + t2 + t1 + a0
+    std::vector<hc_ct*> t3(t.begin() + 3 * n * h, t.begin() + 3 * n * h + n);
+    std::vector<const hc_ct*> t2(t.begin() + 3 * n * h + n, t.begin() + 3 * n * h + 2 * n);
+    std::vector<const hc_ct*> t1(t.begin() + 3 * n * h + 2 * n, t.begin() + 3 * n * h + 3 * n);
+    add_into(ctx, t3, t2, lv - 3);
+    add_into(ctx, t3, t1, lv - 3);
     std::vector<u64> sc;
-    constant_residues(ctx, lv - 3, a0 * s3, false, sc);
+    constant_residues(ctx, lv - 3, c[4 * h] * t3[0]->scale, false, sc);
     std::vector<BufPtr> keep;
     std::vector<CtRef> tr;
-    for (auto* t : t3) tr.push_back(t->ref());
+    for (auto* x : t3) tr.push_back(x->ref());
     const CtRef* td = refs_dev(ctx, tr, keep);
     launch_scalar(ctx, true, td, td, (int)t3.size(), 2, lv - 2, upload(ctx, sc, keep));
-    free_all(t2);
-    free_all(t1);
     return t3;
   };
-  std::vector<hc_ct*> qa = deg3(c[0], c[1], c[2], c[3]);
-  std::vector<hc_ct*> qb = deg3(c[4], c[5], c[6], c[7]);
+  std::vector<hc_ct*> qa = deg3(0);
+  std::vector<hc_ct*> qb = deg3(1);
   std::vector<hc_ct*> u4d = views_at(ctx, to_const(u4), lv - 3);
   std::vector<hc_ct*> prod = mul_rr(ctx, evk, to_const(qb), to_const(u4d));         // lv-4
   std::vector<hc_ct*> qa2 = mulc_rs(ctx, to_const(qa), 1.0, prod[0]->scale * q3 / qa[0]->scale);
   add_into(ctx, prod, to_const(qa2), lv - 4);
-  for (auto* v : {&u2, &u4, &ud1, &u3, &u2d, &ud2, &qa, &qb, &u4d, &qa2}) free_all(*v);
+  free_all(u43);  // u4 and u3
+  for (size_t i = 0; i < t.size(); ++i)  // the t2, t1 parts (t3 parts are qa, qb)
+    if ((i / n) % 3 != 0) delete t[i];
+  free_all(m);
+  for (auto* v : {&u2, &ud1, &u2d, &ud2, &qa, &qb, &u4d, &qa2}) free_all(*v);
   return prod;
 }
 }  // namespace
@@ -2029,12 +2045,7 @@ extern "C" int hc_enc_poly_act(hc_ctx* ctx, const hc_evk* evk, const hc_ct* cons
     const double a0 = coeffs[0], a1 = coeffs[1], a2 = coeffs[2];
     const bool square = (a0 == 0 && a1 == 0 && a2 == 1);
     HC_CHECK(level >= (square ? 1 : 2), HC_ERR_DEPTH, "not enough levels for the activation");
-    std::vector<int> idx(n), off(n + 1);
-    for (int i = 0; i < n; ++i) idx[i] = i;
-    std::iota(off.begin(), off.end(), 0);
-    std::vector<hc_ct*> d = tensor_acc(ctx, xs, xs, idx, idx, off, level, xs[0]->scale * xs[0]->scale);
-    std::vector<hc_ct*> t = relin_rescale(ctx, evk, d, nullptr);
-    free_all(d);
+    std::vector<hc_ct*> t = mul_relin_rescale_cts(ctx, evk, xs.data(), xs.data(), n);  // rs(rl(u u))
     if (square) {
       for (int i = 0; i < n; ++i) y[i] = t[i];
       return;
