@@ -252,6 +252,15 @@ HI64_PER_SM_CLK = 6.6
 MULMODS_PER_SM_CLK = 1.0 / (2.0 / LO64_PER_SM_CLK + 1.0 / HI64_PER_SM_CLK)
 
 
+# Busy share of the integer multiplier (ncu sm__pipe_fmaheavy_cycles_active,
+# % of peak) per kernel, from the same captures as the traffic above
+# (profiles/ntt_fwd_passes_deep_n16_l20.md, keyswitch_kernels_deep_n16_l20.md).
+NCU_INT_PIPE_BUSY = {
+    "ntt_fwd_cols": 0.755, "ntt_fwd_rows": 0.730, "ntt_fwd_cols_ksr": 0.753, "ntt_fwd_rows_ksr": 0.729,
+    "k_modup_bconv": 0.739, "k_key_product": 0.714, "k_moddown_bconv": 0.746, "k_tensor_pair": 0.731,
+}
+
+
 def butterflies_per_unit(name, n):
     """Butterflies of one limb in one NTT pass (the column pass takes the first
     floor(log N / 2) stages, the row pass the rest)."""
@@ -868,7 +877,8 @@ def run_gpu(args, rank, world, local):
         roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak, "traffic": traffic, "peak_source": hbm["peak_source"]}
     roofline.update({"bytes_per_launch": alg_bytes / max(cnt, 1), "avg_launch_us": 1000.0 * tot / max(cnt, 1),
-                     "share_of_step": tot / ms})
+                     "share_of_step": tot / ms,
+                     "integer_pipe_busy_ncu": NCU_INT_PIPE_BUSY.get(dom)})
     kern_summary = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / ms, 4)}
                     for k, v in sorted(kernels.items(), key=lambda kv: -kv[1][1])}
     line = {
