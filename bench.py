@@ -235,6 +235,7 @@ def run_reference(args, rank, world):
 # kernel version on a smaller batch (profiles/ntt_fwd_passes_deep_n16_l20.md:
 # 336 limbs per launch), scaled to a launch by its units.  Set an entry to
 # None when its kernel changes until it is captured again.
+NCU_NTT_VARIANT = 1  # block size (HC_TUNE_NTT) of the NTT capture below
 NCU_TRAFFIC_PER_UNIT = {
     "ntt_fwd_cols": (176.303e6 + 120.248e6) / 336,
     "ntt_fwd_rows": (209.214e6 + 122.685e6) / 336,
@@ -858,6 +859,8 @@ def run_gpu(args, rank, world, local):
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = peaks.get("hbm_gbs", 6800.0)
     tpu = NCU_TRAFFIC_PER_UNIT.get(dom)
+    if dom.startswith("ntt_") and tuning is not None and not tuning.startswith("ntt_variant %d " % NCU_NTT_VARIANT):
+        tpu = None  # the tuned block size is not the one the traffic was captured with
     traffic = tpu * units / max(cnt, 1) if tpu else None
     hbm = {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}

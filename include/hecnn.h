@@ -286,7 +286,8 @@ int hc_relin_noalloc(hc_ctx *ctx, const hc_evk *evk, const hc_ct *x, hc_ct *out)
  * hc_autotune times each knob's candidates on scratch data shaped like
  * `items` ciphertext pairs at the top level (one knob at a time, the others
  * at their current values, three timed launches each after a warm-up) and
- * keeps the fastest.  `report` (may be NULL; cap bytes, always
+ * keeps the fastest, unless it is less than 2 % faster than the knob's
+ * current value (which then stays).  `report` (may be NULL; cap bytes, always
  * NUL-terminated) receives one line per knob: the chosen value and the
  * microseconds per launch of every candidate.  Not capturable; it
  * synchronises the context stream.

@@ -1613,6 +1613,10 @@ extern "C" int hc_tune_get(const hc_ctx* ctx, int knob) {
   }
 }
 
+// A candidate replaces the current value only when it is at least 2 %
+// faster, so timing noise does not flip the choice.
+constexpr double kSwitchGain = 0.98;
+
 extern "C" int hc_autotune(hc_ctx* ctx, const hc_evk* evk, int items, char* report, size_t cap) {
   if (!ctx) return HC_ERR_INVALID;
   std::vector<cudaEvent_t> evs;
@@ -1652,8 +1656,9 @@ extern "C" int hc_autotune(hc_ctx* ctx, const hc_evk* evk, int items, char* repo
     // NTT: forward and inverse transforms of m degree-1 ciphertexts
     {
       const LimbSet cs = limbset_base(cts, 2 * nq * limb, nq * limb, 2, nq, 0, nullptr);
-      double best = 1e300;
-      int pick = 0;
+      const int incumbent = ctx->tune.ntt_variant[ctx->P.log_n];
+      double best = 1e300, inc_us = 1e300;
+      int pick = incumbent;
       std::string t;
       for (int v = 0; v <= (ctx->P.log_n >= 13 ? 2 : 1); ++v) {
         ctx->tune.ntt_variant[ctx->P.log_n] = v;
@@ -1663,16 +1668,19 @@ extern "C" int hc_autotune(hc_ctx* ctx, const hc_evk* evk, int items, char* repo
         });
         std::snprintf(line, sizeof line, " %d:%.1f", v, us);
         t += line;
+        if (v == incumbent) inc_us = us;
         if (us < best) best = us, pick = v;
       }
+      if (best > kSwitchGain * inc_us) pick = incumbent;
       ctx->tune.ntt_variant[ctx->P.log_n] = pick;
       std::snprintf(line, sizeof line, "ntt_variant %d us%s\n", pick, t.c_str());
       rep += line;
     }
     // key product over the raised digits
     {
-      double best = 1e300;
-      int pick = 1;
+      const int incumbent = ctx->tune.kp_zmul;
+      double best = 1e300, inc_us = 1e300;
+      int pick = incumbent;
       std::string t;
       for (int z : {1, 2, 4, 8}) {
         ctx->tune.kp_zmul = z;
@@ -1682,16 +1690,19 @@ extern "C" int hc_autotune(hc_ctx* ctx, const hc_evk* evk, int items, char* repo
         });
         std::snprintf(line, sizeof line, " %d:%.1f", z, us);
         t += line;
+        if (z == incumbent) inc_us = us;
         if (us < best) best = us, pick = z;
       }
+      if (best > kSwitchGain * inc_us) pick = incumbent;
       ctx->tune.kp_zmul = pick;
       std::snprintf(line, sizeof line, "key_product_z %d us%s\n", pick, t.c_str());
       rep += line;
     }
     // ModUp conversion of digit 0
     {
-      double best = 1e300;
-      int pick = 1;
+      const int incumbent = ctx->tune.modup_split;
+      double best = 1e300, inc_us = 1e300;
+      int pick = incumbent;
       std::string t;
       for (int sp : {1, 2, 4}) {
         ctx->tune.modup_split = sp;
@@ -1700,8 +1711,10 @@ extern "C" int hc_autotune(hc_ctx* ctx, const hc_evk* evk, int items, char* repo
         });
         std::snprintf(line, sizeof line, " %d:%.1f", sp, us);
         t += line;
+        if (sp == incumbent) inc_us = us;
         if (us < best) best = us, pick = sp;
       }
+      if (best > kSwitchGain * inc_us) pick = incumbent;
       ctx->tune.modup_split = pick;
       std::snprintf(line, sizeof line, "modup_split %d us%s\n", pick, t.c_str());
       rep += line;
