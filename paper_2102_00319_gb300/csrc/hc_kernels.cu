@@ -140,27 +140,43 @@ __global__ void k_tensor_acc(const CtRef* out, const CtRef* x, const CtRef* w, c
   const int o = blockIdx.y, l = blockIdx.z;
   const DMod md = T.mods[l];
   const size_t lo = (size_t)l * n + c;
-  U128 a0{0, 0}, a1{0, 0}, a2{0, 0};
+  // Karatsuba per term: s += (x0 + x1)(w0 + w1), so that the middle sum is
+  // s - a0 - a2 (exact: s dominates a0 + a2 term by term); three products
+  // per term instead of four
+  U128 a0{0, 0}, s{0, 0}, a2{0, 0};
   const int t0 = off[o], t1 = off[o + 1];
   int cnt = 0;
+  auto middle = [&]() {  // s - a0 - a2 in 128 bits
+    U128 m = s;
+    u64 t = m.lo - a0.lo;
+    m.hi -= a0.hi + (m.lo < a0.lo);
+    m.lo = t;
+    t = m.lo - a2.lo;
+    m.hi -= a2.hi + (m.lo < a2.lo);
+    m.lo = t;
+    return m;
+  };
   for (int t = t0; t < t1; ++t) {
     const CtRef X = x[xi[t]], Wt = w[wi[t]];
     const u64 x0 = X.p[lo], x1 = X.p[X.stride + lo];
     const u64 w0 = Wt.p[lo], w1 = Wt.p[Wt.stride + lo];
     mac(a0, x0, w0);
-    mac(a1, x0, w1);
-    mac(a1, x1, w0);
+    mac(s, x0 + x1, w0 + w1);
     mac(a2, x1, w1);
     if (++cnt == chunk) {
+      // fold: keep the three sums' residues, with s carrying r0 + r1 + r2 so
+      // that s - a0 - a2 still yields the middle residue
       cnt = 0;
-      a0 = U128{reduce128_est(a0, md), 0};
-      a1 = U128{reduce128_est(a1, md), 0};
-      a2 = U128{reduce128_est(a2, md), 0};
+      const u64 r1 = reduce128_est(middle(), md);
+      const u64 r0 = reduce128_est(a0, md), r2 = reduce128_est(a2, md);
+      a0 = U128{r0, 0};
+      a2 = U128{r2, 0};
+      s = U128{r0 + r1 + r2, 0};
     }
   }
   const CtRef O = out[o];
   O.p[lo] = reduce128_est(a0, md);
-  O.p[O.stride + lo] = reduce128_est(a1, md);
+  O.p[O.stride + lo] = reduce128_est(middle(), md);
   O.p[2 * O.stride + lo] = reduce128_est(a2, md);
 }
 
@@ -476,12 +492,13 @@ void launch_tensor_pair(hc_ctx* ctx, const CtRef* out, const CtRef* a, const CtR
 void launch_tensor_acc(hc_ctx* ctx, const CtRef* out, const CtRef* x, const CtRef* w, const int* xi,
                        const int* wi, const int* off, int nout, int nl) {
   if (nout <= 0) return;
-  // products are < qmax^2 and a1 gains two per term: fold before 2^128
+  // the Karatsuba sum gains (x0 + x1)(w0 + w1) < 4 qmax^2 per term (on top
+  // of a folded residue below 3 qmax): fold before 2^128
   u64 qmax = 0;
   for (int i = 0; i < nl; ++i) qmax = ctx->P.chain[i] > qmax ? ctx->P.chain[i] : qmax;
   unsigned __int128 sq = (unsigned __int128)qmax * qmax;
   unsigned __int128 lim = (~(unsigned __int128)0) - ((unsigned __int128)1 << 64);
-  unsigned __int128 per = lim / (2 * sq);
+  unsigned __int128 per = lim / (4 * sq);
   int chunk = per > 1024 ? 1024 : (int)per - 1;
   HC_CHECK(chunk >= 1, HC_ERR_INVALID, "primes too large for lazy accumulation");
   HC_CHECK(nout <= 65535, HC_ERR_INVALID, "too many outputs in one launch");
