@@ -147,3 +147,18 @@ def test_layer_edge_cases(net):
     assert len(gp) == len(op_) == 2
     for g, o in zip(gp, op_):
         p.assert_same(g, o, "odd pool")
+
+
+def test_fc_long_sum_folds_bit_exact(net):
+    """An FC output summing 150 products with a 60-bit prime in the chain: the
+    tensor kernel's 128-bit sums fold every 63 terms (Karatsuba middle sum
+    carried through the folds); bit-exact against the oracle."""
+    p = net["p"]
+    op = p.op
+    n_in, n_out = 150, 2
+    xs = [p.encrypt_values(W.slot_values(300 + i, op.K), level=2, nonce=3000 + i) for i in range(n_in)]
+    ws = [p.encrypt_values(W.slot_values(600 + i, op.K), level=3, nonce=4000 + i) for i in range(n_in * n_out)]
+    got = H.hc_enc_fc(p.ctx, p.g_evk, H.HC_PACK_BATCH, [g for g, _ in xs], [g for g, _ in ws], n_out)
+    want = cnn.enc_fc(op, p.o_evk, [o for _, o in xs], [o for _, o in ws], n_out)
+    for g, o in zip(got, want):
+        p.assert_same(g, o, "fc 150 terms")

@@ -182,6 +182,24 @@ def test_ntt_tile_variants_match_oracle(log_n):
         H.hc_tune_set(p.ctx, H.HC_TUNE_NTT, 3)
 
 
+def test_batch_larger_than_workspace_chunk(pair):
+    """300 pairs at N = 2^10: the key switch works in chunks of at most 256
+    items, so the batch runs as 256 + a ragged 44.  Items on both sides of the
+    chunk boundary match the oracle; all 300 match the unfused three-call
+    form (relinearise, then rescale)."""
+    op = pair.op
+    lv = 2
+    A = [pair.encrypt_values(W.slot_values(1000 + i, op.K), level=lv, nonce=10000 + i) for i in range(300)]
+    B = [pair.encrypt_values(W.slot_values(2000 + i, op.K), level=lv, nonce=20000 + i) for i in range(300)]
+    r = H.hc_mul_relin_rescale_batch(pair.ctx, pair.g_evk, [g for g, _ in A], [g for g, _ in B])
+    for i in (0, 255, 256, 299):
+        (_, oa), (_, ob) = A[i], B[i]
+        pair.assert_same(r[i], ckks.rescale(op, ckks.relin(op, pair.o_evk, ckks.mul(op, oa, ob))), "item %d" % i)
+    for i in range(300):
+        g = H.hc_rescale(pair.ctx, H.hc_relin(pair.ctx, pair.g_evk, H.hc_mul(pair.ctx, A[i][0], B[i][0])))
+        np.testing.assert_array_equal(H.hc_ct_export(pair.ctx, r[i])[0], H.hc_ct_export(pair.ctx, g)[0])
+
+
 def test_import_rejects_out_of_range(pair):
     data = np.zeros((2, 1, pair.op.N), dtype=np.uint64)
     data[1, 0, 7] = pair.op.q[0]
