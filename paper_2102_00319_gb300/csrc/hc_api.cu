@@ -183,9 +183,9 @@ void modup_digits(hc_ctx* ctx, int level, const std::vector<CtRef>& xs, const u6
       launch_ew(ctx, 3, refs_dev(ctx, er, keep), refs_dev(ctx, xsh, keep), nullptr, m, 1, d1 - d0);
     }
     launch_modup_bconv_fast(ctx, level, j, xc, x_is, ext + (size_t)j * ext_words, ext_is, m);
-    u64* ej = ext + (size_t)j * ext_words;
-    if (d0 > 0) launch_ntt(ctx, limbset_base(ej, ext_is, 0, 1, d0, 0, emap), m, false);
-    launch_ntt(ctx, limbset_base(ej, ext_is, 0, 1, next - d1, d1, emap), m, false);
+    LimbSet e = limbset_base(ext + (size_t)j * ext_words, ext_is, 0, 1, next - (d1 - d0), 0, emap);
+    e.slot_map = ctx->modup_slots_of(level, j);  // the raised slots, one launch
+    launch_ntt(ctx, e, m, false);
   }
 }
 
@@ -656,6 +656,19 @@ void build_tables(hc_ctx* ctx) {
     for (int s = 0; s < l + 1 + alpha; ++s) maps[(size_t)l * W + s] = s <= l ? s : L + 1 + (s - l - 1);
   for (int i = 0; i < HC_MAX_CHAIN; ++i) maps[(size_t)(L + 1) * W + i] = i;
   ctx->ext_map = (int*)put(maps.data(), maps.size() * sizeof(int));
+  // per (level, digit): the ext slots outside the digit, in order
+  std::vector<int> slots;
+  for (int l = 0; l <= L; ++l) {
+    LevelConsts& lc = ctx->lv[l];
+    lc.modup_slots_off.clear();
+    for (int j = 0; j < lc.dnum; ++j) {
+      const int d0 = j * alpha, d1 = std::min(d0 + alpha, l + 1);
+      lc.modup_slots_off.push_back((int)slots.size());
+      for (int t = 0; t < l + 1 + alpha; ++t)
+        if (t < d0 || t >= d1) slots.push_back(t);
+    }
+  }
+  ctx->modup_slots = (int*)put(slots.data(), std::max<size_t>(1, slots.size()) * sizeof(int));
 }
 }  // namespace
 
@@ -1442,8 +1455,9 @@ std::vector<std::vector<hc_ct*>> rotate_hoisted_batch(hc_ctx* ctx, const hc_evk*
       launch_ew(ctx, 3, refs_dev(ctx, own_dst, keep), refs_dev(ctx, own_src, keep), nullptr, m, 1, d1 - d0);
       u64* ej = ext + (size_t)j * ext_words;
       launch_modup_bconv_fast(ctx, level, j, xc, x_is, ej, ext_is, m);
-      if (d0 > 0) launch_ntt(ctx, limbset_base(ej, ext_is, 0, 1, d0, 0, emap), m, false);
-      launch_ntt(ctx, limbset_base(ej, ext_is, 0, 1, next - d1, d1, emap), m, false);
+      LimbSet e = limbset_base(ej, ext_is, 0, 1, next - (d1 - d0), 0, emap);
+      e.slot_map = ctx->modup_slots_of(level, j);
+      launch_ntt(ctx, e, m, false);
     }
     const CtRef* ext_r = refs_dev(ctx, ers, keep);
     const CtRef* extg_r = refs_dev(ctx, egr, keep);

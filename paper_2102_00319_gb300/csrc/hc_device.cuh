@@ -76,6 +76,7 @@ struct LimbSet {
   int nlimb;
   int l0;
   const int* prime_map;
+  const int* slot_map;  // optional: limb l lives at slot slot_map[l] instead of l0 + l
 };
 
 __device__ __forceinline__ u64* limb_ptr(const LimbSet& s, int z, int k, int slot, int n) {

@@ -63,6 +63,9 @@ struct LevelConsts {
   std::vector<int> modup_off;
   // rescale: q_l^{-1} mod q_i (+sh) for i < l, q_l mod q_i
   int rescale_off = -1;
+  // ModUp digit j: offset in hc_ctx::modup_slots of the ext slots outside
+  // the digit ([0, d0) then [d1, l + 1 + alpha)), one transform launch each
+  std::vector<int> modup_slots_off;
 };
 
 // Tile and launch-shape choices (set by hc_autotune or hc_tune_set).
@@ -87,6 +90,7 @@ struct hc_ctx {
   std::vector<LevelConsts> lv;
   int moddown_off = -1;      // (P/p_k)^{-1} mod p_k (+sh); (P/p_k) mod q_i; P^{-1} mod q_i (+sh)
   int* ext_map = nullptr;    // [level][L+1+alpha] chain index of ext slot
+  int* modup_slots = nullptr;  // per (level, digit): ext slots raised by that digit's ModUp
   std::string err;
   uint64_t launches = 0;
   // tracing: events around launches while `prof` is set
@@ -102,6 +106,7 @@ struct hc_ctx {
   void free_words(u64* p);
   BufPtr buffer(size_t words);
   const int* ext_map_of(int level) const { return ext_map + level * (P.L + 1 + P.alpha); }
+  const int* modup_slots_of(int level, int digit) const { return modup_slots + lv[level].modup_slots_off[digit]; }
   const u64* ks(int off) const { return ks_dev + off; }
 };
 

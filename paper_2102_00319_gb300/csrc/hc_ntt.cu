@@ -87,7 +87,8 @@ template <int LOGN>
 __device__ __forceinline__ void limb_meta(const LimbSet& s, u64*& a, int& pid) {
   const int y = blockIdx.y;
   const int k = y / s.nlimb;
-  const int slot = s.l0 + y - k * s.nlimb;
+  const int l = y - k * s.nlimb;
+  const int slot = s.slot_map ? s.slot_map[l] : s.l0 + l;
   a = limb_ptr(s, blockIdx.z, k, slot, 1 << LOGN);
   pid = limb_prime(s, slot);
 }
@@ -420,6 +421,7 @@ void launch_ntt_from(hc_ctx* ctx, const LimbSet& s, const LimbSet* in, int items
 }
 
 void launch_ntt_ksr(hc_ctx* ctx, const LimbSet& s, int items, const KsrFuse& fuse) {
-  HC_CHECK(s.npoly == 2 && s.l0 == 0 && !s.prime_map && !s.refs, HC_ERR_INVALID, "fused tail needs plain z limbs");
+  HC_CHECK(s.npoly == 2 && s.l0 == 0 && !s.prime_map && !s.slot_map && !s.refs, HC_ERR_INVALID,
+           "fused tail needs plain z limbs");
   ntt_dispatch(ctx, s, nullptr, items, false, true, &fuse);
 }
