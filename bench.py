@@ -237,10 +237,10 @@ def run_reference(args, rank, world):
 # None when its kernel changes until it is captured again.
 NCU_NTT_VARIANT = 1  # block size (HC_TUNE_NTT) of the NTT capture below
 NCU_TRAFFIC_PER_UNIT = {
-    "ntt_fwd_cols": (176.303e6 + 120.248e6) / 336,
-    "ntt_fwd_rows": (209.214e6 + 122.685e6) / 336,
-    "ntt_fwd_cols_ksr": (352.510e6 + 279.961e6) / 640,
-    "ntt_fwd_rows_ksr": (1114.173e6 + 317.006e6) / 640,
+    "ntt_fwd_cols": (176.321e6 + 120.213e6) / 336,
+    "ntt_fwd_rows": (209.276e6 + 122.754e6) / 336,
+    "ntt_fwd_cols_ksr": (352.481e6 + 279.976e6) / 640,
+    "ntt_fwd_rows_ksr": (1113.881e6 + 317.208e6) / 640,
 }
 
 
