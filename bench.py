@@ -127,7 +127,8 @@ class Clocks:
     def __init__(self, index):
         self.proc = None
         self.index = index
-        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % os.getpid())
+        import tempfile
+        self.path = os.path.join(tempfile.gettempdir(), "hecnn_bench_clocks_%d.csv" % os.getpid())
 
     def start(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
