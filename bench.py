@@ -233,9 +233,10 @@ def run_reference(args, rank, world):
 # Algorithmic HBM bytes per work unit (one N-word limb of the launch's output
 # domain), per kernel; dnum = 3 at the top level of this workload.
 # DRAM bytes (read + write) per work unit from one ncu capture of the same
-# kernel version on a smaller batch (profiles/ntt_fwd_passes_deep_n16_l20.md:
-# 336 limbs per launch), scaled to a launch by its units.  Set an entry to
-# None when its kernel changes until it is captured again.
+# kernel version on a smaller batch (one step of 16 pairs run by
+# paper_2102_00319_gb300/probes/one_step.py: 336 limbs per ModUp transform
+# launch, 640 per fused-tail launch), scaled to a launch by its units.  Set
+# an entry to None when its kernel changes until it is captured again.
 NCU_NTT_VARIANT = 1  # block size (HC_TUNE_NTT) of the NTT capture below
 NCU_TRAFFIC_PER_UNIT = {
     "ntt_fwd_cols": (176.321e6 + 120.213e6) / 336,
@@ -255,8 +256,8 @@ MULMODS_PER_SM_CLK = 1.0 / (2.0 / LO64_PER_SM_CLK + 1.0 / HI64_PER_SM_CLK)
 
 
 # Busy share of the integer multiplier (ncu sm__pipe_fmaheavy_cycles_active,
-# % of peak) per kernel, from the same captures as the traffic above
-# (profiles/ntt_fwd_passes_deep_n16_l20.md, keyswitch_kernels_deep_n16_l20.md).
+# % of peak) per kernel, from the same one-step captures as the traffic
+# above (NTT passes, and the tensor, conversion and key-product kernels).
 NCU_INT_PIPE_BUSY = {
     "ntt_fwd_cols": 0.755, "ntt_fwd_rows": 0.730, "ntt_fwd_cols_ksr": 0.753, "ntt_fwd_rows_ksr": 0.729,
     "k_modup_bconv": 0.739, "k_key_product": 0.714, "k_moddown_bconv": 0.746, "k_tensor_pair": 0.731,
