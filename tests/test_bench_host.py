@@ -1,0 +1,62 @@
+"""Host-side logic of bench.py (no GPU): the roofline unit counts, the
+replica seeds and timing reduction, and the launch-list summary."""
+import importlib.util
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_butterfly_and_mulmod_counts(bench):
+    n = 1 << 16
+    # column pass: stages 0..7, row pass: stages 8..15, N/2 butterflies each
+    assert bench.butterflies_per_unit("ntt_fwd_cols", n) == 8 * n // 2
+    assert bench.butterflies_per_unit("ntt_inv_rows", n) == 8 * n // 2
+    assert bench.butterflies_per_unit("ntt_fwd_cols", 1 << 15) == 7 * (1 << 14)
+    assert bench.butterflies_per_unit("ntt_fwd_rows", 1 << 15) == 8 * (1 << 14)
+    assert bench.mulmods_per_unit("ntt_fwd_rows", n) == 4 * n
+    assert bench.mulmods_per_unit("ntt_fwd_rows_ksr", n) == 4 * n + 2 * n
+    assert bench.mulmods_per_unit("ntt_fwd_cols_ksr", n) == 4 * n + 1.75 * n
+
+
+def test_multiplier_peak_from_measured_rates(bench):
+    # 1 / (2/14.4 + 1/6.6) Shoup products per SM per clock
+    assert abs(bench.MULMODS_PER_SM_CLK - 3.4435) < 1e-3
+    assert abs(bench.MULMODS_PER_SM_CLK * 152 * 2070e6 / 1e9 - 1083.46) < 0.1
+
+
+def test_bytes_per_unit(bench):
+    n, limb = 1 << 16, 8 << 16
+    assert bench.bytes_per_unit("ntt_fwd_rows", n, 3) == 2 * limb
+    assert bench.bytes_per_unit("ntt_fwd_rows_ksr", n, 3) == 4 * limb
+    assert bench.bytes_per_unit("k_tensor_pair", n, 3) == 7 * limb
+    assert bench.bytes_per_unit("k_key_product", n, 3) == 11 * limb
+
+
+def test_summarize_launch_list(bench, tmp_path, capsys):
+    """Two steps in a synthetic ncu CSV: the summary covers exactly the
+    second one (from its tensor kernel to the fused-tail NTT after k_ksr_cl)."""
+    step = ["k_tensor_pair", "k_rows", "k_cols", "k_modup_bconv_h", "k_key_product_t", "k_ksr_last",
+            "k_ksr_cl", "k_cols", "k_rows"]
+    lines = ['"ID","Kernel Name","Metric Name","Metric Unit","Metric Value"']
+    i = 0
+    for rep in range(2):
+        for k in step:
+            us = 10.0 * (rep + 1)
+            lines.append('"%d","void <unnamed>::%s<1>(int)","gpu__time_duration.sum","us","%.1f"' % (i, k, us))
+            i += 1
+    p = tmp_path / "launches.csv"
+    p.write_text("\n".join(lines) + "\n")
+    bench.summarize_ncu(str(p), 2)
+    out = capsys.readouterr().out
+    assert "| (step) | 9 | 180.0 | 1.000 |" in out
+    assert "| k_rows | 2 | 40.0 |" in out
