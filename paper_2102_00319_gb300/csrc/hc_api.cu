@@ -247,9 +247,14 @@ void keyswitch_batch(hc_ctx* ctx, const u64* key, int level, const std::vector<C
 // per limb serves both; the last limb of relin_k is formed in coefficient
 // form from INTT(base_k[l] + u_k[l] P^{-1}) - z_k[l] P^{-1}.  Bit-identical to
 // keyswitch_batch followed by rescale_batch.  out: degree-1, level l-1.
+// With coeff_out the results go there in coefficient form instead (2 polys x
+// l limbs per item, `out` unused): by linearity the inverse NTT of
+// base_k[i] + u_k[i] P^{-1} minus (z_k[i] P^{-1} + [c_l]_{q_i}), times
+// q_l^{-1}, is the inverse NTT of the NTT-form result, so the same words come
+// out with one transform per limb instead of two.
 void keyswitch_rescale_batch(hc_ctx* ctx, const u64* key, int level, const std::vector<CtRef>& x,
                              const std::vector<CtRef>* base0, const std::vector<CtRef>* base1,
-                             const std::vector<CtRef>& out) {
+                             const std::vector<CtRef>& out, const LimbSet* coeff_out = nullptr) {
   const int n = ctx->P.n, alpha = ctx->P.alpha;
   const int nq = level + 1, next = nq + alpha, dnum = ctx->lv[level].dnum;
   const int total = (int)x.size();
@@ -264,7 +269,8 @@ void keyswitch_rescale_batch(hc_ctx* ctx, const u64* key, int level, const std::
     std::vector<BufPtr> keep;
     std::vector<CtRef> xs(x.begin() + s0, x.begin() + s0 + m);
     const CtRef* xr = refs_dev(ctx, xs, keep);
-    const CtRef* orr = refs_dev(ctx, std::vector<CtRef>(out.begin() + s0, out.begin() + s0 + m), keep);
+    const CtRef* orr =
+        coeff_out ? nullptr : refs_dev(ctx, std::vector<CtRef>(out.begin() + s0, out.begin() + s0 + m), keep);
     const CtRef* b0 = nullptr;
     const CtRef* b1 = nullptr;
     if (base0) b0 = refs_dev(ctx, std::vector<CtRef>(base0->begin() + s0, base0->begin() + s0 + m), keep);
@@ -304,7 +310,16 @@ void keyswitch_rescale_batch(hc_ctx* ctx, const u64* key, int level, const std::
     f.base0 = b0;
     f.base1 = b1;
     f.out = orr;
-    launch_ntt_ksr(ctx, limbset_base(zq, z_is, (u64)nq * n, 2, level, 0, nullptr), m, f);
+    if (coeff_out) {
+      f.z = zq;
+      f.z_item_stride = z_is;
+      f.z_poly_stride = (u64)nq * n;
+      LimbSet co = *coeff_out;
+      co.base += (size_t)s0 * co.item_stride;
+      launch_intt_ksr(ctx, co, m, f);
+    } else {
+      launch_ntt_ksr(ctx, limbset_base(zq, z_is, (u64)nq * n, 2, level, 0, nullptr), m, f);
+    }
   }
 }
 
@@ -388,7 +403,7 @@ std::vector<hc_ct*> tensor_acc(hc_ctx* ctx, const std::vector<const hc_ct*>& xs,
 // A bias is added to (d0, d1) before the key switch, which equals adding it
 // to the relinearised ciphertext.
 std::vector<hc_ct*> relin_rescale(hc_ctx* ctx, const hc_evk* evk, const std::vector<hc_ct*>& d,
-                                  const std::vector<const hc_ct*>* bias) {
+                                  const std::vector<const hc_ct*>* bias, const LimbSet* coeff_out = nullptr) {
   if (d.empty()) return {};
   const int level = d[0]->level;
   HC_CHECK(level >= 1, HC_ERR_DEPTH, "no level left to rescale");
@@ -405,17 +420,21 @@ std::vector<hc_ct*> relin_rescale(hc_ctx* ctx, const hc_evk* evk, const std::vec
     const CtRef* dd = refs_dev(ctx, dr, keep);
     launch_ew(ctx, 0, dd, dd, refs_dev(ctx, br, keep), (int)d.size(), 2, level + 1);
   }
-  std::vector<hc_ct*> out = new_cts(ctx, (int)d.size(), level - 1, 1, d[0]->scale / (double)ctx->P.chain[level]);
+  // with coeff_out the results are written there and no ciphertexts are made
+  std::vector<hc_ct*> out;
+  if (!coeff_out) out = new_cts(ctx, (int)d.size(), level - 1, 1, d[0]->scale / (double)ctx->P.chain[level]);
   std::vector<CtRef> x, b0, b1, o;
   for (size_t i = 0; i < d.size(); ++i) {
     HC_CHECK(d[i]->degree == 2 && d[i]->level == level, HC_ERR_INVALID, "relin batch needs degree-2 cts at one level");
-    out[i]->scale = d[i]->scale / (double)ctx->P.chain[level];
     x.push_back(CtRef{d[i]->data + 2 * d[i]->stride, d[i]->stride});
     b0.push_back(CtRef{d[i]->data, d[i]->stride});
     b1.push_back(CtRef{d[i]->data + d[i]->stride, d[i]->stride});
-    o.push_back(out[i]->ref());
+    if (!coeff_out) {
+      out[i]->scale = d[i]->scale / (double)ctx->P.chain[level];
+      o.push_back(out[i]->ref());
+    }
   }
-  keyswitch_rescale_batch(ctx, evk->relin.buf->ptr, level, x, &b0, &b1, o);
+  keyswitch_rescale_batch(ctx, evk->relin.buf->ptr, level, x, &b0, &b1, o, coeff_out);
   return out;
 }
 
@@ -615,6 +634,19 @@ void build_tables(hc_ctx* ctx) {
       for (int i = 0; i < l; ++i) inv_l[i] = hch::invmod(ql % P.chain[i], P.chain[i]);
       for (int i = 0; i < l; ++i) ks.push_back(inv_l[i]);
       for (int i = 0; i < l; ++i) ks.push_back(hch::shoup_of(inv_l[i], P.chain[i]));
+      // the coefficient-form relinearise + rescale tail: N^{-1} q_l^{-1}, P^{-1} q_l^{-1}
+      std::vector<u64> nq(l), pq(l);
+      for (int i = 0; i < l; ++i) {
+        const u64 qi = P.chain[i];
+        u64 pprod = 1;
+        for (int m = 0; m < alpha; ++m) pprod = hch::mulmod(pprod, P.chain[L + 1 + m] % qi, qi);
+        nq[i] = hch::mulmod(hch::invmod((u64)P.n % qi, qi), inv_l[i], qi);
+        pq[i] = hch::mulmod(hch::invmod(pprod, qi), inv_l[i], qi);
+      }
+      for (int i = 0; i < l; ++i) ks.push_back(nq[i]);
+      for (int i = 0; i < l; ++i) ks.push_back(hch::shoup_of(nq[i], P.chain[i]));
+      for (int i = 0; i < l; ++i) ks.push_back(pq[i]);
+      for (int i = 0; i < l; ++i) ks.push_back(hch::shoup_of(pq[i], P.chain[i]));
     }
   }
   ctx->moddown_off = (int)ks.size();
@@ -1546,8 +1578,10 @@ extern "C" int hc_rotate_hoisted(hc_ctx* ctx, const hc_evk* evk, const hc_ct* x,
 
 namespace {
 // n products a[i] b[i], relinearised and rescaled (one pass of each kernel).
+// With coeff_out the results are written there in coefficient form (2 polys
+// x level-1 limbs per item) and no ciphertexts are returned.
 std::vector<hc_ct*> mul_relin_rescale_cts(hc_ctx* ctx, const hc_evk* evk, const hc_ct* const* a,
-                                          const hc_ct* const* b, int n) {
+                                          const hc_ct* const* b, int n, const LimbSet* coeff_out = nullptr) {
   const int level = a[0]->level;
   for (int i = 0; i < n; ++i) {
     check_ct(ctx, a[i]);
@@ -1573,8 +1607,8 @@ std::vector<hc_ct*> mul_relin_rescale_cts(hc_ctx* ctx, const hc_evk* evk, const 
     }
   }
   for (int i = 0; i < n; ++i) d[i]->scale = a[i]->scale * b[i]->scale;
-  std::vector<hc_ct*> r = relin_rescale(ctx, evk, d, nullptr);
-  for (int i = 0; i < n; ++i) r[i]->scale = d[i]->scale / (double)ctx->P.chain[level];
+  std::vector<hc_ct*> r = relin_rescale(ctx, evk, d, nullptr, coeff_out);
+  for (size_t i = 0; i < r.size(); ++i) r[i]->scale = d[i]->scale / (double)ctx->P.chain[level];
   free_all(d);
   return r;
 }
@@ -1813,20 +1847,16 @@ extern "C" int hc_mul_relin_rescale_host(hc_ctx* ctx, const hc_evk* evk, const u
         x[j]->scale = a_meta[c * m0 + j].scale;
         x[m + j]->scale = b_meta[c * m0 + j].scale;
       }
-      std::vector<hc_ct*> r = mul_relin_rescale_cts(ctx, evk, x.data(), x.data() + m, m);
-      free_all(x);  // stream-ordered: the copies into x finished before this stream's first use
+      // the products come out in coefficient form straight into the staging slab
       BufPtr staged = ctx->buffer(m * out_words);
       keep.push_back(staged);
-      std::vector<CtRef> rr;
-      for (auto* ct : r) rr.push_back(ct->ref());
-      LimbSet src{};
-      src.refs = refs_dev(ctx, rr, keep);
-      src.npoly = 2;
-      src.nlimb = level;
-      launch_ntt_from(ctx, limbset_base(staged->ptr, out_words, (u64)level * N, 2, level, 0, nullptr), &src, m,
-                      true);
-      for (int j = 0; j < m; ++j) out_meta[c * m0 + j] = hc_ct_meta{level - 1, 1, r[j]->scale};
-      free_all(r);
+      const LimbSet co = limbset_base(staged->ptr, out_words, (u64)level * N, 2, level, 0, nullptr);
+      mul_relin_rescale_cts(ctx, evk, x.data(), x.data() + m, m, &co);
+      free_all(x);  // stream-ordered: the copies into x finished before this stream's first use
+      for (int j = 0; j < m; ++j) {
+        const int i = c * m0 + j;
+        out_meta[i] = hc_ct_meta{level - 1, 1, a_meta[i].scale * b_meta[i].scale / (double)ctx->P.chain[level]};
+      }
       const cudaEvent_t done = event();
       HC_CUDA(cudaEventRecord(done, ctx->stream));
       HC_CUDA(cudaStreamWaitEvent(d2h, done, 0));

@@ -50,6 +50,10 @@ struct CtRef {
 //   cl[z][k][coefficient];
 // - last pass, on store: out_k[i] = (base_k[i] + acc_k[i] P^{-1} - NTT(x))
 //   q_l^{-1}, written to the output ciphertexts instead of back into z.
+// The same tail in coefficient form is carried by the inverse NTT of
+// y = base_k[i] + acc_k[i] P^{-1} (formed on load by the first pass); the
+// last pass stores out_k[i] = (INTT(y) - z_k[i] P^{-1} - [c_l]_{q_i}) q_l^{-1}
+// into the transform's own limbs, with N^{-1} folded into q_l^{-1}.
 struct KsrFuse {
   const u64* cl;        // [item][2][N] signed centred c_l
   const u64* pinv;      // P^{-1} mod q_i (i <= level)
@@ -61,6 +65,11 @@ struct KsrFuse {
   const CtRef* out;     // level-1 outputs
   const u64* qlinv;     // q_l^{-1} mod q_i, then its Shoup companions
   int level;
+  // coefficient-form tail only
+  const u64* z;         // z_k[i] at z + item*z_item_stride + k*z_poly_stride + i*N
+  u64 z_item_stride, z_poly_stride;
+  const u64* nqlinv;    // N^{-1} q_l^{-1} mod q_i, then its Shoup companions
+  const u64* pqlinv;    // P^{-1} q_l^{-1} mod q_i, then its Shoup companions
 };
 
 // A set of limbs for batched per-limb kernels (NTT, copies): for batch item

@@ -61,7 +61,8 @@ struct LevelConsts {
   int dnum = 0;
   // ModUp digit j: hat_inv[i] (+sh) for i < |D_j|, then hat_mod[t][i] for t < ext
   std::vector<int> modup_off;
-  // rescale: q_l^{-1} mod q_i (+sh) for i < l, q_l mod q_i
+  // rescale: q_l^{-1} mod q_i (+sh), then N^{-1} q_l^{-1} (+sh) and
+  // P^{-1} q_l^{-1} (+sh), each for i < l
   int rescale_off = -1;
   // ModUp digit j: offset in hc_ctx::modup_slots of the ext slots outside
   // the digit ([0, d0) then [d1, l + 1 + alpha)), one transform launch each
@@ -209,6 +210,10 @@ void launch_ntt_from(hc_ctx* ctx, const LimbSet& s, const LimbSet* in, int items
 // Forward NTT of the converted limbs z (2 polys x level limbs per item)
 // carrying the fused relinearise + rescale tail (KsrFuse): writes f.out.
 void launch_ntt_ksr(hc_ctx* ctx, const LimbSet& z, int items, const KsrFuse& f);
+// Inverse NTT into `out` (2 polys x level plain limbs per item) carrying the
+// coefficient-form tail of KsrFuse: out holds the relinearised and rescaled
+// polynomials in coefficient form (f.out is not used).
+void launch_intt_ksr(hc_ctx* ctx, const LimbSet& out, int items, const KsrFuse& f);
 
 // Samplers writing coefficient-form limbs dst + r*N for chain indices ids[r].
 void launch_sample_ternary(hc_ctx* ctx, u64 seed, u64 tag, u64* dst, const int* ids, int nl);

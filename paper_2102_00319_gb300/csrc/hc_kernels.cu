@@ -1016,6 +1016,8 @@ void ksr_constants(hc_ctx* ctx, int level, KsrFuse& f) {
   f.pinv = pinv;
   f.pinv_sh = pinv + (L + 1);
   f.qlinv = ctx->ks(ctx->lv[level].rescale_off);
+  f.nqlinv = f.qlinv + 2 * level;
+  f.pqlinv = f.qlinv + 4 * level;
   f.level = level;
 }
 

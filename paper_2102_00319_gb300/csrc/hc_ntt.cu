@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(1 << TL) k_cols(LimbSet s, LimbSet in, int use
   const int fslot = blockIdx.y % s.nlimb, fpoly = blockIdx.y / s.nlimb;
   const u64* fcl = FUSE ? f.cl + ((size_t)blockIdx.z * 2 + fpoly) * ((size_t)1 << LOGN) + blockIdx.x * TC : nullptr;
   if (!INV) {
-    // round 1: 2^K1 rows strided by 2^K2 -> stages 0..K1-1
+    // first register round: 2^K1 rows strided by 2^K2 -> stages 0..K1-1
     for (u32 w = threadIdx.x; w < (TC << K2); w += kThreads) {
       const u32 c = w & (TC - 1), r0 = w >> TCL;
       u64 x[1 << K1];
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(1 << TL) k_cols(LimbSet s, LimbSet in, int use
       for (int i = 0; i < (1 << K1); ++i) sm[((r0 + (i << K2)) << TCL) + c] = x[i];
     }
     __syncthreads();
-    // round 2: 2^K2 adjacent rows -> stages K1..N1-1
+    // second register round: 2^K2 adjacent rows -> stages K1..N1-1
     for (u32 w = threadIdx.x; w < (TC << K1); w += kThreads) {
       const u32 c = w & (TC - 1), g = w >> TCL;
       u64 x[1 << K2];
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(1 << TL) k_cols(LimbSet s, LimbSet in, int use
       for (int i = 0; i < (1 << K2); ++i) a[(((g << K2) + i) << N2) + c] = reduce4(x[i], q);
     }
   } else {
-    // round A: 2^K2 adjacent rows -> stages N1-1 .. K1
+    // first inverse round: 2^K2 adjacent rows -> stages N1-1 .. K1
     for (u32 w = threadIdx.x; w < (TC << K1); w += kThreads) {
       const u32 c = w & (TC - 1), g = w >> TCL;
       u64 x[1 << K2];
@@ -168,8 +168,12 @@ __global__ void __launch_bounds__(1 << TL) k_cols(LimbSet s, LimbSet in, int use
       for (int i = 0; i < (1 << K2); ++i) sm[(((g << K2) + i) << TCL) + c] = x[i];
     }
     __syncthreads();
-    // round B: 2^K1 rows strided by 2^K2 -> stages K1-1 .. 0, then N^{-1}
+    // second inverse round: 2^K1 rows strided by 2^K2 -> stages K1-1 .. 0, then N^{-1}
     const u64 ni = T.ninv[pid], nis = T.ninv_sh[pid];
+    // coefficient-form relinearise + rescale tail: z_k[i] and c_l of this block
+    const u64* fz = FUSE ? f.z + (size_t)blockIdx.z * f.z_item_stride + (size_t)fpoly * f.z_poly_stride +
+                               ((size_t)fslot << LOGN) + blockIdx.x * TC
+                         : nullptr;
     for (u32 w = threadIdx.x; w < (TC << K2); w += kThreads) {
       const u32 c = w & (TC - 1), r0 = w >> TCL;
       u64 x[1 << K1];
@@ -177,8 +181,22 @@ __global__ void __launch_bounds__(1 << TL) k_cols(LimbSet s, LimbSet in, int use
       for (int i = 0; i < (1 << K1); ++i) x[i] = sm[((r0 + (i << K2)) << TCL) + c];
       inv_block<K1, K2 + N2, K1 - 1, LOGN>(x, r0 << N2, tw, q);
 #pragma unroll
-      for (int i = 0; i < (1 << K1); ++i)
-        a[((r0 + (i << K2)) << N2) + c] = reduce4(scale ? shoup_lazy(x[i], ni, nis, q) : x[i], q);
+      for (int i = 0; i < (1 << K1); ++i) {
+        const u32 e = ((r0 + (i << K2)) << N2) + c;
+        if constexpr (FUSE) {
+          // (INTT(y) - z P^{-1} - [c_l]_{q_i}) q_l^{-1}, N^{-1} folded into the first constant
+          const int lv = f.level;
+          const u64 yv = csub(shoup_lazy(x[i], f.nqlinv[fslot], f.nqlinv[lv + fslot], q), q);
+          const u64 zv = shoup(fz[e], f.pqlinv[fslot], f.pqlinv[lv + fslot], q);
+          const long long cl = (long long)fcl[e];
+          const u64 mag = cl < 0 ? (u64)(-cl) : (u64)cl;
+          const u64 cv = shoup(mag, f.qlinv[fslot], f.qlinv[lv + fslot], q);
+          const u64 t = subm(yv, zv, q);
+          a[e] = cl < 0 ? addm(t, cv, q) : subm(t, cv, q);
+        } else {
+          a[e] = reduce4(scale ? shoup_lazy(x[i], ni, nis, q) : x[i], q);
+        }
+      }
     }
   }
 }
@@ -202,7 +220,7 @@ __global__ void __launch_bounds__(1 << TL) k_rows(LimbSet s, LimbSet in, int use
   const u64* srcin = ain + ((size_t)row0 << N2);
   auto sidx = [](u32 r, u32 j) { return r * PADW + j + (j >> K2); };
   if (!INV) {
-    // round 1: 2^K1 points strided by 2^K2 (straight from global)
+    // first register round: 2^K1 points strided by 2^K2 (straight from global)
     for (u32 w = threadIdx.x; w < (RP << K2); w += kThreads) {
       const u32 r = w >> K2, r0 = w & ((1 << K2) - 1);
       u64 x[1 << K1];
@@ -213,7 +231,7 @@ __global__ void __launch_bounds__(1 << TL) k_rows(LimbSet s, LimbSet in, int use
       for (int i = 0; i < (1 << K1); ++i) sm[sidx(r, r0 + (i << K2))] = x[i];
     }
     __syncthreads();
-    // round 2: 2^K2 adjacent points; the results go back through shared
+    // second register round: 2^K2 adjacent points; the results go back through shared
     // memory so that the stores to global memory are row-contiguous across
     // the warp (measured faster than each thread storing its own points)
     for (u32 w = threadIdx.x; w < (RP << K1); w += kThreads) {
@@ -257,26 +275,59 @@ __global__ void __launch_bounds__(1 << TL) k_rows(LimbSet s, LimbSet in, int use
       for (u32 e = threadIdx.x; e < (RP << N2); e += kThreads) src[e] = sm[sidx(e >> N2, e & (C - 1))];
     }
   } else {
-    // round A: 2^K2 adjacent points read straight from global memory as
+    // first inverse round: 2^K2 adjacent points read straight from global memory as
     // 16-byte pairs (a thread's points are contiguous and 16-byte aligned;
     // measured faster than staging the tile through shared memory)
     // -> stages LOGN-1 .. LOGN-K2
+    // coefficient-form relinearise + rescale tail: y = base_k[i] + acc_k[i] P^{-1} on load
+    const u64* faccp = nullptr;
+    const u64* fbp = nullptr;
+    u64 fpv = 0, fpvs = 0;
+    if constexpr (FUSE) {
+      const int slot = blockIdx.y % s.nlimb, k = blockIdx.y / s.nlimb, z = blockIdx.z;
+      const size_t li0 = ((size_t)slot << LOGN) + ((size_t)row0 << N2);
+      faccp = f.acc + (size_t)z * f.acc_item_stride + (size_t)k * f.acc_poly_stride + li0;
+      const CtRef* base = k == 0 ? f.base0 : f.base1;
+      fbp = base ? base[z].p + li0 : nullptr;
+      fpv = f.pinv[slot];
+      fpvs = f.pinv_sh[slot];
+    }
     for (u32 w = threadIdx.x; w < (RP << K1); w += kThreads) {
       const u32 r = w >> K1, g = w & ((1 << K1) - 1);
       u64 x[1 << K2];
-      const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(srcin + (r << N2) + (g << K2));
+      if constexpr (FUSE) {
+        const u32 o = (r << N2) + (g << K2);
+        const ulonglong2* a2 = reinterpret_cast<const ulonglong2*>(faccp + o);
 #pragma unroll
-      for (int i = 0; i < (1 << K2); i += 2) {
-        const ulonglong2 v = s2[i >> 1];
-        x[i] = v.x;
-        x[i + 1] = v.y;
+        for (int i = 0; i < (1 << K2); i += 2) {
+          const ulonglong2 v = a2[i >> 1];
+          x[i] = shoup(v.x, fpv, fpvs, q);
+          x[i + 1] = shoup(v.y, fpv, fpvs, q);
+        }
+        if (fbp) {
+          const ulonglong2* b2 = reinterpret_cast<const ulonglong2*>(fbp + o);
+#pragma unroll
+          for (int i = 0; i < (1 << K2); i += 2) {
+            const ulonglong2 v = b2[i >> 1];
+            x[i] = addm(x[i], v.x, q);
+            x[i + 1] = addm(x[i + 1], v.y, q);
+          }
+        }
+      } else {
+        const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(srcin + (r << N2) + (g << K2));
+#pragma unroll
+        for (int i = 0; i < (1 << K2); i += 2) {
+          const ulonglong2 v = s2[i >> 1];
+          x[i] = v.x;
+          x[i + 1] = v.y;
+        }
       }
       inv_block<K2, 0, LOGN - 1, LOGN>(x, ((row0 + r) << N2) + (g << K2), tw, q);
 #pragma unroll
       for (int i = 0; i < (1 << K2); ++i) sm[sidx(r, (g << K2) + i)] = x[i];
     }
     __syncthreads();
-    // round B: 2^K1 points strided by 2^K2 -> stages LOGN-K2-1 .. N1 (to global)
+    // second inverse round: 2^K1 points strided by 2^K2 -> stages LOGN-K2-1 .. N1 (to global)
     for (u32 w = threadIdx.x; w < (RP << K2); w += kThreads) {
       const u32 r = w >> K2, r0 = w & ((1 << K2) - 1);
       u64 x[1 << K1];
@@ -323,10 +374,11 @@ void launch_pass_cols_t(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, co
   constexpr int TCL = ColTile<N1, N2, TL>::TCL;
   dim3 grid(1u << (N2 - TCL), ylimbs, items);
   const size_t smem = ((size_t)1 << (N1 + TCL)) * sizeof(u64);
-  ProfScope p(ctx, INV ? "ntt_inv_cols" : (fuse ? "ntt_fwd_cols_ksr" : "ntt_fwd_cols"), (uint64_t)ylimbs * items);
-  if (!INV && fuse)
-    k_cols<false, LOGN, Sp::K1, Sp::K2, TCL, true, TL><<<grid, 1 << TL, smem, ctx->stream>>>(s, s, 0, 1, *fuse,
-                                                                                           ctx->tab);
+  ProfScope p(ctx, INV ? (fuse ? "ntt_inv_cols_ksr" : "ntt_inv_cols") : (fuse ? "ntt_fwd_cols_ksr" : "ntt_fwd_cols"),
+              (uint64_t)ylimbs * items);
+  if (fuse)
+    k_cols<INV, LOGN, Sp::K1, Sp::K2, TCL, true, TL><<<grid, 1 << TL, smem, ctx->stream>>>(s, s, 0, 1, *fuse,
+                                                                                         ctx->tab);
   else
     k_cols<INV, LOGN, Sp::K1, Sp::K2, TCL, false, TL><<<grid, 1 << TL, smem, ctx->stream>>>(
         s, in ? *in : s, in ? 1 : 0, scale ? 1 : 0, KsrFuse{}, ctx->tab);
@@ -340,10 +392,11 @@ void launch_pass_rows_t(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, co
   constexpr int RPL = RowTile<N1, N2, TL>::RPL;
   dim3 grid(1u << (N1 - RPL), ylimbs, items);
   const size_t smem = ((size_t)1 << RPL) * RowTile<N1, N2, TL>::PADW * sizeof(u64);
-  ProfScope p(ctx, INV ? "ntt_inv_rows" : (fuse ? "ntt_fwd_rows_ksr" : "ntt_fwd_rows"), (uint64_t)ylimbs * items);
-  if (!INV && fuse)
-    k_rows<false, LOGN, Sp::K1, Sp::K2, RPL, true, TL><<<grid, 1 << TL, smem, ctx->stream>>>(s, s, 0, *fuse,
-                                                                                           ctx->tab);
+  ProfScope p(ctx, INV ? (fuse ? "ntt_inv_rows_ksr" : "ntt_inv_rows") : (fuse ? "ntt_fwd_rows_ksr" : "ntt_fwd_rows"),
+              (uint64_t)ylimbs * items);
+  if (fuse)
+    k_rows<INV, LOGN, Sp::K1, Sp::K2, RPL, true, TL><<<grid, 1 << TL, smem, ctx->stream>>>(s, s, 0, *fuse,
+                                                                                         ctx->tab);
   else
     k_rows<INV, LOGN, Sp::K1, Sp::K2, RPL, false, TL><<<grid, 1 << TL, smem, ctx->stream>>>(
         s, in ? *in : s, in ? 1 : 0, KsrFuse{}, ctx->tab);
@@ -384,8 +437,8 @@ void ntt_logn(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, bool inverse
     launch_pass_cols<false, LOGN>(ctx, s, items, ylimbs, in, true, fuse);
     launch_pass_rows<false, LOGN>(ctx, s, items, ylimbs, nullptr, fuse);
   } else {
-    launch_pass_rows<true, LOGN>(ctx, s, items, ylimbs, in);
-    launch_pass_cols<true, LOGN>(ctx, s, items, ylimbs, nullptr, scale);
+    launch_pass_rows<true, LOGN>(ctx, s, items, ylimbs, in, fuse);
+    launch_pass_cols<true, LOGN>(ctx, s, items, ylimbs, nullptr, scale, fuse);
   }
 }
 
@@ -424,4 +477,11 @@ void launch_ntt_ksr(hc_ctx* ctx, const LimbSet& s, int items, const KsrFuse& fus
   HC_CHECK(s.npoly == 2 && s.l0 == 0 && !s.prime_map && !s.slot_map && !s.refs, HC_ERR_INVALID,
            "fused tail needs plain z limbs");
   ntt_dispatch(ctx, s, nullptr, items, false, true, &fuse);
+}
+
+void launch_intt_ksr(hc_ctx* ctx, const LimbSet& out, int items, const KsrFuse& fuse) {
+  HC_CHECK(out.npoly == 2 && out.l0 == 0 && !out.prime_map && !out.slot_map && !out.refs && fuse.z &&
+               fuse.nqlinv && fuse.pqlinv,
+           HC_ERR_INVALID, "coefficient-form tail needs plain output limbs and its constants");
+  ntt_dispatch(ctx, out, nullptr, items, true, true, &fuse);
 }

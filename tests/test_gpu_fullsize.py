@@ -70,6 +70,11 @@ def test_deep_n16_batch_sampled_bit_exact():
         r = H.hc_mul_relin_rescale_batch(p.ctx, p.g_evk, [A[k] for k in ks], [Bc[k] for k in ks])
         for k, c in zip(ks, r):
             np.testing.assert_array_equal(H.hc_ct_export(p.ctx, c)[0], eager[k])
+        hk = [np.zeros((2, p.op.L, p.op.N), dtype=np.uint64) for _ in ks]
+        H.hc_mul_relin_rescale_host(p.ctx, p.g_evk, [a_arr[k] for k in ks], [metas[k] for k in ks],
+                                    [b_arr[k] for k in ks], [metas[k] for k in ks], hk)
+        for k, h in zip(ks, hk):
+            np.testing.assert_array_equal(h, eager[k])
     H.hc_tune_set(p.ctx, H.HC_TUNE_NTT, default)
     # property at full size: slot products of encoded vectors
     za, zb = W.slot_values(1, p.op.K), W.slot_values(2, p.op.K)

@@ -108,17 +108,42 @@ def test_host_pipeline_matches_device_batch(pair):
         H.hc_mul_relin_rescale_host(pair.ctx, pair.g_evk, bad, a_m, b_arr, b_m, outs, chunk=2)
 
 
+def _host_products(p, ga, gb, lv):
+    """The host-to-host call on exported inputs: coefficient-form outputs."""
+    a_arr = [H.hc_ct_export(p.ctx, c)[0] for c in ga]
+    b_arr = [H.hc_ct_export(p.ctx, c)[0] for c in gb]
+    a_m = [(lv, 1, c.meta().scale) for c in ga]
+    b_m = [(lv, 1, c.meta().scale) for c in gb]
+    outs = [np.zeros((2, lv, p.op.N), dtype=np.uint64) for _ in ga]
+    metas = H.hc_mul_relin_rescale_host(p.ctx, p.g_evk, a_arr, a_m, b_arr, b_m, outs)
+    return outs, metas
+
+
+def _assert_host_same(out, meta, octx, what):
+    assert (meta.level, meta.degree, meta.scale) == (octx.level, octx.degree, octx.scale), what
+    if not np.array_equal(out, octx.c):
+        bad = np.argwhere(out != octx.c)
+        raise AssertionError("%s: %d of %d words differ, first at %s" % (what, len(bad), out.size, bad[:3].tolist()))
+
+
 def test_batch_mul_relin_rescale_every_level_and_edges(pair):
     """The fused batch at every level down to 1 (truncated last digit at low
-    levels, a one-limb fused tail at level 1) equals the oracle; an empty
-    batch, an aliased pair (a is b) and level 0 behave."""
+    levels, a one-limb fused tail at level 1) equals the oracle, in NTT form
+    (device batch) and in coefficient form (host call, whose tail is carried
+    by the inverse transform); an empty batch, an aliased pair (a is b) and
+    level 0 behave."""
     op = pair.op
     for lv in range(op.L, 0, -1):
         ga, oa = pair.encrypt_values(W.slot_values(80 + lv, op.K), level=lv, nonce=800 + lv)
         gb, ob = pair.encrypt_values(W.slot_values(90 + lv, op.K), level=lv, nonce=900 + lv)
         r = H.hc_mul_relin_rescale_batch(pair.ctx, pair.g_evk, [ga, ga], [gb, ga])
-        pair.assert_same(r[0], ckks.rescale(op, ckks.relin(op, pair.o_evk, ckks.mul(op, oa, ob))), "l=%d" % lv)
-        pair.assert_same(r[1], ckks.rescale(op, ckks.relin(op, pair.o_evk, ckks.mul(op, oa, oa))), "a*a l=%d" % lv)
+        want_ab = ckks.rescale(op, ckks.relin(op, pair.o_evk, ckks.mul(op, oa, ob)))
+        want_aa = ckks.rescale(op, ckks.relin(op, pair.o_evk, ckks.mul(op, oa, oa)))
+        pair.assert_same(r[0], want_ab, "l=%d" % lv)
+        pair.assert_same(r[1], want_aa, "a*a l=%d" % lv)
+        outs, metas = _host_products(pair, [ga, ga], [gb, ga], lv)
+        _assert_host_same(outs[0], metas[0], want_ab, "host l=%d" % lv)
+        _assert_host_same(outs[1], metas[1], want_aa, "host a*a l=%d" % lv)
     assert H.hc_mul_relin_rescale_batch(pair.ctx, pair.g_evk, [], []) == []
     assert H.hc_ct_import_batch(pair.ctx, [], []) == []
     H.hc_ct_export_batch(pair.ctx, [], [])
@@ -178,6 +203,8 @@ def test_ntt_tile_variants_match_oracle(log_n):
         H.hc_tune_set(p.ctx, H.HC_TUNE_NTT, v)
         p.assert_same(H.hc_mul_relin_rescale_batch(p.ctx, p.g_evk, [ga], [gb])[0], want_m, "mul v=%d" % v)
         p.assert_same(H.hc_rotate(p.ctx, p.g_evk, ga, 5), want_r, "rot v=%d" % v)
+        outs, metas = _host_products(p, [ga], [gb], op.L)
+        _assert_host_same(outs[0], metas[0], want_m, "host v=%d" % v)
     with pytest.raises(H.HcError):
         H.hc_tune_set(p.ctx, H.HC_TUNE_NTT, 3)
 
