@@ -10,7 +10,10 @@ so no flush is needed between steps).
 
 The JSON line also carries:
   e2e           the same metric through the C ABI from pinned HOST buffers
-                (coefficient-form import, NTT, compute, INTT, export),
+                (coefficient-form import, forward NTT, the operation with
+                its relinearise + rescale tail carried by the inverse NTT,
+                coefficient-form export), with the plain pinned-copy rates
+                of the same buffers measured beside it,
   roofline      the dominant kernel's algorithmic bytes / its device time
                 (CUDA events around every launch on the context stream),
   cpu_baseline  the CPU oracle on this host (bounded sample, rank 0, N=1),
@@ -837,6 +840,27 @@ def run_gpu(args, rank, world, local):
 
     for _ in range(2 if args.e2e_steps > 0 else 0):  # untimed: the memory pool reaches its steady size
         e2e_step()
+    # the plain pinned-copy rates of the same buffers on this machine, for reading
+    # the e2e number (the host link is shared with the box's other GPUs)
+    copy_gbs = None
+    if args.e2e_steps > 0:
+        staging = torch.empty(sum(a.size for a in in_arrays), dtype=torch.int64, device="cuda")
+        c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        barrier()
+        c0.record(stream)
+        o = 0
+        for pin, a, _ in host_in:
+            staging[o:o + a.size].copy_(pin, non_blocking=True)
+            o += a.size
+        c1.record(stream)
+        o = 0
+        for buf in host_out:
+            buf.copy_(staging[o:o + buf.numel()], non_blocking=True)
+            o += buf.numel()
+        c2.record(stream)
+        barrier()
+        copy_gbs = {"h2d": h2d / c0.elapsed_time(c1) / 1e6, "d2h": d2h / c1.elapsed_time(c2) / 1e6}
+        del staging
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
@@ -893,7 +917,8 @@ def run_gpu(args, rank, world, local):
         "config": {"workload": "deep_n16_l20", "N": n, "L": L, "alpha": alpha, "dnum": dnum, "batch": Bn,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (%.2f GB of resident ciphertexts)" % (2 * Bn * 2 * (L + 1) * n * 8 / 1e9)},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "pinned_copy_gbs": copy_gbs},
         "gpu_launches": launches, "roofline": roofline, "clocks": clk, "kernels": kern_summary,
         "tuning": tuning,
         "forms": {"graph": graph_value, "eager": eager_value, "unit": UNIT,

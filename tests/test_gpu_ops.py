@@ -85,9 +85,10 @@ def test_batch_import_export_match_single(pair):
 def test_host_pipeline_matches_device_batch(pair):
     """The host-to-host pipelined call gives, word for word, the exported
     results of the device-resident batch call, for a ragged last chunk and
-    for the automatic chunking; an out-of-range input residue is rejected."""
+    for the automatic chunking (12 pairs: six chunks of 2); an
+    out-of-range input residue and a negative chunk are rejected."""
     op = pair.op
-    lv, n = 3, 5
+    lv, n = 3, 12
     ga = [pair.encrypt_values(W.slot_values(60 + i, op.K), level=lv, nonce=600 + i)[0] for i in range(n)]
     gb = [pair.encrypt_values(W.slot_values(70 + i, op.K), level=lv, nonce=700 + i)[0] for i in range(n)]
     want = [H.hc_ct_export(pair.ctx, c)[0] for c in H.hc_mul_relin_rescale_batch(pair.ctx, pair.g_evk, ga, gb)]
@@ -106,6 +107,8 @@ def test_host_pipeline_matches_device_batch(pair):
     outs = [np.zeros((2, lv, op.N), dtype=np.uint64) for _ in range(n)]
     with pytest.raises(H.HcError):
         H.hc_mul_relin_rescale_host(pair.ctx, pair.g_evk, bad, a_m, b_arr, b_m, outs, chunk=2)
+    with pytest.raises(H.HcError):
+        H.hc_mul_relin_rescale_host(pair.ctx, pair.g_evk, a_arr, a_m, b_arr, b_m, outs, chunk=-1)
 
 
 def _host_products(p, ga, gb, lv):
