@@ -238,14 +238,13 @@ def run_reference(args, rank, world):
 # DRAM bytes (read + write) per work unit from one ncu capture of the same
 # kernel version on a smaller batch (one step of 16 pairs run by
 # paper_2102_00319_gb300/probes/one_step.py: 336 limbs per ModUp transform
-# launch, 640 per fused-tail launch), scaled to a launch by its units.  Set
-# an entry to None when its kernel changes until it is captured again.
+# launch), scaled to a launch by its units.  A kernel without an entry (the
+# fused-tail passes changed after their capture) reports no traffic until it
+# is captured again.
 NCU_NTT_VARIANT = 1  # block size (HC_TUNE_NTT) of the NTT capture below
 NCU_TRAFFIC_PER_UNIT = {
     "ntt_fwd_cols": (176.321e6 + 120.213e6) / 336,
     "ntt_fwd_rows": (209.276e6 + 122.754e6) / 336,
-    "ntt_fwd_cols_ksr": (352.481e6 + 279.976e6) / 640,
-    "ntt_fwd_rows_ksr": (1113.881e6 + 317.208e6) / 640,
 }
 
 
@@ -278,14 +277,13 @@ def butterflies_per_unit(name, n):
 def mulmods_per_unit(name, n):
     """Shoup modular products (two 64-bit low products and one high) of one limb
     in one NTT pass: one per butterfly, plus the fused relinearise + rescale
-    tail of the `_ksr` passes (row pass: acc P^{-1} and the q_l^{-1} factor per
-    coefficient; column pass: z P^{-1} and the reduction of the lifted |c_l|,
-    a low and a high product, counted as 0.75)."""
+    tail of the `_ksr` passes: the row pass multiplies each coefficient by
+    q_l^{-1}; the column pass adds z and the lifted c_l without a product
+    (P^{-1} is folded into the keys and the conversion constants, and |c_l| is
+    below every q_i of this chain)."""
     b = butterflies_per_unit(name, n)
     if name == "ntt_fwd_rows_ksr":
-        return b + 2 * n
-    if name == "ntt_fwd_cols_ksr":
-        return b + 1.75 * n
+        return b + n
     return b
 
 

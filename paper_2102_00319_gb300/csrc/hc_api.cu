@@ -634,19 +634,11 @@ void build_tables(hc_ctx* ctx) {
       for (int i = 0; i < l; ++i) inv_l[i] = hch::invmod(ql % P.chain[i], P.chain[i]);
       for (int i = 0; i < l; ++i) ks.push_back(inv_l[i]);
       for (int i = 0; i < l; ++i) ks.push_back(hch::shoup_of(inv_l[i], P.chain[i]));
-      // the coefficient-form relinearise + rescale tail: N^{-1} q_l^{-1}, P^{-1} q_l^{-1}
-      std::vector<u64> nq(l), pq(l);
-      for (int i = 0; i < l; ++i) {
-        const u64 qi = P.chain[i];
-        u64 pprod = 1;
-        for (int m = 0; m < alpha; ++m) pprod = hch::mulmod(pprod, P.chain[L + 1 + m] % qi, qi);
-        nq[i] = hch::mulmod(hch::invmod((u64)P.n % qi, qi), inv_l[i], qi);
-        pq[i] = hch::mulmod(hch::invmod(pprod, qi), inv_l[i], qi);
-      }
+      // the coefficient-form relinearise + rescale tail: N^{-1} q_l^{-1}
+      std::vector<u64> nq(l);
+      for (int i = 0; i < l; ++i) nq[i] = hch::mulmod(hch::invmod((u64)P.n % P.chain[i], P.chain[i]), inv_l[i], P.chain[i]);
       for (int i = 0; i < l; ++i) ks.push_back(nq[i]);
       for (int i = 0; i < l; ++i) ks.push_back(hch::shoup_of(nq[i], P.chain[i]));
-      for (int i = 0; i < l; ++i) ks.push_back(pq[i]);
-      for (int i = 0; i < l; ++i) ks.push_back(hch::shoup_of(pq[i], P.chain[i]));
     }
   }
   ctx->moddown_off = (int)ks.size();
@@ -661,24 +653,14 @@ void build_tables(hc_ctx* ctx) {
     }
     for (int k = 0; k < alpha; ++k) ks.push_back(hinv[k]);
     for (int k = 0; k < alpha; ++k) ks.push_back(hch::shoup_of(hinv[k], P.chain[L + 1 + k]));
+    // (P/p_k) P^{-1} = p_k^{-1} mod q_i: the conversion's output comes out
+    // already multiplied by P^{-1}, matching the key product's Q limbs (the
+    // switching keys' Q limbs carry P^{-1}, see key_scale), so ModDown needs
+    // no multiplication by P^{-1} of its own
     for (int i = 0; i <= L; ++i) {
       const u64 qi = P.chain[i];
-      for (int k = 0; k < alpha; ++k) {
-        u64 prod = 1 % qi;
-        for (int m = 0; m < alpha; ++m)
-          if (m != k) prod = hch::mulmod(prod, P.chain[L + 1 + m] % qi, qi);
-        ks.push_back(prod);
-      }
+      for (int k = 0; k < alpha; ++k) ks.push_back(hch::invmod(P.chain[L + 1 + k] % qi, qi));
     }
-    std::vector<u64> pinv(L + 1);
-    for (int i = 0; i <= L; ++i) {
-      const u64 qi = P.chain[i];
-      u64 prod = 1;
-      for (int m = 0; m < alpha; ++m) prod = hch::mulmod(prod, P.chain[L + 1 + m] % qi, qi);
-      pinv[i] = hch::invmod(prod, qi);
-    }
-    for (int i = 0; i <= L; ++i) ks.push_back(pinv[i]);
-    for (int i = 0; i <= L; ++i) ks.push_back(hch::shoup_of(pinv[i], P.chain[i]));
   }
   ctx->ks_dev = (u64*)put(ks.data(), ks.size() * sizeof(u64));
   // ext maps per level followed by an identity map of HC_MAX_CHAIN entries
@@ -812,16 +794,24 @@ u64 galois_elt(const hc_params& P, long long r) {
   return hch::powmod(5, (u64)rr, 2 * (u64)P.n);
 }
 
-// Switching key for s' (NTT form over the whole chain) -> s.
 // Multiplies every limb of a switching key ([npoly][chain][N]) by 2^64 mod q
-// (into Montgomery form) or by its inverse (back), in place.
+// (into Montgomery form: the key product reduces its sums with one
+// Montgomery reduction) and its limbs of Q (t <= L) also by P^{-1} mod q_t
+// (ModDown's division by P, folded into the key product), or by the inverse
+// of that (back to the plain key), in place.
 void key_scale(hc_ctx* ctx, u64* key, int npoly, bool inverse, std::vector<BufPtr>& keep) {
-  const int nc = ctx->P.nchain();
+  const hc_params& P = ctx->P;
+  const int nc = P.nchain();
   std::vector<u64> sc(2 * nc);
   for (int t = 0; t < nc; ++t) {
-    const u64 q = ctx->P.chain[t];
-    const u64 r = (u64)(((unsigned __int128)1 << 64) % q);
-    sc[t] = inverse ? hch::invmod(r, q) : r;
+    const u64 q = P.chain[t];
+    u64 f = (u64)(((unsigned __int128)1 << 64) % q);
+    if (t <= P.L) {
+      u64 pm = 1;
+      for (int k = 0; k < P.alpha; ++k) pm = hch::mulmod(pm, P.chain[P.L + 1 + k] % q, q);
+      f = hch::mulmod(f, hch::invmod(pm, q), q);
+    }
+    sc[t] = inverse ? hch::invmod(f, q) : f;
     sc[nc + t] = hch::shoup_of(sc[t], q);
   }
   std::vector<CtRef> rk{CtRef{key, (u64)nc * ctx->P.n}};
@@ -829,6 +819,7 @@ void key_scale(hc_ctx* ctx, u64* key, int npoly, bool inverse, std::vector<BufPt
   launch_scalar(ctx, false, dk, dk, 1, npoly, nc, upload(ctx, sc, keep));
 }
 
+// Switching key for s' (NTT form over the whole chain) -> s.
 void make_switch_key(hc_ctx* ctx, const u64* s_ntt, const u64* sp_ntt, u64 seed, u64 g, SwitchKeyDev& out) {
   const hc_params& P = ctx->P;
   const int nc = P.nchain(), n = P.n;
@@ -870,8 +861,7 @@ void make_switch_key(hc_ctx* ctx, const u64* s_ntt, const u64* sp_ntt, u64 seed,
     launch_scalar(ctx, false, dt, dsp, 1, 1, nc, upload(ctx, sc, keep));
     launch_ew(ctx, 0, db, db, dt, 1, 1, nc);
   }
-  // stored in Montgomery form (x 2^64 mod q): the key product reduces its
-  // sums with one Montgomery reduction
+  // stored in Montgomery form, the limbs of Q times P^{-1}
   key_scale(ctx, out.buf->ptr, 2 * P.dnum, false, keep);
   HC_CUDA(cudaStreamSynchronize(ctx->stream));
 }

@@ -44,20 +44,20 @@ struct CtRef {
 };
 
 // The fused tail of relinearise + rescale carried by the forward NTT of the
-// converted limbs z_k[i] (i < level, poly k < 2, item z):
-// - first pass, on load: x = z_k[i] P^{-1} + [c_l]_{q_i}, with c_l the
-//   centred last limb of the relinearised poly stored as a signed integer in
+// converted limbs z_k[i] (i < level, poly k < 2, item z).  ModDown's P^{-1}
+// is already in z (conversion constants) and in the key-product
+// accumulators acc (the keys' Q limbs), so:
+// - first pass, on load: x = z_k[i] + [c_l]_{q_i}, with c_l the centred last
+//   limb of the relinearised poly stored as a signed integer in
 //   cl[z][k][coefficient];
-// - last pass, on store: out_k[i] = (base_k[i] + acc_k[i] P^{-1} - NTT(x))
-//   q_l^{-1}, written to the output ciphertexts instead of back into z.
+// - last pass, on store: out_k[i] = (base_k[i] + acc_k[i] - NTT(x)) q_l^{-1},
+//   written to the output ciphertexts instead of back into z.
 // The same tail in coefficient form is carried by the inverse NTT of
-// y = base_k[i] + acc_k[i] P^{-1} (formed on load by the first pass); the
-// last pass stores out_k[i] = (INTT(y) - z_k[i] P^{-1} - [c_l]_{q_i}) q_l^{-1}
-// into the transform's own limbs, with N^{-1} folded into q_l^{-1}.
+// y = base_k[i] + acc_k[i] (formed on load by the first pass); the last pass
+// stores out_k[i] = INTT(y) q_l^{-1} - (z_k[i] + [c_l]_{q_i}) q_l^{-1} into
+// the transform's own limbs, with N^{-1} folded into the first constant.
 struct KsrFuse {
   const u64* cl;        // [item][2][N] signed centred c_l
-  const u64* pinv;      // P^{-1} mod q_i (i <= level)
-  const u64* pinv_sh;
   const u64* acc;       // key-product accumulators, NTT form
   u64 acc_item_stride, acc_poly_stride;
   const CtRef* base0;   // (d0, d1) or null
@@ -65,12 +65,13 @@ struct KsrFuse {
   const CtRef* out;     // level-1 outputs
   const u64* qlinv;     // q_l^{-1} mod q_i, then its Shoup companions
   int level;
+  int cl_small;         // every q_i (i < level) exceeds |c_l|: [c_l]_{q_i} needs no reduction
   // coefficient-form tail only
   const u64* z;         // z_k[i] at z + item*z_item_stride + k*z_poly_stride + i*N
   u64 z_item_stride, z_poly_stride;
   const u64* nqlinv;    // N^{-1} q_l^{-1} mod q_i, then its Shoup companions
-  const u64* pqlinv;    // P^{-1} q_l^{-1} mod q_i, then its Shoup companions
 };
+
 
 // A set of limbs for batched per-limb kernels (NTT, copies): for batch item
 // z, poly k < npoly and limb slot l0 <= s < l0 + nlimb the limb lives at
@@ -173,4 +174,13 @@ __device__ __forceinline__ u64 mulm(u64 a, u64 b, const DMod& m) {
   U128 x{a * b, __umul64hi(a, b)};
   return reduce128(x, m);
 }
+// [c]_q of a signed integer c stored in a word (the centred c_l of the
+// fused tail); `small` says |c| < q is known.
+__device__ __forceinline__ u64 lift_signed(u64 word, const DMod& md, int small) {
+  const long long c = (long long)word;
+  const u64 mag = c < 0 ? (u64)(-c) : (u64)c;
+  const u64 m = small ? mag : csub(shoup_lazy(mag, 1, md.one_sh, md.q), md.q);
+  return c < 0 ? negm(m, md.q) : m;
+}
 #endif  // __CUDACC__
+

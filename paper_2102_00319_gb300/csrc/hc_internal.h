@@ -61,8 +61,7 @@ struct LevelConsts {
   int dnum = 0;
   // ModUp digit j: hat_inv[i] (+sh) for i < |D_j|, then hat_mod[t][i] for t < ext
   std::vector<int> modup_off;
-  // rescale: q_l^{-1} mod q_i (+sh), then N^{-1} q_l^{-1} (+sh) and
-  // P^{-1} q_l^{-1} (+sh), each for i < l
+  // rescale: q_l^{-1} mod q_i (+sh), then N^{-1} q_l^{-1} (+sh), each for i < l
   int rescale_off = -1;
   // ModUp digit j: offset in hc_ctx::modup_slots of the ext slots outside
   // the digit ([0, d0) then [d1, l + 1 + alpha)), one transform launch each
@@ -89,7 +88,7 @@ struct hc_ctx {
   std::vector<void*> owned;  // table allocations
   u64* ks_dev = nullptr;     // flat constant buffer
   std::vector<LevelConsts> lv;
-  int moddown_off = -1;      // (P/p_k)^{-1} mod p_k (+sh); (P/p_k) mod q_i; P^{-1} mod q_i (+sh)
+  int moddown_off = -1;      // (P/p_k)^{-1} N^{-1} mod p_k (+sh); p_k^{-1} mod q_i
   int* ext_map = nullptr;    // [level][L+1+alpha] chain index of ext slot
   int* modup_slots = nullptr;  // per (level, digit): ext slots raised by that digit's ModUp
   std::string err;
@@ -277,5 +276,5 @@ void launch_ksr_last(hc_ctx* ctx, int level, const u64* acc, u64 acc_item_stride
 // In place over tl: the centred c_l = t_k - z_k[l] P^{-1} mod q_l as a signed
 // integer per coefficient (coefficient-form tl from the inverse NTT).
 void launch_ksr_cl(hc_ctx* ctx, int level, u64* tl, const u64* zq, u64 z_item_stride, int items);
-// Constants of the fused tail at `level` (pinv, pinv_sh, qlinv into f).
+// Constants of the fused tail at `level` (q_l^{-1}, N^{-1} q_l^{-1}, whether c_l needs reducing) into f.
 void ksr_constants(hc_ctx* ctx, int level, KsrFuse& f);

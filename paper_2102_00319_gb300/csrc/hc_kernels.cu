@@ -278,8 +278,9 @@ __global__ void k_key_product(const u64* ext, u64 ext_item_stride, const u64* ke
   o[(size_t)next * n] = redc(a1, md);
 }
 
-// ModDown conversion P -> Q_level of both polys.
-// cst: [alpha] hat_inv, [alpha] hat_inv_sh, [L+1][alpha] hat_mod, [L+1] pinv, [L+1] pinv_sh
+// ModDown conversion P -> Q_level of both polys, times P^{-1}.
+// cst: [alpha] hat_inv, [alpha] hat_inv_sh, [L+1][alpha] hat_mod with
+// hat_mod[t][k] = (P/p_k) P^{-1} = p_k^{-1} mod q_t
 __global__ void k_moddown_bconv(const u64* src, u64 src_item_stride, u64 src_poly_stride, u64* zq,
                                 u64 z_item_stride, const u64* cst, int alpha, int nq, int L,
                                 Tables T) {
@@ -302,10 +303,11 @@ __global__ void k_moddown_bconv(const u64* src, u64 src_item_stride, u64 src_pol
   }
 }
 
+// out_k = base_k + u_k - NTT(z_k): the key product's Q limbs u and the
+// conversion z both carry ModDown's P^{-1} already.
 __global__ void k_moddown_combine(const u64* acc, u64 acc_item_stride, u64 acc_poly_stride,
                                   const u64* zq, u64 z_item_stride, const CtRef* base0,
-                                  const CtRef* base1, const CtRef* out, const u64* pinv,
-                                  const u64* pinv_sh, int nq, Tables T) {
+                                  const CtRef* base1, const CtRef* out, int nq, Tables T) {
   const int n = 1 << T.log_n;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
@@ -314,7 +316,7 @@ __global__ void k_moddown_combine(const u64* acc, u64 acc_item_stride, u64 acc_p
   const size_t li = (size_t)i * n + c;
   const u64 u = acc[(size_t)z * acc_item_stride + (size_t)k * acc_poly_stride + li];
   const u64 zz = zq[(size_t)z * z_item_stride + (size_t)k * nq * n + li];
-  u64 r = shoup(subm(u, zz, q), pinv[i], pinv_sh[i], q);
+  u64 r = subm(u, zz, q);
   const CtRef* base = k == 0 ? base0 : base1;
   if (base) r = addm(r, base[z].p[li], q);
   out[z].p[(size_t)k * out[z].stride + li] = r;
@@ -561,15 +563,11 @@ void launch_moddown_bconv(hc_ctx* ctx, int level, const u64* accp_coef, u64 accp
 void launch_moddown_combine(hc_ctx* ctx, int level, const u64* acc, u64 acc_item_stride, const u64* z,
                             u64 z_item_stride, const CtRef* base0, const CtRef* base1, const CtRef* out,
                             int items) {
-  const int nq = level + 1, next = level + 1 + ctx->P.alpha, L = ctx->P.L, a = ctx->P.alpha;
-  const u64* cst = ctx->ks(ctx->moddown_off);
-  const u64* pinv = cst + 2 * a + (size_t)(L + 1) * a;
-  const u64* pinv_sh = pinv + (L + 1);
+  const int nq = level + 1, next = level + 1 + ctx->P.alpha;
     {
       ProfScope prof_(ctx, "k_moddown_combine", (uint64_t)items * 2 * nq);
       k_moddown_combine<<<grid_for(ctx, 2 * nq, items), kT, 0, ctx->stream>>>(
-        acc, acc_item_stride, (u64)next * ctx->P.n, z, z_item_stride, base0, base1, out, pinv, pinv_sh, nq,
-        ctx->tab);
+        acc, acc_item_stride, (u64)next * ctx->P.n, z, z_item_stride, base0, base1, out, nq, ctx->tab);
     }
   LAUNCH_DONE(ctx);
 }
@@ -765,7 +763,8 @@ __global__ void __launch_bounds__(kT) k_moddown_bconv_h(const u64* src, u64 src_
   }
 }
 
-// ModDown conversion P -> Q_level of both polys (ALPHA special primes).
+// ModDown conversion P -> Q_level of both polys (ALPHA special primes), times
+// P^{-1} (folded into the constants, as in k_moddown_bconv).
 template <int ALPHA>
 __global__ void __launch_bounds__(kT) k_moddown_bconv_t(const u64* src, u64 src_item_stride, u64 src_poly_stride,
                                                          u64* zq, u64 z_item_stride, const u64* cst, int nq, int L,
@@ -848,26 +847,26 @@ __global__ void __launch_bounds__(kT) k_key_product_t(const u64* ext, u64 ext_it
   }
 }
 
-// Fused relinearise + rescale, step 1: t_k = base_k[l] + acc_k[l] P^{-1}
-// (NTT form, last limb only).
+// Fused relinearise + rescale, step 1: t_k = base_k[l] + acc_k[l] (NTT
+// form, last limb only; the key product's Q limbs carry P^{-1} already).
 __global__ void k_ksr_last(const u64* acc, u64 acc_item_stride, u64 acc_poly_stride, const CtRef* base0,
-                           const CtRef* base1, u64* tl, int level, u64 pinv, u64 pinv_sh, Tables T) {
+                           const CtRef* base1, u64* tl, int level, Tables T) {
   const int n = 1 << T.log_n;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
   const int k = blockIdx.y, z = blockIdx.z;
   const u64 q = T.mods[level].q;
   const size_t li = (size_t)level * n + c;
-  u64 r = shoup(acc[(size_t)z * acc_item_stride + (size_t)k * acc_poly_stride + li], pinv, pinv_sh, q);
+  u64 r = acc[(size_t)z * acc_item_stride + (size_t)k * acc_poly_stride + li];
   const CtRef* base = k == 0 ? base0 : base1;
   if (base) r = addm(r, base[z].p[li], q);
   tl[((size_t)z * 2 + k) * n + c] = r;
 }
 
-// Step 2 of the fused form: the centred c_l = t_k - z_k[l] P^{-1} mod q_l
-// stored over t_k as a signed integer (the forward NTT of z lifts it).
-__global__ void k_ksr_cl(u64* tl, const u64* zq, u64 z_item_stride, int level, u64 pinv_l, u64 pinv_l_sh,
-                         Tables T) {
+// Step 2 of the fused form: the centred c_l = t_k - z_k[l] mod q_l (z
+// carries P^{-1}) stored over t_k as a signed integer (the transform of the
+// other limbs lifts it).
+__global__ void k_ksr_cl(u64* tl, const u64* zq, u64 z_item_stride, int level, Tables T) {
   const int n = 1 << T.log_n;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
@@ -875,7 +874,7 @@ __global__ void k_ksr_cl(u64* tl, const u64* zq, u64 z_item_stride, int level, u
   const u64 ql = T.mods[level].q;
   const u64* zk = zq + (size_t)z * z_item_stride + (size_t)k * (level + 1) * n;
   u64* t = tl + ((size_t)z * 2 + k) * n + c;
-  const u64 cl = subm(*t, shoup(zk[(size_t)level * n + c], pinv_l, pinv_l_sh, ql), ql);
+  const u64 cl = subm(*t, zk[(size_t)level * n + c], ql);
   const bool neg = cl > (ql - 1) / 2;
   *t = neg ? (u64)(-(long long)(ql - cl)) : cl;
 }
@@ -981,43 +980,28 @@ void launch_key_product_batched(hc_ctx* ctx, int level, const u64* ext, u64 ext_
 
 void launch_ksr_last(hc_ctx* ctx, int level, const u64* acc, u64 acc_item_stride, const CtRef* base0,
                      const CtRef* base1, u64* tl, int items) {
-  const int L = ctx->P.L, a = ctx->P.alpha, next = level + 1 + a;
-  const u64* cst = ctx->ks(ctx->moddown_off);
-  (void)cst;
-  // P^{-1} mod q_level, computed on the host
-  u64 pl = 1;
-  const u64 ql = ctx->P.chain[level];
-  for (int m = 0; m < a; ++m) pl = hch::mulmod(pl, ctx->P.chain[L + 1 + m] % ql, ql);
-  pl = hch::invmod(pl, ql);
+  const int next = level + 1 + ctx->P.alpha;
   ProfScope prof_(ctx, "k_ksr_last", (uint64_t)items * 2);
   k_ksr_last<<<grid_for(ctx, 2, items), kT, 0, ctx->stream>>>(acc, acc_item_stride, (u64)next * ctx->P.n, base0, base1,
-                                                             tl, level, pl, hch::shoup_of(pl, ql), ctx->tab);
+                                                             tl, level, ctx->tab);
   ctx->launches++;
   check_launch(ctx);
 }
 
-
 void launch_ksr_cl(hc_ctx* ctx, int level, u64* tl, const u64* zq, u64 z_item_stride, int items) {
-  const int L = ctx->P.L, a = ctx->P.alpha;
   ProfScope prof_(ctx, "k_ksr_cl", (uint64_t)items * 2);
-  const u64 ql = ctx->P.chain[level];
-  u64 p = 1;
-  for (int m = 0; m < a; ++m) p = hch::mulmod(p, ctx->P.chain[L + 1 + m] % ql, ql);
-  p = hch::invmod(p, ql);
-  k_ksr_cl<<<grid_for(ctx, 2, items), kT, 0, ctx->stream>>>(tl, zq, z_item_stride, level, p, hch::shoup_of(p, ql),
-                                                             ctx->tab);
+  k_ksr_cl<<<grid_for(ctx, 2, items), kT, 0, ctx->stream>>>(tl, zq, z_item_stride, level, ctx->tab);
   ctx->launches++;
   check_launch(ctx);
 }
 
 void ksr_constants(hc_ctx* ctx, int level, KsrFuse& f) {
-  const int L = ctx->P.L, a = ctx->P.alpha;
-  const u64* pinv = ctx->ks(ctx->moddown_off) + 2 * a + (size_t)(L + 1) * a;
-  f.pinv = pinv;
-  f.pinv_sh = pinv + (L + 1);
   f.qlinv = ctx->ks(ctx->lv[level].rescale_off);
   f.nqlinv = f.qlinv + 2 * level;
-  f.pqlinv = f.qlinv + 4 * level;
   f.level = level;
+  // |c_l| <= (q_l - 1) / 2 is already reduced modulo every q_i above that bound
+  const u64 half = (ctx->P.chain[level] - 1) / 2;
+  f.cl_small = 1;
+  for (int i = 0; i < level; ++i) f.cl_small &= ctx->P.chain[i] > half ? 1 : 0;
 }
 

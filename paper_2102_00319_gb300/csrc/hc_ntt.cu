@@ -130,13 +130,8 @@ __global__ void __launch_bounds__(1 << TL) k_cols(LimbSet s, LimbSet in, int use
       for (int i = 0; i < (1 << K1); ++i) {
         const u32 e = ((r0 + (i << K2)) << N2) + c;
         if constexpr (FUSE) {
-          // z P^{-1} + [c_l]_{q_i}, c_l centred (its sign carried by the stored integer)
-          const DMod md = T.mods[pid];
-          const u64 zp = shoup(ain[e], f.pinv[fslot], f.pinv_sh[fslot], q);
-          const long long cl = (long long)fcl[e];
-          const u64 mag = cl < 0 ? (u64)(-cl) : (u64)cl;
-          const u64 m = csub(shoup_lazy(mag, 1, md.one_sh, q), q);
-          x[i] = addm(zp, cl < 0 ? negm(m, q) : m, q);
+          // z + [c_l]_{q_i} (z carries P^{-1}; c_l centred, its sign carried by the stored integer)
+          x[i] = addm(ain[e], lift_signed(fcl[e], T.mods[pid], f.cl_small), q);
         } else {
           x[i] = ain[e];
         }
@@ -184,15 +179,11 @@ __global__ void __launch_bounds__(1 << TL) k_cols(LimbSet s, LimbSet in, int use
       for (int i = 0; i < (1 << K1); ++i) {
         const u32 e = ((r0 + (i << K2)) << N2) + c;
         if constexpr (FUSE) {
-          // (INTT(y) - z P^{-1} - [c_l]_{q_i}) q_l^{-1}, N^{-1} folded into the first constant
+          // INTT(y) q_l^{-1} - (z + [c_l]_{q_i}) q_l^{-1}, N^{-1} folded into the first constant
           const int lv = f.level;
           const u64 yv = csub(shoup_lazy(x[i], f.nqlinv[fslot], f.nqlinv[lv + fslot], q), q);
-          const u64 zv = shoup(fz[e], f.pqlinv[fslot], f.pqlinv[lv + fslot], q);
-          const long long cl = (long long)fcl[e];
-          const u64 mag = cl < 0 ? (u64)(-cl) : (u64)cl;
-          const u64 cv = shoup(mag, f.qlinv[fslot], f.qlinv[lv + fslot], q);
-          const u64 t = subm(yv, zv, q);
-          a[e] = cl < 0 ? addm(t, cv, q) : subm(t, cv, q);
+          const u64 w = addm(fz[e], lift_signed(fcl[e], T.mods[pid], f.cl_small), q);
+          a[e] = subm(yv, shoup(w, f.qlinv[fslot], f.qlinv[lv + fslot], q), q);
         } else {
           a[e] = reduce4(scale ? shoup_lazy(x[i], ni, nis, q) : x[i], q);
         }
@@ -245,14 +236,14 @@ __global__ void __launch_bounds__(1 << TL) k_rows(LimbSet s, LimbSet in, int use
     }
     __syncthreads();
     if constexpr (FUSE) {
-      // out_k[i] = (base_k[i] + acc_k[i] P^{-1} - w) q_l^{-1} for the NTT output w
+      // out_k[i] = (base_k[i] + acc_k[i] - w) q_l^{-1} for the NTT output w (acc carries P^{-1})
       const int slot = blockIdx.y % s.nlimb, k = blockIdx.y / s.nlimb, z = blockIdx.z;
       const size_t li0 = ((size_t)slot << LOGN) + ((size_t)row0 << N2);
       const u64* accp = f.acc + (size_t)z * f.acc_item_stride + (size_t)k * f.acc_poly_stride + li0;
       const CtRef* base = k == 0 ? f.base0 : f.base1;
       const u64* bp = base ? base[z].p + li0 : nullptr;
       u64* op = f.out[z].p + (size_t)k * f.out[z].stride + li0;
-      const u64 pv = f.pinv[slot], pvs = f.pinv_sh[slot], qv = f.qlinv[slot], qvs = f.qlinv[f.level + slot];
+      const u64 qv = f.qlinv[slot], qvs = f.qlinv[f.level + slot];
       // four elements per thread per step: their global loads are in flight together
       constexpr u32 kTile = RP << N2, kU = 4;
       static_assert(kTile % (kThreads * kU) == 0, "epilogue tile");
@@ -266,7 +257,7 @@ __global__ void __launch_bounds__(1 << TL) k_rows(LimbSet s, LimbSet in, int use
 #pragma unroll
         for (u32 u = 0; u < kU; ++u) {
           const u32 e = e0 + u * kThreads;
-          u64 r = addm(shoup(av[u], pv, pvs, q), bv[u], q);
+          u64 r = addm(av[u], bv[u], q);
           r = subm(r, sm[sidx(e >> N2, e & (C - 1))], q);
           op[e] = shoup(r, qv, qvs, q);
         }
@@ -279,18 +270,15 @@ __global__ void __launch_bounds__(1 << TL) k_rows(LimbSet s, LimbSet in, int use
     // 16-byte pairs (a thread's points are contiguous and 16-byte aligned;
     // measured faster than staging the tile through shared memory)
     // -> stages LOGN-1 .. LOGN-K2
-    // coefficient-form relinearise + rescale tail: y = base_k[i] + acc_k[i] P^{-1} on load
+    // coefficient-form relinearise + rescale tail: y = base_k[i] + acc_k[i] on load
     const u64* faccp = nullptr;
     const u64* fbp = nullptr;
-    u64 fpv = 0, fpvs = 0;
     if constexpr (FUSE) {
       const int slot = blockIdx.y % s.nlimb, k = blockIdx.y / s.nlimb, z = blockIdx.z;
       const size_t li0 = ((size_t)slot << LOGN) + ((size_t)row0 << N2);
       faccp = f.acc + (size_t)z * f.acc_item_stride + (size_t)k * f.acc_poly_stride + li0;
       const CtRef* base = k == 0 ? f.base0 : f.base1;
       fbp = base ? base[z].p + li0 : nullptr;
-      fpv = f.pinv[slot];
-      fpvs = f.pinv_sh[slot];
     }
     for (u32 w = threadIdx.x; w < (RP << K1); w += kThreads) {
       const u32 r = w >> K1, g = w & ((1 << K1) - 1);
@@ -301,8 +289,8 @@ __global__ void __launch_bounds__(1 << TL) k_rows(LimbSet s, LimbSet in, int use
 #pragma unroll
         for (int i = 0; i < (1 << K2); i += 2) {
           const ulonglong2 v = a2[i >> 1];
-          x[i] = shoup(v.x, fpv, fpvs, q);
-          x[i + 1] = shoup(v.y, fpv, fpvs, q);
+          x[i] = v.x;
+          x[i + 1] = v.y;
         }
         if (fbp) {
           const ulonglong2* b2 = reinterpret_cast<const ulonglong2*>(fbp + o);
@@ -481,7 +469,7 @@ void launch_ntt_ksr(hc_ctx* ctx, const LimbSet& s, int items, const KsrFuse& fus
 
 void launch_intt_ksr(hc_ctx* ctx, const LimbSet& out, int items, const KsrFuse& fuse) {
   HC_CHECK(out.npoly == 2 && out.l0 == 0 && !out.prime_map && !out.slot_map && !out.refs && fuse.z &&
-               fuse.nqlinv && fuse.pqlinv,
+               fuse.nqlinv,
            HC_ERR_INVALID, "coefficient-form tail needs plain output limbs and its constants");
   ntt_dispatch(ctx, out, nullptr, items, true, true, &fuse);
 }

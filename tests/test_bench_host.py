@@ -24,8 +24,8 @@ def test_butterfly_and_mulmod_counts(bench):
     assert bench.butterflies_per_unit("ntt_fwd_cols", 1 << 15) == 7 * (1 << 14)
     assert bench.butterflies_per_unit("ntt_fwd_rows", 1 << 15) == 8 * (1 << 14)
     assert bench.mulmods_per_unit("ntt_fwd_rows", n) == 4 * n
-    assert bench.mulmods_per_unit("ntt_fwd_rows_ksr", n) == 4 * n + 2 * n
-    assert bench.mulmods_per_unit("ntt_fwd_cols_ksr", n) == 4 * n + 1.75 * n
+    assert bench.mulmods_per_unit("ntt_fwd_rows_ksr", n) == 4 * n + n
+    assert bench.mulmods_per_unit("ntt_fwd_cols_ksr", n) == 4 * n
 
 
 def test_multiplier_peak_from_measured_rates(bench):
