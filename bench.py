@@ -238,13 +238,15 @@ def run_reference(args, rank, world):
 # DRAM bytes (read + write) per work unit from one ncu capture of the same
 # kernel version on a smaller batch (one step of 16 pairs run by
 # paper_2102_00319_gb300/probes/one_step.py: 336 limbs per ModUp transform
-# launch), scaled to a launch by its units.  A kernel without an entry (the
-# fused-tail passes changed after their capture) reports no traffic until it
-# is captured again.
+# launch, 640 per fused-tail launch), scaled to a launch by its units.  A
+# kernel without an entry reports no traffic; an entry goes when its kernel
+# changes, until it is captured again.
 NCU_NTT_VARIANT = 1  # block size (HC_TUNE_NTT) of the NTT capture below
 NCU_TRAFFIC_PER_UNIT = {
     "ntt_fwd_cols": (176.321e6 + 120.213e6) / 336,
     "ntt_fwd_rows": (209.276e6 + 122.754e6) / 336,
+    "ntt_fwd_cols_ksr": (352.485e6 + 279.450e6) / 640,
+    "ntt_fwd_rows_ksr": (1114.837e6 + 316.936e6) / 640,
 }
 
 
