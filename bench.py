@@ -441,14 +441,16 @@ def uneven_leg(H, W, np, torch, local):
     """64 independent single-ciphertext inferences (8x8 image, 3x3 conv by
     rotations, x^2) at N = 2^13 / 2^14 / 2^15 and 3..12 levels, run four ways:
     one ABI call per HE op, one layer call per instance, batched per ring
-    degree and level, and the batched form captured in one CUDA graph."""
-    stream = torch.cuda.Stream(device=local)
+    degree and level, and the batched form captured in one CUDA graph.  Each
+    ring degree's context has its own stream, so the three ring degrees' work
+    overlaps on the device (as parallel branches of the graph)."""
     inst = W.uneven_instances(64)
     ctxs, keys, ws, xs = {}, {}, {}, []
+    streams = {log_n: torch.cuda.Stream(device=local) for log_n in (13, 14, 15)}
     for log_n in (13, 14, 15):
         ps = W.uneven_params(log_n)
         params = H.hc_params_create(ps.log_n, list(ps.q_bits), list(ps.p_bits), ps.log2_scale)
-        ctx = H.hc_ctx_create(params, local, stream.cuda_stream)
+        ctx = H.hc_ctx_create(params, local, streams[log_n].cuda_stream)
         ctxs[log_n] = ctx
         keys[log_n] = H.hc_keygen(ctx, W.MASTER_SEED + 3 + log_n, W.SINGLE_CONV_STEPS)
         filt = W.conv_weights(40 + log_n, 1, 3, 3)[0, :, :, 0].reshape(-1)

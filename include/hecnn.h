@@ -304,8 +304,13 @@ int hc_tune_get(const hc_ctx *ctx, int knob);
 /* ------------------------------------------------------- graph capture */
 /*
  * One CUDA graph for a whole multi-instance computation, replayed with one
- * launch.  The n contexts must share one CUDA stream that is not the legacy
- * default stream.  hc_graph_begin gives each context an arena of
+ * launch.  The n contexts (distinct, none on the legacy default stream) may
+ * share one CUDA stream or use several: the capture runs on the first
+ * context's stream, every other stream joins it at hc_graph_begin and is
+ * joined back at hc_graph_end, so work issued on different contexts' streams
+ * becomes parallel branches of the graph (ordered as the streams order it),
+ * and hc_graph_launch runs it on the first context's stream.  hc_graph_begin
+ * gives each context an arena of
  * arena_bytes device bytes (allocated before capture starts) from which every
  * temporary and every output created until hc_graph_end is carved, so the
  * captured work allocates nothing; small index tables are written by kernels

@@ -2291,24 +2291,39 @@ struct hc_graph {
 };
 
 namespace {
-int check_graph_ctxs(hc_ctx* const* ctxs, int n, cudaStream_t* stream) {
+// The contexts of one capture: non-null, distinct, none capturing, every
+// stream not the legacy default.  *stream = the first context's stream (the
+// capture's origin); *others = the other contexts' streams, each once.
+int check_graph_ctxs(hc_ctx* const* ctxs, int n, cudaStream_t* stream, std::vector<cudaStream_t>* others) {
   if (!ctxs || n <= 0) return HC_ERR_INVALID;
-  for (int i = 0; i < n; ++i)
-    if (!ctxs[i] || ctxs[i]->stream != ctxs[0]->stream) return HC_ERR_INVALID;
-  if (ctxs[0]->stream == nullptr) return HC_ERR_INVALID;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i] || ctxs[i]->stream == nullptr) return HC_ERR_INVALID;
+    for (int k = 0; k < i; ++k)
+      if (ctxs[k] == ctxs[i]) return HC_ERR_INVALID;
+  }
   *stream = ctxs[0]->stream;
+  others->clear();
+  for (int i = 1; i < n; ++i) {
+    const cudaStream_t s = ctxs[i]->stream;
+    if (s != *stream && std::find(others->begin(), others->end(), s) == others->end()) others->push_back(s);
+  }
   return HC_OK;
 }
 }  // namespace
 
+// Capture on the first context's stream; every other stream joins the
+// capture through an event recorded on the origin (a fork), so the contexts'
+// work becomes parallel branches of one graph, joined again at the end.
 extern "C" int hc_graph_begin(hc_ctx* const* ctxs, int n, size_t arena_bytes) {
   cudaStream_t st;
-  int rc = check_graph_ctxs(ctxs, n, &st);
+  std::vector<cudaStream_t> others;
+  int rc = check_graph_ctxs(ctxs, n, &st, &others);
   if (rc != HC_OK) return rc;
   return guard(ctxs[0], [&] {
     const size_t words = std::max<size_t>(arena_bytes / 8, 32);
     for (int i = 0; i < n; ++i) HC_CHECK(!ctxs[i]->arena, HC_ERR_INVALID, "context already capturing");
     HC_CUDA(cudaStreamSynchronize(st));
+    for (cudaStream_t s : others) HC_CUDA(cudaStreamSynchronize(s));
     for (int i = 0; i < n; ++i) {
       void* p = nullptr;
       if (cudaMalloc(&p, words * 8) != cudaSuccess) {
@@ -2323,13 +2338,41 @@ extern "C" int hc_graph_begin(hc_ctx* const* ctxs, int n, size_t arena_bytes) {
       ctxs[i]->arena_words = words;
       ctxs[i]->arena_off = 0;
     }
+    hc_ctx* lead = ctxs[0];
+    lead->capture_joined.clear();
+    lead->capture_events.assign(2 * others.size(), nullptr);
+    for (auto& e : lead->capture_events) HC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     HC_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    for (size_t k = 0; k < others.size(); ++k) {
+      if (cudaEventRecord(lead->capture_events[2 * k], st) != cudaSuccess ||
+          cudaStreamWaitEvent(others[k], lead->capture_events[2 * k], 0) != cudaSuccess) {
+        // undo: join what was forked, end and drop the capture, free the arenas
+        for (size_t j = 0; j < lead->capture_joined.size(); ++j) {
+          cudaEventRecord(lead->capture_events[2 * j + 1], lead->capture_joined[j]);
+          cudaStreamWaitEvent(st, lead->capture_events[2 * j + 1], 0);
+        }
+        cudaGraph_t gr = nullptr;
+        cudaStreamEndCapture(st, &gr);
+        if (gr) cudaGraphDestroy(gr);
+        cudaGetLastError();
+        for (cudaEvent_t e : lead->capture_events) cudaEventDestroy(e);
+        lead->capture_events.clear();
+        lead->capture_joined.clear();
+        for (int i = 0; i < n; ++i) {
+          cudaFree(ctxs[i]->arena);
+          ctxs[i]->arena = nullptr;
+        }
+        throw HcError{HC_ERR_CUDA, "cannot fork the capture to another context's stream"};
+      }
+      lead->capture_joined.push_back(others[k]);
+    }
   });
 }
 
 extern "C" int hc_graph_end(hc_ctx* const* ctxs, int n, hc_graph** out) {
   cudaStream_t st;
-  int rc = check_graph_ctxs(ctxs, n, &st);
+  std::vector<cudaStream_t> others;
+  int rc = check_graph_ctxs(ctxs, n, &st, &others);
   if (rc != HC_OK) return rc;
   auto* g = new hc_graph();
   g->stream = st;
@@ -2338,11 +2381,21 @@ extern "C" int hc_graph_end(hc_ctx* const* ctxs, int n, hc_graph** out) {
     ctxs[i]->arena = nullptr;
     ctxs[i]->arena_words = ctxs[i]->arena_off = 0;
   }
-  rc = guard(ctxs[0], [&] {
+  hc_ctx* lead = ctxs[0];
+  // join every forked stream back into the origin and end the capture,
+  // whatever happened while capturing (an invalidated capture fails here)
+  const std::vector<cudaStream_t>& joined = lead->capture_joined;
+  for (size_t k = 0; k < joined.size() && 2 * k + 1 < lead->capture_events.size(); ++k) {
+    cudaEventRecord(lead->capture_events[2 * k + 1], joined[k]);
+    cudaStreamWaitEvent(st, lead->capture_events[2 * k + 1], 0);
+  }
+  const cudaError_t e = cudaStreamEndCapture(st, &g->graph);
+  for (cudaEvent_t ev : lead->capture_events) cudaEventDestroy(ev);
+  lead->capture_events.clear();
+  lead->capture_joined.clear();
+  rc = guard(lead, [&] {
+    HC_CHECK(e == cudaSuccess && g->graph, HC_ERR_CUDA, std::string("capture failed: ") + cudaGetErrorString(e));
     HC_CHECK(out, HC_ERR_INVALID, "null output");
-    cudaError_t e = cudaStreamEndCapture(st, &g->graph);
-    HC_CHECK(e == cudaSuccess && g->graph, HC_ERR_CUDA,
-             std::string("capture failed: ") + cudaGetErrorString(e));
     HC_CUDA(cudaGraphInstantiate(&g->exec, g->graph, 0));
     *out = g;
   });

@@ -101,6 +101,10 @@ struct hc_ctx {
   // capture arena: while set, buffer() bump-allocates here instead of the allocator
   u64* arena = nullptr;
   size_t arena_words = 0, arena_off = 0;
+  // graph capture led by this context: the other contexts' streams joined
+  // to it (fork events recorded at the start) and the events to destroy
+  std::vector<cudaStream_t> capture_joined;
+  std::vector<cudaEvent_t> capture_events;
 
   u64* alloc_words(size_t words);
   void free_words(u64* p);

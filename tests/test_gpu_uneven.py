@@ -14,13 +14,11 @@ pytestmark = pytest.mark.gpu
 SAMPLED = {0, 1, 2}  # one instance per ring degree (levels 3, 10, 7)
 
 
-@pytest.fixture(scope="module")
-def setup():
-    import torch
-
-    stream = torch.cuda.Stream()
+def build(streams):
+    """The workload on three contexts (N = 2^13, 2^14, 2^15) whose streams are
+    streams[0], streams[1], streams[2] (the same stream three times, or three)."""
     ctxs, keys, oracle_keys, ws, ows = {}, {}, {}, {}, {}
-    for log_n in (13, 14, 15):
+    for log_n, stream in zip((13, 14, 15), streams):
         ps = W.uneven_params(log_n)
         params = H.hc_params_create(ps.log_n, list(ps.q_bits), list(ps.p_bits), ps.log2_scale)
         ctx = H.hc_ctx_create(params, 0, stream.cuda_stream)
@@ -57,6 +55,14 @@ def setup():
     for c in ctxs.values():
         H.hc_sync(c)
     return dict(ctxs=ctxs, keys=keys, oracle_keys=oracle_keys, ws=ws, ows=ows, inst=inst, xs=xs, oxs=oxs, imgs=imgs)
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import torch
+
+    stream = torch.cuda.Stream()
+    return build([stream] * 3)
 
 
 def run_batched(S):
@@ -128,3 +134,30 @@ def test_uneven_outputs_decrypt_to_conv_squared(setup):
         # scale 2^30 with 30-bit primes at N up to 2^15 keeps about ten bits
         # of slot precision through conv and x^2 (observed errors ~1e-3)
         assert np.max(np.abs(valid - ref.reshape(-1))) < 2.0 ** -8, i
+
+
+def test_uneven_graph_with_a_stream_per_ring_degree(setup):
+    """The same workload on contexts with one stream per ring degree: eager
+    batched calls and one graph whose three branches run concurrently give
+    the single-stream results word for word."""
+    import torch
+
+    S = setup
+    ref = run_batched(S)
+    ref_words = [export(S, i, ref[i]) for i in range(len(ref))]
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    M = build(streams)
+    got = run_batched(M)
+    for i in range(len(got)):
+        assert np.array_equal(export(M, i, got[i]), ref_words[i]), i
+    ctx_list = [M["ctxs"][k] for k in (13, 14, 15)]
+    H.hc_graph_begin(ctx_list, 8 << 30)
+    cap = run_batched(M)
+    g = H.hc_graph_end(ctx_list)
+    for rep in range(2):
+        H.hc_graph_launch(g)
+        H.hc_sync(ctx_list[0])
+        for i in range(len(ref)):
+            assert np.array_equal(export(M, i, cap[i]), ref_words[i]), (rep, i)
+    del cap
+    del g
