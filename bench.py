@@ -557,18 +557,22 @@ def serving_leg(args, H, W, np, torch, local):
     ciphertexts device-resident; admission by device footprint."""
     from paper_2102_00319_gb300 import serving
 
-    stream = torch.cuda.Stream(device=local)
+    sets = [(12, W.SINGLE_N12)] + [(k, W.uneven_params(k)) for k in (13, 14, 15)]
+    # one stream per ring degree: a step's groups of different ring degrees overlap
+    streams = {log_n: torch.cuda.Stream(device=local) for log_n, _ in sets}
 
     def event():
-        e = torch.cuda.Event()
-        e.record(stream)
-        return e
+        evs = []
+        for s in streams.values():
+            e = torch.cuda.Event()
+            e.record(s)
+            evs.append(e)
+        return serving.AllOf(evs)
 
     models, pks = {}, {}
-    sets = [(12, W.SINGLE_N12)] + [(k, W.uneven_params(k)) for k in (13, 14, 15)]
     for log_n, ps in sets:
         params = H.hc_params_create(ps.log_n, list(ps.q_bits), list(ps.p_bits), ps.log2_scale)
-        ctx = H.hc_ctx_create(params, local, stream.cuda_stream)
+        ctx = H.hc_ctx_create(params, local, streams[log_n].cuda_stream)
         sk, pk, evk = H.hc_keygen(ctx, W.MASTER_SEED + 5 + log_n, W.SINGLE_CONV_STEPS)
         filt = W.conv_weights(60 + log_n, 1, 3, 3)[0, :, :, 0].reshape(-1)
         ws = [H.hc_encrypt(ctx, pk, H.hc_encode(ctx, np.full(ctx.n // 2, v), 2.0 ** 30, ctx.L), 3, t)

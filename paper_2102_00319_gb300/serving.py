@@ -10,7 +10,8 @@ weights and request ciphertexts stay resident in device memory.  The loop:
 * groups the admitted requests by ring degree and launches one batched step
   per group (hc_enc_conv2d_single_batch, then x^2 per level) without waiting
   for earlier steps, so work of successive admissions overlaps on the GPU,
-* retires a step when its CUDA event has completed and records each
+* retires a step when its CUDA event has completed (with a stream per ring
+  degree, the events of all the streams: `AllOf`) and records each
   request's latency from arrival to completion.
 
 All computation runs in libhecnn; this module only schedules calls.
@@ -139,6 +140,17 @@ class Server:
 
     def busy(self):
         return bool(self.queue or self.inflight)
+
+
+class AllOf:
+    """Completion of several events (one per stream, when the models' contexts
+    run on separate streams): query() is true once every one has completed."""
+
+    def __init__(self, events):
+        self.events = list(events)
+
+    def query(self):
+        return all(e.query() for e in self.events)
 
 
 def poisson_arrivals(rate: float, count: int, seed: int) -> np.ndarray:

@@ -14,12 +14,14 @@ from paper_2102_00319_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def build_models(stream):
+SETS = [(12, W.SINGLE_N12)] + [(k, W.uneven_params(k)) for k in (13, 14, 15)]
+
+
+def build_models(streams):
     models, sks = {}, {}
-    sets = [(12, W.SINGLE_N12)] + [(k, W.uneven_params(k)) for k in (13, 14, 15)]
-    for log_n, ps in sets:
+    for log_n, ps in SETS:
         params = H.hc_params_create(ps.log_n, list(ps.q_bits), list(ps.p_bits), ps.log2_scale)
-        ctx = H.hc_ctx_create(params, 0, stream.cuda_stream)
+        ctx = H.hc_ctx_create(params, 0, streams[log_n].cuda_stream)
         sk, pk, evk = H.hc_keygen(ctx, W.MASTER_SEED + 5 + log_n, W.SINGLE_CONV_STEPS)
         filt = W.conv_weights(60 + log_n, 1, 3, 3)[0, :, :, 0].reshape(-1)
         ws = [H.hc_encrypt(ctx, pk, H.hc_encode(ctx, np.full(ctx.n // 2, v), 2.0 ** 30, ctx.L), 3, t)
@@ -44,17 +46,25 @@ def make_requests(models, sks, count, seed):
     return reqs, imgs
 
 
-def test_served_results_equal_alone_and_decrypt():
+@pytest.mark.parametrize("per_degree_streams", [False, True])
+def test_served_results_equal_alone_and_decrypt(per_degree_streams):
+    """One stream for all ring degrees, or one per ring degree (the steps'
+    groups then overlap on the device; completion is the event of every
+    stream)."""
     import torch
 
-    stream = torch.cuda.Stream()
+    one_stream = torch.cuda.Stream()
+    streams = {log_n: (torch.cuda.Stream() if per_degree_streams else one_stream) for log_n, _ in SETS}
 
     def event():
-        e = torch.cuda.Event()
-        e.record(stream)
-        return e
+        evs = []
+        for s in set(streams.values()):
+            e = torch.cuda.Event()
+            e.record(s)
+            evs.append(e)
+        return serving.AllOf(evs)
 
-    models, sks = build_models(stream)
+    models, sks = build_models(streams)
     reqs, imgs = make_requests(models, sks, 24, 500)
     one = serving.footprint_bytes(models[15], 12)
     srv = serving.Server(models=models, budget_bytes=6 * one, max_batch=16)

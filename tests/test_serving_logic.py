@@ -63,3 +63,11 @@ def test_poisson_arrivals_rate():
     a = serving.poisson_arrivals(100.0, 20000, 1)
     assert np.all(np.diff(a) > 0)
     assert abs(len(a) / a[-1] - 100.0) < 3.0
+
+
+def test_all_of_completes_when_every_event_has():
+    evs = [FakeEvent(0), FakeEvent(2)]
+    done = serving.AllOf(evs)
+    assert not done.query()  # the second event still has polls to go
+    assert not done.query()
+    assert done.query()
