@@ -243,11 +243,11 @@ int hc_mul_relin_rescale_batch(hc_ctx *ctx, const hc_evk *evk, const hc_ct *cons
  * layout, and out_meta[k] its metadata.  The batch runs as a pipeline of
  * chunks of `chunk` pairs (0: about an eighth of n): copies in, the batched
  * operation and copies out of successive chunks overlap on separate CUDA
- * streams; chunk < 0 gives HC_ERR_INVALID.  The relinearise + rescale tail is formed in coefficient form
- * (one inverse transform per output limb, no forward one), with the same
- * words as hc_mul_relin_rescale_batch followed by hc_ct_export.  Pinned
- * host buffers are needed for the overlap.  Inputs are
- * range-checked on the device; a residue >= its prime gives
+ * streams; chunk < 0 gives HC_ERR_INVALID.  The relinearise + rescale tail
+ * is formed in coefficient form (one inverse transform per output limb, no
+ * forward one), with the same words as hc_mul_relin_rescale_batch followed
+ * by hc_ct_export.  Pinned host buffers are needed for the overlap.  Inputs
+ * are range-checked on the device; a residue >= its prime gives
  * HC_ERR_INVALID after the call has run, with out_host not valid.  Returns
  * when every output is in host memory.  Not capturable in a graph. */
 int hc_mul_relin_rescale_host(hc_ctx *ctx, const hc_evk *evk, const uint64_t *const *a_host,
