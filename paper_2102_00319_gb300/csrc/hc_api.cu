@@ -240,18 +240,20 @@ void keyswitch_batch(hc_ctx* ctx, const u64* key, int level, const std::vector<C
 }
 
 // Key switch of x followed by a rescale, fused: with u = key product over
-// Q_l u P and z = FastBConv_{P->Q}([u]_P) (coefficient form),
-//   relin_k[i]  = base_k[i] + u_k[i] P^{-1} - NTT(z_k[i] P^{-1}),
+// Q_l u P and z = FastBConv_{P->Q}([u]_P) (coefficient form), both carrying
+// ModDown's P^{-1} on Q (the keys' Q limbs and the conversion constants hold
+// it: u' = u P^{-1}, z' = z P^{-1}),
+//   relin_k[i]  = base_k[i] + u'_k[i] - NTT(z'_k[i]),
 //   rescale_k[i] = (relin_k[i] - NTT([relin_k[l]] mod q_i)) q_l^{-1},
-// and NTT is linear, so one NTT of (z_k[i] P^{-1} + [relin_k[l]] mod q_i)
-// per limb serves both; the last limb of relin_k is formed in coefficient
-// form from INTT(base_k[l] + u_k[l] P^{-1}) - z_k[l] P^{-1}.  Bit-identical to
-// keyswitch_batch followed by rescale_batch.  out: degree-1, level l-1.
+// and NTT is linear, so one NTT of (z'_k[i] + [relin_k[l]] mod q_i) per limb
+// serves both; the last limb of relin_k is formed in coefficient form from
+// INTT(base_k[l] + u'_k[l]) - z'_k[l].  Bit-identical to keyswitch_batch
+// followed by rescale_batch.  out: degree-1, level l-1.
 // With coeff_out the results go there in coefficient form instead (2 polys x
 // l limbs per item, `out` unused): by linearity the inverse NTT of
-// base_k[i] + u_k[i] P^{-1} minus (z_k[i] P^{-1} + [c_l]_{q_i}), times
-// q_l^{-1}, is the inverse NTT of the NTT-form result, so the same words come
-// out with one transform per limb instead of two.
+// base_k[i] + u'_k[i] minus (z'_k[i] + [c_l]_{q_i}), times q_l^{-1}, is the
+// inverse NTT of the NTT-form result, so the same words come out with one
+// transform per limb instead of two.
 void keyswitch_rescale_batch(hc_ctx* ctx, const u64* key, int level, const std::vector<CtRef>& x,
                              const std::vector<CtRef>* base0, const std::vector<CtRef>* base1,
                              const std::vector<CtRef>& out, const LimbSet* coeff_out = nullptr) {
@@ -299,7 +301,7 @@ void keyswitch_rescale_batch(hc_ctx* ctx, const u64* key, int level, const std::
     launch_ksr_last(ctx, level, acc, acc_is, b0, b1, tl, m);
     launch_ntt(ctx, limbset_base(tl, 2 * (u64)n, (u64)n, 2, 1, 0, ident_map(ctx) + level), m, true);
     // c_l (centred, signed) over tl; the forward NTT of z lifts it on load and
-    // forms (base + acc P^{-1} - NTT(.)) q_l^{-1} on store
+    // forms (base + acc - NTT(.)) q_l^{-1} on store (acc and z carry P^{-1})
     launch_ksr_cl(ctx, level, tl, zq, z_is, m);
     KsrFuse f{};
     ksr_constants(ctx, level, f);

@@ -244,13 +244,17 @@ void launch_automorph(hc_ctx* ctx, const CtRef* out, const CtRef* a, int items, 
 // limbs of x (items), writes the ext limbs outside the digit into ext.
 void launch_modup_bconv(hc_ctx* ctx, int level, int j, const u64* xcoef, u64 x_item_stride,
                         u64* ext, u64 ext_item_stride, int items);
-// Key product: acc[z][k][slot] = sum_j ext[z][j][slot] * key_j[k][chain(slot)].
+// Key product: acc[z][k][slot] = sum_j ext[z][j][slot] * key_j[k][chain(slot)]
+// (keys stored in Montgomery form, their Q limbs times P^{-1}: the Q slots of
+// acc come out divided by P modulo q_i).
 void launch_key_product(hc_ctx* ctx, int level, const u64* ext, u64 ext_item_stride,
                         const u64* key, u64* acc, u64 acc_item_stride, int items);
-// ModDown conversion of the P part of acc (coefficient form) into z over Q_level.
+// ModDown conversion of the P part of acc (coefficient form) into z over
+// Q_level, times P^{-1} (folded into the constants).
 void launch_moddown_bconv(hc_ctx* ctx, int level, const u64* accp_coef, u64 accp_item_stride,
                           u64* z, u64 z_item_stride, int items);
-// out_k = base_k + (acc_k - z_k) P^{-1} over Q_level (base may be null per k).
+// out_k = base_k + acc_k - z_k over Q_level (base may be null per k): ModDown
+// with P^{-1} already in acc's Q limbs (the keys) and in z (the constants).
 void launch_moddown_combine(hc_ctx* ctx, int level, const u64* acc, u64 acc_item_stride,
                             const u64* z, u64 z_item_stride, const CtRef* base0,
                             const CtRef* base1, const CtRef* out, int items);
@@ -277,7 +281,8 @@ void launch_key_product_batched(hc_ctx* ctx, int level, const u64* ext, u64 ext_
 // Fused relinearise + rescale tail (see hc_kernels.cu).
 void launch_ksr_last(hc_ctx* ctx, int level, const u64* acc, u64 acc_item_stride, const CtRef* base0,
                      const CtRef* base1, u64* tl, int items);
-// In place over tl: the centred c_l = t_k - z_k[l] P^{-1} mod q_l as a signed
+// In place over tl: the centred c_l = t_k - z_k[l] mod q_l (z carrying
+// P^{-1}) as a signed
 // integer per coefficient (coefficient-form tl from the inverse NTT).
 void launch_ksr_cl(hc_ctx* ctx, int level, u64* tl, const u64* zq, u64 z_item_stride, int items);
 // Constants of the fused tail at `level` (q_l^{-1}, N^{-1} q_l^{-1}, whether c_l needs reducing) into f.
