@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tiles and launch shapes")
     ap.add_argument("--graph-arena-gib", type=int, default=0,
                     help="device arena of the captured step (0: 4 GiB + 0.2 GiB per pair)")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--e2e-chunk", type=int, default=0, help="pairs per pipeline chunk of the host call (0: auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-ops", type=int, default=1, help="oracle operations in the CPU sample")
@@ -844,7 +844,7 @@ def run_gpu(args, rank, world, local):
         return H.hc_mul_relin_rescale_host(ctx, evk, in_arrays[:Bn], in_metas[:Bn], in_arrays[Bn:], in_metas[Bn:],
                                            out_arrays, chunk=args.e2e_chunk)
 
-    for _ in range(2 if args.e2e_steps > 0 else 0):  # untimed: the memory pool reaches its steady size
+    for _ in range(3 if args.e2e_steps > 0 else 0):  # untimed: the memory pool reaches its steady size
         e2e_step()
     # the plain pinned-copy rates of the same buffers on this machine, for reading
     # the e2e number (the host link is shared with the box's other GPUs)
@@ -869,10 +869,13 @@ def run_gpu(args, rank, world, local):
         del staging
     barrier()
     t0 = time.perf_counter()
+    e2e_marks = []  # each call returns with its outputs in host memory
     for _ in range(args.e2e_steps):
         e2e_step()
+        e2e_marks.append(time.perf_counter())
     barrier()
     t_e2e = max_over_ranks(max(time.perf_counter() - t0, 1e-9), device="cuda")
+    e2e_step_ms = [round(1000.0 * (b - a), 2) for a, b in zip([t0] + e2e_marks[:-1], e2e_marks)]
     e2e_value = Bn * args.e2e_steps * world / t_e2e if args.e2e_steps > 0 else None
     if args.e2e_steps > 0:  # the host-side result decrypts to the product
         m0 = e2e_step()[0]
@@ -924,7 +927,7 @@ def run_gpu(args, rank, world, local):
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (%.2f GB of resident ciphertexts)" % (2 * Bn * 2 * (L + 1) * n * 8 / 1e9)},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "pinned_copy_gbs": copy_gbs},
+                "pinned_copy_gbs": copy_gbs, "step_ms": e2e_step_ms},
         "gpu_launches": launches, "roofline": roofline, "clocks": clk, "kernels": kern_summary,
         "tuning": tuning,
         "forms": {"graph": graph_value, "eager": eager_value, "unit": UNIT,
