@@ -988,7 +988,8 @@ extern "C" int hc_evk_export(hc_ctx* ctx, const hc_evk* evk, uint64_t g, uint64_
       HC_CHECK(it != evk->galois.end(), HC_ERR_NO_KEY, "no such Galois key");
       k = &it->second;
     }
-    // back from the stored Montgomery form, then as any other polynomial
+    // back from the stored form (Montgomery, the Q limbs times P^{-1}), then
+    // as any other polynomial
     std::vector<BufPtr> keep;
     BufPtr plain = ctx->buffer(2 * poly * ctx->P.dnum);
     keep.push_back(plain);
