@@ -308,8 +308,11 @@ int hc_tune_get(const hc_ctx *ctx, int knob);
  * share one CUDA stream or use several: the capture runs on the first
  * context's stream, every other stream joins it at hc_graph_begin and is
  * joined back at hc_graph_end, so work issued on different contexts' streams
- * becomes parallel branches of the graph (ordered as the streams order it),
- * and hc_graph_launch runs it on the first context's stream.  hc_graph_begin
+ * becomes parallel branches of the graph (ordered as the streams order it).
+ * hc_graph_launch runs it on the first context's stream, after the work
+ * already issued on every captured context's stream, and makes later work
+ * on those streams wait for it, so each context sees the launch in its own
+ * stream order (results can be read through any of them).  hc_graph_begin
  * gives each context an arena of
  * arena_bytes device bytes (allocated before capture starts) from which every
  * temporary and every output created until hc_graph_end is carved, so the

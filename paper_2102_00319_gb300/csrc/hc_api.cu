@@ -2291,6 +2291,10 @@ struct hc_graph {
   cudaGraphExec_t exec = nullptr;
   cudaStream_t stream = nullptr;
   std::vector<void*> arenas;
+  // the other captured contexts' streams, and one event per stream plus one
+  // for the origin, ordering each launch against work on those streams
+  std::vector<cudaStream_t> joined;
+  std::vector<cudaEvent_t> order;
 };
 
 namespace {
@@ -2395,11 +2399,14 @@ extern "C" int hc_graph_end(hc_ctx* const* ctxs, int n, hc_graph** out) {
   const cudaError_t e = cudaStreamEndCapture(st, &g->graph);
   for (cudaEvent_t ev : lead->capture_events) cudaEventDestroy(ev);
   lead->capture_events.clear();
+  g->joined = lead->capture_joined;
   lead->capture_joined.clear();
   rc = guard(lead, [&] {
     HC_CHECK(e == cudaSuccess && g->graph, HC_ERR_CUDA, std::string("capture failed: ") + cudaGetErrorString(e));
     HC_CHECK(out, HC_ERR_INVALID, "null output");
     HC_CUDA(cudaGraphInstantiate(&g->exec, g->graph, 0));
+    g->order.assign(g->joined.size() + 1, nullptr);
+    for (auto& ev : g->order) HC_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     *out = g;
   });
   if (rc != HC_OK) {
@@ -2409,9 +2416,22 @@ extern "C" int hc_graph_end(hc_ctx* const* ctxs, int n, hc_graph** out) {
   return rc;
 }
 
+// The graph runs on the origin stream, after the work already issued on the
+// other captured contexts' streams, and later work on those streams waits
+// for it: each context sees the launch in its own stream order.
 extern "C" int hc_graph_launch(hc_graph* g) {
-  if (!g || !g->exec) return HC_ERR_INVALID;
-  return cudaGraphLaunch(g->exec, g->stream) == cudaSuccess ? HC_OK : HC_ERR_CUDA;
+  if (!g || !g->exec || g->order.size() != g->joined.size() + 1) return HC_ERR_INVALID;
+  for (size_t k = 0; k < g->joined.size(); ++k)
+    if (cudaEventRecord(g->order[k], g->joined[k]) != cudaSuccess ||
+        cudaStreamWaitEvent(g->stream, g->order[k], 0) != cudaSuccess)
+      return HC_ERR_CUDA;
+  if (cudaGraphLaunch(g->exec, g->stream) != cudaSuccess) return HC_ERR_CUDA;
+  if (!g->joined.empty()) {
+    if (cudaEventRecord(g->order.back(), g->stream) != cudaSuccess) return HC_ERR_CUDA;
+    for (cudaStream_t s : g->joined)
+      if (cudaStreamWaitEvent(s, g->order.back(), 0) != cudaSuccess) return HC_ERR_CUDA;
+  }
+  return HC_OK;
 }
 
 extern "C" void hc_graph_destroy(hc_graph* g) {
@@ -2419,6 +2439,8 @@ extern "C" void hc_graph_destroy(hc_graph* g) {
   if (g->stream) cudaStreamSynchronize(g->stream);
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
+  for (cudaEvent_t e : g->order)
+    if (e) cudaEventDestroy(e);
   for (void* p : g->arenas) cudaFree(p);
   delete g;
 }
