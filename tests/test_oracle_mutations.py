@@ -176,3 +176,48 @@ def test_public_key_pin_rejects_sign_error():
 
     assert identity_small(good)
     assert not identity_small(bad)
+
+
+def _automorph_int(m, g):
+    """kappa_g on an integer polynomial: X^i -> X^{i g} in Z[X]/(X^N + 1)."""
+    n = len(m)
+    out = np.zeros(n, dtype=np.float64)
+    for i, c in enumerate(m):
+        e = (i * g) % (2 * n)
+        if e < n:
+            out[e] += c
+        else:
+            out[e - n] -= c
+    return out
+
+
+def rotation_ok(encode_real, decode_real, n=64):
+    """Slot rotation pin: kappa_5 of an encoded vector decodes to the vector
+    shifted left by one slot."""
+    z = np.random.default_rng(9).uniform(-1, 1, n // 2)
+    m = encode_real(z, n)
+    back = decode_real(_automorph_int(m, 5), n)
+    return np.max(np.abs(back - np.roll(z, -1))) < 1e-9
+
+
+def test_rotation_pin_rejects_slot_order_by_generator_3(monkeypatch):
+    from oracle import encoding
+
+    def enc(z, n):
+        return encoding.encode_real_coeffs(z, n, 1.0)
+
+    def dec(m, n):
+        return encoding.decode_coeffs(m, n, 1.0).real
+
+    assert rotation_ok(enc, dec)
+
+    def group_of_3(n):  # slots ordered by powers of 3 instead of 5
+        out = np.empty(n // 2, dtype=np.int64)
+        g = 1
+        for j in range(n // 2):
+            out[j] = g
+            g = (g * 3) % (2 * n)
+        return out
+
+    monkeypatch.setattr(encoding, "_rot_group", group_of_3)
+    assert not rotation_ok(enc, dec)
