@@ -88,3 +88,47 @@ def test_key_product_halves_form_equals_the_sum(dnum, bits):
         s = acc30_sum(ys, stored)
         assert (s >> 64) < t
         assert redc(s & M64, s >> 64, t) == sum(y * k for y, k in zip(ys, ks)) * P_inv % t
+
+
+def tensor_replay(xs, ws, q, chunk):
+    """k_tensor_acc for one coefficient: 128-bit sums a0 = sum x0 w0,
+    s = sum (x0 + x1)(w0 + w1), a2 = sum x1 w1, folded to residues every
+    `chunk` terms with s carrying r0 + r1 + r2; the middle output is
+    s - a0 - a2 (k_tensor_pair is the one-term case)."""
+    from test_modular_bounds_host import reduce128_est
+
+    def red(v):
+        assert 0 <= v < 1 << 128
+        return reduce128_est(v & M64, v >> 64, q)
+
+    a0 = s = a2 = 0
+    for cnt, ((x0, x1), (w0, w1)) in enumerate(zip(xs, ws), 1):
+        a0 += x0 * w0
+        s += (x0 + x1) * (w0 + w1)
+        a2 += x1 * w1
+        assert s < 1 << 128
+        if cnt % chunk == 0:
+            r1 = red(s - a0 - a2)
+            r0, r2 = red(a0), red(a2)
+            a0, a2, s = r0, r2, r0 + r1 + r2
+    return red(a0), red(s - a0 - a2), red(a2)
+
+
+@pytest.mark.parametrize("terms,bits", [(1, 61), (25, 40), (25, 60), (150, 60), (1800, 61)])
+def test_tensor_accumulation_equals_the_products(terms, bits):
+    q = primes([bits])[0]
+    lim = (1 << 128) - 1 - (1 << 64)
+    per = lim // (4 * q * q)
+    chunk = 1024 if per > 1024 else per - 1
+    rng = random.Random(terms + bits)
+    for trial in range(20 if terms > 100 else 100):
+        if trial == 0:
+            xs = [(q - 1, q - 1)] * terms
+            ws = [(q - 1, q - 1)] * terms
+        else:
+            xs = [(rng.randrange(q), rng.randrange(q)) for _ in range(terms)]
+            ws = [(rng.randrange(q), rng.randrange(q)) for _ in range(terms)]
+        d0 = sum(x0 * w0 for (x0, _), (w0, _) in zip(xs, ws)) % q
+        d1 = sum(x0 * w1 + x1 * w0 for (x0, x1), (w0, w1) in zip(xs, ws)) % q
+        d2 = sum(x1 * w1 for (_, x1), (_, w1) in zip(xs, ws)) % q
+        assert tensor_replay(xs, ws, q, chunk) == (d0, d1, d2)
