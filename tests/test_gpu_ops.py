@@ -273,6 +273,23 @@ def test_mul_relin_rescale_61bit_primes():
     p.assert_same(gr, ckks.relin(op, p.o_evk, ckks.mul(op, oa, ob)), "61-bit relin")
 
 
+def test_mul_relin_rescale_base_prime_below_half_the_last():
+    """A chain whose q_0 (30 bits) is below half of the rescaled prime (45
+    bits): the centred last limb then needs reducing modulo q_0 in the fused
+    tail (every other chain here skips that reduction).  Device batch and
+    host call both give the oracle's words."""
+    from hc_pair import Pair
+    p = Pair(10, [30, 45, 45], [50], 25, seed=15)
+    op = p.op
+    za, zb = W.slot_values(13, op.K), W.slot_values(14, op.K)
+    ga, oa = p.encrypt(p.encode_int(za), nonce=1)
+    gb, ob = p.encrypt(p.encode_int(zb), nonce=2)
+    want = ckks.rescale(op, ckks.relin(op, p.o_evk, ckks.mul(op, oa, ob)))
+    p.assert_same(H.hc_mul_relin_rescale_batch(p.ctx, p.g_evk, [ga], [gb])[0], want, "small q_0")
+    outs, metas = _host_products(p, [ga], [gb], op.L)
+    _assert_host_same(outs[0], metas[0], want, "host small q_0")
+
+
 def test_rescale_degree2_and_level_errors(pair):
     op = pair.op
     ga, oa = pair.encrypt_values(W.slot_values(3, op.K), level=2, nonce=40)
