@@ -213,3 +213,32 @@ def test_inverse_pass_pair_returns_the_coefficients(logn, tl, bits):
     assert R.inverse(R.forward(a)) == a
     # without N^{-1} the inverse gives N times the coefficients
     assert R.inverse(R.forward(a), scale=False) == [v * R.n % q for v in a]
+
+
+@pytest.mark.parametrize("logn,g_steps", [(10, 1), (10, 3), (11, -1), (12, 17)])
+def test_automorphism_index_map_in_the_transform_domain(logn, g_steps):
+    """k_automorph permutes NTT slots: slot k holds a(psi^{e_k}) with
+    e_k = 2 brv(k) + 1, and kappa_g(a)(psi^e) = a(psi^{e g}), so output slot
+    k reads input slot brv((e_k g mod 2N - 1) / 2).  Replayed on the
+    transform above, it must equal the transform of X -> X^g applied to the
+    coefficients (with the negacyclic sign)."""
+    q = largest_prime(50, 2 << logn)
+    R = Replay(logn, 7, q)
+    n = R.n
+    g = pow(5, g_steps % (n // 2), 2 * n) if g_steps >= 0 else 2 * n - 1  # a rotation, or conjugation
+    rng = random.Random(logn + g)
+    a = [rng.randrange(q) for _ in range(n)]
+    kappa = [0] * n
+    for i, c in enumerate(a):
+        e = i * g % (2 * n)
+        if e < n:
+            kappa[e] = (kappa[e] + c) % q
+        else:
+            kappa[e - n] = (kappa[e - n] - c) % q
+    fa = R.forward(a)
+    moved = []
+    for k in range(n):
+        e = 2 * brv(k, logn) + 1
+        e2 = e * g % (2 * n)
+        moved.append(fa[brv((e2 - 1) // 2, logn)])
+    assert moved == R.forward(kappa)
