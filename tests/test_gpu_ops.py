@@ -304,6 +304,23 @@ def test_rescale_degree2_and_level_errors(pair):
     assert e.value.code == -2
 
 
+def test_missing_key_and_scale_mismatch_are_error_codes(pair):
+    """A rotation without its Galois key gives HC_ERR_NO_KEY and an addition
+    of operands whose scales differ gives HC_ERR_SCALE_MISMATCH, both before
+    any device work; the context keeps working."""
+    op = pair.op
+    ga, oa = pair.encrypt_values(W.slot_values(5, op.K), level=2, nonce=50)
+    with pytest.raises(H.HcError) as e:
+        H.hc_rotate(pair.ctx, pair.g_evk, ga, 2)  # keys exist for 1, 3, -1, 5, 17 only
+    assert e.value.code == -4
+    sq = H.hc_rescale(pair.ctx, H.hc_relin(pair.ctx, pair.g_evk, H.hc_mul(pair.ctx, ga, ga)))  # level 1, scale s^2 / q_2
+    g1 = H.hc_drop_to_level(pair.ctx, ga, 1)  # level 1, scale s
+    with pytest.raises(H.HcError) as e:
+        H.hc_add(pair.ctx, sq, g1)
+    assert e.value.code == -3
+    pair.assert_same(H.hc_rotate(pair.ctx, pair.g_evk, ga, 1), ckks.rotate(op, pair.o_evk, oa, 1), "after errors")
+
+
 def test_rotations_bit_exact(pair):
     op = pair.op
     z = W.slot_values(4, op.K)
