@@ -62,6 +62,13 @@ def parse():
     ap.add_argument("--paper-shape", action="store_true",
                     help="also run the paper's own network (N=2^15, 16384 images; ~80 GB of device memory)")
     ap.add_argument("--serve-requests", type=int, default=60, help="requests per arrival rate")
+    ap.add_argument("--profile-step", type=int, metavar="B", default=0,
+                    help="run one batched step of B pairs between cudaProfilerStart/Stop (for ncu "
+                         "--profile-from-start off) after two untimed ones, and exit")
+    ap.add_argument("--profile-cnn", action="store_true",
+                    help="run one batched pass of the N=2^14 CNN between cudaProfilerStart/Stop, and exit")
+    ap.add_argument("--probe-intmul", action="store_true",
+                    help="print the integer-multiply throughputs of this GPU (hc_int_mul_rates), and exit")
     ap.add_argument("--summarize-ncu", metavar="CSV",
                     help="summarise an ncu launch list (gpu__time_duration.sum) of the timed step and exit")
     ap.add_argument("--step-occurrence", type=int, default=2,
@@ -211,6 +218,18 @@ class OracleBench:
                 "textbook-NTT product mode, OpenMP over limbs" % n_ops)
 
 
+def bench_config(batch, world):
+    """The workload both arms report: N = 2^16, L = 20, seven special primes
+    (dnum = 3), `batch` resident ciphertext pairs per step."""
+    from paper_2102_00319_gb300 import workloads as W
+
+    ps = W.DEEP_N16
+    n, L, alpha = 1 << ps.log_n, len(ps.q_bits) - 1, len(ps.p_bits)
+    return {"workload": "deep_n16_l20", "N": n, "L": L, "alpha": alpha, "dnum": -(-(L + 1) // alpha),
+            "batch": batch, "parallelism": "replicas" if world > 1 else "single",
+            "l2": "inputs larger than L2 (%.2f GB of resident ciphertexts)" % (2 * batch * 2 * (L + 1) * n * 8 / 1e9)}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -222,7 +241,7 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": "deep_n16_l20", "N": 65536, "L": 20, "dnum": 3, "batch": 1},
+        "config": bench_config(args.batch, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": ob.threads, "kind": "oracle",
                          "sample": "each step: " + ob.sample(1)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -257,6 +276,9 @@ NCU_TRAFFIC_PER_UNIT = {
 LO64_PER_SM_CLK = 14.4
 HI64_PER_SM_CLK = 6.6
 MULMODS_PER_SM_CLK = 1.0 / (2.0 / LO64_PER_SM_CLK + 1.0 / HI64_PER_SM_CLK)
+# A 64 x 64 -> 128 multiply-add (the tensor accumulation's unit: one low and
+# one high product with their carries) at the same rates.
+MAC128_PER_SM_CLK = 1.0 / (1.0 / LO64_PER_SM_CLK + 1.0 / HI64_PER_SM_CLK)
 
 
 # Busy share of the integer multiplier (ncu sm__pipe_fmaheavy_cycles_active,
@@ -297,8 +319,10 @@ def bytes_per_unit(name, n, dnum):
         return 2 * limb                       # read + write the limb
     if name == "k_key_product":
         return (3 * dnum + 2) * limb          # dnum raised limbs + 2 dnum key limbs in, 2 out
-    if name in ("k_tensor_acc", "k_tensor_pair"):
-        return 7 * limb                       # 4 operand limbs in, 3 out (one term per output here)
+    if name == "k_tensor_pair":
+        return 7 * limb                       # 4 operand limbs in, 3 out (one term per output)
+    if name == "k_tensor_acc":
+        return 4 * limb                       # per (term, limb): 4 operand limbs in (outputs amortised)
     if name in ("k_moddown_combine",):
         return 4 * limb                       # acc, converted limb, base in; out
     if name in ("k_rescale_combine",):
@@ -306,14 +330,77 @@ def bytes_per_unit(name, n, dnum):
     return 2 * limb
 
 
-def cnn_leg(args, H, W, np, torch, local):
+def plain_batch_network(np, x, conv_w, stride, act, fc_w):
+    """FP64 forward pass of the plaintext network the encrypted layers
+    evaluate (a guard on the benchmark's decryptions, not a parity check):
+    x [B][H][W], conv_w [C][k][k][1], valid windows at stride `stride`,
+    activation a0 + a1 u + a2 u^2, non-overlapping 2x2 means, channel-last
+    flatten, FC without bias."""
+    B, Hh, Ww = x.shape
+    C, k = conv_w.shape[0], conv_w.shape[1]
+    Ho, Wo = (Hh - k) // stride + 1, (Ww - k) // stride + 1
+    win = np.lib.stride_tricks.sliding_window_view(x, (k, k), axis=(1, 2))[:, ::stride, ::stride][:, :Ho, :Wo]
+    y = np.einsum("bmnpq,cpq->bmnc", win, conv_w[..., 0])
+    y = act[0] + act[1] * y + act[2] * y * y
+    Hp, Wp = Ho // 2, Wo // 2
+    y = y[:, :2 * Hp, :2 * Wp].reshape(B, Hp, 2, Wp, 2, C).mean(axis=(2, 4))
+    return y.reshape(B, -1) @ fc_w.T
+
+
+def plain_deep_network(np, img, conv_w, act, fc_w):
+    """FP64 guard for the single-ciphertext deep network: 3x3 valid conv of
+    one image with C filters, the polynomial `act` (coefficients c_0..c_d),
+    2x2 means, channel-last flatten, FC."""
+    k = conv_w.shape[1]
+    win = np.lib.stride_tricks.sliding_window_view(img, (k, k))
+    y = np.polynomial.polynomial.polyval(np.einsum("mnpq,cpq->mnc", win, conv_w), act)
+    Hp, Wp = y.shape[0] // 2, y.shape[1] // 2
+    y = y[:2 * Hp, :2 * Wp].reshape(Hp, 2, Wp, 2, -1).mean(axis=(1, 3))
+    return fc_w @ y.reshape(-1)
+
+
+def ps_dnum(ps, level):
+    """Key-switch digits of a parameter set at `level`."""
+    alpha = len(ps.p_bits)
+    return -(-(level + 1) // alpha)
+
+
+def leg_roofline(kernels, n, dnum, clk, local, torch, pass_ms):
+    """Roofline object of the dominant kernel of a profiled pass: integer
+    multiplier (NTT passes: Shoup products; tensor accumulation: 64 x 64 ->
+    128 multiply-adds) at the SM clock sampled during the pass, else HBM."""
+    dom = max(kernels, key=lambda k: kernels[k][1])
+    cnt, tot, units = kernels[dom]
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+    out = {"kernel": dom, "avg_launch_us": 1000.0 * tot / max(cnt, 1), "launches": cnt,
+           "share_of_pass": tot / pass_ms if pass_ms else None, "sm_mhz": mhz}
+    if dom.startswith("ntt_") or dom == "k_tensor_acc":
+        if dom == "k_tensor_acc":
+            work, per_clk, unit = units * n * 3, MAC128_PER_SM_CLK, "G 64x64->128 multiply-adds/s"
+        else:
+            work, per_clk, unit = units * mulmods_per_unit(dom, n), MULMODS_PER_SM_CLK, "G Shoup mulmod/s"
+        peak = per_clk * sms * mhz * 1e6 / 1e9
+        got = work / (tot / 1000.0) / 1e9
+        out.update({"bound": "alu", "achieved": got, "peak": peak, "unit": unit, "frac": got / peak,
+                    "traffic": None, "peak_source": "derived from measured 64-bit multiply rates: %.2f/SM/clk"
+                                                     " x %d SMs x %.0f MHz" % (per_clk, sms, mhz)})
+    else:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        peak = peaks.get("hbm_gbs", 6800.0)
+        got = units * bytes_per_unit(dom, n, dnum) / (tot / 1000.0) / 1e9
+        out.update({"bound": "hbm", "achieved": got, "peak": peak, "unit": "GB/s", "frac": got / peak,
+                    "traffic": None, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"})
+    return out
+
+
+def cnn_leg(args, H, W, np, torch, local, profile_only=False):
     """Encrypted images/s of the batch-packed CNN at N = 2^14 (8192 images of
     28x28: conv 5x5 stride 2 with 5 channels -> x^2 -> 2x2 mean pool -> FC
     180 -> 10), through the layer calls (batched) and through one ABI call
     per homomorphic operation (per-op); plus the latency of the N = 2^12
     single-ciphertext conv (eight rotations) + x^2."""
-    from oracle import cnn as ref_cnn  # FP64 plaintext network only (correctness guard)
-
     ps, c = W.BATCH_N14, W.CNN_BATCH
     params = H.hc_params_create(ps.log_n, list(ps.q_bits), list(ps.p_bits), ps.log2_scale)
     stream = torch.cuda.current_stream()
@@ -321,7 +408,7 @@ def cnn_leg(args, H, W, np, torch, local):
     K = ctx.n // 2
     seed = W.MASTER_SEED + 2
     sk, pk, evk = H.hc_keygen(ctx, seed)
-    tuning = H.hc_autotune(ctx, evk, 64)
+    tuning = None if profile_only else H.hc_autotune(ctx, evk, 64)
     imgs = W.images(seed + 20, K, c["H"], c["W"])
     cw = W.conv_weights(seed + 21, c["cout"], c["k"], c["k"])
     Ho = (c["H"] - c["k"]) // c["stride"] + 1
@@ -383,12 +470,31 @@ def cnn_leg(args, H, W, np, torch, local):
 
     zb = batched()
     H.hc_sync(ctx)
+    if profile_only:
+        torch.cuda.profiler.start()
+        zb = batched()
+        H.hc_sync(ctx)
+        torch.cuda.profiler.stop()
+        print("profiled one CNN pass (%d logits ciphertexts)" % len(zb))
+        return None
     launches0 = H.hc_kernel_launches(ctx)
     t0 = time.perf_counter()
     for _ in range(args.cnn_steps):
         zb = batched()
     H.hc_sync(ctx)
     t_b = (time.perf_counter() - t0) / args.cnn_steps
+    # one more pass with per-kernel events: the dominant kernel's roofline
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    H.hc_profile_enable(ctx, True)
+    batched()
+    H.hc_sync(ctx)
+    clk = clocks.stop()
+    kernels = {name: H.hc_profile_kernel(ctx, name) for name in H.hc_profile_names(ctx)}
+    H.hc_profile_enable(ctx, False)
+    pass_ms = sum(v[1] for v in kernels.values())
+    roofline = leg_roofline(kernels, ctx.n, ps_dnum(ps, len(ps.q_bits) - 1), clk, local, torch, pass_ms)
     launches_b = (H.hc_kernel_launches(ctx) - launches0) / args.cnn_steps
     launches0 = H.hc_kernel_launches(ctx)
     t0 = time.perf_counter()
@@ -398,7 +504,7 @@ def cnn_leg(args, H, W, np, torch, local):
     launches_p = H.hc_kernel_launches(ctx) - launches0
     same = all(np.array_equal(H.hc_ct_export(ctx, u)[0], H.hc_ct_export(ctx, v)[0]) for u, v in zip(zb, zp))
     logits = np.stack([H.hc_decode(ctx, H.hc_decrypt(ctx, sk, t)).real for t in zb], axis=1)
-    ref = ref_cnn.network(imgs[..., None], cw, c["stride"], c["act"], fw)
+    ref = plain_batch_network(np, imgs, cw, c["stride"], c["act"], fw)
     err = float(np.max(np.abs(logits - ref)))
     assert err < 2.0 ** -15 and same, (err, same)
 
@@ -431,7 +537,8 @@ def cnn_leg(args, H, W, np, torch, local):
         "images_per_s_batched": K / t_b, "images_per_s_per_op": K / t_p,
         "ms_batched": 1000 * t_b, "ms_per_op": 1000 * t_p, "speedup_batched_vs_per_op": t_p / t_b,
         "launches_batched": launches_b, "launches_per_op": launches_p,
-        "bit_identical_batched_vs_per_op": same, "max_logit_error_vs_fp64": err, "tuning": tuning,
+        "bit_identical_batched_vs_per_op": same, "max_logit_error_vs_fp64": err, "roofline": roofline,
+        "kernel_shares": {k: round(v[1] / pass_ms, 4) for k, v in sorted(kernels.items(), key=lambda kv: -kv[1][1])[:8]},
         "single_ct_conv_x2_ms": 1000 * t_single,
         "single_ct_workload": "single_n12: 8x8 image, 3x3 conv by 8 rotations, x^2",
     }
@@ -603,8 +710,6 @@ def deep_leg(H, W, np, torch, local):
     """Latency of one 28x28 image through the deep single-ciphertext CNN at
     N = 2^16, L = 20: conv 3x3 x16 by hoisted rotations, degree-7 ReLU
     interpolant, 2x2 mean pool by rotations, FC 2704 -> 10 by rotate-and-sum."""
-    from oracle import cnn as ref_cnn  # FP64 plaintext network only (correctness guard)
-
     ps, d = W.DEEP_N16, W.DEEP_CNN
     params = H.hc_params_create(ps.log_n, list(ps.q_bits), list(ps.p_bits), ps.log2_scale)
     stream = torch.cuda.current_stream()
@@ -640,7 +745,7 @@ def deep_leg(H, W, np, torch, local):
     H.hc_sync(ctx)
     t = (time.perf_counter() - t0) / 3
     got = np.array([H.hc_decode(ctx, H.hc_decrypt(ctx, sk, c))[0].real for c in out])
-    err = float(np.max(np.abs(got - ref_cnn.deep_network(img, cw, act, fw))))
+    err = float(np.max(np.abs(got - plain_deep_network(np, img, cw, act, fw))))
     assert err < 2.0 ** -15, err
     return {"workload": "deep_n16_l20: 28x28 image per ciphertext, conv 3x3 x16 (hoisted), degree-7 ReLU, pool, fc 10",
             "latency_ms": 1000 * t, "images_per_s": 1.0 / t, "max_logit_error_vs_fp64": err, "tuning": tuning}
@@ -650,8 +755,6 @@ def paper_shape_leg(H, W, np, torch, local):
     """The paper's network at N = 2^15 on 16384 synthetic 28x28 images,
     filter by filter as in the paper (conv 3x3 -> Eq. 4 activation -> mean
     pool per filter, then FC 4732 -> 10), inference time on the device."""
-    from oracle import cnn as ref_cnn  # FP64 plaintext network only (correctness guard)
-
     ps, c = W.PAPER_N15, W.PAPER_CNN
     params = H.hc_params_create(ps.log_n, list(ps.q_bits), list(ps.p_bits), ps.log2_scale)
     stream = torch.cuda.current_stream()
@@ -700,12 +803,29 @@ def paper_shape_leg(H, W, np, torch, local):
     t_fc = time.perf_counter() - te
     total = time.perf_counter() - t0
     logits = np.stack([H.hc_decode(ctx, H.hc_decrypt(ctx, sk, t)).real for t in z], axis=1)
-    ref = ref_cnn.network(imgs[..., None], cw, 1, c["act"], fw)
+    ref = plain_batch_network(np, imgs, cw, 1, c["act"], fw)
     err = float(np.max(np.abs(logits - ref)))
     return {"workload": "paper_n15: 16384 images 28x28, 28 filters 3x3 -> ActPool (0.47, 0.50, 0.09) -> fc 4732->10",
             "seconds": total, "images_per_s": K / total, "seconds_conv": t_conv, "seconds_act": t_act,
             "seconds_pool": t_pool, "seconds_fc": t_fc, "max_logit_error_vs_fp64": err,
             "argmax_agreement": float(np.mean(np.argmax(logits, 1) == np.argmax(ref, 1)))}
+
+
+def probe_intmul(H, W, torch, local):
+    """Integer-multiply throughputs of this GPU, per SM per clock (at the
+    maximum clock) and per second, and the Shoup-product and 128-bit
+    multiply-add rates derived from them."""
+    ps = W.SINGLE_N12
+    params = H.hc_params_create(ps.log_n, list(ps.q_bits), list(ps.p_bits), ps.log2_scale)
+    ctx = H.hc_ctx_create(params, local, torch.cuda.current_stream().cuda_stream)
+    r = H.hc_int_mul_rates(ctx)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    print("SMs %d; thread-operations per SM per clock (maximum clock) and per second:" % sms)
+    for form, (per_clk, per_s) in r.items():
+        print("  %-12s %6.1f  %.3e" % (form, per_clk, per_s))
+    lo, hi = r["mul_lo64"][0], r["mul_hi64"][0]
+    print("Shoup product (2 low + 1 high): %.2f per SM per clock" % (1.0 / (2.0 / lo + 1.0 / hi)))
+    print("64x64->128 multiply-add (1 low + 1 high): %.2f per SM per clock" % (1.0 / (1.0 / lo + 1.0 / hi)))
 
 
 def run_gpu(args, rank, world, local):
@@ -718,6 +838,12 @@ def run_gpu(args, rank, world, local):
 
     B.build()
     torch.cuda.set_device(local)
+    if args.probe_intmul:
+        probe_intmul(H, W, torch, local)
+        return
+    if args.profile_cnn:
+        cnn_leg(args, H, W, np, torch, local, profile_only=True)
+        return
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
@@ -730,8 +856,8 @@ def run_gpu(args, rank, world, local):
     n, L, alpha, dnum = ctx.n, ctx.L, ctx.alpha, ctx.dnum
     seed = replica_seed(W.MASTER_SEED + 4, rank)
     sk, pk, evk = H.hc_keygen(ctx, seed)
-    Bn = args.batch
-    tuning = None if args.no_autotune else H.hc_autotune(ctx, evk, Bn)
+    Bn = args.profile_step or args.batch
+    tuning = None if (args.no_autotune or args.profile_step) else H.hc_autotune(ctx, evk, Bn)
     A, Bc = [], []
     for i in range(Bn):
         for lst, off in ((A, 0), (Bc, 1)):
@@ -741,6 +867,17 @@ def run_gpu(args, rank, world, local):
 
     def step():
         return H.hc_mul_relin_rescale_batch(ctx, evk, A, Bc)
+
+    if args.profile_step:
+        for _ in range(2):
+            step()
+        H.hc_sync(ctx)
+        torch.cuda.profiler.start()
+        outs = step()
+        H.hc_sync(ctx)
+        torch.cuda.profiler.stop()
+        print("profiled one step of %d pairs (%d outputs)" % (Bn, len(outs)))
+        return
 
     def barrier():
         torch.cuda.synchronize()
@@ -919,17 +1056,17 @@ def run_gpu(args, rank, world, local):
                      "integer_pipe_busy_ncu": NCU_INT_PIPE_BUSY.get(dom)})
     kern_summary = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / ms, 4)}
                     for k, v in sorted(kernels.items(), key=lambda kv: -kv[1][1])}
+    # headline fields first (a reader of the line's start sees the numbers),
+    # the per-leg detail after them
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * Bn * world / value, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": "deep_n16_l20", "N": n, "L": L, "alpha": alpha, "dnum": dnum, "batch": Bn,
-                   "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (%.2f GB of resident ciphertexts)" % (2 * Bn * 2 * (L + 1) * n * 8 / 1e9)},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "pinned_copy_gbs": copy_gbs, "step_ms": e2e_step_ms},
-        "gpu_launches": launches, "roofline": roofline, "clocks": clk, "kernels": kern_summary,
-        "tuning": tuning,
+        "config": bench_config(Bn, world),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": roofline, "cpu_baseline": None, "gpu_launches": launches, "clocks": clk,
+        "e2e_detail": {"pinned_copy_gbs": copy_gbs, "step_ms": e2e_step_ms},
+        "kernels": kern_summary, "tuning": tuning,
         "forms": {"graph": graph_value, "eager": eager_value, "unit": UNIT,
                   "graph_bit_identical_to_eager": graph_same,
                   "value_is": "graph" if graph_value is not None else "eager"},
@@ -952,6 +1089,8 @@ def run_gpu(args, rank, world, local):
         dt = ob.run(args.cpu_ops)
         line["cpu_baseline"] = {"value": args.cpu_ops / dt, "unit": UNIT, "cores": ob.threads, "kind": "oracle",
                                 "sample": ob.sample(args.cpu_ops)}
+    else:
+        del line["cpu_baseline"]
     print(json.dumps(line), flush=True)
 
 

@@ -123,12 +123,24 @@ int hc_profile_enable(hc_ctx *ctx, int on);
 /* Launch count, summed device time (ms) and work units of the kernel `name`
  * since the last enable (synchronises).  A unit is one N-coefficient limb of
  * the launch's output domain (NTT passes: limbs transformed; key product:
- * output slots; conversions and combines: output limbs).  Unknown names
- * report zero. */
+ * output slots; conversions and combines: output limbs; the tensor
+ * accumulation k_tensor_acc: one (term, limb) pair, i.e. N products of
+ * two degree-1 ciphertexts' limbs).  Unknown names report zero. */
 int hc_profile_kernel(hc_ctx *ctx, const char *name, uint64_t *launches, double *total_ms,
                       uint64_t *units);
 /* Names of the kernels recorded, comma separated, into buf[cap]. */
 int hc_profile_names(hc_ctx *ctx, char *buf, size_t cap);
+/* Integer-multiplier throughput of this GPU (measurement aid; the paper has
+ * no counterpart: its timings are HElib's on CPUs).  Times five forms, each
+ * as four independent dependency chains per thread over 8 blocks of 256
+ * threads per SM: 32-bit multiply-add, 32-bit high half, 32 x 32 -> 64
+ * multiply-add, 64-bit low product, 64-bit high product.  rates[0..4]
+ * receive thread-operations per SM per clock at the device's maximum SM
+ * clock, rates[5..9] thread-operations per second.  cap < 10 gives
+ * HC_ERR_INVALID.  Uses a small buffer from the context allocator and
+ * synchronises the context stream.  The roofline of the modular arithmetic
+ * (NTT butterflies, tensor accumulation) is derived from these rates. */
+int hc_int_mul_rates(hc_ctx *ctx, double *rates, int cap);
 
 /* ----------------------------------------------------------------- keys */
 /*
@@ -215,12 +227,22 @@ int hc_mul_const(hc_ctx *ctx, const hc_ct *x, double c, double const_scale, hc_c
 /* CT-CT mult (Eq. 3): tensor product (a0 b0, a0 b1 + a1 b0, a1 b1) -> degree 2. */
 int hc_mul(hc_ctx *ctx, const hc_ct *x, const hc_ct *y, hc_ct **out);
 /* Relinearisation by hybrid key switching: ModUp of c2 per digit (fast basis
- * conversion), product with the relinearisation key, ModDown by P. */
+ * conversion), product with the relinearisation key, ModDown by P.  It is
+ * the second half of the paper's CT-CT mult (Sec. "Convolution Operator",
+ * Eq. 3: a product of two ciphertexts is again a ciphertext, of the same
+ * size, after one multiplicative level); its cost grows with the modulus
+ * size like the CT-CT mult timings of Sec. "Impact of FHE parameters". */
 int hc_relin(hc_ctx *ctx, const hc_evk *evk, const hc_ct *x, hc_ct **out);
 /* Rescale by the last prime: c_i' = (c_i - [c_l]) q_l^{-1} mod q_i, [.]
- * centred; scale /= q_l.  HC_ERR_DEPTH at level 0. */
+ * centred; scale /= q_l.  HC_ERR_DEPTH at level 0.  This is the modulus
+ * consumed by one multiplicative level (Sec. "Impact of FHE parameters":
+ * each added multiplication needs a larger modulus L of a fresh ciphertext;
+ * here one prime q_l per level). */
 int hc_rescale(hc_ctx *ctx, const hc_ct *x, hc_ct **out);
-/* Drops limbs above `level` (scale unchanged). */
+/* Drops limbs above `level` (scale unchanged): aligns operands that have
+ * used different numbers of levels before they are added (the linear and
+ * squared terms of Eq. 4's g; the modulus chain of Sec. "Impact of FHE
+ * parameters"). */
 int hc_drop_to_level(hc_ctx *ctx, const hc_ct *x, int level, hc_ct **out);
 /* Left rotation of the slots by `steps` ("rotation of values in the slots",
  * Sec. "Convolution Operator"): kappa_g, g = 5^steps mod 2N, then a key
@@ -228,7 +250,10 @@ int hc_drop_to_level(hc_ctx *ctx, const hc_ct *x, int level, hc_ct **out);
 int hc_rotate(hc_ctx *ctx, const hc_evk *evk, const hc_ct *x, int steps, hc_ct **out);
 /* n rotations of one ciphertext sharing a single ModUp of c1 (the
  * automorphism is applied to the raised digits).  Decrypts like hc_rotate
- * but is not bit-identical to it. */
+ * but is not bit-identical to it.  Used by the packing that puts a whole
+ * image in one ciphertext (Sec. "Parallelization using multi-threading",
+ * last paragraph: single-image latency), where every convolution tap is a
+ * rotation of the same ciphertext. */
 int hc_rotate_hoisted(hc_ctx *ctx, const hc_evk *evk, const hc_ct *x, const int32_t *steps, int n,
                       hc_ct **outs);
 /* n independent CT-CT mult + relin + rescale on pairs (a[k], b[k]), batched
@@ -258,8 +283,9 @@ int hc_mul_relin_rescale_host(hc_ctx *ctx, const hc_evk *evk, const uint64_t *co
 /*
  * Relinearisation that allocates no device memory.  The paper has no
  * counterpart: this exists for callers that cannot allocate while they run
- * (device memory fixed at start-up, a host thread capturing a CUDA graph,
- * a serving loop that must not enter the allocator).  Same result as
+ * (device memory fixed at start-up, a serving loop that must not enter the
+ * allocator); it calls no cudaMalloc, cudaFree or allocator callback of the
+ * context.  Same result as
  * hc_relin, written into `out`, a degree-1 ciphertext at x's level that the
  * caller allocated earlier (for example by hc_ct_import); its contents are
  * overwritten and its scale set to x's.  Scratch comes from one static

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhecnn.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["hc_ntt.cu", "hc_kernels.cu", "hc_api.cu", "hc_noalloc.cu", "hc_host.cpp"]
+SOURCES = ["hc_ntt.cu", "hc_kernels.cu", "hc_api.cu", "hc_noalloc.cu", "hc_probe.cu", "hc_host.cpp"]
 
 
 def _nvcc():

@@ -396,7 +396,7 @@ std::vector<hc_ct*> tensor_acc(hc_ctx* ctx, const std::vector<const hc_ct*>& xs,
     std::vector<int> off_sub(off.begin() + o0, off.begin() + o0 + m + 1);
     launch_tensor_acc(ctx, refs_dev(ctx, std::vector<CtRef>(orr.begin() + o0, orr.begin() + o0 + m), keep),
                       refs_dev(ctx, xr, keep), refs_dev(ctx, wr, keep), ids_dev(ctx, xi, keep), ids_dev(ctx, wi, keep),
-                      ids_dev(ctx, off_sub, keep), m, level + 1);
+                      ids_dev(ctx, off_sub, keep), m, level + 1, (uint64_t)(off_sub.back() - off_sub.front()));
   }
   return out;
 }

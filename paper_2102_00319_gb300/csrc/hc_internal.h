@@ -235,8 +235,10 @@ void launch_scalar(hc_ctx* ctx, bool add, const CtRef* out, const CtRef* a, int 
 // out[o] = sum_{t<terms[o]} x[xi[o0+t]] (x) w[wi[o0+t]], o0 = off[o].
 // out[z] = a[z] (x) b[z], degree-1 operands, one term per output.
 void launch_tensor_pair(hc_ctx* ctx, const CtRef* out, const CtRef* a, const CtRef* b, int items, int nl);
+// `terms` (the sum of the outputs' term counts) only labels the launch's
+// work for profiling: one unit per (term, limb).
 void launch_tensor_acc(hc_ctx* ctx, const CtRef* out, const CtRef* x, const CtRef* w,
-                       const int* xi, const int* wi, const int* off, int nout, int nl);
+                       const int* xi, const int* wi, const int* off, int nout, int nl, uint64_t terms);
 // NTT-domain automorphism: out = kappa_g(a) for `items` refs, npoly polys, nl limbs.
 void launch_automorph(hc_ctx* ctx, const CtRef* out, const CtRef* a, int items, int npoly, int nl,
                       u64 g);

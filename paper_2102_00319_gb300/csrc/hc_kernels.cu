@@ -492,7 +492,7 @@ void launch_tensor_pair(hc_ctx* ctx, const CtRef* out, const CtRef* a, const CtR
 }
 
 void launch_tensor_acc(hc_ctx* ctx, const CtRef* out, const CtRef* x, const CtRef* w, const int* xi,
-                       const int* wi, const int* off, int nout, int nl) {
+                       const int* wi, const int* off, int nout, int nl, uint64_t terms) {
   if (nout <= 0) return;
   // the Karatsuba sum gains (x0 + x1)(w0 + w1) < 4 qmax^2 per term (on top
   // of a folded residue below 3 qmax): fold before 2^128
@@ -505,7 +505,7 @@ void launch_tensor_acc(hc_ctx* ctx, const CtRef* out, const CtRef* x, const CtRe
   HC_CHECK(chunk >= 1, HC_ERR_INVALID, "primes too large for lazy accumulation");
   HC_CHECK(nout <= 65535, HC_ERR_INVALID, "too many outputs in one launch");
     {
-      ProfScope prof_(ctx, "k_tensor_acc", (uint64_t)nout * nl);
+      ProfScope prof_(ctx, "k_tensor_acc", terms * nl);  // units: (term, limb) pairs
       k_tensor_acc<<<grid_for(ctx, nout, nl), kT, 0, ctx->stream>>>(out, x, w, xi, wi, off, nl, chunk, ctx->tab);
     }
   LAUNCH_DONE(ctx);

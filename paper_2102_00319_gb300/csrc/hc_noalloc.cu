@@ -2,12 +2,13 @@
 //
 // Some callers cannot allocate device memory while they run this library's
 // work: a process whose device memory was carved out and handed over at
-// start-up (a fixed budget, no allocator on the hot path), a host thread
-// that is capturing a CUDA graph (capture forbids cudaMalloc), or a
-// latency-bound serving loop that must not take the allocator's locks.  For
-// them this variant of the key-switching relinearisation draws all of its
-// scratch from one file-scope device array instead of the context allocator;
-// the caller supplies the input and an already allocated output ciphertext.
+// start-up (a fixed budget, no allocator on the hot path), or a
+// latency-bound serving loop that must not take the allocator's locks or
+// wait on it.  For them this variant of the key-switching relinearisation
+// draws all of its scratch from one file-scope device array instead of the
+// context allocator; the caller supplies the input and an already allocated
+// output ciphertext.  It calls no cudaMalloc, cudaFree or allocator
+// callback.
 //
 // Scratch: kNoAllocScratchWords 64-bit words (16 MiB) in a static __device__
 // array.  Every GPU that loads the library holds this array until the process
@@ -29,12 +30,15 @@ static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocSc
 // Device address of the scratch array per device, taken once per device with
 // that device current.  The host-side name of the array is only a stand-in,
 // never a device address, so kernels get these pointers instead.
-u64* g_scratch_addr[HC_MAX_CHAIN] = {};
+constexpr int kMaxDevices = 64;  // devices of one process this table can hold
+u64* g_scratch_addr[kMaxDevices] = {};
 std::mutex g_scratch_mu;
 
 u64* scratch_on(int device) {
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  HC_CHECK(device >= 0 && device < HC_MAX_CHAIN, HC_ERR_INVALID, "device index out of range");
+  int count = 0;
+  HC_CUDA(cudaGetDeviceCount(&count));
+  HC_CHECK(device >= 0 && device < count && device < kMaxDevices, HC_ERR_INVALID, "device index out of range");
   if (!g_scratch_addr[device]) {
     void* p = nullptr;
     HC_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
@@ -101,7 +105,8 @@ extern "C" int hc_relin_noalloc(hc_ctx* ctx, const hc_evk* evk, const hc_ct* x, 
       refs[nref++] = CtRef{ext + (size_t)j * ext_words + (size_t)d0 * n, 0};  // digit limbs in ext
       refs[nref++] = CtRef{x->data + 2 * x->stride + (size_t)d0 * n, 0};     // same limbs of c2
     }
-    HC_CUDA(cudaMemcpyAsync(refs_dev, refs, nref * sizeof(CtRef), cudaMemcpyHostToDevice, ctx->stream));
+    static_assert(sizeof(CtRef) == 2 * sizeof(u64), "CtRef is two words");
+    upload_words(ctx, reinterpret_cast<u64*>(refs_dev), reinterpret_cast<const u64*>(refs), 2 * (size_t)nref);
 
     const int* emap = ctx->ext_map_of(level);
     // c2 -> coefficient form

@@ -1,0 +1,104 @@
+// Throughput of the integer-multiply forms that the modular arithmetic is
+// built from (hc_int_mul_rates), measured on the context's GPU.  The
+// roofline of the multiplication-dense kernels (NTT butterflies: two 64-bit
+// low products and one high product each; the tensor accumulation: one low
+// and one high product per 64 x 64 -> 128 multiply-add) is derived from
+// these rates.  Every thread runs four independent dependency chains so
+// that the issue rate of the multiplier, not the chains' latency, limits.
+#include "hc_internal.h"
+
+namespace {
+
+constexpr int kProbeIters = 4096;
+constexpr int kProbeForms = 5;
+
+template <int KIND>
+__global__ void k_probe_chains(u64* out, u64 c, u64 d) {
+  u64 x0 = threadIdx.x + 1, x1 = x0 * 3, x2 = x0 * 5, x3 = x0 * 7;
+  u32 a0 = (u32)x0, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3;
+  const u32 cc = (u32)c, dd = (u32)d;
+#pragma unroll 8
+  for (int i = 0; i < kProbeIters; ++i) {
+    if constexpr (KIND == 0) {  // 32-bit multiply-add
+      a0 = a0 * cc + dd;
+      a1 = a1 * cc + dd;
+      a2 = a2 * cc + dd;
+      a3 = a3 * cc + dd;
+    } else if constexpr (KIND == 1) {  // high half of a 32 x 32 product, accumulated
+      a0 += __umulhi(a0, cc);
+      a1 += __umulhi(a1, cc);
+      a2 += __umulhi(a2, cc);
+      a3 += __umulhi(a3, cc);
+    } else if constexpr (KIND == 2) {  // 32 x 32 -> 64 multiply-add
+      x0 += (u64)a0 * cc;
+      x1 += (u64)a1 * cc;
+      x2 += (u64)a2 * cc;
+      x3 += (u64)a3 * cc;
+      a0 ^= (u32)x0;
+      a1 ^= (u32)x1;
+      a2 ^= (u32)x2;
+      a3 ^= (u32)x3;
+    } else if constexpr (KIND == 3) {  // low 64 bits of a 64 x 64 product, plus an add
+      x0 = x0 * c + d;
+      x1 = x1 * c + d;
+      x2 = x2 * c + d;
+      x3 = x3 * c + d;
+    } else {  // high 64 bits of a 64 x 64 product, accumulated
+      x0 += __umul64hi(x0, c);
+      x1 += __umul64hi(x1, c);
+      x2 += __umul64hi(x2, c);
+      x3 += __umul64hi(x3, c);
+    }
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = x0 ^ x1 ^ x2 ^ x3 ^ a0 ^ a1 ^ a2 ^ a3;
+}
+
+template <int KIND>
+double probe_ops_per_s(hc_ctx* ctx, u64* out, int blocks, int threads, cudaEvent_t e0, cudaEvent_t e1) {
+  k_probe_chains<KIND><<<blocks, threads, 0, ctx->stream>>>(out, 0x9e3779b97f4a7c15ull, 12345);  // warm-up
+  HC_CUDA(cudaEventRecord(e0, ctx->stream));
+  k_probe_chains<KIND><<<blocks, threads, 0, ctx->stream>>>(out, 0x9e3779b97f4a7c15ull, 12345);
+  HC_CUDA(cudaEventRecord(e1, ctx->stream));
+  HC_CUDA(cudaEventSynchronize(e1));
+  ctx->launches += 2;
+  float ms = 0;
+  HC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  return (double)blocks * threads * kProbeIters * 4 / (ms * 1e-3);
+}
+
+}  // namespace
+
+extern "C" int hc_int_mul_rates(hc_ctx* ctx, double* rates, int cap) {
+  if (!ctx) return HC_ERR_INVALID;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  try {
+    HC_CHECK(rates && cap >= 2 * kProbeForms, HC_ERR_INVALID, "rates needs 10 entries");
+    int sms = 0, khz = 0;
+    HC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    HC_CUDA(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, ctx->device));
+    const int threads = 256, blocks = sms * 8;
+    BufPtr buf = ctx->buffer((size_t)blocks * threads);
+    HC_CUDA(cudaEventCreate(&e0));
+    HC_CUDA(cudaEventCreate(&e1));
+    double r[kProbeForms];
+    r[0] = probe_ops_per_s<0>(ctx, buf->ptr, blocks, threads, e0, e1);
+    r[1] = probe_ops_per_s<1>(ctx, buf->ptr, blocks, threads, e0, e1);
+    r[2] = probe_ops_per_s<2>(ctx, buf->ptr, blocks, threads, e0, e1);
+    r[3] = probe_ops_per_s<3>(ctx, buf->ptr, blocks, threads, e0, e1);
+    r[4] = probe_ops_per_s<4>(ctx, buf->ptr, blocks, threads, e0, e1);
+    HC_CUDA(cudaGetLastError());
+    for (int i = 0; i < kProbeForms; ++i) {
+      rates[i] = r[i] / sms / (khz * 1e3);  // per SM per clock at the device's maximum clock
+      rates[kProbeForms + i] = r[i];        // thread-operations per second
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->err.clear();
+    return HC_OK;
+  } catch (const HcError& e) {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    ctx->err = e.msg;
+    return e.code;
+  }
+}

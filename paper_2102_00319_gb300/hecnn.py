@@ -43,7 +43,7 @@ EXPORTS = [
     "hc_mul_relin_rescale_batch", "hc_enc_conv2d", "hc_enc_poly_act", "hc_enc_pool", "hc_enc_fc",
     "hc_relin_noalloc", "hc_graph_begin", "hc_graph_end", "hc_graph_launch", "hc_graph_destroy",
     "hc_enc_conv2d_single_batch", "hc_enc_fc_rotsum", "hc_ct_import_batch", "hc_ct_export_batch",
-    "hc_mul_relin_rescale_host", "hc_autotune", "hc_tune_set", "hc_tune_get",
+    "hc_mul_relin_rescale_host", "hc_autotune", "hc_tune_set", "hc_tune_get", "hc_int_mul_rates",
 ]
 
 
@@ -99,6 +99,7 @@ def load(path: str = LIB_PATH):
         "hc_profile_kernel": (c_int, [vp, ctypes.c_char_p, ctypes.POINTER(u64), ctypes.POINTER(dbl),
                                       ctypes.POINTER(u64)]),
         "hc_profile_names": (c_int, [vp, ctypes.c_char_p, ctypes.c_size_t]),
+        "hc_int_mul_rates": (c_int, [vp, ctypes.POINTER(dbl), c_int]),
         "hc_keygen": (c_int, [vp, u64, ctypes.POINTER(ctypes.c_int32), c_int, pp, pp, pp]),
         "hc_sk_destroy": (None, [vp]), "hc_pk_destroy": (None, [vp]), "hc_evk_destroy": (None, [vp]),
         "hc_sk_export": (c_int, [vp, vp, ctypes.POINTER(ctypes.c_int8), ctypes.c_size_t]),
@@ -337,6 +338,17 @@ def hc_profile_names(ctx):
     buf = ctypes.create_string_buffer(8192)
     _check(ctx, load().hc_profile_names(ctx.ptr, buf, 8192))
     return [x for x in buf.value.decode().split(",") if x]
+
+
+INT_MUL_FORMS = ("imad32", "umulhi32", "imad_wide32", "mul_lo64", "mul_hi64")
+
+
+def hc_int_mul_rates(ctx):
+    """{form: (ops per SM per clock at the maximum clock, ops per second)} of
+    the integer-multiply forms, measured on the context's GPU."""
+    r = (ctypes.c_double * 10)()
+    _check(ctx, load().hc_int_mul_rates(ctx.ptr, r, 10))
+    return {f: (r[i], r[5 + i]) for i, f in enumerate(INT_MUL_FORMS)}
 
 
 def hc_keygen(ctx, seed, rot_steps=()):

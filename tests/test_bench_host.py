@@ -82,4 +82,42 @@ def test_reference_arm_prints_the_contract_line():
     assert d["value"] > 0 and d["unit"] == "ops/s" and d["higher_is_better"] is True
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
-    assert d["config"]["workload"] == "deep_n16_l20"
+    assert d["config"] == bench_config_of_default()
+
+
+def test_plain_guards_equal_the_oracle_networks(bench):
+    """The benchmark's FP64 decryption guards compute the same networks as the
+    oracle's plaintext CNNs (batch-packed and single-image deep)."""
+    import numpy as np
+
+    from oracle import cnn
+
+    rng = np.random.default_rng(5)
+    for (hh, k, stride, cout, act) in ((28, 5, 2, 5, (0.0, 0.0, 1.0)), (12, 3, 1, 3, (0.47, 0.50, 0.09)),
+                                       (9, 3, 1, 2, (0.1, 0.2, 0.3))):
+        x = rng.random((4, hh, hh))
+        cw = rng.normal(0, 0.3, (cout, k, k, 1))
+        ho = (hh - k) // stride + 1
+        fw = rng.normal(0, 0.3, (10, (ho // 2) ** 2 * cout))
+        got = bench.plain_batch_network(np, x, cw, stride, act, fw)
+        want = cnn.network(x[..., None], cw, stride, act, fw)
+        assert np.allclose(got, want, rtol=1e-12, atol=1e-12)
+    img = rng.random((28, 28))
+    cw = rng.normal(0, 0.3, (4, 3, 3))
+    act = list(rng.normal(0, 1, 8))
+    fw = rng.normal(0, 0.3, (10, 13 * 13 * 4))
+    assert np.allclose(bench.plain_deep_network(np, img, cw, act, fw), cnn.deep_network(img, cw, act, fw),
+                       rtol=1e-11, atol=1e-11)
+
+
+def test_both_arms_report_one_config(bench):
+    c = bench.bench_config(64, 1)
+    assert (c["workload"], c["N"], c["L"], c["alpha"], c["dnum"], c["batch"]) == ("deep_n16_l20", 65536, 20, 7, 3, 64)
+    assert c["parallelism"] == "single" and bench.bench_config(64, 2)["parallelism"] == "replicas"
+
+
+def bench_config_of_default():
+    spec = importlib.util.spec_from_file_location("bench_cfg", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod.bench_config(64, 1)
