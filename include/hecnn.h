@@ -311,7 +311,13 @@ int hc_relin_noalloc(hc_ctx *ctx, const hc_evk *evk, const hc_ct *x, hc_ct *out)
  *   HC_TUNE_KEY_PRODUCT_Z   item groups of a key-product launch, as a
  *                           multiple (1..64) of the default;
  *   HC_TUNE_MODUP_SPLIT     blocks (1..64) over which a ModUp conversion
- *                           splits its output primes.
+ *                           splits its output primes;
+ *   HC_TUNE_TENSOR_GROUP    sums of tensor products (conv, FC): 0 = one
+ *                           output per thread, g = 1..5 (default 5) = up to
+ *                           g outputs sharing their x operands per thread
+ *                           (a conv position's channels, an FC's classes),
+ *                           each x word loaded once; not timed by
+ *                           hc_autotune.
  * hc_autotune times each knob's candidates on scratch data shaped like
  * `items` ciphertext pairs at the top level (one knob at a time, the others
  * at their current values, three timed launches each after a warm-up) and
@@ -321,7 +327,7 @@ int hc_relin_noalloc(hc_ctx *ctx, const hc_evk *evk, const hc_ct *x, hc_ct *out)
  * microseconds per launch of every candidate.  Not capturable; it
  * synchronises the context stream.
  */
-enum { HC_TUNE_NTT = 0, HC_TUNE_KEY_PRODUCT_Z = 1, HC_TUNE_MODUP_SPLIT = 2 };
+enum { HC_TUNE_NTT = 0, HC_TUNE_KEY_PRODUCT_Z = 1, HC_TUNE_MODUP_SPLIT = 2, HC_TUNE_TENSOR_GROUP = 3 };
 int hc_autotune(hc_ctx *ctx, const hc_evk *evk, int items, char *report, size_t cap);
 int hc_tune_set(hc_ctx *ctx, int knob, int value);
 /* The knob's current value, or a negative error code. */

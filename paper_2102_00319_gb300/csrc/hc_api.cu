@@ -391,6 +391,47 @@ std::vector<hc_ct*> tensor_acc(hc_ctx* ctx, const std::vector<const hc_ct*>& xs,
   for (auto* c : xs) xr.push_back(c->ref());
   for (auto* c : ws) wr.push_back(c->ref());
   for (auto* c : out) orr.push_back(c->ref());
+  // Grouped form: the largest G (up to the tuning knob, at most 5) such that
+  // the outputs split into consecutive runs of G with identical x sequences
+  // (a conv position's channels, an FC layer's classes).
+  const int gmax = std::min(5, ctx->tune.tensor_group);
+  auto same_x = [&](int a, int b) {
+    if (off[a + 1] - off[a] != off[b + 1] - off[b]) return false;
+    return std::equal(xi.begin() + off[a], xi.begin() + off[a + 1], xi.begin() + off[b]);
+  };
+  int G = 0;
+  for (int cand = gmax; cand >= 1 && !G; --cand) {
+    if (nout % cand) continue;
+    bool ok = true;
+    for (int g0 = 0; g0 < nout && ok; g0 += cand)
+      for (int k = 1; k < cand && ok; ++k) ok = same_x(g0, g0 + k);
+    if (ok) G = cand;
+  }
+  if (G >= 1) {
+    const int ngroups = nout / G;
+    std::vector<int> gxi, gwi, goff{0};
+    for (int g = 0; g < ngroups; ++g) {
+      const int o = g * G, nt = off[o + 1] - off[o];
+      for (int t = 0; t < nt; ++t) {
+        gxi.push_back(xi[off[o] + t]);
+        for (int k = 0; k < G; ++k) gwi.push_back(wi[off[o + k] + t]);
+      }
+      goff.push_back((int)gxi.size());
+    }
+    const CtRef* xd = refs_dev(ctx, xr, keep);
+    const CtRef* wd = refs_dev(ctx, wr, keep);
+    const int* gxid = ids_dev(ctx, gxi, keep);
+    const int* gwid = ids_dev(ctx, gwi, keep);
+    for (int g0 = 0; g0 < ngroups; g0 += 65535) {
+      const int m = std::min(65535, ngroups - g0);
+      std::vector<int> off_sub(goff.begin() + g0, goff.begin() + g0 + m + 1);
+      launch_tensor_acc_grouped(
+          ctx, G, refs_dev(ctx, std::vector<CtRef>(orr.begin() + (size_t)g0 * G, orr.begin() + (size_t)(g0 + m) * G), keep),
+          xd, wd, gxid, gwid, ids_dev(ctx, off_sub, keep), m, level + 1,
+          (uint64_t)(off_sub.back() - off_sub.front()) * G);
+    }
+    return out;
+  }
   for (int o0 = 0; o0 < nout; o0 += 65535) {
     const int m = std::min(65535, nout - o0);
     std::vector<int> off_sub(off.begin() + o0, off.begin() + o0 + m + 1);
@@ -1638,6 +1679,10 @@ extern "C" int hc_tune_set(hc_ctx* ctx, int knob, int value) {
         HC_CHECK(value >= 1 && value <= 64, HC_ERR_INVALID, "ModUp split must be 1..64");
         ctx->tune.modup_split = value;
         break;
+      case HC_TUNE_TENSOR_GROUP:
+        HC_CHECK(value >= 0 && value <= 5, HC_ERR_INVALID, "tensor group must be 0..5");
+        ctx->tune.tensor_group = value;
+        break;
       default:
         throw HcError{HC_ERR_INVALID, "unknown tuning knob"};
     }
@@ -1650,6 +1695,7 @@ extern "C" int hc_tune_get(const hc_ctx* ctx, int knob) {
     case HC_TUNE_NTT: return ctx->tune.ntt_variant[ctx->P.log_n];
     case HC_TUNE_KEY_PRODUCT_Z: return ctx->tune.kp_zmul;
     case HC_TUNE_MODUP_SPLIT: return ctx->tune.modup_split;
+    case HC_TUNE_TENSOR_GROUP: return ctx->tune.tensor_group;
     default: return HC_ERR_INVALID;
   }
 }

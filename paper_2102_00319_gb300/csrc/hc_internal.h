@@ -75,6 +75,7 @@ struct HcTune {
   int ntt_variant[17] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
   int kp_zmul = 1;           // key product: item groups in the grid's z, times the default
   int modup_split = 1;       // ModUp conversion: output primes split over this many blocks
+  int tensor_group = 5;      // tensor accumulation: 0 = per output, g = up to g outputs sharing x loads
 };
 
 struct hc_ctx {
@@ -235,6 +236,11 @@ void launch_scalar(hc_ctx* ctx, bool add, const CtRef* out, const CtRef* a, int 
 // out[o] = sum_{t<terms[o]} x[xi[o0+t]] (x) w[wi[o0+t]], o0 = off[o].
 // out[z] = a[z] (x) b[z], degree-1 operands, one term per output.
 void launch_tensor_pair(hc_ctx* ctx, const CtRef* out, const CtRef* a, const CtRef* b, int items, int nl);
+// Grouped form: groups of G (1..5) outputs sharing one x sequence,
+//   out[g G + k] = sum_{t in [off[g], off[g+1])} x[xi[t]] (x) w[wi[t G + k]],
+// the same words as the per-output form with the x operands loaded once.
+void launch_tensor_acc_grouped(hc_ctx* ctx, int G, const CtRef* out, const CtRef* x, const CtRef* w, const int* xi,
+                               const int* wi, const int* off, int ngroups, int nl, uint64_t terms);
 // `terms` (the sum of the outputs' term counts) only labels the launch's
 // work for profiling: one unit per (term, limb).
 void launch_tensor_acc(hc_ctx* ctx, const CtRef* out, const CtRef* x, const CtRef* w,

@@ -180,6 +180,95 @@ __global__ void k_tensor_acc(const CtRef* out, const CtRef* x, const CtRef* w, c
   O.p[2 * O.stride + lo] = reduce128_est(a2, md);
 }
 
+// G outputs that share one sequence of x operands (the output channels of a
+// conv position, the classes of an FC layer):
+//   out[g G + k] = sum_{t in [off[g], off[g+1])} x[xi[t]] (x) w[wi[t G + k]],
+// accumulated like k_tensor_acc (Karatsuba per term, 128-bit sums folded every
+// `chunk` terms).  Each x word is loaded once for its G products, which cuts
+// the operand loads per term from 4 to 2 + 2/G words.  The operands' limb
+// pointers are staged in shared memory a tile of terms at a time by the
+// whole block (one group and one limb per block), so the term loop issues
+// only independent data loads instead of chains of dependent pointer loads.
+template <int G>
+__global__ void __launch_bounds__(kT, G >= 4 ? 2 : 3) k_tensor_acc_g(const CtRef* out, const CtRef* x, const CtRef* w,
+                                                     const int* xi, const int* wi, const int* off, int chunk,
+                                                     Tables T) {
+  constexpr int TT = 32;  // terms per staged tile
+  __shared__ const u64* s_xp[TT];
+  __shared__ u64 s_xs[TT];
+  __shared__ const u64* s_wp[TT][G];
+  __shared__ u64 s_wstr[TT][G];
+  const int n = 1 << T.log_n;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;  // n is a multiple of the block size
+  const int g = blockIdx.y, l = blockIdx.z;
+  const DMod md = T.mods[l];
+  const size_t lofs = (size_t)l * n;
+  U128 a0[G], sm[G], a2[G];
+#pragma unroll
+  for (int k = 0; k < G; ++k) a0[k] = sm[k] = a2[k] = U128{0, 0};
+  auto middle = [](const U128& s, const U128& x0, const U128& x2) {  // s - x0 - x2 in 128 bits
+    U128 m = s;
+    u64 t = m.lo - x0.lo;
+    m.hi -= x0.hi + (m.lo < x0.lo);
+    m.lo = t;
+    t = m.lo - x2.lo;
+    m.hi -= x2.hi + (m.lo < x2.lo);
+    m.lo = t;
+    return m;
+  };
+  const int t0 = off[g], t1 = off[g + 1];
+  int cnt = 0;
+  for (int tb = t0; tb < t1; tb += TT) {
+    const int nt = min(TT, t1 - tb);
+    __syncthreads();  // the previous tile's pointers are no longer read
+    for (int i = threadIdx.x; i < nt * (G + 1); i += blockDim.x) {
+      const int t = i / (G + 1), k = i - t * (G + 1);
+      if (k == 0) {
+        const CtRef X = x[xi[tb + t]];
+        s_xp[t] = X.p + lofs;
+        s_xs[t] = X.stride;
+      } else {
+        const CtRef Wt = w[wi[(size_t)(tb + t) * G + (k - 1)]];
+        s_wp[t][k - 1] = Wt.p + lofs;
+        s_wstr[t][k - 1] = Wt.stride;
+      }
+    }
+    __syncthreads();
+    for (int t = 0; t < nt; ++t) {
+      const u64* xp = s_xp[t] + c;
+      const u64 x0 = xp[0], x1 = xp[s_xs[t]];
+      const u64 xsum = x0 + x1;
+#pragma unroll
+      for (int k = 0; k < G; ++k) {
+        const u64* wp = s_wp[t][k] + c;
+        const u64 w0 = wp[0], w1 = wp[s_wstr[t][k]];
+        mac(a0[k], x0, w0);
+        mac(sm[k], xsum, w0 + w1);
+        mac(a2[k], x1, w1);
+      }
+      if (++cnt == chunk) {
+        cnt = 0;
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+          const u64 r1 = reduce128_est(middle(sm[k], a0[k], a2[k]), md);
+          const u64 r0 = reduce128_est(a0[k], md), r2 = reduce128_est(a2[k], md);
+          a0[k] = U128{r0, 0};
+          a2[k] = U128{r2, 0};
+          sm[k] = U128{r0 + r1 + r2, 0};
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < G; ++k) {
+    const CtRef O = out[(size_t)g * G + k];
+    const size_t lo = lofs + c;
+    O.p[lo] = reduce128_est(a0[k], md);
+    O.p[O.stride + lo] = reduce128_est(middle(sm[k], a0[k], a2[k]), md);
+    O.p[2 * O.stride + lo] = reduce128_est(a2[k], md);
+  }
+}
+
 // out[z] = a[z] (x) b[z] (one term per output): d0 = a0 b0, d2 = a1 b1 and
 // d1 = (a0 + a1)(b0 + b1) - d0 - d2 in 128 bits (three products instead of
 // four; a0 + a1 < 2q keeps the product below 2^124 and the difference is the
@@ -491,11 +580,11 @@ void launch_tensor_pair(hc_ctx* ctx, const CtRef* out, const CtRef* a, const CtR
   check_launch(ctx);
 }
 
-void launch_tensor_acc(hc_ctx* ctx, const CtRef* out, const CtRef* x, const CtRef* w, const int* xi,
-                       const int* wi, const int* off, int nout, int nl, uint64_t terms) {
-  if (nout <= 0) return;
-  // the Karatsuba sum gains (x0 + x1)(w0 + w1) < 4 qmax^2 per term (on top
-  // of a folded residue below 3 qmax): fold before 2^128
+namespace {
+// The fold interval of the lazy 128-bit sums: the Karatsuba sum gains
+// (x0 + x1)(w0 + w1) < 4 qmax^2 per term (on top of a folded residue below
+// 3 qmax), so fold before 2^128.
+int tensor_fold_chunk(hc_ctx* ctx, int nl) {
   u64 qmax = 0;
   for (int i = 0; i < nl; ++i) qmax = ctx->P.chain[i] > qmax ? ctx->P.chain[i] : qmax;
   unsigned __int128 sq = (unsigned __int128)qmax * qmax;
@@ -503,6 +592,35 @@ void launch_tensor_acc(hc_ctx* ctx, const CtRef* out, const CtRef* x, const CtRe
   unsigned __int128 per = lim / (4 * sq);
   int chunk = per > 1024 ? 1024 : (int)per - 1;
   HC_CHECK(chunk >= 1, HC_ERR_INVALID, "primes too large for lazy accumulation");
+  return chunk;
+}
+}  // namespace
+
+void launch_tensor_acc_grouped(hc_ctx* ctx, int G, const CtRef* out, const CtRef* x, const CtRef* w, const int* xi,
+                               const int* wi, const int* off, int ngroups, int nl, uint64_t terms) {
+  if (ngroups <= 0) return;
+  HC_CHECK(G >= 1 && G <= 5, HC_ERR_INVALID, "tensor group size must be 1..5");
+  HC_CHECK(ngroups <= 65535, HC_ERR_INVALID, "too many output groups in one launch");
+  HC_CHECK(ctx->P.n % kT == 0, HC_ERR_INVALID, "ring degree below the block size");
+  const int chunk = tensor_fold_chunk(ctx, nl);
+  const dim3 grid((unsigned)(ctx->P.n / kT), (unsigned)ngroups, (unsigned)nl);
+  {
+    ProfScope prof_(ctx, "k_tensor_acc", terms * nl);  // units: (term, limb) pairs
+    switch (G) {
+      case 1: k_tensor_acc_g<1><<<grid, kT, 0, ctx->stream>>>(out, x, w, xi, wi, off, chunk, ctx->tab); break;
+      case 2: k_tensor_acc_g<2><<<grid, kT, 0, ctx->stream>>>(out, x, w, xi, wi, off, chunk, ctx->tab); break;
+      case 3: k_tensor_acc_g<3><<<grid, kT, 0, ctx->stream>>>(out, x, w, xi, wi, off, chunk, ctx->tab); break;
+      case 4: k_tensor_acc_g<4><<<grid, kT, 0, ctx->stream>>>(out, x, w, xi, wi, off, chunk, ctx->tab); break;
+      default: k_tensor_acc_g<5><<<grid, kT, 0, ctx->stream>>>(out, x, w, xi, wi, off, chunk, ctx->tab); break;
+    }
+  }
+  LAUNCH_DONE(ctx);
+}
+
+void launch_tensor_acc(hc_ctx* ctx, const CtRef* out, const CtRef* x, const CtRef* w, const int* xi,
+                       const int* wi, const int* off, int nout, int nl, uint64_t terms) {
+  if (nout <= 0) return;
+  const int chunk = tensor_fold_chunk(ctx, nl);
   HC_CHECK(nout <= 65535, HC_ERR_INVALID, "too many outputs in one launch");
     {
       ProfScope prof_(ctx, "k_tensor_acc", terms * nl);  // units: (term, limb) pairs

@@ -26,6 +26,7 @@ ERRORS = {
 HC_TUNE_NTT = 0
 HC_TUNE_KEY_PRODUCT_Z = 1
 HC_TUNE_MODUP_SPLIT = 2
+HC_TUNE_TENSOR_GROUP = 3
 HC_PACK_BATCH = 0
 HC_PACK_SINGLE = 1
 HC_PACK_SINGLE_HOISTED = 2

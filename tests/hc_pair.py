@@ -63,3 +63,62 @@ class Pair:
     def decrypt_oracle(self, octx):
         d = ckks.decrypt(self.op, self.o_sk, octx)
         return encoding.decode(d.m, self.op.q[: octx.level + 1], self.op.N, octx.scale)
+
+
+# ---- oracle work in spawned worker processes ----------------------------
+# (spawn, never fork, so that the children inherit no CUDA state)
+_W = {}
+
+
+def _oracle_worker_init(param_args, pk_b, pk_a):
+    import os
+
+    os.environ["OMP_NUM_THREADS"] = "1"
+    _W["op"] = ckks.Params(*param_args)
+    _W["pk"] = ckks.PublicKey(pk_b, pk_a)
+
+
+def oracle_tensor_partial(job):
+    """sum_k x_k (x) w_k by the oracle over the terms of `job`, each term a
+    pair of (integer-plaintext seed, bound, level, encryption seed, nonce)
+    specs encrypted by the oracle itself."""
+    from paper_2102_00319_gb300 import workloads as W
+
+    op, pk = _W["op"], _W["pk"]
+    acc = None
+    for xs, ws in job:
+        cts = []
+        for (mseed, bound, level, eseed, nonce) in (xs, ws):
+            m = W.int_plaintext(mseed, op.N, bound)
+            cts.append(ckks.encrypt(op, pk, ckks.plaintext_from_ints(op, m, level, op.scale), eseed, nonce))
+        t = ckks.mul(op, cts[0], cts[1])
+        if acc is None:
+            acc = t.c.copy()
+        else:
+            qs = ckks.primes_of(op, range(t.level + 1))
+            for k in range(3):
+                acc[k] = ckks.padd(acc[k], t.c[k], qs)
+    return acc
+
+
+def oracle_tensor_sum_parallel(op, o_pk, terms, workers=None):
+    """The oracle's degree-2 sum of tensor products over `terms` (see
+    oracle_tensor_partial), split over spawned worker processes; the partial
+    sums are added modulo each prime (exact)."""
+    import multiprocessing as mp
+    import os
+
+    workers = workers or max(1, os.cpu_count() or 1)
+    chunks = [terms[i::workers * 2] for i in range(workers * 2)]
+    chunks = [c for c in chunks if c]
+    ctxm = mp.get_context("spawn")
+    args = ((op.log_n, list(op.q_bits), list(op.p_bits), op.log2_scale), o_pk.b, o_pk.a)
+    with ctxm.Pool(workers, initializer=_oracle_worker_init, initargs=args) as pool:
+        parts = pool.map(oracle_tensor_partial, chunks)
+    level = terms[0][0][2]
+    qs = ckks.primes_of(op, range(level + 1))
+    acc = parts[0]
+    for p in parts[1:]:
+        for k in range(3):
+            acc[k] = ckks.padd(acc[k], p[k], qs)
+    return ckks.Ciphertext(acc, level, op.scale * op.scale)

@@ -162,3 +162,37 @@ def test_fc_long_sum_folds_bit_exact(net):
     want = cnn.enc_fc(op, p.o_evk, [o for _, o in xs], [o for _, o in ws], n_out)
     for g, o in zip(got, want):
         p.assert_same(g, o, "fc 150 terms")
+
+
+def test_tensor_group_choices_bit_identical(net):
+    """Every HC_TUNE_TENSOR_GROUP value (0: one output per thread; 1..5: up to
+    that many outputs sharing their x loads) gives the oracle's words for the
+    conv (3 channels per position) and an FC with 150 terms over 2 classes
+    (several staged tiles of terms, a ragged last tile, folds of the 128-bit
+    sums)."""
+    p = net["p"]
+    op, ctx, evk = p.op, p.ctx, p.g_evk
+    gx = [g for g, _ in net["xs"]]
+    gw = [g for g, _ in net["ws"]]
+    oy = cnn.enc_conv2d_batch(op, p.o_evk, [o for _, o in net["xs"]], net["H"], net["W"], 1,
+                              [o for _, o in net["ws"]], net["cout"], net["k"], net["k"], net["s"])
+    n_in, n_out = 150, 2
+    fx = [p.encrypt_values(W.slot_values(700 + i, op.K), level=2, nonce=5000 + i) for i in range(n_in)]
+    fwc = [p.encrypt_values(W.slot_values(900 + i, op.K), level=2, nonce=6000 + i) for i in range(n_in * n_out)]
+    of = cnn.enc_fc(op, p.o_evk, [o for _, o in fx], [o for _, o in fwc], n_out)
+    default = H.hc_tune_get(ctx, H.HC_TUNE_TENSOR_GROUP)
+    assert default == 5
+    try:
+        for v in range(6):
+            H.hc_tune_set(ctx, H.HC_TUNE_TENSOR_GROUP, v)
+            gy = H.hc_enc_conv2d(ctx, evk, H.HC_PACK_BATCH, gx, net["H"], net["W"], 1, gw, net["cout"], net["k"],
+                                 net["k"], net["s"])
+            for i, (g, o) in enumerate(zip(gy, oy)):
+                p.assert_same(g, o, "group %d conv %d" % (v, i))
+            gf = H.hc_enc_fc(ctx, evk, H.HC_PACK_BATCH, [g for g, _ in fx], [g for g, _ in fwc], n_out)
+            for i, (g, o) in enumerate(zip(gf, of)):
+                p.assert_same(g, o, "group %d fc %d" % (v, i))
+    finally:
+        H.hc_tune_set(ctx, H.HC_TUNE_TENSOR_GROUP, default)
+    with pytest.raises(H.HcError):
+        H.hc_tune_set(ctx, H.HC_TUNE_TENSOR_GROUP, 6)
