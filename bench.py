@@ -544,6 +544,59 @@ def cnn_leg(args, H, W, np, torch, local, profile_only=False):
     }
 
 
+def cnn_sharded_leg(H, W, np, torch, local, rank, world):
+    """The N = 2^14 batch-packed CNN split over the ranks by output channel
+    (paper_2102_00319_gb300.sharding): each rank runs conv -> x^2 -> pool and
+    the FC's partial sums for its channels, the partial ciphertexts' words
+    are all-gathered (NCCL) and summed by the library's modular add, then
+    relinearised and rescaled.  Every rank uses the same keys and inputs
+    (one network); images/s = 8192 / the slowest rank's time."""
+    import torch.distributed as dist
+
+    from paper_2102_00319_gb300 import sharding as S
+
+    ps, c = W.BATCH_N14, W.CNN_BATCH
+    params = H.hc_params_create(ps.log_n, list(ps.q_bits), list(ps.p_bits), ps.log2_scale)
+    ctx = H.hc_ctx_create(params, local, torch.cuda.current_stream().cuda_stream)
+    K, seed, scale = ctx.n // 2, W.MASTER_SEED + 2, 2.0 ** ps.log2_scale
+    sk, pk, evk = H.hc_keygen(ctx, seed)
+    plan = S.ShardPlan(H=c["H"], W=c["W"], cin=1, cout=c["cout"], kh=c["k"], kw=c["k"], stride=c["stride"],
+                       n_out=c["n_out"], world=world)
+    imgs = W.images(seed + 20, K, c["H"], c["W"])
+    cw = W.conv_weights(seed + 21, c["cout"], c["k"], c["k"])
+    fw = W.fc_weights(seed + 22, c["n_out"], plan.n_in)
+
+    def const_ct(v, nonce):
+        m = np.zeros(ctx.n, dtype=np.int64)
+        m[0] = int(np.round(v * scale))
+        return H.hc_encrypt(ctx, pk, H.hc_pt_from_coeffs(ctx, m, ctx.L, scale), seed + 5, nonce)
+
+    xs = [H.hc_encrypt(ctx, pk, H.hc_encode(ctx, imgs[:, h, w], scale, ctx.L), seed + 5, h * c["W"] + w)
+          for h in range(c["H"]) for w in range(c["W"])]
+    ws = [const_ct(cw[co, a, b, 0], 1000 + (co * c["k"] + a) * c["k"] + b)
+          for co in range(c["cout"]) for a in range(c["k"]) for b in range(c["k"])]
+    fws = [const_ct(fw[r, i], 2000 + r * plan.n_in + i) for r in range(c["n_out"]) for i in range(plan.n_in)]
+    dev = torch.device("cuda", local)
+
+    def run():
+        return S.sharded_cnn(H, ctx, evk, plan, rank, xs, ws, fws, c["act"], device=dev)
+
+    run()
+    H.hc_sync(ctx)
+    dist.barrier()
+    t0 = time.perf_counter()
+    z = run()
+    H.hc_sync(ctx)
+    t = max_over_ranks(time.perf_counter() - t0, device="cuda")
+    logits = np.stack([H.hc_decode(ctx, H.hc_decrypt(ctx, sk, u)).real for u in z], axis=1)
+    err = float(np.max(np.abs(logits - plain_batch_network(np, imgs, cw, c["stride"], c["act"], fw))))
+    assert err < 2.0 ** -15, err
+    return {"workload": "batch_n14 CNN sharded by output channel over %d ranks (all-gather of the partial FC"
+                        " ciphertexts, modular add in the library)" % world,
+            "images_per_s": K / t, "ms": 1000 * t, "channels_per_rank": [len(plan.channels(r)) for r in range(world)],
+            "max_logit_error_vs_fp64": err}
+
+
 def uneven_leg(H, W, np, torch, local):
     """64 independent single-ciphertext inferences (8x8 image, 3x3 conv by
     rotations, x^2) at N = 2^13 / 2^14 / 2^15 and 3..12 levels, run four ways:
@@ -1020,6 +1073,7 @@ def run_gpu(args, rank, world, local):
         e2e_err = float(np.max(np.abs(H.hc_decode(ctx, H.hc_decrypt(ctx, sk, back)) - za * zb)))
         assert e2e_err < 2.0 ** -15, "host-to-host result decrypts wrong (max error %g)" % e2e_err
 
+    sharded = cnn_sharded_leg(H, W, np, torch, local, rank, world) if world > 1 and not args.no_cnn else None
     if rank != 0:
         return
     # ---------------- roofline of the dominant kernel
@@ -1074,13 +1128,18 @@ def run_gpu(args, rank, world, local):
                    "form": "hc_mul, hc_relin, hc_rescale per pair (unfused relin and rescale, one pair per call)"},
         "check": {"max_slot_error": err},
     }
-    if not args.no_cnn:
+    if sharded is not None:
+        line["cnn_sharded"] = sharded
+    # the single-GPU legs run at N = 1 only (at N > 1 the GPUs are held for the
+    # replicated metric and the sharded CNN)
+    single = world == 1
+    if not args.no_cnn and single:
         line["cnn"] = cnn_leg(args, H, W, np, torch, local)
-    if not args.no_uneven:
+    if not args.no_uneven and single:
         line["uneven"] = uneven_leg(H, W, np, torch, local)
-    if not args.no_serve:
+    if not args.no_serve and single:
         line["serving"] = serving_leg(args, H, W, np, torch, local)
-    if not args.no_deep:
+    if not args.no_deep and single:
         line["deep"] = deep_leg(H, W, np, torch, local)
     if args.paper_shape:
         line["paper_shape"] = paper_shape_leg(H, W, np, torch, local)

@@ -304,10 +304,18 @@ int hc_relin_noalloc(hc_ctx *ctx, const hc_evk *evk, const hc_ct *x, hc_ct *out)
  * Tile and launch shapes picked by measurement.  The paper has no
  * counterpart (its CPU code has no tiles); results are bit-identical for
  * every choice, only the speed changes.  Knobs:
- *   HC_TUNE_NTT             NTT block size for the context's ring degree:
+ *   HC_TUNE_NTT             NTT form for the context's ring degree:
+ *                           two passes through global memory with blocks of
  *                           0 = 256 threads (tiles of 16 columns / rows at
  *                           N = 2^16), 1 = 128 threads (tiles of 8, the
  *                           default), 2 = 64 threads (tiles of 4; N >= 2^13);
+ *                           or one pass (N >= 2^13): each limb held in the
+ *                           shared memory of a cluster of N / 2^14 CTAs (one
+ *                           CTA up to 2^14), the stages across CTAs through
+ *                           distributed shared memory, register rounds of up
+ *                           to 5 (3) or 4 (4) stages.  The transforms that
+ *                           carry the fused relinearise + rescale tail stay
+ *                           two-pass (128-thread tiles under 3 and 4);
  *   HC_TUNE_KEY_PRODUCT_Z   item groups of a key-product launch, as a
  *                           multiple (1..64) of the default;
  *   HC_TUNE_MODUP_SPLIT     blocks (1..64) over which a ModUp conversion
@@ -437,6 +445,24 @@ int hc_enc_pool(hc_ctx *ctx, const hc_evk *evk, hc_packing packing, const hc_ct 
  */
 int hc_enc_fc(hc_ctx *ctx, const hc_evk *evk, hc_packing packing, const hc_ct *const *x, int n_in,
               const hc_ct *const *w, const hc_ct *const *bias, int n_out, hc_ct **y);
+/*
+ * The FC layer's sums of tensor products before relinearisation:
+ * y[r] = sum_k x_k (x) w[r*n_in + k], degree 2, at the activations' level,
+ * scale(x) * scale(w) (HC_PACK_BATCH only).  For the FC split over the
+ * filters that the paper's multi-threading assigns to separate threads
+ * (Sec. "Parallelization using multi-threading"): each part covers the
+ * activations of its own filters; the parts are added (hc_add, exact
+ * modular addition) and the sum relinearised and rescaled once (hc_relin,
+ * hc_rescale), which gives the words of hc_enc_fc over all inputs.
+ */
+int hc_enc_fc_partial(hc_ctx *ctx, hc_packing packing, const hc_ct *const *x, int n_in, const hc_ct *const *w,
+                      int n_out, hc_ct **y);
+/* n relinearisations each followed by a rescale, batched into one pass of
+ * each kernel with the rescale fused into ModDown's transform: the second
+ * half of the FC (and conv) outputs' CT-CT mult (Eq. 3).  d[k]: degree-2
+ * ciphertexts at one level >= 1; outs[k] = rescale(relin(d[k])), the same
+ * words as hc_rescale(hc_relin(d[k])) and as the tail of hc_enc_fc. */
+int hc_relin_rescale_batch(hc_ctx *ctx, const hc_evk *evk, const hc_ct *const *d, int n, hc_ct **outs);
 
 /*
  * Fully connected layer on single-ciphertext activations: x[c] (c < C)

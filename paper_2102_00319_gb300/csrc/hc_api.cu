@@ -1667,8 +1667,8 @@ extern "C" int hc_tune_set(hc_ctx* ctx, int knob, int value) {
   return guard(ctx, [&] {
     switch (knob) {
       case HC_TUNE_NTT:
-        HC_CHECK(value >= 0 && value <= (ctx->P.log_n >= 13 ? 2 : 1), HC_ERR_INVALID,
-                 "NTT variant must be 0, 1 (or 2 for N >= 2^13)");
+        HC_CHECK(value >= 0 && value <= (ctx->P.log_n >= 13 ? 4 : 1), HC_ERR_INVALID,
+                 "NTT variant must be 0, 1 (or 2..4 for N >= 2^13)");
         ctx->tune.ntt_variant[ctx->P.log_n] = value;
         break;
       case HC_TUNE_KEY_PRODUCT_Z:
@@ -1747,7 +1747,7 @@ extern "C" int hc_autotune(hc_ctx* ctx, const hc_evk* evk, int items, char* repo
       double best = 1e300, inc_us = 1e300;
       int pick = incumbent;
       std::string t;
-      for (int v = 0; v <= (ctx->P.log_n >= 13 ? 2 : 1); ++v) {
+      for (int v = 0; v <= (ctx->P.log_n >= 13 ? 4 : 1); ++v) {
         ctx->tune.ntt_variant[ctx->P.log_n] = v;
         const double us = time_us([&] {
           launch_ntt(ctx, cs, m, false);
@@ -2284,38 +2284,48 @@ extern "C" int hc_enc_pool(hc_ctx* ctx, const hc_evk* evk, hc_packing packing, c
   });
 }
 
+namespace {
+// Degree-2 sums of the FC layer: d_r = sum_k x_k (x) w_{r n_in + k}, the
+// weights viewed at the activations' level.  Caller frees the results.
+std::vector<hc_ct*> fc_tensor_sums(hc_ctx* ctx, const hc_ct* const* x, int n_in, const hc_ct* const* w, int n_out) {
+  std::vector<const hc_ct*> xs(x, x + n_in);
+  const int level = xs[0]->level;
+  for (auto* c : xs) {
+    check_ct(ctx, c);
+    HC_CHECK(c->level == level && c->degree == 1, HC_ERR_LEVEL_MISMATCH, "inputs at different levels");
+    check_scales(c->scale, xs[0]->scale);
+  }
+  std::vector<const hc_ct*> ws;
+  std::vector<hc_ct*> views;
+  for (int i = 0; i < n_in * n_out; ++i) {
+    check_ct(ctx, w[i]);
+    HC_CHECK(w[i]->level >= level && w[i]->degree == 1, HC_ERR_LEVEL_MISMATCH, "weight below the activations");
+    check_scales(w[i]->scale, w[0]->scale);
+    views.push_back(new hc_ct{ctx, w[i]->buf, w[i]->data, w[i]->stride, level, 1, w[i]->scale});
+    ws.push_back(views.back());
+  }
+  std::vector<int> xi, wi, off{0};
+  for (int r = 0; r < n_out; ++r) {
+    for (int k = 0; k < n_in; ++k) {
+      xi.push_back(k);
+      wi.push_back(r * n_in + k);
+    }
+    off.push_back((int)xi.size());
+  }
+  std::vector<hc_ct*> d = tensor_acc(ctx, xs, ws, xi, wi, off, level, xs[0]->scale * ws[0]->scale);
+  free_all(views);
+  return d;
+}
+}  // namespace
+
 extern "C" int hc_enc_fc(hc_ctx* ctx, const hc_evk* evk, hc_packing packing, const hc_ct* const* x, int n_in,
                          const hc_ct* const* w, const hc_ct* const* bias, int n_out, hc_ct** y) {
   if (!ctx) return HC_ERR_INVALID;
   return guard(ctx, [&] {
     HC_CHECK(packing == HC_PACK_BATCH, HC_ERR_INVALID, "fc supports batch packing");
     HC_CHECK(evk && x && w && y && n_in > 0 && n_out > 0, HC_ERR_INVALID, "bad arguments");
-    std::vector<const hc_ct*> xs(x, x + n_in);
-    const int level = xs[0]->level;
-    for (auto* c : xs) {
-      check_ct(ctx, c);
-      HC_CHECK(c->level == level && c->degree == 1, HC_ERR_LEVEL_MISMATCH, "inputs at different levels");
-      check_scales(c->scale, xs[0]->scale);
-    }
-    HC_CHECK(level >= 1, HC_ERR_DEPTH, "no level left");
-    std::vector<const hc_ct*> ws;
-    std::vector<hc_ct*> views;
-    for (int i = 0; i < n_in * n_out; ++i) {
-      check_ct(ctx, w[i]);
-      HC_CHECK(w[i]->level >= level && w[i]->degree == 1, HC_ERR_LEVEL_MISMATCH, "weight below the activations");
-      check_scales(w[i]->scale, w[0]->scale);
-      views.push_back(new hc_ct{ctx, w[i]->buf, w[i]->data, w[i]->stride, level, 1, w[i]->scale});
-      ws.push_back(views.back());
-    }
-    std::vector<int> xi, wi, off{0};
-    for (int r = 0; r < n_out; ++r) {
-      for (int k = 0; k < n_in; ++k) {
-        xi.push_back(k);
-        wi.push_back(r * n_in + k);
-      }
-      off.push_back((int)xi.size());
-    }
-    std::vector<hc_ct*> d = tensor_acc(ctx, xs, ws, xi, wi, off, level, xs[0]->scale * ws[0]->scale);
+    HC_CHECK(x[0] && x[0]->level >= 1, HC_ERR_DEPTH, "no level left");
+    std::vector<hc_ct*> d = fc_tensor_sums(ctx, x, n_in, w, n_out);
     std::vector<const hc_ct*> bs;
     if (bias)
       for (int r = 0; r < n_out; ++r) {
@@ -2324,8 +2334,34 @@ extern "C" int hc_enc_fc(hc_ctx* ctx, const hc_evk* evk, hc_packing packing, con
       }
     std::vector<hc_ct*> r = relin_rescale(ctx, evk, d, bias ? &bs : nullptr);
     free_all(d);
-    free_all(views);
     for (int i = 0; i < n_out; ++i) y[i] = r[i];
+  });
+}
+
+extern "C" int hc_relin_rescale_batch(hc_ctx* ctx, const hc_evk* evk, const hc_ct* const* d, int n, hc_ct** outs) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    HC_CHECK(evk && d && outs && n > 0, HC_ERR_INVALID, "bad arguments");
+    std::vector<hc_ct*> in;
+    for (int i = 0; i < n; ++i) {
+      check_ct(ctx, d[i]);
+      HC_CHECK(d[i]->level == d[0]->level, HC_ERR_LEVEL_MISMATCH, "batch mixes levels");
+      in.push_back(const_cast<hc_ct*>(d[i]));  // read only
+    }
+    std::vector<hc_ct*> r = relin_rescale(ctx, evk, in, nullptr);
+    for (int i = 0; i < n; ++i) outs[i] = r[i];
+  });
+}
+
+extern "C" int hc_enc_fc_partial(hc_ctx* ctx, hc_packing packing, const hc_ct* const* x, int n_in,
+                                 const hc_ct* const* w, int n_out, hc_ct** y) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    HC_CHECK(packing == HC_PACK_BATCH, HC_ERR_INVALID, "fc supports batch packing");
+    HC_CHECK(x && w && y && n_in > 0 && n_out > 0, HC_ERR_INVALID, "bad arguments");
+    HC_CHECK(x[0], HC_ERR_INVALID, "null input");
+    std::vector<hc_ct*> d = fc_tensor_sums(ctx, x, n_in, w, n_out);
+    for (int i = 0; i < n_out; ++i) y[i] = d[i];
   });
 }
 

@@ -22,6 +22,8 @@
 // short-distance stages), with one shared-memory exchange between them.
 // The inverse runs the rounds and the passes in the opposite order.  Each
 // pass reads and writes each limb once.
+#include <cooperative_groups.h>
+
 #include "hc_internal.h"
 
 namespace {
@@ -399,7 +401,7 @@ void launch_pass_cols(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, cons
   if constexpr (LOGN >= 13) {
     if (v == 2) return launch_pass_cols_t<INV, LOGN, 6>(ctx, s, items, ylimbs, in, scale, fuse);
   }
-  if (v >= 1)
+  if (v == 1 || v >= 3)
     launch_pass_cols_t<INV, LOGN, 7>(ctx, s, items, ylimbs, in, scale, fuse);
   else
     launch_pass_cols_t<INV, LOGN, 8>(ctx, s, items, ylimbs, in, scale, fuse);
@@ -412,15 +414,248 @@ void launch_pass_rows(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, cons
   if constexpr (LOGN >= 13) {
     if (v == 2) return launch_pass_rows_t<INV, LOGN, 6>(ctx, s, items, ylimbs, in, fuse);
   }
-  if (v >= 1)
+  if (v == 1 || v >= 3)
     launch_pass_rows_t<INV, LOGN, 7>(ctx, s, items, ylimbs, in, fuse);
   else
     launch_pass_rows_t<INV, LOGN, 8>(ctx, s, items, ylimbs, in, fuse);
 }
 
+// ---------------------------------------------------------------------------
+// Single-pass transform: one limb of N = CL 2^LQ points held in the shared
+// memory of a cluster of CL CTAs (2^LQ = 16384 words, 128 KiB, per CTA), so
+// that each limb is read from and written to global memory once.
+//
+// Forward (stage st: half distance N / 2^{st+1}): the first C = log2 CL
+// stages pair points of different CTAs.  CTA r takes the offsets j in
+// [r Q / CL, (r+1) Q / CL) of every CTA's chunk (Q = 2^LQ), loads the CL
+// points j + k Q straight from global memory, runs stages 0..C-1 on them in
+// registers and stores point k into CTA k's shared memory (distributed
+// shared memory) at local index j.  After a cluster barrier every CTA holds
+// its contiguous chunk [r Q, (r+1) Q), whose remaining LQ stages stay
+// inside it: register rounds of 5 or 4 stages between shared-memory
+// exchanges, then a coalesced copy to global memory.
+// Inverse: the same in reverse: the chunk's LQ stages first, a cluster
+// barrier, then stages C-1..0 across the CTAs with distributed-shared-memory
+// loads and the results (times N^{-1} unless the caller folds it) written to
+// global memory; a last cluster barrier keeps each CTA's shared memory alive
+// until the others have read it.  Cluster barriers are hardware barriers
+// (no spin loop).  With CL = 1 (N <= 2^14) the chunk is the whole limb.
+// Shared-memory words are padded by one per 16 (index i at i + i / 16), so
+// the rounds with contiguous points per thread do not conflict on banks.
+constexpr int kOnePassThreadsLog = 9;  // 512 threads per CTA
+
+__device__ __forceinline__ u32 opad(u32 i) { return i + (i >> 4); }
+
+// Local rounds of the chunk's LQ stages, forward order: round i covers
+// stages S0(i) .. S0(i) + K(i) - 1.  WIDE = 1: rounds of up to 5 stages (32
+// points per thread, three rounds); WIDE = 0: up to 4 (16 points, four).
+template <int LQ, int WIDE>
+struct OnePassRounds;
+template <>
+struct OnePassRounds<14, 1> {
+  static constexpr int n = 3;
+  static constexpr int s0[4] = {0, 5, 10, 14};
+  static constexpr int k[4] = {5, 5, 4, 0};
+};
+template <>
+struct OnePassRounds<14, 0> {
+  static constexpr int n = 4;
+  static constexpr int s0[4] = {0, 4, 8, 11};
+  static constexpr int k[4] = {4, 4, 3, 3};
+};
+template <>
+struct OnePassRounds<13, 1> {
+  static constexpr int n = 3;
+  static constexpr int s0[4] = {0, 5, 9, 13};
+  static constexpr int k[4] = {5, 4, 4, 0};
+};
+template <>
+struct OnePassRounds<13, 0> {
+  static constexpr int n = 4;
+  static constexpr int s0[4] = {0, 4, 7, 10};
+  static constexpr int k[4] = {4, 3, 3, 3};
+};
+
+// One register round of local stages S0..S0+K-1 over the CTA's chunk in
+// shared memory (forward, or inverse in reverse stage order).  Group g of
+// 2^K points: local index ((g >> LS) << (LS + K)) + (g & (2^LS - 1)) + (m << LS),
+// LS = LQ - S0 - K; its global index adds r 2^LQ.
+template <bool INV, int LOGN, int LQ, int S0, int K>
+__device__ __forceinline__ void onepass_round(u64* sm, u32 r, const ulonglong2* tw, u64 q) {
+  if constexpr (K > 0) {
+    constexpr int C = LOGN - LQ, LS = LQ - S0 - K;
+    constexpr u32 kThreads = 1u << kOnePassThreadsLog;
+    constexpr u32 kGroups = 1u << (LQ - K);
+    static_assert(kGroups % kThreads == 0 || kGroups < kThreads, "groups per thread");
+    for (u32 g = threadIdx.x; g < kGroups; g += kThreads) {
+      const u32 lo = g & ((1u << LS) - 1), hi = g >> LS;
+      const u32 i0 = (hi << (LS + K)) + lo;
+      const u32 jb = (r << LQ) + i0;
+      u64 x[1 << K];
+#pragma unroll
+      for (int m = 0; m < (1 << K); ++m) x[m] = sm[opad(i0 + ((u32)m << LS))];
+      if constexpr (!INV)
+        fwd_block<K, LS, C + S0, LOGN>(x, jb, tw, q);
+      else
+        inv_block<K, LS, C + S0 + K - 1, LOGN>(x, jb, tw, q);
+#pragma unroll
+      for (int m = 0; m < (1 << K); ++m) sm[opad(i0 + ((u32)m << LS))] = x[m];
+    }
+  }
+}
+
+template <bool INV, int LOGN, int LQ, int WIDE>
+__device__ __forceinline__ void onepass_local(u64* sm, u32 r, const ulonglong2* tw, u64 q) {
+  using R = OnePassRounds<LQ, WIDE>;
+  if constexpr (!INV) {
+    onepass_round<false, LOGN, LQ, R::s0[0], R::k[0]>(sm, r, tw, q);
+    __syncthreads();
+    onepass_round<false, LOGN, LQ, R::s0[1], R::k[1]>(sm, r, tw, q);
+    __syncthreads();
+    onepass_round<false, LOGN, LQ, R::s0[2], R::k[2]>(sm, r, tw, q);
+    if constexpr (R::n > 3) {
+      __syncthreads();
+      onepass_round<false, LOGN, LQ, R::s0[3], R::k[3]>(sm, r, tw, q);
+    }
+  } else {
+    if constexpr (R::n > 3) {
+      onepass_round<true, LOGN, LQ, R::s0[3], R::k[3]>(sm, r, tw, q);
+      __syncthreads();
+    }
+    onepass_round<true, LOGN, LQ, R::s0[2], R::k[2]>(sm, r, tw, q);
+    __syncthreads();
+    onepass_round<true, LOGN, LQ, R::s0[1], R::k[1]>(sm, r, tw, q);
+    __syncthreads();
+    onepass_round<true, LOGN, LQ, R::s0[0], R::k[0]>(sm, r, tw, q);
+  }
+}
+
+template <bool INV, int LOGN, int LQ, int WIDE>
+__global__ void __launch_bounds__(1u << kOnePassThreadsLog, 1) k_ntt_onepass(LimbSet s, LimbSet in, int use_in,
+                                                                             int scale, Tables T) {
+  namespace cg = cooperative_groups;
+  constexpr int C = LOGN - LQ, CL = 1 << C, Q = 1 << LQ;
+  constexpr u32 kThreads = 1u << kOnePassThreadsLog;
+  extern __shared__ u64 sm[];
+  u64* a;
+  int pid;
+  limb_meta<LOGN>(s, a, pid);
+  const u64* ain = use_in ? input_limb<LOGN>(s, in) : a;
+  const u64 q = T.mods[pid].q;
+  const ulonglong2* tw = (INV ? T.inv2 : T.fwd2) + ((size_t)pid << LOGN);
+  const u32 r = CL > 1 ? cg::this_cluster().block_rank() : 0;
+  const u64* src = ain + ((size_t)r << LQ);
+  u64* dst = a + ((size_t)r << LQ);
+  if constexpr (!INV) {
+    if constexpr (CL > 1) {
+      cg::cluster_group cl = cg::this_cluster();
+      cl.sync();  // every CTA of the cluster has started before remote stores
+      constexpr u32 kJ = Q / CL;
+      u64* peer[CL];
+#pragma unroll
+      for (int k = 0; k < CL; ++k) peer[k] = cl.map_shared_rank(sm, k);
+      for (u32 t = threadIdx.x; t < kJ; t += kThreads) {
+        const u32 j = r * kJ + t;
+        u64 x[CL];
+#pragma unroll
+        for (int k = 0; k < CL; ++k) x[k] = ain[j + ((u32)k << LQ)];
+        fwd_block<C, LQ, 0, LOGN>(x, j, tw, q);
+#pragma unroll
+        for (int k = 0; k < CL; ++k) peer[k][opad(j)] = x[k];
+      }
+      cl.sync();  // the chunks are complete (remote stores visible)
+    } else {
+      for (u32 e = threadIdx.x; e < (u32)Q; e += kThreads) sm[opad(e)] = src[e];
+      __syncthreads();
+    }
+    onepass_local<false, LOGN, LQ, WIDE>(sm, r, tw, q);
+    __syncthreads();
+    for (u32 e = threadIdx.x; e < (u32)Q; e += kThreads) dst[e] = reduce4(sm[opad(e)], q);
+  } else {
+    for (u32 e = threadIdx.x; e < (u32)Q; e += kThreads) sm[opad(e)] = src[e];
+    __syncthreads();
+    onepass_local<true, LOGN, LQ, WIDE>(sm, r, tw, q);
+    const u64 ni = T.ninv[pid], nis = T.ninv_sh[pid];
+    if constexpr (CL > 1) {
+      cg::cluster_group cl = cg::this_cluster();
+      cl.sync();  // every chunk's local stages are done
+      constexpr u32 kJ = Q / CL;
+      const u64* peer[CL];
+#pragma unroll
+      for (int k = 0; k < CL; ++k) peer[k] = cl.map_shared_rank(sm, k);
+      for (u32 t = threadIdx.x; t < kJ; t += kThreads) {
+        const u32 j = r * kJ + t;
+        u64 x[CL];
+#pragma unroll
+        for (int k = 0; k < CL; ++k) x[k] = peer[k][opad(j)];
+        inv_block<C, LQ, C - 1, LOGN>(x, j, tw, q);
+#pragma unroll
+        for (int k = 0; k < CL; ++k) a[j + ((u32)k << LQ)] = reduce4(scale ? shoup_lazy(x[k], ni, nis, q) : x[k], q);
+      }
+      cl.sync();  // no CTA leaves while the others still read its shared memory
+    } else {
+      __syncthreads();
+      for (u32 e = threadIdx.x; e < (u32)Q; e += kThreads) {
+        const u64 v = sm[opad(e)];
+        dst[e] = reduce4(scale ? shoup_lazy(v, ni, nis, q) : v, q);
+      }
+    }
+  }
+}
+
+template <int LOGN>
+constexpr int onepass_lq() {
+  return LOGN >= 14 ? 14 : 13;
+}
+
+template <bool INV, int LOGN, int WIDE>
+void launch_onepass(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, const LimbSet* in, bool scale) {
+  constexpr int LQ = onepass_lq<LOGN>();
+  constexpr int CL = 1 << (LOGN - LQ);
+  const size_t smem = (size_t)((1 << LQ) + (1 << (LQ - 4))) * sizeof(u64);
+  auto kern = k_ntt_onepass<INV, LOGN, LQ, WIDE>;
+  static unsigned long long attr_set = 0;  // per instantiation, one bit per device
+  if (ctx->device < 64 && !(attr_set >> ctx->device & 1)) {
+    HC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr_set |= 1ull << ctx->device;
+  } else if (ctx->device >= 64) {
+    HC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  }
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3((unsigned)CL, (unsigned)ylimbs, (unsigned)items);
+  lc.blockDim = dim3(1u << kOnePassThreadsLog);
+  lc.dynamicSmemBytes = smem;
+  lc.stream = ctx->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  ProfScope p(ctx, INV ? "ntt_inv_onepass" : "ntt_fwd_onepass", (uint64_t)ylimbs * items);
+  HC_CUDA(cudaLaunchKernelEx(&lc, kern, s, in ? *in : s, in ? 1 : 0, scale ? 1 : 0, ctx->tab));
+}
+
 template <int LOGN>
 void ntt_logn(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, bool inverse, const LimbSet* in, bool scale,
               const KsrFuse* fuse = nullptr) {
+  if constexpr (LOGN >= 13) {
+    // variants 3 / 4: plain transforms in one pass, rounds of up to 5 / 4
+    // stages (the fused-tail transforms stay two-pass, 128-thread tiles)
+    const int v = ctx->tune.ntt_variant[LOGN];
+    if (!fuse && (v == 3 || v == 4)) {
+      if (inverse) {
+        if (v == 3) launch_onepass<true, LOGN, 1>(ctx, s, items, ylimbs, in, scale);
+        else launch_onepass<true, LOGN, 0>(ctx, s, items, ylimbs, in, scale);
+      } else {
+        if (v == 3) launch_onepass<false, LOGN, 1>(ctx, s, items, ylimbs, in, scale);
+        else launch_onepass<false, LOGN, 0>(ctx, s, items, ylimbs, in, scale);
+      }
+      ctx->launches -= 1;  // one launch instead of two (the caller counts two)
+      return;
+    }
+  }
   if (!inverse) {
     launch_pass_cols<false, LOGN>(ctx, s, items, ylimbs, in, true, fuse);
     launch_pass_rows<false, LOGN>(ctx, s, items, ylimbs, nullptr, fuse);

@@ -45,6 +45,7 @@ EXPORTS = [
     "hc_relin_noalloc", "hc_graph_begin", "hc_graph_end", "hc_graph_launch", "hc_graph_destroy",
     "hc_enc_conv2d_single_batch", "hc_enc_fc_rotsum", "hc_ct_import_batch", "hc_ct_export_batch",
     "hc_mul_relin_rescale_host", "hc_autotune", "hc_tune_set", "hc_tune_get", "hc_int_mul_rates",
+    "hc_enc_fc_partial", "hc_relin_rescale_batch",
 ]
 
 
@@ -138,6 +139,8 @@ def load(path: str = LIB_PATH):
         "hc_enc_poly_act": (c_int, [vp, vp, pp, c_int, ctypes.POINTER(dbl), c_int, pp]),
         "hc_enc_pool": (c_int, [vp, vp, c_int, pp, c_int, c_int, c_int, pp]),
         "hc_enc_fc": (c_int, [vp, vp, c_int, pp, c_int, pp, pp, c_int, pp]),
+        "hc_enc_fc_partial": (c_int, [vp, c_int, pp, c_int, pp, c_int, pp]),
+        "hc_relin_rescale_batch": (c_int, [vp, vp, pp, c_int, pp]),
         "hc_relin_noalloc": (c_int, [vp, vp, vp, vp]),
         "hc_graph_begin": (c_int, [pp, c_int, ctypes.c_size_t]),
         "hc_graph_end": (c_int, [pp, c_int, pp]),
@@ -645,6 +648,20 @@ def hc_enc_fc_rotsum(ctx, evk, x, w, n_out, span_log2):
     outs = _outs(n_out)
     _check(ctx, load().hc_enc_fc_rotsum(ctx.ptr, evk.ptr, _ptr_array(x), len(x), _ptr_array(w), n_out, span_log2,
                                         outs))
+    return _wrap_outs(ctx, outs, n_out)
+
+
+def hc_relin_rescale_batch(ctx, evk, d):
+    """[rescale(relin(c)) for c in d], one batched pass (degree-2 inputs at one level)."""
+    outs = _outs(len(d))
+    _check(ctx, load().hc_relin_rescale_batch(ctx.ptr, evk.ptr, _ptr_array(d), len(d), outs))
+    return _wrap_outs(ctx, outs, len(d))
+
+
+def hc_enc_fc_partial(ctx, packing, x, w, n_out):
+    """Degree-2 sums y[r] = sum_k x_k (x) w[r n_in + k] (no relinearisation)."""
+    outs = _outs(n_out)
+    _check(ctx, load().hc_enc_fc_partial(ctx.ptr, packing, _ptr_array(x), len(x), _ptr_array(w), n_out, outs))
     return _wrap_outs(ctx, outs, n_out)
 
 

@@ -190,11 +190,13 @@ def test_autotune_and_every_tuning_choice_bit_identical(pair):
     H.hc_tune_set(pair.ctx, H.HC_TUNE_MODUP_SPLIT, 1)
 
 
-@pytest.mark.parametrize("log_n", [13, 14, 15])
+@pytest.mark.parametrize("log_n", [13, 14, 15, 16])
 def test_ntt_tile_variants_match_oracle(log_n):
-    """Every NTT block size the tuner can pick at N = 2^13..2^15 (including
-    the 64-thread tiles that exist only there) gives the oracle's words for a
-    multiply + relinearise + rescale and a rotation."""
+    """Every NTT form the tuner can pick at N = 2^13..2^16 (two-pass block
+    sizes including the 64-thread tiles that exist only there, and the
+    single-pass transforms on one CTA (2^13, 2^14) or a cluster of two or
+    four (2^15, 2^16)) gives the oracle's words for a multiply + relinearise
+    + rescale, a rotation and the host-to-host call."""
     from hc_pair import Pair
     p = Pair(log_n, [50, 30, 30], [50], 30, seed=70 + log_n, rot_steps=[5])
     op = p.op
@@ -202,14 +204,14 @@ def test_ntt_tile_variants_match_oracle(log_n):
     gb, ob = p.encrypt_values(W.slot_values(72, op.K), nonce=2)
     want_m = ckks.rescale(op, ckks.relin(op, p.o_evk, ckks.mul(op, oa, ob)))
     want_r = ckks.rotate(op, p.o_evk, oa, 5)
-    for v in (0, 1, 2):
+    for v in (0, 1, 2, 3, 4):
         H.hc_tune_set(p.ctx, H.HC_TUNE_NTT, v)
         p.assert_same(H.hc_mul_relin_rescale_batch(p.ctx, p.g_evk, [ga], [gb])[0], want_m, "mul v=%d" % v)
         p.assert_same(H.hc_rotate(p.ctx, p.g_evk, ga, 5), want_r, "rot v=%d" % v)
         outs, metas = _host_products(p, [ga], [gb], op.L)
         _assert_host_same(outs[0], metas[0], want_m, "host v=%d" % v)
     with pytest.raises(H.HcError):
-        H.hc_tune_set(p.ctx, H.HC_TUNE_NTT, 3)
+        H.hc_tune_set(p.ctx, H.HC_TUNE_NTT, 5)
 
 
 def test_batch_larger_than_workspace_chunk(pair):
