@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tiles and launch shapes")
     ap.add_argument("--graph-arena-gib", type=int, default=0,
                     help="device arena of the captured step (0: 4 GiB + 0.2 GiB per pair)")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--e2e-chunk", type=int, default=0, help="pairs per pipeline chunk of the host call (0: auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-ops", type=int, default=1, help="oracle operations in the CPU sample")
@@ -61,7 +61,9 @@ def parse():
     ap.add_argument("--no-deep", action="store_true", help="skip the deep single-ciphertext CNN leg")
     ap.add_argument("--paper-shape", action="store_true",
                     help="also run the paper's own network (N=2^15, 16384 images; ~80 GB of device memory)")
-    ap.add_argument("--serve-requests", type=int, default=60, help="requests per arrival rate")
+    ap.add_argument("--serve-requests", type=int, default=500, help="requests per arrival rate")
+    ap.add_argument("--serve-budget-mib", type=int, default=1024,
+                    help="device-footprint budget of the serving loop's admission (MiB)")
     ap.add_argument("--profile-step", type=int, metavar="B", default=0,
                     help="run one batched step of B pairs between cudaProfilerStart/Stop (for ncu "
                          "--profile-from-start off) after two untimed ones, and exit")
@@ -650,17 +652,15 @@ def uneven_leg(H, W, np, torch, local):
         return out
 
     def batched():
+        # per ring degree: one conv call and one activation call over all its
+        # instances (their levels run as concurrent branches inside the calls)
         out = [None] * len(inst)
         for log_n, ctx in ctxs.items():
             idx = [i for i, (ln, _) in enumerate(inst) if ln == log_n]
             evk = keys[log_n][2]
             y = H.hc_enc_conv2d_single_batch(ctx, evk, [xs[i] for i in idx], 8, ws[log_n], 1, 3, 3)
-            groups = {}
-            for i, c in zip(idx, y):
-                groups.setdefault(inst[i][1], []).append((i, c))
-            for lv, items in sorted(groups.items()):
-                for (i, _), r in zip(items, H.hc_enc_poly_act(ctx, evk, [c for _, c in items], (0.0, 0.0, 1.0))):
-                    out[i] = r
+            for i, r in zip(idx, H.hc_enc_poly_act(ctx, evk, y, (0.0, 0.0, 1.0))):
+                out[i] = r
         return out
 
     def timed(fn, reps):
@@ -739,11 +739,13 @@ def serving_leg(args, H, W, np, torch, local):
               for t, v in enumerate(filt)]
         models[log_n] = serving.Model(ctx=ctx, evk=evk, weights=ws, n=ctx.n, n_special=len(ps.p_bits))
         pks[log_n] = pk
-    budget = 16 << 30
+    budget = args.serve_budget_mib << 20
     out = {"workload": "single-ct conv 3x3 + x^2 requests: 1/4 at N=2^12 (L=2), 3/4 uneven N=2^13..2^15 (3-12 levels)",
            "budget_bytes": budget, "rates": {}}
     inst = W.uneven_instances(args.serve_requests)
-    for k, rate in enumerate((20.0, 50.0, 100.0, 200.0)):
+    # the paper-style rates, then two above the loop's capacity (saturation:
+    # throughput plateaus, queueing grows, admission by footprint binds)
+    for k, rate in enumerate((20.0, 50.0, 100.0, 200.0, 1000.0, 4000.0)):
         reqs = []
         for i in range(args.serve_requests):
             log_n, lv = (12, 2) if i % 4 == 0 else inst[i]
@@ -1067,6 +1069,14 @@ def run_gpu(args, rank, world, local):
     t_e2e = max_over_ranks(max(time.perf_counter() - t0, 1e-9), device="cuda")
     e2e_step_ms = [round(1000.0 * (b - a), 2) for a, b in zip([t0] + e2e_marks[:-1], e2e_marks)]
     e2e_value = Bn * args.e2e_steps * world / t_e2e if args.e2e_steps > 0 else None
+    e2e_timeline = None
+    if args.e2e_steps > 0:
+        # one more call with events around each chunk's copies in, kernels and
+        # copies out (ms from the call's start), to read the overlap from
+        H.hc_profile_enable(ctx, True)
+        e2e_step()
+        e2e_timeline = [[round(v, 2) for v in c] for c in H.hc_profile_host_timeline(ctx)]
+        H.hc_profile_enable(ctx, False)
     if args.e2e_steps > 0:  # the host-side result decrypts to the product
         m0 = e2e_step()[0]
         back = H.hc_ct_import(ctx, out_arrays[0], m0.level, m0.degree, m0.scale)
@@ -1119,7 +1129,12 @@ def run_gpu(args, rank, world, local):
         "config": bench_config(Bn, world),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": roofline, "cpu_baseline": None, "gpu_launches": launches, "clocks": clk,
-        "e2e_detail": {"pinned_copy_gbs": copy_gbs, "step_ms": e2e_step_ms},
+        "e2e_detail": {"pinned_copy_gbs": copy_gbs, "step_ms": e2e_step_ms,
+                       "step_ms_median": statistics.median(e2e_step_ms) if e2e_step_ms else None,
+                       "step_ms_min_max": [min(e2e_step_ms), max(e2e_step_ms)] if e2e_step_ms else None,
+                       "ops_per_s_at_median": Bn / statistics.median(e2e_step_ms) * 1000 if e2e_step_ms else None,
+                       "chunk_timeline_ms": e2e_timeline,
+                       "chunk_timeline_fields": "per chunk: copy-in start, end, kernels start, end, copy-out start, end"},
         "kernels": kern_summary, "tuning": tuning,
         "forms": {"graph": graph_value, "eager": eager_value, "unit": UNIT,
                   "graph_bit_identical_to_eager": graph_same,

@@ -130,6 +130,13 @@ int hc_profile_kernel(hc_ctx *ctx, const char *name, uint64_t *launches, double 
                       uint64_t *units);
 /* Names of the kernels recorded, comma separated, into buf[cap]. */
 int hc_profile_names(hc_ctx *ctx, char *buf, size_t cap);
+/* Timeline of the last hc_mul_relin_rescale_host call made while profiling
+ * was enabled: for each pipeline chunk c, out[6c .. 6c+5] = milliseconds
+ * from the call's start to the start and end of the chunk's copies in, of
+ * its kernels and of its copies out (CUDA events on the three streams).
+ * Writes min(count, cap) values (out may be NULL) and returns the count
+ * (6 x chunks; 0 if no such call was profiled). */
+int hc_profile_host_timeline(const hc_ctx *ctx, double *out, int cap);
 /* Integer-multiplier throughput of this GPU (measurement aid; the paper has
  * no counterpart: its timings are HElib's on CPUs).  Times five forms, each
  * as four independent dependency chains per thread over 8 blocks of 256
@@ -404,9 +411,11 @@ int hc_enc_conv2d(hc_ctx *ctx, const hc_evk *evk, hc_packing packing, const hc_c
  *   y[i*cout + co] = sum_{p,q} rot(x[i], p*W + q) (x) w[(co*kh + p)*kw + q],
  * one relinearisation and one rescale per output.  Images may sit at
  * different levels: they are grouped by level and every rotation step runs
- * as one batched key switch per group; weights at a higher level are
- * dropped to each group's level.  Bit-identical to hc_enc_conv2d with
- * HC_PACK_SINGLE applied image by image.
+ * as one batched key switch per group, the groups concurrently on side
+ * streams joined back to the context stream (concurrent branches when
+ * captured into a graph); weights at a higher level are dropped to each
+ * group's level.  Bit-identical to hc_enc_conv2d with HC_PACK_SINGLE
+ * applied image by image.
  */
 int hc_enc_conv2d_single_batch(hc_ctx *ctx, const hc_evk *evk, const hc_ct *const *x, int nimg, int W,
                                const hc_ct *const *w, int cout, int kh, int kw, hc_ct **y);
@@ -423,7 +432,10 @@ int hc_enc_conv2d_single_batch(hc_ctx *ctx, const hc_evk *evk, const hc_ct *cons
  * deg3(a) = a0 + a1 u + a2 u2 + a3 u3 at level l-3 with the scale of
  * rs(u3 * a3 @ q_{l-2}) (the u and u2 terms brought to it by their
  * constant's scale); out = rs(rl(deg3(c4..c7) u4)) + rs(deg3(c0..c3) * 1 @ s)
- * with s chosen to match scales.  degree must be 2 or 7.
+ * with s chosen to match scales.  degree must be 2 or 7.  Degree 2 accepts
+ * inputs at several levels (each level's inputs form one batch; the
+ * batches run concurrently on side streams joined back to the context
+ * stream); degree 7 needs one level.
  */
 int hc_enc_poly_act(hc_ctx *ctx, const hc_evk *evk, const hc_ct *const *x, int n,
                     const double *coeffs, int degree, hc_ct **y);

@@ -123,6 +123,65 @@ hc_ct* new_ct(hc_ctx* ctx, int level, int degree, double scale) {
 }
 
 // Outputs sharing one slab.
+// Runs fn(b) for b in [0, nb) on side streams forked from the context
+// stream and joined back to it: every launcher inside fn sees ctx->stream
+// set to branch b's stream, so independent groups of work (the levels of a
+// mixed batch) overlap on the device; captured into a graph the branches
+// become concurrent nodes.  Memory a branch allocates and frees is ordered
+// on its own stream; results stay usable on the context stream after the
+// join.  nb <= 1 runs inline.  On an error the branches already issued are
+// still joined before the error propagates.
+template <class F>
+void fork_join(hc_ctx* ctx, int nb, F&& fn) {
+  if (nb <= 1) {
+    if (nb == 1) fn(0);
+    return;
+  }
+  const cudaStream_t home = ctx->stream;
+  while ((int)ctx->aux_streams.size() < nb) {
+    cudaStream_t st = nullptr;
+    HC_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    ctx->aux_streams.push_back(st);
+  }
+  auto mark = [](cudaStream_t st) {
+    cudaEvent_t e = nullptr;
+    HC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    const cudaError_t r = cudaEventRecord(e, st);
+    if (r != cudaSuccess) {
+      cudaEventDestroy(e);
+      throw HcError{HC_ERR_CUDA, std::string("cudaEventRecord: ") + cudaGetErrorString(r)};
+    }
+    return e;
+  };
+  cudaEvent_t fork = mark(home);
+  int started = 0;
+  auto join = [&]() {
+    ctx->stream = home;
+    for (int b = 0; b < started; ++b) {
+      cudaEvent_t e = nullptr;
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) {
+        if (cudaEventRecord(e, ctx->aux_streams[b]) == cudaSuccess) cudaStreamWaitEvent(home, e, 0);
+        cudaEventDestroy(e);
+      }
+    }
+    cudaEventDestroy(fork);
+  };
+  try {
+    for (int b = 0; b < nb; ++b) {
+      const cudaStream_t st = ctx->aux_streams[b];
+      HC_CUDA(cudaStreamWaitEvent(st, fork, 0));
+      ++started;
+      ctx->stream = st;
+      fn(b);
+      ctx->stream = home;
+    }
+  } catch (...) {
+    join();
+    throw;
+  }
+  join();
+}
+
 std::vector<hc_ct*> new_cts(hc_ctx* ctx, int count, int level, int degree, double scale) {
   std::vector<hc_ct*> out;
   if (count <= 0) return out;
@@ -763,6 +822,10 @@ extern "C" void hc_ctx_destroy(hc_ctx* ctx) {
   recycle_events(ctx);
   for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
   for (void* d : ctx->owned) cudaFree(d);
+  for (cudaStream_t st : ctx->aux_streams) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
   delete ctx;
 }
 
@@ -807,6 +870,14 @@ extern "C" int hc_profile_kernel(hc_ctx* ctx, const char* name, uint64_t* launch
     *total_ms = ms;
     *units = ctx->prof_units[name];
   });
+}
+
+extern "C" int hc_profile_host_timeline(const hc_ctx* ctx, double* out, int cap) {
+  if (!ctx) return HC_ERR_INVALID;
+  const int n = (int)ctx->host_timeline.size();
+  if (out)
+    for (int i = 0; i < n && i < cap; ++i) out[i] = ctx->host_timeline[i];
+  return n;
 }
 
 extern "C" int hc_profile_names(hc_ctx* ctx, char* buf, size_t cap) {
@@ -1870,6 +1941,19 @@ extern "C" int hc_mul_relin_rescale_host(hc_ctx* ctx, const hc_evk* evk, const u
       evs.push_back(e);
       return e;
     };
+    // with profiling on: timing events around each chunk's copies in, its
+    // kernels and its copies out, relative to the call's start
+    const bool tl = ctx->prof;
+    std::vector<cudaEvent_t> tev;  // [chunk][h2d b, h2d e, compute b, compute e, d2h b, d2h e], then the start
+    auto tmark = [&](cudaStream_t st) -> cudaEvent_t {
+      cudaEvent_t e;
+      HC_CUDA(cudaEventCreate(&e));
+      evs.push_back(e);
+      HC_CUDA(cudaEventRecord(e, st));
+      return e;
+    };
+    cudaEvent_t t_start = tl ? tmark(ctx->stream) : nullptr;
+    if (tl) tev.assign((size_t)6 * nch, nullptr);
     BufPtr flags = ctx->buffer(nch);
     keep.push_back(flags);
     HC_CUDA(cudaMemsetAsync(flags->ptr, 0, nch * sizeof(u64), ctx->stream));
@@ -1881,12 +1965,14 @@ extern "C" int hc_mul_relin_rescale_host(hc_ctx* ctx, const hc_evk* evk, const u
     std::vector<cudaEvent_t> copied(nch);
     for (int c = 0; c < nch; ++c) {
       const int m = (int)ins[c].size() / 2;
+      if (tl) tev[6 * c + 0] = tmark(h2d);
       for (int j = 0; j < m; ++j) {
         const int i = first[c] + j;
         HC_CUDA(cudaMemcpyAsync(ins[c][j]->data, a_host[i], 2 * stride * sizeof(u64), cudaMemcpyHostToDevice, h2d));
         HC_CUDA(cudaMemcpyAsync(ins[c][m + j]->data, b_host[i], 2 * stride * sizeof(u64), cudaMemcpyHostToDevice,
                                 h2d));
       }
+      if (tl) tev[6 * c + 1] = tmark(h2d);
       copied[c] = event();
       HC_CUDA(cudaEventRecord(copied[c], h2d));
     }
@@ -1894,6 +1980,7 @@ extern "C" int hc_mul_relin_rescale_host(hc_ctx* ctx, const hc_evk* evk, const u
       std::vector<hc_ct*>& x = ins[c];
       const int m = (int)x.size() / 2;
       HC_CUDA(cudaStreamWaitEvent(ctx->stream, copied[c], 0));
+      if (tl) tev[6 * c + 2] = tmark(ctx->stream);
       launch_check_range(ctx, x[0]->data, 4 * m, level + 1, stride, (unsigned long long*)(flags->ptr + c));
       launch_ntt(ctx, limbset_base(x[0]->data, 2 * stride, stride, 2, level + 1, 0, nullptr), 2 * m, false);
       for (int j = 0; j < m; ++j) {
@@ -1910,12 +1997,15 @@ extern "C" int hc_mul_relin_rescale_host(hc_ctx* ctx, const hc_evk* evk, const u
         const int i = first[c] + j;
         out_meta[i] = hc_ct_meta{level - 1, 1, a_meta[i].scale * b_meta[i].scale / (double)ctx->P.chain[level]};
       }
+      if (tl) tev[6 * c + 3] = tmark(ctx->stream);
       const cudaEvent_t done = event();
       HC_CUDA(cudaEventRecord(done, ctx->stream));
       HC_CUDA(cudaStreamWaitEvent(d2h, done, 0));
+      if (tl) tev[6 * c + 4] = tmark(d2h);
       for (int j = 0; j < m; ++j)
         HC_CUDA(cudaMemcpyAsync(out_host[first[c] + j], staged->ptr + (size_t)j * out_words, out_words * sizeof(u64),
                                 cudaMemcpyDeviceToHost, d2h));
+      if (tl) tev[6 * c + 5] = tmark(d2h);
     }
     // staged buffers go back to the pool only after the copies out
     const cudaEvent_t drained = event();
@@ -1924,6 +2014,14 @@ extern "C" int hc_mul_relin_rescale_host(hc_ctx* ctx, const hc_evk* evk, const u
     std::vector<u64> bad(nch);
     HC_CUDA(cudaMemcpyAsync(bad.data(), flags->ptr, nch * sizeof(u64), cudaMemcpyDeviceToHost, ctx->stream));
     HC_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (tl) {
+      ctx->host_timeline.assign(tev.size(), 0.0);
+      for (size_t k = 0; k < tev.size(); ++k) {
+        float ms = 0;
+        HC_CUDA(cudaEventElapsedTime(&ms, t_start, tev[k]));
+        ctx->host_timeline[k] = ms;
+      }
+    }
     for (u64 b : bad) HC_CHECK(b == 0, HC_ERR_INVALID, "input residue not below its prime (outputs not valid)");
   });
   // on an error the side streams may still be writing into inputs: drain them first
@@ -2145,60 +2243,74 @@ extern "C" int hc_enc_poly_act(hc_ctx* ctx, const hc_evk* evk, const hc_ct* cons
       return;
     }
     if (n == 0) return;
-    std::vector<const hc_ct*> xs(x, x + n);
-    const int level = xs[0]->level;
-    for (auto* c : xs) {
-      check_ct(ctx, c);
-      HC_CHECK(c->level == level && c->degree == 1, HC_ERR_LEVEL_MISMATCH, "inputs at different levels");
-      check_scales(c->scale, xs[0]->scale);
+    // inputs may sit at several levels: one group per level, each a branch of
+    // its own (fork_join), the same circuit as a call per level
+    std::map<int, std::vector<int>> by_level;
+    for (int i = 0; i < n; ++i) {
+      check_ct(ctx, x[i]);
+      HC_CHECK(x[i]->degree == 1, HC_ERR_LEVEL_MISMATCH, "inputs must be degree 1");
+      by_level[x[i]->level].push_back(i);
     }
     const double a0 = coeffs[0], a1 = coeffs[1], a2 = coeffs[2];
     const bool square = (a0 == 0 && a1 == 0 && a2 == 1);
-    HC_CHECK(level >= (square ? 1 : 2), HC_ERR_DEPTH, "not enough levels for the activation");
-    std::vector<hc_ct*> t = mul_relin_rescale_cts(ctx, evk, xs.data(), xs.data(), n);  // rs(rl(u u))
-    if (square) {
-      for (int i = 0; i < n; ++i) y[i] = t[i];
-      return;
+    for (auto& kv : by_level) {
+      HC_CHECK(kv.first >= (square ? 1 : 2), HC_ERR_DEPTH, "not enough levels for the activation");
+      for (int i : kv.second) check_scales(x[i]->scale, x[kv.second[0]]->scale);
     }
-    std::vector<const hc_ct*> tc(t.begin(), t.end());
-    std::vector<hc_ct*> t2m = mul_const_cts(ctx, tc, a2, (double)ctx->P.chain[level - 1]);
-    std::vector<hc_ct*> t2(n);
-    {
-      std::vector<const hc_ct*> c(t2m.begin(), t2m.end());
-      t2 = new_cts(ctx, n, level - 2, 1, t2m[0]->scale / (double)ctx->P.chain[level - 1]);
-      rescale_cts(ctx, c, t2);
-      for (int i = 0; i < n; ++i) t2[i]->scale = t2m[i]->scale / (double)ctx->P.chain[level - 1];
-    }
-    free_all(t2m);
-    free_all(t);
-    if (a1 != 0) {
-      const double cs = t2[0]->scale * (double)ctx->P.chain[level] / xs[0]->scale;
-      std::vector<hc_ct*> vm = mul_const_cts(ctx, xs, a1, cs);
-      std::vector<const hc_ct*> c(vm.begin(), vm.end());
-      std::vector<hc_ct*> v = new_cts(ctx, n, level - 1, 1, vm[0]->scale / (double)ctx->P.chain[level]);
-      rescale_cts(ctx, c, v);
-      free_all(vm);
-      std::vector<BufPtr> keep;
-      std::vector<CtRef> tr, vr;
-      for (int i = 0; i < n; ++i) {
-        check_scales(t2[i]->scale, v[i]->scale);
-        tr.push_back(t2[i]->ref());
-        vr.push_back(v[i]->ref());  // v's limbs 0..level-2 are its drop to t2's level
+    const std::vector<std::pair<int, std::vector<int>>> glist(by_level.begin(), by_level.end());
+    std::vector<hc_ct*> res(n, nullptr);
+    fork_join(ctx, (int)glist.size(), [&](int branch) {
+      const int level = glist[branch].first;
+      const std::vector<int>& idx = glist[branch].second;
+      const int m = (int)idx.size();
+      std::vector<const hc_ct*> xs;
+      for (int i : idx) xs.push_back(x[i]);
+      std::vector<hc_ct*> t = mul_relin_rescale_cts(ctx, evk, xs.data(), xs.data(), m);  // rs(rl(u u))
+      if (square) {
+        for (int k = 0; k < m; ++k) res[idx[k]] = t[k];
+        return;
       }
-      const CtRef* td = refs_dev(ctx, tr, keep);
-      launch_ew(ctx, 0, td, td, refs_dev(ctx, vr, keep), n, 2, level - 1);
-      free_all(v);
-    }
-    if (a0 != 0) {
-      std::vector<u64> sc;
-      constant_residues(ctx, level - 2, a0 * t2[0]->scale, false, sc);
-      std::vector<BufPtr> keep;
-      std::vector<CtRef> tr;
-      for (int i = 0; i < n; ++i) tr.push_back(t2[i]->ref());
-      const CtRef* td = refs_dev(ctx, tr, keep);
-      launch_scalar(ctx, true, td, td, n, 2, level - 1, upload(ctx, sc, keep));
-    }
-    for (int i = 0; i < n; ++i) y[i] = t2[i];
+      std::vector<const hc_ct*> tc(t.begin(), t.end());
+      std::vector<hc_ct*> t2m = mul_const_cts(ctx, tc, a2, (double)ctx->P.chain[level - 1]);
+      std::vector<hc_ct*> t2(m);
+      {
+        std::vector<const hc_ct*> c(t2m.begin(), t2m.end());
+        t2 = new_cts(ctx, m, level - 2, 1, t2m[0]->scale / (double)ctx->P.chain[level - 1]);
+        rescale_cts(ctx, c, t2);
+        for (int k = 0; k < m; ++k) t2[k]->scale = t2m[k]->scale / (double)ctx->P.chain[level - 1];
+      }
+      free_all(t2m);
+      free_all(t);
+      if (a1 != 0) {
+        const double cs = t2[0]->scale * (double)ctx->P.chain[level] / xs[0]->scale;
+        std::vector<hc_ct*> vm = mul_const_cts(ctx, xs, a1, cs);
+        std::vector<const hc_ct*> c(vm.begin(), vm.end());
+        std::vector<hc_ct*> v = new_cts(ctx, m, level - 1, 1, vm[0]->scale / (double)ctx->P.chain[level]);
+        rescale_cts(ctx, c, v);
+        free_all(vm);
+        std::vector<BufPtr> keep;
+        std::vector<CtRef> tr, vr;
+        for (int k = 0; k < m; ++k) {
+          check_scales(t2[k]->scale, v[k]->scale);
+          tr.push_back(t2[k]->ref());
+          vr.push_back(v[k]->ref());  // v's limbs 0..level-2 are its drop to t2's level
+        }
+        const CtRef* td = refs_dev(ctx, tr, keep);
+        launch_ew(ctx, 0, td, td, refs_dev(ctx, vr, keep), m, 2, level - 1);
+        free_all(v);
+      }
+      if (a0 != 0) {
+        std::vector<u64> sc;
+        constant_residues(ctx, level - 2, a0 * t2[0]->scale, false, sc);
+        std::vector<BufPtr> keep;
+        std::vector<CtRef> tr;
+        for (int k = 0; k < m; ++k) tr.push_back(t2[k]->ref());
+        const CtRef* td = refs_dev(ctx, tr, keep);
+        launch_scalar(ctx, true, td, td, m, 2, level - 1, upload(ctx, sc, keep));
+      }
+      for (int k = 0; k < m; ++k) res[idx[k]] = t2[k];
+    });
+    for (int i = 0; i < n; ++i) y[i] = res[i];
   });
 }
 
@@ -2557,9 +2669,11 @@ extern "C" int hc_enc_conv2d_single_batch(hc_ctx* ctx, const hc_evk* evk, const 
       check_ct(ctx, w[i]);
       HC_CHECK(w[i]->degree == 1, HC_ERR_INVALID, "weights need degree 1");
     }
-    for (auto& kv : groups) {
-      const int level = kv.first, nq = level + 1;
-      const std::vector<int>& idx = kv.second;
+    // one branch per level: the levels' work overlaps on the device
+    const std::vector<std::pair<int, std::vector<int>>> glist(groups.begin(), groups.end());
+    fork_join(ctx, (int)glist.size(), [&](int branch) {
+      const int level = glist[branch].first, nq = level + 1;
+      const std::vector<int>& idx = glist[branch].second;
       const int G = (int)idx.size();
       std::vector<BufPtr> keep;
       // rotated images, step-major: rot[t * G + g]
@@ -2613,7 +2727,7 @@ extern "C" int hc_enc_conv2d_single_batch(hc_ctx* ctx, const hc_evk* evk, const 
       free_all(d);
       free_all(rot);
       free_all(wv);
-    }
+    });
   });
 }
 

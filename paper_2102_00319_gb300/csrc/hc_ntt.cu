@@ -442,7 +442,6 @@ void launch_pass_rows(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, cons
 // (no spin loop).  With CL = 1 (N <= 2^14) the chunk is the whole limb.
 // Shared-memory words are padded by one per 16 (index i at i + i / 16), so
 // the rounds with contiguous points per thread do not conflict on banks.
-constexpr int kOnePassThreadsLog = 9;  // 512 threads per CTA
 
 __device__ __forceinline__ u32 opad(u32 i) { return i + (i >> 4); }
 
@@ -480,11 +479,11 @@ struct OnePassRounds<13, 0> {
 // shared memory (forward, or inverse in reverse stage order).  Group g of
 // 2^K points: local index ((g >> LS) << (LS + K)) + (g & (2^LS - 1)) + (m << LS),
 // LS = LQ - S0 - K; its global index adds r 2^LQ.
-template <bool INV, int LOGN, int LQ, int S0, int K>
+template <bool INV, int LOGN, int LQ, int TL, int S0, int K>
 __device__ __forceinline__ void onepass_round(u64* sm, u32 r, const ulonglong2* tw, u64 q) {
   if constexpr (K > 0) {
     constexpr int C = LOGN - LQ, LS = LQ - S0 - K;
-    constexpr u32 kThreads = 1u << kOnePassThreadsLog;
+    constexpr u32 kThreads = 1u << TL;
     constexpr u32 kGroups = 1u << (LQ - K);
     static_assert(kGroups % kThreads == 0 || kGroups < kThreads, "groups per thread");
     for (u32 g = threadIdx.x; g < kGroups; g += kThreads) {
@@ -504,38 +503,48 @@ __device__ __forceinline__ void onepass_round(u64* sm, u32 r, const ulonglong2* 
   }
 }
 
-template <bool INV, int LOGN, int LQ, int WIDE>
+template <bool INV, int LOGN, int LQ, int TL, int WIDE>
 __device__ __forceinline__ void onepass_local(u64* sm, u32 r, const ulonglong2* tw, u64 q) {
   using R = OnePassRounds<LQ, WIDE>;
   if constexpr (!INV) {
-    onepass_round<false, LOGN, LQ, R::s0[0], R::k[0]>(sm, r, tw, q);
+    onepass_round<false, LOGN, LQ, TL, R::s0[0], R::k[0]>(sm, r, tw, q);
     __syncthreads();
-    onepass_round<false, LOGN, LQ, R::s0[1], R::k[1]>(sm, r, tw, q);
+    onepass_round<false, LOGN, LQ, TL, R::s0[1], R::k[1]>(sm, r, tw, q);
     __syncthreads();
-    onepass_round<false, LOGN, LQ, R::s0[2], R::k[2]>(sm, r, tw, q);
+    onepass_round<false, LOGN, LQ, TL, R::s0[2], R::k[2]>(sm, r, tw, q);
     if constexpr (R::n > 3) {
       __syncthreads();
-      onepass_round<false, LOGN, LQ, R::s0[3], R::k[3]>(sm, r, tw, q);
+      onepass_round<false, LOGN, LQ, TL, R::s0[3], R::k[3]>(sm, r, tw, q);
     }
   } else {
     if constexpr (R::n > 3) {
-      onepass_round<true, LOGN, LQ, R::s0[3], R::k[3]>(sm, r, tw, q);
+      onepass_round<true, LOGN, LQ, TL, R::s0[3], R::k[3]>(sm, r, tw, q);
       __syncthreads();
     }
-    onepass_round<true, LOGN, LQ, R::s0[2], R::k[2]>(sm, r, tw, q);
+    onepass_round<true, LOGN, LQ, TL, R::s0[2], R::k[2]>(sm, r, tw, q);
     __syncthreads();
-    onepass_round<true, LOGN, LQ, R::s0[1], R::k[1]>(sm, r, tw, q);
+    onepass_round<true, LOGN, LQ, TL, R::s0[1], R::k[1]>(sm, r, tw, q);
     __syncthreads();
-    onepass_round<true, LOGN, LQ, R::s0[0], R::k[0]>(sm, r, tw, q);
+    onepass_round<true, LOGN, LQ, TL, R::s0[0], R::k[0]>(sm, r, tw, q);
   }
 }
 
-template <bool INV, int LOGN, int LQ, int WIDE>
-__global__ void __launch_bounds__(1u << kOnePassThreadsLog, 1) k_ntt_onepass(LimbSet s, LimbSet in, int use_in,
-                                                                             int scale, Tables T) {
+// Blocks per SM the launch bounds ask for: one 512-thread CTA with a 2^14
+// chunk, three 256-thread CTAs with 2^13 chunks (their shared memory fits).
+template <int TL>
+constexpr int onepass_min_blocks() {
+  return TL >= 9 ? 1 : 3;
+}
+
+template <bool INV, int LOGN, int LQ, int TL, int WIDE>
+__global__ void __launch_bounds__(1u << TL, onepass_min_blocks<TL>())
+    k_ntt_onepass(LimbSet s, LimbSet in, int use_in, int scale, Tables T) {
   namespace cg = cooperative_groups;
   constexpr int C = LOGN - LQ, CL = 1 << C, Q = 1 << LQ;
-  constexpr u32 kThreads = 1u << kOnePassThreadsLog;
+  constexpr u32 kThreads = 1u << TL;
+  constexpr u32 kJ = Q / CL;                         // cross-CTA offsets per CTA
+  constexpr u32 kJT = CL > 1 ? kJ / kThreads : 1;    // ... per thread
+  static_assert(CL == 1 || kJ % kThreads == 0, "cross-CTA offsets per thread");
   extern __shared__ u64 sm[];
   u64* a;
   int pid;
@@ -549,50 +558,53 @@ __global__ void __launch_bounds__(1u << kOnePassThreadsLog, 1) k_ntt_onepass(Lim
   if constexpr (!INV) {
     if constexpr (CL > 1) {
       cg::cluster_group cl = cg::this_cluster();
+      // all of this thread's loads first (kJT offsets x CL points in flight)
+      u64 x[kJT][CL];
+#pragma unroll
+      for (u32 v = 0; v < kJT; ++v)
+#pragma unroll
+        for (int k = 0; k < CL; ++k) x[v][k] = ain[r * kJ + v * kThreads + threadIdx.x + ((u32)k << LQ)];
+#pragma unroll
+      for (u32 v = 0; v < kJT; ++v) fwd_block<C, LQ, 0, LOGN>(x[v], r * kJ + v * kThreads + threadIdx.x, tw, q);
       cl.sync();  // every CTA of the cluster has started before remote stores
-      constexpr u32 kJ = Q / CL;
-      u64* peer[CL];
 #pragma unroll
-      for (int k = 0; k < CL; ++k) peer[k] = cl.map_shared_rank(sm, k);
-      for (u32 t = threadIdx.x; t < kJ; t += kThreads) {
-        const u32 j = r * kJ + t;
-        u64 x[CL];
+      for (int k = 0; k < CL; ++k) {
+        u64* peer = cl.map_shared_rank(sm, k);
 #pragma unroll
-        for (int k = 0; k < CL; ++k) x[k] = ain[j + ((u32)k << LQ)];
-        fwd_block<C, LQ, 0, LOGN>(x, j, tw, q);
-#pragma unroll
-        for (int k = 0; k < CL; ++k) peer[k][opad(j)] = x[k];
+        for (u32 v = 0; v < kJT; ++v) peer[opad(r * kJ + v * kThreads + threadIdx.x)] = x[v][k];
       }
       cl.sync();  // the chunks are complete (remote stores visible)
     } else {
       for (u32 e = threadIdx.x; e < (u32)Q; e += kThreads) sm[opad(e)] = src[e];
       __syncthreads();
     }
-    onepass_local<false, LOGN, LQ, WIDE>(sm, r, tw, q);
+    onepass_local<false, LOGN, LQ, TL, WIDE>(sm, r, tw, q);
     __syncthreads();
     for (u32 e = threadIdx.x; e < (u32)Q; e += kThreads) dst[e] = reduce4(sm[opad(e)], q);
   } else {
     for (u32 e = threadIdx.x; e < (u32)Q; e += kThreads) sm[opad(e)] = src[e];
     __syncthreads();
-    onepass_local<true, LOGN, LQ, WIDE>(sm, r, tw, q);
+    onepass_local<true, LOGN, LQ, TL, WIDE>(sm, r, tw, q);
     const u64 ni = T.ninv[pid], nis = T.ninv_sh[pid];
     if constexpr (CL > 1) {
       cg::cluster_group cl = cg::this_cluster();
       cl.sync();  // every chunk's local stages are done
-      constexpr u32 kJ = Q / CL;
-      const u64* peer[CL];
+      u64 x[kJT][CL];
 #pragma unroll
-      for (int k = 0; k < CL; ++k) peer[k] = cl.map_shared_rank(sm, k);
-      for (u32 t = threadIdx.x; t < kJ; t += kThreads) {
-        const u32 j = r * kJ + t;
-        u64 x[CL];
+      for (int k = 0; k < CL; ++k) {
+        const u64* peer = cl.map_shared_rank(sm, k);
 #pragma unroll
-        for (int k = 0; k < CL; ++k) x[k] = peer[k][opad(j)];
-        inv_block<C, LQ, C - 1, LOGN>(x, j, tw, q);
-#pragma unroll
-        for (int k = 0; k < CL; ++k) a[j + ((u32)k << LQ)] = reduce4(scale ? shoup_lazy(x[k], ni, nis, q) : x[k], q);
+        for (u32 v = 0; v < kJT; ++v) x[v][k] = peer[opad(r * kJ + v * kThreads + threadIdx.x)];
       }
-      cl.sync();  // no CTA leaves while the others still read its shared memory
+      cl.sync();  // all remote reads are done before any CTA of the cluster exits
+#pragma unroll
+      for (u32 v = 0; v < kJT; ++v) {
+        const u32 j = r * kJ + v * kThreads + threadIdx.x;
+        inv_block<C, LQ, C - 1, LOGN>(x[v], j, tw, q);
+#pragma unroll
+        for (int k = 0; k < CL; ++k)
+          a[j + ((u32)k << LQ)] = reduce4(scale ? shoup_lazy(x[v][k], ni, nis, q) : x[v][k], q);
+      }
     } else {
       __syncthreads();
       for (u32 e = threadIdx.x; e < (u32)Q; e += kThreads) {
@@ -603,27 +615,27 @@ __global__ void __launch_bounds__(1u << kOnePassThreadsLog, 1) k_ntt_onepass(Lim
   }
 }
 
-template <int LOGN>
-constexpr int onepass_lq() {
-  return LOGN >= 14 ? 14 : 13;
-}
-
-template <bool INV, int LOGN, int WIDE>
+// Forms: CHUNK14 = 1: chunks of 2^14 words per 512-thread CTA (one per SM;
+// clusters of N / 2^14), rounds of up to 5 stages; CHUNK14 = 0: chunks of
+// 2^13 words per 256-thread CTA (three per SM; clusters of N / 2^13, at most
+// 8), rounds of up to 4 stages.
+template <bool INV, int LOGN, int CHUNK14>
 void launch_onepass(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, const LimbSet* in, bool scale) {
-  constexpr int LQ = onepass_lq<LOGN>();
+  constexpr int LQ = (CHUNK14 && LOGN >= 14) ? 14 : 13;
+  constexpr int TL = CHUNK14 ? 9 : 8;
+  constexpr int WIDE = CHUNK14 ? 1 : 0;
   constexpr int CL = 1 << (LOGN - LQ);
+  static_assert(CL <= 8, "portable cluster size");
   const size_t smem = (size_t)((1 << LQ) + (1 << (LQ - 4))) * sizeof(u64);
-  auto kern = k_ntt_onepass<INV, LOGN, LQ, WIDE>;
+  auto kern = k_ntt_onepass<INV, LOGN, LQ, TL, WIDE>;
   static unsigned long long attr_set = 0;  // per instantiation, one bit per device
-  if (ctx->device < 64 && !(attr_set >> ctx->device & 1)) {
+  if (ctx->device >= 64 || !(attr_set >> ctx->device & 1)) {
     HC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr_set |= 1ull << ctx->device;
-  } else if (ctx->device >= 64) {
-    HC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (ctx->device < 64) attr_set |= 1ull << ctx->device;
   }
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3((unsigned)CL, (unsigned)ylimbs, (unsigned)items);
-  lc.blockDim = dim3(1u << kOnePassThreadsLog);
+  lc.blockDim = dim3(1u << TL);
   lc.dynamicSmemBytes = smem;
   lc.stream = ctx->stream;
   cudaLaunchAttribute at[1];

@@ -45,7 +45,7 @@ EXPORTS = [
     "hc_relin_noalloc", "hc_graph_begin", "hc_graph_end", "hc_graph_launch", "hc_graph_destroy",
     "hc_enc_conv2d_single_batch", "hc_enc_fc_rotsum", "hc_ct_import_batch", "hc_ct_export_batch",
     "hc_mul_relin_rescale_host", "hc_autotune", "hc_tune_set", "hc_tune_get", "hc_int_mul_rates",
-    "hc_enc_fc_partial", "hc_relin_rescale_batch",
+    "hc_enc_fc_partial", "hc_relin_rescale_batch", "hc_profile_host_timeline",
 ]
 
 
@@ -102,6 +102,7 @@ def load(path: str = LIB_PATH):
                                       ctypes.POINTER(u64)]),
         "hc_profile_names": (c_int, [vp, ctypes.c_char_p, ctypes.c_size_t]),
         "hc_int_mul_rates": (c_int, [vp, ctypes.POINTER(dbl), c_int]),
+        "hc_profile_host_timeline": (c_int, [vp, ctypes.POINTER(dbl), c_int]),
         "hc_keygen": (c_int, [vp, u64, ctypes.POINTER(ctypes.c_int32), c_int, pp, pp, pp]),
         "hc_sk_destroy": (None, [vp]), "hc_pk_destroy": (None, [vp]), "hc_evk_destroy": (None, [vp]),
         "hc_sk_export": (c_int, [vp, vp, ctypes.POINTER(ctypes.c_int8), ctypes.c_size_t]),
@@ -342,6 +343,16 @@ def hc_profile_names(ctx):
     buf = ctypes.create_string_buffer(8192)
     _check(ctx, load().hc_profile_names(ctx.ptr, buf, 8192))
     return [x for x in buf.value.decode().split(",") if x]
+
+
+def hc_profile_host_timeline(ctx):
+    """Per chunk of the last profiled host-to-host call: (copy-in start, end,
+    kernels start, end, copy-out start, end) in ms from the call's start."""
+    L = load()
+    n = L.hc_profile_host_timeline(ctx.ptr, None, 0)
+    buf = (ctypes.c_double * max(1, n))()
+    L.hc_profile_host_timeline(ctx.ptr, buf, n)
+    return [tuple(buf[6 * c: 6 * c + 6]) for c in range(n // 6)]
 
 
 INT_MUL_FORMS = ("imad32", "umulhi32", "imad_wide32", "mul_lo64", "mul_hi64")

@@ -8,7 +8,7 @@ weights and request ciphertexts stay resident in device memory.  The loop:
 * admits queued requests while the estimated device footprint of everything
   in flight stays under a budget (admission by HBM footprint),
 * groups the admitted requests by ring degree and launches one batched step
-  per group (hc_enc_conv2d_single_batch, then x^2 per level) without waiting
+  per group (hc_enc_conv2d_single_batch, then x^2) without waiting
   for earlier steps, so work of successive admissions overlaps on the GPU,
 * retires a step when its CUDA event has completed (with a stream per ring
   degree, the events of all the streams: `AllOf`) and records each
@@ -85,6 +85,7 @@ class Server:
     used_bytes: int = 0
     peak_bytes: int = 0
     done: list = field(default_factory=list)
+    budget_waits: int = 0       # ticks on which the queue head did not fit the budget
 
     def submit(self, req: Request):
         self.queue.append(req)
@@ -97,14 +98,11 @@ class Server:
         for log_n, group in sorted(by_n.items()):
             m = self.models[log_n]
             y = H.hc_enc_conv2d_single_batch(m.ctx, m.evk, [r.ct for r in group], m.width, m.weights, 1, m.kh, m.kw)
-            levels = {}
-            for r, c in zip(group, y):
-                levels.setdefault(c.level, []).append((r, c))
-            for lv, items in sorted(levels.items()):
-                acts = H.hc_enc_poly_act(m.ctx, m.evk, [c for _, c in items], (0.0, 0.0, 1.0))
-                for (r, _), a in zip(items, acts):
-                    r.result = a
-                    outputs.append(a)
+            # one activation call over every level of the group (the library
+            # runs each level's batch as a concurrent branch)
+            for r, a in zip(group, H.hc_enc_poly_act(m.ctx, m.evk, y, (0.0, 0.0, 1.0))):
+                r.result = a
+                outputs.append(a)
         return stream_event_factory()
 
     def tick(self, stream_event_factory):
@@ -126,6 +124,7 @@ class Server:
             r = self.queue[0]
             fb = footprint_bytes(self.models[r.log_n], r.ct.level)
             if self.used_bytes + nbytes + fb > self.budget_bytes and (admit or self.inflight):
+                self.budget_waits += 1
                 break
             admit.append(self.queue.pop(0))
             nbytes += fb
@@ -176,9 +175,13 @@ def run(server: Server, requests: list, arrivals, stream_event_factory, poll_s: 
             wait = (pending[0][0] - now) if pending and not server.busy() else poll_s
             time.sleep(max(0.0, min(wait, poll_s if server.busy() else wait)))
     lat = np.array([r.done - r.arrival for r in requests])
+    queued = np.array([r.admitted - r.arrival for r in requests])
     span = max(r.done for r in requests) - t0
     return {
         "requests": len(requests), "p50_ms": float(np.percentile(lat, 50) * 1e3),
         "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
-        "images_per_s": len(requests) / span, "peak_admitted_bytes": server.peak_bytes,
+        "queue_p50_ms": float(np.percentile(queued, 50) * 1e3), "queue_p99_ms": float(np.percentile(queued, 99) * 1e3),
+        "images_per_s": len(requests) / span, "offered_per_s": len(requests) / max(float(arrivals[-1]), 1e-9),
+        "peak_admitted_bytes": server.peak_bytes, "budget_bytes": server.budget_bytes,
+        "budget_waits": server.budget_waits,
     }

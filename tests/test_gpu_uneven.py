@@ -65,12 +65,18 @@ def setup():
     return build([stream] * 3)
 
 
-def run_batched(S):
+def run_batched(S, mixed=True):
+    """Per ring degree: one conv call over all its instances, then the
+    activation in one call over all levels (mixed) or one call per level."""
     out = [None] * len(S["inst"])
     for log_n, ctx in S["ctxs"].items():
         idx = [i for i, (ln, _) in enumerate(S["inst"]) if ln == log_n]
         evk = S["keys"][log_n][2]
         y = H.hc_enc_conv2d_single_batch(ctx, evk, [S["xs"][i] for i in idx], 8, S["ws"][log_n], 1, 3, 3)
+        if mixed:
+            for i, r in zip(idx, H.hc_enc_poly_act(ctx, evk, y, (0.0, 0.0, 1.0))):
+                out[i] = r
+            continue
         by_level = {}
         for i, c in zip(idx, y):
             by_level.setdefault(S["inst"][i][1], []).append((i, c))
@@ -92,9 +98,10 @@ def test_uneven_batched_and_graph_match_per_instance(setup):
         ctx, evk = S["ctxs"][log_n], S["keys"][log_n][2]
         y = H.hc_enc_conv2d(ctx, evk, H.HC_PACK_SINGLE, [S["xs"][i]], 8, 8, 1, S["ws"][log_n], 1, 3, 3, 1)
         ref.append(H.hc_enc_poly_act(ctx, evk, y, (0.0, 0.0, 1.0))[0])
-    got = run_batched(S)
-    for i in range(len(ref)):
-        assert np.array_equal(export(S, i, got[i]), export(S, i, ref[i])), i
+    for mixed in (True, False):
+        got = run_batched(S, mixed)
+        for i in range(len(ref)):
+            assert np.array_equal(export(S, i, got[i]), export(S, i, ref[i])), (mixed, i)
     ctx_list = [S["ctxs"][k] for k in (13, 14, 15)]
     H.hc_graph_begin(ctx_list, 8 << 30)
     cap = run_batched(S)

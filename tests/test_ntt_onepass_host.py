@@ -1,6 +1,9 @@
 """CPU replay of the single-pass NTT kernel (k_ntt_onepass in csrc/hc_ntt.cu):
 one limb of N = CL 2^LQ points over a cluster of CL CTAs, each holding a
-chunk of 2^LQ words in padded shared memory (index i at i + i / 16).
+chunk of 2^LQ words in padded shared memory (index i at i + i / 16), in
+both forms: 2^14-word chunks on 512 threads with rounds of up to 5 stages,
+and 2^13-word chunks on 256 threads with rounds of up to 4 (clusters of up
+to 8).
 
 Replayed exactly as the kernel indexes: the cross-CTA stages (forward:
 CTA r takes offsets j in [r Q / CL, (r+1) Q / CL), loads the CL points
@@ -21,7 +24,6 @@ import pytest
 from test_modular_bounds_host import largest_prime, shoup_lazy, shoup_of
 from test_ntt_replay_host import Replay, brv
 
-THREADS = 512
 ROUNDS = {  # (LQ, WIDE) -> [(S0, K)], forward order, as OnePassRounds
     (14, 1): [(0, 5), (5, 5), (10, 4)],
     (14, 0): [(0, 4), (4, 4), (8, 3), (11, 3)],
@@ -34,11 +36,13 @@ def opad(i):
     return i + (i >> 4)
 
 
-def lq_of(logn):
-    return 14 if logn >= 14 else 13
+def form(logn, chunk14):
+    """(LQ, threads, WIDE) of launch_onepass<INV, LOGN, CHUNK14>."""
+    lq = 14 if (chunk14 and logn >= 14) else 13
+    return lq, (512 if chunk14 else 256), (1 if chunk14 else 0)
 
 
-def check_round_geometry(LQ, S0, K):
+def check_round_geometry(LQ, S0, K, THREADS):
     LS = LQ - S0 - K
     groups = 1 << (LQ - K)
     # the kernel's thread loop: g = threadIdx.x, += 512, while g < groups
@@ -53,24 +57,28 @@ def check_round_geometry(LQ, S0, K):
     assert max(opad(i) for i in seen) < (1 << LQ) + (1 << (LQ - 4))
 
 
-@pytest.mark.parametrize("key", sorted(ROUNDS))
-def test_round_schedules_cover_the_chunk(key):
-    LQ, wide = key
-    rounds = ROUNDS[key]
+@pytest.mark.parametrize("logn,chunk14", [(l, c) for l in (13, 14, 15, 16) for c in (0, 1)])
+def test_round_schedules_cover_the_chunk(logn, chunk14):
+    LQ, threads, wide = form(logn, chunk14)
+    cl = 1 << (logn - LQ)
+    assert cl <= 8  # portable cluster size
+    if cl > 1:
+        assert ((1 << LQ) // cl) % threads == 0  # cross-CTA offsets per thread
+    rounds = ROUNDS[(LQ, wide)]
     assert sum(k for _, k in rounds) == LQ
     s = 0
     for S0, K in rounds:
         assert S0 == s and 1 <= K <= 5
         s += K
-        check_round_geometry(LQ, S0, K)
+        check_round_geometry(LQ, S0, K, threads)
 
 
 class OnePass(Replay):
     """Replay of k_ntt_onepass<INV, LOGN, LQ, WIDE> for one limb."""
 
-    def __init__(self, logn, q, wide):
+    def __init__(self, logn, q, chunk14):
         super().__init__(logn, 7, q)
-        self.LQ = lq_of(logn)
+        self.LQ, self.threads, wide = form(logn, chunk14)
         self.C = logn - self.LQ
         self.CL = 1 << self.C
         self.Q = 1 << self.LQ
@@ -99,7 +107,7 @@ class OnePass(Replay):
         sms = [[None] * self.padq for _ in range(CL)]
         if CL > 1:
             kJ = Q // CL
-            assert kJ % THREADS == 0
+            assert kJ % self.threads == 0
             for r in range(CL):
                 for t in range(kJ):
                     j = r * kJ + t
@@ -148,12 +156,12 @@ class OnePass(Replay):
         return out
 
 
-@pytest.mark.parametrize("logn,wide,bits", [(13, 1, 60), (13, 0, 40), (14, 1, 50), (14, 0, 61), (15, 1, 60),
-                                            (16, 1, 50), (16, 0, 60)])
-def test_onepass_forward_and_inverse(logn, wide, bits):
+@pytest.mark.parametrize("logn,chunk14,bits", [(13, 1, 60), (13, 0, 40), (14, 1, 50), (14, 0, 61), (15, 1, 60),
+                                               (15, 0, 50), (16, 1, 50), (16, 0, 60)])
+def test_onepass_forward_and_inverse(logn, chunk14, bits):
     q = largest_prime(bits, 2 << logn)
-    R = OnePass(logn, q, wide)
-    rng = random.Random(logn * 10 + wide)
+    R = OnePass(logn, q, chunk14)
+    rng = random.Random(logn * 10 + chunk14)
     a = [rng.randrange(q) for _ in range(R.n)]
     a[0], a[-1] = q - 1, q - 1
     got = R.forward(a)
