@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--profile-step", type=int, metavar="B", default=0,
                     help="run one batched step of B pairs between cudaProfilerStart/Stop (for ncu "
                          "--profile-from-start off) after two untimed ones, and exit")
+    ap.add_argument("--ntt-variant", type=int, default=-1,
+                    help="force HC_TUNE_NTT for the main step (0-2 two-pass block sizes, 3-4 single-pass) after tuning")
     ap.add_argument("--profile-cnn", action="store_true",
                     help="run one batched pass of the N=2^14 CNN between cudaProfilerStart/Stop, and exit")
     ap.add_argument("--probe-intmul", action="store_true",
@@ -879,8 +881,8 @@ def probe_intmul(H, W, torch, local):
     for form, (per_clk, per_s) in r.items():
         print("  %-12s %6.1f  %.3e" % (form, per_clk, per_s))
     lo, hi = r["mul_lo64"][0], r["mul_hi64"][0]
-    print("Shoup product (2 low + 1 high): %.2f per SM per clock" % (1.0 / (2.0 / lo + 1.0 / hi)))
-    print("64x64->128 multiply-add (1 low + 1 high): %.2f per SM per clock" % (1.0 / (1.0 / lo + 1.0 / hi)))
+    print("derived: Shoup product (2 low + 1 high): %.2f per SM per clock" % (1.0 / (2.0 / lo + 1.0 / hi)))
+    print("derived: 64x64->128 multiply-add (1 low + 1 high): %.2f per SM per clock" % (1.0 / (1.0 / lo + 1.0 / hi)))
 
 
 def run_gpu(args, rank, world, local):
@@ -913,6 +915,9 @@ def run_gpu(args, rank, world, local):
     sk, pk, evk = H.hc_keygen(ctx, seed)
     Bn = args.profile_step or args.batch
     tuning = None if (args.no_autotune or args.profile_step) else H.hc_autotune(ctx, evk, Bn)
+    if args.ntt_variant >= 0:
+        H.hc_tune_set(ctx, H.HC_TUNE_NTT, args.ntt_variant)
+        tuning = (tuning or "") + "forced ntt_variant %d\n" % args.ntt_variant
     A, Bc = [], []
     for i in range(Bn):
         for lst, off in ((A, 0), (Bc, 1)):

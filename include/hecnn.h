@@ -138,13 +138,15 @@ int hc_profile_names(hc_ctx *ctx, char *buf, size_t cap);
  * (6 x chunks; 0 if no such call was profiled). */
 int hc_profile_host_timeline(const hc_ctx *ctx, double *out, int cap);
 /* Integer-multiplier throughput of this GPU (measurement aid; the paper has
- * no counterpart: its timings are HElib's on CPUs).  Times five forms, each
- * as four independent dependency chains per thread over 8 blocks of 256
- * threads per SM: 32-bit multiply-add, 32-bit high half, 32 x 32 -> 64
- * multiply-add, 64-bit low product, 64-bit high product.  rates[0..4]
- * receive thread-operations per SM per clock at the device's maximum SM
- * clock, rates[5..9] thread-operations per second.  cap < 10 gives
- * HC_ERR_INVALID.  Uses a small buffer from the context allocator and
+ * no counterpart: its timings are HElib's on CPUs).  Times eight forms,
+ * each as four independent dependency chains per thread over 8 blocks of
+ * 256 threads per SM: 32-bit multiply-add, 32-bit high half, 32 x 32 -> 64
+ * multiply-add, 64-bit low product, 64-bit high product, 64 x 64 -> 128
+ * multiply-accumulate with carry (the tensor sums' step), lazy Shoup
+ * product by a constant, and Harvey's lazy Cooley-Tukey butterfly (the
+ * NTT's step).  rates[0..7] receive operations per SM per clock at the
+ * device's maximum SM clock, rates[8..15] operations per second.  cap < 16
+ * gives HC_ERR_INVALID.  Uses a small buffer from the context allocator and
  * synchronises the context stream.  The roofline of the modular arithmetic
  * (NTT butterflies, tensor accumulation) is derived from these rates. */
 int hc_int_mul_rates(hc_ctx *ctx, double *rates, int cap);

@@ -355,15 +355,18 @@ def hc_profile_host_timeline(ctx):
     return [tuple(buf[6 * c: 6 * c + 6]) for c in range(n // 6)]
 
 
-INT_MUL_FORMS = ("imad32", "umulhi32", "imad_wide32", "mul_lo64", "mul_hi64")
+INT_MUL_FORMS = ("imad32", "umulhi32", "imad_wide32", "mul_lo64", "mul_hi64", "mac128", "shoup_lazy",
+                 "ct_butterfly")
 
 
 def hc_int_mul_rates(ctx):
     """{form: (ops per SM per clock at the maximum clock, ops per second)} of
-    the integer-multiply forms, measured on the context's GPU."""
-    r = (ctypes.c_double * 10)()
-    _check(ctx, load().hc_int_mul_rates(ctx.ptr, r, 10))
-    return {f: (r[i], r[5 + i]) for i, f in enumerate(INT_MUL_FORMS)}
+    the integer-multiply forms and the modular units of work, measured on
+    the context's GPU."""
+    k = len(INT_MUL_FORMS)
+    r = (ctypes.c_double * (2 * k))()
+    _check(ctx, load().hc_int_mul_rates(ctx.ptr, r, 2 * k))
+    return {f: (r[i], r[k + i]) for i, f in enumerate(INT_MUL_FORMS)}
 
 
 def hc_keygen(ctx, seed, rot_steps=()):
