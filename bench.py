@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--paper-shape", action="store_true",
                     help="also run the paper's own network (N=2^15, 16384 images; ~80 GB of device memory)")
     ap.add_argument("--serve-requests", type=int, default=500, help="requests per arrival rate")
-    ap.add_argument("--serve-budget-mib", type=int, default=1024,
+    ap.add_argument("--serve-budget-mib", type=int, default=4096,
                     help="device-footprint budget of the serving loop's admission (MiB)")
     ap.add_argument("--profile-step", type=int, metavar="B", default=0,
                     help="run one batched step of B pairs between cudaProfilerStart/Stop (for ncu "
@@ -273,16 +273,22 @@ NCU_TRAFFIC_PER_UNIT = {
 }
 
 
-# Integer-multiplier roofline of the NTT passes: 64-bit low and high
-# products per SM per clock on GB300, measured by
-# paper_2102_00319_gb300/probes/intmul_throughput.cu.  A Shoup product (one
-# per butterfly) takes two low products and one high product.
-LO64_PER_SM_CLK = 14.4
-HI64_PER_SM_CLK = 6.6
+# Integer-multiplier roofline: 64-bit low and high products per SM per clock
+# on GB300, measured by `python bench.py --probe-intmul` (hc_int_mul_rates;
+# profiles/intmul_throughput_gb300.md).  A Shoup product (one per
+# butterfly) takes two low products and one high product; a 64 x 64 -> 128
+# multiply-add (the tensor accumulation's unit) one of each.  These derived
+# rates are the roofline peaks.
+LO64_PER_SM_CLK = 15.2
+HI64_PER_SM_CLK = 7.0
 MULMODS_PER_SM_CLK = 1.0 / (2.0 / LO64_PER_SM_CLK + 1.0 / HI64_PER_SM_CLK)
-# A 64 x 64 -> 128 multiply-add (the tensor accumulation's unit: one low and
-# one high product with their carries) at the same rates.
 MAC128_PER_SM_CLK = 1.0 / (1.0 / LO64_PER_SM_CLK + 1.0 / HI64_PER_SM_CLK)
+# The same probe times the units of work themselves (independent chains of
+# the exact instruction sequence): Harvey's lazy butterfly with its Shoup
+# product and the carry-chained 128-bit multiply-accumulate.  Reported beside
+# the derived peak as `unit_op` (what the arithmetic itself allows).
+BUTTERFLY_PER_SM_CLK = 2.8
+MAC128_CHAIN_PER_SM_CLK = 3.9
 
 
 # Busy share of the integer multiplier (ncu sm__pipe_fmaheavy_cycles_active,
@@ -382,13 +388,18 @@ def leg_roofline(kernels, n, dnum, clk, local, torch, pass_ms):
     if dom.startswith("ntt_") or dom == "k_tensor_acc":
         if dom == "k_tensor_acc":
             work, per_clk, unit = units * n * 3, MAC128_PER_SM_CLK, "G 64x64->128 multiply-adds/s"
+            unit_clk, unit_src = MAC128_CHAIN_PER_SM_CLK, "measured carry-chained 128-bit multiply-accumulate"
         else:
             work, per_clk, unit = units * mulmods_per_unit(dom, n), MULMODS_PER_SM_CLK, "G Shoup mulmod/s"
+            unit_clk, unit_src = BUTTERFLY_PER_SM_CLK, "measured lazy CT butterfly chains"
         peak = per_clk * sms * mhz * 1e6 / 1e9
+        unit_peak = unit_clk * sms * mhz * 1e6 / 1e9
         got = work / (tot / 1000.0) / 1e9
         out.update({"bound": "alu", "achieved": got, "peak": peak, "unit": unit, "frac": got / peak,
                     "traffic": None, "peak_source": "derived from measured 64-bit multiply rates: %.2f/SM/clk"
-                                                     " x %d SMs x %.0f MHz" % (per_clk, sms, mhz)})
+                                                     " x %d SMs x %.0f MHz" % (per_clk, sms, mhz),
+                    "unit_op": {"peak": unit_peak, "frac": got / unit_peak,
+                                "source": "%s: %.1f/SM/clk" % (unit_src, unit_clk)}})
     else:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
@@ -1112,10 +1123,13 @@ def run_gpu(args, rank, world, local):
         mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
         peak_alu = MULMODS_PER_SM_CLK * sms * mhz * 1e6 / 1e9
         got = units * mulmods_per_unit(dom, n) / (tot / 1000.0) / 1e9
+        unit_peak = BUTTERFLY_PER_SM_CLK * sms * mhz * 1e6 / 1e9
         roofline = {"bound": "alu", "kernel": dom, "achieved": got, "peak": peak_alu, "unit": "G Shoup mulmod/s",
                     "frac": got / peak_alu, "traffic": traffic,
                     "peak_source": "derived from measured 64-bit multiply rates: %.2f Shoup products/SM/clk"
                                    " x %d SMs x %.0f MHz" % (MULMODS_PER_SM_CLK, sms, mhz),
+                    "unit_op": {"peak": unit_peak, "frac": got / unit_peak,
+                                "source": "measured lazy CT butterfly chains: %.1f/SM/clk" % BUTTERFLY_PER_SM_CLK},
                     "hbm": hbm}
     else:
         roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -252,9 +252,21 @@ void modup_digits(hc_ctx* ctx, int level, const std::vector<CtRef>& xs, const u6
 // Key switching of a batch of single polynomials x (NTT form, level l):
 //   out_k = base_k + KS(x)_k,  k = 0, 1 (base_k may be null).
 // ---------------------------------------------------------------------
+// Per-item switching keys: keys[i] switches item i (runs of equal keys share
+// one key-product launch; every other stage is one launch over all items).
+void keyswitch_batch_keys(hc_ctx* ctx, const std::vector<const u64*>& keys, int level, const std::vector<CtRef>& x,
+                          const std::vector<CtRef>* base0, const std::vector<CtRef>* base1,
+                          const std::vector<CtRef>& out);
+
 void keyswitch_batch(hc_ctx* ctx, const u64* key, int level, const std::vector<CtRef>& x,
                      const std::vector<CtRef>* base0, const std::vector<CtRef>* base1,
                      const std::vector<CtRef>& out) {
+  keyswitch_batch_keys(ctx, std::vector<const u64*>(x.size(), key), level, x, base0, base1, out);
+}
+
+void keyswitch_batch_keys(hc_ctx* ctx, const std::vector<const u64*>& keys, int level, const std::vector<CtRef>& x,
+                          const std::vector<CtRef>* base0, const std::vector<CtRef>* base1,
+                          const std::vector<CtRef>& out) {
   const int n = ctx->P.n, alpha = ctx->P.alpha;
   const int nq = level + 1, next = nq + alpha, dnum = ctx->lv[level].dnum;
   const int total = (int)x.size();
@@ -289,7 +301,13 @@ void keyswitch_batch(hc_ctx* ctx, const u64* key, int level, const std::vector<C
     xin.nlimb = nq;
     launch_ntt_from(ctx, limbset_base(xc, x_is, 0, 1, nq, 0, nullptr), &xin, m, true, false);
     modup_digits(ctx, level, xs, xc, x_is, ext, ext_is, m, keep);
-    launch_key_product_batched(ctx, level, ext, ext_is, key, acc, acc_is, m, dnum <= 8 ? xr : nullptr);
+    for (int r0 = 0; r0 < m;) {  // one key-product launch per run of items sharing a key
+      int r1 = r0 + 1;
+      while (r1 < m && keys[s0 + r1] == keys[s0 + r0]) ++r1;
+      launch_key_product_batched(ctx, level, ext + (size_t)r0 * ext_is, ext_is, keys[s0 + r0],
+                                 acc + (size_t)r0 * acc_is, acc_is, r1 - r0, dnum <= 8 ? xr + r0 : nullptr);
+      r0 = r1;
+    }
     // ModDown
     launch_ntt(ctx, limbset_base(acc, acc_is, ext_words, 2, alpha, nq, emap), m, true, false);
     launch_moddown_bconv_fast(ctx, level, acc + (size_t)nq * n, acc_is, zq, z_is, m);
@@ -1641,21 +1659,28 @@ std::vector<hc_ct*> rotate_one(hc_ctx* ctx, const hc_evk* evk, const hc_ct* x, c
   std::vector<hc_ct*> outs = new_cts(ctx, (int)steps.size(), level, 1, x->scale);
   std::vector<BufPtr> keep;
   const CtRef* xr = refs_dev(ctx, {x->ref()}, keep);
-  BufPtr tmp = ctx->buffer(2 * (size_t)nq * n);
+  // kappa_g(x) of every step into one slab, then one key switch over the
+  // steps with each step's Galois key
+  int nrot = 0;
+  for (u64 g : gs) nrot += g != 1;
+  BufPtr tmp = ctx->buffer(std::max<size_t>(1, 2 * (size_t)nrot * nq * n));
   keep.push_back(tmp);
-  const CtRef tr{tmp->ptr, (u64)nq * n};
-  const CtRef* trd = refs_dev(ctx, {tr}, keep);
+  std::vector<CtRef> xs, b0, o;
+  std::vector<const u64*> ks;
   for (size_t i = 0; i < gs.size(); ++i) {
     const CtRef* od = refs_dev(ctx, {outs[i]->ref()}, keep);
     if (gs[i] == 1) {
       launch_ew(ctx, 3, od, xr, nullptr, 1, 2, nq);
       continue;
     }
-    launch_automorph(ctx, trd, xr, 1, 2, nq, gs[i]);
-    std::vector<CtRef> xs{CtRef{tmp->ptr + (size_t)nq * n, (u64)nq * n}}, b0{CtRef{tmp->ptr, (u64)nq * n}},
-        o{outs[i]->ref()};
-    keyswitch_batch(ctx, evk->galois.at(gs[i]).buf->ptr, level, xs, &b0, nullptr, o);
+    u64* base = tmp->ptr + xs.size() * 2 * (size_t)nq * n;
+    launch_automorph(ctx, refs_dev(ctx, {CtRef{base, (u64)nq * n}}, keep), xr, 1, 2, nq, gs[i]);
+    xs.push_back(CtRef{base + (size_t)nq * n, (u64)nq * n});
+    b0.push_back(CtRef{base, (u64)nq * n});
+    o.push_back(outs[i]->ref());
+    ks.push_back(evk->galois.at(gs[i]).buf->ptr);
   }
+  if (!xs.empty()) keyswitch_batch_keys(ctx, ks, level, xs, &b0, nullptr, o);
   return outs;
 }
 }  // namespace
@@ -2678,30 +2703,42 @@ extern "C" int hc_enc_conv2d_single_batch(hc_ctx* ctx, const hc_evk* evk, const 
       std::vector<BufPtr> keep;
       // rotated images, step-major: rot[t * G + g]
       std::vector<hc_ct*> rot = new_cts(ctx, T * G, level, 1, x[idx[0]]->scale);
-      BufPtr tmp = ctx->buffer(2 * (size_t)G * nq * n);
-      keep.push_back(tmp);
-      std::vector<CtRef> xr, tr, t0, t1;
+      std::vector<CtRef> xr;
       for (int gi = 0; gi < G; ++gi) {
         const hc_ct* c = x[idx[gi]];
         check_scales(c->scale, x[idx[0]]->scale);
         xr.push_back(c->ref());
-        u64* base = tmp->ptr + (size_t)gi * 2 * nq * n;
-        tr.push_back(CtRef{base, (u64)nq * n});
-        t0.push_back(CtRef{base, (u64)nq * n});
-        t1.push_back(CtRef{base + (size_t)nq * n, (u64)nq * n});
       }
       const CtRef* xrd = refs_dev(ctx, xr, keep);
-      const CtRef* trd = refs_dev(ctx, tr, keep);
+      // kappa_g of every image for every rotation step into one slab, then one
+      // key switch over all (step, image) items with each step's Galois key
+      int nrot = 0;
+      for (int t = 0; t < T; ++t) nrot += gs[t] != 1;
+      BufPtr tmp = ctx->buffer(std::max<size_t>(1, 2 * (size_t)nrot * G * nq * n));
+      keep.push_back(tmp);
+      std::vector<CtRef> t0, t1, o;
+      std::vector<const u64*> ks;
+      int nr = 0;  // rotation steps placed so far
       for (int t = 0; t < T; ++t) {
-        std::vector<CtRef> o;
-        for (int gi = 0; gi < G; ++gi) o.push_back(rot[t * G + gi]->ref());
+        std::vector<CtRef> ot;
+        for (int gi = 0; gi < G; ++gi) ot.push_back(rot[t * G + gi]->ref());
         if (gs[t] == 1) {
-          launch_ew(ctx, 3, refs_dev(ctx, o, keep), xrd, nullptr, G, 2, nq);
+          launch_ew(ctx, 3, refs_dev(ctx, ot, keep), xrd, nullptr, G, 2, nq);
           continue;
         }
-        launch_automorph(ctx, trd, xrd, G, 2, nq, gs[t]);
-        keyswitch_batch(ctx, evk->galois.at(gs[t]).buf->ptr, level, t1, &t0, nullptr, o);
+        std::vector<CtRef> tr;
+        for (int gi = 0; gi < G; ++gi) {
+          u64* base = tmp->ptr + ((size_t)nr * G + gi) * 2 * nq * n;
+          tr.push_back(CtRef{base, (u64)nq * n});
+          t0.push_back(CtRef{base, (u64)nq * n});
+          t1.push_back(CtRef{base + (size_t)nq * n, (u64)nq * n});
+          o.push_back(ot[gi]);
+          ks.push_back(evk->galois.at(gs[t]).buf->ptr);
+        }
+        launch_automorph(ctx, refs_dev(ctx, tr, keep), xrd, G, 2, nq, gs[t]);
+        ++nr;
       }
+      if (!o.empty()) keyswitch_batch_keys(ctx, ks, level, t1, &t0, nullptr, o);
       // weights viewed at this level
       std::vector<hc_ct*> wv;
       std::vector<const hc_ct*> ws;

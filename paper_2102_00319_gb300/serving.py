@@ -53,17 +53,20 @@ class Request:
 
 def footprint_bytes(model: Model, level: int) -> int:
     """Device bytes one request holds while in flight: input, kh*kw rotated
-    copies, tensor outputs, key-switch workspace and the outputs."""
+    copies, the kh*kw - 1 automorphed copies and their key-switch workspaces
+    (the rotations of a step run as one batched key switch), tensor outputs
+    and the outputs."""
     n, nq = model.n, level + 1
     alpha = model.n_special
     nxt = nq + alpha
     dnum = -(-nq // alpha)
     limb = 8 * n
     ct = 2 * nq * limb
-    rotated = model.kh * model.kw * ct
+    taps = model.kh * model.kw
+    rotated = taps * ct
     ks = (nq + dnum * nxt + 2 * nxt + 2 * nq + 2) * limb
     outs = 3 * nq * limb + 2 * ct
-    return ct + rotated + ks + outs
+    return ct + rotated + (taps - 1) * (ct + ks) + outs
 
 
 @dataclass

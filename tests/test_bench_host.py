@@ -29,9 +29,15 @@ def test_butterfly_and_mulmod_counts(bench):
 
 
 def test_multiplier_peak_from_measured_rates(bench):
-    # 1 / (2/14.4 + 1/6.6) Shoup products per SM per clock
-    assert abs(bench.MULMODS_PER_SM_CLK - 3.4435) < 1e-3
-    assert abs(bench.MULMODS_PER_SM_CLK * 152 * 2070e6 / 1e9 - 1083.46) < 0.1
+    # 1 / (2/15.2 + 1/7.0) Shoup products and 1 / (1/15.2 + 1/7.0) 128-bit
+    # multiply-adds per SM per clock
+    assert abs(bench.MULMODS_PER_SM_CLK - 1.0 / (2 / 15.2 + 1 / 7.0)) < 1e-12
+    assert abs(bench.MULMODS_PER_SM_CLK - 3.6438) < 1e-3
+    assert abs(bench.MULMODS_PER_SM_CLK * 152 * 2070e6 / 1e9 - 1146.50) < 0.1
+    assert abs(bench.MAC128_PER_SM_CLK - 4.7928) < 1e-3
+    # the measured unit-of-work rates sit below the derived ones
+    assert bench.BUTTERFLY_PER_SM_CLK < bench.MULMODS_PER_SM_CLK
+    assert bench.MAC128_CHAIN_PER_SM_CLK < bench.MAC128_PER_SM_CLK
 
 
 def test_bytes_per_unit(bench):
