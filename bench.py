@@ -260,9 +260,9 @@ def run_reference(args, rank, world):
 # domain), per kernel; dnum = 3 at the top level of this workload.
 # DRAM bytes (read + write) per work unit from one ncu capture of the same
 # kernel version on a smaller batch (one step of 16 pairs run by
-# paper_2102_00319_gb300/probes/one_step.py: 336 limbs per ModUp transform
-# launch, 640 per fused-tail launch), scaled to a launch by its units.  A
-# kernel without an entry reports no traffic; an entry goes when its kernel
+# `python bench.py --profile-step 16`: 336 limbs per ModUp transform launch,
+# 640 per fused-tail launch), scaled to a launch by its units.  A kernel
+# without an entry reports no traffic; an entry goes when its kernel
 # changes, until it is captured again.
 NCU_NTT_VARIANT = 1  # block size (HC_TUNE_NTT) of the NTT capture below
 NCU_TRAFFIC_PER_UNIT = {
@@ -688,7 +688,7 @@ def uneven_leg(H, W, np, torch, local):
     t_op, r_op = timed(per_op, 1)
     t_inst, r_inst = timed(per_instance, 2)
     t_b, r_b = timed(batched, 3)
-    H.hc_graph_begin(order, 8 << 30)
+    H.hc_graph_begin(order, 32 << 30)
     r_g = batched()
     g = H.hc_graph_end(order)
     t_g, _ = timed(lambda: H.hc_graph_launch(g), 5)
@@ -706,7 +706,7 @@ def uneven_leg(H, W, np, torch, local):
     for log_n, ctx in ctxs.items():
         n_i = sum(1 for ln, _ in inst if ln == log_n)
         tuning["N=2^%d" % log_n] = H.hc_autotune(ctx, keys[log_n][2], max(1, n_i))
-    H.hc_graph_begin(order, 8 << 30)
+    H.hc_graph_begin(order, 32 << 30)
     r_t = batched()
     gt = H.hc_graph_end(order)
     t_t, _ = timed(lambda: H.hc_graph_launch(gt), 5)

@@ -103,7 +103,7 @@ def test_uneven_batched_and_graph_match_per_instance(setup):
         for i in range(len(ref)):
             assert np.array_equal(export(S, i, got[i]), export(S, i, ref[i])), (mixed, i)
     ctx_list = [S["ctxs"][k] for k in (13, 14, 15)]
-    H.hc_graph_begin(ctx_list, 8 << 30)
+    H.hc_graph_begin(ctx_list, 32 << 30)
     cap = run_batched(S)
     g = H.hc_graph_end(ctx_list)
     for rep in range(2):
@@ -158,7 +158,7 @@ def test_uneven_graph_with_a_stream_per_ring_degree(setup):
     for i in range(len(got)):
         assert np.array_equal(export(M, i, got[i]), ref_words[i]), i
     ctx_list = [M["ctxs"][k] for k in (13, 14, 15)]
-    H.hc_graph_begin(ctx_list, 8 << 30)
+    H.hc_graph_begin(ctx_list, 32 << 30)
     cap = run_batched(M)
     g = H.hc_graph_end(ctx_list)
     for rep in range(2):
