@@ -1052,7 +1052,7 @@ def run_gpu(args, rank, world, local):
         return H.hc_mul_relin_rescale_host(ctx, evk, in_arrays[:Bn], in_metas[:Bn], in_arrays[Bn:], in_metas[Bn:],
                                            out_arrays, chunk=args.e2e_chunk)
 
-    for _ in range(3 if args.e2e_steps > 0 else 0):  # untimed: the memory pool reaches its steady size
+    for _ in range(5 if args.e2e_steps > 0 else 0):  # untimed: the memory pool reaches its steady size
         e2e_step()
     # the plain pinned-copy rates of the same buffers on this machine, for reading
     # the e2e number (the host link is shared with the box's other GPUs)
@@ -1078,21 +1078,21 @@ def run_gpu(args, rank, world, local):
     barrier()
     t0 = time.perf_counter()
     e2e_marks = []  # each call returns with its outputs in host memory
+    e2e_calls = []  # per call, from its event timeline: (copies in, kernels, device span) in ms
     for _ in range(args.e2e_steps):
         e2e_step()
         e2e_marks.append(time.perf_counter())
+        tl = H.hc_profile_host_timeline(ctx)
+        if tl:
+            e2e_calls.append([round(tl[-1][1] - tl[0][0], 2), round(sum(c[3] - c[2] for c in tl), 2),
+                              round(tl[-1][5], 2)])
     barrier()
     t_e2e = max_over_ranks(max(time.perf_counter() - t0, 1e-9), device="cuda")
     e2e_step_ms = [round(1000.0 * (b - a), 2) for a, b in zip([t0] + e2e_marks[:-1], e2e_marks)]
     e2e_value = Bn * args.e2e_steps * world / t_e2e if args.e2e_steps > 0 else None
-    e2e_timeline = None
-    if args.e2e_steps > 0:
-        # one more call with events around each chunk's copies in, kernels and
-        # copies out (ms from the call's start), to read the overlap from
-        H.hc_profile_enable(ctx, True)
-        e2e_step()
-        e2e_timeline = [[round(v, 2) for v in c] for c in H.hc_profile_host_timeline(ctx)]
-        H.hc_profile_enable(ctx, False)
+    # the last timed call's events around each chunk's copies in, kernels and
+    # copies out (ms from the call's start), to read the overlap from
+    e2e_timeline = [[round(v, 2) for v in c] for c in H.hc_profile_host_timeline(ctx)] if args.e2e_steps else None
     if args.e2e_steps > 0:  # the host-side result decrypts to the product
         m0 = e2e_step()[0]
         back = H.hc_ct_import(ctx, out_arrays[0], m0.level, m0.degree, m0.scale)
@@ -1153,6 +1153,8 @@ def run_gpu(args, rank, world, local):
                        "step_ms_min_max": [min(e2e_step_ms), max(e2e_step_ms)] if e2e_step_ms else None,
                        "ops_per_s_at_median": Bn / statistics.median(e2e_step_ms) * 1000 if e2e_step_ms else None,
                        "chunk_timeline_ms": e2e_timeline,
+                       "per_call_device_ms": e2e_calls,
+                       "per_call_fields": "copies in span, sum of chunk kernel spans, device span (events)",
                        "chunk_timeline_fields": "per chunk: copy-in start, end, kernels start, end, copy-out start, end"},
         "kernels": kern_summary, "tuning": tuning,
         "forms": {"graph": graph_value, "eager": eager_value, "unit": UNIT,

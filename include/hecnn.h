@@ -130,12 +130,12 @@ int hc_profile_kernel(hc_ctx *ctx, const char *name, uint64_t *launches, double 
                       uint64_t *units);
 /* Names of the kernels recorded, comma separated, into buf[cap]. */
 int hc_profile_names(hc_ctx *ctx, char *buf, size_t cap);
-/* Timeline of the last hc_mul_relin_rescale_host call made while profiling
- * was enabled: for each pipeline chunk c, out[6c .. 6c+5] = milliseconds
+/* Timeline of the last hc_mul_relin_rescale_host call on this context: for
+ * each pipeline chunk c, out[6c .. 6c+5] = milliseconds
  * from the call's start to the start and end of the chunk's copies in, of
  * its kernels and of its copies out (CUDA events on the three streams).
  * Writes min(count, cap) values (out may be NULL) and returns the count
- * (6 x chunks; 0 if no such call was profiled). */
+ * (6 x chunks; 0 before the first such call). */
 int hc_profile_host_timeline(const hc_ctx *ctx, double *out, int cap);
 /* Integer-multiplier throughput of this GPU (measurement aid; the paper has
  * no counterpart: its timings are HElib's on CPUs).  Times eight forms,

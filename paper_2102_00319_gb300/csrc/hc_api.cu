@@ -844,6 +844,11 @@ extern "C" void hc_ctx_destroy(hc_ctx* ctx) {
     cudaStreamSynchronize(st);
     cudaStreamDestroy(st);
   }
+  for (cudaStream_t st : ctx->copy_streams)
+    if (st) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
   delete ctx;
 }
 
@@ -1958,17 +1963,20 @@ extern "C" int hc_mul_relin_rescale_host(hc_ctx* ctx, const hc_evk* evk, const u
     const int nch = (int)sizes.size();
     std::vector<int> first(nch + 1, 0);  // pair index of each chunk's first pair
     for (int c = 0; c < nch; ++c) first[c + 1] = first[c] + sizes[c];
-    HC_CUDA(cudaStreamCreateWithFlags(&h2d, cudaStreamNonBlocking));
-    HC_CUDA(cudaStreamCreateWithFlags(&d2h, cudaStreamNonBlocking));
+    // the copy streams live as long as the context (no stream creation per call)
+    for (cudaStream_t& st : ctx->copy_streams)
+      if (!st) HC_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    h2d = ctx->copy_streams[0];
+    d2h = ctx->copy_streams[1];
     auto event = [&]() {
       cudaEvent_t e;
       HC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
       evs.push_back(e);
       return e;
     };
-    // with profiling on: timing events around each chunk's copies in, its
-    // kernels and its copies out, relative to the call's start
-    const bool tl = ctx->prof;
+    // timing events around each chunk's copies in, its kernels and its copies
+    // out, relative to the call's start (read back by hc_profile_host_timeline)
+    const bool tl = true;  // 48 events per call: cheap, and every call's timeline can be read back
     std::vector<cudaEvent_t> tev;  // [chunk][h2d b, h2d e, compute b, compute e, d2h b, d2h e], then the start
     auto tmark = [&](cudaStream_t st) -> cudaEvent_t {
       cudaEvent_t e;
@@ -2055,8 +2063,6 @@ extern "C" int hc_mul_relin_rescale_host(hc_ctx* ctx, const hc_evk* evk, const u
   keep.clear();
   for (auto& v : ins) free_all(v);
   for (cudaEvent_t e : evs) cudaEventDestroy(e);
-  if (h2d) cudaStreamDestroy(h2d);
-  if (d2h) cudaStreamDestroy(d2h);
   return rc;
 }
 

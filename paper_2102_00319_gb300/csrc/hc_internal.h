@@ -99,8 +99,8 @@ struct hc_ctx {
   std::map<std::string, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>> prof_events;
   std::map<std::string, uint64_t> prof_units;
   std::vector<cudaEvent_t> event_pool;
-  // the last profiled host-to-host call: per chunk, ms from the call's start
-  // to the start and end of its copies in, its kernels and its copies out
+  // the last host-to-host call: per chunk, ms from the call's start to the
+  // start and end of its copies in, its kernels and its copies out
   std::vector<double> host_timeline;
   // capture arena: while set, buffer() bump-allocates here instead of the allocator
   u64* arena = nullptr;
@@ -110,6 +110,8 @@ struct hc_ctx {
   std::vector<cudaStream_t> capture_joined;
   // side streams of fork_join (created on first use, destroyed with the context)
   std::vector<cudaStream_t> aux_streams;
+  // copy-in and copy-out streams of the host-to-host call (created on first use)
+  cudaStream_t copy_streams[2] = {nullptr, nullptr};
   std::vector<cudaEvent_t> capture_events;
 
   u64* alloc_words(size_t words);
