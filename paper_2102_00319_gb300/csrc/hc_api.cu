@@ -1974,6 +1974,10 @@ extern "C" int hc_mul_relin_rescale_host(hc_ctx* ctx, const hc_evk* evk, const u
       evs.push_back(e);
       return e;
     };
+    // the second compute stream starts after the work already on the context stream
+    const cudaEvent_t start2 = event();
+    HC_CUDA(cudaEventRecord(start2, ctx->stream));
+    HC_CUDA(cudaStreamWaitEvent(ctx->copy_streams[2], start2, 0));
     // timing events around each chunk's copies in, its kernels and its copies
     // out, relative to the call's start (read back by hc_profile_host_timeline)
     const bool tl = true;  // 48 events per call: cheap, and every call's timeline can be read back
@@ -2012,6 +2016,15 @@ extern "C" int hc_mul_relin_rescale_host(hc_ctx* ctx, const hc_evk* evk, const u
     for (int c = 0; c < nch; ++c) {
       std::vector<hc_ct*>& x = ins[c];
       const int m = (int)x.size() / 2;
+      // odd chunks compute on a second stream, so one chunk's kernels fill the
+      // other's last waves (their buffers are disjoint; outputs are ordered by
+      // the copy-out stream's waits)
+      struct StreamSwap {
+        hc_ctx* c;
+        cudaStream_t home;
+        ~StreamSwap() { c->stream = home; }
+      } swap{ctx, ctx->stream};
+      if (c % 2 == 1) ctx->stream = ctx->copy_streams[2];
       HC_CUDA(cudaStreamWaitEvent(ctx->stream, copied[c], 0));
       if (tl) tev[6 * c + 2] = tmark(ctx->stream);
       launch_check_range(ctx, x[0]->data, 4 * m, level + 1, stride, (unsigned long long*)(flags->ptr + c));
@@ -2040,6 +2053,7 @@ extern "C" int hc_mul_relin_rescale_host(hc_ctx* ctx, const hc_evk* evk, const u
                                 cudaMemcpyDeviceToHost, d2h));
       if (tl) tev[6 * c + 5] = tmark(d2h);
     }
+    // (the context stream is restored at the end of every chunk)
     // staged buffers go back to the pool only after the copies out
     const cudaEvent_t drained = event();
     HC_CUDA(cudaEventRecord(drained, d2h));
@@ -2060,6 +2074,7 @@ extern "C" int hc_mul_relin_rescale_host(hc_ctx* ctx, const hc_evk* evk, const u
   // on an error the side streams may still be writing into inputs: drain them first
   if (h2d) cudaStreamSynchronize(h2d);
   if (d2h) cudaStreamSynchronize(d2h);
+  if (ctx->copy_streams[2]) cudaStreamSynchronize(ctx->copy_streams[2]);
   keep.clear();
   for (auto& v : ins) free_all(v);
   for (cudaEvent_t e : evs) cudaEventDestroy(e);

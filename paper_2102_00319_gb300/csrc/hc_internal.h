@@ -110,8 +110,9 @@ struct hc_ctx {
   std::vector<cudaStream_t> capture_joined;
   // side streams of fork_join (created on first use, destroyed with the context)
   std::vector<cudaStream_t> aux_streams;
-  // copy-in and copy-out streams of the host-to-host call (created on first use)
-  cudaStream_t copy_streams[2] = {nullptr, nullptr};
+  // copy-in, copy-out and second compute stream of the host-to-host call
+  // (created on first use)
+  cudaStream_t copy_streams[3] = {nullptr, nullptr, nullptr};
   std::vector<cudaEvent_t> capture_events;
 
   u64* alloc_words(size_t words);
