@@ -73,6 +73,8 @@ def parse():
                     help="run one batched pass of the N=2^14 CNN between cudaProfilerStart/Stop, and exit")
     ap.add_argument("--probe-intmul", action="store_true",
                     help="print the integer-multiply throughputs of this GPU (hc_int_mul_rates), and exit")
+    ap.add_argument("--probe-tc-conversion", action="store_true",
+                    help="time the pieces of a split-integer tensor-core ModUp conversion against the IMAD one, and exit")
     ap.add_argument("--summarize-ncu", metavar="CSV",
                     help="summarise an ncu launch list (gpu__time_duration.sum) of the timed step and exit")
     ap.add_argument("--step-occurrence", type=int, default=2,
@@ -896,6 +898,55 @@ def probe_intmul(H, W, torch, local):
     print("derived: 64x64->128 multiply-add (1 low + 1 high): %.2f per SM per clock" % (1.0 / (1.0 / lo + 1.0 / hi)))
 
 
+def probe_tc_conversion(H, W, np, torch, local):
+    """One ModUp digit at N = 2^16, L = 20 (7 inputs -> 21 outputs per
+    coefficient) for 16 items, three ways: the library's IMAD conversion
+    (k_modup_bconv, per-kernel events in a batched step), the split-integer
+    GEMM a tensor-core form would run ((16 N) x 56 bytes times 56 x 315:
+    8-bit chunks in bf16, fp32 partial sums; cuBLAS through torch, output
+    written to memory), and the per-output epilogue such a form would need
+    on top (hc_int_mul_rates' split_conv_epilogue: no memory traffic)."""
+    ps = W.DEEP_N16
+    params = H.hc_params_create(ps.log_n, list(ps.q_bits), list(ps.p_bits), ps.log2_scale)
+    stream = torch.cuda.Stream(device=local)
+    torch.cuda.set_stream(stream)
+    ctx = H.hc_ctx_create(params, local, stream.cuda_stream)
+    n, L, items = ctx.n, ctx.L, 16
+    sk, pk, evk = H.hc_keygen(ctx, 7)
+    cts = [H.hc_encrypt(ctx, pk, H.hc_encode(ctx, W.slot_values(i, n // 2), 2.0 ** ps.log2_scale, L), 17, i)
+           for i in range(2 * items)]
+    for _ in range(2):
+        H.hc_mul_relin_rescale_batch(ctx, evk, cts[:items], cts[items:])
+    H.hc_sync(ctx)
+    H.hc_profile_enable(ctx, True)
+    H.hc_mul_relin_rescale_batch(ctx, evk, cts[:items], cts[items:])
+    H.hc_sync(ctx)
+    cnt, ms, units = H.hc_profile_kernel(ctx, "k_modup_bconv")
+    H.hc_profile_enable(ctx, False)
+    imad_outputs_per_s = units * n / (ms / 1000.0)
+    M, K, Nn = items * n, 56, 315
+    a = torch.randint(0, 256, (M, K), device="cuda").to(torch.bfloat16)
+    b = torch.randint(0, 256, (K, Nn), device="cuda").to(torch.bfloat16)
+    for _ in range(3):
+        c = a @ b
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(10):
+        c = a @ b
+    e1.record(stream)
+    torch.cuda.synchronize()
+    gemm_us = 1000.0 * e0.elapsed_time(e1) / 10
+    epi = H.hc_int_mul_rates(ctx)["split_conv_epilogue"][1]
+    digit_outputs = items * n * 21
+    print("one ModUp digit, 16 items at N = 2^16 (%d output residues):" % digit_outputs)
+    print("  IMAD conversion (k_modup_bconv):        %7.1f us  (%.1f G outputs/s, %d launches)"
+          % (1e6 * digit_outputs / imad_outputs_per_s, imad_outputs_per_s / 1e9, cnt))
+    print("  split-integer GEMM, bf16 (cuBLAS):      %7.1f us  (%.1f TFLOP/s, %.0f MB of partial sums)"
+          % (gemm_us, 2 * M * K * Nn / gemm_us / 1e6, c.numel() * c.element_size() / 1e6))
+    print("  its epilogue alone (no memory traffic): %7.1f us  (%.1f G outputs/s)"
+          % (1e6 * digit_outputs / epi, epi / 1e9))
+
+
 def run_gpu(args, rank, world, local):
     import numpy as np
     import torch
@@ -908,6 +959,9 @@ def run_gpu(args, rank, world, local):
     torch.cuda.set_device(local)
     if args.probe_intmul:
         probe_intmul(H, W, torch, local)
+        return
+    if args.probe_tc_conversion:
+        probe_tc_conversion(H, W, np, torch, local)
         return
     if args.profile_cnn:
         cnn_leg(args, H, W, np, torch, local, profile_only=True)

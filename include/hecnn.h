@@ -143,10 +143,12 @@ int hc_profile_host_timeline(const hc_ctx *ctx, double *out, int cap);
  * 256 threads per SM: 32-bit multiply-add, 32-bit high half, 32 x 32 -> 64
  * multiply-add, 64-bit low product, 64-bit high product, 64 x 64 -> 128
  * multiply-accumulate with carry (the tensor sums' step), lazy Shoup
- * product by a constant, and Harvey's lazy Cooley-Tukey butterfly (the
- * NTT's step).  rates[0..7] receive operations per SM per clock at the
- * device's maximum SM clock, rates[8..15] operations per second.  cap < 16
- * gives HC_ERR_INVALID.  Uses a small buffer from the context allocator and
+ * product by a constant, Harvey's lazy Cooley-Tukey butterfly (the NTT's
+ * step), and the epilogue of a split-integer (tensor-core) basis
+ * conversion per output residue: 15 fp32 partial sums to integers, their
+ * 128-bit assembly and its reduction.  rates[0..8] receive operations per
+ * SM per clock at the device's maximum SM clock, rates[9..17] operations
+ * per second.  cap < 18 gives HC_ERR_INVALID.  Uses a small buffer from the context allocator and
  * synchronises the context stream.  The roofline of the modular arithmetic
  * (NTT butterflies, tensor accumulation) is derived from these rates. */
 int hc_int_mul_rates(hc_ctx *ctx, double *rates, int cap);
@@ -275,9 +277,10 @@ int hc_mul_relin_rescale_batch(hc_ctx *ctx, const hc_evk *evk, const hc_ct *cons
  * (a_meta/b_meta give level, degree and scale); out_host[k] (capacity
  * out_cap[k] words >= 2 level N) receives the product, rescaled, in the same
  * layout, and out_meta[k] its metadata.  The batch runs as a pipeline of
- * chunks of `chunk` pairs (0: about an eighth of n): copies in, the batched
- * operation and copies out of successive chunks overlap on separate CUDA
- * streams; chunk < 0 gives HC_ERR_INVALID.  The relinearise + rescale tail
+ * chunks of `chunk` pairs (0: about a sixteenth of n from 32 pairs up, an
+ * eighth below): copies in, the batched operation and copies out of
+ * successive chunks overlap on separate CUDA streams, the chunks' kernels
+ * round-robin over HC_TUNE_HOST_STREAMS streams; chunk < 0 gives HC_ERR_INVALID.  The relinearise + rescale tail
  * is formed in coefficient form (one inverse transform per output limb, no
  * forward one), with the same words as hc_mul_relin_rescale_batch followed
  * by hc_ct_export.  Pinned host buffers are needed for the overlap.  Inputs
@@ -334,6 +337,10 @@ int hc_relin_noalloc(hc_ctx *ctx, const hc_evk *evk, const hc_ct *x, hc_ct *out)
  *                           g outputs sharing their x operands per thread
  *                           (a conv position's channels, an FC's classes),
  *                           each x word loaded once; not timed by
+ *                           hc_autotune;
+ *   HC_TUNE_HOST_STREAMS    hc_mul_relin_rescale_host: its chunks' kernels
+ *                           round-robin over 1..4 streams (default 2: the
+ *                           context stream and one more); not timed by
  *                           hc_autotune.
  * hc_autotune times each knob's candidates on scratch data shaped like
  * `items` ciphertext pairs at the top level (one knob at a time, the others
@@ -344,7 +351,8 @@ int hc_relin_noalloc(hc_ctx *ctx, const hc_evk *evk, const hc_ct *x, hc_ct *out)
  * microseconds per launch of every candidate.  Not capturable; it
  * synchronises the context stream.
  */
-enum { HC_TUNE_NTT = 0, HC_TUNE_KEY_PRODUCT_Z = 1, HC_TUNE_MODUP_SPLIT = 2, HC_TUNE_TENSOR_GROUP = 3 };
+enum { HC_TUNE_NTT = 0, HC_TUNE_KEY_PRODUCT_Z = 1, HC_TUNE_MODUP_SPLIT = 2, HC_TUNE_TENSOR_GROUP = 3,
+       HC_TUNE_HOST_STREAMS = 4 };
 int hc_autotune(hc_ctx *ctx, const hc_evk *evk, int items, char *report, size_t cap);
 int hc_tune_set(hc_ctx *ctx, int knob, int value);
 /* The knob's current value, or a negative error code. */

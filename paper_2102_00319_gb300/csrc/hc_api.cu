@@ -1784,6 +1784,10 @@ extern "C" int hc_tune_set(hc_ctx* ctx, int knob, int value) {
         HC_CHECK(value >= 0 && value <= 5, HC_ERR_INVALID, "tensor group must be 0..5");
         ctx->tune.tensor_group = value;
         break;
+      case HC_TUNE_HOST_STREAMS:
+        HC_CHECK(value >= 1 && value <= 4, HC_ERR_INVALID, "host streams must be 1..4");
+        ctx->tune.host_streams = value;
+        break;
       default:
         throw HcError{HC_ERR_INVALID, "unknown tuning knob"};
     }
@@ -1797,6 +1801,7 @@ extern "C" int hc_tune_get(const hc_ctx* ctx, int knob) {
     case HC_TUNE_KEY_PRODUCT_Z: return ctx->tune.kp_zmul;
     case HC_TUNE_MODUP_SPLIT: return ctx->tune.modup_split;
     case HC_TUNE_TENSOR_GROUP: return ctx->tune.tensor_group;
+    case HC_TUNE_HOST_STREAMS: return ctx->tune.host_streams;
     default: return HC_ERR_INVALID;
   }
 }
@@ -1923,7 +1928,9 @@ namespace {
 // small chunks at both ends (shorter exposed first copy in and last copy
 // out) gained nothing, the small chunks costing as much as they hide.
 std::vector<int> host_chunks(int n, int chunk) {
-  const int m = chunk > 0 ? chunk : std::max(1, (n + 7) / 8);
+  // automatic: sixteen chunks from 32 pairs up (measured best with the
+  // chunks' kernels on two streams: 4 pairs of 64), about eight below
+  const int m = chunk > 0 ? chunk : (n >= 32 ? (n + 15) / 16 : std::max(1, (n + 7) / 8));
   std::vector<int> sizes;
   for (int r = n; r > 0; r -= m) sizes.push_back(std::min(m, r));
   return sizes;
@@ -1974,10 +1981,11 @@ extern "C" int hc_mul_relin_rescale_host(hc_ctx* ctx, const hc_evk* evk, const u
       evs.push_back(e);
       return e;
     };
-    // the second compute stream starts after the work already on the context stream
+    // the extra compute streams start after the work already on the context stream
+    const int ncs = std::max(1, std::min(4, ctx->tune.host_streams));
     const cudaEvent_t start2 = event();
     HC_CUDA(cudaEventRecord(start2, ctx->stream));
-    HC_CUDA(cudaStreamWaitEvent(ctx->copy_streams[2], start2, 0));
+    for (int k = 2; k < 1 + ncs; ++k) HC_CUDA(cudaStreamWaitEvent(ctx->copy_streams[k], start2, 0));
     // timing events around each chunk's copies in, its kernels and its copies
     // out, relative to the call's start (read back by hc_profile_host_timeline)
     const bool tl = true;  // 48 events per call: cheap, and every call's timeline can be read back
@@ -2016,15 +2024,16 @@ extern "C" int hc_mul_relin_rescale_host(hc_ctx* ctx, const hc_evk* evk, const u
     for (int c = 0; c < nch; ++c) {
       std::vector<hc_ct*>& x = ins[c];
       const int m = (int)x.size() / 2;
-      // odd chunks compute on a second stream, so one chunk's kernels fill the
-      // other's last waves (their buffers are disjoint; outputs are ordered by
-      // the copy-out stream's waits)
+      // chunks round-robin over the compute streams (the context stream and
+      // ncs - 1 others), so one chunk's kernels fill the previous one's last
+      // waves (their buffers are disjoint; outputs are ordered by the
+      // copy-out stream's waits)
       struct StreamSwap {
         hc_ctx* c;
         cudaStream_t home;
         ~StreamSwap() { c->stream = home; }
       } swap{ctx, ctx->stream};
-      if (c % 2 == 1) ctx->stream = ctx->copy_streams[2];
+      if (c % ncs != 0) ctx->stream = ctx->copy_streams[1 + c % ncs];
       HC_CUDA(cudaStreamWaitEvent(ctx->stream, copied[c], 0));
       if (tl) tev[6 * c + 2] = tmark(ctx->stream);
       launch_check_range(ctx, x[0]->data, 4 * m, level + 1, stride, (unsigned long long*)(flags->ptr + c));
@@ -2074,7 +2083,8 @@ extern "C" int hc_mul_relin_rescale_host(hc_ctx* ctx, const hc_evk* evk, const u
   // on an error the side streams may still be writing into inputs: drain them first
   if (h2d) cudaStreamSynchronize(h2d);
   if (d2h) cudaStreamSynchronize(d2h);
-  if (ctx->copy_streams[2]) cudaStreamSynchronize(ctx->copy_streams[2]);
+  for (int k = 2; k < 5; ++k)
+    if (ctx->copy_streams[k]) cudaStreamSynchronize(ctx->copy_streams[k]);
   keep.clear();
   for (auto& v : ins) free_all(v);
   for (cudaEvent_t e : evs) cudaEventDestroy(e);

@@ -76,6 +76,7 @@ struct HcTune {
   int kp_zmul = 1;           // key product: item groups in the grid's z, times the default
   int modup_split = 1;       // ModUp conversion: output primes split over this many blocks
   int tensor_group = 5;      // tensor accumulation: 0 = per output, g = up to g outputs sharing x loads
+  int host_streams = 2;      // host-to-host call: chunks' kernels round-robin over this many streams (1..4)
 };
 
 struct hc_ctx {
@@ -110,9 +111,9 @@ struct hc_ctx {
   std::vector<cudaStream_t> capture_joined;
   // side streams of fork_join (created on first use, destroyed with the context)
   std::vector<cudaStream_t> aux_streams;
-  // copy-in, copy-out and second compute stream of the host-to-host call
-  // (created on first use)
-  cudaStream_t copy_streams[3] = {nullptr, nullptr, nullptr};
+  // copy-in and copy-out streams of the host-to-host call, then its extra
+  // compute streams (created on first use)
+  cudaStream_t copy_streams[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   std::vector<cudaEvent_t> capture_events;
 
   u64* alloc_words(size_t words);

@@ -10,16 +10,19 @@
 namespace {
 
 constexpr int kProbeIters = 4096;
-constexpr int kProbeForms = 8;
+constexpr int kProbeForms = 9;
 
 template <int KIND>
 __global__ void k_probe_chains(u64* out, u64 c, u64 d) {
   u64 x0 = threadIdx.x + 1, x1 = x0 * 3, x2 = x0 * 5, x3 = x0 * 7;
   u32 a0 = (u32)x0, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3;
   const u32 cc = (u32)c, dd = (u32)d;
-  // the Shoup constant of w = c mod d (forms 6 and 7), outside the timed loop's body
-  const u64 w = KIND >= 6 ? c % d : 0;
+  // constants outside the timed loop's body: w = c mod d (forms 6, 7) or
+  // 2^64 mod d (form 8) with its Shoup companion, floor(2^64 / d) (form 8)
+  const unsigned __int128 two64 = (unsigned __int128)1 << 64;
+  const u64 w = KIND == 8 ? (u64)(two64 % d) : (KIND >= 6 ? c % d : 0);
   const u64 wsh = KIND >= 6 ? (u64)(((unsigned __int128)w << 64) / d) : 0;
+  const u64 onesh = KIND == 8 ? (u64)(two64 / d) : 0;
   const u64 q2 = 2 * d;
 #pragma unroll 8
   for (int i = 0; i < kProbeIters; ++i) {
@@ -67,6 +70,41 @@ __global__ void k_probe_chains(u64* out, u64 c, u64 d) {
       x1 = shoup_lazy(x1, w, wsh, d);
       x2 = shoup_lazy(x2, w, wsh, d);
       x3 = shoup_lazy(x3, w, wsh, d);
+    } else if constexpr (KIND == 8) {
+      // the epilogue a split-integer tensor-core basis conversion would need
+      // per output residue: 15 fp32 partial sums (exact integers below 2^22,
+      // here from a linear congruential sequence, as a fused kernel would
+      // hold them on chip), converted to integers, assembled as
+      // sum_s P_s 2^{8 s} in 128 bits and reduced modulo q (= d)
+      u64 r[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        U128 y{0, 0};
+        u32 st = a0 + 977u * (u32)k + (u32)i;
+#pragma unroll
+        for (int sft = 0; sft < 15; ++sft) {
+          st = st * 1664525u + 1013904223u;
+          const u64 v = (u64)__float2uint_rz((float)(st >> 10));
+          const int sh = 8 * sft;
+          if (sh < 64) {
+            const u64 lo = v << sh, hi = sh ? (v >> (64 - sh)) : 0;
+            const u64 t = y.lo + lo;
+            y.hi += hi + (t < lo);
+            y.lo = t;
+          } else {
+            y.hi += v << (sh - 64);
+          }
+        }
+        const u64 t = shoup_lazy(y.hi & ((1ull << 62) - 1), w, wsh, d);
+        u64 z = t + (y.lo - __umul64hi(y.lo, onesh) * d);
+        z = z >= 2 * d ? z - 2 * d : z;
+        r[k] = z >= d ? z - d : z;
+      }
+      x0 ^= r[0];
+      x1 ^= r[1];
+      x2 ^= r[2];
+      x3 ^= r[3];
+      a0 ^= (u32)r[0];
     } else {  // Harvey's lazy Cooley-Tukey butterfly on two pairs (the NTT's unit of work)
       u64 X = x0 >= q2 ? x0 - q2 : x0, T = shoup_lazy(x1, w, wsh, d);
       x0 = X + T;
@@ -104,7 +142,7 @@ extern "C" int hc_int_mul_rates(hc_ctx* ctx, double* rates, int cap) {
   if (!ctx) return HC_ERR_INVALID;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   try {
-    HC_CHECK(rates && cap >= 2 * kProbeForms, HC_ERR_INVALID, "rates needs 16 entries");
+    HC_CHECK(rates && cap >= 2 * kProbeForms, HC_ERR_INVALID, "rates needs 18 entries");
     int sms = 0, khz = 0;
     HC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
     HC_CUDA(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, ctx->device));
@@ -121,6 +159,7 @@ extern "C" int hc_int_mul_rates(hc_ctx* ctx, double* rates, int cap) {
     r[5] = probe_ops_per_s<5>(ctx, buf->ptr, blocks, threads, e0, e1);
     r[6] = probe_ops_per_s<6>(ctx, buf->ptr, blocks, threads, e0, e1);
     r[7] = probe_ops_per_s<7>(ctx, buf->ptr, blocks, threads, e0, e1) / 2;  // two butterflies per chain step
+    r[8] = probe_ops_per_s<8>(ctx, buf->ptr, blocks, threads, e0, e1);      // four output residues per step
     HC_CUDA(cudaGetLastError());
     for (int i = 0; i < kProbeForms; ++i) {
       rates[i] = r[i] / sms / (khz * 1e3);  // per SM per clock at the device's maximum clock

@@ -27,6 +27,7 @@ HC_TUNE_NTT = 0
 HC_TUNE_KEY_PRODUCT_Z = 1
 HC_TUNE_MODUP_SPLIT = 2
 HC_TUNE_TENSOR_GROUP = 3
+HC_TUNE_HOST_STREAMS = 4
 HC_PACK_BATCH = 0
 HC_PACK_SINGLE = 1
 HC_PACK_SINGLE_HOISTED = 2
@@ -356,7 +357,7 @@ def hc_profile_host_timeline(ctx):
 
 
 INT_MUL_FORMS = ("imad32", "umulhi32", "imad_wide32", "mul_lo64", "mul_hi64", "mac128", "shoup_lazy",
-                 "ct_butterfly")
+                 "ct_butterfly", "split_conv_epilogue")
 
 
 def hc_int_mul_rates(ctx):

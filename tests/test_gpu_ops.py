@@ -96,12 +96,24 @@ def test_host_pipeline_matches_device_batch(pair):
     b_arr = [H.hc_ct_export(pair.ctx, c)[0] for c in gb]
     a_m = [(lv, 1, c.meta().scale) for c in ga]
     b_m = [(lv, 1, c.meta().scale) for c in gb]
-    for chunk in (2, 0, 7):
-        outs = [np.zeros((2, lv, op.N), dtype=np.uint64) for _ in range(n)]
-        metas = H.hc_mul_relin_rescale_host(pair.ctx, pair.g_evk, a_arr, a_m, b_arr, b_m, outs, chunk=chunk)
-        for o, w, m in zip(outs, want, metas):
-            np.testing.assert_array_equal(o, w)
-            assert (m.level, m.degree) == (lv - 1, 1)
+    default_streams = H.hc_tune_get(pair.ctx, H.HC_TUNE_HOST_STREAMS)
+    assert default_streams == 2
+    try:
+        for streams in (1, 2, 3, 4):  # chunks' kernels round-robin over this many streams
+            H.hc_tune_set(pair.ctx, H.HC_TUNE_HOST_STREAMS, streams)
+            for chunk in (2, 0, 7):
+                outs = [np.zeros((2, lv, op.N), dtype=np.uint64) for _ in range(n)]
+                metas = H.hc_mul_relin_rescale_host(pair.ctx, pair.g_evk, a_arr, a_m, b_arr, b_m, outs, chunk=chunk)
+                for o, w, m in zip(outs, want, metas):
+                    np.testing.assert_array_equal(o, w)
+                    assert (m.level, m.degree) == (lv - 1, 1)
+                tl = H.hc_profile_host_timeline(pair.ctx)
+                assert len(tl) == (6 if chunk == 0 else -(-n // chunk))
+                assert all(c[0] <= c[1] <= c[2] <= c[3] <= c[4] <= c[5] for c in tl)
+        with pytest.raises(H.HcError):
+            H.hc_tune_set(pair.ctx, H.HC_TUNE_HOST_STREAMS, 5)
+    finally:
+        H.hc_tune_set(pair.ctx, H.HC_TUNE_HOST_STREAMS, default_streams)
     bad = [a.copy() for a in a_arr]
     bad[4][0, 1, 3] = np.uint64(op.q[1])
     outs = [np.zeros((2, lv, op.N), dtype=np.uint64) for _ in range(n)]
