@@ -690,6 +690,17 @@ def uneven_leg(H, W, np, torch, local):
     t_op, r_op = timed(per_op, 1)
     t_inst, r_inst = timed(per_instance, 2)
     t_b, r_b = timed(batched, 3)
+    # one more batched pass with per-kernel events on every context: the
+    # summed kernel time against the wall time shows how busy the device is
+    for c in order:
+        H.hc_profile_enable(c, True)
+    t_p0 = time.perf_counter()
+    batched()
+    sync()
+    t_prof = time.perf_counter() - t_p0
+    kernel_ms = sum(H.hc_profile_kernel(c, nm)[1] for c in order for nm in H.hc_profile_names(c))
+    for c in order:
+        H.hc_profile_enable(c, False)
     H.hc_graph_begin(order, 32 << 30)
     r_g = batched()
     g = H.hc_graph_end(order)
@@ -722,6 +733,7 @@ def uneven_leg(H, W, np, torch, local):
         "ms_per_op_calls": 1000 * t_op, "ms_per_instance_layers": 1000 * t_inst,
         "ms_batched": 1000 * t_b, "ms_graph_launch": 1000 * t_g, "ms_graph_launch_autotuned": 1000 * t_t,
         "inferences_per_s_graph": len(inst) / min(t_g, t_t), "speedup_graph_vs_per_op": t_op / min(t_g, t_t),
+        "batched_kernel_ms_sum": kernel_ms, "batched_wall_ms_profiled": 1000 * t_prof,
         "bit_identical_all_forms": same, "tuning": tuning,
     }
 

@@ -196,3 +196,22 @@ def test_tensor_group_choices_bit_identical(net):
         H.hc_tune_set(ctx, H.HC_TUNE_TENSOR_GROUP, default)
     with pytest.raises(H.HcError):
         H.hc_tune_set(ctx, H.HC_TUNE_TENSOR_GROUP, 6)
+
+
+def test_activation_over_mixed_levels(net):
+    """hc_enc_poly_act over inputs at several levels (each level's batch a
+    concurrent branch) gives each input the words of a call at its own level
+    and of the oracle, for x^2 and for Eq. 4's g."""
+    p = net["p"]
+    op = p.op
+    levels = [4, 2, 3, 4, 2, 3, 4]
+    pairs = [p.encrypt_values(W.slot_values(800 + i, op.K, -1.2, 1.2), level=lv, nonce=8000 + i)
+             for i, lv in enumerate(levels)]
+    gs = [g for g, _ in pairs]
+    for coeffs in ((0.0, 0.0, 1.0), (0.47, 0.50, 0.09)):
+        got = H.hc_enc_poly_act(p.ctx, p.g_evk, gs, coeffs)
+        for i, (g, o) in enumerate(pairs):
+            alone = H.hc_enc_poly_act(p.ctx, p.g_evk, [g], coeffs)[0]
+            assert np.array_equal(H.hc_ct_export(p.ctx, got[i])[0], H.hc_ct_export(p.ctx, alone)[0]), (coeffs, i)
+            if i < 3:
+                p.assert_same(got[i], cnn.enc_poly_act(op, p.o_evk, o, coeffs), "mixed-level g %d" % i)
