@@ -224,6 +224,58 @@ class OracleBench:
                 "textbook-NTT product mode, OpenMP over limbs" % n_ops)
 
 
+class OracleCnnSlice:
+    """The CPU oracle on a labelled slice of the N = 2^14 batch-packed CNN
+    (8192 images): one conv output (25 tensor terms, relinearise, rescale),
+    one x^2 activation, one 2x2 mean pool and one FC class (180 terms,
+    relinearise, rescale), each timed once and extrapolated to the network's
+    720 conv outputs, 720 activations, 180 pools and 10 classes.  The terms
+    reuse one pair of ciphertexts (the oracle's cost does not depend on the
+    values)."""
+
+    def __init__(self, seed=0x2102_0031_9002):
+        import numpy as np
+
+        from oracle import ckks, cnn
+        from paper_2102_00319_gb300 import workloads as W
+
+        self.ckks, self.cnn = ckks, cnn
+        ps = W.BATCH_N14
+        self.op = op = ckks.Params(ps.log_n, list(ps.q_bits), list(ps.p_bits), ps.log2_scale)
+        self.sk, self.pk, self.evk = ckks.keygen(op, seed)
+
+        def enc(level, nonce):
+            m = W.int_plaintext(seed + nonce, op.N, 2 ** 30)
+            return ckks.encrypt(op, self.pk, ckks.plaintext_from_ints(op, m, level, op.scale), seed + 7, nonce)
+
+        self.x6, self.w6 = enc(op.L, 1), enc(op.L, 2)
+        self.x3, self.w3 = enc(3, 3), enc(3, 4)
+        self.threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+    def run(self):
+        c, op, evk = self.ckks, self.op, self.evk
+        t = {}
+        t0 = time.perf_counter()
+        y = c.rescale(op, c.relin(op, evk, c.tensor_sum(op, [self.x6] * 25, [self.w6] * 25)))
+        t["conv_output"] = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        a = self.cnn.enc_square(op, evk, y)
+        t["activation"] = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        s4 = c.add(op, c.add(op, a, a), c.add(op, a, a))
+        c.rescale(op, c.mul_const(op, s4, 0.25, float(op.q[s4.level])))
+        t["pool_output"] = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        c.rescale(op, c.relin(op, evk, c.tensor_sum(op, [self.x3] * 180, [self.w3] * 180)))
+        t["fc_class"] = time.perf_counter() - t0
+        total = 720 * t["conv_output"] + 720 * t["activation"] + 180 * t["pool_output"] + 10 * t["fc_class"]
+        return {"value": 8192 / total, "unit": "images/s", "cores": self.threads, "kind": "oracle",
+                "sample": "one conv output, one x^2, one pool output and one FC class of the N=2^14 batch CNN "
+                          "(textbook-NTT product mode), timed once each and extrapolated to 720 / 720 / 180 / 10 "
+                          "per 8192-image batch",
+                "seconds": {k: round(v, 3) for k, v in t.items()}, "extrapolated_batch_s": total}
+
+
 def bench_config(batch, world):
     """The workload both arms report: N = 2^16, L = 20, seven special primes
     (dnum = 3), `batch` resident ciphertext pairs per step."""
@@ -1250,6 +1302,8 @@ def run_gpu(args, rank, world, local):
         dt = ob.run(args.cpu_ops)
         line["cpu_baseline"] = {"value": args.cpu_ops / dt, "unit": UNIT, "cores": ob.threads, "kind": "oracle",
                                 "sample": ob.sample(args.cpu_ops)}
+        if not args.no_cnn:
+            line["cpu_baseline_cnn"] = OracleCnnSlice().run()
     else:
         del line["cpu_baseline"]
     print(json.dumps(line), flush=True)

@@ -127,3 +127,14 @@ def bench_config_of_default():
     mod = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(mod)
     return mod.bench_config(64, 1)
+
+
+def test_oracle_cnn_slice_extrapolates_the_batch(bench):
+    """The labelled CPU-oracle slice of the N = 2^14 CNN times each piece and
+    extrapolates to 720 conv outputs, 720 activations, 180 pools, 10 classes."""
+    r = bench.OracleCnnSlice().run()
+    t = r["seconds"]
+    assert set(t) == {"conv_output", "activation", "pool_output", "fc_class"}
+    want = 720 * t["conv_output"] + 720 * t["activation"] + 180 * t["pool_output"] + 10 * t["fc_class"]
+    assert abs(r["extrapolated_batch_s"] - want) < 0.01 * want + 0.01
+    assert r["unit"] == "images/s" and r["kind"] == "oracle" and abs(r["value"] - 8192 / r["extrapolated_batch_s"]) < 1e-6
