@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tiles and launch shapes")
     ap.add_argument("--graph-arena-gib", type=int, default=0,
                     help="device arena of the captured step (0: 4 GiB + 0.2 GiB per pair)")
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--e2e-chunk", type=int, default=0, help="pairs per pipeline chunk of the host call (0: auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-ops", type=int, default=1, help="oracle operations in the CPU sample")

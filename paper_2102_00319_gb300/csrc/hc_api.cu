@@ -301,13 +301,15 @@ void keyswitch_batch_keys(hc_ctx* ctx, const std::vector<const u64*>& keys, int 
     xin.nlimb = nq;
     launch_ntt_from(ctx, limbset_base(xc, x_is, 0, 1, nq, 0, nullptr), &xin, m, true, false);
     modup_digits(ctx, level, xs, xc, x_is, ext, ext_is, m, keep);
-    for (int r0 = 0; r0 < m;) {  // one key-product launch per run of items sharing a key
-      int r1 = r0 + 1;
-      while (r1 < m && keys[s0 + r1] == keys[s0 + r0]) ++r1;
-      launch_key_product_batched(ctx, level, ext + (size_t)r0 * ext_is, ext_is, keys[s0 + r0],
-                                 acc + (size_t)r0 * acc_is, acc_is, r1 - r0, dnum <= 8 ? xr + r0 : nullptr);
-      r0 = r1;
+    // one key-product launch: a shared key, or a device table of per-item keys
+    bool same_key = true;
+    for (int r = 1; r < m; ++r) same_key = same_key && keys[s0 + r] == keys[s0];
+    const u64* const* item_keys = nullptr;
+    if (!same_key) {
+      item_keys = upload(ctx, std::vector<const u64*>(keys.begin() + s0, keys.begin() + s0 + m), keep);
     }
+    launch_key_product_batched(ctx, level, ext, ext_is, keys[s0], acc, acc_is, m, dnum <= 8 ? xr : nullptr,
+                               item_keys);
     // ModDown
     launch_ntt(ctx, limbset_base(acc, acc_is, ext_words, 2, alpha, nq, emap), m, true, false);
     launch_moddown_bconv_fast(ctx, level, acc + (size_t)nq * n, acc_is, zq, z_is, m);
@@ -1548,10 +1550,11 @@ std::vector<hc_ct*> rotate_batch(hc_ctx* ctx, const hc_evk* evk, const std::vect
 }
 
 // Hoisted rotations of m ciphertexts at one level by every step in `steps`:
-// one ModUp of all the c1's, then per step the automorphism of the raised
-// digits, the key product, ModDown and the automorphism of c0, each one
-// launch over the m items.  out[step][item]; the same words as m separate
-// hoisted calls.
+// one ModUp of all the c1's, then the automorphism of the raised digits, the
+// key product, ModDown and the automorphism of c0, each one launch over the
+// (step, ciphertext) items of as many steps as the workspace holds, every
+// item with its own Galois element and key.  out[step][item]; the same words
+// as m separate hoisted calls.
 std::vector<std::vector<hc_ct*>> rotate_hoisted_batch(hc_ctx* ctx, const hc_evk* evk,
                                                       const std::vector<const hc_ct*>& xs,
                                                       const std::vector<int>& steps) {
@@ -1576,27 +1579,35 @@ std::vector<std::vector<hc_ct*>> rotate_hoisted_batch(hc_ctx* ctx, const hc_evk*
   const int* emap = ctx->ext_map_of(level);
   const u64 x_is = (u64)nq * n, ext_is = (u64)dnum * ext_words, acc_is = 2 * (u64)ext_words,
             z_is = 2 * (u64)nq * n, c0_is = (u64)nq * n;
-  const size_t per_item = x_is + 2 * ext_is + acc_is + z_is + c0_is;
-  const int chunk = (int)std::min<size_t>(256, std::max<size_t>(1, kWorkspaceBytes / (per_item * 8)));
+  // the steps that rotate; groups of them share each launch after ModUp
+  std::vector<int> rk;
+  for (size_t k = 0; k < gs.size(); ++k) {
+    if (gs[k] != 1) rk.push_back((int)k);
+  }
+  const size_t item_words = x_is + ext_is;                     // c1 in coefficient form, raised digits
+  const size_t step_words = ext_is + acc_is + z_is + c0_is;    // per (step, item): kappa_g digits .. kappa_g c0
+  const size_t ws_words = kWorkspaceBytes / 8;
+  const int chunk = (int)std::min<size_t>(256, std::max<size_t>(1, ws_words / (item_words + step_words)));
   for (int s0 = 0; s0 < total; s0 += chunk) {
     const int m = std::min(chunk, total - s0);
+    // as many rotating steps per launch as the workspace holds (at least one)
+    const size_t room = ws_words / m > item_words ? (ws_words / m - item_words) / step_words : 0;
+    const int sg = (int)std::max<size_t>(1, std::min<size_t>(rk.size(), room));
     std::vector<BufPtr> keep;
-    BufPtr work = ctx->buffer(per_item * m);
+    BufPtr work = ctx->buffer(item_words * m + step_words * (size_t)m * std::max(1, sg));
     keep.push_back(work);
     u64* xc = work->ptr;                      // [m][nq][N]
     u64* ext = xc + x_is * m;                 // [m][dnum][next][N]
-    u64* extg = ext + ext_is * m;             // [m][dnum][next][N]
-    u64* acc = extg + ext_is * m;             // [m][2][next][N]
-    u64* zq = acc + acc_is * m;               // [m][2][nq][N]
-    u64* c0g = zq + z_is * m;                 // [m][nq][N]
-    std::vector<CtRef> c1s, c0s, xsr, ers, egr, c0d, od;
+    u64* extg = ext + ext_is * m;             // [sg][m][dnum][next][N]
+    u64* acc = extg + ext_is * m * sg;        // [sg][m][2][next][N]
+    u64* zq = acc + acc_is * m * sg;          // [sg][m][2][nq][N]
+    u64* c0g = zq + z_is * m * sg;            // [sg][m][nq][N]
+    std::vector<CtRef> c1s, c0s, xsr;
     for (int i = 0; i < m; ++i) {
       const hc_ct* x = xs[s0 + i];
       c1s.push_back(CtRef{x->data + x->stride, 0});
       c0s.push_back(CtRef{x->data, 0});
-      ers.push_back(CtRef{ext + ext_is * i, (u64)ext_words});
-      egr.push_back(CtRef{extg + ext_is * i, (u64)ext_words});
-      c0d.push_back(CtRef{c0g + c0_is * i, 0});
+      xsr.push_back(x->ref());
     }
     // c1 -> coefficient form (N^{-1} left to the conversion constants)
     LimbSet c1in{};
@@ -1619,28 +1630,41 @@ std::vector<std::vector<hc_ct*>> rotate_hoisted_batch(hc_ctx* ctx, const hc_evk*
       e.slot_map = ctx->modup_slots_of(level, j);
       launch_ntt(ctx, e, m, false);
     }
-    const CtRef* ext_r = refs_dev(ctx, ers, keep);
-    const CtRef* extg_r = refs_dev(ctx, egr, keep);
-    const CtRef* c0s_r = refs_dev(ctx, c0s, keep);
-    const CtRef* c0d_r = refs_dev(ctx, c0d, keep);
-    for (size_t k = 0; k < gs.size(); ++k) {
+    for (size_t k = 0; k < gs.size(); ++k) {  // steps that do not rotate: a copy
+      if (gs[k] != 1) continue;
       std::vector<CtRef> orr;
       for (int i = 0; i < m; ++i) orr.push_back(outs[k][s0 + i]->ref());
-      const CtRef* od_r = refs_dev(ctx, orr, keep);
-      if (gs[k] == 1) {
-        std::vector<CtRef> xr;
-        for (int i = 0; i < m; ++i) xr.push_back(xs[s0 + i]->ref());
-        launch_ew(ctx, 3, od_r, refs_dev(ctx, xr, keep), nullptr, m, 2, nq);
-        continue;
+      launch_ew(ctx, 3, refs_dev(ctx, orr, keep), refs_dev(ctx, xsr, keep), nullptr, m, 2, nq);
+    }
+    for (size_t r0 = 0; r0 < rk.size(); r0 += sg) {
+      const int ns = (int)std::min<size_t>(sg, rk.size() - r0), mi = ns * m;  // items: (step, ciphertext)
+      std::vector<CtRef> ers, egr, c0src, c0d, od;
+      std::vector<const u64*> keys;
+      std::vector<u64> gitem;
+      for (int t = 0; t < ns; ++t) {
+        const int k = rk[r0 + t];
+        for (int i = 0; i < m; ++i) {
+          const size_t it = (size_t)t * m + i;
+          ers.push_back(CtRef{ext + ext_is * i, (u64)ext_words});
+          egr.push_back(CtRef{extg + ext_is * it, (u64)ext_words});
+          c0src.push_back(c0s[i]);
+          c0d.push_back(CtRef{c0g + c0_is * it, 0});
+          od.push_back(outs[k][s0 + i]->ref());
+          keys.push_back(evk->galois.at(gs[k]).buf->ptr);
+          gitem.push_back(gs[k]);
+        }
       }
+      const u64* gd = upload(ctx, gitem, keep);
+      const u64* const* kd = ns > 1 ? upload(ctx, keys, keep) : nullptr;
+      const CtRef* c0d_r = refs_dev(ctx, c0d, keep);
       // kappa_g on every raised digit (the NTT-domain permutation is the same for every prime)
-      launch_automorph(ctx, extg_r, ext_r, m, dnum, next, gs[k]);
-      launch_key_product_batched(ctx, level, extg, ext_is, evk->galois.at(gs[k]).buf->ptr, acc, acc_is, m);
-      launch_ntt(ctx, limbset_base(acc, acc_is, ext_words, 2, alpha, nq, emap), m, true, false);
-      launch_moddown_bconv_fast(ctx, level, acc + (size_t)nq * n, acc_is, zq, z_is, m);
-      launch_ntt(ctx, limbset_base(zq, z_is, (u64)nq * n, 2, nq, 0, nullptr), m, false);
-      launch_automorph(ctx, c0d_r, c0s_r, m, 1, nq, gs[k]);
-      launch_moddown_combine(ctx, level, acc, acc_is, zq, z_is, c0d_r, nullptr, od_r, m);
+      launch_automorph_items(ctx, refs_dev(ctx, egr, keep), refs_dev(ctx, ers, keep), mi, dnum, next, gd);
+      launch_key_product_batched(ctx, level, extg, ext_is, keys[0], acc, acc_is, mi, nullptr, kd);
+      launch_ntt(ctx, limbset_base(acc, acc_is, ext_words, 2, alpha, nq, emap), mi, true, false);
+      launch_moddown_bconv_fast(ctx, level, acc + (size_t)nq * n, acc_is, zq, z_is, mi);
+      launch_ntt(ctx, limbset_base(zq, z_is, (u64)nq * n, 2, nq, 0, nullptr), mi, false);
+      launch_automorph_items(ctx, c0d_r, refs_dev(ctx, c0src, keep), mi, 1, nq, gd);
+      launch_moddown_combine(ctx, level, acc, acc_is, zq, z_is, c0d_r, nullptr, refs_dev(ctx, od, keep), mi);
     }
   }
   return outs;
@@ -1670,22 +1694,27 @@ std::vector<hc_ct*> rotate_one(hc_ctx* ctx, const hc_evk* evk, const hc_ct* x, c
   for (u64 g : gs) nrot += g != 1;
   BufPtr tmp = ctx->buffer(std::max<size_t>(1, 2 * (size_t)nrot * nq * n));
   keep.push_back(tmp);
-  std::vector<CtRef> xs, b0, o;
+  std::vector<CtRef> xs, b0, o, src;
   std::vector<const u64*> ks;
+  std::vector<u64> gitem;
   for (size_t i = 0; i < gs.size(); ++i) {
-    const CtRef* od = refs_dev(ctx, {outs[i]->ref()}, keep);
     if (gs[i] == 1) {
-      launch_ew(ctx, 3, od, xr, nullptr, 1, 2, nq);
+      launch_ew(ctx, 3, refs_dev(ctx, {outs[i]->ref()}, keep), xr, nullptr, 1, 2, nq);
       continue;
     }
     u64* base = tmp->ptr + xs.size() * 2 * (size_t)nq * n;
-    launch_automorph(ctx, refs_dev(ctx, {CtRef{base, (u64)nq * n}}, keep), xr, 1, 2, nq, gs[i]);
     xs.push_back(CtRef{base + (size_t)nq * n, (u64)nq * n});
     b0.push_back(CtRef{base, (u64)nq * n});
+    src.push_back(x->ref());
     o.push_back(outs[i]->ref());
     ks.push_back(evk->galois.at(gs[i]).buf->ptr);
+    gitem.push_back(gs[i]);
   }
-  if (!xs.empty()) keyswitch_batch_keys(ctx, ks, level, xs, &b0, nullptr, o);
+  if (!xs.empty()) {  // b0 holds each step's (c0, c1) pair: one automorphism launch for all steps
+    launch_automorph_items(ctx, refs_dev(ctx, b0, keep), refs_dev(ctx, src, keep), (int)xs.size(), 2, nq,
+                           upload(ctx, gitem, keep));
+    keyswitch_batch_keys(ctx, ks, level, xs, &b0, nullptr, o);
+  }
   return outs;
 }
 }  // namespace
@@ -2747,9 +2776,10 @@ extern "C" int hc_enc_conv2d_single_batch(hc_ctx* ctx, const hc_evk* evk, const 
       for (int t = 0; t < T; ++t) nrot += gs[t] != 1;
       BufPtr tmp = ctx->buffer(std::max<size_t>(1, 2 * (size_t)nrot * G * nq * n));
       keep.push_back(tmp);
-      std::vector<CtRef> t0, t1, o;
+      std::vector<CtRef> t0, t1, o, src;
       std::vector<const u64*> ks;
-      int nr = 0;  // rotation steps placed so far
+      std::vector<u64> gitem;  // each (step, image) item's Galois element
+      int nr = 0;              // rotation steps placed so far
       for (int t = 0; t < T; ++t) {
         std::vector<CtRef> ot;
         for (int gi = 0; gi < G; ++gi) ot.push_back(rot[t * G + gi]->ref());
@@ -2757,19 +2787,22 @@ extern "C" int hc_enc_conv2d_single_batch(hc_ctx* ctx, const hc_evk* evk, const 
           launch_ew(ctx, 3, refs_dev(ctx, ot, keep), xrd, nullptr, G, 2, nq);
           continue;
         }
-        std::vector<CtRef> tr;
         for (int gi = 0; gi < G; ++gi) {
           u64* base = tmp->ptr + ((size_t)nr * G + gi) * 2 * nq * n;
-          tr.push_back(CtRef{base, (u64)nq * n});
           t0.push_back(CtRef{base, (u64)nq * n});
           t1.push_back(CtRef{base + (size_t)nq * n, (u64)nq * n});
+          src.push_back(xr[gi]);
           o.push_back(ot[gi]);
           ks.push_back(evk->galois.at(gs[t]).buf->ptr);
+          gitem.push_back(gs[t]);
         }
-        launch_automorph(ctx, refs_dev(ctx, tr, keep), xrd, G, 2, nq, gs[t]);
         ++nr;
       }
-      if (!o.empty()) keyswitch_batch_keys(ctx, ks, level, t1, &t0, nullptr, o);
+      if (!o.empty()) {  // t0 holds each item's (c0, c1) pair: one automorphism launch for all
+        launch_automorph_items(ctx, refs_dev(ctx, t0, keep), refs_dev(ctx, src, keep), (int)o.size(), 2, nq,
+                               upload(ctx, gitem, keep));
+        keyswitch_batch_keys(ctx, ks, level, t1, &t0, nullptr, o);
+      }
       // weights viewed at this level
       std::vector<hc_ct*> wv;
       std::vector<const hc_ct*> ws;

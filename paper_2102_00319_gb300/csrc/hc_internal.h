@@ -257,6 +257,9 @@ void launch_tensor_acc(hc_ctx* ctx, const CtRef* out, const CtRef* x, const CtRe
 // NTT-domain automorphism: out = kappa_g(a) for `items` refs, npoly polys, nl limbs.
 void launch_automorph(hc_ctx* ctx, const CtRef* out, const CtRef* a, int items, int npoly, int nl,
                       u64 g);
+// The same with a Galois element per item (gs: device array of `items`).
+void launch_automorph_items(hc_ctx* ctx, const CtRef* out, const CtRef* a, int items, int npoly, int nl,
+                            const u64* gs);
 // ModUp basis conversion of digit j at level `level`: reads coefficient-form
 // limbs of x (items), writes the ext limbs outside the digit into ext.
 void launch_modup_bconv(hc_ctx* ctx, int level, int j, const u64* xcoef, u64 x_item_stride,
@@ -294,7 +297,8 @@ void launch_modup_bconv_fast(hc_ctx* ctx, int level, int j, const u64* xcoef, u6
 void launch_moddown_bconv_fast(hc_ctx* ctx, int level, const u64* accp_coef, u64 accp_item_stride, u64* z,
                                u64 z_item_stride, int items);
 void launch_key_product_batched(hc_ctx* ctx, int level, const u64* ext, u64 ext_item_stride, const u64* key,
-                                u64* acc, u64 acc_item_stride, int items, const CtRef* digit_src = nullptr);
+                                u64* acc, u64 acc_item_stride, int items, const CtRef* digit_src = nullptr,
+                                const u64* const* item_keys = nullptr);  // per-item keys override `key`
 // Fused relinearise + rescale tail (see hc_kernels.cu).
 void launch_ksr_last(hc_ctx* ctx, int level, const u64* acc, u64 acc_item_stride, const CtRef* base0,
                      const CtRef* base1, u64* tl, int items);

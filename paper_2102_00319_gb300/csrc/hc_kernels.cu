@@ -299,14 +299,15 @@ __global__ void k_tensor_pair(const CtRef* out, const CtRef* a, const CtRef* b, 
 
 // NTT-domain automorphism: slot k holds a(psi^{e_k}), e_k = 2 brv(k) + 1;
 // kappa_g(a)(psi^{e}) = a(psi^{e g}).
-__global__ void k_automorph(const CtRef* out, const CtRef* a, int nl, u64 g, Tables T) {
+// gs (may be null): per-item Galois elements, overriding g.
+__global__ void k_automorph(const CtRef* out, const CtRef* a, int nl, u64 g, const u64* gs, Tables T) {
   const int logn = T.log_n, n = 1 << logn;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const int poly = blockIdx.y / nl, l = blockIdx.y % nl, z = blockIdx.z;
   const u64 mask = 2 * (u64)n - 1;
   const u64 e = 2 * (u64)(__brev((unsigned)k) >> (32 - logn)) + 1;
-  const u64 e2 = (e * g) & mask;
+  const u64 e2 = (e * (gs ? gs[blockIdx.z] : g)) & mask;
   const int src = (int)(__brev((unsigned)((e2 - 1) >> 1)) >> (32 - logn));
   out[z].p[poly * out[z].stride + (size_t)l * n + k] = a[z].p[poly * a[z].stride + (size_t)l * n + src];
 }
@@ -342,7 +343,7 @@ __global__ void k_modup_bconv(const u64* xcoef, u64 x_item_stride, u64* ext, u64
 // high word stays below q.
 __global__ void k_key_product(const u64* ext, u64 ext_item_stride, const u64* key, u64* acc,
                               u64 acc_item_stride, int dnum, int next, int nchain, const int* emap,
-                              Tables T) {
+                              const u64* const* item_keys, Tables T) {
   const int n = 1 << T.log_n;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
@@ -357,8 +358,9 @@ __global__ void k_key_product(const u64* ext, u64 ext_item_stride, const u64* ke
       a1 = U128{reduce128(a1, md), 0};
     }
     const u64 y = e[(size_t)j * next * n];
-    const u64* kb = key + ((size_t)(2 * j) * nchain + pid) * n + c;
-    const u64* ka = key + ((size_t)(2 * j + 1) * nchain + pid) * n + c;
+    const u64* kz = item_keys ? item_keys[z] : key;  // per-item switching key, if given
+    const u64* kb = kz + ((size_t)(2 * j) * nchain + pid) * n + c;
+    const u64* ka = kz + ((size_t)(2 * j + 1) * nchain + pid) * n + c;
     mac(a0, y, *kb);
     mac(a1, y, *ka);
   }
@@ -633,8 +635,19 @@ void launch_automorph(hc_ctx* ctx, const CtRef* out, const CtRef* a, int items, 
   if (items <= 0) return;
     {
       ProfScope prof_(ctx, "k_automorph", (uint64_t)items * npoly * nl);
-      k_automorph<<<grid_for(ctx, npoly * nl, items), kT, 0, ctx->stream>>>(out, a, nl, g, ctx->tab);
+      k_automorph<<<grid_for(ctx, npoly * nl, items), kT, 0, ctx->stream>>>(out, a, nl, g, nullptr, ctx->tab);
     }
+  LAUNCH_DONE(ctx);
+}
+
+void launch_automorph_items(hc_ctx* ctx, const CtRef* out, const CtRef* a, int items, int npoly, int nl,
+                            const u64* gs) {
+  if (items <= 0) return;
+  HC_CHECK(items <= 65535, HC_ERR_INVALID, "too many automorphism items for one launch");
+  {
+    ProfScope prof_(ctx, "k_automorph", (uint64_t)items * npoly * nl);
+    k_automorph<<<grid_for(ctx, npoly * nl, items), kT, 0, ctx->stream>>>(out, a, nl, 1, gs, ctx->tab);
+  }
   LAUNCH_DONE(ctx);
 }
 
@@ -661,7 +674,7 @@ void launch_key_product(hc_ctx* ctx, int level, const u64* ext, u64 ext_item_str
       ProfScope prof_(ctx, "k_key_product", (uint64_t)items * next);
       k_key_product<<<grid_for(ctx, next, items), kT, 0, ctx->stream>>>(
         ext, ext_item_stride, key, acc, acc_item_stride, ctx->lv[level].dnum, next, ctx->P.nchain(),
-        ctx->ext_map_of(level), ctx->tab);
+        ctx->ext_map_of(level), nullptr, ctx->tab);
     }
   LAUNCH_DONE(ctx);
 }
@@ -918,7 +931,7 @@ template <int DNUM, bool HALVES>
 __global__ void __launch_bounds__(kT) k_key_product_t(const u64* ext, u64 ext_item_stride, const u64* key, u64* acc,
                                                        u64 acc_item_stride, int next, int nchain, const int* emap,
                                                        int items, const CtRef* digit_src, int alpha, int nq,
-                                                       Tables T) {
+                                                       const u64* const* item_keys, Tables T) {
   const int n = 1 << T.log_n;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
@@ -927,17 +940,23 @@ __global__ void __launch_bounds__(kT) k_key_product_t(const u64* ext, u64 ext_it
   const DMod md = T.mods[pid];
   u64 kb[DNUM], ka[DNUM];
   Half30 hb[DNUM], ha[DNUM];  // (used by the halves form only)
+  // the key limbs of this slot: once for all items, or per item when every
+  // item carries its own switching key
+  auto load_keys = [&](const u64* kbase) {
 #pragma unroll
-  for (int j = 0; j < DNUM; ++j) {
-    kb[j] = key[((size_t)(2 * j) * nchain + pid) * n + c];
-    ka[j] = key[((size_t)(2 * j + 1) * nchain + pid) * n + c];
-    if constexpr (HALVES) {
-      hb[j] = halves30(kb[j]);
-      ha[j] = halves30(ka[j]);
+    for (int j = 0; j < DNUM; ++j) {
+      kb[j] = kbase[((size_t)(2 * j) * nchain + pid) * n + c];
+      ka[j] = kbase[((size_t)(2 * j + 1) * nchain + pid) * n + c];
+      if constexpr (HALVES) {
+        hb[j] = halves30(kb[j]);
+        ha[j] = halves30(ka[j]);
+      }
     }
-  }
+  };
+  if (!item_keys) load_keys(key);
   const int own = (digit_src && s < nq) ? s / alpha : -1;  // the digit whose block holds slot s
   for (int z = blockIdx.z; z < items; z += gridDim.z) {
+    if (item_keys) load_keys(item_keys[z]);
     const u64* e = ext + (size_t)z * ext_item_stride + (size_t)s * n + c;
     u64* o = acc + (size_t)z * acc_item_stride + (size_t)s * n + c;
     if constexpr (HALVES) {
@@ -1063,7 +1082,8 @@ void launch_moddown_bconv_fast(hc_ctx* ctx, int level, const u64* accp_coef, u64
 }
 
 void launch_key_product_batched(hc_ctx* ctx, int level, const u64* ext, u64 ext_item_stride, const u64* key,
-                                u64* acc, u64 acc_item_stride, int items, const CtRef* digit_src) {
+                                u64* acc, u64 acc_item_stride, int items, const CtRef* digit_src,
+                                const u64* const* item_keys) {
   const int next = level + 1 + ctx->P.alpha, dnum = ctx->lv[level].dnum;
   // a few item groups in z so small batches still fill the GPU
   const int zgroups =
@@ -1076,11 +1096,13 @@ void launch_key_product_batched(hc_ctx* ctx, int level, const u64* ext, u64 ext_
     if (halves)                                                                                                 \
       k_key_product_t<D, true><<<g, kT, 0, ctx->stream>>>(ext, ext_item_stride, key, acc, acc_item_stride,    \
                                                           next, ctx->P.nchain(), ctx->ext_map_of(level), items, \
-                                                          digit_src, ctx->P.alpha, level + 1, ctx->tab);       \
+                                                          digit_src, ctx->P.alpha, level + 1, item_keys,       \
+                                                          ctx->tab);                                           \
     else                                                                                                        \
       k_key_product_t<D, false><<<g, kT, 0, ctx->stream>>>(ext, ext_item_stride, key, acc, acc_item_stride,   \
                                                            next, ctx->P.nchain(), ctx->ext_map_of(level),      \
-                                                           items, digit_src, ctx->P.alpha, level + 1, ctx->tab); \
+                                                           items, digit_src, ctx->P.alpha, level + 1, item_keys, \
+                                                           ctx->tab);                                            \
     break;
   switch (dnum) {
     HC_KP(1) HC_KP(2) HC_KP(3) HC_KP(4) HC_KP(5) HC_KP(6) HC_KP(7) HC_KP(8)
@@ -1088,7 +1110,7 @@ void launch_key_product_batched(hc_ctx* ctx, int level, const u64* ext, u64 ext_
       HC_CHECK(!digit_src, HC_ERR_INVALID, "digit sources need a specialised key product");
       const dim3 g2 = grid_for(ctx, next, items);
       k_key_product<<<g2, kT, 0, ctx->stream>>>(ext, ext_item_stride, key, acc, acc_item_stride, dnum, next,
-                                                ctx->P.nchain(), ctx->ext_map_of(level), ctx->tab);
+                                                ctx->P.nchain(), ctx->ext_map_of(level), item_keys, ctx->tab);
     }
   }
 #undef HC_KP
