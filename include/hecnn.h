@@ -429,6 +429,17 @@ int hc_enc_conv2d(hc_ctx *ctx, const hc_evk *evk, hc_packing packing, const hc_c
  */
 int hc_enc_conv2d_single_batch(hc_ctx *ctx, const hc_evk *evk, const hc_ct *const *x, int nimg, int W,
                                const hc_ct *const *w, int cout, int kh, int kw, hc_ct **y);
+/*
+ * The same convolution with hoisted rotations: per level group one ModUp of
+ * every image's c1, then one key product (reading the raised digits through
+ * each step's automorphism), one ModDown and one automorphism of c0 over all
+ * (step, image) items.  Bit-identical to hc_enc_conv2d with
+ * HC_PACK_SINGLE_HOISTED applied image by image (not to
+ * hc_enc_conv2d_single_batch: the two rotation forms round differently).
+ * Same arguments and errors as hc_enc_conv2d_single_batch.
+ */
+int hc_enc_conv2d_single_hoisted_batch(hc_ctx *ctx, const hc_evk *evk, const hc_ct *const *x, int nimg, int W,
+                                       const hc_ct *const *w, int cout, int kh, int kw, hc_ct **y);
 
 /*
  * Polynomial activation g(u) = c0 + c1 u + c2 u^2 (Eq. 4, the paper's

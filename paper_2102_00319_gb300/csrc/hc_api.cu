@@ -1550,11 +1550,11 @@ std::vector<hc_ct*> rotate_batch(hc_ctx* ctx, const hc_evk* evk, const std::vect
 }
 
 // Hoisted rotations of m ciphertexts at one level by every step in `steps`:
-// one ModUp of all the c1's, then the automorphism of the raised digits, the
-// key product, ModDown and the automorphism of c0, each one launch over the
-// (step, ciphertext) items of as many steps as the workspace holds, every
-// item with its own Galois element and key.  out[step][item]; the same words
-// as m separate hoisted calls.
+// one ModUp of all the c1's, then the key product (reading the raised digits
+// through the automorphism), ModDown and the automorphism of c0, each one
+// launch over the (step, ciphertext) items of as many steps as the workspace
+// holds, every item with its own Galois element and key.  out[step][item];
+// the same words as m separate hoisted calls.
 std::vector<std::vector<hc_ct*>> rotate_hoisted_batch(hc_ctx* ctx, const hc_evk* evk,
                                                       const std::vector<const hc_ct*>& xs,
                                                       const std::vector<int>& steps) {
@@ -1585,7 +1585,7 @@ std::vector<std::vector<hc_ct*>> rotate_hoisted_batch(hc_ctx* ctx, const hc_evk*
     if (gs[k] != 1) rk.push_back((int)k);
   }
   const size_t item_words = x_is + ext_is;                     // c1 in coefficient form, raised digits
-  const size_t step_words = ext_is + acc_is + z_is + c0_is;    // per (step, item): kappa_g digits .. kappa_g c0
+  const size_t step_words = acc_is + z_is + c0_is;             // per (step, item): key product .. kappa_g c0
   const size_t ws_words = kWorkspaceBytes / 8;
   const int chunk = (int)std::min<size_t>(256, std::max<size_t>(1, ws_words / (item_words + step_words)));
   for (int s0 = 0; s0 < total; s0 += chunk) {
@@ -1598,8 +1598,7 @@ std::vector<std::vector<hc_ct*>> rotate_hoisted_batch(hc_ctx* ctx, const hc_evk*
     keep.push_back(work);
     u64* xc = work->ptr;                      // [m][nq][N]
     u64* ext = xc + x_is * m;                 // [m][dnum][next][N]
-    u64* extg = ext + ext_is * m;             // [sg][m][dnum][next][N]
-    u64* acc = extg + ext_is * m * sg;        // [sg][m][2][next][N]
+    u64* acc = ext + ext_is * m;              // [sg][m][2][next][N]
     u64* zq = acc + acc_is * m * sg;          // [sg][m][2][nq][N]
     u64* c0g = zq + z_is * m * sg;            // [sg][m][nq][N]
     std::vector<CtRef> c1s, c0s, xsr;
@@ -1638,15 +1637,13 @@ std::vector<std::vector<hc_ct*>> rotate_hoisted_batch(hc_ctx* ctx, const hc_evk*
     }
     for (size_t r0 = 0; r0 < rk.size(); r0 += sg) {
       const int ns = (int)std::min<size_t>(sg, rk.size() - r0), mi = ns * m;  // items: (step, ciphertext)
-      std::vector<CtRef> ers, egr, c0src, c0d, od;
+      std::vector<CtRef> c0src, c0d, od;
       std::vector<const u64*> keys;
       std::vector<u64> gitem;
       for (int t = 0; t < ns; ++t) {
         const int k = rk[r0 + t];
         for (int i = 0; i < m; ++i) {
           const size_t it = (size_t)t * m + i;
-          ers.push_back(CtRef{ext + ext_is * i, (u64)ext_words});
-          egr.push_back(CtRef{extg + ext_is * it, (u64)ext_words});
           c0src.push_back(c0s[i]);
           c0d.push_back(CtRef{c0g + c0_is * it, 0});
           od.push_back(outs[k][s0 + i]->ref());
@@ -1657,9 +1654,10 @@ std::vector<std::vector<hc_ct*>> rotate_hoisted_batch(hc_ctx* ctx, const hc_evk*
       const u64* gd = upload(ctx, gitem, keep);
       const u64* const* kd = ns > 1 ? upload(ctx, keys, keep) : nullptr;
       const CtRef* c0d_r = refs_dev(ctx, c0d, keep);
-      // kappa_g on every raised digit (the NTT-domain permutation is the same for every prime)
-      launch_automorph_items(ctx, refs_dev(ctx, egr, keep), refs_dev(ctx, ers, keep), mi, dnum, next, gd);
-      launch_key_product_batched(ctx, level, extg, ext_is, keys[0], acc, acc_is, mi, nullptr, kd);
+      // the key product reads kappa_g of every raised digit in place (the
+      // NTT-domain permutation is the same for every prime): item t m + i
+      // uses ciphertext i's digits
+      launch_key_product_batched(ctx, level, ext, ext_is, keys[0], acc, acc_is, mi, nullptr, kd, gd, m);
       launch_ntt(ctx, limbset_base(acc, acc_is, ext_words, 2, alpha, nq, emap), mi, true, false);
       launch_moddown_bconv_fast(ctx, level, acc + (size_t)nq * n, acc_is, zq, z_is, mi);
       launch_ntt(ctx, limbset_base(zq, z_is, (u64)nq * n, 2, nq, 0, nullptr), mi, false);
@@ -2727,8 +2725,9 @@ extern "C" void hc_graph_destroy(hc_graph* g) {
 // =====================================================================
 // Batched single-ciphertext convolution
 // =====================================================================
-extern "C" int hc_enc_conv2d_single_batch(hc_ctx* ctx, const hc_evk* evk, const hc_ct* const* x, int nimg, int W,
-                                          const hc_ct* const* w, int cout, int kh, int kw, hc_ct** y) {
+namespace {
+int conv2d_single_batch(hc_ctx* ctx, const hc_evk* evk, const hc_ct* const* x, int nimg, int W,
+                        const hc_ct* const* w, int cout, int kh, int kw, hc_ct** y, bool hoisted) {
   if (!ctx) return HC_ERR_INVALID;
   return guard(ctx, [&] {
     HC_CHECK(evk && nimg >= 0 && (nimg == 0 || (x && w && y)) && W > 0 && cout > 0 && kh > 0 && kw > 0,
@@ -2761,47 +2760,56 @@ extern "C" int hc_enc_conv2d_single_batch(hc_ctx* ctx, const hc_evk* evk, const 
       const std::vector<int>& idx = glist[branch].second;
       const int G = (int)idx.size();
       std::vector<BufPtr> keep;
-      // rotated images, step-major: rot[t * G + g]
-      std::vector<hc_ct*> rot = new_cts(ctx, T * G, level, 1, x[idx[0]]->scale);
       std::vector<CtRef> xr;
+      std::vector<const hc_ct*> xg;
       for (int gi = 0; gi < G; ++gi) {
         const hc_ct* c = x[idx[gi]];
         check_scales(c->scale, x[idx[0]]->scale);
         xr.push_back(c->ref());
+        xg.push_back(c);
       }
-      const CtRef* xrd = refs_dev(ctx, xr, keep);
-      // kappa_g of every image for every rotation step into one slab, then one
-      // key switch over all (step, image) items with each step's Galois key
-      int nrot = 0;
-      for (int t = 0; t < T; ++t) nrot += gs[t] != 1;
-      BufPtr tmp = ctx->buffer(std::max<size_t>(1, 2 * (size_t)nrot * G * nq * n));
-      keep.push_back(tmp);
-      std::vector<CtRef> t0, t1, o, src;
-      std::vector<const u64*> ks;
-      std::vector<u64> gitem;  // each (step, image) item's Galois element
-      int nr = 0;              // rotation steps placed so far
-      for (int t = 0; t < T; ++t) {
-        std::vector<CtRef> ot;
-        for (int gi = 0; gi < G; ++gi) ot.push_back(rot[t * G + gi]->ref());
-        if (gs[t] == 1) {
-          launch_ew(ctx, 3, refs_dev(ctx, ot, keep), xrd, nullptr, G, 2, nq);
-          continue;
+      // rotated images, step-major: rot[t * G + g]
+      std::vector<hc_ct*> rot;
+      if (hoisted) {  // one ModUp per image; every step's key switch after it batched
+        std::vector<std::vector<hc_ct*>> hr = rotate_hoisted_batch(ctx, evk, xg, steps);
+        for (int t = 0; t < T; ++t)
+          for (int gi = 0; gi < G; ++gi) rot.push_back(hr[t][gi]);
+      } else {
+        rot = new_cts(ctx, T * G, level, 1, x[idx[0]]->scale);
+        const CtRef* xrd = refs_dev(ctx, xr, keep);
+        // kappa_g of every image for every rotation step into one slab, then one
+        // key switch over all (step, image) items with each step's Galois key
+        int nrot = 0;
+        for (int t = 0; t < T; ++t) nrot += gs[t] != 1;
+        BufPtr tmp = ctx->buffer(std::max<size_t>(1, 2 * (size_t)nrot * G * nq * n));
+        keep.push_back(tmp);
+        std::vector<CtRef> t0, t1, o, src;
+        std::vector<const u64*> ks;
+        std::vector<u64> gitem;  // each (step, image) item's Galois element
+        int nr = 0;              // rotation steps placed so far
+        for (int t = 0; t < T; ++t) {
+          std::vector<CtRef> ot;
+          for (int gi = 0; gi < G; ++gi) ot.push_back(rot[t * G + gi]->ref());
+          if (gs[t] == 1) {
+            launch_ew(ctx, 3, refs_dev(ctx, ot, keep), xrd, nullptr, G, 2, nq);
+            continue;
+          }
+          for (int gi = 0; gi < G; ++gi) {
+            u64* base = tmp->ptr + ((size_t)nr * G + gi) * 2 * nq * n;
+            t0.push_back(CtRef{base, (u64)nq * n});
+            t1.push_back(CtRef{base + (size_t)nq * n, (u64)nq * n});
+            src.push_back(xr[gi]);
+            o.push_back(ot[gi]);
+            ks.push_back(evk->galois.at(gs[t]).buf->ptr);
+            gitem.push_back(gs[t]);
+          }
+          ++nr;
         }
-        for (int gi = 0; gi < G; ++gi) {
-          u64* base = tmp->ptr + ((size_t)nr * G + gi) * 2 * nq * n;
-          t0.push_back(CtRef{base, (u64)nq * n});
-          t1.push_back(CtRef{base + (size_t)nq * n, (u64)nq * n});
-          src.push_back(xr[gi]);
-          o.push_back(ot[gi]);
-          ks.push_back(evk->galois.at(gs[t]).buf->ptr);
-          gitem.push_back(gs[t]);
+        if (!o.empty()) {  // t0 holds each item's (c0, c1) pair: one automorphism launch for all
+          launch_automorph_items(ctx, refs_dev(ctx, t0, keep), refs_dev(ctx, src, keep), (int)o.size(), 2, nq,
+                                 upload(ctx, gitem, keep));
+          keyswitch_batch_keys(ctx, ks, level, t1, &t0, nullptr, o);
         }
-        ++nr;
-      }
-      if (!o.empty()) {  // t0 holds each item's (c0, c1) pair: one automorphism launch for all
-        launch_automorph_items(ctx, refs_dev(ctx, t0, keep), refs_dev(ctx, src, keep), (int)o.size(), 2, nq,
-                               upload(ctx, gitem, keep));
-        keyswitch_batch_keys(ctx, ks, level, t1, &t0, nullptr, o);
       }
       // weights viewed at this level
       std::vector<hc_ct*> wv;
@@ -2830,6 +2838,18 @@ extern "C" int hc_enc_conv2d_single_batch(hc_ctx* ctx, const hc_evk* evk, const 
       free_all(wv);
     });
   });
+}
+}  // namespace
+
+extern "C" int hc_enc_conv2d_single_batch(hc_ctx* ctx, const hc_evk* evk, const hc_ct* const* x, int nimg, int W,
+                                          const hc_ct* const* w, int cout, int kh, int kw, hc_ct** y) {
+  return conv2d_single_batch(ctx, evk, x, nimg, W, w, cout, kh, kw, y, false);
+}
+
+extern "C" int hc_enc_conv2d_single_hoisted_batch(hc_ctx* ctx, const hc_evk* evk, const hc_ct* const* x, int nimg,
+                                                  int W, const hc_ct* const* w, int cout, int kh, int kw,
+                                                  hc_ct** y) {
+  return conv2d_single_batch(ctx, evk, x, nimg, W, w, cout, kh, kw, y, true);
 }
 
 // =====================================================================

@@ -298,7 +298,9 @@ void launch_moddown_bconv_fast(hc_ctx* ctx, int level, const u64* accp_coef, u64
                                u64 z_item_stride, int items);
 void launch_key_product_batched(hc_ctx* ctx, int level, const u64* ext, u64 ext_item_stride, const u64* key,
                                 u64* acc, u64 acc_item_stride, int items, const CtRef* digit_src = nullptr,
-                                const u64* const* item_keys = nullptr);  // per-item keys override `key`
+                                const u64* const* item_keys = nullptr,  // per-item keys override `key`
+                                const u64* gs = nullptr,                // per-item Galois element: read kappa_g(ext)
+                                int ext_items = 0);                     // item z reads ext item z % ext_items
 // Fused relinearise + rescale tail (see hc_kernels.cu).
 void launch_ksr_last(hc_ctx* ctx, int level, const u64* acc, u64 acc_item_stride, const CtRef* base0,
                      const CtRef* base1, u64* tl, int items);

@@ -300,15 +300,23 @@ __global__ void k_tensor_pair(const CtRef* out, const CtRef* a, const CtRef* b, 
 // NTT-domain automorphism: slot k holds a(psi^{e_k}), e_k = 2 brv(k) + 1;
 // kappa_g(a)(psi^{e}) = a(psi^{e g}).
 // gs (may be null): per-item Galois elements, overriding g.
+// The slot of kappa_g's input that lands in slot k of its output, for
+// polynomials in NTT form with bit-reversed evaluation order: slot k holds
+// the evaluation at psi^e, e = 2 brev(k) + 1, and kappa_g(a)(psi^e) =
+// a(psi^{e g}).
+__device__ __forceinline__ int automorph_src(int k, u64 g, int logn) {
+  const u64 mask = (2ull << logn) - 1;
+  const u64 e = 2 * (u64)(__brev((unsigned)k) >> (32 - logn)) + 1;
+  const u64 e2 = (e * g) & mask;
+  return (int)(__brev((unsigned)((e2 - 1) >> 1)) >> (32 - logn));
+}
+
 __global__ void k_automorph(const CtRef* out, const CtRef* a, int nl, u64 g, const u64* gs, Tables T) {
   const int logn = T.log_n, n = 1 << logn;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const int poly = blockIdx.y / nl, l = blockIdx.y % nl, z = blockIdx.z;
-  const u64 mask = 2 * (u64)n - 1;
-  const u64 e = 2 * (u64)(__brev((unsigned)k) >> (32 - logn)) + 1;
-  const u64 e2 = (e * (gs ? gs[blockIdx.z] : g)) & mask;
-  const int src = (int)(__brev((unsigned)((e2 - 1) >> 1)) >> (32 - logn));
+  const int src = automorph_src(k, gs ? gs[blockIdx.z] : g, logn);
   out[z].p[poly * out[z].stride + (size_t)l * n + k] = a[z].p[poly * a[z].stride + (size_t)l * n + src];
 }
 
@@ -343,14 +351,16 @@ __global__ void k_modup_bconv(const u64* xcoef, u64 x_item_stride, u64* ext, u64
 // high word stays below q.
 __global__ void k_key_product(const u64* ext, u64 ext_item_stride, const u64* key, u64* acc,
                               u64 acc_item_stride, int dnum, int next, int nchain, const int* emap,
-                              const u64* const* item_keys, Tables T) {
+                              const u64* const* item_keys, const u64* gs, int ext_items, Tables T) {
   const int n = 1 << T.log_n;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
   const int s = blockIdx.y, z = blockIdx.z;
   const int pid = emap[s];
   const DMod md = T.mods[pid];
-  const u64* e = ext + (size_t)z * ext_item_stride + (size_t)s * n + c;
+  // item z reads the raised digits of item z mod ext_items, through kappa_g when gs is given
+  const int ce = gs ? automorph_src(c, gs[z], T.log_n) : c;
+  const u64* e = ext + (size_t)(z < ext_items ? z : z % ext_items) * ext_item_stride + (size_t)s * n + ce;
   U128 a0{0, 0}, a1{0, 0};
   for (int j = 0; j < dnum; ++j) {
     if (j > 0 && j % 7 == 0) {
@@ -674,7 +684,7 @@ void launch_key_product(hc_ctx* ctx, int level, const u64* ext, u64 ext_item_str
       ProfScope prof_(ctx, "k_key_product", (uint64_t)items * next);
       k_key_product<<<grid_for(ctx, next, items), kT, 0, ctx->stream>>>(
         ext, ext_item_stride, key, acc, acc_item_stride, ctx->lv[level].dnum, next, ctx->P.nchain(),
-        ctx->ext_map_of(level), nullptr, ctx->tab);
+        ctx->ext_map_of(level), nullptr, nullptr, items, ctx->tab);
     }
   LAUNCH_DONE(ctx);
 }
@@ -931,7 +941,8 @@ template <int DNUM, bool HALVES>
 __global__ void __launch_bounds__(kT) k_key_product_t(const u64* ext, u64 ext_item_stride, const u64* key, u64* acc,
                                                        u64 acc_item_stride, int next, int nchain, const int* emap,
                                                        int items, const CtRef* digit_src, int alpha, int nq,
-                                                       const u64* const* item_keys, Tables T) {
+                                                       const u64* const* item_keys, const u64* gs, int ext_items,
+                                                       Tables T) {
   const int n = 1 << T.log_n;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
@@ -957,7 +968,9 @@ __global__ void __launch_bounds__(kT) k_key_product_t(const u64* ext, u64 ext_it
   const int own = (digit_src && s < nq) ? s / alpha : -1;  // the digit whose block holds slot s
   for (int z = blockIdx.z; z < items; z += gridDim.z) {
     if (item_keys) load_keys(item_keys[z]);
-    const u64* e = ext + (size_t)z * ext_item_stride + (size_t)s * n + c;
+    // item z reads the raised digits of item z mod ext_items, through kappa_g when gs is given
+    const int ce = gs ? automorph_src(c, gs[z], T.log_n) : c;
+    const u64* e = ext + (size_t)(z < ext_items ? z : z % ext_items) * ext_item_stride + (size_t)s * n + ce;
     u64* o = acc + (size_t)z * acc_item_stride + (size_t)s * n + c;
     if constexpr (HALVES) {
       // every operand below 2^60: 30-bit halves, carry-free partial sums
@@ -1083,7 +1096,9 @@ void launch_moddown_bconv_fast(hc_ctx* ctx, int level, const u64* accp_coef, u64
 
 void launch_key_product_batched(hc_ctx* ctx, int level, const u64* ext, u64 ext_item_stride, const u64* key,
                                 u64* acc, u64 acc_item_stride, int items, const CtRef* digit_src,
-                                const u64* const* item_keys) {
+                                const u64* const* item_keys, const u64* gs, int ext_items) {
+  if (ext_items <= 0) ext_items = items;
+  HC_CHECK(!(gs && digit_src), HC_ERR_INVALID, "digit sources are not read through an automorphism");
   const int next = level + 1 + ctx->P.alpha, dnum = ctx->lv[level].dnum;
   // a few item groups in z so small batches still fill the GPU
   const int zgroups =
@@ -1096,13 +1111,13 @@ void launch_key_product_batched(hc_ctx* ctx, int level, const u64* ext, u64 ext_
     if (halves)                                                                                                 \
       k_key_product_t<D, true><<<g, kT, 0, ctx->stream>>>(ext, ext_item_stride, key, acc, acc_item_stride,    \
                                                           next, ctx->P.nchain(), ctx->ext_map_of(level), items, \
-                                                          digit_src, ctx->P.alpha, level + 1, item_keys,       \
-                                                          ctx->tab);                                           \
+                                                          digit_src, ctx->P.alpha, level + 1, item_keys, gs,   \
+                                                          ext_items, ctx->tab);                                \
     else                                                                                                        \
       k_key_product_t<D, false><<<g, kT, 0, ctx->stream>>>(ext, ext_item_stride, key, acc, acc_item_stride,   \
                                                            next, ctx->P.nchain(), ctx->ext_map_of(level),      \
                                                            items, digit_src, ctx->P.alpha, level + 1, item_keys, \
-                                                           ctx->tab);                                            \
+                                                           gs, ext_items, ctx->tab);                             \
     break;
   switch (dnum) {
     HC_KP(1) HC_KP(2) HC_KP(3) HC_KP(4) HC_KP(5) HC_KP(6) HC_KP(7) HC_KP(8)
@@ -1110,7 +1125,8 @@ void launch_key_product_batched(hc_ctx* ctx, int level, const u64* ext, u64 ext_
       HC_CHECK(!digit_src, HC_ERR_INVALID, "digit sources need a specialised key product");
       const dim3 g2 = grid_for(ctx, next, items);
       k_key_product<<<g2, kT, 0, ctx->stream>>>(ext, ext_item_stride, key, acc, acc_item_stride, dnum, next,
-                                                ctx->P.nchain(), ctx->ext_map_of(level), item_keys, ctx->tab);
+                                                ctx->P.nchain(), ctx->ext_map_of(level), item_keys, gs, ext_items,
+                                                ctx->tab);
     }
   }
 #undef HC_KP

@@ -44,7 +44,7 @@ EXPORTS = [
     "hc_relin", "hc_rescale", "hc_drop_to_level", "hc_rotate", "hc_rotate_hoisted",
     "hc_mul_relin_rescale_batch", "hc_enc_conv2d", "hc_enc_poly_act", "hc_enc_pool", "hc_enc_fc",
     "hc_relin_noalloc", "hc_graph_begin", "hc_graph_end", "hc_graph_launch", "hc_graph_destroy",
-    "hc_enc_conv2d_single_batch", "hc_enc_fc_rotsum", "hc_ct_import_batch", "hc_ct_export_batch",
+    "hc_enc_conv2d_single_batch", "hc_enc_conv2d_single_hoisted_batch", "hc_enc_fc_rotsum", "hc_ct_import_batch", "hc_ct_export_batch",
     "hc_mul_relin_rescale_host", "hc_autotune", "hc_tune_set", "hc_tune_get", "hc_int_mul_rates",
     "hc_enc_fc_partial", "hc_relin_rescale_batch", "hc_profile_host_timeline",
 ]
@@ -149,6 +149,7 @@ def load(path: str = LIB_PATH):
         "hc_graph_launch": (c_int, [vp]),
         "hc_graph_destroy": (None, [vp]),
         "hc_enc_conv2d_single_batch": (c_int, [vp, vp, pp, c_int, c_int, pp, c_int, c_int, c_int, pp]),
+        "hc_enc_conv2d_single_hoisted_batch": (c_int, [vp, vp, pp, c_int, c_int, pp, c_int, c_int, c_int, pp]),
         "hc_enc_fc_rotsum": (c_int, [vp, vp, pp, c_int, pp, c_int, c_int, pp]),
     }
     for name, (res, args) in sig.items():
@@ -639,6 +640,14 @@ def hc_enc_conv2d_single_batch(ctx, evk, x, W, w, cout, kh, kw):
     outs = _outs(nout)
     _check(ctx, load().hc_enc_conv2d_single_batch(ctx.ptr, evk.ptr, _ptr_array(x), len(x), W, _ptr_array(w), cout,
                                                   kh, kw, outs))
+    return _wrap_outs(ctx, outs, nout)
+
+
+def hc_enc_conv2d_single_hoisted_batch(ctx, evk, x, W, w, cout, kh, kw):
+    nout = len(x) * cout
+    outs = _outs(nout)
+    _check(ctx, load().hc_enc_conv2d_single_hoisted_batch(ctx.ptr, evk.ptr, _ptr_array(x), len(x), W, _ptr_array(w),
+                                                          cout, kh, kw, outs))
     return _wrap_outs(ctx, outs, nout)
 
 

@@ -8,7 +8,7 @@ weights and request ciphertexts stay resident in device memory.  The loop:
 * admits queued requests while the estimated device footprint of everything
   in flight stays under a budget (admission by HBM footprint),
 * groups the admitted requests by ring degree and launches one batched step
-  per group (hc_enc_conv2d_single_batch, then x^2) without waiting
+  per group (hc_enc_conv2d_single_batch or its hoisted form, then x^2) without waiting
   for earlier steps, so work of successive admissions overlaps on the GPU,
 * retires a step when its CUDA event has completed (with a stream per ring
   degree, the events of all the streams: `AllOf`) and records each
@@ -38,6 +38,7 @@ class Model:
     width: int = 8
     kh: int = 3
     kw: int = 3
+    hoisted: bool = False   # rotations hoisted (one ModUp per image) or plain
 
 
 @dataclass
@@ -53,9 +54,11 @@ class Request:
 
 def footprint_bytes(model: Model, level: int) -> int:
     """Device bytes one request holds while in flight: input, kh*kw rotated
-    copies, the kh*kw - 1 automorphed copies and their key-switch workspaces
-    (the rotations of a step run as one batched key switch), tensor outputs
-    and the outputs."""
+    copies, the rotations' key-switch workspaces, tensor outputs and the
+    outputs.  Plain rotations: kh*kw - 1 automorphed copies, each with a
+    whole key-switch workspace (one batched key switch over the steps).
+    Hoisted: one coefficient copy of c1 and its raised digits, then per step
+    the key product, ModDown's conversion and the automorphed c0."""
     n, nq = model.n, level + 1
     alpha = model.n_special
     nxt = nq + alpha
@@ -64,8 +67,12 @@ def footprint_bytes(model: Model, level: int) -> int:
     ct = 2 * nq * limb
     taps = model.kh * model.kw
     rotated = taps * ct
-    ks = (nq + dnum * nxt + 2 * nxt + 2 * nq + 2) * limb
     outs = 3 * nq * limb + 2 * ct
+    if model.hoisted:
+        raised = (nq + dnum * nxt) * limb
+        per_step = (2 * nxt + 2 * nq + nq) * limb
+        return ct + rotated + raised + (taps - 1) * per_step + outs
+    ks = (nq + dnum * nxt + 2 * nxt + 2 * nq + 2) * limb
     return ct + rotated + (taps - 1) * (ct + ks) + outs
 
 
@@ -100,7 +107,8 @@ class Server:
         outputs = []
         for log_n, group in sorted(by_n.items()):
             m = self.models[log_n]
-            y = H.hc_enc_conv2d_single_batch(m.ctx, m.evk, [r.ct for r in group], m.width, m.weights, 1, m.kh, m.kw)
+            conv = H.hc_enc_conv2d_single_hoisted_batch if m.hoisted else H.hc_enc_conv2d_single_batch
+            y = conv(m.ctx, m.evk, [r.ct for r in group], m.width, m.weights, 1, m.kh, m.kw)
             # one activation call over every level of the group (the library
             # runs each level's batch as a concurrent branch)
             for r, a in zip(group, H.hc_enc_poly_act(m.ctx, m.evk, y, (0.0, 0.0, 1.0))):

@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 SETS = [(12, W.SINGLE_N12)] + [(k, W.uneven_params(k)) for k in (13, 14, 15)]
 
 
-def build_models(streams):
+def build_models(streams, hoisted=False):
     models, sks = {}, {}
     for log_n, ps in SETS:
         params = H.hc_params_create(ps.log_n, list(ps.q_bits), list(ps.p_bits), ps.log2_scale)
@@ -26,7 +26,8 @@ def build_models(streams):
         filt = W.conv_weights(60 + log_n, 1, 3, 3)[0, :, :, 0].reshape(-1)
         ws = [H.hc_encrypt(ctx, pk, H.hc_encode(ctx, np.full(ctx.n // 2, v), 2.0 ** 30, ctx.L), 3, t)
               for t, v in enumerate(filt)]
-        models[log_n] = serving.Model(ctx=ctx, evk=evk, weights=ws, n=ctx.n, n_special=len(ps.p_bits))
+        models[log_n] = serving.Model(ctx=ctx, evk=evk, weights=ws, n=ctx.n, n_special=len(ps.p_bits),
+                                      hoisted=hoisted)
         sks[log_n] = (sk, pk)
     return models, sks
 
@@ -46,11 +47,11 @@ def make_requests(models, sks, count, seed):
     return reqs, imgs
 
 
-@pytest.mark.parametrize("per_degree_streams", [False, True])
-def test_served_results_equal_alone_and_decrypt(per_degree_streams):
+@pytest.mark.parametrize("per_degree_streams,hoisted", [(False, False), (True, False), (True, True)])
+def test_served_results_equal_alone_and_decrypt(per_degree_streams, hoisted):
     """One stream for all ring degrees, or one per ring degree (the steps'
     groups then overlap on the device; completion is the event of every
-    stream)."""
+    stream); plain or hoisted rotations."""
     import torch
 
     one_stream = torch.cuda.Stream()
@@ -64,7 +65,7 @@ def test_served_results_equal_alone_and_decrypt(per_degree_streams):
             evs.append(e)
         return serving.AllOf(evs)
 
-    models, sks = build_models(streams)
+    models, sks = build_models(streams, hoisted)
     reqs, imgs = make_requests(models, sks, 24, 500)
     one = serving.footprint_bytes(models[15], 12)
     srv = serving.Server(models=models, budget_bytes=6 * one, max_batch=16)

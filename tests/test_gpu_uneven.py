@@ -1,8 +1,9 @@
 """Batched uneven multi-instance execution: 64 single-ciphertext inferences
 (conv by rotations, then x^2) at mixed ring degrees and levels, run (a) one
 instance at a time through the layer calls, (b) batched per ring degree with
-hc_enc_conv2d_single_batch, (c) captured into one CUDA graph and replayed.
-(a), (b), (c) are bit-identical; sampled instances match the oracle."""
+hc_enc_conv2d_single_batch (or its hoisted form), (c) captured into one CUDA
+graph and replayed.  (a), (b), (c) are bit-identical; sampled instances
+match the oracle in both rotation forms."""
 import numpy as np
 import pytest
 
@@ -65,14 +66,16 @@ def setup():
     return build([stream] * 3)
 
 
-def run_batched(S, mixed=True):
-    """Per ring degree: one conv call over all its instances, then the
-    activation in one call over all levels (mixed) or one call per level."""
+def run_batched(S, mixed=True, hoisted=False):
+    """Per ring degree: one conv call over all its instances (plain or
+    hoisted rotations), then the activation in one call over all levels
+    (mixed) or one call per level."""
     out = [None] * len(S["inst"])
+    conv = H.hc_enc_conv2d_single_hoisted_batch if hoisted else H.hc_enc_conv2d_single_batch
     for log_n, ctx in S["ctxs"].items():
         idx = [i for i, (ln, _) in enumerate(S["inst"]) if ln == log_n]
         evk = S["keys"][log_n][2]
-        y = H.hc_enc_conv2d_single_batch(ctx, evk, [S["xs"][i] for i in idx], 8, S["ws"][log_n], 1, 3, 3)
+        y = conv(ctx, evk, [S["xs"][i] for i in idx], 8, S["ws"][log_n], 1, 3, 3)
         if mixed:
             for i, r in zip(idx, H.hc_enc_poly_act(ctx, evk, y, (0.0, 0.0, 1.0))):
                 out[i] = r
@@ -114,6 +117,44 @@ def test_uneven_batched_and_graph_match_per_instance(setup):
             assert np.array_equal(export(S, i, cap[i]), export(S, i, ref[i])), (rep, i)
     del cap
     del g
+
+
+def test_uneven_hoisted_batch_matches_per_instance_and_graph(setup):
+    """The hoisted batched conv equals hc_enc_conv2d with
+    HC_PACK_SINGLE_HOISTED instance by instance, eager and as a graph."""
+    S = setup
+    ref = []
+    for i, (log_n, lv) in enumerate(S["inst"]):
+        ctx, evk = S["ctxs"][log_n], S["keys"][log_n][2]
+        y = H.hc_enc_conv2d(ctx, evk, H.HC_PACK_SINGLE_HOISTED, [S["xs"][i]], 8, 8, 1, S["ws"][log_n], 1, 3, 3, 1)
+        ref.append(H.hc_enc_poly_act(ctx, evk, y, (0.0, 0.0, 1.0))[0])
+    ref_words = [export(S, i, ref[i]) for i in range(len(ref))]
+    got = run_batched(S, hoisted=True)
+    for i in range(len(ref)):
+        assert np.array_equal(export(S, i, got[i]), ref_words[i]), i
+    ctx_list = [S["ctxs"][k] for k in (13, 14, 15)]
+    H.hc_graph_begin(ctx_list, 32 << 30)
+    cap = run_batched(S, hoisted=True)
+    g = H.hc_graph_end(ctx_list)
+    H.hc_graph_launch(g)
+    for c in ctx_list:
+        H.hc_sync(c)
+    for i in range(len(ref)):
+        assert np.array_equal(export(S, i, cap[i]), ref_words[i]), i
+    del cap
+    del g
+
+
+def test_uneven_hoisted_sampled_instances_match_oracle(setup):
+    S = setup
+    got = run_batched(S, hoisted=True)
+    for i in sorted(SAMPLED):
+        log_n, lv = S["inst"][i]
+        op, osk, opk, oevk = S["oracle_keys"][log_n]
+        (y,) = cnn.enc_conv2d_single_hoisted(op, oevk, S["oxs"][i], 8, S["ows"][log_n], 3, 3, 1)
+        exp = cnn.enc_poly_act(op, oevk, y, (0.0, 0.0, 1.0))
+        data, meta = H.hc_ct_export(S["ctxs"][log_n], got[i])
+        assert meta.level == exp.level == lv - 2 and np.array_equal(data, exp.c), i
 
 
 def test_uneven_sampled_instances_match_oracle(setup):

@@ -46,6 +46,33 @@ def test_admission_respects_budget_and_completes(monkeypatch):
     assert srv.peak_bytes <= 3 * one
 
 
+def test_hoisted_model_calls_the_hoisted_conv_and_is_counted_smaller(monkeypatch):
+    calls = []
+
+    def fake(name):
+        def conv(ctx, evk, xs, W, ws, cout, kh, kw):
+            calls.append(name)
+            return [FakeCt(x.level - 1) for x in xs]
+        return conv
+
+    monkeypatch.setattr(serving.H, "hc_enc_conv2d_single_batch", fake("plain"))
+    monkeypatch.setattr(serving.H, "hc_enc_conv2d_single_hoisted_batch", fake("hoisted"))
+    monkeypatch.setattr(serving.H, "hc_enc_poly_act", lambda ctx, evk, xs, c: [FakeCt(x.level - 1) for x in xs])
+    plain = serving.Model(ctx=None, evk=None, weights=[None] * 9, n=1 << 13, n_special=1)
+    hoisted = serving.Model(ctx=None, evk=None, weights=[None] * 9, n=1 << 13, n_special=1, hoisted=True)
+    # one raised copy of c1 instead of eight whole key-switch workspaces
+    for level in (3, 7, 12):
+        assert serving.footprint_bytes(hoisted, level) < serving.footprint_bytes(plain, level)
+    for model, name in ((plain, "plain"), (hoisted, "hoisted")):
+        calls.clear()
+        srv = serving.Server(models={13: model}, budget_bytes=1 << 40, max_batch=4)
+        for i in range(3):
+            srv.submit(serving.Request(i, 13, FakeCt(5), 0.0))
+        while srv.busy():
+            srv.tick(lambda: FakeEvent(0))
+        assert calls == [name]
+
+
 def test_oversized_request_runs_alone():
     model = serving.Model(ctx=None, evk=None, weights=[None] * 9, n=1 << 12, n_special=1)
     assert serving.footprint_bytes(model, 2) > 0
