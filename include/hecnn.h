@@ -325,9 +325,13 @@ int hc_relin_noalloc(hc_ctx *ctx, const hc_evk *evk, const hc_ct *x, hc_ct *out)
  *                           shared memory of a cluster of N / 2^14 CTAs (one
  *                           CTA up to 2^14), the stages across CTAs through
  *                           distributed shared memory, register rounds of up
- *                           to 5 (3) or 4 (4) stages.  The transforms that
- *                           carry the fused relinearise + rescale tail stay
- *                           two-pass (128-thread tiles under 3 and 4);
+ *                           to 5 (3) or 4 (4) stages; or 5 = the 128-thread
+ *                           two-pass form pipelined (N >= 2^13): as many
+ *                           CTAs as are resident at once, each copying its
+ *                           next tile into shared memory asynchronously while
+ *                           it transforms the current one.  The transforms
+ *                           that carry the fused relinearise + rescale tail
+ *                           stay two-pass (128-thread tiles under 3, 4, 5);
  *   HC_TUNE_KEY_PRODUCT_Z   item groups of a key-product launch, as a
  *                           multiple (1..64) of the default;
  *   HC_TUNE_MODUP_SPLIT     blocks (1..64) over which a ModUp conversion

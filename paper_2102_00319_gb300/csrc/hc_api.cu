@@ -1795,8 +1795,8 @@ extern "C" int hc_tune_set(hc_ctx* ctx, int knob, int value) {
   return guard(ctx, [&] {
     switch (knob) {
       case HC_TUNE_NTT:
-        HC_CHECK(value >= 0 && value <= (ctx->P.log_n >= 13 ? 4 : 1), HC_ERR_INVALID,
-                 "NTT variant must be 0, 1 (or 2..4 for N >= 2^13)");
+        HC_CHECK(value >= 0 && value <= (ctx->P.log_n >= 13 ? 5 : 1), HC_ERR_INVALID,
+                 "NTT variant must be 0, 1 (or 2..5 for N >= 2^13)");
         ctx->tune.ntt_variant[ctx->P.log_n] = value;
         break;
       case HC_TUNE_KEY_PRODUCT_Z:
@@ -1880,7 +1880,7 @@ extern "C" int hc_autotune(hc_ctx* ctx, const hc_evk* evk, int items, char* repo
       double best = 1e300, inc_us = 1e300;
       int pick = incumbent;
       std::string t;
-      for (int v = 0; v <= (ctx->P.log_n >= 13 ? 4 : 1); ++v) {
+      for (int v = 0; v <= (ctx->P.log_n >= 13 ? 5 : 1); ++v) {
         ctx->tune.ntt_variant[ctx->P.log_n] = v;
         const double us = time_us([&] {
           launch_ntt(ctx, cs, m, false);

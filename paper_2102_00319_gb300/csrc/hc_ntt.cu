@@ -330,6 +330,262 @@ __global__ void __launch_bounds__(1 << TL) k_rows(LimbSet s, LimbSet in, int use
   }
 }
 
+// ---------------------------------------------------------------------------
+// Pipelined passes (tuning variant 5).  The same column and row passes as
+// above, with a grid of at most as many CTAs as are resident at once; each
+// CTA walks the tiles t = blockIdx.x, + gridDim.x, ... and, while it
+// transforms tile t in shared memory, copies tile t + gridDim.x into a
+// second buffer with asynchronous 16-byte copies (cp.async), so that the
+// loads of one tile overlap the butterflies of the previous one.  The
+// butterflies and their twiddle indices are those of k_cols / k_rows, so
+// the words are the same.  Plain transforms only (the fused-tail passes
+// keep the per-tile kernels).
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// every committed group but the newest one has landed (this thread's copies)
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Tile t of a pass over tiles_x tiles per limb, ylimbs limb rows per item:
+// its output and input limbs, the limb's prime and the tile's index in it.
+struct PipeTile {
+  u64* a;
+  const u64* ain;
+  int pid;
+  int bx;
+};
+
+template <int LOGN>
+__device__ __forceinline__ PipeTile pipe_tile(const LimbSet& s, const LimbSet& in, int use_in, int t, int tiles_x,
+                                              int ylimbs) {
+  PipeTile p;
+  p.bx = t % tiles_x;
+  const int yz = t / tiles_x;
+  const int y = yz % ylimbs, z = yz / ylimbs;
+  const int k = y / s.nlimb, l = y - k * s.nlimb;
+  const int slot = s.slot_map ? s.slot_map[l] : s.l0 + l;
+  p.a = limb_ptr(s, z, k, slot, 1 << LOGN);
+  p.pid = limb_prime(s, slot);
+  p.ain = use_in ? limb_ptr(in, z, k, in.l0 + l, 1 << LOGN) : p.a;
+  return p;
+}
+
+// Column pass, pipelined.  Shared tile [row][col] as in k_cols, each group
+// of 2^K2 rows shifted by 8 more words, so that the 2^K2-adjacent-row round
+// reads whole 128-byte bank lines.
+template <bool INV, int LOGN, int K1, int K2, int TCL, int TL>
+__global__ void __launch_bounds__(1 << TL) k_cols_pipe(LimbSet s, LimbSet in, int use_in, int scale, int tiles_x,
+                                                       int ylimbs, int total, Tables T) {
+  constexpr int N1 = K1 + K2, N2 = LOGN - N1, TC = 1 << TCL;
+  constexpr u32 kThreads = 1u << TL;
+  constexpr int TILE = (1 << (N1 + TCL)) + (8 << K1);
+  static_assert(TCL >= 1, "16-byte copies need two columns per row");
+  extern __shared__ __align__(16) u64 sm[];
+  auto sidx = [](u32 row, u32 c) { return (row << TCL) + c + ((row >> K2) << 3); };
+  int t = blockIdx.x;
+  if (t >= total) return;
+  auto fetch = [&](int tt, u64* buf) {
+    const PipeTile p = pipe_tile<LOGN>(s, in, use_in, tt, tiles_x, ylimbs);
+    const u64* g = p.ain + p.bx * TC;
+    const bool aligned = ((reinterpret_cast<uintptr_t>(g) & 15) == 0);
+    for (u32 ch = threadIdx.x; ch < (TILE - (8 << K1)) / 2; ch += kThreads) {
+      const u32 row = ch >> (TCL - 1), c = (ch & ((TC >> 1) - 1)) << 1;
+      const u64* src = g + ((size_t)row << N2) + c;
+      if (aligned) {
+        cp_async16(buf + sidx(row, c), src);
+      } else {  // plain loads for a limb that does not start on a 16-byte boundary
+        buf[sidx(row, c)] = src[0];
+        buf[sidx(row, c) + 1] = src[1];
+      }
+    }
+  };
+  int cur = 0;
+  fetch(t, sm);
+  cp_async_commit();
+  for (; t < total; t += gridDim.x) {
+    if (t + (int)gridDim.x < total) fetch(t + gridDim.x, sm + (cur ^ 1) * TILE);
+    cp_async_commit();
+    cp_async_wait_prev();
+    __syncthreads();
+    u64* buf = sm + cur * TILE;
+    const PipeTile p = pipe_tile<LOGN>(s, in, use_in, t, tiles_x, ylimbs);
+    const u64 q = T.mods[p.pid].q;
+    const ulonglong2* tw = (INV ? T.inv2 : T.fwd2) + ((size_t)p.pid << LOGN);
+    u64* a = p.a + p.bx * TC;
+    if (!INV) {
+      // 2^K1 rows strided by 2^K2 -> stages 0..K1-1, in place
+      for (u32 w = threadIdx.x; w < (TC << K2); w += kThreads) {
+        const u32 c = w & (TC - 1), r0 = w >> TCL;
+        u64 x[1 << K1];
+#pragma unroll
+        for (int i = 0; i < (1 << K1); ++i) x[i] = buf[sidx(r0 + (i << K2), c)];
+        fwd_block<K1, K2 + N2, 0, LOGN>(x, r0 << N2, tw, q);
+#pragma unroll
+        for (int i = 0; i < (1 << K1); ++i) buf[sidx(r0 + (i << K2), c)] = x[i];
+      }
+      __syncthreads();
+      // 2^K2 adjacent rows -> stages K1..N1-1, to global memory
+      for (u32 w = threadIdx.x; w < (TC << K1); w += kThreads) {
+        const u32 c = w & (TC - 1), g = w >> TCL;
+        u64 x[1 << K2];
+#pragma unroll
+        for (int i = 0; i < (1 << K2); ++i) x[i] = buf[sidx((g << K2) + i, c)];
+        fwd_block<K2, N2, K1, LOGN>(x, (g << K2) << N2, tw, q);
+#pragma unroll
+        for (int i = 0; i < (1 << K2); ++i) a[(((g << K2) + i) << N2) + c] = reduce4(x[i], q);
+      }
+    } else {
+      // 2^K2 adjacent rows -> stages N1-1 .. K1, in place
+      for (u32 w = threadIdx.x; w < (TC << K1); w += kThreads) {
+        const u32 c = w & (TC - 1), g = w >> TCL;
+        u64 x[1 << K2];
+#pragma unroll
+        for (int i = 0; i < (1 << K2); ++i) x[i] = buf[sidx((g << K2) + i, c)];
+        inv_block<K2, N2, N1 - 1, LOGN>(x, (g << K2) << N2, tw, q);
+#pragma unroll
+        for (int i = 0; i < (1 << K2); ++i) buf[sidx((g << K2) + i, c)] = x[i];
+      }
+      __syncthreads();
+      // 2^K1 rows strided by 2^K2 -> stages K1-1 .. 0, then N^{-1}, to global memory
+      const u64 ni = T.ninv[p.pid], nis = T.ninv_sh[p.pid];
+      for (u32 w = threadIdx.x; w < (TC << K2); w += kThreads) {
+        const u32 c = w & (TC - 1), r0 = w >> TCL;
+        u64 x[1 << K1];
+#pragma unroll
+        for (int i = 0; i < (1 << K1); ++i) x[i] = buf[sidx(r0 + (i << K2), c)];
+        inv_block<K1, K2 + N2, K1 - 1, LOGN>(x, r0 << N2, tw, q);
+#pragma unroll
+        for (int i = 0; i < (1 << K1); ++i)
+          a[((r0 + (i << K2)) << N2) + c] = reduce4(scale ? shoup_lazy(x[i], ni, nis, q) : x[i], q);
+      }
+    }
+    __syncthreads();  // the buffer is refilled two tiles on
+    cur ^= 1;
+  }
+  cp_async_wait_all();
+}
+
+// Row pass, pipelined.  Rows padded by two words per 2^K2 (the 16-byte
+// copies stay aligned; the strided round reads whole bank lines and the
+// adjacent round reads 16-byte pairs without conflicts).
+template <bool INV, int LOGN, int K1, int K2, int RPL, int TL>
+__global__ void __launch_bounds__(1 << TL) k_rows_pipe(LimbSet s, LimbSet in, int use_in, int tiles_x, int ylimbs,
+                                                       int total, Tables T) {
+  constexpr u32 kThreads = 1u << TL;
+  constexpr int N2 = K1 + K2, N1 = LOGN - N2, C = 1 << N2, RP = 1 << RPL;
+  constexpr int PADW = C + (C >> (K2 - 1));
+  constexpr int TILE = RP * PADW;
+  static_assert(K2 >= 1, "16-byte pairs need two adjacent points");
+  extern __shared__ __align__(16) u64 sm[];
+  auto sidx = [](u32 r, u32 j) { return r * PADW + j + ((j >> K2) << 1); };
+  int t = blockIdx.x;
+  if (t >= total) return;
+  auto fetch = [&](int tt, u64* buf) {
+    const PipeTile p = pipe_tile<LOGN>(s, in, use_in, tt, tiles_x, ylimbs);
+    const u64* g = p.ain + ((size_t)p.bx * RP << N2);
+    const bool aligned = ((reinterpret_cast<uintptr_t>(g) & 15) == 0);
+    for (u32 ch = threadIdx.x; ch < (RP << N2) / 2; ch += kThreads) {
+      const u32 e = ch << 1, r = e >> N2, j = e & (C - 1);
+      if (aligned) {
+        cp_async16(buf + sidx(r, j), g + e);
+      } else {
+        buf[sidx(r, j)] = g[e];
+        buf[sidx(r, j) + 1] = g[e + 1];
+      }
+    }
+  };
+  int cur = 0;
+  fetch(t, sm);
+  cp_async_commit();
+  for (; t < total; t += gridDim.x) {
+    if (t + (int)gridDim.x < total) fetch(t + gridDim.x, sm + (cur ^ 1) * TILE);
+    cp_async_commit();
+    cp_async_wait_prev();
+    __syncthreads();
+    u64* buf = sm + cur * TILE;
+    const PipeTile p = pipe_tile<LOGN>(s, in, use_in, t, tiles_x, ylimbs);
+    const u64 q = T.mods[p.pid].q;
+    const ulonglong2* tw = (INV ? T.inv2 : T.fwd2) + ((size_t)p.pid << LOGN);
+    const u32 row0 = p.bx * RP;
+    u64* dst = p.a + ((size_t)row0 << N2);
+    if (!INV) {
+      // 2^K1 points strided by 2^K2 -> stages N1 .. N1+K1-1, in place
+      for (u32 w = threadIdx.x; w < (RP << K2); w += kThreads) {
+        const u32 r = w >> K2, r0 = w & ((1 << K2) - 1);
+        u64 x[1 << K1];
+#pragma unroll
+        for (int i = 0; i < (1 << K1); ++i) x[i] = buf[sidx(r, r0 + (i << K2))];
+        fwd_block<K1, K2, N1, LOGN>(x, ((row0 + r) << N2) + r0, tw, q);
+#pragma unroll
+        for (int i = 0; i < (1 << K1); ++i) buf[sidx(r, r0 + (i << K2))] = x[i];
+      }
+      __syncthreads();
+      // 2^K2 adjacent points -> the last K2 stages, reduced, in place
+      for (u32 w = threadIdx.x; w < (RP << K1); w += kThreads) {
+        const u32 r = w >> K1, g = w & ((1 << K1) - 1);
+        ulonglong2* v2 = reinterpret_cast<ulonglong2*>(buf + sidx(r, g << K2));
+        u64 x[1 << K2];
+#pragma unroll
+        for (int i = 0; i < (1 << K2); i += 2) {
+          const ulonglong2 v = v2[i >> 1];
+          x[i] = v.x;
+          x[i + 1] = v.y;
+        }
+        fwd_block<K2, 0, N1 + K1, LOGN>(x, ((row0 + r) << N2) + (g << K2), tw, q);
+#pragma unroll
+        for (int i = 0; i < (1 << K2); i += 2) v2[i >> 1] = make_ulonglong2(reduce4(x[i], q), reduce4(x[i + 1], q));
+      }
+      __syncthreads();
+      // row-contiguous 16-byte stores
+      const bool aligned = ((reinterpret_cast<uintptr_t>(dst) & 15) == 0);
+      for (u32 ch = threadIdx.x; ch < (RP << N2) / 2; ch += kThreads) {
+        const u32 e = ch << 1, r = e >> N2, j = e & (C - 1);
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(buf + sidx(r, j));
+        if (aligned) {
+          *reinterpret_cast<ulonglong2*>(dst + e) = v;
+        } else {
+          dst[e] = v.x;
+          dst[e + 1] = v.y;
+        }
+      }
+    } else {
+      // 2^K2 adjacent points -> stages LOGN-1 .. LOGN-K2, in place
+      for (u32 w = threadIdx.x; w < (RP << K1); w += kThreads) {
+        const u32 r = w >> K1, g = w & ((1 << K1) - 1);
+        ulonglong2* v2 = reinterpret_cast<ulonglong2*>(buf + sidx(r, g << K2));
+        u64 x[1 << K2];
+#pragma unroll
+        for (int i = 0; i < (1 << K2); i += 2) {
+          const ulonglong2 v = v2[i >> 1];
+          x[i] = v.x;
+          x[i + 1] = v.y;
+        }
+        inv_block<K2, 0, LOGN - 1, LOGN>(x, ((row0 + r) << N2) + (g << K2), tw, q);
+#pragma unroll
+        for (int i = 0; i < (1 << K2); i += 2) v2[i >> 1] = make_ulonglong2(x[i], x[i + 1]);
+      }
+      __syncthreads();
+      // 2^K1 points strided by 2^K2 -> stages LOGN-K2-1 .. N1, to global memory
+      for (u32 w = threadIdx.x; w < (RP << K2); w += kThreads) {
+        const u32 r = w >> K2, r0 = w & ((1 << K2) - 1);
+        u64 x[1 << K1];
+#pragma unroll
+        for (int i = 0; i < (1 << K1); ++i) x[i] = buf[sidx(r, r0 + (i << K2))];
+        inv_block<K1, K2, LOGN - 1 - K2, LOGN>(x, ((row0 + r) << N2) + r0, tw, q);
+#pragma unroll
+        for (int i = 0; i < (1 << K1); ++i) dst[(r << N2) + r0 + (i << K2)] = reduce4(x[i], q);
+      }
+    }
+    __syncthreads();  // the buffer is refilled two tiles on
+    cur ^= 1;
+  }
+  cp_async_wait_all();
+}
+
 // Pass geometry for ring degree 2^LOGN: the column pass takes floor(LOGN/2)
 // stages, the row pass the rest; each pass splits into two register rounds.
 template <int n>
@@ -390,6 +646,49 @@ void launch_pass_rows_t(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, co
   else
     k_rows<INV, LOGN, Sp::K1, Sp::K2, RPL, false, TL><<<grid, 1 << TL, smem, ctx->stream>>>(
         s, in ? *in : s, in ? 1 : 0, KsrFuse{}, ctx->tab);
+}
+
+// Pipelined passes: 128-thread CTAs, as many as are resident at once (at
+// most one per tile).
+template <typename K>
+int pipe_grid(hc_ctx* ctx, K kern, size_t smem, long long total) {
+  int per_sm = 0, sms = 0;
+  HC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem));
+  HC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+  return (int)std::min<long long>(total, (long long)std::max(1, per_sm) * sms);
+}
+
+template <bool INV, int LOGN>
+void launch_pass_cols_pipe(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, const LimbSet* in, bool scale) {
+  constexpr int TL = 7, N1 = LOGN / 2, N2 = LOGN - N1;
+  using Sp = Split<N1>;
+  constexpr int TCL = ColTile<N1, N2, TL>::TCL;
+  constexpr int TILE = (1 << (N1 + TCL)) + (8 << Sp::K1);
+  const int tiles_x = 1 << (N2 - TCL);
+  const long long total = (long long)tiles_x * ylimbs * items;
+  HC_CHECK(total < (1ll << 31), HC_ERR_INVALID, "NTT batch too large");
+  const size_t smem = 2 * (size_t)TILE * sizeof(u64);
+  auto kern = k_cols_pipe<INV, LOGN, Sp::K1, Sp::K2, TCL, TL>;
+  const int grid = pipe_grid(ctx, kern, smem, total);
+  ProfScope p(ctx, INV ? "ntt_inv_cols" : "ntt_fwd_cols", (uint64_t)ylimbs * items);
+  kern<<<grid, 1 << TL, smem, ctx->stream>>>(s, in ? *in : s, in ? 1 : 0, scale ? 1 : 0, tiles_x, ylimbs,
+                                             (int)total, ctx->tab);
+}
+
+template <bool INV, int LOGN>
+void launch_pass_rows_pipe(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, const LimbSet* in) {
+  constexpr int TL = 7, N1 = LOGN / 2, N2 = LOGN - N1;
+  using Sp = Split<N2>;
+  constexpr int RPL = RowTile<N1, N2, TL>::RPL;
+  constexpr int PADW = (1 << N2) + ((1 << N2) >> (Sp::K2 - 1));
+  const int tiles_x = 1 << (N1 - RPL);
+  const long long total = (long long)tiles_x * ylimbs * items;
+  HC_CHECK(total < (1ll << 31), HC_ERR_INVALID, "NTT batch too large");
+  const size_t smem = 2 * ((size_t)1 << RPL) * PADW * sizeof(u64);
+  auto kern = k_rows_pipe<INV, LOGN, Sp::K1, Sp::K2, RPL, TL>;
+  const int grid = pipe_grid(ctx, kern, smem, total);
+  ProfScope p(ctx, INV ? "ntt_inv_rows" : "ntt_fwd_rows", (uint64_t)ylimbs * items);
+  kern<<<grid, 1 << TL, smem, ctx->stream>>>(s, in ? *in : s, in ? 1 : 0, tiles_x, ylimbs, (int)total, ctx->tab);
 }
 
 // variant 0: 256-thread blocks, 1: 128-thread blocks, 2: 64-thread blocks
@@ -665,6 +964,19 @@ void ntt_logn(hc_ctx* ctx, const LimbSet& s, int items, int ylimbs, bool inverse
         else launch_onepass<false, LOGN, 0>(ctx, s, items, ylimbs, in, scale);
       }
       ctx->launches -= 1;  // one launch instead of two (the caller counts two)
+      return;
+    }
+  }
+  if constexpr (LOGN >= 13) {
+    // variant 5: pipelined two-pass transforms (fused-tail ones as variant 1)
+    if (!fuse && ctx->tune.ntt_variant[LOGN] == 5) {
+      if (!inverse) {
+        launch_pass_cols_pipe<false, LOGN>(ctx, s, items, ylimbs, in, true);
+        launch_pass_rows_pipe<false, LOGN>(ctx, s, items, ylimbs, nullptr);
+      } else {
+        launch_pass_rows_pipe<true, LOGN>(ctx, s, items, ylimbs, in);
+        launch_pass_cols_pipe<true, LOGN>(ctx, s, items, ylimbs, nullptr, scale);
+      }
       return;
     }
   }

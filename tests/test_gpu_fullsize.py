@@ -65,7 +65,7 @@ def test_deep_n16_batch_sampled_bit_exact():
         np.testing.assert_array_equal(host[i], eager[i])
     # the other NTT tile shapes at N = 2^16 (autotuning choices) give the same words
     default = H.hc_tune_get(p.ctx, H.HC_TUNE_NTT)
-    for v in (0, 1, 2, 3, 4):
+    for v in (0, 1, 2, 3, 4, 5):
         H.hc_tune_set(p.ctx, H.HC_TUNE_NTT, v)
         r = H.hc_mul_relin_rescale_batch(p.ctx, p.g_evk, [A[k] for k in ks], [Bc[k] for k in ks])
         for k, c in zip(ks, r):

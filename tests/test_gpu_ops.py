@@ -205,9 +205,9 @@ def test_autotune_and_every_tuning_choice_bit_identical(pair):
 @pytest.mark.parametrize("log_n", [13, 14, 15, 16])
 def test_ntt_tile_variants_match_oracle(log_n):
     """Every NTT form the tuner can pick at N = 2^13..2^16 (two-pass block
-    sizes including the 64-thread tiles that exist only there, and the
+    sizes including the 64-thread tiles that exist only there, the
     single-pass transforms on one CTA (2^13, 2^14) or a cluster of two or
-    four (2^15, 2^16)) gives the oracle's words for a multiply + relinearise
+    four (2^15, 2^16), and the pipelined two-pass form) gives the oracle's words for a multiply + relinearise
     + rescale, a rotation and the host-to-host call."""
     from hc_pair import Pair
     p = Pair(log_n, [50, 30, 30], [50], 30, seed=70 + log_n, rot_steps=[5])
@@ -216,14 +216,14 @@ def test_ntt_tile_variants_match_oracle(log_n):
     gb, ob = p.encrypt_values(W.slot_values(72, op.K), nonce=2)
     want_m = ckks.rescale(op, ckks.relin(op, p.o_evk, ckks.mul(op, oa, ob)))
     want_r = ckks.rotate(op, p.o_evk, oa, 5)
-    for v in (0, 1, 2, 3, 4):
+    for v in (0, 1, 2, 3, 4, 5):
         H.hc_tune_set(p.ctx, H.HC_TUNE_NTT, v)
         p.assert_same(H.hc_mul_relin_rescale_batch(p.ctx, p.g_evk, [ga], [gb])[0], want_m, "mul v=%d" % v)
         p.assert_same(H.hc_rotate(p.ctx, p.g_evk, ga, 5), want_r, "rot v=%d" % v)
         outs, metas = _host_products(p, [ga], [gb], op.L)
         _assert_host_same(outs[0], metas[0], want_m, "host v=%d" % v)
     with pytest.raises(H.HcError):
-        H.hc_tune_set(p.ctx, H.HC_TUNE_NTT, 5)
+        H.hc_tune_set(p.ctx, H.HC_TUNE_NTT, 6)
 
 
 def test_batch_larger_than_workspace_chunk(pair):

@@ -124,3 +124,73 @@ def test_row_pass_covers_each_coefficient_once(logn, tl):
         k_u = 4
         assert k_tile % (threads * k_u) == 0
     assert np.all(reads == 1) and np.all(writes == 1)
+
+
+@pytest.mark.parametrize("logn", [13, 14, 15, 16])
+def test_pipelined_passes_index_arithmetic(logn):
+    """The pipelined passes (tuning variant 5, 128-thread CTAs): the 16-byte
+    asynchronous copies of a tile land on 16-byte-aligned shared-memory
+    words inside the buffer and cover the tile once; both register rounds
+    read and write exactly the staged words; the global reads and writes of
+    a tile stay inside its limb; two buffers fit in 48 KB."""
+    n1 = logn // 2
+    n2 = logn - n1
+    # column pass: rows of TC words, each group of 2^K2 rows shifted by 8 words
+    k1, k2, _ = split(n1)
+    tcl = col_tile(n1, n2, 7)
+    tc = 1 << tcl
+    tile = (1 << (n1 + tcl)) + (8 << k1)
+
+    def sidx(row, c):
+        return (row << tcl) + c + ((row >> k2) << 3)
+
+    tiles_x = 1 << (n2 - tcl)
+    staged, gmax = set(), 0
+    for ch in range((1 << (n1 + tcl)) // 2):
+        row, c = ch >> (tcl - 1), (ch & ((tc >> 1) - 1)) << 1
+        d = sidx(row, c)
+        assert d % 2 == 0 and d + 1 < tile and sidx(row, c + 1) == d + 1
+        staged.update((d, d + 1))
+        gmax = max(gmax, (tiles_x - 1) * tc + (row << n2) + c + 1)
+    assert gmax < (1 << logn) and len(staged) == (1 << n1) * tc
+    strided, adjacent, out = set(), set(), set()
+    for w in range(tc << k2):
+        c, r0 = w & (tc - 1), w >> tcl
+        strided.update(sidx(r0 + (i << k2), c) for i in range(1 << k1))
+    for w in range(tc << k1):
+        c, g = w & (tc - 1), w >> tcl
+        for i in range(1 << k2):
+            adjacent.add(sidx((g << k2) + i, c))
+            out.add((((g << k2) + i) << n2) + c)
+    assert strided == adjacent == staged
+    assert len(out) == (1 << n1) * tc and max(out) + (tiles_x - 1) * tc < (1 << logn)
+    assert 2 * tile * 8 <= SMEM_LIMIT
+    # row pass: RP rows of C words, two words of padding per 2^K2
+    k1, k2, _ = split(n2)
+    rpl, _ = row_tile(n1, n2, 7)
+    rp, c_ = 1 << rpl, 1 << n2
+    padw = c_ + (c_ >> (k2 - 1))
+
+    def sidr(r, j):
+        return r * padw + j + ((j >> k2) << 1)
+
+    staged = set()
+    for ch in range((rp << n2) // 2):
+        e = ch << 1
+        r, j = e >> n2, e & (c_ - 1)
+        d = sidr(r, j)
+        assert d % 2 == 0 and d + 1 < rp * padw and sidr(r, j + 1) == d + 1
+        staged.update((d, d + 1))
+    assert len(staged) == rp * c_
+    strided, adjacent = set(), set()
+    for w in range(rp << k2):
+        r, r0 = w >> k2, w & ((1 << k2) - 1)
+        strided.update(sidr(r, r0 + (i << k2)) for i in range(1 << k1))
+    for w in range(rp << k1):
+        r, g = w >> k1, w & ((1 << k1) - 1)
+        base = sidr(r, g << k2)
+        assert base % 2 == 0 and all(sidr(r, (g << k2) + i) == base + i for i in range(1 << k2))
+        adjacent.update(base + i for i in range(1 << k2))
+    assert strided == adjacent == staged
+    assert (1 << (n1 - rpl)) * rp * c_ == 1 << logn
+    assert 2 * rp * padw * 8 <= SMEM_LIMIT
