@@ -9,11 +9,14 @@ pairs already resident in HBM (B pairs occupy far more than the 129 MB L2,
 so no flush is needed between steps).
 
 The JSON line also carries:
-  e2e           the same metric through the C ABI from pinned HOST buffers
-                (coefficient-form import, forward NTT, the operation with
-                its relinearise + rescale tail carried by the inverse NTT,
-                coefficient-form export), with the plain pinned-copy rates
-                of the same buffers measured beside it,
+  e2e           the same metric through the C ABI from pinned HOST buffers:
+                by default ciphertexts in evaluation form in and out
+                (hc_mul_relin_rescale_host_eval: range check, the
+                operation, copies overlapped chunk by chunk); the
+                coefficient-form call (forward NTT of the inputs, the
+                relinearise + rescale tail carried by the inverse NTT) is
+                timed briefly beside it (e2e_detail.other_form), with the
+                plain pinned-copy rates of the same buffers,
   roofline      the dominant kernel's algorithmic bytes / its device time
                 (CUDA events around every launch on the context stream),
   cpu_baseline  the CPU oracle on this host (bounded sample, rank 0, N=1),
@@ -52,6 +55,9 @@ def parse():
                     help="device arena of the captured step (0: 4 GiB + 0.2 GiB per pair)")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--e2e-chunk", type=int, default=0, help="pairs per pipeline chunk of the host call (0: auto)")
+    ap.add_argument("--e2e-form", choices=("eval", "coeff"), default="eval",
+                    help="host buffers in evaluation (NTT) form or coefficient form; the other form is timed briefly "
+                         "for e2e_detail")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-ops", type=int, default=1, help="oracle operations in the CPU sample")
     ap.add_argument("--no-cnn", action="store_true", help="skip the encrypted-CNN images/s leg")
@@ -71,6 +77,9 @@ def parse():
                     help="force HC_TUNE_NTT for the main step (0-2 two-pass block sizes, 3-4 single-pass) after tuning")
     ap.add_argument("--profile-cnn", action="store_true",
                     help="run one batched pass of the N=2^14 CNN between cudaProfilerStart/Stop, and exit")
+    ap.add_argument("--profile-uneven", action="store_true",
+                    help="run one hoisted batched pass of the 64 uneven instances between cudaProfilerStart/Stop, "
+                         "and exit")
     ap.add_argument("--probe-intmul", action="store_true",
                     help="print the integer-multiply throughputs of this GPU (hc_int_mul_rates), and exit")
     ap.add_argument("--probe-tc-conversion", action="store_true",
@@ -78,7 +87,8 @@ def parse():
     ap.add_argument("--summarize-ncu", metavar="CSV",
                     help="summarise an ncu launch list (gpu__time_duration.sum) of the timed step and exit")
     ap.add_argument("--step-occurrence", type=int, default=2,
-                    help="which occurrence of the step's first kernel starts the timed step (warm-up = 1)")
+                    help="which occurrence of the step's first kernel starts the timed step (warm-up = 1; "
+                         "0 = every launch in the list)")
     return ap.parse_args()
 
 
@@ -92,13 +102,16 @@ def summarize_ncu(path, occurrence):
     rows = [r for r in csv.DictReader(l for l in open(path) if l.startswith('"'))
             if r.get("Metric Name") == "gpu__time_duration.sum"]
     names = [re.sub(r"^.*?::", "", r["Kernel Name"]).split("(")[0].split("<")[0] for r in rows]
-    starts = [i for i, n in enumerate(names) if n == "k_tensor_pair"]
-    a = starts[occurrence - 1]
-    b = starts[occurrence] if occurrence < len(starts) else len(rows)
-    # the step ends with the forward NTT (column then row pass) that carries the
-    # fused relinearise + rescale tail, right after the c_l kernel
-    ends = [i for i in range(a, b) if names[i] == "k_ksr_cl"]
-    b = min(ends[-1] + 3, b)
+    if occurrence == 0:  # every launch of the list (a capture of one profiled region)
+        a, b = 0, len(rows)
+    else:
+        starts = [i for i, n in enumerate(names) if n == "k_tensor_pair"]
+        a = starts[occurrence - 1]
+        b = starts[occurrence] if occurrence < len(starts) else len(rows)
+        # the step ends with the forward NTT (column then row pass) that carries the
+        # fused relinearise + rescale tail, right after the c_l kernel
+        ends = [i for i in range(a, b) if names[i] == "k_ksr_cl"]
+        b = min(ends[-1] + 3, b)
     per = {}
     for i in range(a, b):
         t = float(rows[i]["Metric Value"]) * (1e-3 if rows[i]["Metric Unit"] == "ns" else 1.0)
@@ -666,7 +679,7 @@ def cnn_sharded_leg(H, W, np, torch, local, rank, world):
             "max_logit_error_vs_fp64": err}
 
 
-def uneven_leg(H, W, np, torch, local):
+def uneven_leg(H, W, np, torch, local, profile_only=False):
     """64 independent single-ciphertext inferences (8x8 image, 3x3 conv by
     rotations, x^2) at N = 2^13 / 2^14 / 2^15 and 3..12 levels, run four ways:
     one ABI call per HE op, one layer call per instance, batched per ring
@@ -756,6 +769,16 @@ def uneven_leg(H, W, np, torch, local):
         del g
         return t_g, words
 
+    if profile_only:  # one hoisted batched pass between profiler start and stop (ncu launch lists)
+        for _ in range(2):
+            batched(True)
+        sync()
+        torch.cuda.profiler.start()
+        batched(True)
+        sync()
+        torch.cuda.profiler.stop()
+        print("profiled one hoisted batched pass of the 64 uneven instances")
+        return None
     forms, same = {}, True
     for hoisted in (False, True):
         t_op, r_op = timed(lambda: per_op(hoisted), 1)
@@ -1046,6 +1069,9 @@ def run_gpu(args, rank, world, local):
     if args.profile_cnn:
         cnn_leg(args, H, W, np, torch, local, profile_only=True)
         return
+    if args.profile_uneven:
+        uneven_leg(H, W, np, torch, local, profile_only=True)
+        return
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
@@ -1164,9 +1190,13 @@ def run_gpu(args, rank, world, local):
     per_op_value = Bn * 2 * world / max_over_ranks(time.perf_counter() - t0, device="cuda")
 
     # ---------------- e2e through the C ABI from pinned host memory
+    # the ciphertexts as a client holds them: evaluation form (the form the
+    # device computes in, hc_ct_export_eval) or coefficient form (hc_ct_export)
+    eval_form = args.e2e_form == "eval"
+    export = H.hc_ct_export_eval if eval_form else H.hc_ct_export
     host_in = []
     for c in A + Bc:
-        data, meta = H.hc_ct_export(ctx, c)
+        data, meta = export(ctx, c)
         pin = torch.empty(data.size, dtype=torch.int64, pin_memory=True)
         arr = pin.numpy().view(np.uint64).reshape(data.shape)
         arr[...] = data
@@ -1180,14 +1210,13 @@ def run_gpu(args, rank, world, local):
     in_arrays = [a for _, a, _ in host_in]
     in_metas = [(m.level, m.degree, m.scale) for _, _, m in host_in]
 
-    def e2e_step():
+    def e2e_step(form=None):
         # pinned host buffers in, pinned host buffers out: copies in, the batched
         # operation and copies out overlap chunk by chunk inside the call
+        ev = eval_form if form is None else form
         return H.hc_mul_relin_rescale_host(ctx, evk, in_arrays[:Bn], in_metas[:Bn], in_arrays[Bn:], in_metas[Bn:],
-                                           out_arrays, chunk=args.e2e_chunk)
+                                           out_arrays, chunk=args.e2e_chunk, eval_form=ev)
 
-    for _ in range(5 if args.e2e_steps > 0 else 0):  # untimed: the memory pool reaches its steady size
-        e2e_step()
     # the plain pinned-copy rates of the same buffers on this machine, for reading
     # the e2e number (the host link is shared with the box's other GPUs)
     copy_gbs = None
@@ -1209,10 +1238,13 @@ def run_gpu(args, rank, world, local):
         barrier()
         copy_gbs = {"h2d": h2d / c0.elapsed_time(c1) / 1e6, "d2h": d2h / c1.elapsed_time(c2) / 1e6}
         del staging
+    for _ in range(5 if args.e2e_steps > 0 else 0):  # untimed: the memory pool reaches its steady size
+        e2e_step()
     barrier()
     t0 = time.perf_counter()
     e2e_marks = []  # each call returns with its outputs in host memory
     e2e_calls = []  # per call, from its event timeline: (copies in, kernels, device span) in ms
+    slowest_tl = None
     for _ in range(args.e2e_steps):
         e2e_step()
         e2e_marks.append(time.perf_counter())
@@ -1220,6 +1252,8 @@ def run_gpu(args, rank, world, local):
         if tl:
             e2e_calls.append([round(tl[-1][1] - tl[0][0], 2), round(sum(c[3] - c[2] for c in tl), 2),
                               round(tl[-1][5], 2)])
+            if e2e_calls[-1][2] >= max(c[2] for c in e2e_calls):  # the slowest call's chunks, to read outliers from
+                slowest_tl = [[round(v, 2) for v in c] for c in tl]
     barrier()
     t_e2e = max_over_ranks(max(time.perf_counter() - t0, 1e-9), device="cuda")
     e2e_step_ms = [round(1000.0 * (b - a), 2) for a, b in zip([t0] + e2e_marks[:-1], e2e_marks)]
@@ -1229,9 +1263,25 @@ def run_gpu(args, rank, world, local):
     e2e_timeline = [[round(v, 2) for v in c] for c in H.hc_profile_host_timeline(ctx)] if args.e2e_steps else None
     if args.e2e_steps > 0:  # the host-side result decrypts to the product
         m0 = e2e_step()[0]
-        back = H.hc_ct_import(ctx, out_arrays[0], m0.level, m0.degree, m0.scale)
+        imp = H.hc_ct_import_eval if eval_form else H.hc_ct_import
+        back = imp(ctx, out_arrays[0], m0.level, m0.degree, m0.scale)
         e2e_err = float(np.max(np.abs(H.hc_decode(ctx, H.hc_decrypt(ctx, sk, back)) - za * zb)))
         assert e2e_err < 2.0 ** -15, "host-to-host result decrypts wrong (max error %g)" % e2e_err
+    # the other host form, briefly, on the same pinned buffers refilled
+    other_form = None
+    if args.e2e_steps > 0:
+        other = H.hc_ct_export if eval_form else H.hc_ct_export_eval
+        for (pin, arr, _), c in zip(host_in, A + Bc):
+            arr[...] = other(ctx, c)[0]
+        for _ in range(2):
+            e2e_step(not eval_form)
+        o_ms = []
+        for _ in range(5):
+            t1 = time.perf_counter()
+            e2e_step(not eval_form)
+            o_ms.append(1000.0 * (time.perf_counter() - t1))
+        other_form = {"form": "coeff" if eval_form else "eval", "step_ms": [round(v, 2) for v in o_ms],
+                      "ops_per_s_at_median": Bn / statistics.median(o_ms) * 1000}
 
     sharded = cnn_sharded_leg(H, W, np, torch, local, rank, world) if world > 1 and not args.no_cnn else None
     if rank != 0:
@@ -1282,14 +1332,15 @@ def run_gpu(args, rank, world, local):
         "config": bench_config(Bn, world),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": roofline, "cpu_baseline": None, "gpu_launches": launches, "clocks": clk,
-        "e2e_detail": {"pinned_copy_gbs": copy_gbs, "step_ms": e2e_step_ms,
+        "e2e_detail": {"form": args.e2e_form, "pinned_copy_gbs": copy_gbs, "step_ms": e2e_step_ms,
                        "step_ms_median": statistics.median(e2e_step_ms) if e2e_step_ms else None,
                        "step_ms_min_max": [min(e2e_step_ms), max(e2e_step_ms)] if e2e_step_ms else None,
                        "ops_per_s_at_median": Bn / statistics.median(e2e_step_ms) * 1000 if e2e_step_ms else None,
                        "chunk_timeline_ms": e2e_timeline,
                        "per_call_device_ms": e2e_calls,
                        "per_call_fields": "copies in span, sum of chunk kernel spans, device span (events)",
-                       "chunk_timeline_fields": "per chunk: copy-in start, end, kernels start, end, copy-out start, end"},
+                       "chunk_timeline_fields": "per chunk: copy-in start, end, kernels start, end, copy-out start, end",
+                       "other_form": other_form, "slowest_call_timeline_ms": slowest_tl},
         "kernels": kern_summary, "tuning": tuning,
         "forms": {"graph": graph_value, "eager": eager_value, "unit": UNIT,
                   "graph_bit_identical_to_eager": graph_same,

@@ -25,7 +25,8 @@
  *   stream-ordered pool on the context stream).
  * - Ciphertexts live on the device in evaluation (NTT) form.  Import and
  *   export use COEFFICIENT form: layout [poly][limb][coeff] of uint64
- *   residues in [0, q_limb), limb i over prime q_i.
+ *   residues in [0, q_limb), limb i over prime q_i; the *_eval calls move
+ *   the evaluation-form words in the same layout.
  * - A context is not thread-safe: one host thread at a time.
  */
 #ifndef HECNN_H
@@ -221,6 +222,14 @@ int hc_ct_import_batch(hc_ctx *ctx, const uint64_t *const *host, const hc_ct_met
 /* Batched export: one inverse NTT launch for all, asynchronous copies into
  * host[i] (capacity cap[i] words), one synchronisation. */
 int hc_ct_export_batch(hc_ctx *ctx, const hc_ct *const *cts, int n, uint64_t *const *host, const size_t *cap);
+/* Evaluation-form export and import: the device words as they are (each
+ * limb the negacyclic NTT of the residue polynomial, slot k holding the
+ * value at psi^(2 brv(k) + 1)), the same [degree+1][level+1][N] layout, no
+ * transform.  The form in which a client that computes in evaluation form
+ * hands ciphertexts over; import range-checks (residue >= q: HC_ERR_INVALID).
+ * Export synchronises. */
+int hc_ct_export_eval(hc_ctx *ctx, const hc_ct *ct, uint64_t *out, size_t cap_words, hc_ct_meta *meta);
+int hc_ct_import_eval(hc_ctx *ctx, const uint64_t *host, const hc_ct_meta *meta, hc_ct **out);
 int hc_ct_meta_of(const hc_ct *ct, hc_ct_meta *meta);
 void hc_ct_destroy(hc_ct *);
 
@@ -291,6 +300,15 @@ int hc_mul_relin_rescale_host(hc_ctx *ctx, const hc_evk *evk, const uint64_t *co
                               const hc_ct_meta *a_meta, const uint64_t *const *b_host,
                               const hc_ct_meta *b_meta, int n, int chunk, uint64_t *const *out_host,
                               const size_t *out_cap, hc_ct_meta *out_meta);
+/* The same host-to-host call with the ciphertexts in evaluation form (the
+ * hc_ct_export_eval layout) in and out: no forward transform of the inputs
+ * and the device batch's own relinearise + rescale tail, so each output
+ * equals hc_mul_relin_rescale_batch's followed by hc_ct_export_eval.  Same
+ * arguments, chunking, range check and errors as hc_mul_relin_rescale_host. */
+int hc_mul_relin_rescale_host_eval(hc_ctx *ctx, const hc_evk *evk, const uint64_t *const *a_host,
+                                   const hc_ct_meta *a_meta, const uint64_t *const *b_host,
+                                   const hc_ct_meta *b_meta, int n, int chunk, uint64_t *const *out_host,
+                                   const size_t *out_cap, hc_ct_meta *out_meta);
 
 /*
  * Relinearisation that allocates no device memory.  The paper has no

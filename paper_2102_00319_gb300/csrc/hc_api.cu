@@ -1312,6 +1312,44 @@ extern "C" int hc_ct_import(hc_ctx* ctx, const uint64_t* host, const hc_ct_meta*
   });
 }
 
+extern "C" int hc_ct_export_eval(hc_ctx* ctx, const hc_ct* ct, uint64_t* out, size_t cap, hc_ct_meta* meta) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    check_ct(ctx, ct);
+    const int np = ct->degree + 1, nl = ct->level + 1;
+    const size_t limbs = (size_t)nl * ctx->P.n;
+    HC_CHECK(out && cap >= np * limbs, HC_ERR_INVALID, "output buffer too small");
+    for (int k = 0; k < np; ++k)  // each polynomial's limbs are contiguous on the device
+      HC_CUDA(cudaMemcpyAsync(out + k * limbs, ct->data + k * ct->stride, limbs * sizeof(u64), cudaMemcpyDeviceToHost,
+                              ctx->stream));
+    HC_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (meta) *meta = hc_ct_meta{ct->level, ct->degree, ct->scale};
+  });
+}
+
+extern "C" int hc_ct_import_eval(hc_ctx* ctx, const uint64_t* host, const hc_ct_meta* meta, hc_ct** out) {
+  if (!ctx) return HC_ERR_INVALID;
+  return guard(ctx, [&] {
+    HC_CHECK(host && meta && out, HC_ERR_INVALID, "null argument");
+    HC_CHECK(meta->level >= 0 && meta->level <= ctx->P.L && (meta->degree == 1 || meta->degree == 2),
+             HC_ERR_INVALID, "bad metadata");
+    hc_ct* c = new_ct(ctx, meta->level, meta->degree, meta->scale);
+    std::unique_ptr<hc_ct> hold(c);
+    const size_t words = (size_t)(meta->degree + 1) * (meta->level + 1) * ctx->P.n;
+    HC_CUDA(cudaMemcpyAsync(c->data, host, words * sizeof(u64), cudaMemcpyHostToDevice, ctx->stream));
+    std::vector<BufPtr> keep;
+    BufPtr flag = ctx->buffer(1);
+    keep.push_back(flag);
+    HC_CUDA(cudaMemsetAsync(flag->ptr, 0, sizeof(u64), ctx->stream));
+    launch_check_range(ctx, c->data, meta->degree + 1, meta->level + 1, c->stride, (unsigned long long*)flag->ptr);
+    u64 bad = 0;
+    HC_CUDA(cudaMemcpyAsync(&bad, flag->ptr, sizeof(u64), cudaMemcpyDeviceToHost, ctx->stream));
+    HC_CUDA(cudaStreamSynchronize(ctx->stream));
+    HC_CHECK(bad == 0, HC_ERR_INVALID, "imported residue not below its prime");
+    *out = hold.release();
+  });
+}
+
 extern "C" int hc_ct_import_batch(hc_ctx* ctx, const uint64_t* const* host, const hc_ct_meta* metas, int n,
                                   hc_ct** out) {
   if (!ctx) return HC_ERR_INVALID;
@@ -1968,10 +2006,12 @@ std::vector<int> host_chunks(int n, int chunk) {
 // stream never waits on the compute stream), every chunk's inputs are queued
 // on the copy-in stream at once, and chunk c's compute waits only for its own
 // copies; its outputs go back on the copy-out stream while chunk c + 1 runs.
-extern "C" int hc_mul_relin_rescale_host(hc_ctx* ctx, const hc_evk* evk, const uint64_t* const* a_host,
-                                         const hc_ct_meta* a_meta, const uint64_t* const* b_host,
-                                         const hc_ct_meta* b_meta, int n, int chunk, uint64_t* const* out_host,
-                                         const size_t* out_cap, hc_ct_meta* out_meta) {
+// eval: host buffers in evaluation (NTT) form, so the chunks' inputs need no
+// forward transforms and the products keep the device batch's forward tail.
+namespace {
+int host_pipeline(hc_ctx* ctx, const hc_evk* evk, const uint64_t* const* a_host, const hc_ct_meta* a_meta,
+                  const uint64_t* const* b_host, const hc_ct_meta* b_meta, int n, int chunk,
+                  uint64_t* const* out_host, const size_t* out_cap, hc_ct_meta* out_meta, bool eval) {
   if (!ctx) return HC_ERR_INVALID;
   cudaStream_t h2d = nullptr, d2h = nullptr;
   std::vector<cudaEvent_t> evs;
@@ -2064,16 +2104,29 @@ extern "C" int hc_mul_relin_rescale_host(hc_ctx* ctx, const hc_evk* evk, const u
       HC_CUDA(cudaStreamWaitEvent(ctx->stream, copied[c], 0));
       if (tl) tev[6 * c + 2] = tmark(ctx->stream);
       launch_check_range(ctx, x[0]->data, 4 * m, level + 1, stride, (unsigned long long*)(flags->ptr + c));
-      launch_ntt(ctx, limbset_base(x[0]->data, 2 * stride, stride, 2, level + 1, 0, nullptr), 2 * m, false);
+      if (!eval) launch_ntt(ctx, limbset_base(x[0]->data, 2 * stride, stride, 2, level + 1, 0, nullptr), 2 * m, false);
       for (int j = 0; j < m; ++j) {
         x[j]->scale = a_meta[first[c] + j].scale;
         x[m + j]->scale = b_meta[first[c] + j].scale;
       }
-      // the products come out in coefficient form straight into the staging slab
-      BufPtr staged = ctx->buffer(m * out_words);
-      keep.push_back(staged);
-      const LimbSet co = limbset_base(staged->ptr, out_words, (u64)level * N, 2, level, 0, nullptr);
-      mul_relin_rescale_cts(ctx, evk, x.data(), x.data() + m, m, &co);
+      std::vector<const u64*> src(m);  // each product's [2][level][N] words on the device
+      if (eval) {
+        // the device batch's products, evaluation form; their slab lives until the copies out are done
+        std::vector<hc_ct*> r = mul_relin_rescale_cts(ctx, evk, x.data(), x.data() + m, m);
+        for (int j = 0; j < m; ++j) {
+          HC_CHECK(r[j]->stride == (size_t)level * N, HC_ERR_INVALID, "unexpected product layout");
+          keep.push_back(r[j]->buf);
+          src[j] = r[j]->data;
+        }
+        free_all(r);
+      } else {
+        // the products come out in coefficient form straight into the staging slab
+        BufPtr staged = ctx->buffer(m * out_words);
+        keep.push_back(staged);
+        const LimbSet co = limbset_base(staged->ptr, out_words, (u64)level * N, 2, level, 0, nullptr);
+        mul_relin_rescale_cts(ctx, evk, x.data(), x.data() + m, m, &co);
+        for (int j = 0; j < m; ++j) src[j] = staged->ptr + (size_t)j * out_words;
+      }
       free_all(x);  // stream-ordered: the copies into x finished before this stream's first use
       for (int j = 0; j < m; ++j) {
         const int i = first[c] + j;
@@ -2085,8 +2138,7 @@ extern "C" int hc_mul_relin_rescale_host(hc_ctx* ctx, const hc_evk* evk, const u
       HC_CUDA(cudaStreamWaitEvent(d2h, done, 0));
       if (tl) tev[6 * c + 4] = tmark(d2h);
       for (int j = 0; j < m; ++j)
-        HC_CUDA(cudaMemcpyAsync(out_host[first[c] + j], staged->ptr + (size_t)j * out_words, out_words * sizeof(u64),
-                                cudaMemcpyDeviceToHost, d2h));
+        HC_CUDA(cudaMemcpyAsync(out_host[first[c] + j], src[j], out_words * sizeof(u64), cudaMemcpyDeviceToHost, d2h));
       if (tl) tev[6 * c + 5] = tmark(d2h);
     }
     // (the context stream is restored at the end of every chunk)
@@ -2116,6 +2168,21 @@ extern "C" int hc_mul_relin_rescale_host(hc_ctx* ctx, const hc_evk* evk, const u
   for (auto& v : ins) free_all(v);
   for (cudaEvent_t e : evs) cudaEventDestroy(e);
   return rc;
+}
+}  // namespace
+
+extern "C" int hc_mul_relin_rescale_host(hc_ctx* ctx, const hc_evk* evk, const uint64_t* const* a_host,
+                                         const hc_ct_meta* a_meta, const uint64_t* const* b_host,
+                                         const hc_ct_meta* b_meta, int n, int chunk, uint64_t* const* out_host,
+                                         const size_t* out_cap, hc_ct_meta* out_meta) {
+  return host_pipeline(ctx, evk, a_host, a_meta, b_host, b_meta, n, chunk, out_host, out_cap, out_meta, false);
+}
+
+extern "C" int hc_mul_relin_rescale_host_eval(hc_ctx* ctx, const hc_evk* evk, const uint64_t* const* a_host,
+                                              const hc_ct_meta* a_meta, const uint64_t* const* b_host,
+                                              const hc_ct_meta* b_meta, int n, int chunk, uint64_t* const* out_host,
+                                              const size_t* out_cap, hc_ct_meta* out_meta) {
+  return host_pipeline(ctx, evk, a_host, a_meta, b_host, b_meta, n, chunk, out_host, out_cap, out_meta, true);
 }
 
 // =====================================================================

@@ -45,7 +45,8 @@ EXPORTS = [
     "hc_mul_relin_rescale_batch", "hc_enc_conv2d", "hc_enc_poly_act", "hc_enc_pool", "hc_enc_fc",
     "hc_relin_noalloc", "hc_graph_begin", "hc_graph_end", "hc_graph_launch", "hc_graph_destroy",
     "hc_enc_conv2d_single_batch", "hc_enc_conv2d_single_hoisted_batch", "hc_enc_fc_rotsum", "hc_ct_import_batch", "hc_ct_export_batch",
-    "hc_mul_relin_rescale_host", "hc_autotune", "hc_tune_set", "hc_tune_get", "hc_int_mul_rates",
+    "hc_mul_relin_rescale_host", "hc_mul_relin_rescale_host_eval", "hc_ct_export_eval", "hc_ct_import_eval",
+    "hc_autotune", "hc_tune_set", "hc_tune_get", "hc_int_mul_rates",
     "hc_enc_fc_partial", "hc_relin_rescale_batch", "hc_profile_host_timeline",
 ]
 
@@ -126,6 +127,11 @@ def load(path: str = LIB_PATH):
         "hc_tune_get": (c_int, [vp, c_int]),
         "hc_mul_relin_rescale_host": (c_int, [vp, vp, pp, ctypes.POINTER(CtMeta), pp, ctypes.POINTER(CtMeta), c_int,
                                               c_int, pp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(CtMeta)]),
+        "hc_mul_relin_rescale_host_eval": (c_int, [vp, vp, pp, ctypes.POINTER(CtMeta), pp, ctypes.POINTER(CtMeta),
+                                                   c_int, c_int, pp, ctypes.POINTER(ctypes.c_size_t),
+                                                   ctypes.POINTER(CtMeta)]),
+        "hc_ct_export_eval": (c_int, [vp, vp, ctypes.POINTER(u64), ctypes.c_size_t, ctypes.POINTER(CtMeta)]),
+        "hc_ct_import_eval": (c_int, [vp, ctypes.POINTER(u64), ctypes.POINTER(CtMeta), pp]),
         "hc_ct_destroy": (None, [vp]),
         "hc_add": (c_int, [vp, vp, vp, pp]), "hc_sub": (c_int, [vp, vp, vp, pp]),
         "hc_add_const": (c_int, [vp, vp, dbl, pp]),
@@ -460,6 +466,23 @@ def hc_ct_import(ctx, data, level, degree, scale) -> Ciphertext:
     return Ciphertext(out.value, ctx)
 
 
+def hc_ct_export_eval(ctx, ct) -> tuple:
+    """The device words in evaluation (NTT) form, [degree+1][level+1][N]."""
+    m = ct.meta()
+    out = np.zeros((m.degree + 1, m.level + 1, ctx.n), dtype=np.uint64)
+    meta = CtMeta()
+    _check(ctx, load().hc_ct_export_eval(ctx.ptr, ct.ptr, _u64p(out), out.size, ctypes.byref(meta)))
+    return out, meta
+
+
+def hc_ct_import_eval(ctx, data, level, degree, scale) -> Ciphertext:
+    d = np.ascontiguousarray(data, dtype=np.uint64)
+    meta = CtMeta(level, degree, float(scale))
+    out = _out()
+    _check(ctx, load().hc_ct_import_eval(ctx.ptr, _u64p(d), ctypes.byref(meta), ctypes.byref(out)))
+    return Ciphertext(out.value, ctx)
+
+
 def hc_ct_import_batch(ctx, arrays, metas):
     """arrays: C-contiguous uint64 arrays [degree+1][level+1][N] (pinned for
     asynchronous copies); metas: (level, degree, scale) per ciphertext."""
@@ -486,10 +509,11 @@ def hc_ct_export_batch(ctx, cts, arrays):
     _check(ctx, load().hc_ct_export_batch(ctx.ptr, _ptr_array(cts), n, ptrs, caps))
 
 
-def hc_mul_relin_rescale_host(ctx, evk, a_arrays, a_metas, b_arrays, b_metas, out_arrays, chunk=0):
+def hc_mul_relin_rescale_host(ctx, evk, a_arrays, a_metas, b_arrays, b_metas, out_arrays, chunk=0, eval_form=False):
     """Host-to-host batch: a_arrays/b_arrays are C-contiguous uint64
-    [2][level+1][N] coefficient-form ciphertexts with (level, degree, scale)
-    metas; out_arrays receive [2][level][N].  Returns the output metas."""
+    [2][level+1][N] ciphertexts (coefficient form, or evaluation form with
+    eval_form) with (level, degree, scale) metas; out_arrays receive
+    [2][level][N] in the same form.  Returns the output metas."""
     n = len(a_arrays)
     if not (len(b_arrays) == len(a_metas) == len(b_metas) == len(out_arrays) == n):
         raise ValueError("one entry per pair in every list")
@@ -507,8 +531,9 @@ def hc_mul_relin_rescale_host(ctx, evk, a_arrays, a_metas, b_arrays, b_metas, ou
 
     caps = (ctypes.c_size_t * max(1, n))(*[o.size for o in out_arrays])
     out_m = (CtMeta * max(1, n))()
-    _check(ctx, load().hc_mul_relin_rescale_host(ctx.ptr, evk.ptr, ptrs(a_arrays), metas(a_metas), ptrs(b_arrays),
-                                                 metas(b_metas), n, int(chunk), ptrs(out_arrays), caps, out_m))
+    fn = load().hc_mul_relin_rescale_host_eval if eval_form else load().hc_mul_relin_rescale_host
+    _check(ctx, fn(ctx.ptr, evk.ptr, ptrs(a_arrays), metas(a_metas), ptrs(b_arrays), metas(b_metas), n, int(chunk),
+                   ptrs(out_arrays), caps, out_m))
     return [out_m[i] for i in range(n)]
 
 

@@ -63,6 +63,15 @@ def test_deep_n16_batch_sampled_bit_exact():
     H.hc_mul_relin_rescale_host(p.ctx, p.g_evk, a_arr, metas, b_arr, metas, host)
     for i in range(B):
         np.testing.assert_array_equal(host[i], eager[i])
+    # the evaluation-form host call: the device batch's words, exported in that form
+    ea = [H.hc_ct_export_eval(p.ctx, c)[0] for c in A]
+    eb = [H.hc_ct_export_eval(p.ctx, c)[0] for c in Bc]
+    host_e = [np.zeros((2, p.op.L, p.op.N), dtype=np.uint64) for _ in range(B)]
+    H.hc_mul_relin_rescale_host(p.ctx, p.g_evk, ea, metas, eb, metas, host_e, eval_form=True)
+    for i in ks:
+        ct = H.hc_ct_import_eval(p.ctx, host_e[i], p.op.L - 1, 1, 1.0)
+        np.testing.assert_array_equal(H.hc_ct_export(p.ctx, ct)[0], eager[i])
+    del ea, eb, host_e
     # the other NTT tile shapes at N = 2^16 (autotuning choices) give the same words
     default = H.hc_tune_get(p.ctx, H.HC_TUNE_NTT)
     for v in (0, 1, 2, 3, 4, 5):

@@ -123,6 +123,44 @@ def test_host_pipeline_matches_device_batch(pair):
         H.hc_mul_relin_rescale_host(pair.ctx, pair.g_evk, a_arr, a_m, b_arr, b_m, outs, chunk=-1)
 
 
+def test_evaluation_form_host_call_and_export(pair):
+    """Evaluation-form export/import round-trips the device words; the
+    evaluation-form host-to-host call equals the device batch exported in
+    that form, and its outputs, imported back and exported in coefficient
+    form, equal the coefficient-form host call's words (which the oracle
+    pins elsewhere), for chunk sizes 2, automatic and a ragged 5; an
+    out-of-range residue is rejected by the import and by the call."""
+    op = pair.op
+    lv, n = 3, 12
+    ga = [pair.encrypt_values(W.slot_values(160 + i, op.K), level=lv, nonce=1600 + i)[0] for i in range(n)]
+    gb = [pair.encrypt_values(W.slot_values(170 + i, op.K), level=lv, nonce=1700 + i)[0] for i in range(n)]
+    ea = [H.hc_ct_export_eval(pair.ctx, c)[0] for c in ga]
+    eb = [H.hc_ct_export_eval(pair.ctx, c)[0] for c in gb]
+    back = H.hc_ct_import_eval(pair.ctx, ea[0], lv, 1, ga[0].meta().scale)
+    np.testing.assert_array_equal(H.hc_ct_export(pair.ctx, back)[0], H.hc_ct_export(pair.ctx, ga[0])[0])
+    np.testing.assert_array_equal(H.hc_ct_export_eval(pair.ctx, back)[0], ea[0])
+    want = [H.hc_ct_export_eval(pair.ctx, c)[0] for c in H.hc_mul_relin_rescale_batch(pair.ctx, pair.g_evk, ga, gb)]
+    coeff, _ = _host_products(pair, ga, gb, lv)
+    a_m = [(lv, 1, c.meta().scale) for c in ga]
+    b_m = [(lv, 1, c.meta().scale) for c in gb]
+    for chunk in (2, 0, 5):
+        outs = [np.zeros((2, lv, op.N), dtype=np.uint64) for _ in range(n)]
+        metas = H.hc_mul_relin_rescale_host(pair.ctx, pair.g_evk, ea, a_m, eb, b_m, outs, chunk=chunk, eval_form=True)
+        for o, w, c, m in zip(outs, want, coeff, metas):
+            np.testing.assert_array_equal(o, w)
+            assert (m.level, m.degree) == (lv - 1, 1)
+            ct = H.hc_ct_import_eval(pair.ctx, o, m.level, m.degree, m.scale)
+            np.testing.assert_array_equal(H.hc_ct_export(pair.ctx, ct)[0], c)
+    bad = ea[4].copy()
+    bad[1, 2, 7] = np.uint64(op.q[2])
+    with pytest.raises(H.HcError):
+        H.hc_ct_import_eval(pair.ctx, bad, lv, 1, 1.0)
+    outs = [np.zeros((2, lv, op.N), dtype=np.uint64) for _ in range(n)]
+    with pytest.raises(H.HcError):
+        H.hc_mul_relin_rescale_host(pair.ctx, pair.g_evk, ea[:4] + [bad] + ea[5:], a_m, eb, b_m, outs, chunk=2,
+                                    eval_form=True)
+
+
 def _host_products(p, ga, gb, lv):
     """The host-to-host call on exported inputs: coefficient-form outputs."""
     a_arr = [H.hc_ct_export(p.ctx, c)[0] for c in ga]

@@ -85,4 +85,10 @@ def test_served_results_equal_alone_and_decrypt(per_degree_streams, hoisted):
         filt = W.conv_weights(60 + r.log_n, 1, 3, 3)[0, :, :, 0]
         ref = cnn.conv2d(imgs[i][None, :, :, None], filt[None, :, :, None])[0, :, :, 0] ** 2
         valid = np.array([v[p * 8 + q] for p in range(6) for q in range(6)])
-        assert np.max(np.abs(valid - ref.reshape(-1))) < 2.0 ** -8, i
+        # scale 2^30 with 30-bit primes and one special prime: about 2^-10
+        # per slot with plain rotations; hoisted rotations carry the key
+        # switch's structured noise (the uncentred digit lift of the fast
+        # basis conversion) into output slot 0, 3-5e-3 in the oracle's own
+        # hoisted convolution of these requests, so 2^-7 there
+        tol = 2.0 ** -7 if hoisted else 2.0 ** -8
+        assert np.max(np.abs(valid - ref.reshape(-1))) < tol, i
