@@ -226,21 +226,40 @@ const int* ident_map(hc_ctx* ctx) { return ctx->ext_map + (ctx->P.L + 1) * (ctx-
 // of xc (coefficient form) to the other slots of Q_l u P, in NTT form.  A
 // digit's own slots are taken from x by the specialised key product; with
 // more than eight digits they are copied into ext instead.
+// ModUp of m items: xs[i] their c1 (NTT form), xc the same in coefficient
+// form.  Digits with alpha primes run together: one conversion launch and
+// one transform launch over all their raised slots (a 2-D slot map, digit
+// by digit); a last, shorter digit gets launches of its own.  With copy_own
+// the digits' own slots are copied from xs into ext as well (one launch);
+// otherwise the key product reads them from xs.
 void modup_digits(hc_ctx* ctx, int level, const std::vector<CtRef>& xs, const u64* xc, u64 x_is, u64* ext, u64 ext_is,
-                  int m, std::vector<BufPtr>& keep) {
+                  int m, std::vector<BufPtr>& keep, bool copy_own) {
   const int n = ctx->P.n, alpha = ctx->P.alpha, nq = level + 1, next = nq + alpha, dnum = ctx->lv[level].dnum;
   const size_t ext_words = (size_t)next * n;
   const int* emap = ctx->ext_map_of(level);
-  for (int j = 0; j < dnum; ++j) {
-    const int d0 = j * alpha, d1 = std::min(d0 + alpha, nq);
-    if (dnum > 8) {
-      std::vector<CtRef> er(m), xsh(m);
-      for (int i = 0; i < m; ++i) {
-        er[i] = CtRef{ext + ext_is * i + (size_t)j * ext_words + (size_t)d0 * n, 0};
-        xsh[i] = CtRef{xs[i].p + (size_t)d0 * n, 0};
-      }
-      launch_ew(ctx, 3, refs_dev(ctx, er, keep), refs_dev(ctx, xsh, keep), nullptr, m, 1, d1 - d0);
+  const int full = nq / alpha;  // digits with alpha primes (the first ones)
+  if (copy_own) {
+    for (int j0 = 0; j0 < dnum; j0 = std::max(j0 + 1, full)) {
+      // the full digits in one launch, then the shorter last one
+      const int j1 = j0 < full ? full : dnum, ns = std::min(alpha, nq - j0 * alpha);
+      std::vector<CtRef> er, xsh;
+      for (int i = 0; i < m; ++i)
+        for (int j = j0; j < j1; ++j) {
+          er.push_back(CtRef{ext + ext_is * i + (size_t)j * ext_words + (size_t)j * alpha * n, 0});
+          xsh.push_back(CtRef{xs[i].p + (size_t)j * alpha * n, 0});
+        }
+      launch_ew(ctx, 3, refs_dev(ctx, er, keep), refs_dev(ctx, xsh, keep), nullptr, (int)er.size(), 1, ns);
     }
+  }
+  if (full > 0 && alpha <= 8) {
+    launch_modup_bconv_fast(ctx, level, 0, xc, x_is, ext, ext_is, m, full);
+    LimbSet e = limbset_base(ext, ext_is, ext_words, full, next - alpha, 0, emap);
+    e.slot_map = ctx->modup_slots_of(level, 0);  // digit-major: each full digit's next - alpha raised slots
+    e.slot_map_2d = 1;
+    launch_ntt(ctx, e, m, false);
+  }
+  for (int j = (alpha <= 8 ? full : 0); j < dnum; ++j) {
+    const int d0 = j * alpha, d1 = std::min(d0 + alpha, nq);
     launch_modup_bconv_fast(ctx, level, j, xc, x_is, ext + (size_t)j * ext_words, ext_is, m);
     LimbSet e = limbset_base(ext + (size_t)j * ext_words, ext_is, 0, 1, next - (d1 - d0), 0, emap);
     e.slot_map = ctx->modup_slots_of(level, j);  // the raised slots, one launch
@@ -300,7 +319,7 @@ void keyswitch_batch_keys(hc_ctx* ctx, const std::vector<const u64*>& keys, int 
     xin.npoly = 1;
     xin.nlimb = nq;
     launch_ntt_from(ctx, limbset_base(xc, x_is, 0, 1, nq, 0, nullptr), &xin, m, true, false);
-    modup_digits(ctx, level, xs, xc, x_is, ext, ext_is, m, keep);
+    modup_digits(ctx, level, xs, xc, x_is, ext, ext_is, m, keep, dnum > 8);
     // one key-product launch: a shared key, or a device table of per-item keys
     bool same_key = true;
     for (int r = 1; r < m; ++r) same_key = same_key && keys[s0 + r] == keys[s0];
@@ -372,7 +391,7 @@ void keyswitch_rescale_batch(hc_ctx* ctx, const u64* key, int level, const std::
     xin.nlimb = nq;
     const LimbSet xcs = limbset_base(xc, x_is, 0, 1, nq, 0, nullptr);
     launch_ntt_from(ctx, xcs, &xin, m, true, false);
-    modup_digits(ctx, level, xs, xc, x_is, ext, ext_is, m, keep);
+    modup_digits(ctx, level, xs, xc, x_is, ext, ext_is, m, keep, dnum > 8);
     // the digits' own slots are read from x itself (specialised key product)
     launch_key_product_batched(ctx, level, ext, ext_is, key, acc, acc_is, m, dnum <= 8 ? xr : nullptr);
     launch_ntt(ctx, limbset_base(acc, acc_is, ext_words, 2, alpha, nq, emap), m, true, false);
@@ -1652,21 +1671,9 @@ std::vector<std::vector<hc_ct*>> rotate_hoisted_batch(hc_ctx* ctx, const hc_evk*
     c1in.npoly = 1;
     c1in.nlimb = nq;
     launch_ntt_from(ctx, limbset_base(xc, x_is, 0, 1, nq, 0, nullptr), &c1in, m, true, false);
-    for (int j = 0; j < dnum; ++j) {
-      const int d0 = j * alpha, d1 = std::min(d0 + alpha, nq);
-      // the digit's own slots are c1 itself (the automorphism below moves them too)
-      std::vector<CtRef> own_dst(m), own_src(m);
-      for (int i = 0; i < m; ++i) {
-        own_dst[i] = CtRef{ext + ext_is * i + (size_t)j * ext_words + (size_t)d0 * n, 0};
-        own_src[i] = CtRef{c1s[i].p + (size_t)d0 * n, 0};
-      }
-      launch_ew(ctx, 3, refs_dev(ctx, own_dst, keep), refs_dev(ctx, own_src, keep), nullptr, m, 1, d1 - d0);
-      u64* ej = ext + (size_t)j * ext_words;
-      launch_modup_bconv_fast(ctx, level, j, xc, x_is, ej, ext_is, m);
-      LimbSet e = limbset_base(ej, ext_is, 0, 1, next - (d1 - d0), 0, emap);
-      e.slot_map = ctx->modup_slots_of(level, j);
-      launch_ntt(ctx, e, m, false);
-    }
+    // the digits' own slots are c1 itself, copied (the key product reads
+    // every slot through the automorphism)
+    modup_digits(ctx, level, c1s, xc, x_is, ext, ext_is, m, keep, true);
     for (size_t k = 0; k < gs.size(); ++k) {  // steps that do not rotate: a copy
       if (gs[k] != 1) continue;
       std::vector<CtRef> orr;

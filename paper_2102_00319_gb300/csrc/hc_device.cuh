@@ -77,6 +77,15 @@ struct KsrFuse {
 // z, poly k < npoly and limb slot l0 <= s < l0 + nlimb the limb lives at
 //   (refs ? refs[z].p + k*refs[z].stride : base + z*item_stride + k*poly_stride) + s*N
 // and is taken modulo chain prime prime_map ? prime_map[s] : s.
+// A ModUp conversion over a run of full digits in one launch: blockIdx.y /
+// split picks the digit, blockIdx.y % split the part of its output primes.
+struct DigitGrid {
+  int split;
+  int alpha;
+  u64 ext_digit_stride;  // words between two digits' raised limbs
+  u64 cst_digit_stride;  // words between two digits' constants
+};
+
 struct LimbSet {
   const CtRef* refs;
   u64* base;
@@ -87,6 +96,7 @@ struct LimbSet {
   int l0;
   const int* prime_map;
   const int* slot_map;  // optional: limb l lives at slot slot_map[l] instead of l0 + l
+  int slot_map_2d;      // with slot_map: poly k's limb l lives at slot_map[k * nlimb + l]
 };
 
 __device__ __forceinline__ u64* limb_ptr(const LimbSet& s, int z, int k, int slot, int n) {

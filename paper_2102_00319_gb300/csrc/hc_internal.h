@@ -293,7 +293,7 @@ void launch_sum4(hc_ctx* ctx, const CtRef* out, const CtRef* x, const int* idx, 
 
 // Specialised key-switching launchers (same results as the generic ones).
 void launch_modup_bconv_fast(hc_ctx* ctx, int level, int j, const u64* xcoef, u64 x_item_stride, u64* ext,
-                             u64 ext_item_stride, int items);
+                             u64 ext_item_stride, int items, int ndig = 1);  // digits j .. j + ndig - 1, all full
 void launch_moddown_bconv_fast(hc_ctx* ctx, int level, const u64* accp_coef, u64 accp_item_stride, u64* z,
                                u64 z_item_stride, int items);
 void launch_key_product_batched(hc_ctx* ctx, int level, const u64* ext, u64 ext_item_stride, const u64* key,

@@ -769,7 +769,12 @@ namespace {
 template <int NS>
 __global__ void __launch_bounds__(kT) k_modup_bconv_t(const u64* xcoef, u64 x_item_stride, u64* ext,
                                                        u64 ext_item_stride, const u64* cst, int d0, int next,
-                                                       const int* emap, Tables T) {
+                                                       const int* emap, DigitGrid dg, Tables T) {
+  // digit d0 / alpha + blockIdx.y / split of a run of full digits
+  const int dj = blockIdx.y / dg.split;
+  d0 += dj * dg.alpha;
+  cst += dj * dg.cst_digit_stride;
+  ext += dj * dg.ext_digit_stride;
   extern __shared__ u64 sh[];
   u64* hm = sh;                          // [next][NS]
   DMod* md = (DMod*)(sh + next * NS);    // [next]
@@ -841,7 +846,13 @@ __device__ __forceinline__ U128 acc30_value(const Acc30& a) {
 template <int NS>
 __global__ void __launch_bounds__(kT) k_modup_bconv_h(const u64* xcoef, u64 x_item_stride, u64* ext,
                                                        u64 ext_item_stride, const u64* cst, int d0, int next,
-                                                       const int* emap, Tables T) {
+                                                       const int* emap, DigitGrid dg, Tables T) {
+  // digit d0 / alpha + blockIdx.y / split of a run of full digits; part
+  // blockIdx.y % split of its output primes
+  const int dj = blockIdx.y / dg.split, part = blockIdx.y - dj * dg.split;
+  d0 += dj * dg.alpha;
+  cst += dj * dg.cst_digit_stride;
+  ext += dj * dg.ext_digit_stride;
   extern __shared__ u64 sh[];
   uint4* hm = reinterpret_cast<uint4*>(sh);  // [next][NS] halves, Montgomery form
   DMod* md = (DMod*)(sh + 2 * next * NS);    // [next]
@@ -861,9 +872,9 @@ __global__ void __launch_bounds__(kT) k_modup_bconv_h(const u64* xcoef, u64 x_it
   Half30 v[NS];
 #pragma unroll
   for (int i = 0; i < NS; ++i) v[i] = halves30(shoup(x[(size_t)(d0 + i) * n + c], cst[i], cst[NS + i], md[d0 + i].q));
-  // the output primes may be split over gridDim.y blocks (a tuning choice)
-  const int per = (next + gridDim.y - 1) / gridDim.y, t_end = min(next, ((int)blockIdx.y + 1) * per);
-  for (int t = blockIdx.y * per; t < t_end; ++t) {
+  // the output primes may be split over dg.split blocks (a tuning choice)
+  const int per = (next + dg.split - 1) / dg.split, t_end = min(next, (part + 1) * per);
+  for (int t = part * per; t < t_end; ++t) {
     if (t >= d0 && t < d0 + NS) continue;
     Acc30 acc{0, 0, 0};
 #pragma unroll
@@ -1033,26 +1044,34 @@ __global__ void k_ksr_cl(u64* tl, const u64* zq, u64 z_item_stride, int level, T
 }  // namespace
 
 void launch_modup_bconv_fast(hc_ctx* ctx, int level, int j, const u64* xcoef, u64 x_item_stride, u64* ext,
-                             u64 ext_item_stride, int items) {
+                             u64 ext_item_stride, int items, int ndig) {
   const int alpha = ctx->P.alpha;
   const int d0 = j * alpha;
   const int ns = std::min(alpha, level + 1 - d0);
   const int next = level + 1 + alpha;
+  HC_CHECK(ndig >= 1 && (ndig == 1 || (j + ndig) * alpha <= level + 1), HC_ERR_INVALID,
+           "a multi-digit conversion covers full digits only");
+  HC_CHECK(ndig == 1 || ns <= 8, HC_ERR_INVALID, "multi-digit conversions need a specialised kernel");
   const u64* cst = ctx->ks(ctx->lv[level].modup_off[j]);
   // (the halves form stages 16 bytes per constant, the other 8)
   const size_t smem = (size_t)next * ns * 2 * sizeof(u64) + (size_t)next * sizeof(DMod);
   const bool halves_split = ctx->P.below_2_60 && ns <= 8;
-  const dim3 g = grid_for(ctx, halves_split ? std::max(1, std::min(ctx->tune.modup_split, next)) : 1, items);
-  ProfScope prof_(ctx, "k_modup_bconv", (uint64_t)items * (next - ns));
+  DigitGrid dg;
+  dg.split = halves_split ? std::max(1, std::min(ctx->tune.modup_split, next)) : 1;
+  dg.alpha = alpha;
+  dg.ext_digit_stride = (u64)next * ctx->P.n;        // digit j's raised limbs follow digit j - 1's
+  dg.cst_digit_stride = (u64)(2 + next) * alpha;     // a full digit's constants: hat_inv, its Shoup, hat_mod
+  const dim3 g = grid_for(ctx, dg.split * ndig, items);
+  ProfScope prof_(ctx, "k_modup_bconv", (uint64_t)items * ndig * (next - ns));
   const bool halves = ctx->P.below_2_60;
 #define HC_MODUP(NS)                                                                                          \
   case NS:                                                                                                    \
     if (halves)                                                                                               \
       k_modup_bconv_h<NS><<<g, kT, smem, ctx->stream>>>(xcoef, x_item_stride, ext, ext_item_stride, cst, d0, \
-                                                         next, ctx->ext_map_of(level), ctx->tab);             \
+                                                         next, ctx->ext_map_of(level), dg, ctx->tab);         \
     else                                                                                                      \
       k_modup_bconv_t<NS><<<g, kT, smem, ctx->stream>>>(xcoef, x_item_stride, ext, ext_item_stride, cst, d0, \
-                                                         next, ctx->ext_map_of(level), ctx->tab);             \
+                                                         next, ctx->ext_map_of(level), dg, ctx->tab);         \
     break;
   switch (ns) {
     HC_MODUP(1) HC_MODUP(2) HC_MODUP(3) HC_MODUP(4) HC_MODUP(5) HC_MODUP(6) HC_MODUP(7) HC_MODUP(8)

@@ -90,7 +90,7 @@ __device__ __forceinline__ void limb_meta(const LimbSet& s, u64*& a, int& pid) {
   const int y = blockIdx.y;
   const int k = y / s.nlimb;
   const int l = y - k * s.nlimb;
-  const int slot = s.slot_map ? s.slot_map[l] : s.l0 + l;
+  const int slot = s.slot_map ? s.slot_map[s.slot_map_2d ? y : l] : s.l0 + l;
   a = limb_ptr(s, blockIdx.z, k, slot, 1 << LOGN);
   pid = limb_prime(s, slot);
 }
@@ -367,7 +367,7 @@ __device__ __forceinline__ PipeTile pipe_tile(const LimbSet& s, const LimbSet& i
   const int yz = t / tiles_x;
   const int y = yz % ylimbs, z = yz / ylimbs;
   const int k = y / s.nlimb, l = y - k * s.nlimb;
-  const int slot = s.slot_map ? s.slot_map[l] : s.l0 + l;
+  const int slot = s.slot_map ? s.slot_map[s.slot_map_2d ? y : l] : s.l0 + l;
   p.a = limb_ptr(s, z, k, slot, 1 << LOGN);
   p.pid = limb_prime(s, slot);
   p.ain = use_in ? limb_ptr(in, z, k, in.l0 + l, 1 << LOGN) : p.a;
