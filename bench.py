@@ -861,9 +861,9 @@ def serving_leg(args, H, W, np, torch, local):
     out = {"workload": "single-ct conv 3x3 + x^2 requests: 1/4 at N=2^12 (L=2), 3/4 uneven N=2^13..2^15 (3-12 levels)",
            "rotations": "hoisted", "budget_bytes": budget, "rates": {}}
     inst = W.uneven_instances(args.serve_requests)
-    # the paper-style rates, then two above the loop's capacity (saturation:
+    # the paper-style rates, then three towards and above the loop's capacity (saturation:
     # throughput plateaus, queueing grows, admission by footprint binds)
-    for k, rate in enumerate((20.0, 50.0, 100.0, 200.0, 1000.0, 4000.0)):
+    for k, rate in enumerate((20.0, 50.0, 100.0, 200.0, 1000.0, 4000.0, 16000.0)):
         reqs = []
         for i in range(args.serve_requests):
             log_n, lv = (12, 2) if i % 4 == 0 else inst[i]
