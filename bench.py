@@ -327,16 +327,17 @@ def run_reference(args, rank, world):
 # domain), per kernel; dnum = 3 at the top level of this workload.
 # DRAM bytes (read + write) per work unit from one ncu capture of the same
 # kernel version on a smaller batch (one step of 16 pairs run by
-# `python bench.py --profile-step 16`: 336 limbs per ModUp transform launch,
-# 640 per fused-tail launch), scaled to a launch by its units.  A kernel
+# `python bench.py --profile-step 16`: 1008 limbs per ModUp transform launch
+# (three digits of 21 raised limbs for 16 items), 640 per fused-tail launch),
+# scaled to a launch by its units.  A kernel
 # without an entry reports no traffic; an entry goes when its kernel
 # changes, until it is captured again.
 NCU_NTT_VARIANT = 1  # block size (HC_TUNE_NTT) of the NTT capture below
 NCU_TRAFFIC_PER_UNIT = {
-    "ntt_fwd_cols": (176.321e6 + 120.213e6) / 336,
-    "ntt_fwd_rows": (209.276e6 + 122.754e6) / 336,
-    "ntt_fwd_cols_ksr": (352.485e6 + 279.450e6) / 640,
-    "ntt_fwd_rows_ksr": (1114.837e6 + 316.936e6) / 640,
+    "ntt_fwd_cols": (528.662e6 + 472.601e6) / 1008,
+    "ntt_fwd_rows": (641.045e6 + 477.845e6) / 1008,
+    "ntt_fwd_cols_ksr": (352.459e6 + 276.417e6) / 640,
+    "ntt_fwd_rows_ksr": (1114.162e6 + 314.338e6) / 640,
 }
 
 
