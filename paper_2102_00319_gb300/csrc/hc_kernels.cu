@@ -948,7 +948,7 @@ __global__ void __launch_bounds__(kT) k_moddown_bconv_t(const u64* src, u64 src_
 // the 2 DNUM key words of (s, c) stay in registers across the batch.
 // digit_src (optional): the digit's own slots s in [j alpha, j alpha + alpha)
 // come from digit_src[z] (NTT-form input) instead of ext.
-template <int DNUM, bool HALVES>
+template <int DNUM, bool HALVES, bool GATHER>
 __global__ void __launch_bounds__(kT) k_key_product_t(const u64* ext, u64 ext_item_stride, const u64* key, u64* acc,
                                                        u64 acc_item_stride, int next, int nchain, const int* emap,
                                                        int items, const CtRef* digit_src, int alpha, int nq,
@@ -979,9 +979,15 @@ __global__ void __launch_bounds__(kT) k_key_product_t(const u64* ext, u64 ext_it
   const int own = (digit_src && s < nq) ? s / alpha : -1;  // the digit whose block holds slot s
   for (int z = blockIdx.z; z < items; z += gridDim.z) {
     if (item_keys) load_keys(item_keys[z]);
-    // item z reads the raised digits of item z mod ext_items, through kappa_g when gs is given
-    const int ce = gs ? automorph_src(c, gs[z], T.log_n) : c;
-    const u64* e = ext + (size_t)(z < ext_items ? z : z % ext_items) * ext_item_stride + (size_t)s * n + ce;
+    // GATHER: item z reads the raised digits of item z mod ext_items,
+    // through kappa_g when gs is given; otherwise its own, in place
+    const u64* e = ext + (size_t)s * n;
+    if constexpr (GATHER) {
+      const int ce = gs ? automorph_src(c, gs[z], T.log_n) : c;
+      e += (size_t)(z < ext_items ? z : z % ext_items) * ext_item_stride + ce;
+    } else {
+      e += (size_t)z * ext_item_stride + c;
+    }
     u64* o = acc + (size_t)z * acc_item_stride + (size_t)s * n + c;
     if constexpr (HALVES) {
       // every operand below 2^60: 30-bit halves, carry-free partial sums
@@ -1113,11 +1119,33 @@ void launch_moddown_bconv_fast(hc_ctx* ctx, int level, const u64* accp_coef, u64
   check_launch(ctx);
 }
 
+// The four forms of k_key_product_t<D>: 30-bit halves or 64-bit products,
+// with or without the gathered (shared, automorphed) digit reads.
+template <int D>
+void key_product_t_launch(bool halves, bool gather, dim3 g, cudaStream_t st, const u64* ext, u64 ext_is,
+                          const u64* key, u64* acc, u64 acc_is, int next, int nchain, const int* emap, int items,
+                          const CtRef* digit_src, int alpha, int nq, const u64* const* item_keys, const u64* gs,
+                          int ext_items, const Tables& T) {
+  if (halves && gather)
+    k_key_product_t<D, true, true><<<g, kT, 0, st>>>(ext, ext_is, key, acc, acc_is, next, nchain, emap, items,
+                                                     digit_src, alpha, nq, item_keys, gs, ext_items, T);
+  else if (halves)
+    k_key_product_t<D, true, false><<<g, kT, 0, st>>>(ext, ext_is, key, acc, acc_is, next, nchain, emap, items,
+                                                      digit_src, alpha, nq, item_keys, gs, ext_items, T);
+  else if (gather)
+    k_key_product_t<D, false, true><<<g, kT, 0, st>>>(ext, ext_is, key, acc, acc_is, next, nchain, emap, items,
+                                                      digit_src, alpha, nq, item_keys, gs, ext_items, T);
+  else
+    k_key_product_t<D, false, false><<<g, kT, 0, st>>>(ext, ext_is, key, acc, acc_is, next, nchain, emap, items,
+                                                       digit_src, alpha, nq, item_keys, gs, ext_items, T);
+}
+
 void launch_key_product_batched(hc_ctx* ctx, int level, const u64* ext, u64 ext_item_stride, const u64* key,
                                 u64* acc, u64 acc_item_stride, int items, const CtRef* digit_src,
                                 const u64* const* item_keys, const u64* gs, int ext_items) {
   if (ext_items <= 0) ext_items = items;
   HC_CHECK(!(gs && digit_src), HC_ERR_INVALID, "digit sources are not read through an automorphism");
+  const bool gather = gs || ext_items != items;
   const int next = level + 1 + ctx->P.alpha, dnum = ctx->lv[level].dnum;
   // a few item groups in z so small batches still fill the GPU
   const int zgroups =
@@ -1127,16 +1155,9 @@ void launch_key_product_batched(hc_ctx* ctx, int level, const u64* ext, u64 ext_
   const bool halves = ctx->P.below_2_60;
 #define HC_KP(D)                                                                                                \
   case D:                                                                                                       \
-    if (halves)                                                                                                 \
-      k_key_product_t<D, true><<<g, kT, 0, ctx->stream>>>(ext, ext_item_stride, key, acc, acc_item_stride,    \
-                                                          next, ctx->P.nchain(), ctx->ext_map_of(level), items, \
-                                                          digit_src, ctx->P.alpha, level + 1, item_keys, gs,   \
-                                                          ext_items, ctx->tab);                                \
-    else                                                                                                        \
-      k_key_product_t<D, false><<<g, kT, 0, ctx->stream>>>(ext, ext_item_stride, key, acc, acc_item_stride,   \
-                                                           next, ctx->P.nchain(), ctx->ext_map_of(level),      \
-                                                           items, digit_src, ctx->P.alpha, level + 1, item_keys, \
-                                                           gs, ext_items, ctx->tab);                             \
+    key_product_t_launch<D>(halves, gather, g, ctx->stream, ext, ext_item_stride, key, acc, acc_item_stride,    \
+                            next, ctx->P.nchain(), ctx->ext_map_of(level), items, digit_src, ctx->P.alpha,      \
+                            level + 1, item_keys, gs, ext_items, ctx->tab);                                     \
     break;
   switch (dnum) {
     HC_KP(1) HC_KP(2) HC_KP(3) HC_KP(4) HC_KP(5) HC_KP(6) HC_KP(7) HC_KP(8)
