@@ -286,8 +286,8 @@ int hc_mul_relin_rescale_batch(hc_ctx *ctx, const hc_evk *evk, const hc_ct *cons
  * (a_meta/b_meta give level, degree and scale); out_host[k] (capacity
  * out_cap[k] words >= 2 level N) receives the product, rescaled, in the same
  * layout, and out_meta[k] its metadata.  The batch runs as a pipeline of
- * chunks of `chunk` pairs (0: about a sixteenth of n from 32 pairs up, an
- * eighth below): copies in, the batched operation and copies out of
+ * chunks of `chunk` pairs (0: about a sixteenth of n from 32 pairs up,
+ * the last of them split into halves, 4 -> 2, 1, 1; an eighth below): copies in, the batched operation and copies out of
  * successive chunks overlap on separate CUDA streams, the chunks' kernels
  * round-robin over HC_TUNE_HOST_STREAMS streams; chunk < 0 gives HC_ERR_INVALID.  The relinearise + rescale tail
  * is formed in coefficient form (one inverse transform per output limb, no
