@@ -921,8 +921,35 @@ def deep_leg(H, W, np, torch, local):
     got = np.array([H.hc_decode(ctx, H.hc_decrypt(ctx, sk, c))[0].real for c in out])
     err = float(np.max(np.abs(got - plain_deep_network(np, img, cw, act, fw))))
     assert err < 2.0 ** -15, err
+
+    # throughput: B images at once (one hoisted batched conv, one activation
+    # call and one pool call over all B x C channels, the FC per image);
+    # image 0 is the image above, so its logits equal the single-image ones
+    B = 8
+    xs = [x] + [H.hc_encrypt(ctx, pk, H.hc_encode(ctx, np.pad(W.images(70 + b, 1, 28, 28)[0].reshape(-1),
+                                                              (0, K - 784)), scale, ctx.L), 3, 5000 + b)
+                for b in range(1, B)]
+
+    def infer_batch():
+        y = H.hc_enc_conv2d_single_hoisted_batch(ctx, evk, xs, 28, wc, C, 3, 3)
+        a = H.hc_enc_poly_act(ctx, evk, y, act)
+        pl = H.hc_enc_pool(ctx, evk, H.HC_PACK_SINGLE, a, B * C, 26, 28)
+        return [H.hc_enc_fc_rotsum(ctx, evk, pl[b * C:(b + 1) * C], vc, n_out, 10) for b in range(B)]
+
+    outb = infer_batch()
+    H.hc_sync(ctx)
+    t0 = time.perf_counter()
+    for _ in range(2):
+        outb = infer_batch()
+    H.hc_sync(ctx)
+    tb = (time.perf_counter() - t0) / 2
+    same = all(np.array_equal(H.hc_ct_export(ctx, a)[0], H.hc_ct_export(ctx, b)[0]) for a, b in zip(outb[0], out))
+    assert same, "batched deep inference differs from the single-image one"
     return {"workload": "deep_n16_l20: 28x28 image per ciphertext, conv 3x3 x16 (hoisted), degree-7 ReLU, pool, fc 10",
-            "latency_ms": 1000 * t, "images_per_s": 1.0 / t, "max_logit_error_vs_fp64": err, "tuning": tuning}
+            "latency_ms": 1000 * t, "images_per_s": 1.0 / t, "max_logit_error_vs_fp64": err,
+            "batched": {"images": B, "ms_per_batch": 1000 * tb, "images_per_s": B / tb,
+                        "image0_bit_identical_to_single": same},
+            "tuning": tuning}
 
 
 def paper_shape_leg(H, W, np, torch, local):

@@ -92,3 +92,35 @@ def test_deep_n16_logits_and_sampled_channel():
     got = np.array([p.decrypt_gpu(t)[0].real for t in out])
     ref = cnn.deep_network(img, cw, act, fw)
     assert np.max(np.abs(got - ref)) < TOL
+
+
+def test_deep_small_batch_of_images_matches_one_by_one():
+    """Three images through the deep network at once (the hoisted batched
+    conv, one activation call and one pool call over every image's channels,
+    the FC per image) give each image's single-image words."""
+    from hc_pair import Pair
+    p = Pair(11, [60] + [40] * 8, [60, 60], 40, seed=43, rot_steps=W.deep_rot_steps(28, 10))
+    op = p.op
+    C, n_out, B = 2, 3, 3
+    _, cw, fw = setup_net(p, C, n_out, 80)
+    act = list(W.relu_cheb7())
+    xs = []
+    for b in range(B):
+        z = np.zeros(op.K)
+        z[:784] = W.images(90 + b, 1, 28, 28)[0].reshape(-1)
+        xs.append(p.encrypt_values(z, nonce=1 + b)[0])
+    wc = [p.encrypt_values(np.full(op.K, cw[co, a, b]), nonce=10 + co * 9 + a * 3 + b)[0]
+          for co in range(C) for a in range(3) for b in range(3)]
+    V = W.deep_fc_vectors(fw, C, 13, 13, 28, op.K)
+    vc = [p.encrypt_values(V[r, c], nonce=100 + r * C + c)[0] for r in range(n_out) for c in range(C)]
+    y = H.hc_enc_conv2d_single_hoisted_batch(p.ctx, p.g_evk, xs, 28, wc, C, 3, 3)
+    a = H.hc_enc_poly_act(p.ctx, p.g_evk, y, act)
+    pl = H.hc_enc_pool(p.ctx, p.g_evk, H.HC_PACK_SINGLE, a, B * C, 26, 28)
+    for b in range(B):
+        zb = H.hc_enc_fc_rotsum(p.ctx, p.g_evk, pl[b * C:(b + 1) * C], vc, n_out, 10)
+        y1 = H.hc_enc_conv2d(p.ctx, p.g_evk, H.HC_PACK_SINGLE_HOISTED, [xs[b]], 28, 28, 1, wc, C, 3, 3, 1)
+        a1 = H.hc_enc_poly_act(p.ctx, p.g_evk, y1, act)
+        p1 = H.hc_enc_pool(p.ctx, p.g_evk, H.HC_PACK_SINGLE, a1, C, 26, 28)
+        z1 = H.hc_enc_fc_rotsum(p.ctx, p.g_evk, p1, vc, n_out, 10)
+        for r in range(n_out):
+            np.testing.assert_array_equal(H.hc_ct_export(p.ctx, zb[r])[0], H.hc_ct_export(p.ctx, z1[r])[0])
