@@ -66,6 +66,11 @@ def test_summarize_launch_list(bench, tmp_path, capsys):
     out = capsys.readouterr().out
     assert "| (step) | 9 | 180.0 | 1.000 |" in out
     assert "| k_rows | 2 | 40.0 |" in out
+    # occurrence 0: every launch of the list (a capture of one profiled region)
+    bench.summarize_ncu(str(p), 0)
+    out = capsys.readouterr().out
+    assert "| (step) | 18 | 270.0 | 1.000 |" in out
+    assert "| k_rows | 4 | 60.0 |" in out
 
 
 def test_reference_arm_prints_the_contract_line():
