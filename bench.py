@@ -826,6 +826,9 @@ def uneven_leg(H, W, np, torch, local, profile_only=False):
         "ms_graph_launch": best, "form": best_form, "inferences_per_s_graph": len(inst) / (best / 1000),
         "speedup_graph_vs_per_op": forms[best_form]["ms_per_op_calls"] / best,
         "forms": forms, "bit_identical_all_forms": same, "tuning": tuning,
+        "roofline": None,
+        "roofline_note": "the level groups run as concurrent branches, so per-kernel event times overlap; "
+                         "kernel shares come from the serialised ncu launch list instead",
     }
 
 
@@ -921,6 +924,20 @@ def deep_leg(H, W, np, torch, local):
     got = np.array([H.hc_decode(ctx, H.hc_decrypt(ctx, sk, c))[0].real for c in out])
     err = float(np.max(np.abs(got - plain_deep_network(np, img, cw, act, fw))))
     assert err < 2.0 ** -15, err
+    # one more pass with per-kernel events (one stream, no concurrent
+    # branches at one level): the dominant kernel's roofline
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    H.hc_profile_enable(ctx, True)
+    infer()
+    H.hc_sync(ctx)
+    clk = clocks.stop()
+    kernels = {name: H.hc_profile_kernel(ctx, name) for name in H.hc_profile_names(ctx)}
+    H.hc_profile_enable(ctx, False)
+    pass_ms = sum(v[1] for v in kernels.values())
+    roofline = leg_roofline(kernels, ctx.n, ps_dnum(ps, len(ps.q_bits) - 1), clk, local, torch, pass_ms)
+    shares = {k: round(v[1] / pass_ms, 3) for k, v in sorted(kernels.items(), key=lambda kv: -kv[1][1])[:6]}
 
     # throughput: B images at once (one hoisted batched conv, one activation
     # call and one pool call over all B x C channels, the FC per image);
@@ -949,7 +966,7 @@ def deep_leg(H, W, np, torch, local):
             "latency_ms": 1000 * t, "images_per_s": 1.0 / t, "max_logit_error_vs_fp64": err,
             "batched": {"images": B, "ms_per_batch": 1000 * tb, "images_per_s": B / tb,
                         "image0_bit_identical_to_single": same},
-            "tuning": tuning}
+            "roofline": roofline, "kernel_shares": shares, "tuning": tuning}
 
 
 def paper_shape_leg(H, W, np, torch, local):
