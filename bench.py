@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tiles and launch shapes")
     ap.add_argument("--graph-arena-gib", type=int, default=0,
                     help="device arena of the captured step (0: 4 GiB + 0.2 GiB per pair)")
-    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--e2e-chunk", type=int, default=0, help="pairs per pipeline chunk of the host call (0: auto)")
     ap.add_argument("--e2e-form", choices=("eval", "coeff"), default="eval",
                     help="host buffers in evaluation (NTT) form or coefficient form; the other form is timed briefly "
