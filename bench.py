@@ -862,7 +862,7 @@ def serving_leg(args, H, W, np, torch, local):
         models[log_n] = serving.Model(ctx=ctx, evk=evk, weights=ws, n=ctx.n, n_special=len(ps.p_bits), hoisted=True)
         pks[log_n] = pk
     budget = args.serve_budget_mib << 20
-    out = {"workload": "single-ct conv 3x3 + x^2 requests: 1/4 at N=2^12 (L=2), 3/4 uneven N=2^13..2^15 (3-12 levels)",
+    out = {"workload": "single-ct conv 3x3 + x^2 requests: half at N=2^12 (L=2), half uneven N=2^13..2^15 (3-12 levels)",
            "rotations": "hoisted", "budget_bytes": budget, "rates": {}}
     inst = W.uneven_instances(args.serve_requests)
     # the paper-style rates, then three towards and above the loop's capacity (saturation:
@@ -870,7 +870,7 @@ def serving_leg(args, H, W, np, torch, local):
     for k, rate in enumerate((20.0, 50.0, 100.0, 200.0, 1000.0, 4000.0, 16000.0)):
         reqs = []
         for i in range(args.serve_requests):
-            log_n, lv = (12, 2) if i % 4 == 0 else inst[i]
+            log_n, lv = (12, 2) if i % 2 == 0 else inst[i]
             m = models[log_n]
             z = np.zeros(m.n // 2)
             z[:64] = W.images(7000 + 100 * k + i, 1, 8, 8)[0].reshape(-1)

@@ -36,7 +36,7 @@ def make_requests(models, sks, count, seed):
     reqs, imgs = [], []
     inst = W.uneven_instances(count)
     for i in range(count):
-        log_n, lv = (12, 2) if i % 4 == 0 else inst[i]
+        log_n, lv = (12, 2) if i % 2 == 0 else inst[i]
         m = models[log_n]
         img = W.images(seed + i, 1, 8, 8)[0]
         z = np.zeros(m.n // 2)
