@@ -237,6 +237,48 @@ class OracleBench:
                 "textbook-NTT product mode, OpenMP over limbs" % n_ops)
 
 
+class OracleSchoolbookSlice:
+    """The oracle's schoolbook mode (the ring product by its definition, the
+    negacyclic convolution) on a labelled slice of one HMult+relin+rescale at
+    N = 2^16, L = 20: one limb product per host thread at once (OpenMP over
+    limbs), timed, and extrapolated to the operation's 252 limb products (the
+    tensor's 4 x 21, the key product's 2 x 3 digits x 28 limbs); the rest of
+    the operation (conversions, additions) is linear and not counted."""
+
+    PRODUCTS_PER_OP = 4 * 21 + 2 * 3 * 28
+
+    def run(self, log_n=None):
+        import math
+
+        import numpy as np
+
+        from oracle import _lib, ckks
+        from paper_2102_00319_gb300 import workloads as W
+
+        ps = W.DEEP_N16
+        op = ckks.Params(log_n or ps.log_n, list(ps.q_bits), list(ps.p_bits), ps.log2_scale)
+        threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        limbs = min(threads, len(op.q))
+        primes = np.array(op.q[:limbs], dtype=np.uint64)
+        rng = np.random.default_rng(0x2102_0031_9004)
+        a = np.stack([rng.integers(0, int(q), op.N, dtype=np.uint64) for q in primes])
+        b = np.stack([rng.integers(0, int(q), op.N, dtype=np.uint64) for q in primes])
+        L = _lib.lib()
+        mode = L.or_get_mode()
+        L.or_set_mode(0)
+        try:
+            t0 = time.perf_counter()
+            ckks.pmul(a, b, primes)
+            t = time.perf_counter() - t0
+        finally:
+            L.or_set_mode(mode)
+        per_op = math.ceil(self.PRODUCTS_PER_OP / limbs) * t
+        return {"value": 1.0 / per_op, "unit": UNIT, "cores": threads, "kind": "oracle",
+                "sample": "schoolbook mode: %d limb products of N = 2^%d at once (one per thread) in %.1f s, "
+                          "extrapolated to the %d limb products of one HMult+relin+rescale at L = 20"
+                          % (limbs, op.log_n, t, self.PRODUCTS_PER_OP)}
+
+
 class OracleCnnSlice:
     """The CPU oracle on a labelled slice of the N = 2^14 batch-packed CNN
     (8192 images): one conv output (25 tensor terms, relinearise, rescale),
@@ -1414,6 +1456,7 @@ def run_gpu(args, rank, world, local):
         dt = ob.run(args.cpu_ops)
         line["cpu_baseline"] = {"value": args.cpu_ops / dt, "unit": UNIT, "cores": ob.threads, "kind": "oracle",
                                 "sample": ob.sample(args.cpu_ops)}
+        line["cpu_baseline_schoolbook"] = OracleSchoolbookSlice().run()
         if not args.no_cnn:
             line["cpu_baseline_cnn"] = OracleCnnSlice().run()
     else:

@@ -143,3 +143,14 @@ def test_oracle_cnn_slice_extrapolates_the_batch(bench):
     want = 720 * t["conv_output"] + 720 * t["activation"] + 180 * t["pool_output"] + 10 * t["fc_class"]
     assert abs(r["extrapolated_batch_s"] - want) < 0.01 * want + 0.01
     assert r["unit"] == "images/s" and r["kind"] == "oracle" and abs(r["value"] - 8192 / r["extrapolated_batch_s"]) < 1e-6
+
+
+def test_schoolbook_slice_counts_the_operation_products(bench):
+    """The schoolbook-mode slice extrapolates to the tensor's 4 x 21 and the
+    key product's 2 x 3 x 28 limb products and restores the oracle's mode."""
+    from oracle import _lib
+    assert bench.OracleSchoolbookSlice.PRODUCTS_PER_OP == 252
+    mode = _lib.lib().or_get_mode()
+    r = bench.OracleSchoolbookSlice().run(log_n=10)
+    assert _lib.lib().or_get_mode() == mode
+    assert r["kind"] == "oracle" and r["value"] > 0 and "N = 2^10" in r["sample"] and "252" in r["sample"]
