@@ -241,11 +241,14 @@ class OracleSchoolbookSlice:
     """The oracle's schoolbook mode (the ring product by its definition, the
     negacyclic convolution) on a labelled slice of one HMult+relin+rescale at
     N = 2^16, L = 20: one limb product per host thread at once (OpenMP over
-    limbs), timed, and extrapolated to the operation's 252 limb products (the
-    tensor's 4 x 21, the key product's 2 x 3 digits x 28 limbs); the rest of
-    the operation (conversions, additions) is linear and not counted."""
+    limbs) at N = 2^14, timed, scaled by (2^16 / 2^14)^2 = 16 (a schoolbook
+    product costs N^2 multiply-adds) and extrapolated to the operation's 252
+    limb products (the tensor's 4 x 21, the key product's 2 x 3 digits x 28
+    limbs); the rest of the operation (conversions, additions) is linear and
+    not counted."""
 
     PRODUCTS_PER_OP = 4 * 21 + 2 * 3 * 28
+    LOG_N_TIMED = 14
 
     def run(self, log_n=None):
         import math
@@ -256,7 +259,8 @@ class OracleSchoolbookSlice:
         from paper_2102_00319_gb300 import workloads as W
 
         ps = W.DEEP_N16
-        op = ckks.Params(log_n or ps.log_n, list(ps.q_bits), list(ps.p_bits), ps.log2_scale)
+        op = ckks.Params(log_n or self.LOG_N_TIMED, list(ps.q_bits), list(ps.p_bits), ps.log2_scale)
+        scale_up = float(1 << (ps.log_n - op.log_n)) ** 2
         threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
         limbs = min(threads, len(op.q))
         primes = np.array(op.q[:limbs], dtype=np.uint64)
@@ -272,11 +276,12 @@ class OracleSchoolbookSlice:
             t = time.perf_counter() - t0
         finally:
             L.or_set_mode(mode)
-        per_op = math.ceil(self.PRODUCTS_PER_OP / limbs) * t
+        per_op = math.ceil(self.PRODUCTS_PER_OP / limbs) * t * scale_up
         return {"value": 1.0 / per_op, "unit": UNIT, "cores": threads, "kind": "oracle",
-                "sample": "schoolbook mode: %d limb products of N = 2^%d at once (one per thread) in %.1f s, "
-                          "extrapolated to the %d limb products of one HMult+relin+rescale at L = 20"
-                          % (limbs, op.log_n, t, self.PRODUCTS_PER_OP)}
+                "sample": "schoolbook mode: %d limb products of N = 2^%d at once (one per thread) in %.2f s, "
+                          "scaled by %g to N = 2^%d and extrapolated to the %d limb products of one "
+                          "HMult+relin+rescale at L = 20" % (limbs, op.log_n, t, scale_up, ps.log_n,
+                                                            self.PRODUCTS_PER_OP)}
 
 
 class OracleCnnSlice:
