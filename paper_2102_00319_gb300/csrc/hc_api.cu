@@ -1608,9 +1608,10 @@ std::vector<hc_ct*> rotate_batch(hc_ctx* ctx, const hc_evk* evk, const std::vect
 
 // Hoisted rotations of m ciphertexts at one level by every step in `steps`:
 // one ModUp of all the c1's, then the key product (reading the raised digits
-// through the automorphism), ModDown and the automorphism of c0, each one
-// launch over the (step, ciphertext) items of as many steps as the workspace
-// holds, every item with its own Galois element and key.  out[step][item];
+// through the automorphism) and ModDown (adding c0 read through the
+// automorphism), each one launch over the (step, ciphertext) items of as
+// many steps as the workspace holds, every item with its own Galois element
+// and key.  out[step][item];
 // the same words as m separate hoisted calls.
 std::vector<std::vector<hc_ct*>> rotate_hoisted_batch(hc_ctx* ctx, const hc_evk* evk,
                                                       const std::vector<const hc_ct*>& xs,
@@ -1635,14 +1636,14 @@ std::vector<std::vector<hc_ct*>> rotate_hoisted_batch(hc_ctx* ctx, const hc_evk*
   const size_t ext_words = (size_t)next * n;
   const int* emap = ctx->ext_map_of(level);
   const u64 x_is = (u64)nq * n, ext_is = (u64)dnum * ext_words, acc_is = 2 * (u64)ext_words,
-            z_is = 2 * (u64)nq * n, c0_is = (u64)nq * n;
+            z_is = 2 * (u64)nq * n;
   // the steps that rotate; groups of them share each launch after ModUp
   std::vector<int> rk;
   for (size_t k = 0; k < gs.size(); ++k) {
     if (gs[k] != 1) rk.push_back((int)k);
   }
   const size_t item_words = x_is + ext_is;                     // c1 in coefficient form, raised digits
-  const size_t step_words = acc_is + z_is + c0_is;             // per (step, item): key product .. kappa_g c0
+  const size_t step_words = acc_is + z_is;                     // per (step, item): key product, ModDown
   const size_t ws_words = kWorkspaceBytes / 8;
   const int chunk = (int)std::min<size_t>(256, std::max<size_t>(1, ws_words / (item_words + step_words)));
   for (int s0 = 0; s0 < total; s0 += chunk) {
@@ -1657,7 +1658,6 @@ std::vector<std::vector<hc_ct*>> rotate_hoisted_batch(hc_ctx* ctx, const hc_evk*
     u64* ext = xc + x_is * m;                 // [m][dnum][next][N]
     u64* acc = ext + ext_is * m;              // [sg][m][2][next][N]
     u64* zq = acc + acc_is * m * sg;          // [sg][m][2][nq][N]
-    u64* c0g = zq + z_is * m * sg;            // [sg][m][nq][N]
     std::vector<CtRef> c1s, c0s, xsr;
     for (int i = 0; i < m; ++i) {
       const hc_ct* x = xs[s0 + i];
@@ -1682,15 +1682,13 @@ std::vector<std::vector<hc_ct*>> rotate_hoisted_batch(hc_ctx* ctx, const hc_evk*
     }
     for (size_t r0 = 0; r0 < rk.size(); r0 += sg) {
       const int ns = (int)std::min<size_t>(sg, rk.size() - r0), mi = ns * m;  // items: (step, ciphertext)
-      std::vector<CtRef> c0src, c0d, od;
+      std::vector<CtRef> c0src, od;
       std::vector<const u64*> keys;
       std::vector<u64> gitem;
       for (int t = 0; t < ns; ++t) {
         const int k = rk[r0 + t];
         for (int i = 0; i < m; ++i) {
-          const size_t it = (size_t)t * m + i;
           c0src.push_back(c0s[i]);
-          c0d.push_back(CtRef{c0g + c0_is * it, 0});
           od.push_back(outs[k][s0 + i]->ref());
           keys.push_back(evk->galois.at(gs[k]).buf->ptr);
           gitem.push_back(gs[k]);
@@ -1698,7 +1696,6 @@ std::vector<std::vector<hc_ct*>> rotate_hoisted_batch(hc_ctx* ctx, const hc_evk*
       }
       const u64* gd = upload(ctx, gitem, keep);
       const u64* const* kd = ns > 1 ? upload(ctx, keys, keep) : nullptr;
-      const CtRef* c0d_r = refs_dev(ctx, c0d, keep);
       // the key product reads kappa_g of every raised digit in place (the
       // NTT-domain permutation is the same for every prime): item t m + i
       // uses ciphertext i's digits
@@ -1706,8 +1703,9 @@ std::vector<std::vector<hc_ct*>> rotate_hoisted_batch(hc_ctx* ctx, const hc_evk*
       launch_ntt(ctx, limbset_base(acc, acc_is, ext_words, 2, alpha, nq, emap), mi, true, false);
       launch_moddown_bconv_fast(ctx, level, acc + (size_t)nq * n, acc_is, zq, z_is, mi);
       launch_ntt(ctx, limbset_base(zq, z_is, (u64)nq * n, 2, nq, 0, nullptr), mi, false);
-      launch_automorph_items(ctx, c0d_r, refs_dev(ctx, c0src, keep), mi, 1, nq, gd);
-      launch_moddown_combine(ctx, level, acc, acc_is, zq, z_is, c0d_r, nullptr, refs_dev(ctx, od, keep), mi);
+      // out = kappa_g(c0) + ModDown(key product): c0 read through the automorphism
+      launch_moddown_combine(ctx, level, acc, acc_is, zq, z_is, refs_dev(ctx, c0src, keep), nullptr,
+                             refs_dev(ctx, od, keep), mi, gd);
     }
   }
   return outs;

@@ -275,9 +275,9 @@ void launch_moddown_bconv(hc_ctx* ctx, int level, const u64* accp_coef, u64 accp
                           u64* z, u64 z_item_stride, int items);
 // out_k = base_k + acc_k - z_k over Q_level (base may be null per k): ModDown
 // with P^{-1} already in acc's Q limbs (the keys) and in z (the constants).
-void launch_moddown_combine(hc_ctx* ctx, int level, const u64* acc, u64 acc_item_stride,
-                            const u64* z, u64 z_item_stride, const CtRef* base0,
-                            const CtRef* base1, const CtRef* out, int items);
+void launch_moddown_combine(hc_ctx* ctx, int level, const u64* acc, u64 acc_item_stride, const u64* z,
+                            u64 z_item_stride, const CtRef* base0, const CtRef* base1, const CtRef* out,
+                            int items, const u64* base0_gs = nullptr);  // base0 read through kappa_{gs[z]}
 // Rescale: lift[z][k][i] = centred(last[z][k]) mod q_i, i < level.
 void launch_rescale_lift(hc_ctx* ctx, int level, const u64* last, u64* lift, int items, int npoly);
 // out[z][k][i] = (in_i - lift_i) * q_level^{-1}.

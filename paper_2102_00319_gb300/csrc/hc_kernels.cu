@@ -406,9 +406,12 @@ __global__ void k_moddown_bconv(const u64* src, u64 src_item_stride, u64 src_pol
 
 // out_k = base_k + u_k - NTT(z_k): the key product's Q limbs u and the
 // conversion z both carry ModDown's P^{-1} already.
+// GATHER: base0 is read through item z's automorphism kappa_{gs[z]} (the
+// c0 of a hoisted rotation), so it needs no automorphed copy of its own.
+template <bool GATHER>
 __global__ void k_moddown_combine(const u64* acc, u64 acc_item_stride, u64 acc_poly_stride,
                                   const u64* zq, u64 z_item_stride, const CtRef* base0,
-                                  const CtRef* base1, const CtRef* out, int nq, Tables T) {
+                                  const CtRef* base1, const CtRef* out, int nq, const u64* gs, Tables T) {
   const int n = 1 << T.log_n;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
@@ -419,7 +422,13 @@ __global__ void k_moddown_combine(const u64* acc, u64 acc_item_stride, u64 acc_p
   const u64 zz = zq[(size_t)z * z_item_stride + (size_t)k * nq * n + li];
   u64 r = subm(u, zz, q);
   const CtRef* base = k == 0 ? base0 : base1;
-  if (base) r = addm(r, base[z].p[li], q);
+  if (base) {
+    size_t bi = li;
+    if constexpr (GATHER) {
+      if (k == 0) bi = (size_t)i * n + automorph_src(c, gs[z], T.log_n);
+    }
+    r = addm(r, base[z].p[bi], q);
+  }
   out[z].p[(size_t)k * out[z].stride + li] = r;
 }
 
@@ -703,12 +712,16 @@ void launch_moddown_bconv(hc_ctx* ctx, int level, const u64* accp_coef, u64 accp
 
 void launch_moddown_combine(hc_ctx* ctx, int level, const u64* acc, u64 acc_item_stride, const u64* z,
                             u64 z_item_stride, const CtRef* base0, const CtRef* base1, const CtRef* out,
-                            int items) {
+                            int items, const u64* base0_gs) {
   const int nq = level + 1, next = level + 1 + ctx->P.alpha;
     {
       ProfScope prof_(ctx, "k_moddown_combine", (uint64_t)items * 2 * nq);
-      k_moddown_combine<<<grid_for(ctx, 2 * nq, items), kT, 0, ctx->stream>>>(
-        acc, acc_item_stride, (u64)next * ctx->P.n, z, z_item_stride, base0, base1, out, nq, ctx->tab);
+      if (base0_gs)
+        k_moddown_combine<true><<<grid_for(ctx, 2 * nq, items), kT, 0, ctx->stream>>>(
+          acc, acc_item_stride, (u64)next * ctx->P.n, z, z_item_stride, base0, base1, out, nq, base0_gs, ctx->tab);
+      else
+        k_moddown_combine<false><<<grid_for(ctx, 2 * nq, items), kT, 0, ctx->stream>>>(
+          acc, acc_item_stride, (u64)next * ctx->P.n, z, z_item_stride, base0, base1, out, nq, nullptr, ctx->tab);
     }
   LAUNCH_DONE(ctx);
 }

@@ -58,7 +58,7 @@ def footprint_bytes(model: Model, level: int) -> int:
     outputs.  Plain rotations: kh*kw - 1 automorphed copies, each with a
     whole key-switch workspace (one batched key switch over the steps).
     Hoisted: one coefficient copy of c1 and its raised digits, then per step
-    the key product, ModDown's conversion and the automorphed c0."""
+    the key product and ModDown's conversion."""
     n, nq = model.n, level + 1
     alpha = model.n_special
     nxt = nq + alpha
@@ -70,7 +70,7 @@ def footprint_bytes(model: Model, level: int) -> int:
     outs = 3 * nq * limb + 2 * ct
     if model.hoisted:
         raised = (nq + dnum * nxt) * limb
-        per_step = (2 * nxt + 2 * nq + nq) * limb
+        per_step = (2 * nxt + 2 * nq) * limb
         return ct + rotated + raised + (taps - 1) * per_step + outs
     ks = (nq + dnum * nxt + 2 * nxt + 2 * nq + 2) * limb
     return ct + rotated + (taps - 1) * (ct + ks) + outs
