@@ -55,6 +55,8 @@ def parse():
                     help="device arena of the captured step (0: 4 GiB + 0.2 GiB per pair)")
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--e2e-chunk", type=int, default=0, help="pairs per pipeline chunk of the host call (0: auto)")
+    ap.add_argument("--e2e-inflight", type=int, default=2,
+                    help="evaluation-form host calls in flight at once (1: each call waits for its outputs)")
     ap.add_argument("--e2e-form", choices=("eval", "coeff"), default="eval",
                     help="host buffers in evaluation (NTT) form or coefficient form; the other form is timed briefly "
                          "for e2e_detail")
@@ -1294,11 +1296,17 @@ def run_gpu(args, rank, world, local):
         arr[...] = data
         host_in.append((pin, arr, meta))
     out_words = 2 * L * n
+    # calls in flight at once (evaluation form): each writes its own outputs
+    inflight = max(1, args.e2e_inflight) if eval_form else 1
     host_out = [torch.empty(out_words, dtype=torch.int64, pin_memory=True) for _ in range(Bn)]
+    host_out_more = [[torch.empty(out_words, dtype=torch.int64, pin_memory=True) for _ in range(Bn)]
+                     for _ in range(inflight - 1)]
     h2d = sum(a.nbytes for _, a, _ in host_in)
     d2h = Bn * out_words * 8
 
     out_arrays = [buf.numpy().view(np.uint64).reshape(2, L, n) for buf in host_out]
+    out_sets = [out_arrays] + [[buf.numpy().view(np.uint64).reshape(2, L, n) for buf in bufs]
+                               for bufs in host_out_more]
     in_arrays = [a for _, a, _ in host_in]
     in_metas = [(m.level, m.degree, m.scale) for _, _, m in host_in]
 
@@ -1330,22 +1338,42 @@ def run_gpu(args, rank, world, local):
         barrier()
         copy_gbs = {"h2d": h2d / c0.elapsed_time(c1) / 1e6, "d2h": d2h / c1.elapsed_time(c2) / 1e6}
         del staging
-    for _ in range(5 if args.e2e_steps > 0 else 0):  # untimed: the memory pool reaches its steady size
-        e2e_step()
+    def issue(k):
+        # an evaluation-form call left in flight (its wait comes later)
+        return H.hc_mul_relin_rescale_host_async(ctx, evk, in_arrays[:Bn], in_metas[:Bn], in_arrays[Bn:],
+                                                 in_metas[Bn:], out_sets[k % inflight], chunk=args.e2e_chunk)
+
+    for k in range(5 if args.e2e_steps > 0 else 0):  # untimed: the memory pool reaches its steady size
+        e2e_step() if inflight == 1 else issue(k).wait()
     barrier()
     t0 = time.perf_counter()
     e2e_marks = []  # each call returns with its outputs in host memory
     e2e_calls = []  # per call, from its event timeline: (copies in, kernels, device span) in ms
     slowest_tl = None
-    for _ in range(args.e2e_steps):
-        e2e_step()
+
+    def done():
         e2e_marks.append(time.perf_counter())
         tl = H.hc_profile_host_timeline(ctx)
         if tl:
             e2e_calls.append([round(tl[-1][1] - tl[0][0], 2), round(sum(c[3] - c[2] for c in tl), 2),
                               round(tl[-1][5], 2)])
             if e2e_calls[-1][2] >= max(c[2] for c in e2e_calls):  # the slowest call's chunks, to read outliers from
-                slowest_tl = [[round(v, 2) for v in c] for c in tl]
+                return [[round(v, 2) for v in c] for c in tl]
+        return None
+
+    pending = []
+    for k in range(args.e2e_steps):
+        if inflight == 1:
+            e2e_step()
+            slowest_tl = done() or slowest_tl
+            continue
+        pending.append(issue(k))
+        if len(pending) == inflight:  # the oldest call's outputs are in host memory when its wait returns
+            pending.pop(0).wait()
+            slowest_tl = done() or slowest_tl
+    for op in pending:
+        op.wait()
+        slowest_tl = done() or slowest_tl
     barrier()
     t_e2e = max_over_ranks(max(time.perf_counter() - t0, 1e-9), device="cuda")
     e2e_step_ms = [round(1000.0 * (b - a), 2) for a, b in zip([t0] + e2e_marks[:-1], e2e_marks)]
@@ -1424,7 +1452,8 @@ def run_gpu(args, rank, world, local):
         "config": bench_config(Bn, world),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": roofline, "cpu_baseline": None, "gpu_launches": launches, "clocks": clk,
-        "e2e_detail": {"form": args.e2e_form, "pinned_copy_gbs": copy_gbs, "step_ms": e2e_step_ms,
+        "e2e_detail": {"form": args.e2e_form, "calls_in_flight": inflight, "pinned_copy_gbs": copy_gbs,
+                       "step_ms": e2e_step_ms,
                        "step_ms_median": statistics.median(e2e_step_ms) if e2e_step_ms else None,
                        "step_ms_min_max": [min(e2e_step_ms), max(e2e_step_ms)] if e2e_step_ms else None,
                        "ops_per_s_at_median": Bn / statistics.median(e2e_step_ms) * 1000 if e2e_step_ms else None,

@@ -309,6 +309,22 @@ int hc_mul_relin_rescale_host_eval(hc_ctx *ctx, const hc_evk *evk, const uint64_
                                    const hc_ct_meta *a_meta, const uint64_t *const *b_host,
                                    const hc_ct_meta *b_meta, int n, int chunk, uint64_t *const *out_host,
                                    const size_t *out_cap, hc_ct_meta *out_meta);
+/* The evaluation-form call without waiting for it: the copies and kernels
+ * are enqueued (out_meta is written at once), *op receives a handle, and
+ * hc_host_op_wait(op) returns when every output is in host memory (with
+ * the call's result code: a residue >= its prime gives HC_ERR_INVALID
+ * there) and releases the handle.  Several calls on one context may be in
+ * flight at once, so that one call's copies in overlap the previous call's
+ * last kernels and copies out; host buffers must stay valid and unchanged
+ * until their call's wait returns.  Each handle is waited for exactly once;
+ * destroy the context only after every wait.  The call's timeline
+ * (hc_profile_host_timeline) is recorded by its wait. */
+typedef struct hc_host_op hc_host_op;
+int hc_mul_relin_rescale_host_eval_async(hc_ctx *ctx, const hc_evk *evk, const uint64_t *const *a_host,
+                                         const hc_ct_meta *a_meta, const uint64_t *const *b_host,
+                                         const hc_ct_meta *b_meta, int n, int chunk, uint64_t *const *out_host,
+                                         const size_t *out_cap, hc_ct_meta *out_meta, hc_host_op **op);
+int hc_host_op_wait(hc_host_op *op);
 
 /*
  * Relinearisation that allocates no device memory.  The paper has no

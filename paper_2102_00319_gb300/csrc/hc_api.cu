@@ -870,6 +870,7 @@ extern "C" void hc_ctx_destroy(hc_ctx* ctx) {
       cudaStreamSynchronize(st);
       cudaStreamDestroy(st);
     }
+  if (ctx->flag_stream) cudaStreamDestroy(ctx->flag_stream);
   delete ctx;
 }
 
@@ -2022,14 +2023,49 @@ std::vector<int> host_chunks(int n, int chunk) {
 // eval: host buffers in evaluation (NTT) form, so the chunks' inputs need no
 // forward transforms and the products keep the device batch's forward tail.
 namespace {
+// Waits for a host-to-host call's copies out, reads its range-check flags
+// on a stream of their own (the context's other streams may already carry
+// the next call), records its timeline and releases its buffers and events.
+int host_op_finish(hc_host_op* op_raw) {
+  std::unique_ptr<hc_host_op> op(op_raw);
+  hc_ctx* ctx = op->ctx;
+  const int rc = guard(ctx, [&] {
+    if (!op->drained) return;  // an empty call
+    HC_CUDA(cudaEventSynchronize(op->drained));
+    if (!ctx->flag_stream) HC_CUDA(cudaStreamCreateWithFlags(&ctx->flag_stream, cudaStreamNonBlocking));
+    std::vector<u64> bad(op->nch);
+    HC_CUDA(cudaStreamWaitEvent(ctx->flag_stream, op->drained, 0));
+    HC_CUDA(cudaMemcpyAsync(bad.data(), op->flags->ptr, op->nch * sizeof(u64), cudaMemcpyDeviceToHost,
+                            ctx->flag_stream));
+    HC_CUDA(cudaStreamSynchronize(ctx->flag_stream));
+    if (op->t_start) {
+      ctx->host_timeline.assign(op->tev.size(), 0.0);
+      for (size_t k = 0; k < op->tev.size(); ++k) {
+        float ms = 0;
+        HC_CUDA(cudaEventElapsedTime(&ms, op->t_start, op->tev[k]));
+        ctx->host_timeline[k] = ms;
+      }
+    }
+    for (u64 b : bad) HC_CHECK(b == 0, HC_ERR_INVALID, "input residue not below its prime (outputs not valid)");
+  });
+  op->flags.reset();
+  op->keep.clear();
+  for (cudaEvent_t e : op->evs) cudaEventDestroy(e);
+  return rc;
+}
+
 int host_pipeline(hc_ctx* ctx, const hc_evk* evk, const uint64_t* const* a_host, const hc_ct_meta* a_meta,
                   const uint64_t* const* b_host, const hc_ct_meta* b_meta, int n, int chunk,
-                  uint64_t* const* out_host, const size_t* out_cap, hc_ct_meta* out_meta, bool eval) {
+                  uint64_t* const* out_host, const size_t* out_cap, hc_ct_meta* out_meta, bool eval,
+                  hc_host_op** async_out) {
   if (!ctx) return HC_ERR_INVALID;
+  if (async_out) *async_out = nullptr;
   cudaStream_t h2d = nullptr, d2h = nullptr;
-  std::vector<cudaEvent_t> evs;
+  std::unique_ptr<hc_host_op> op(new hc_host_op);
+  op->ctx = ctx;
+  std::vector<cudaEvent_t>& evs = op->evs;
   std::vector<std::vector<hc_ct*>> ins;
-  std::vector<BufPtr> keep;  // released only after the side streams are drained
+  std::vector<BufPtr>& keep = op->keep;  // released only after the side streams are drained
   int rc = guard(ctx, [&] {
     HC_CHECK(evk && n >= 0 && (n == 0 || (a_host && b_host && a_meta && b_meta && out_host && out_cap && out_meta)),
              HC_ERR_INVALID, "null argument");
@@ -2069,7 +2105,7 @@ int host_pipeline(hc_ctx* ctx, const hc_evk* evk, const uint64_t* const* a_host,
     // timing events around each chunk's copies in, its kernels and its copies
     // out, relative to the call's start (read back by hc_profile_host_timeline)
     const bool tl = true;  // 48 events per call: cheap, and every call's timeline can be read back
-    std::vector<cudaEvent_t> tev;  // [chunk][h2d b, h2d e, compute b, compute e, d2h b, d2h e], then the start
+    std::vector<cudaEvent_t>& tev = op->tev;  // [chunk][h2d b, h2d e, compute b, compute e, d2h b, d2h e]
     auto tmark = [&](cudaStream_t st) -> cudaEvent_t {
       cudaEvent_t e;
       HC_CUDA(cudaEventCreate(&e));
@@ -2077,10 +2113,12 @@ int host_pipeline(hc_ctx* ctx, const hc_evk* evk, const uint64_t* const* a_host,
       HC_CUDA(cudaEventRecord(e, st));
       return e;
     };
-    cudaEvent_t t_start = tl ? tmark(ctx->stream) : nullptr;
+    op->t_start = tl ? tmark(ctx->stream) : nullptr;
     if (tl) tev.assign((size_t)6 * nch, nullptr);
     BufPtr flags = ctx->buffer(nch);
     keep.push_back(flags);
+    op->flags = flags;
+    op->nch = nch;
     HC_CUDA(cudaMemsetAsync(flags->ptr, 0, nch * sizeof(u64), ctx->stream));
     const size_t stride = (size_t)(level + 1) * N;  // one polynomial
     for (int c = 0; c < nch; ++c) ins.push_back(new_cts(ctx, 2 * sizes[c], level, 1, 1.0));  // a's, b's: one slab
@@ -2156,22 +2194,18 @@ int host_pipeline(hc_ctx* ctx, const hc_evk* evk, const uint64_t* const* a_host,
     }
     // (the context stream is restored at the end of every chunk)
     // staged buffers go back to the pool only after the copies out
-    const cudaEvent_t drained = event();
-    HC_CUDA(cudaEventRecord(drained, d2h));
-    HC_CUDA(cudaStreamWaitEvent(ctx->stream, drained, 0));
-    std::vector<u64> bad(nch);
-    HC_CUDA(cudaMemcpyAsync(bad.data(), flags->ptr, nch * sizeof(u64), cudaMemcpyDeviceToHost, ctx->stream));
-    HC_CUDA(cudaStreamSynchronize(ctx->stream));
-    if (tl) {
-      ctx->host_timeline.assign(tev.size(), 0.0);
-      for (size_t k = 0; k < tev.size(); ++k) {
-        float ms = 0;
-        HC_CUDA(cudaEventElapsedTime(&ms, t_start, tev[k]));
-        ctx->host_timeline[k] = ms;
-      }
-    }
-    for (u64 b : bad) HC_CHECK(b == 0, HC_ERR_INVALID, "input residue not below its prime (outputs not valid)");
+    op->drained = event();
+    HC_CUDA(cudaEventRecord(op->drained, d2h));
+    // a synchronous call orders the context stream after its copies out; an
+    // asynchronous one leaves it free, so that the next call's copies in can
+    // start while this call's last chunk still computes and copies out
+    if (!async_out) HC_CUDA(cudaStreamWaitEvent(ctx->stream, op->drained, 0));
   });
+  if (rc == HC_OK && async_out) {  // the caller waits with hc_host_op_wait
+    *async_out = op.release();
+    return HC_OK;
+  }
+  if (rc == HC_OK) return host_op_finish(op.release());
   // on an error the side streams may still be writing into inputs: drain them first
   if (h2d) cudaStreamSynchronize(h2d);
   if (d2h) cudaStreamSynchronize(d2h);
@@ -2188,14 +2222,34 @@ extern "C" int hc_mul_relin_rescale_host(hc_ctx* ctx, const hc_evk* evk, const u
                                          const hc_ct_meta* a_meta, const uint64_t* const* b_host,
                                          const hc_ct_meta* b_meta, int n, int chunk, uint64_t* const* out_host,
                                          const size_t* out_cap, hc_ct_meta* out_meta) {
-  return host_pipeline(ctx, evk, a_host, a_meta, b_host, b_meta, n, chunk, out_host, out_cap, out_meta, false);
+  return host_pipeline(ctx, evk, a_host, a_meta, b_host, b_meta, n, chunk, out_host, out_cap, out_meta, false,
+                       nullptr);
 }
 
 extern "C" int hc_mul_relin_rescale_host_eval(hc_ctx* ctx, const hc_evk* evk, const uint64_t* const* a_host,
                                               const hc_ct_meta* a_meta, const uint64_t* const* b_host,
                                               const hc_ct_meta* b_meta, int n, int chunk, uint64_t* const* out_host,
                                               const size_t* out_cap, hc_ct_meta* out_meta) {
-  return host_pipeline(ctx, evk, a_host, a_meta, b_host, b_meta, n, chunk, out_host, out_cap, out_meta, true);
+  return host_pipeline(ctx, evk, a_host, a_meta, b_host, b_meta, n, chunk, out_host, out_cap, out_meta, true,
+                       nullptr);
+}
+
+extern "C" int hc_mul_relin_rescale_host_eval_async(hc_ctx* ctx, const hc_evk* evk, const uint64_t* const* a_host,
+                                                    const hc_ct_meta* a_meta, const uint64_t* const* b_host,
+                                                    const hc_ct_meta* b_meta, int n, int chunk,
+                                                    uint64_t* const* out_host, const size_t* out_cap,
+                                                    hc_ct_meta* out_meta, hc_host_op** op) {
+  if (!ctx) return HC_ERR_INVALID;
+  if (!op) {
+    ctx->err = "null op";
+    return HC_ERR_INVALID;
+  }
+  return host_pipeline(ctx, evk, a_host, a_meta, b_host, b_meta, n, chunk, out_host, out_cap, out_meta, true, op);
+}
+
+extern "C" int hc_host_op_wait(hc_host_op* op) {
+  if (!op) return HC_ERR_INVALID;
+  return host_op_finish(op);
 }
 
 // =====================================================================

@@ -114,6 +114,7 @@ struct hc_ctx {
   // copy-in and copy-out streams of the host-to-host call, then its extra
   // compute streams (created on first use)
   cudaStream_t copy_streams[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaStream_t flag_stream = nullptr;  // reads a finished host call's range-check flags
   std::vector<cudaEvent_t> capture_events;
 
   u64* alloc_words(size_t words);
@@ -130,6 +131,19 @@ struct hc_pt {
   u64* data;  // [level+1][N], NTT form
   int level;
   double scale;
+};
+
+// A host-to-host call in flight (hc_mul_relin_rescale_host_eval_async): its
+// events, the buffers it still uses and its range-check flags.
+struct hc_host_op {
+  hc_ctx* ctx = nullptr;
+  std::vector<cudaEvent_t> evs;  // every event of the call (destroyed at the end)
+  std::vector<cudaEvent_t> tev;  // per chunk: copies in, kernels, copies out (begin, end)
+  cudaEvent_t t_start = nullptr;
+  cudaEvent_t drained = nullptr;  // the last copy out
+  std::vector<BufPtr> keep;
+  BufPtr flags;
+  int nch = 0;
 };
 
 struct hc_ct {

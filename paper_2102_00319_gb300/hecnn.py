@@ -46,6 +46,7 @@ EXPORTS = [
     "hc_relin_noalloc", "hc_graph_begin", "hc_graph_end", "hc_graph_launch", "hc_graph_destroy",
     "hc_enc_conv2d_single_batch", "hc_enc_conv2d_single_hoisted_batch", "hc_enc_fc_rotsum", "hc_ct_import_batch", "hc_ct_export_batch",
     "hc_mul_relin_rescale_host", "hc_mul_relin_rescale_host_eval", "hc_ct_export_eval", "hc_ct_import_eval",
+    "hc_mul_relin_rescale_host_eval_async", "hc_host_op_wait",
     "hc_autotune", "hc_tune_set", "hc_tune_get", "hc_int_mul_rates",
     "hc_enc_fc_partial", "hc_relin_rescale_batch", "hc_profile_host_timeline",
 ]
@@ -130,6 +131,11 @@ def load(path: str = LIB_PATH):
         "hc_mul_relin_rescale_host_eval": (c_int, [vp, vp, pp, ctypes.POINTER(CtMeta), pp, ctypes.POINTER(CtMeta),
                                                    c_int, c_int, pp, ctypes.POINTER(ctypes.c_size_t),
                                                    ctypes.POINTER(CtMeta)]),
+        "hc_mul_relin_rescale_host_eval_async": (c_int, [vp, vp, pp, ctypes.POINTER(CtMeta), pp,
+                                                         ctypes.POINTER(CtMeta), c_int, c_int, pp,
+                                                         ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(CtMeta),
+                                                         ctypes.POINTER(vp)]),
+        "hc_host_op_wait": (c_int, [vp]),
         "hc_ct_export_eval": (c_int, [vp, vp, ctypes.POINTER(u64), ctypes.c_size_t, ctypes.POINTER(CtMeta)]),
         "hc_ct_import_eval": (c_int, [vp, ctypes.POINTER(u64), ctypes.POINTER(CtMeta), pp]),
         "hc_ct_destroy": (None, [vp]),
@@ -535,6 +541,46 @@ def hc_mul_relin_rescale_host(ctx, evk, a_arrays, a_metas, b_arrays, b_metas, ou
     _check(ctx, fn(ctx.ptr, evk.ptr, ptrs(a_arrays), metas(a_metas), ptrs(b_arrays), metas(b_metas), n, int(chunk),
                    ptrs(out_arrays), caps, out_m))
     return [out_m[i] for i in range(n)]
+
+
+class HostOp:
+    """A host-to-host call in flight: keeps its buffers alive until wait()."""
+
+    def __init__(self, ctx, handle, keepalive, metas):
+        self.ctx, self.handle, self._keepalive, self.metas = ctx, handle, keepalive, metas
+
+    def wait(self):
+        """Returns the output metas once every output is in host memory."""
+        if self.handle is None:
+            return self.metas
+        h, self.handle = self.handle, None
+        _check(self.ctx, load().hc_host_op_wait(h))
+        self._keepalive = None
+        return self.metas
+
+
+def hc_mul_relin_rescale_host_async(ctx, evk, a_arrays, a_metas, b_arrays, b_metas, out_arrays, chunk=0):
+    """The evaluation-form host-to-host batch without waiting: returns a
+    HostOp whose wait() returns the output metas; the arrays must not be
+    touched before it."""
+    n = len(a_arrays)
+    if not (len(b_arrays) == len(a_metas) == len(b_metas) == len(out_arrays) == n):
+        raise ValueError("one entry per pair in every list")
+    for a, (lv, dg, _) in zip(list(a_arrays) + list(b_arrays), list(a_metas) + list(b_metas)):
+        if a.dtype != np.uint64 or not a.flags.c_contiguous or a.size != (dg + 1) * (lv + 1) * ctx.n:
+            raise ValueError("inputs must be C-contiguous uint64 of (degree+1)*(level+1)*N words")
+    if any(o.dtype != np.uint64 or not o.flags.c_contiguous or not o.flags.writeable for o in out_arrays):
+        raise ValueError("outputs must be writeable C-contiguous uint64 arrays")
+    ptr = lambda arrs: (ctypes.c_void_p * max(1, n))(*[x.ctypes.data for x in arrs])
+    meta = lambda ms: (CtMeta * max(1, n))(*[CtMeta(lv, dg, float(sc)) for lv, dg, sc in ms])
+    args = [ptr(a_arrays), meta(a_metas), ptr(b_arrays), meta(b_metas), ptr(out_arrays),
+            (ctypes.c_size_t * max(1, n))(*[o.size for o in out_arrays]), (CtMeta * max(1, n))()]
+    handle = ctypes.c_void_p()
+    _check(ctx, load().hc_mul_relin_rescale_host_eval_async(ctx.ptr, evk.ptr, args[0], args[1], args[2], args[3], n,
+                                                           int(chunk), args[4], args[5], args[6],
+                                                           ctypes.byref(handle)))
+    metas = [args[6][i] for i in range(n)]
+    return HostOp(ctx, handle.value, (list(a_arrays), list(b_arrays), list(out_arrays), args), metas)
 
 
 def hc_autotune(ctx, evk, items):

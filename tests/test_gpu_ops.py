@@ -128,8 +128,9 @@ def test_evaluation_form_host_call_and_export(pair):
     evaluation-form host-to-host call equals the device batch exported in
     that form, and its outputs, imported back and exported in coefficient
     form, equal the coefficient-form host call's words (which the oracle
-    pins elsewhere), for chunk sizes 2, automatic and a ragged 5; an
-    out-of-range residue is rejected by the import and by the call."""
+    pins elsewhere), for chunk sizes 2, automatic and a ragged 5, also with
+    three asynchronous calls in flight; an out-of-range residue is rejected
+    by the import, by the call and by an asynchronous call's wait."""
     op = pair.op
     lv, n = 3, 12
     ga = [pair.encrypt_values(W.slot_values(160 + i, op.K), level=lv, nonce=1600 + i)[0] for i in range(n)]
@@ -151,10 +152,24 @@ def test_evaluation_form_host_call_and_export(pair):
             assert (m.level, m.degree) == (lv - 1, 1)
             ct = H.hc_ct_import_eval(pair.ctx, o, m.level, m.degree, m.scale)
             np.testing.assert_array_equal(H.hc_ct_export(pair.ctx, ct)[0], c)
+    # three calls in flight at once (each with its own outputs), waited for in turn
+    sets = [[np.zeros((2, lv, op.N), dtype=np.uint64) for _ in range(n)] for _ in range(3)]
+    ops = [H.hc_mul_relin_rescale_host_async(pair.ctx, pair.g_evk, ea, a_m, eb, b_m, outs, chunk=chunk)
+           for outs, chunk in zip(sets, (2, 0, 5))]
+    for hop, outs in zip(ops, sets):
+        metas = hop.wait()
+        assert len(H.hc_profile_host_timeline(pair.ctx)) >= 1
+        for o, w, m in zip(outs, want, metas):
+            np.testing.assert_array_equal(o, w)
+            assert (m.level, m.degree) == (lv - 1, 1)
     bad = ea[4].copy()
     bad[1, 2, 7] = np.uint64(op.q[2])
     with pytest.raises(H.HcError):
         H.hc_ct_import_eval(pair.ctx, bad, lv, 1, 1.0)
+    hop = H.hc_mul_relin_rescale_host_async(pair.ctx, pair.g_evk, ea[:4] + [bad] + ea[5:], a_m, eb, b_m, sets[0],
+                                            chunk=2)
+    with pytest.raises(H.HcError):
+        hop.wait()
     outs = [np.zeros((2, lv, op.N), dtype=np.uint64) for _ in range(n)]
     with pytest.raises(H.HcError):
         H.hc_mul_relin_rescale_host(pair.ctx, pair.g_evk, ea[:4] + [bad] + ea[5:], a_m, eb, b_m, outs, chunk=2,
