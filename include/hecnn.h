@@ -316,7 +316,8 @@ int hc_mul_relin_rescale_host_eval(hc_ctx *ctx, const hc_evk *evk, const uint64_
  * there) and releases the handle.  Several calls on one context may be in
  * flight at once, so that one call's copies in overlap the previous call's
  * last kernels and copies out; host buffers must stay valid and unchanged
- * until their call's wait returns.  Each handle is waited for exactly once;
+ * until their call's wait returns.  chunk = 0 here means eighths of n from
+ * 32 pairs up (about n / 8 below).  Each handle is waited for exactly once;
  * destroy the context only after every wait.  The call's timeline
  * (hc_profile_host_timeline) is recorded by its wait. */
 typedef struct hc_host_op hc_host_op;
